@@ -1,0 +1,933 @@
+/*
+ * crmc_oracle.c -- plain, slow, FP64 CPU oracle for the charge-regulation
+ * Monte Carlo (CR-MC) stage of the hybrid MD/CR-MC method of Curk, Yuan and
+ * Luijten (arXiv:2109.07527), plus the MD forces and the Langevin
+ * velocity-Verlet step that consume the regulated charges.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header,
+ * table or constant generator with the CUDA path; it is compiled separately
+ * with plain gcc (-O2 -ffp-contract=off, no fast-math).
+ *
+ * What it follows (sections / equations of the paper):
+ *   - Sec. II.B, Eqs. (acid_new)-(salt_new): three generalised reactions
+ *     A <-> A- + X+,  B <-> B+ + X-,  0 <-> X+ + X-.
+ *   - Sec. II.C: six moves (forward/reverse of each reaction) proposed with
+ *     equal probability; participants drawn uniformly among the eligible
+ *     particles; no eligible particle -> automatic rejection.
+ *   - Sec. II.C, Eq. (QQ) and the acceptance rules Eqs. (acidacc), (MCmetro),
+ *     the base pair, (MCsaltf), (MCmetro2), written in log form.
+ *   - App. C, Eq. (pIXgen): 10^-pI_X = 10^-pI_S + 10^-min(pH, pOH).
+ *   - Eq. (LJe)/(LJ): WCA with an optional expanded distance Delta.
+ * Readings where the paper is silent (all stated in the design notes):
+ *   - The energy model is a damped-shifted-force (DSF) Coulomb cutoff sum plus
+ *     WCA (the paper uses PPPM), with the DSF self term.
+ *   - Moves are domain-local under an 8-colour checkerboard schedule: the
+ *     paired ion is inserted in / deleted from the trial's domain, and the
+ *     acceptance uses that domain's volume and counts.  The "global" schedule
+ *     (one domain = the whole box) is the paper's rule verbatim.
+ *   - pKw = 14 unless given; rho0 = 1 M; rho0*N_A = 0.602214076 nm^-3.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with the counter
+ *     layout documented at or_trial().
+ *
+ * Parity pins for every function are in tests/test_oracle_*.py (closed forms,
+ * exact enumeration, flux symmetry, known-answer vectors, invariants).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_NEUTRAL (-2)
+#define OR_ERR_CAPACITY (-4)
+#define OR_ERR_BOND (-6)
+#define OR_ERR_NOMEM (-8)
+
+enum { T_BEAD = 0, T_ACID = 1, T_BASE = 2, T_XP = 3, T_XM = 4, T_CORE = 5 };
+enum { R_ACID = 0, R_BASE = 1, R_SALT = 2 };
+enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
+#define CLS_NONE 3
+#define BIG_TERM 1048576.0 /* 2^20 kT: larger pair changes count as overlaps */
+
+/* Planted mistakes, used only by the tests that show the pins catch them. */
+enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
+       PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5 };
+
+/* ----------------------------------------------------------------------- */
+/* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
+ * 64-bit key bumped by the Weyl constants between rounds (Salmon et al.,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11). */
+static void philox(const uint32_t c_in[4], const uint32_t k_in[2], uint32_t out[4]) {
+  uint32_t c0 = c_in[0], c1 = c_in[1], c2 = c_in[2], c3 = c_in[3];
+  uint32_t k0 = k_in[0], k1 = k_in[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void or_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox(ctr, key, out); }
+
+/* integer in [0, n) from one 32-bit word: floor(w * n / 2^32) */
+static int64_t pick(uint32_t w, int64_t n) { return (int64_t)(((uint64_t)w * (uint64_t)n) >> 32); }
+
+/* uniform in (0,1) with 53 random bits from two words */
+static double unif53(uint32_t whi, uint32_t wlo) {
+  double a = (double)(whi >> 5), b = (double)(wlo >> 6);
+  return (a * 67108864.0 + b + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+/* ----------------------------------------------------------------------- */
+typedef struct {
+  int32_t n, capacity;
+  double box_L, sigma_nm;
+  double lB, rc, alpha;
+  int32_t dsf_self, ion_coupling, ion_cls;
+  double pH, pKw, pIS_plus, pIS_minus;
+  int32_t pIX_explicit;
+  double pIX_plus, pIX_minus;
+  int32_t nc, domain_cells, trials_per_domain, schedule, cells_per_rc;
+  double wca_eps[16], wca_sig[16], wca_del[16];
+  int32_t wca_on[16];
+  double fene_K, fene_R0;
+  int32_t n_bonds;
+} or_params;
+
+typedef struct {
+  int32_t move, flags;
+  uint64_t id_a, id_b;
+  double dE, S, lnA, lnu;
+} or_trial;
+
+typedef struct {
+  /* box, cells and schedule */
+  double L, a;
+  float Lf, scf;
+  int nc, k, nd, ncol, m, global;
+  /* energy model */
+  double lB, rc, alpha, phi_c1, phi_c2, self_coef;
+  int dsf_self, ion_coupling, ion_cls;
+  double eps[4][4], sig[4][4], del[4][4], wcut[4][4];
+  int on[4][4];
+  /* chemistry (log form) */
+  double pH, pOH, pIXp, pIXm, ln_z1, ln_salt;
+  int n_sites;
+  double *lnK; /* per site: ln10*(pH-pKa-pI_X+) for acids, ln10*(pOH-pKb-pI_X-) for bases */
+  int react[3], n_react;
+  /* particles */
+  int n, cap;
+  float *x, *y, *z;
+  int *type, *cls, *site, *st; /* st: 1 = ionised site */
+  uint64_t *id;
+  double *vx, *vy, *vz, *fx, *fy, *fz;
+  int f_valid;
+  /* bonds (by particle id, which is the input index for permanent particles) */
+  int nb;
+  int *bi, *bj;
+  double K, R0;
+  /* counters */
+  uint64_t sweep, md_evals;
+  int64_t stats[16];
+  int plant;
+} Oracle;
+
+static int g_plant = PLANT_NONE;
+void or_plant(int kind) { g_plant = kind; }
+
+static const double LN10 = 2.302585092994045684;
+static const double RHO0_NA = 0.602214076; /* 1 M in nm^-3 */
+
+/* DSF pair potential (Fennell & Gezelter 2006): phi(rc) = 0 and phi'(rc) = 0. */
+static double dsf_phi(const Oracle *o, double r) {
+  return erfc(o->alpha * r) / r - o->phi_c1 + o->phi_c2 * (r - o->rc);
+}
+/* -d phi / dr */
+static double dsf_force(const Oracle *o, double r) {
+  double ar = o->alpha * r;
+  return erfc(ar) / (r * r) + 2.0 * o->alpha / sqrt(M_PI) * exp(-ar * ar) / r - o->phi_c2;
+}
+
+/* WCA / expanded WCA, Eq. (LJe) with C = 1/4: s = r - Delta */
+static double wca_u(double eps, double sig, double s) {
+  double sr6 = pow(sig / s, 6.0);
+  return 4.0 * eps * (sr6 * sr6 - sr6) + eps;
+}
+static double wca_f(double eps, double sig, double s) { /* -dU/ds */
+  double sr6 = pow(sig / s, 6.0);
+  return 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / s;
+}
+
+double or_dsf_phi(double alpha, double rc, double r) {
+  Oracle o; memset(&o, 0, sizeof o);
+  o.alpha = alpha; o.rc = rc;
+  o.phi_c1 = erfc(alpha * rc) / rc;
+  o.phi_c2 = erfc(alpha * rc) / (rc * rc) + 2.0 * alpha / sqrt(M_PI) * exp(-alpha * alpha * rc * rc) / rc;
+  return dsf_phi(&o, r);
+}
+double or_dsf_force(double alpha, double rc, double r) {
+  Oracle o; memset(&o, 0, sizeof o);
+  o.alpha = alpha; o.rc = rc;
+  o.phi_c2 = erfc(alpha * rc) / (rc * rc) + 2.0 * alpha / sqrt(M_PI) * exp(-alpha * alpha * rc * rc) / rc;
+  return dsf_force(&o, r);
+}
+double or_wca_u(double eps, double sig, double del, double r) {
+  double s = r - del;
+  if (s >= pow(2.0, 1.0 / 6.0) * sig) return 0.0;
+  return wca_u(eps, sig, s);
+}
+
+static double min_image(double d, double L) { return d - L * nearbyint(d / L); }
+
+/* charge that enters the energy */
+static double qeff(const Oracle *o, int t, int ionised) {
+  switch (t) {
+    case T_ACID: return ionised ? -1.0 : 0.0;
+    case T_BASE: return ionised ? 1.0 : 0.0;
+    case T_XP: return o->ion_coupling ? 1.0 : 0.0;
+    case T_XM: return o->ion_coupling ? -1.0 : 0.0;
+    default: return 0.0;
+  }
+}
+static int qnom(int t, int ionised) {
+  switch (t) {
+    case T_ACID: return ionised ? -1 : 0;
+    case T_BASE: return ionised ? 1 : 0;
+    case T_XP: return 1;
+    case T_XM: return -1;
+    default: return 0;
+  }
+}
+
+/* cell of a coordinate: floor(fl32(x * (nc/L))) clamped; taken in FP32 on
+ * both sides because it decides an integer (which domain owns a particle). */
+static int cell_of(const Oracle *o, float x) {
+  float t = x * o->scf;
+  int c = (int)floorf(t);
+  if (c < 0) c = 0;
+  if (c >= o->nc) c = o->nc - 1;
+  return c;
+}
+
+/* domain index and canonical in-domain cell rank of a position, for offset off */
+static void domain_of(const Oracle *o, const int off[3], float x, float y, float z, int *dom, int *rank) {
+  int c[3] = {cell_of(o, x), cell_of(o, y), cell_of(o, z)};
+  int dd[3], ll[3];
+  for (int i = 0; i < 3; ++i) {
+    int s = ((c[i] - off[i]) % o->nc + o->nc) % o->nc;
+    dd[i] = s / o->k;
+    ll[i] = s % o->k;
+  }
+  *dom = dd[0] + o->nd * (dd[1] + o->nd * dd[2]);
+  *rank = ll[0] + o->k * (ll[1] + o->k * ll[2]);
+}
+
+/* ----------------------------------------------------------------------- */
+void or_destroy(Oracle *o) {
+  if (!o) return;
+  free(o->x); free(o->y); free(o->z); free(o->type); free(o->cls); free(o->site); free(o->st);
+  free(o->id); free(o->vx); free(o->vy); free(o->vz); free(o->fx); free(o->fy); free(o->fz);
+  free(o->lnK); free(o->bi); free(o->bj);
+  free(o);
+}
+
+/* pI of the grouped ion from the salt pI and the reservoir pH, Eq. (pIXgen) */
+static double pIX_of(double pIS, double pH, double pOH) {
+  double m = pH < pOH ? pH : pOH;
+  return -log10(pow(10.0, -pIS) + pow(10.0, -m));
+}
+
+Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, const int32_t *cls,
+                  const int8_t *state, const double *pK, const int32_t *bonds, const float *vel,
+                  int32_t *err) {
+  *err = OR_ERR_ARG;
+  if (p->n < 0 || p->capacity < p->n || p->box_L <= 0 || p->rc <= 0) return NULL;
+  Oracle *o = (Oracle *)calloc(1, sizeof(Oracle));
+  if (!o) { *err = OR_ERR_NOMEM; return NULL; }
+  o->Lf = (float)p->box_L;
+  o->L = (double)o->Lf;
+  o->lB = p->lB; o->rc = p->rc; o->alpha = p->alpha;
+  o->dsf_self = p->dsf_self; o->ion_coupling = p->ion_coupling; o->ion_cls = p->ion_cls;
+  if (2.0 * o->rc > o->L) { free(o); return NULL; }
+  o->phi_c1 = erfc(o->alpha * o->rc) / o->rc;
+  o->phi_c2 = erfc(o->alpha * o->rc) / (o->rc * o->rc) +
+              2.0 * o->alpha / sqrt(M_PI) * exp(-o->alpha * o->alpha * o->rc * o->rc) / o->rc;
+  o->self_coef = -(erfc(o->alpha * o->rc) / (2.0 * o->rc) + o->alpha / sqrt(M_PI));
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      o->eps[i][j] = p->wca_eps[4 * i + j];
+      o->sig[i][j] = p->wca_sig[4 * i + j];
+      o->del[i][j] = p->wca_del[4 * i + j];
+      o->on[i][j] = (i != CLS_NONE && j != CLS_NONE) ? p->wca_on[4 * i + j] : 0;
+      o->wcut[i][j] = o->del[i][j] + pow(2.0, 1.0 / 6.0) * o->sig[i][j];
+    }
+  /* cells and domains: cell side a >= rc/h; a domain is k^3 cells with
+   * k*a >= rc, so same-colour domains are at least rc apart.  Domain-local
+   * moves conserve each domain's net charge, so k >= 2 is what lets charge
+   * cross cell boundaries when the per-sweep offset re-partitions the box. */
+  int h = p->cells_per_rc > 0 ? p->cells_per_rc : 2;
+  int nc = p->nc > 0 ? p->nc : (int)floor(h * o->L / o->rc);
+  o->global = p->schedule == 1;
+  if (nc < 1) { free(o); return NULL; }
+  if (o->global) {
+    o->nc = nc; o->k = nc; o->nd = 1; o->ncol = 1;
+  } else {
+    int k = p->domain_cells > 0 ? p->domain_cells : h;
+    if (p->nc <= 0) nc = (nc / (2 * k)) * (2 * k);
+    if (nc < 2 * k || nc % (2 * k) != 0) { free(o); return NULL; }
+    o->nc = nc; o->k = k; o->nd = nc / k; o->ncol = 8;
+    if ((double)k * (o->L / nc) < o->rc) { free(o); return NULL; }
+  }
+  o->a = o->L / o->nc;
+  if (o->a * h < o->rc) { free(o); return NULL; }
+  o->scf = (float)((double)o->nc / o->L);
+  o->m = p->trials_per_domain > 0 ? p->trials_per_domain : 1;
+  /* chemistry */
+  o->pH = p->pH;
+  o->pOH = p->pKw - p->pH;
+  if (p->pIX_explicit) { o->pIXp = p->pIX_plus; o->pIXm = p->pIX_minus; }
+  else { o->pIXp = pIX_of(p->pIS_plus, o->pH, o->pOH); o->pIXm = pIX_of(p->pIS_minus, o->pH, o->pOH); }
+  double D = o->global ? o->L : o->k * o->a;
+  double v_nm3 = pow(D * p->sigma_nm, 3.0);
+  o->ln_z1 = log(RHO0_NA * v_nm3);
+  o->ln_salt = -LN10 * (o->pIXp + o->pIXm);
+  /* particles */
+  o->n = p->n; o->cap = p->capacity;
+  size_t C = (size_t)(o->cap > 0 ? o->cap : 1);
+  o->x = malloc(C * sizeof(float)); o->y = malloc(C * sizeof(float)); o->z = malloc(C * sizeof(float));
+  o->type = malloc(C * sizeof(int)); o->cls = malloc(C * sizeof(int)); o->site = malloc(C * sizeof(int));
+  o->st = malloc(C * sizeof(int)); o->id = malloc(C * sizeof(uint64_t));
+  o->vx = calloc(C, sizeof(double)); o->vy = calloc(C, sizeof(double)); o->vz = calloc(C, sizeof(double));
+  o->fx = calloc(C, sizeof(double)); o->fy = calloc(C, sizeof(double)); o->fz = calloc(C, sizeof(double));
+  int ns = 0, nA = 0, nB = 0;
+  for (int i = 0; i < p->n; ++i) if (type[i] == T_ACID || type[i] == T_BASE) ns++;
+  o->lnK = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(double));
+  int qsum = 0;
+  ns = 0;
+  for (int i = 0; i < p->n; ++i) {
+    float X = xyz[3 * i], Y = xyz[3 * i + 1], Z = xyz[3 * i + 2];
+    if (!(X >= 0.0f && X < o->Lf && Y >= 0.0f && Y < o->Lf && Z >= 0.0f && Z < o->Lf)) { or_destroy(o); return NULL; }
+    if (type[i] < 0 || type[i] > T_CORE || cls[i] < 0 || cls[i] > 3) { or_destroy(o); return NULL; }
+    o->x[i] = X; o->y[i] = Y; o->z[i] = Z;
+    o->type[i] = type[i];
+    o->cls[i] = (type[i] == T_XP || type[i] == T_XM) ? (o->ion_coupling ? o->ion_cls : CLS_NONE) : cls[i];
+    o->id[i] = (uint64_t)i;
+    o->site[i] = -1;
+    o->st[i] = 0;
+    if (type[i] == T_ACID || type[i] == T_BASE) {
+      o->site[i] = ns;
+      o->st[i] = state[i] ? 1 : 0;
+      if (type[i] == T_ACID) { o->lnK[ns] = LN10 * ((o->pH - pK[i]) - o->pIXp); nA++; }
+      else { o->lnK[ns] = LN10 * ((o->pOH - pK[i]) - o->pIXm); nB++; }
+      ns++;
+    }
+    qsum += qnom(type[i], o->st[i]);
+    if (vel) { o->vx[i] = vel[3 * i]; o->vy[i] = vel[3 * i + 1]; o->vz[i] = vel[3 * i + 2]; }
+  }
+  o->n_sites = ns;
+  if (qsum != 0) { or_destroy(o); *err = OR_ERR_NEUTRAL; return NULL; }
+  o->n_react = 0;
+  if (nA > 0) o->react[o->n_react++] = R_ACID;
+  if (nB > 0) o->react[o->n_react++] = R_BASE;
+  o->react[o->n_react++] = R_SALT;
+  /* bonds */
+  o->nb = p->n_bonds; o->K = p->fene_K; o->R0 = p->fene_R0;
+  o->bi = malloc((size_t)(o->nb > 0 ? o->nb : 1) * sizeof(int));
+  o->bj = malloc((size_t)(o->nb > 0 ? o->nb : 1) * sizeof(int));
+  for (int b = 0; b < o->nb; ++b) {
+    int i = bonds[2 * b], j = bonds[2 * b + 1];
+    if (i < 0 || j < 0 || i >= p->n || j >= p->n || type[i] == T_XP || type[i] == T_XM ||
+        type[j] == T_XP || type[j] == T_XM) { or_destroy(o); return NULL; }
+    o->bi[b] = i; o->bj[b] = j;
+  }
+  o->plant = g_plant;
+  *err = OR_OK;
+  return o;
+}
+
+/* ----------------------------------------------------------------------- */
+/* Energy of one pair in a given state.  qi, qj are effective charges. */
+static double pair_u(const Oracle *o, double qi, int ci, double qj, int cj, double r, int *overlap,
+                     int check_hard) {
+  double u = 0.0;
+  if (r < o->rc && qi != 0.0 && qj != 0.0) u += o->lB * qi * qj * dsf_phi(o, r);
+  if (o->on[ci][cj] && r < o->wcut[ci][cj]) {
+    double s = r - o->del[ci][cj];
+    if (check_hard && s < 0.5 * o->sig[ci][cj]) { *overlap = 1; return 0.0; }
+    u += wca_u(o->eps[ci][cj], o->sig[ci][cj], s);
+  }
+  return u;
+}
+
+typedef struct {
+  int idx;              /* index of an existing particle, -1 for an inserted one */
+  float x, y, z;
+  int cls;
+  double q_old, q_new;  /* effective charges in the old / new state */
+  int pres_old, pres_new;
+} change_t;
+
+static double dist(const Oracle *o, float ax, float ay, float az, float bx, float by, float bz) {
+  double dx = min_image((double)ax - (double)bx, o->L);
+  double dy = min_image((double)ay - (double)by, o->L);
+  double dz = min_image((double)az - (double)bz, o->L);
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* Delta E = E_new - E_old, summed pair by pair over every pair that contains a
+ * changed particle, plus the DSF self-energy change.  S = sum of |pair
+ * changes|, the scale for the FP32 tolerance. */
+static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, double *S_out) {
+  double dE = 0.0, S = 0.0;
+  *overlap = 0;
+  for (int a = 0; a < nc; ++a) {
+    for (int j = 0; j < o->n; ++j) {
+      int skip = 0;
+      for (int b = 0; b < nc; ++b) if (c[b].idx == j) skip = 1;
+      if (skip) continue;
+      double qj = qeff(o, o->type[j], o->st[j]);
+      double r = dist(o, c[a].x, c[a].y, c[a].z, o->x[j], o->y[j], o->z[j]);
+      int ov = 0;
+      double un = c[a].pres_new ? pair_u(o, c[a].q_new, c[a].cls, qj, o->cls[j], r, &ov, !c[a].pres_old) : 0.0;
+      double uo = c[a].pres_old ? pair_u(o, c[a].q_old, c[a].cls, qj, o->cls[j], r, &ov, 0) : 0.0;
+      double du = un - uo;
+      if (ov || !(fabs(du) < BIG_TERM)) { *overlap = 1; continue; }
+      dE += du;
+      S += fabs(du);
+    }
+  }
+  /* pairs among the changed particles themselves */
+  if (g_plant != PLANT_DROP_PAIR_CC) {
+    for (int a = 0; a < nc; ++a)
+      for (int b = a + 1; b < nc; ++b) {
+        double r = dist(o, c[a].x, c[a].y, c[a].z, c[b].x, c[b].y, c[b].z);
+        int ov = 0;
+        int hard = (c[a].pres_new && !c[a].pres_old) || (c[b].pres_new && !c[b].pres_old);
+        double un = (c[a].pres_new && c[b].pres_new) ? pair_u(o, c[a].q_new, c[a].cls, c[b].q_new, c[b].cls, r, &ov, hard) : 0.0;
+        double uo = (c[a].pres_old && c[b].pres_old) ? pair_u(o, c[a].q_old, c[a].cls, c[b].q_old, c[b].cls, r, &ov, 0) : 0.0;
+        double du = un - uo;
+        if (ov || !(fabs(du) < BIG_TERM)) { *overlap = 1; continue; }
+        dE += du;
+        S += fabs(du);
+      }
+  }
+  if (o->dsf_self && g_plant != PLANT_DROP_SELF) {
+    for (int a = 0; a < nc; ++a) {
+      double ds = o->lB * o->self_coef *
+                  ((c[a].pres_new ? c[a].q_new * c[a].q_new : 0.0) - (c[a].pres_old ? c[a].q_old * c[a].q_old : 0.0));
+      dE += ds;
+      S += fabs(ds);
+    }
+  }
+  *S_out = S;
+  return dE;
+}
+
+/* kind of a particle for the eligibility lists */
+enum { K_A0 = 0, K_A1 = 1, K_B0 = 2, K_B1 = 3, K_XP = 4, K_XM = 5, K_OTHER = 6 };
+static int kind_of(const Oracle *o, int j) {
+  switch (o->type[j]) {
+    case T_ACID: return o->st[j] ? K_A1 : K_A0;
+    case T_BASE: return o->st[j] ? K_B1 : K_B0;
+    case T_XP: return K_XP;
+    case T_XM: return K_XM;
+    default: return K_OTHER;
+  }
+}
+
+typedef struct { int rank; uint64_t id; int idx; } elig_t;
+static int elig_cmp(const void *pa, const void *pb) {
+  const elig_t *a = pa, *b = pb;
+  if (a->rank != b->rank) return a->rank < b->rank ? -1 : 1;
+  if (a->id != b->id) return a->id < b->id ? -1 : 1;
+  return 0;
+}
+
+/* index of the k-th particle of a kind in domain d, in canonical order:
+ * in-domain cells in (z, y, x) order, then ascending id within a cell */
+static int kth_eligible(const Oracle *o, const int off[3], int d, int kind, int64_t kth, elig_t *buf) {
+  int cnt = 0;
+  for (int j = 0; j < o->n; ++j) {
+    if (kind_of(o, j) != kind) continue;
+    int dom, rank;
+    domain_of(o, off, o->x[j], o->y[j], o->z[j], &dom, &rank);
+    if (dom != d) continue;
+    buf[cnt].rank = rank; buf[cnt].id = o->id[j]; buf[cnt].idx = j; cnt++;
+  }
+  qsort(buf, (size_t)cnt, sizeof(elig_t), elig_cmp);
+  if (kth < 0 || kth >= cnt) return -1;
+  return buf[kth].idx;
+}
+
+static void domain_counts(const Oracle *o, const int off[3], int d, int64_t cnt[7]) {
+  for (int i = 0; i < 7; ++i) cnt[i] = 0;
+  for (int j = 0; j < o->n; ++j) {
+    int dom, rank;
+    domain_of(o, off, o->x[j], o->y[j], o->z[j], &dom, &rank);
+    if (dom == d) cnt[kind_of(o, j)]++;
+  }
+}
+
+/* insertion coordinate: u = c0 + k*f (exact), wrapped into [0, nc), times the
+ * cell side, rounded once to FP32; f carries the top 24 bits of w */
+static float insert_coord(const Oracle *o, int c0, uint32_t w) {
+  double f = (double)(w >> 8) * (1.0 / 16777216.0);
+  double u = (double)c0 + (double)o->k * f;
+  if (u >= (double)o->nc) u -= (double)o->nc;
+  double xd = u * o->a;
+  float xf = (float)xd;
+  if (xf >= o->Lf) xf -= o->Lf;
+  return xf;
+}
+
+static void remove_particle(Oracle *o, int j) {
+  int last = o->n - 1;
+  if (j != last) {
+    o->x[j] = o->x[last]; o->y[j] = o->y[last]; o->z[j] = o->z[last];
+    o->type[j] = o->type[last]; o->cls[j] = o->cls[last]; o->site[j] = o->site[last];
+    o->st[j] = o->st[last]; o->id[j] = o->id[last];
+    o->vx[j] = o->vx[last]; o->vy[j] = o->vy[last]; o->vz[j] = o->vz[last];
+    o->fx[j] = o->fx[last]; o->fy[j] = o->fy[last]; o->fz[j] = o->fz[last];
+  }
+  o->n--;
+}
+
+static int add_ion(Oracle *o, int t, float x, float y, float z, uint64_t id) {
+  if (o->n >= o->cap) return OR_ERR_CAPACITY;
+  int j = o->n++;
+  o->x[j] = x; o->y[j] = y; o->z[j] = z;
+  o->type[j] = t; o->cls[j] = o->ion_coupling ? o->ion_cls : CLS_NONE;
+  o->site[j] = -1; o->st[j] = 0; o->id[j] = id;
+  o->vx[j] = o->vy[j] = o->vz[j] = 0.0;
+  o->fx[j] = o->fy[j] = o->fz[j] = 0.0;
+  return OR_OK;
+}
+
+static int net_charge(const Oracle *o) {
+  int q = 0;
+  for (int j = 0; j < o->n; ++j) q += qnom(o->type[j], o->st[j]);
+  return q;
+}
+
+/* One trial (phase phi, domain d, trial k in the domain).
+ * Philox key = (seed_lo, seed_hi); counters (k, d, phi, purpose):
+ *   purpose 0 -> w0 move, w1 site choice, w2 first ion choice, w3 second ion choice
+ *   purpose 1 -> w0..w2 position of ion A, w3 x of ion B
+ *   purpose 2 -> w0, w1 y, z of ion B; w2, w3 the Metropolis uniform
+ * New ion ids: (phi+1) << 32 | 2*(d*m + k) + b, b = 0 (ion A / X+) or 1 (X-). */
+static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint32_t phi, int d, int k,
+                        or_trial *rec, int forced, elig_t *buf, int64_t *hist, int hist_n,
+                        int64_t *trans) {
+  uint32_t c0[4] = {(uint32_t)k, (uint32_t)d, phi, 0u}, c1[4] = {(uint32_t)k, (uint32_t)d, phi, 1u},
+           c2[4] = {(uint32_t)k, (uint32_t)d, phi, 2u};
+  uint32_t P0[4], P1[4], P2[4];
+  philox(c0, key, P0); philox(c1, key, P1); philox(c2, key, P2);
+  int mv = (int)pick(P0[0], 2 * o->n_react);
+  int r = o->react[mv >> 1];
+  int fwd = (mv & 1) == 0;
+  or_trial t;
+  t.move = 2 * r + (fwd ? 0 : 1);
+  t.flags = 0; t.id_a = UINT64_MAX; t.id_b = UINT64_MAX;
+  t.dE = 0.0; t.S = 0.0; t.lnA = -INFINITY;
+  t.lnu = log(unif53(P2[2], P2[3]));
+  o->stats[t.move]++;
+
+  int64_t cnt[7];
+  domain_counts(o, off, d, cnt);
+  /* origin cell of the domain and the two candidate insertion points */
+  int dd[3] = {d % o->nd, (d / o->nd) % o->nd, d / (o->nd * o->nd)};
+  int org[3];
+  for (int i = 0; i < 3; ++i) org[i] = (off[i] + dd[i] * o->k) % o->nc;
+  float pa[3] = {insert_coord(o, org[0], P1[0]), insert_coord(o, org[1], P1[1]), insert_coord(o, org[2], P1[2])};
+  float pb[3] = {insert_coord(o, org[0], P1[3]), insert_coord(o, org[1], P2[0]), insert_coord(o, org[2], P2[1])};
+  uint64_t base = ((uint64_t)(phi + 1u) << 32);
+  uint64_t idA = base | (uint64_t)(uint32_t)(2u * ((uint32_t)d * (uint32_t)o->m + (uint32_t)k));
+  uint64_t idB = idA + 1u;
+
+  change_t ch[2];
+  int nch = 0;
+  int site = -1, ionA = -1, ionB = -1;
+  double ln_ratio = 0.0; /* log of the combinatorial / chemical factor */
+  int noelig = 0, edge = 0;
+  double lnz = o->ln_z1;
+  if (g_plant == PLANT_WRONG_VOLUME) lnz += 1.0;
+  if (r == R_ACID || r == R_BASE) {
+    int k0 = r == R_ACID ? K_A0 : K_B0, k1 = r == R_ACID ? K_A1 : K_B1;
+    int kx = r == R_ACID ? K_XP : K_XM;
+    double qs = r == R_ACID ? -1.0 : 1.0;
+    if (fwd) {
+      if (cnt[k0] == 0) noelig = 1;
+      else {
+        site = kth_eligible(o, off, d, k0, pick(P0[1], cnt[k0]), buf);
+        int dom, rank;
+        domain_of(o, off, pa[0], pa[1], pa[2], &dom, &rank);
+        if (dom != d) edge = 1;
+        t.id_a = o->id[site]; t.id_b = idA;
+        ch[0] = (change_t){site, o->x[site], o->y[site], o->z[site], o->cls[site], 0.0, qs, 1, 1};
+        ch[1] = (change_t){-1, pa[0], pa[1], pa[2], o->ion_coupling ? o->ion_cls : CLS_NONE, 0.0,
+                           o->ion_coupling ? -qs : 0.0, 0, 1};
+        nch = 2;
+        ln_ratio = log((double)cnt[k0]) + lnz - log((double)(cnt[k1] + 1));
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt[kx] + 1));
+        ln_ratio += o->lnK[o->site[site]];
+      }
+    } else {
+      if (cnt[k1] == 0 || cnt[kx] == 0) noelig = 1;
+      else {
+        site = kth_eligible(o, off, d, k1, pick(P0[1], cnt[k1]), buf);
+        ionA = kth_eligible(o, off, d, kx, pick(P0[2], cnt[kx]), buf);
+        t.id_a = o->id[site]; t.id_b = o->id[ionA];
+        ch[0] = (change_t){site, o->x[site], o->y[site], o->z[site], o->cls[site], qs, 0.0, 1, 1};
+        ch[1] = (change_t){ionA, o->x[ionA], o->y[ionA], o->z[ionA], o->cls[ionA],
+                           qeff(o, o->type[ionA], 0), 0.0, 1, 0};
+        nch = 2;
+        ln_ratio = log((double)cnt[k1]) - log((double)(cnt[k0] + 1)) - lnz;
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt[kx]);
+        ln_ratio -= o->lnK[o->site[site]];
+      }
+    }
+  } else { /* salt */
+    if (fwd) {
+      int dom, rank;
+      domain_of(o, off, pa[0], pa[1], pa[2], &dom, &rank);
+      if (dom != d) edge = 1;
+      domain_of(o, off, pb[0], pb[1], pb[2], &dom, &rank);
+      if (dom != d) edge = 1;
+      t.id_a = idA; t.id_b = idB;
+      int icls = o->ion_coupling ? o->ion_cls : CLS_NONE;
+      ch[0] = (change_t){-1, pa[0], pa[1], pa[2], icls, 0.0, o->ion_coupling ? 1.0 : 0.0, 0, 1};
+      ch[1] = (change_t){-1, pb[0], pb[1], pb[2], icls, 0.0, o->ion_coupling ? -1.0 : 0.0, 0, 1};
+      nch = 2;
+      ln_ratio = 2.0 * lnz + o->ln_salt;
+      if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt[K_XP] + 1)) + log((double)(cnt[K_XM] + 1));
+    } else {
+      if (cnt[K_XP] == 0 || cnt[K_XM] == 0) noelig = 1;
+      else {
+        ionA = kth_eligible(o, off, d, K_XP, pick(P0[2], cnt[K_XP]), buf);
+        ionB = kth_eligible(o, off, d, K_XM, pick(P0[3], cnt[K_XM]), buf);
+        t.id_a = o->id[ionA]; t.id_b = o->id[ionB];
+        ch[0] = (change_t){ionA, o->x[ionA], o->y[ionA], o->z[ionA], o->cls[ionA], qeff(o, T_XP, 0), 0.0, 1, 0};
+        ch[1] = (change_t){ionB, o->x[ionB], o->y[ionB], o->z[ionB], o->cls[ionB], qeff(o, T_XM, 0), 0.0, 1, 0};
+        nch = 2;
+        ln_ratio = -2.0 * lnz - o->ln_salt;
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt[K_XP]) + log((double)cnt[K_XM]);
+      }
+    }
+  }
+  int accept = 0;
+  if (noelig) t.flags |= F_NOELIG;
+  else if (edge) t.flags |= F_EDGE;
+  else {
+    int ov = 0;
+    double S = 0.0;
+    double dE = delta_E(o, ch, nch, &ov, &S);
+    if (g_plant == PLANT_DE_SIGN) dE = -dE;
+    t.S = S;
+    if (ov) { t.flags |= F_OVERLAP; t.dE = INFINITY; }
+    else {
+      t.dE = dE;
+      t.lnA = ln_ratio - dE;
+      accept = t.lnu < t.lnA;
+    }
+  }
+  if (forced >= 0 && !(t.flags & (F_NOELIG | F_EDGE | F_OVERLAP))) accept = forced;
+  if (accept) {
+    t.flags |= F_ACC;
+    o->stats[6 + t.move]++;
+    o->f_valid = 0;
+    int s_before = 0;
+    if (hist_n > 0) for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0 && o->site[j] < hist_n && o->st[j]) s_before |= 1 << o->site[j];
+    if (r == R_ACID || r == R_BASE) {
+      if (fwd) {
+        o->st[site] = 1;
+        if (add_ion(o, r == R_ACID ? T_XP : T_XM, pa[0], pa[1], pa[2], idA)) return OR_ERR_CAPACITY;
+      } else {
+        o->st[site] = 0;
+        remove_particle(o, ionA);
+      }
+    } else {
+      if (fwd) {
+        if (add_ion(o, T_XP, pa[0], pa[1], pa[2], idA)) return OR_ERR_CAPACITY;
+        if (add_ion(o, T_XM, pb[0], pb[1], pb[2], idB)) return OR_ERR_CAPACITY;
+      } else {
+        int hi = ionA > ionB ? ionA : ionB, lo = ionA > ionB ? ionB : ionA;
+        remove_particle(o, hi);
+        remove_particle(o, lo);
+      }
+    }
+    if (trans && (r == R_ACID || r == R_BASE) && o->site[site] < hist_n) {
+      int s_after = s_before ^ (1 << o->site[site]);
+      trans[(int64_t)s_before * hist_n + o->site[site]]++;
+      (void)s_after;
+    }
+  }
+  if (hist && hist_n > 0) {
+    int s = 0;
+    for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0 && o->site[j] < hist_n && o->st[j]) s |= 1 << o->site[j];
+    hist[s]++;
+  }
+  if (rec) *rec = t;
+  if (net_charge(o) != 0) return OR_ERR_NEUTRAL;
+  return OR_OK;
+}
+
+int64_t or_trials_per_sweep(const Oracle *o) {
+  return (int64_t)o->nd * o->nd * o->nd * o->m;
+}
+
+/* Run n_trials (a multiple of the trials per sweep).  Sweeps continue the
+ * context's sweep counter.  log: one record per trial in schedule order
+ * (colour phases in order, domains ascending, trials in the domain).
+ * forced: optional per-trial decision override (-1 = none) used only to step
+ * over a tie at the acceptance threshold.  hist/trans: optional state
+ * histogram over the first hist_n sites and site-flip transition counts. */
+int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, const int8_t *forced,
+                 int64_t *hist, int32_t hist_n, int64_t *trans) {
+  int64_t per = or_trials_per_sweep(o);
+  if (n_trials < 0 || n_trials % per != 0) return OR_ERR_ARG;
+  if (hist_n < 0 || hist_n > 20) return OR_ERR_ARG;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  elig_t *buf = malloc((size_t)(o->cap > 0 ? o->cap : 1) * sizeof(elig_t));
+  int64_t t = 0;
+  int rc = OR_OK;
+  for (int64_t sw = 0; sw < n_trials / per && rc == OR_OK; ++sw) {
+    uint64_t s = o->sweep++;
+    int off[3] = {0, 0, 0};
+    if (!o->global) {
+      uint32_t c[4] = {0u, 0u, (uint32_t)s, 4u}, w[4];
+      philox(c, key, w);
+      for (int i = 0; i < 3; ++i) off[i] = (int)pick(w[i], o->nc);
+    }
+    for (int col = 0; col < o->ncol && rc == OR_OK; ++col) {
+      uint32_t phi = (uint32_t)(s * (uint64_t)o->ncol + (uint64_t)col);
+      int ndom = o->nd * o->nd * o->nd;
+      for (int d = 0; d < ndom && rc == OR_OK; ++d) {
+        int dx = d % o->nd, dy = (d / o->nd) % o->nd, dz = d / (o->nd * o->nd);
+        int colour = o->global ? 0 : ((dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2));
+        if (colour != col) continue;
+        for (int k = 0; k < o->m && rc == OR_OK; ++k, ++t) {
+          int f = forced ? forced[t] : -1;
+          rc = or_trial_one(o, key, off, phi, d, k, log ? &log[t] : NULL, f, buf, hist, hist_n, trans);
+        }
+      }
+    }
+  }
+  free(buf);
+  return rc;
+}
+
+/* counts: [n_A, n_A-, n_B, n_B+, n_X+, n_X-, n, net charge] */
+void or_counts(const Oracle *o, int64_t *out) {
+  int64_t c[8] = {0};
+  for (int j = 0; j < o->n; ++j) {
+    switch (o->type[j]) {
+      case T_ACID: c[0]++; if (o->st[j]) c[1]++; break;
+      case T_BASE: c[2]++; if (o->st[j]) c[3]++; break;
+      case T_XP: c[4]++; break;
+      case T_XM: c[5]++; break;
+      default: break;
+    }
+  }
+  c[6] = o->n;
+  c[7] = net_charge(o);
+  memcpy(out, c, sizeof c);
+}
+
+void or_stats(const Oracle *o, int64_t *out) { memcpy(out, o->stats, sizeof o->stats); }
+
+int32_t or_n(const Oracle *o) { return o->n; }
+int32_t or_geometry(const Oracle *o, int32_t *out) {
+  out[0] = o->nc; out[1] = o->k; out[2] = o->nd; out[3] = o->ncol; out[4] = o->m; out[5] = o->global;
+  return OR_OK;
+}
+void or_chem(const Oracle *o, double *out) {
+  out[0] = o->pIXp; out[1] = o->pIXm; out[2] = o->ln_z1; out[3] = o->ln_salt; out[4] = o->a;
+  out[5] = o->self_coef; out[6] = o->pOH;
+}
+
+/* particle dump in internal order (callers sort by id) */
+void or_particles(const Oracle *o, float *xyz, uint64_t *id, int32_t *type, int8_t *state, double *vel) {
+  for (int j = 0; j < o->n; ++j) {
+    if (xyz) { xyz[3 * j] = o->x[j]; xyz[3 * j + 1] = o->y[j]; xyz[3 * j + 2] = o->z[j]; }
+    if (id) id[j] = o->id[j];
+    if (type) type[j] = o->type[j];
+    if (state) state[j] = (int8_t)o->st[j];
+    if (vel) { vel[3 * j] = o->vx[j]; vel[3 * j + 1] = o->vy[j]; vel[3 * j + 2] = o->vz[j]; }
+  }
+}
+
+/* site states by site index */
+void or_site_states(const Oracle *o, int8_t *out) {
+  for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0) out[o->site[j]] = (int8_t)o->st[j];
+}
+
+/* Total energy of the current configuration (all pairs, brute force). */
+double or_energy(const Oracle *o) {
+  double E = 0.0;
+  for (int i = 0; i < o->n; ++i) {
+    double qi = qeff(o, o->type[i], o->st[i]);
+    for (int j = i + 1; j < o->n; ++j) {
+      int ov = 0;
+      double r = dist(o, o->x[i], o->y[i], o->z[i], o->x[j], o->y[j], o->z[j]);
+      E += pair_u(o, qi, o->cls[i], qeff(o, o->type[j], o->st[j]), o->cls[j], r, &ov, 0);
+    }
+    if (o->dsf_self) E += o->lB * o->self_coef * qi * qi;
+  }
+  return E;
+}
+
+/* FENE bond energy, U = -K R0^2/2 ln(1 - (r/R0)^2) summed over bonds (the
+ * CR-MC moves never change it; the MD tests use it for -grad E). */
+double or_bond_energy(const Oracle *o) {
+  double E = 0.0;
+  int *where = malloc((size_t)(o->cap > 0 ? o->cap : 1) * sizeof(int));
+  for (int j = 0; j < o->cap; ++j) where[j] = -1;
+  for (int j = 0; j < o->n; ++j) if (o->id[j] < (uint64_t)o->cap) where[o->id[j]] = j;
+  for (int b = 0; b < o->nb; ++b) {
+    int i = where[o->bi[b]], j = where[o->bj[b]];
+    double r = dist(o, o->x[i], o->y[i], o->z[i], o->x[j], o->y[j], o->z[j]);
+    double x2 = (r / o->R0) * (r / o->R0);
+    E += x2 < 1.0 ? -0.5 * o->K * o->R0 * o->R0 * log(1.0 - x2) : INFINITY;
+  }
+  free(where);
+  return E;
+}
+
+/* ----------------------------------------------------------------------- */
+/* MD: conservative forces (DSF Coulomb + WCA over all pairs within the
+ * cutoffs, brute force with the minimum image, plus FENE bonds
+ * U = -K R0^2/2 ln(1 - (r/R0)^2)).  fs: per component sum of |pair force|. */
+static int forces_cons(const Oracle *o, double *F, double *fs) {
+  memset(F, 0, (size_t)o->n * 3 * sizeof(double));
+  if (fs) memset(fs, 0, (size_t)o->n * 3 * sizeof(double));
+  for (int i = 0; i < o->n; ++i) {
+    double qi = qeff(o, o->type[i], o->st[i]);
+    for (int j = i + 1; j < o->n; ++j) {
+      double qj = qeff(o, o->type[j], o->st[j]);
+      double d[3] = {min_image((double)o->x[i] - o->x[j], o->L), min_image((double)o->y[i] - o->y[j], o->L),
+                     min_image((double)o->z[i] - o->z[j], o->L)};
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double f = 0.0; /* magnitude along (r_i - r_j)/r, positive = repulsive */
+      if (r < o->rc && qi != 0.0 && qj != 0.0) f += o->lB * qi * qj * dsf_force(o, r);
+      int ci = o->cls[i], cj = o->cls[j];
+      if (o->on[ci][cj] && r < o->wcut[ci][cj]) f += wca_f(o->eps[ci][cj], o->sig[ci][cj], r - o->del[ci][cj]);
+      if (f == 0.0) continue;
+      for (int c = 0; c < 3; ++c) {
+        double fc = f * d[c] / r;
+        F[3 * i + c] += fc;
+        F[3 * j + c] -= fc;
+        if (fs) { fs[3 * i + c] += fabs(fc); fs[3 * j + c] += fabs(fc); }
+      }
+    }
+  }
+  if (o->nb > 0) {
+    /* permanent particles keep their input index as id; map id -> index */
+    int *where = malloc((size_t)o->cap * sizeof(int));
+    for (int j = 0; j < o->cap; ++j) where[j] = -1;
+    for (int j = 0; j < o->n; ++j) if (o->id[j] < (uint64_t)o->cap) where[o->id[j]] = j;
+    for (int b = 0; b < o->nb; ++b) {
+      int i = where[o->bi[b]], j = where[o->bj[b]];
+      double d[3] = {min_image((double)o->x[i] - o->x[j], o->L), min_image((double)o->y[i] - o->y[j], o->L),
+                     min_image((double)o->z[i] - o->z[j], o->L)};
+      double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      double x2 = r2 / (o->R0 * o->R0);
+      if (x2 >= 1.0) { free(where); return OR_ERR_BOND; }
+      double g = -o->K / (1.0 - x2); /* F_i = g * (r_i - r_j) */
+      for (int c = 0; c < 3; ++c) {
+        F[3 * i + c] += g * d[c];
+        F[3 * j + c] -= g * d[c];
+        if (fs) { fs[3 * i + c] += fabs(g * d[c]); fs[3 * j + c] += fabs(g * d[c]); }
+      }
+    }
+    free(where);
+  }
+  return OR_OK;
+}
+
+int32_t or_forces(const Oracle *o, double *F, double *fs) { return forces_cons(o, F, fs); }
+
+/* Langevin part of the force, drawn per particle id and force evaluation:
+ * -gamma v + sqrt(2 gamma T / dt) xi, xi ~ N(0,1) from Box-Muller on Philox
+ * (key = seed, counter = (id_lo, id_hi, eval, 5)), uniforms (w + 0.5) 2^-32. */
+static void langevin(const Oracle *o, double *F, double gamma, double T, double dt, uint64_t seed, uint64_t ev) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  double amp = sqrt(2.0 * gamma * T / dt);
+  for (int j = 0; j < o->n; ++j) {
+    uint32_t c[4] = {(uint32_t)o->id[j], (uint32_t)(o->id[j] >> 32), (uint32_t)ev, 5u}, w[4];
+    philox(c, key, w);
+    double u[4];
+    for (int i = 0; i < 4; ++i) u[i] = ((double)w[i] + 0.5) * (1.0 / 4294967296.0);
+    double r1 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
+    double g[3] = {r1 * cos(2.0 * M_PI * u[1]), r1 * sin(2.0 * M_PI * u[1]), r2 * cos(2.0 * M_PI * u[3])};
+    F[3 * j] += -gamma * o->vx[j] + amp * g[0];
+    F[3 * j + 1] += -gamma * o->vy[j] + amp * g[1];
+    F[3 * j + 2] += -gamma * o->vz[j] + amp * g[2];
+  }
+}
+
+static float wrapf(const Oracle *o, double x) {
+  x -= o->L * floor(x / o->L);
+  float f = (float)x;
+  if (f >= o->Lf) f -= o->Lf;
+  if (f < 0.0f) f = 0.0f;
+  return f;
+}
+
+/* Velocity Verlet with Langevin friction/noise added at each force
+ * evaluation (unit mass, kT = 1).  Forces are re-evaluated first when the
+ * CR-MC stage changed the system since the last evaluation. */
+int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+  double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
+  int rc = OR_OK;
+  if (!o->f_valid) {
+    rc = forces_cons(o, F, NULL);
+    if (rc) { free(F); return rc; }
+    langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
+    for (int j = 0; j < o->n; ++j) { o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2]; }
+    o->f_valid = 1;
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    for (int j = 0; j < o->n; ++j) {
+      o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
+      o->x[j] = wrapf(o, (double)o->x[j] + dt * o->vx[j]);
+      o->y[j] = wrapf(o, (double)o->y[j] + dt * o->vy[j]);
+      o->z[j] = wrapf(o, (double)o->z[j] + dt * o->vz[j]);
+    }
+    rc = forces_cons(o, F, NULL);
+    if (rc) break;
+    langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
+    for (int j = 0; j < o->n; ++j) {
+      o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2];
+      o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
+    }
+  }
+  free(F);
+  return rc;
+}
+
+/* overwrite positions / velocities from id-sorted arrays (used to re-sync the
+ * oracle to a state before a parity window) */
+int32_t or_set_positions(Oracle *o, const uint64_t *ids, const float *xyz, const float *vel, int32_t n) {
+  if (n != o->n) return OR_ERR_ARG;
+  for (int j = 0; j < o->n; ++j) {
+    int lo = 0, hi = n - 1, at = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) / 2;
+      if (ids[mid] == o->id[j]) { at = mid; break; }
+      if (ids[mid] < o->id[j]) lo = mid + 1; else hi = mid - 1;
+    }
+    if (at < 0) return OR_ERR_ARG;
+    o->x[j] = xyz[3 * at]; o->y[j] = xyz[3 * at + 1]; o->z[j] = xyz[3 * at + 2];
+    if (vel) { o->vx[j] = vel[3 * at]; o->vy[j] = vel[3 * at + 1]; o->vz[j] = vel[3 * at + 2]; }
+  }
+  o->f_valid = 0;
+  return OR_OK;
+}
