@@ -1,0 +1,211 @@
+/*
+ * crmc.h -- C ABI of libcrmc.so: the charge-regulation Monte Carlo (CR-MC)
+ * stage of the hybrid MD/CR-MC method (Curk, Yuan & Luijten, arXiv:2109.07527)
+ * on one GB300 GPU, with the MD force/integration step that consumes the
+ * regulated charges.
+ *
+ * Conventions for every entry point:
+ *   - Return value: CR_OK (0) on success, a negative CR_ERR_* code otherwise.
+ *     No C++ exception crosses this boundary.  cr_strerror() names the codes.
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call.  The library owns all device memory of a context; it is
+ *     released by cr_destroy().
+ *   - Work is queued on the context's CUDA stream (cr_set_stream); calls that
+ *     return host data (cr_state, cr_sweep with stats or log, cr_md_forces
+ *     with output) synchronise that stream.
+ *   - Units: lengths in sigma, energies in kT (beta = 1), charges in e.
+ *
+ * The method (paper references):
+ *   Reactions (Sec. II.B, Eqs. acid_new, base_new, salt_new):
+ *       A <-> A- + X+,   B <-> B+ + X-,   0 <-> X+ + X-
+ *   with all monovalent cations grouped into X+ and anions into X-
+ *   (Eqs. mux1, mux2; App. A).  Six moves, forward/reverse with equal
+ *   probability, participants drawn uniformly from the eligible particles,
+ *   automatic rejection when none exists (Sec. II.C).  Acceptance
+ *   (Sec. II.C, Eqs. acidacc, MCmetro, the base pair, MCsaltf, MCmetro2):
+ *     acid fwd : min[1, (nA - nA-) rho0 NA v / ((nA- + 1)(nX+ + 1)) 10^(pH - pKa - pIX+) e^-dE]
+ *     acid rev : min[1, nA- nX+ / ((nA - nA- + 1) rho0 NA v) 10^(-pH + pKa + pIX+) e^-dE]
+ *     base     : the same with pOH, pKb, pIX-, nX-
+ *     salt ins : min[1, (rho0 NA v)^2 / ((nX+ + 1)(nX- + 1)) 10^(-pIX+ - pIX-) e^-dE]
+ *     salt del : min[1, nX+ nX- / (rho0 NA v)^2 10^(pIX+ + pIX-) e^-dE]
+ *   with rho0 = 1 M and 10^-pIX = 10^-pIS + 10^-min(pH, pOH) (App. C, Eq. pIXgen).
+ *   This library evaluates the moves domain-locally: v is the volume of the
+ *   trial's domain, the counts are that domain's counts, and the paired ion
+ *   is inserted in / deleted from that domain; same-colour domains of an
+ *   8-colour checkerboard are at least r_c apart and run concurrently.
+ *   CR_SCHED_GLOBAL (one domain = the box) gives the paper's rule verbatim.
+ *   Energy: damped-shifted-force Coulomb (cutoff r_c, damping alpha, with its
+ *   self term) + WCA / expanded WCA (Eq. LJe); the paper itself uses PPPM.
+ */
+#ifndef CRMC_H
+#define CRMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define CR_OK 0
+#define CR_ERR_INVALID_ARG (-1)   /* bad argument or inconsistent system */
+#define CR_ERR_NOT_NEUTRAL (-2)   /* initial system is not charge neutral */
+#define CR_ERR_CELL_OVERFLOW (-3) /* a cell exceeded its slot capacity */
+#define CR_ERR_CAPACITY (-4)      /* particle capacity exhausted */
+#define CR_ERR_TIMEOUT (-5)       /* a bounded device wait gave up */
+#define CR_ERR_BOND_BROKEN (-6)   /* a FENE bond reached R0 */
+#define CR_ERR_CUDA (-7)          /* a CUDA runtime call failed */
+#define CR_ERR_NOMEM (-8)         /* device or host allocation failed */
+#define CR_ERR_NO_DEVICE (-9)     /* no CUDA device is visible */
+
+/* ---- particle types (input encoding) ---- */
+#define CR_BEAD 0 /* neutral monomer / bead */
+#define CR_ACID 1 /* acid site: neutral A or ionised A- (charge -1) */
+#define CR_BASE 2 /* base site: neutral B or ionised B+ (charge +1) */
+#define CR_XP 3   /* grouped monovalent cation X+ */
+#define CR_XM 4   /* grouped monovalent anion X- */
+#define CR_CORE 5 /* neutral nanoparticle core (expanded WCA) */
+
+/* short-range class 3 never interacts by WCA */
+#define CR_CLS_NONE 3
+
+#define CR_SCHED_COLOURED 0 /* 8-colour checkerboard of domains */
+#define CR_SCHED_GLOBAL 1   /* one domain = the whole box (paper's rule) */
+
+/* trial-record flags */
+#define CR_TRIAL_ACCEPTED 1
+#define CR_TRIAL_NO_ELIGIBLE 2 /* automatic rejection: no eligible particle */
+#define CR_TRIAL_EDGE 4        /* insertion point rounded out of the domain */
+#define CR_TRIAL_OVERLAP 8     /* hard overlap of an inserted ion: dE = +inf */
+
+typedef struct cr_ctx cr_ctx; /* opaque, library-owned */
+
+/* System description, read by cr_init (the arrays are copied). */
+typedef struct {
+  int32_t n;            /* particles at start (>= 0) */
+  int32_t capacity;     /* maximum particles over the run (>= n) */
+  double box_L;         /* side of the cubic periodic box; rounded to FP32 */
+  double sigma_nm;      /* sigma in nm, converts v to nm^3 for rho0 N_A v */
+  const float *xyz;     /* [3n] positions in [0, box_L) */
+  const int32_t *type;  /* [n] CR_BEAD .. CR_CORE */
+  const int32_t *cls;   /* [n] short-range class 0..3 (ions take ion_cls) */
+  const int8_t *state;  /* [n] sites: 1 = ionised; ignored for others */
+  const float *vel;     /* [3n] velocities, or NULL for zero */
+  int32_t n_bonds;      /* FENE bonds */
+  const int32_t *bonds; /* [2 n_bonds] particle indices; no ions */
+  double fene_K, fene_R0;
+  double wca_eps[16], wca_sig[16], wca_del[16]; /* class-pair table [4*ci + cj] */
+  int32_t wca_on[16];
+  double dsf_alpha;        /* DSF damping (1/sigma) */
+  int32_t dsf_self;        /* 1: include the DSF self energy of each charge */
+  int32_t ion_coupling;    /* 1: ions charged and WCA-interacting; 0: ghost ions */
+  int32_t ion_cls;         /* short-range class of X+/X- */
+  int32_t cells_per_rc;    /* h: cell side >= r_c / h (default 2) */
+  int32_t domain_cells;    /* k: a domain is k^3 cells, k * cell >= r_c (default h) */
+  int32_t trials_per_domain; /* m: sequential trials per domain per colour phase */
+  int32_t schedule;        /* CR_SCHED_COLOURED or CR_SCHED_GLOBAL */
+  int32_t nc;              /* cells per dimension; 0 = automatic */
+  int32_t cell_capacity;   /* slots per cell; 0 = automatic */
+} cr_system;
+
+/* Reservoir ions: pI_S of the symmetric salt per sign and pKw; with
+ * pIX_explicit = 1 the grouped pI_X+- are taken as given (e.g. pIX+ = pH,
+ * pIX- = pOH for the conventional reaction ensemble). */
+typedef struct {
+  double pI_S_plus, pI_S_minus, pKw;
+  int32_t pIX_explicit;
+  double pIX_plus, pIX_minus;
+} cr_mu_ions;
+
+/* Per-call statistics (attempts and accepts per move: 2*reaction + reverse,
+ * reaction 0 acid, 1 base, 2 salt). */
+typedef struct {
+  int64_t trials;
+  int64_t attempts[6], accepts[6];
+  int64_t no_eligible, edge, overlap;
+} cr_sweep_stats;
+
+/* One trial record (schedule order: colour phases, domains ascending,
+ * trials within a domain).  ids: UINT64_MAX when unused. */
+typedef struct {
+  int32_t move;  /* 2*reaction + (0 forward, 1 reverse) */
+  int32_t flags; /* CR_TRIAL_* */
+  uint64_t id_a; /* site (acid/base) or first ion (salt) */
+  uint64_t id_b; /* ion paired with the site, or second ion */
+  double dE;     /* energy change (kT); +inf on overlap */
+  double S;      /* sum of |pair changes| (tolerance scale) */
+  double lnA;    /* log acceptance ratio */
+  double lnu;    /* log of the Metropolis uniform */
+} cr_trial;
+
+/* State view: counts always; arrays when non-NULL (sizes >= n, n_sites). */
+typedef struct {
+  int64_t n, n_A, n_Am, n_B, n_Bp, n_Xp, n_Xm, net_charge;
+  double alpha;          /* n_A- / n_A (0 when there are no acids) */
+  float *xyz;            /* [3n] */
+  float *vel;            /* [3n] */
+  float *force;          /* [3n] last evaluated total force */
+  uint64_t *id;          /* [n] particle ids (input index; inserted ions >= 2^32) */
+  int32_t *type;         /* [n] */
+  int8_t *state;         /* [n] 1 = ionised site */
+  int8_t *site_state;    /* [n_sites] by site index (input order of the sites) */
+} cr_state_view;
+
+typedef struct {
+  int32_t nc, k, h, nd, ncol, m, cap, global;
+  int64_t trials_per_sweep;
+  int32_t n_sites, n_perm;
+  double cell_side, domain_side;
+} cr_info;
+
+/* Create a context: copies the system to the device, precomputes the
+ * chemical constants (pH, per-particle pK [n] of sites, reservoir ions,
+ * Bjerrum length lB, cutoff rc).  Errors: INVALID_ARG (geometry, ranges,
+ * rc > L/2), NOT_NEUTRAL, NO_DEVICE, NOMEM, CUDA. */
+int cr_init(cr_ctx **out, const cr_system *sys, double pH, const double *pK, cr_mu_ions mu, double lB,
+            double rc);
+
+/* Run n_trials CR-MC trials (a positive multiple of trials_per_sweep) with
+ * Philox key `seed`; sweeps continue the context's sweep counter.  stats
+ * (nullable) receives this call's counts and synchronises the stream. */
+int cr_sweep(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats);
+
+/* As cr_sweep, and writes one cr_trial per trial to the host array `log`
+ * (n_trials entries).  Slower: used by the parity tests. */
+int cr_sweep_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log);
+
+/* Evaluate the conservative MD forces (DSF Coulomb + WCA + FENE) with the
+ * current charges; they become readable through cr_state().force. */
+int cr_md_forces(cr_ctx *ctx);
+
+/* n_steps of velocity Verlet with Langevin friction gamma and noise at kT = 1
+ * (unit mass), time step dt, noise key seed.  Forces are re-evaluated first
+ * when CR-MC changed the system since the last evaluation.  Errors:
+ * BOND_BROKEN, CELL_OVERFLOW. */
+int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
+
+/* Fill the view (counts always; arrays when non-NULL) and synchronise. */
+int cr_state(cr_ctx *ctx, cr_state_view *out);
+
+/* Geometry and schedule of the context. */
+int cr_get_info(const cr_ctx *ctx, cr_info *out);
+
+/* Use a caller CUDA stream (a cudaStream_t passed as void*; NULL = default). */
+int cr_set_stream(cr_ctx *ctx, void *stream);
+
+/* Check the device error word (synchronises): CR_OK or the first error. */
+int cr_check(cr_ctx *ctx);
+
+void cr_destroy(cr_ctx *ctx);
+const char *cr_strerror(int code);
+
+/* Philox4x32-10 on the device for n consecutive counters (c0 + i, c1, c2, c3),
+ * key (k0, k1); out: host array of 4n words.  Exposed for parity tests. */
+int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,
+              uint32_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRMC_H */

@@ -642,7 +642,6 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
   if (accept) {
     t.flags |= F_ACC;
     o->stats[6 + t.move]++;
-    o->f_valid = 0;
     int s_before = 0;
     if (hist_n > 0) for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0 && o->site[j] < hist_n && o->st[j]) s_before |= 1 << o->site[j];
     if (r == R_ACID || r == R_BASE) {
@@ -697,6 +696,7 @@ int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, cons
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   elig_t *buf = malloc((size_t)(o->cap > 0 ? o->cap : 1) * sizeof(elig_t));
   int64_t t = 0;
+  o->f_valid = 0; /* the MD step re-evaluates forces after every CR-MC call */
   int rc = OR_OK;
   for (int64_t sw = 0; sw < n_trials / per && rc == OR_OK; ++sw) {
     uint64_t s = o->sweep++;

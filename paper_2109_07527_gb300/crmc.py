@@ -1,0 +1,242 @@
+"""Python binding of libcrmc.so (the C ABI in include/crmc.h).
+
+Argument marshalling only: every step of the CR-MC path runs in the library's
+CUDA kernels.  Importing this module loads the library and raises if it has
+not been built (``__graft_entry__.build()`` or ``python -m
+paper_2109_07527_gb300.build``); there is no CPU fallback.  PyTorch, when
+present, supplies the CUDA stream the library queues its work on.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcrmc.so")
+
+CR_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "NOT_NEUTRAL", -3: "CELL_OVERFLOW", -4: "CAPACITY", -5: "TIMEOUT",
+          -6: "BOND_BROKEN", -7: "CUDA", -8: "NOMEM", -9: "NO_DEVICE"}
+SCHED_COLOURED, SCHED_GLOBAL = 0, 1
+TRIAL_ACCEPTED, TRIAL_NO_ELIGIBLE, TRIAL_EDGE, TRIAL_OVERLAP = 1, 2, 4, 8
+
+
+class CrError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what} failed: {ERRORS.get(code, code)} ({_lib().cr_strerror(code).decode()})")
+        self.code = code
+
+
+class cr_system(C.Structure):
+    _fields_ = [("n", C.c_int32), ("capacity", C.c_int32), ("box_L", C.c_double), ("sigma_nm", C.c_double),
+                ("xyz", C.c_void_p), ("type", C.c_void_p), ("cls", C.c_void_p), ("state", C.c_void_p),
+                ("vel", C.c_void_p), ("n_bonds", C.c_int32), ("bonds", C.c_void_p),
+                ("fene_K", C.c_double), ("fene_R0", C.c_double),
+                ("wca_eps", C.c_double * 16), ("wca_sig", C.c_double * 16), ("wca_del", C.c_double * 16),
+                ("wca_on", C.c_int32 * 16),
+                ("dsf_alpha", C.c_double), ("dsf_self", C.c_int32), ("ion_coupling", C.c_int32),
+                ("ion_cls", C.c_int32), ("cells_per_rc", C.c_int32), ("domain_cells", C.c_int32),
+                ("trials_per_domain", C.c_int32), ("schedule", C.c_int32), ("nc", C.c_int32),
+                ("cell_capacity", C.c_int32)]
+
+
+class cr_mu_ions(C.Structure):
+    _fields_ = [("pI_S_plus", C.c_double), ("pI_S_minus", C.c_double), ("pKw", C.c_double),
+                ("pIX_explicit", C.c_int32), ("pIX_plus", C.c_double), ("pIX_minus", C.c_double)]
+
+
+class cr_sweep_stats(C.Structure):
+    _fields_ = [("trials", C.c_int64), ("attempts", C.c_int64 * 6), ("accepts", C.c_int64 * 6),
+                ("no_eligible", C.c_int64), ("edge", C.c_int64), ("overlap", C.c_int64)]
+
+
+class cr_state_view(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_A", C.c_int64), ("n_Am", C.c_int64), ("n_B", C.c_int64),
+                ("n_Bp", C.c_int64), ("n_Xp", C.c_int64), ("n_Xm", C.c_int64), ("net_charge", C.c_int64),
+                ("alpha", C.c_double), ("xyz", C.c_void_p), ("vel", C.c_void_p), ("force", C.c_void_p),
+                ("id", C.c_void_p), ("type", C.c_void_p), ("state", C.c_void_p), ("site_state", C.c_void_p)]
+
+
+class cr_info(C.Structure):
+    _fields_ = [("nc", C.c_int32), ("k", C.c_int32), ("h", C.c_int32), ("nd", C.c_int32), ("ncol", C.c_int32),
+                ("m", C.c_int32), ("cap", C.c_int32), ("global_", C.c_int32), ("trials_per_sweep", C.c_int64),
+                ("n_sites", C.c_int32), ("n_perm", C.c_int32), ("cell_side", C.c_double),
+                ("domain_side", C.c_double)]
+
+
+TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id_b", "<u8"),
+                        ("dE", "<f8"), ("S", "<f8"), ("lnA", "<f8"), ("lnu", "<f8")])
+
+# every entry point of include/crmc.h
+EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
+           "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox")
+
+_L = None
+
+
+def _lib():
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libcrmc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        lib.cr_init.restype = C.c_int
+        lib.cr_init.argtypes = [C.POINTER(P), C.POINTER(cr_system), C.c_double, P, cr_mu_ions, C.c_double, C.c_double]
+        lib.cr_sweep.restype = C.c_int
+        lib.cr_sweep.argtypes = [P, C.c_uint64, C.c_uint64, C.POINTER(cr_sweep_stats)]
+        lib.cr_sweep_log.restype = C.c_int
+        lib.cr_sweep_log.argtypes = [P, C.c_uint64, C.c_uint64, C.POINTER(cr_sweep_stats), P]
+        lib.cr_md_forces.restype = C.c_int
+        lib.cr_md_forces.argtypes = [P]
+        lib.cr_md_step.restype = C.c_int
+        lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        lib.cr_state.restype = C.c_int
+        lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
+        lib.cr_get_info.restype = C.c_int
+        lib.cr_get_info.argtypes = [P, C.POINTER(cr_info)]
+        lib.cr_set_stream.restype = C.c_int
+        lib.cr_set_stream.argtypes = [P, P]
+        lib.cr_check.restype = C.c_int
+        lib.cr_check.argtypes = [P]
+        lib.cr_destroy.restype = None
+        lib.cr_destroy.argtypes = [P]
+        lib.cr_strerror.restype = C.c_char_p
+        lib.cr_strerror.argtypes = [C.c_int]
+        lib.cr_philox.restype = C.c_int
+        lib.cr_philox.argtypes = [C.c_uint32] * 6 + [C.c_int32, P]
+        _L = lib
+    return _L
+
+
+def _chk(code, what):
+    if code != CR_OK:
+        raise CrError(code, what)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def philox(c0, c1, c2, c3, k0, k1, n):
+    """Philox4x32-10 blocks for counters (c0 + i, c1, c2, c3), i < n, on the GPU."""
+    out = np.zeros((n, 4), dtype=np.uint32)
+    _chk(_lib().cr_philox(c0, c1, c2, c3, k0, k1, n, _p(out)), "cr_philox")
+    return out
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+class Context:
+    """A CR-MC system on the GPU (owns one cr_ctx)."""
+
+    def __init__(self, w, schedule=None, trials_per_domain=None, domain_cells=None, cell_capacity=0, stream=None):
+        lib = _lib()
+        q = w.params
+        s = cr_system()
+        self._keep = dict(xyz=np.ascontiguousarray(w.xyz, np.float32), type=np.ascontiguousarray(w.type, np.int32),
+                          cls=np.ascontiguousarray(w.cls, np.int32), state=np.ascontiguousarray(w.state, np.int8),
+                          vel=None if w.vel is None else np.ascontiguousarray(w.vel, np.float32),
+                          bonds=np.ascontiguousarray(w.bonds, np.int32), pK=np.ascontiguousarray(w.pK, np.float64))
+        k = self._keep
+        s.n, s.capacity, s.box_L, s.sigma_nm = w.n, w.capacity, q["box_L"], q["sigma_nm"]
+        s.xyz, s.type, s.cls, s.state, s.vel = _p(k["xyz"]), _p(k["type"]), _p(k["cls"]), _p(k["state"]), _p(k["vel"])
+        s.n_bonds, s.bonds = int(w.bonds.shape[0]), _p(k["bonds"])
+        s.fene_K, s.fene_R0 = q["fene_K"], q["fene_R0"]
+        for i in range(16):
+            s.wca_eps[i], s.wca_sig[i], s.wca_del[i] = q["wca_eps"][i], q["wca_sig"][i], q["wca_del"][i]
+            s.wca_on[i] = int(q["wca_on"][i])
+        s.dsf_alpha, s.dsf_self = q["alpha"], int(q["dsf_self"])
+        s.ion_coupling, s.ion_cls = int(q["ion_coupling"]), int(q["ion_cls"])
+        s.cells_per_rc = int(q.get("cells_per_rc", 2))
+        s.domain_cells = int(domain_cells if domain_cells is not None else q.get("domain_cells", 0))
+        s.trials_per_domain = int(trials_per_domain if trials_per_domain is not None else q["trials_per_domain"])
+        s.schedule = int(schedule if schedule is not None else q["schedule"])
+        s.nc = int(q.get("nc", 0))
+        s.cell_capacity = int(cell_capacity)
+        mu = cr_mu_ions(q["pIS_plus"], q["pIS_minus"], q["pKw"], int(q.get("pIX_explicit", 0)),
+                        q.get("pIX_plus", 0.0), q.get("pIX_minus", 0.0))
+        h = C.c_void_p()
+        _chk(lib.cr_init(C.byref(h), C.byref(s), q["pH"], _p(k["pK"]), mu, q["lB"], q["rc"]), "cr_init")
+        self._h = h
+        self._lib = lib
+        st = stream if stream is not None else _torch_stream()
+        if st is not None:
+            _chk(lib.cr_set_stream(h, st), "cr_set_stream")
+        self.n_sites = w.n_sites
+        self.capacity = w.capacity
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def info(self):
+        i = cr_info()
+        _chk(self._lib.cr_get_info(self._h, C.byref(i)), "cr_get_info")
+        return {f: getattr(i, f) for f, _ in cr_info._fields_}
+
+    @property
+    def trials_per_sweep(self):
+        return int(self.info["trials_per_sweep"])
+
+    def sweep(self, n_trials, seed, stats=False, log=False):
+        st = cr_sweep_stats() if stats else None
+        if log:
+            rec = np.zeros(int(n_trials), dtype=TRIAL_DTYPE)
+            _chk(self._lib.cr_sweep_log(self._h, int(n_trials), int(seed), C.byref(st) if st else None, _p(rec)),
+                 "cr_sweep_log")
+        else:
+            rec = None
+            _chk(self._lib.cr_sweep(self._h, int(n_trials), int(seed), C.byref(st) if st else None), "cr_sweep")
+        out = {}
+        if st is not None:
+            out["stats"] = dict(trials=st.trials, attempts=np.array(st.attempts[:]), accepts=np.array(st.accepts[:]),
+                                no_eligible=st.no_eligible, edge=st.edge, overlap=st.overlap)
+        if rec is not None:
+            out["log"] = rec
+        return out
+
+    def md_forces(self):
+        _chk(self._lib.cr_md_forces(self._h), "cr_md_forces")
+
+    def md_step(self, n_steps, dt, gamma, seed):
+        _chk(self._lib.cr_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_md_step")
+
+    def check(self):
+        _chk(self._lib.cr_check(self._h), "cr_check")
+
+    def counts(self):
+        v = cr_state_view()
+        _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
+        return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
+                    net_charge=v.net_charge, alpha=v.alpha)
+
+    def state(self):
+        """Counts and all particles sorted by id."""
+        c = self.counts()
+        n = int(c["n"])
+        arr = dict(xyz=np.zeros((n, 3), np.float32), vel=np.zeros((n, 3), np.float32),
+                   force=np.zeros((n, 3), np.float32), id=np.zeros(n, np.uint64), type=np.zeros(n, np.int32),
+                   state=np.zeros(n, np.int8), site_state=np.zeros(max(self.n_sites, 1), np.int8))
+        v = cr_state_view()
+        v.xyz, v.vel, v.force = _p(arr["xyz"]), _p(arr["vel"]), _p(arr["force"])
+        v.id, v.type, v.state, v.site_state = _p(arr["id"]), _p(arr["type"]), _p(arr["state"]), _p(arr["site_state"])
+        _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
+        arr["site_state"] = arr["site_state"][: self.n_sites]
+        c.update(arr)
+        return c

@@ -1,0 +1,645 @@
+// crmc_api.cu -- host side of the C ABI declared in include/crmc.h.
+//
+// cr_init lays a system out in cell-major device arrays and precomputes the
+// chemical constants of Sec. II.C / App. C of the paper in FP64; cr_sweep
+// queues the colour phases of the checkerboard schedule; cr_md_step the
+// velocity-Verlet/Langevin step that consumes the regulated charges.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "crmc.h"
+#include "crmc_common.h"
+#include "crmc_kernels.h"
+
+using namespace crmc;
+
+struct cr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  SysParams P{};
+  // schedule / launch shape
+  int threads = 128, R = 4;
+  size_t smem_phase = 0;
+  int kb_md = 1, nb_md = 1, nr_md = 1, rcap_md = 1024, threads_md = 128;
+  int64_t per_sweep = 0;
+  // sizes
+  int n_input = 0, n_sites = 0, n_other = 0;
+  int64_t capacity = 0;
+  // device buffers
+  int *d_cnt = nullptr, *d_cnt2 = nullptr, *d_info = nullptr, *d_info2 = nullptr;
+  float4 *d_pos = nullptr, *d_pos2 = nullptr, *d_vel = nullptr, *d_vel2 = nullptr, *d_frc = nullptr,
+         *d_frc2 = nullptr, *d_fcons = nullptr;
+  unsigned long long *d_pid = nullptr, *d_pid2 = nullptr, *d_stats = nullptr;
+  double *d_lnK = nullptr, *d_lntab = nullptr;
+  long long *d_counts = nullptr;
+  int *d_err = nullptr, *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr, *d_counter = nullptr;
+  cr_trial *d_log = nullptr;
+  size_t log_cap = 0;
+  // MD
+  double fene_K = 30.0, fene_R0 = 1.5;
+  uint64_t sweep = 0;
+  uint32_t md_eval = 0;
+  bool f_valid = false, fcons_valid = false;
+};
+
+namespace {
+
+constexpr double LN10 = 2.302585092994045684;
+constexpr double RHO0_NA = 0.602214076;  // 1 M in nm^-3
+
+int cuda_fail(cudaError_t e) { return e == cudaSuccess ? CR_OK : (e == cudaErrorMemoryAllocation ? CR_ERR_NOMEM : CR_ERR_CUDA); }
+
+#define CR_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+template <typename T>
+int dalloc(T **p, size_t n) {
+  if (n == 0) n = 1;
+  return cuda_fail(cudaMalloc((void **)p, n * sizeof(T)));
+}
+
+double pIX_of(double pIS, double pH, double pOH) {
+  const double m = pH < pOH ? pH : pOH;
+  return -std::log10(std::pow(10.0, -pIS) + std::pow(10.0, -m));
+}
+
+int cell_of_host(float x, float scf, int nc) {
+  const float t = x * scf;  // single IEEE multiply
+  int c = (int)std::floor(t);
+  if (c < 0) c = 0;
+  if (c >= nc) c = nc - 1;
+  return c;
+}
+
+int err_bits_to_code(int bits) {
+  if (bits & ERRB_CELL_OVERFLOW) return CR_ERR_CELL_OVERFLOW;
+  if (bits & ERRB_CAPACITY) return CR_ERR_CAPACITY;
+  if (bits & ERRB_BOND) return CR_ERR_BOND_BROKEN;
+  if (bits & ERRB_TIMEOUT) return CR_ERR_TIMEOUT;
+  if (bits & ERRB_ARG) return CR_ERR_INVALID_ARG;
+  return CR_OK;
+}
+
+}  // namespace
+
+extern "C" const char *cr_strerror(int code) {
+  switch (code) {
+    case CR_OK: return "ok";
+    case CR_ERR_INVALID_ARG: return "invalid argument or inconsistent system";
+    case CR_ERR_NOT_NEUTRAL: return "system is not charge neutral";
+    case CR_ERR_CELL_OVERFLOW: return "a cell exceeded its slot capacity";
+    case CR_ERR_CAPACITY: return "particle capacity exhausted";
+    case CR_ERR_TIMEOUT: return "a bounded device wait gave up";
+    case CR_ERR_BOND_BROKEN: return "a FENE bond reached its maximum extension";
+    case CR_ERR_CUDA: return "CUDA runtime error";
+    case CR_ERR_NOMEM: return "out of memory";
+    case CR_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown error";
+  }
+}
+
+static void free_ctx(cr_ctx *c) {
+  if (!c) return;
+  void *ptrs[] = {c->d_cnt, c->d_cnt2, c->d_info, c->d_info2, c->d_pos, c->d_pos2, c->d_vel, c->d_vel2,
+                  c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
+                  c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+extern "C" void cr_destroy(cr_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const double *pK, cr_mu_ions mu, double lB,
+                       double rc) {
+  if (!out || !sys) return CR_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int n = sys->n;
+  if (n < 0 || sys->capacity < n || !(sys->box_L > 0.0) || !(rc > 0.0) || !(lB >= 0.0) || !(sys->sigma_nm > 0.0))
+    return CR_ERR_INVALID_ARG;
+  if (n > 0 && (!sys->xyz || !sys->type || !sys->cls || !sys->state || !pK)) return CR_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return CR_ERR_NO_DEVICE;
+
+  cr_ctx *c = new (std::nothrow) cr_ctx();
+  if (!c) return CR_ERR_NOMEM;
+  cudaGetDevice(&c->device);
+  SysParams &P = c->P;
+
+  // ---- geometry (cell side >= rc/h, domains of k^3 cells with k*a >= rc)
+  const float Lf = (float)sys->box_L;
+  const double L = (double)Lf;
+  if (2.0 * rc > L) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  const int h = sys->cells_per_rc > 0 ? sys->cells_per_rc : 2;
+  int nc = sys->nc > 0 ? sys->nc : (int)std::floor(h * L / rc);
+  if (nc < 1) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  const bool global = sys->schedule == CR_SCHED_GLOBAL;
+  int k;
+  if (global) {
+    k = nc;
+    if ((long long)nc * nc * nc > 8192) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  } else {
+    k = sys->domain_cells > 0 ? sys->domain_cells : h;
+    if (sys->nc <= 0) nc = (nc / (2 * k)) * (2 * k);
+    if (nc < 2 * k || nc % (2 * k) != 0) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    if ((double)k * (L / nc) < rc) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  }
+  const double a = L / nc;
+  if (a * h < rc) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  P.nc = nc;
+  P.k = k;
+  P.h = h;
+  P.nd = global ? 1 : nc / k;
+  P.ncol = global ? 1 : 8;
+  P.m = sys->trials_per_domain > 0 ? sys->trials_per_domain : 1;
+  P.global = global ? 1 : 0;
+  P.nr = std::min(k + 2 * h, nc);
+  P.ncell = nc * nc * nc;
+  P.Lf = Lf;
+  P.invL = (float)(1.0 / L);
+  P.scf = (float)((double)nc / L);
+  P.a = a;
+  c->per_sweep = (int64_t)P.nd * P.nd * P.nd * P.m;
+
+  // ---- energy constants (FP64 -> FP32)
+  const double alpha = sys->dsf_alpha;
+  const double erc = std::erfc(alpha * rc);
+  P.rc2 = (float)(rc * rc);
+  P.rcf = (float)rc;
+  P.alpha = (float)alpha;
+  P.c1 = (float)(erc / rc);
+  P.c2 = (float)(erc / (rc * rc) + 2.0 * alpha / std::sqrt(M_PI) * std::exp(-alpha * alpha * rc * rc) / rc);
+  P.lBf = (float)lB;
+  P.lB_self = sys->dsf_self ? lB * (-(erc / (2.0 * rc) + alpha / std::sqrt(M_PI))) : 0.0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      WcaEntry &w = P.wca[4 * i + j];
+      w.eps = (float)sys->wca_eps[4 * i + j];
+      w.sig = (float)sys->wca_sig[4 * i + j];
+      w.del = (float)sys->wca_del[4 * i + j];
+      const double cut = sys->wca_del[4 * i + j] + std::pow(2.0, 1.0 / 6.0) * sys->wca_sig[4 * i + j];
+      w.wcut2 = (float)(cut * cut);
+      w.on = (i != CR_CLS_NONE && j != CR_CLS_NONE && sys->wca_on[4 * i + j]) ? 1 : 0;
+    }
+  if (sys->ion_cls < 0 || sys->ion_cls > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  P.ion_cls = sys->ion_coupling ? sys->ion_cls : CR_CLS_NONE;
+  P.ion_q = sys->ion_coupling ? 1.0f : 0.0f;
+
+  // ---- chemistry (log form), Eq. (pIXgen) and the acceptance rules
+  const double pOH = mu.pKw - pH;
+  double pIXp, pIXm;
+  if (mu.pIX_explicit) { pIXp = mu.pIX_plus; pIXm = mu.pIX_minus; }
+  else { pIXp = pIX_of(mu.pI_S_plus, pH, pOH); pIXm = pIX_of(mu.pI_S_minus, pH, pOH); }
+  const double D = global ? L : k * a;
+  P.ln_z1 = std::log(RHO0_NA * std::pow(D * sys->sigma_nm, 3.0));
+  P.ln_salt = -LN10 * (pIXp + pIXm);
+
+  // ---- particles: validate, classify, sort into cells
+  std::vector<int> site_of(n, -1);
+  std::vector<double> lnK;
+  int nA = 0, nB = 0, qsum = 0;
+  for (int i = 0; i < n; ++i) {
+    const float X = sys->xyz[3 * i], Y = sys->xyz[3 * i + 1], Z = sys->xyz[3 * i + 2];
+    if (!(X >= 0.0f && X < Lf && Y >= 0.0f && Y < Lf && Z >= 0.0f && Z < Lf)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    const int t = sys->type[i];
+    if (t < CR_BEAD || t > CR_CORE || sys->cls[i] < 0 || sys->cls[i] > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    if (t == CR_ACID || t == CR_BASE) {
+      site_of[i] = (int)lnK.size();
+      if (t == CR_ACID) { lnK.push_back(LN10 * ((pH - pK[i]) - pIXp)); nA++; }
+      else { lnK.push_back(LN10 * ((pOH - pK[i]) - pIXm)); nB++; }
+      const int ion = sys->state[i] ? 1 : 0;
+      qsum += ion ? (t == CR_ACID ? -1 : 1) : 0;
+    } else if (t == CR_XP) qsum += 1;
+    else if (t == CR_XM) qsum -= 1;
+  }
+  if ((int)lnK.size() >= MAX_SITES) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  if (qsum != 0) { free_ctx(c); return CR_ERR_NOT_NEUTRAL; }
+  P.n_react = 0;
+  if (nA > 0) P.react[P.n_react++] = R_ACID;
+  if (nB > 0) P.react[P.n_react++] = R_BASE;
+  P.react[P.n_react++] = R_SALT;
+  c->n_input = n;
+  c->n_sites = (int)lnK.size();
+  c->capacity = sys->capacity;
+
+  std::vector<int> cell(n);
+  std::vector<int> occ(P.ncell, 0);
+  for (int i = 0; i < n; ++i) {
+    const int cx = cell_of_host(sys->xyz[3 * i], P.scf, nc), cy = cell_of_host(sys->xyz[3 * i + 1], P.scf, nc),
+              cz = cell_of_host(sys->xyz[3 * i + 2], P.scf, nc);
+    cell[i] = cx + nc * (cy + nc * cz);
+    occ[cell[i]]++;
+  }
+  const int max_occ = n > 0 ? *std::max_element(occ.begin(), occ.end()) : 0;
+  int cap = sys->cell_capacity > 0 ? sys->cell_capacity : std::max(32, ((2 * max_occ + 16) + 7) / 8 * 8);
+  if (max_occ > cap) { free_ctx(c); return CR_ERR_CELL_OVERFLOW; }
+  P.cap = cap;
+  const size_t nslot = (size_t)P.ncell * cap;
+  std::vector<int> h_cnt(P.ncell, 0);
+  std::vector<float4> h_pos(nslot, make_float4(0, 0, 0, 0)), h_vel(nslot, make_float4(0, 0, 0, 0));
+  std::vector<unsigned long long> h_pid(nslot, 0);
+  std::vector<int> h_info(nslot, 0), h_perm(std::max(n, 1), -1);
+  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < n; ++i) {  // ascending i == ascending id within every cell
+    const int cc = cell[i];
+    const int g = cc * cap + h_cnt[cc]++;
+    const int t = sys->type[i];
+    const int ion = (t == CR_ACID || t == CR_BASE) && sys->state[i] ? 1 : 0;
+    float q = 0.0f;
+    int cls = sys->cls[i];
+    if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
+    else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
+    else if (t == CR_XP) { q = P.ion_q; cls = P.ion_cls; }
+    else if (t == CR_XM) { q = -P.ion_q; cls = P.ion_cls; }
+    h_pos[g] = make_float4(sys->xyz[3 * i], sys->xyz[3 * i + 1], sys->xyz[3 * i + 2], q);
+    if (sys->vel) h_vel[g] = make_float4(sys->vel[3 * i], sys->vel[3 * i + 1], sys->vel[3 * i + 2], 0.0f);
+    h_pid[g] = (unsigned long long)i;
+    const int site = site_of[i] < 0 ? 0 : site_of[i];
+    h_info[g] = t | (cls << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
+    h_perm[i] = g;
+    int kd = K_OTHER;
+    if (t == CR_ACID) kd = ion ? K_A1 : K_A0;
+    else if (t == CR_BASE) kd = ion ? K_B1 : K_B0;
+    else if (t == CR_XP) kd = K_XP;
+    else if (t == CR_XM) kd = K_XM;
+    kinds[kd]++;
+  }
+  c->n_other = (int)kinds[K_OTHER];
+
+  // ---- bonds (CSR by permanent particle)
+  const int nb = sys->n_bonds;
+  if (nb < 0 || (nb > 0 && !sys->bonds)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  std::vector<int> deg(n + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    const int i = sys->bonds[2 * b], j = sys->bonds[2 * b + 1];
+    if (i < 0 || j < 0 || i >= n || j >= n || i == j) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    const int ti = sys->type[i], tj = sys->type[j];
+    if (ti == CR_XP || ti == CR_XM || tj == CR_XP || tj == CR_XM) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    deg[i + 1]++;
+    deg[j + 1]++;
+  }
+  std::partial_sum(deg.begin(), deg.end(), deg.begin());
+  std::vector<int> nbr(std::max(2 * nb, 1)), fill(deg.begin(), deg.end() - 1);
+  for (int b = 0; b < nb; ++b) {
+    const int i = sys->bonds[2 * b], j = sys->bonds[2 * b + 1];
+    nbr[fill[i]++] = j;
+    nbr[fill[j]++] = i;
+  }
+  c->fene_K = sys->fene_K;
+  c->fene_R0 = sys->fene_R0;
+  if (nb > 0 && !(sys->fene_R0 > 0.0)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+
+  // ---- launch shapes: CTA per domain; halo registers sized from the densest region
+  c->threads = 128;
+  {
+    // halo of a domain whose first cell is (ox, oy, oz): region sum - domain sum
+    int maxh = 0;
+    const int nr = P.nr;
+    if (!global) {
+      for (int oz = 0; oz < nc; ++oz)
+        for (int oy = 0; oy < nc; ++oy)
+          for (int ox = 0; ox < nc; ++ox) {
+            int sum = 0;
+            for (int iz = 0; iz < nr; ++iz)
+              for (int iy = 0; iy < nr; ++iy)
+                for (int ix = 0; ix < nr; ++ix) {
+                  if (ix < k && iy < k && iz < k) continue;
+                  auto rc_ = [&](int i, int o) {
+                    int cc = (i < k + h) ? o + i : o + i - nr;
+                    cc %= nc;
+                    if (cc < 0) cc += nc;
+                    return cc;
+                  };
+                  sum += occ[rc_(ix, ox) + nc * (rc_(iy, oy) + nc * rc_(iz, oz))];
+                }
+            maxh = std::max(maxh, sum);
+          }
+    }
+    const int want = (int)std::ceil(1.25 * maxh / c->threads);
+    int R = 1;
+    while (R < want && R < 16) R *= 2;
+    c->R = R;
+  }
+  P.dcap = (int)std::min<long long>((long long)k * k * k * cap, (long long)sys->capacity + 2);
+  P.lnmax = P.dcap + 2;
+  std::vector<double> h_lntab(P.lnmax);
+  h_lntab[0] = -INFINITY;
+  for (int i = 1; i < P.lnmax; ++i) h_lntab[i] = std::log((double)i);
+  c->smem_phase = phase_smem_bytes(P);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (c->smem_phase > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  // MD blocks: kb^3 cells per CTA
+  c->kb_md = (!global && nc % k == 0) ? k : 1;
+  c->nb_md = nc / c->kb_md;
+  c->nr_md = std::min(c->kb_md + 2 * h, nc);
+  c->rcap_md = 2048;
+
+  // ---- device buffers
+  int rc_ = CR_OK;
+#define ALLOC(p, n_)                      \
+  if ((rc_ = dalloc(&(p), (n_))) != CR_OK) { \
+    free_ctx(c);                          \
+    return rc_;                           \
+  }
+  ALLOC(c->d_cnt, P.ncell);
+  ALLOC(c->d_cnt2, P.ncell);
+  ALLOC(c->d_pos, nslot);
+  ALLOC(c->d_pos2, nslot);
+  ALLOC(c->d_vel, nslot);
+  ALLOC(c->d_vel2, nslot);
+  ALLOC(c->d_frc, nslot);
+  ALLOC(c->d_frc2, nslot);
+  ALLOC(c->d_fcons, nslot);
+  ALLOC(c->d_pid, nslot);
+  ALLOC(c->d_pid2, nslot);
+  ALLOC(c->d_info, nslot);
+  ALLOC(c->d_info2, nslot);
+  ALLOC(c->d_stats, 16);
+  ALLOC(c->d_lnK, std::max<size_t>(lnK.size(), 1));
+  ALLOC(c->d_lntab, P.lnmax);
+  ALLOC(c->d_counts, 8);
+  ALLOC(c->d_err, 1);
+  ALLOC(c->d_perm, std::max(n, 1));
+  ALLOC(c->d_bond_off, n + 1);
+  ALLOC(c->d_bond_nbr, std::max(2 * nb, 1));
+  ALLOC(c->d_counter, 1);
+#undef ALLOC
+#define COPY(dst, src, n_)                                                                           \
+  if ((rc_ = cuda_fail(cudaMemcpy((dst), (src), (n_) * sizeof(*(src)), cudaMemcpyHostToDevice))) != CR_OK) { \
+    free_ctx(c);                                                                                     \
+    return rc_;                                                                                      \
+  }
+  COPY(c->d_cnt, h_cnt.data(), (size_t)P.ncell);
+  COPY(c->d_pos, h_pos.data(), nslot);
+  COPY(c->d_vel, h_vel.data(), nslot);
+  COPY(c->d_pid, h_pid.data(), nslot);
+  COPY(c->d_info, h_info.data(), nslot);
+  if (!lnK.empty()) COPY(c->d_lnK, lnK.data(), lnK.size());
+  COPY(c->d_lntab, h_lntab.data(), (size_t)P.lnmax);
+  COPY(c->d_perm, h_perm.data(), (size_t)std::max(n, 1));
+  COPY(c->d_bond_off, deg.data(), (size_t)n + 1);
+  COPY(c->d_bond_nbr, nbr.data(), nbr.size());
+  COPY(c->d_counts, kinds, (size_t)6);
+#undef COPY
+  cudaMemset(c->d_cnt2, 0, sizeof(int) * P.ncell);
+  cudaMemset(c->d_frc, 0, sizeof(float4) * nslot);
+  cudaMemset(c->d_fcons, 0, sizeof(float4) * nslot);
+  cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16);
+  cudaMemset(c->d_err, 0, sizeof(int));
+  P.lnK = c->d_lnK;
+  P.lntab = c->d_lntab;
+  P.cnt = c->d_cnt;
+  P.pos = c->d_pos;
+  P.vel = c->d_vel;
+  P.pid = c->d_pid;
+  P.info = c->d_info;
+  P.perm_slot = c->d_perm;
+  P.n_perm = n;
+  P.stats = c->d_stats;
+  P.counts = c->d_counts;
+  P.err = c->d_err;
+  P.log = nullptr;
+  P.log_base = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return CR_ERR_CUDA; }
+  *out = c;
+  return CR_OK;
+}
+
+extern "C" int cr_set_stream(cr_ctx *ctx, void *stream) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return CR_OK;
+}
+
+extern "C" int cr_get_info(const cr_ctx *ctx, cr_info *out) {
+  if (!ctx || !out) return CR_ERR_INVALID_ARG;
+  const SysParams &P = ctx->P;
+  out->nc = P.nc;
+  out->k = P.k;
+  out->h = P.h;
+  out->nd = P.nd;
+  out->ncol = P.ncol;
+  out->m = P.m;
+  out->cap = P.cap;
+  out->global = P.global;
+  out->trials_per_sweep = ctx->per_sweep;
+  out->n_sites = ctx->n_sites;
+  out->n_perm = ctx->n_input;
+  out->cell_side = P.a;
+  out->domain_side = P.global ? (double)P.Lf : P.k * P.a;
+  return CR_OK;
+}
+
+extern "C" int cr_check(cr_ctx *ctx) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  int bits = 0;
+  CR_CUDA(cudaMemcpyAsync(&bits, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return err_bits_to_code(bits);
+}
+
+static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  if (n_trials == 0 || n_trials % (uint64_t)ctx->per_sweep != 0) return CR_ERR_INVALID_ARG;
+  SysParams P = ctx->P;
+  cudaStream_t s = ctx->stream;
+  if (stats) CR_CUDA(cudaMemsetAsync(ctx->d_stats, 0, sizeof(unsigned long long) * 16, s));
+  if (log) {
+    if (ctx->log_cap < n_trials) {
+      if (ctx->d_log) cudaFree(ctx->d_log);
+      ctx->d_log = nullptr;
+      ctx->log_cap = 0;
+      CR_CUDA(cudaMalloc((void **)&ctx->d_log, sizeof(cr_trial) * n_trials));
+      ctx->log_cap = n_trials;
+    }
+    P.log = ctx->d_log;
+  }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int grid = P.global ? 1 : (P.nd / 2) * (P.nd / 2) * (P.nd / 2);
+  const uint64_t n_sweeps = n_trials / (uint64_t)ctx->per_sweep;
+  long long base = 0;
+  for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
+    const uint32_t swc = (uint32_t)ctx->sweep++;
+    for (int col = 0; col < P.ncol; ++col) {
+      P.log_base = base;
+      CR_CUDA(launch_phase(P, ctx->R, log != nullptr, grid, ctx->threads, ctx->smem_phase, s, swc, col, k0, k1));
+      base += (long long)grid * P.m;
+    }
+  }
+  ctx->f_valid = false;
+  ctx->fcons_valid = false;
+  if (log) {
+    CR_CUDA(cudaMemcpyAsync(log, ctx->d_log, sizeof(cr_trial) * n_trials, cudaMemcpyDeviceToHost, s));
+  }
+  if (stats) {
+    unsigned long long st[16];
+    CR_CUDA(cudaMemcpyAsync(st, ctx->d_stats, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CR_CUDA(cudaStreamSynchronize(s));
+    stats->trials = (int64_t)st[15];
+    for (int i = 0; i < 6; ++i) {
+      stats->attempts[i] = (int64_t)st[i];
+      stats->accepts[i] = (int64_t)st[6 + i];
+    }
+    stats->no_eligible = (int64_t)st[12];
+    stats->edge = (int64_t)st[13];
+    stats->overlap = (int64_t)st[14];
+  }
+  if (log || stats) {
+    CR_CUDA(cudaStreamSynchronize(s));
+    return cr_check(ctx);
+  }
+  return CR_OK;
+}
+
+extern "C" int cr_sweep(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats) {
+  return sweep_impl(ctx, n_trials, seed, stats, nullptr);
+}
+
+extern "C" int cr_sweep_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log) {
+  if (!log) return CR_ERR_INVALID_ARG;
+  return sweep_impl(ctx, n_trials, seed, stats, log);
+}
+
+static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64_t seed) {
+  MdParams M{};
+  M.dt = (float)dt;
+  M.gamma = (float)gamma;
+  M.amp = dt > 0.0 ? (float)std::sqrt(2.0 * gamma / dt) : 0.0f;
+  M.key0 = (uint32_t)seed;
+  M.key1 = (uint32_t)(seed >> 32);
+  M.eval = ctx->md_eval;
+  M.mode = mode;
+  M.vel = ctx->d_vel;
+  M.fout = mode == 0 ? ctx->d_fcons : ctx->d_frc;
+  M.perm_slot = ctx->d_perm;
+  M.bond_off = ctx->d_bond_off;
+  M.bond_nbr = ctx->d_bond_nbr;
+  M.n_perm = ctx->n_input;
+  M.fene_K = (float)ctx->fene_K;
+  M.inv_R02 = (float)(1.0 / (ctx->fene_R0 * ctx->fene_R0));
+  M.rcap = ctx->rcap_md;
+  return M;
+}
+
+extern "C" int cr_md_forces(cr_ctx *ctx) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
+  CR_CUDA(launch_md_forces(ctx->P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, ctx->stream));
+  ctx->fcons_valid = true;
+  return cr_check(ctx);
+}
+
+extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+  if (!ctx || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  const SysParams &P = ctx->P;
+  RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
+  if (!ctx->f_valid) {
+    MdParams M = md_params(ctx, 1, dt, gamma, seed);
+    CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
+    ctx->md_eval++;
+    ctx->f_valid = true;
+  }
+  for (int st = 0; st < n_steps; ++st) {
+    MdParams M = md_params(ctx, 2, dt, gamma, seed);
+    CR_CUDA(launch_kick_drift(P, M, s));
+    CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
+    CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
+    ctx->md_eval++;
+  }
+  ctx->fcons_valid = false;
+  return CR_OK;
+}
+
+extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
+  if (!ctx || !out) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  long long kinds[6];
+  CR_CUDA(cudaMemcpyAsync(kinds, ctx->d_counts, sizeof(kinds), cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaStreamSynchronize(s));
+  out->n_A = kinds[K_A0] + kinds[K_A1];
+  out->n_Am = kinds[K_A1];
+  out->n_B = kinds[K_B0] + kinds[K_B1];
+  out->n_Bp = kinds[K_B1];
+  out->n_Xp = kinds[K_XP];
+  out->n_Xm = kinds[K_XM];
+  out->n = out->n_A + out->n_B + out->n_Xp + out->n_Xm + ctx->n_other;
+  out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
+  out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
+  const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state;
+  if (!want) return cr_check(ctx);
+  const int64_t n = out->n;
+  float4 *dpos = nullptr, *dvel = nullptr, *dfrc = nullptr;
+  unsigned long long *dpid = nullptr;
+  int *dinfo = nullptr;
+  int rc = CR_OK;
+  if ((rc = dalloc(&dpos, n)) || (rc = dalloc(&dvel, n)) || (rc = dalloc(&dfrc, n)) || (rc = dalloc(&dpid, n)) ||
+      (rc = dalloc(&dinfo, n))) {
+    cudaFree(dpos); cudaFree(dvel); cudaFree(dfrc); cudaFree(dpid); cudaFree(dinfo);
+    return rc;
+  }
+  DumpBufs D{ctx->d_counter, (int)n, dpos, dvel, dfrc, dpid, dinfo, ctx->d_vel,
+             ctx->fcons_valid ? ctx->d_fcons : nullptr};
+  std::vector<float4> hpos(n), hvel(n), hfrc(n, make_float4(0, 0, 0, 0));
+  std::vector<unsigned long long> hpid(n);
+  std::vector<int> hinfo(n);
+  int got = 0;
+  cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_dump(ctx->P, D, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&got, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hpos.data(), dpos, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hvel.data(), dvel, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ctx->fcons_valid)
+    e = cudaMemcpyAsync(hfrc.data(), dfrc, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hpid.data(), dpid, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dpos); cudaFree(dvel); cudaFree(dfrc); cudaFree(dpid); cudaFree(dinfo);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (got != n) return CR_ERR_CUDA;
+  std::vector<int64_t> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return hpid[x] < hpid[y]; });
+  for (int64_t o = 0; o < n; ++o) {
+    const int64_t i = ord[o];
+    if (out->xyz) { out->xyz[3 * o] = hpos[i].x; out->xyz[3 * o + 1] = hpos[i].y; out->xyz[3 * o + 2] = hpos[i].z; }
+    if (out->vel) { out->vel[3 * o] = hvel[i].x; out->vel[3 * o + 1] = hvel[i].y; out->vel[3 * o + 2] = hvel[i].z; }
+    if (out->force) { out->force[3 * o] = hfrc[i].x; out->force[3 * o + 1] = hfrc[i].y; out->force[3 * o + 2] = hfrc[i].z; }
+    if (out->id) out->id[o] = hpid[i];
+    const int info = hinfo[i];
+    const int t = info & INFO_TYPE_MASK;
+    const int ion = (info & INFO_ION_BIT) ? 1 : 0;
+    if (out->type) out->type[o] = t;
+    if (out->state) out->state[o] = (int8_t)ion;
+    if (out->site_state && (t == CR_ACID || t == CR_BASE)) out->site_state[info >> INFO_SITE_SHIFT] = (int8_t)ion;
+  }
+  return cr_check(ctx);
+}
+
+extern "C" int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,
+                         uint32_t *out) {
+  if (n < 0 || (n > 0 && !out)) return CR_ERR_INVALID_ARG;
+  if (n == 0) return CR_OK;
+  uint4 *d = nullptr;
+  CR_CUDA(cudaMalloc((void **)&d, sizeof(uint4) * n));
+  cudaError_t e = launch_philox(c0, c1, c2, c3, k0, k1, n, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return cuda_fail(e);
+}

@@ -1,0 +1,52 @@
+// crmc_kernels.h -- launch interface between the C-ABI host code and the
+// kernels of libcrmc.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "crmc_common.h"
+
+namespace crmc {
+
+struct MdParams {
+  float dt, gamma, amp;   // time step, friction, sqrt(2 gamma kT / dt)
+  uint32_t key0, key1, eval;
+  int mode;               // 0 conservative, 1 + Langevin, 2 + Langevin + half kick
+  float4 *vel, *fout;     // slot arrays
+  const int *perm_slot, *bond_off, *bond_nbr;
+  int n_perm;
+  float fene_K, inv_R02;
+  int rcap;               // region particles staged in shared memory
+};
+
+struct RebuildBufs {
+  int *cnt;
+  float4 *pos;
+  unsigned long long *pid;
+  int *info;
+  float4 *vel, *frc;          // scratch copies
+  float4 *vel_src, *frc_src;  // primary velocity / force arrays
+};
+
+struct DumpBufs {
+  int *counter;
+  int cap;
+  float4 *pos, *vel, *frc;
+  unsigned long long *pid;
+  int *info;
+  const float4 *vel_src, *frc_src;
+};
+
+size_t phase_smem_bytes(const SysParams &P);
+size_t md_smem_bytes(int kb, int nrb, int rcap);
+cudaError_t launch_phase(const SysParams &P, int R, bool log, int grid, int threads, size_t smem, cudaStream_t s,
+                         uint32_t sweep, int colour, uint32_t k0, uint32_t k1);
+cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int kb, int nb_dim, int nrb, int threads,
+                             cudaStream_t s);
+cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s);
+cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s);
+cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
+cudaError_t launch_dump(const SysParams &P, const DumpBufs &D, cudaStream_t s);
+cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
+                          uint4 *out, cudaStream_t s);
+
+}  // namespace crmc

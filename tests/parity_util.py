@@ -1,0 +1,74 @@
+"""GPU-vs-oracle comparison helpers for the parity tests.
+
+Protocol (tolerances written here, used by every parity test):
+  * moves, chosen particle ids, no-eligible / edge / overlap flags: bit-exact;
+  * dE: |dE_gpu - dE_oracle| <= 1e-6 * max(|dE_oracle|, S) + 1e-9, where S is
+    the sum of |pair changes| (FP32 pair terms against FP64);
+  * accept decisions: identical, except a "tie" where |ln u - lnA_oracle| is
+    within tau = 1e-6 * S + 1e-12; the oracle is then re-run with the GPU's
+    decision forced at that trial and the comparison continues;
+  * the final charge states, ids and positions: identical.
+"""
+import numpy as np
+
+import oracle
+
+DE_REL = 1e-6
+STRUCT_FLAGS = oracle.F_NOELIG | oracle.F_EDGE | oracle.F_OVERLAP
+
+
+def de_tol(lo):
+    return DE_REL * np.maximum(np.abs(lo["dE"]), lo["S"]) + 1e-9
+
+
+def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8):
+    """Run the oracle over the same trials (forcing tie decisions) and
+    compare with the GPU trial log.  Returns (oracle, oracle log, ties)."""
+    oracle_kw = oracle_kw or {}
+    forced = np.full(n_trials, -1, np.int8)
+    ties = 0
+    while True:
+        o = oracle.Oracle(w, **oracle_kw)
+        lo = o.sweep(n_trials, seed, log=True, forced=forced)["log"]
+        assert np.array_equal(lg["move"], lo["move"]), _first(lg, lo, "move")
+        bad = np.flatnonzero((lg["flags"] & STRUCT_FLAGS) != (lo["flags"] & STRUCT_FLAGS))
+        dec = np.flatnonzero((lg["flags"] & oracle.F_ACC) != (lo["flags"] & oracle.F_ACC))
+        ids = np.flatnonzero((lg["id_a"] != lo["id_a"]) | (lg["id_b"] != lo["id_b"]))
+        first = min([x[0] for x in (bad, dec, ids) if len(x)] or [n_trials])
+        if first == n_trials:
+            break
+        if len(dec) and dec[0] == first and not (len(bad) and bad[0] == first) and not (len(ids) and ids[0] == first):
+            tau = 1e-6 * lo["S"][first] + 1e-12
+            if abs(lo["lnu"][first] - lo["lnA"][first]) <= tau and ties < max_ties:
+                forced[first] = 1 if (lg["flags"][first] & oracle.F_ACC) else 0
+                ties += 1
+                continue
+        raise AssertionError(f"trial {first}: gpu {lg[first]} oracle {lo[first]}")
+    ok = (lo["flags"] & (oracle.F_NOELIG | oracle.F_EDGE | oracle.F_OVERLAP)) == 0
+    err = np.abs(lg["dE"] - lo["dE"])
+    tol = de_tol(lo)
+    assert np.all(err[ok] <= tol[ok]), f"dE out of tolerance at {np.flatnonzero(ok & (err > tol))[:5]}"
+    lt = np.abs(lg["lnA"] - lo["lnA"])
+    assert np.all(lt[ok] <= tol[ok] + 1e-12 * np.abs(lo["lnA"][ok])), "lnA out of tolerance"
+    assert np.array_equal(lg["lnu"], lo["lnu"]) or np.allclose(lg["lnu"], lo["lnu"], rtol=1e-15, atol=0)
+    return o, lo, ties
+
+
+def _first(lg, lo, field):
+    i = int(np.flatnonzero(lg[field] != lo[field])[0])
+    return f"{field} differs first at trial {i}: gpu {lg[i]} oracle {lo[i]}"
+
+
+def compare_states(g, o, n_sites):
+    sg = g.state()
+    so = o.particles()
+    assert np.array_equal(sg["id"], so["id"]), "particle ids differ"
+    assert np.array_equal(sg["xyz"], so["xyz"]), "positions differ"
+    assert np.array_equal(sg["type"], so["type"])
+    assert np.array_equal(sg["state"], so["state"])
+    assert np.array_equal(sg["site_state"], o.site_states(n_sites))
+    co = o.counts()
+    for k in ("n", "n_Am", "n_Bp", "n_Xp", "n_Xm"):
+        assert sg[k] == co[k], (k, sg[k], co[k])
+    assert sg["net_charge"] == 0
+    return sg, so

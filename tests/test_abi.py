@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point that include/crmc.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "crmc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cr_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_07527_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("cr_init", "cr_sweep", "cr_md_forces", "cr_state"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2109_07527_gb300 import crmc
+    assert sorted(crmc.EXPORTS) == _declared()
+
+
+def test_strerror_names_every_code(lib):
+    lib.cr_strerror.restype = ctypes.c_char_p
+    seen = set()
+    for code in range(0, -10, -1):
+        s = lib.cr_strerror(code).decode()
+        assert s and s != "unknown error"
+        seen.add(s)
+    assert len(seen) == 10
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the ABI structs match the C layout compiled from the header."""
+    import subprocess
+    from paper_2109_07527_gb300 import crmc
+    structs = {"cr_system": crmc.cr_system, "cr_mu_ions": crmc.cr_mu_ions, "cr_sweep_stats": crmc.cr_sweep_stats,
+               "cr_state_view": crmc.cr_state_view, "cr_info": crmc.cr_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crmc.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            cf = "global" if f == "global_" else f
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {cf}));')
+    lines.append('  printf("cr_trial %zu\\n", sizeof(cr_trial));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+    assert int(got["cr_trial"]) == crmc.TRIAL_DTYPE.itemsize

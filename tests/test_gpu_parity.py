@@ -1,0 +1,175 @@
+"""GPU CR-MC path (through the C ABI) against the FP64 oracle, trial by trial.
+
+Decisions and charge states must be identical for the same seed, dE within
+1e-6 of the oracle relative to max(|dE|, sum |pair changes|) (see
+parity_util).  Cases cover several tiles and ragged domains, every move type,
+acid and base sites, ghost and interacting ions, the global and the coloured
+schedule, expanded WCA, and the full-size polyelectrolyte workload.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_07527_gb300 import workloads as W
+from parity_util import compare_logs, compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crmc():
+    from paper_2109_07527_gb300 import crmc as m
+    m._lib()
+    return m
+
+
+def _parity(crmc, w, sweeps, seed, **kw):
+    g = crmc.Context(w, **kw)
+    n = g.trials_per_sweep * sweeps
+    lg = g.sweep(n, seed, log=True)["log"]
+    okw = {k: v for k, v in kw.items() if k in ("schedule", "trials_per_domain", "domain_cells")}
+    o, lo, ties = compare_logs(w, lg, n, seed, okw)
+    compare_states(g, o, w.n_sites)
+    return g, o, lg, lo, ties
+
+
+def test_philox_device_matches_oracle(crmc):
+    out = crmc.philox(0, 7, 11, 3, 0xDEADBEEF, 0x12345678, 4096)
+    for i in (0, 1, 17, 4095):
+        assert out[i].tolist() == oracle.philox([i, 7, 11, 3], [0xDEADBEEF, 0x12345678]).tolist()
+    kat = crmc.philox(0, 0, 0, 0, 0, 0, 1)[0]
+    assert kat.tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+@pytest.mark.parametrize("schedule,m", [(0, 4), (1, 256)])
+def test_parity_ideal_ghost_ions(crmc, schedule, m):
+    w = W.ideal(n_sites=50, pH=5.0, pKa=5.0, n_pairs=20, seed=11, schedule=schedule, trials_per_domain=m)
+    _, _, lg, _, ties = _parity(crmc, w, 20, 5)
+    assert (lg["flags"] & 1).sum() > 100
+
+
+@pytest.mark.parametrize("n_base", [0, 3])
+def test_parity_interacting_sites(crmc, n_base):
+    w = W.enum_sites(n_sites=8, n_base=n_base, seed=3, schedule=1, trials_per_domain=256)
+    if n_base:
+        w.params["pH"] = 7.0
+        w.pK[:] = 7.0
+    _parity(crmc, w, 20, 9)
+
+
+@pytest.mark.parametrize("schedule,m,sweeps", [(0, 10, 16), (1, 500, 20)])
+def test_parity_config1_polyacid(crmc, schedule, m, sweeps):
+    w = W.config1(seed=1, schedule=schedule, trials_per_domain=m)
+    g, o, lg, lo, ties = _parity(crmc, w, sweeps, 1)
+    acc = lg["flags"] & 1
+    assert acc.sum() > 50
+    moves = set(np.unique(lg["move"][acc == 1]).tolist())
+    assert {0, 1, 4, 5} <= moves  # acid and salt, both directions
+
+
+def test_parity_config2_half_box(crmc):
+    """16 chains x 200 at 1/8 of the volume: several domains per colour, ragged cell occupancy."""
+    w = W.config2(seed=2, scale=0.5)
+    _parity(crmc, w, 6, 3)
+
+
+def test_parity_config3_nanoparticles(crmc):
+    """Acid and base sites on two nanoparticle shells, expanded WCA cores (Delta = R - r)."""
+    w = W.config3(separation=12.0, seed=1, L=60.0, n_sites=300)
+    _parity(crmc, w, 8, 4)
+
+
+def test_parity_full_size_polyelectrolyte(crmc):
+    """The benchmark workload itself (L = 120, 3200 sites, ~4000 ion pairs), two sweeps."""
+    w = W.config2(seed=1)
+    g, o, lg, lo, ties = _parity(crmc, w, 2, 1)
+    assert len(lg) == 20000
+    assert ties <= 2
+
+
+def test_repeated_calls_continue_the_chain(crmc):
+    """Two calls of n trials give the same chain as the oracle's two calls."""
+    w = W.config1(seed=4)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    n = g.trials_per_sweep * 3
+    for seed in (7, 7, 8):
+        lg = g.sweep(n, seed, log=True)["log"]
+        lo = o.sweep(n, seed, log=True)["log"]
+        assert np.array_equal(lg["flags"], lo["flags"])
+    compare_states(g, o, w.n_sites)
+
+
+def test_no_sites_only_salt_moves(crmc):
+    w = W.ideal(n_sites=0, n_pairs=30, seed=2)
+    w.params["ion_coupling"] = 1
+    w.params["lB"] = 2.0
+    _parity(crmc, w, 10, 2)
+
+
+def test_empty_box(crmc):
+    w = W.ideal(n_sites=0, n_pairs=0, seed=2)
+    _parity(crmc, w, 5, 1)
+
+
+def test_stats_count_every_trial(crmc):
+    w = W.config1(seed=5)
+    g = crmc.Context(w)
+    n = g.trials_per_sweep * 4
+    st = g.sweep(n, 3, stats=True)["stats"]
+    assert st["trials"] == n and st["attempts"].sum() == n
+    assert 0 < st["accepts"].sum() < n
+
+
+def test_errors(crmc):
+    w = W.config1(seed=1)
+    g = crmc.Context(w)
+    with pytest.raises(crmc.CrError) as e:
+        g.sweep(g.trials_per_sweep + 1, 1)
+    assert e.value.code == -1
+    bad = W.config1(seed=1)
+    bad.state[0] = 1  # one ionised acid without a counterion
+    with pytest.raises(crmc.CrError) as e:
+        crmc.Context(bad)
+    assert e.value.code == -2
+    small = W.config1(seed=1)
+    small.params["rc"] = 25.0  # rc > L/2
+    with pytest.raises(crmc.CrError) as e:
+        crmc.Context(small)
+    assert e.value.code == -1
+
+
+def test_cell_overflow_is_reported(crmc):
+    w = W.ideal(n_sites=40, n_pairs=200, seed=1, pIS=0.0)
+    g = crmc.Context(w, cell_capacity=8)
+    with pytest.raises(crmc.CrError) as e:
+        for s in range(50):
+            g.sweep(g.trials_per_sweep * 4, s, stats=True)
+    assert e.value.code == -3
+
+
+def test_gpu_titration_matches_exact_closed_form(crmc):
+    """GPU alpha of ideal acids at three pH values within 0.005 of the exact
+    finite-box result (Eq. QQ with E = 0)."""
+    from scipy.special import gammaln, ive
+    n, L = 50, 40.0
+    for pH in (4.0, 5.0, 6.0):
+        w = W.ideal(n_sites=n, L=L, pH=pH, pKa=5.0, n_pairs=20, seed=11, trials_per_domain=8)
+        g = crmc.Context(w)
+        ln10 = math.log(10.0)
+        pIX = -math.log10(10 ** -2.0 + 10 ** -min(pH, 14 - pH))
+        lnz = math.log(0.602214076 * (L * 0.355) ** 3) - ln10 * pIX
+        k = np.arange(n + 1)
+        logP = gammaln(n + 1) - gammaln(k + 1) - gammaln(n - k + 1) + k * ln10 * (pH - 5.0) + np.log(ive(k, 2 * math.exp(lnz)))
+        P = np.exp(logP - logP.max())
+        P /= P.sum()
+        exact = float((k * P).sum() / n)
+        tps = g.trials_per_sweep
+        g.sweep(tps * 50, 1)
+        vals = []
+        for b in range(400):
+            g.sweep(tps * 4, 2 + b)
+            vals.append(g.counts()["n_Am"] / n)
+        assert abs(np.mean(vals) - exact) < 0.005, (pH, np.mean(vals), exact)
