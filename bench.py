@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the CR-MC hot path on GB300 (prints one JSON line).
+
+Workload: the polyelectrolyte solution of the paper's method at the size the
+metric is quoted on -- 16 chains x 200 acid beads (pKa 4.5, pH 4.5), L = 120
+sigma, ~4000 ion pairs, r_c = 12 sigma, l_B = 2 sigma -- with synthetic,
+seeded coordinates.  One step = one MD/CR-MC cycle: 10^4 CR-MC trials (one
+sweep of 1000 domains x 10 trials) + one velocity-Verlet/Langevin MD step
+(dt = 0.005, gamma = 1); the full job is 100 steps (10^6 trials).  Inputs
+are resident in HBM; L2 is flushed (256 MB write) between timed steps.
+
+--impl reference times the CPU oracle on the same workload (rank 0 only).
+Under torchrun each rank runs an independent replica (no collective on the
+data path; scaling "weak").
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CR-MC trials/s on 1 GB300 (plain vs surrogate-DA/batched) at |Δα|≤0.005"
+WORKLOAD = ("polyelectrolyte solution: 16 chains x 200 acid beads (pKa 4.5), pH 4.5, L=120 sigma, ~4000 ion pairs, "
+            "rc=12, lB=2, DSF alpha=0.2; step = 1e4 CR-MC trials (1000 domains x 10) + 1 MD step (dt 0.005, gamma 1)")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(rank):
+    from paper_2109_07527_gb300 import workloads as W
+    return W.config2(seed=1 + rank, pH=4.5, trials_per_domain=10)
+
+
+def bytes_per_trial(L, rc, n_particles):
+    """Algorithmic bytes of one trial: for each of the 2 changed particles the
+    27-cell stencil at the reference cell side a = L / floor(L / rc), 16 B per
+    particle (float4 position + charge), plus 64 B for the commit."""
+    a = L / math.floor(L / rc)
+    rho = n_particles / L ** 3
+    return 2.0 * 27.0 * a ** 3 * rho * 16.0 + 64.0
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except (OSError, ValueError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("crmc_kernels.cu", "crmc_device.cuh", "crmc_common.h"):
+        h.update(open(os.path.join(ROOT, "paper_2109_07527_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the phase kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "cr_phase_polyelectrolyte_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_sha") != kernel_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.rows = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self, gpu_index):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        rows = [r for r in self.rows if len(r) >= 9 and r[0] == str(gpu_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(w, sample_sweeps=10):
+    """The oracle as it stands (single thread) on a bounded sample of the
+    workload: sample_sweeps sweeps of 1000 trials (one trial per domain) and one
+    MD step, i.e. the workload's 1 MD step : 1e4 trials mix."""
+    import oracle
+    o = oracle.Oracle(w, trials_per_domain=1)
+    t0 = time.perf_counter()
+    n = 0
+    for s in range(sample_sweeps):
+        o.sweep(o.trials_per_sweep, 1000 + s)
+        n += o.trials_per_sweep
+    o.md_step(1, 0.005, 1.0, 5)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "trials/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_sweeps} sweeps x {o.trials_per_sweep} trials (1 trial per domain) + 1 MD step "
+                      f"of the same workload, {dt:.1f} s on 1 host thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = workload(0)
+    o = oracle.Oracle(w, trials_per_domain=1)
+    tps = o.trials_per_sweep
+    for s in range(args.warmup):
+        o.sweep(tps, 7 + s)
+    t0 = time.perf_counter()
+    n = 0
+    for s in range(args.steps):
+        o.sweep(tps, 100 + s)
+        n += tps
+        if s % 10 == 9:
+            o.md_step(1, 0.005, 1.0, 11)
+    dt = time.perf_counter() - t0
+    v = n / dt
+    sample = (f"{args.steps} steps of {tps} trials (1 trial per domain) with one MD step per 10 steps "
+              f"(the 1 MD : 1e4 trials mix), {dt:.1f} s, 1 host thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
+           "cpu_baseline": {"value": v, "unit": "trials/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_2109_07527_gb300 import crmc
+
+    w = workload(rank)
+    g = crmc.Context(w)
+    info = g.info
+    per_step = g.trials_per_sweep
+    dt, gamma = 0.005, 1.0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for s in range(args.warmup):
+        g.sweep(per_step, 1 + s)
+        g.md_step(1, dt, gamma, 1000 + s)
+    g.check()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    g.set_timing(True)
+    g.timing(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        starts[s].record(stream)
+        g.sweep(per_step, 100 + s)
+        g.md_step(1, dt, gamma, 5000 + s)
+        ends[s].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    cl = clocks.stop(local)
+    tm = g.timing(reset=True)
+    g.set_timing(False)
+    g.check()
+    ms = sum(starts[s].elapsed_time(ends[s]) for s in range(args.steps))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    counts = g.counts()
+    total_trials = per_step * args.steps * world
+    value = total_trials / (ms / 1e3)
+
+    # roofline of the colour-phase kernel (the dominant kernel)
+    L = float(w.params["box_L"])
+    bpt = bytes_per_trial(L, float(w.params["rc"]), counts["n"])
+    trials_per_launch = per_step / 8
+    avg_launch_s = tm["phase_ms"] / max(tm["phase_launches"], 1) / 1e3
+    achieved = bpt * trials_per_launch / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "kernel": "k_cr_phase", "peak_source": peak_kind,
+                "bytes_per_trial": bpt, "trials_per_launch": trials_per_launch,
+                "avg_launch_us": avg_launch_s * 1e6, "phase_share_of_step": tm["phase_ms"] / ms,
+                "md_force_ms_per_step": tm["md_ms"] / args.steps}
+
+    # end to end through the public API with host buffers: each step uploads
+    # the configuration from pinned host memory (cr_load), runs the cycle and
+    # reads the full state back (cr_state)
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        st = g.state()
+        n = int(st["n"])
+        cls0 = np.ascontiguousarray(w.cls, np.int32)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hx, hv, ht, hs = pin(st["xyz"]), pin(st["vel"]), pin(st["type"]), pin(st["state"])
+        ion = (st["type"] == 3) | (st["type"] == 4)
+        hc = pin(np.where(ion, 0, cls0[np.minimum(st["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32))
+        e2e_steps = max(3, min(args.steps, 20))
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(e2e_steps):
+            g.load(n, hx.data_ptr(), hv.data_ptr(), ht.data_ptr(), hc.data_ptr(), hs.data_ptr())
+            h2d += n * (12 + 12 + 4 + 4 + 1)
+            g.sweep(per_step, 9000 + s)
+            g.md_step(1, dt, gamma, 9500 + s)
+            out = g.state()
+            d2h += int(out["n"]) * (16 + 16 + 8 + 4) + 64
+            n = int(out["n"])
+            ion = (out["type"] == 3) | (out["type"] == 4)
+            hx, hv, ht, hs = pin(out["xyz"]), pin(out["vel"]), pin(out["type"]), pin(out["state"])
+            hc = pin(np.where(ion, 0, cls0[np.minimum(out["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32))
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
+               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
+               "note": "per step: cr_load from pinned host buffers + 1e4 trials + 1 MD step + cr_state readback"}
+
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 pair terms / i64 fixed-point sums / f64 Metropolis",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "l2": "flushed (256 MB write) between timed steps",
+                      "trials_per_step": per_step, "md_steps_per_step": 1, "domains": info["nd"] ** 3,
+                      "cell_side": info["cell_side"], "threads_per_domain": 128,
+                      "alpha_end": counts["alpha"], "particles_end": counts["n"],
+                      "parallelism": f"{world} independent replica(s)"},
+           "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e,
+           "md_cr_cycles_per_s": args.steps * world / (ms / 1e3)}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

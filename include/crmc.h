@@ -134,7 +134,7 @@ typedef struct {
   uint64_t id_a; /* site (acid/base) or first ion (salt) */
   uint64_t id_b; /* ion paired with the site, or second ion */
   double dE;     /* energy change (kT); +inf on overlap */
-  double S;      /* sum of |pair changes| (tolerance scale) */
+  double S;      /* gross magnitude of the summed pair terms (tolerance scale) */
   double lnA;    /* log acceptance ratio */
   double lnu;    /* log of the Metropolis uniform */
 } cr_trial;
@@ -145,7 +145,7 @@ typedef struct {
   double alpha;          /* n_A- / n_A (0 when there are no acids) */
   float *xyz;            /* [3n] */
   float *vel;            /* [3n] */
-  float *force;          /* [3n] last evaluated total force */
+  float *force;          /* [3n] forces of the last cr_md_forces (zero once a sweep or step ran) */
   uint64_t *id;          /* [n] particle ids (input index; inserted ions >= 2^32) */
   int32_t *type;         /* [n] */
   int8_t *state;         /* [n] 1 = ionised site */
@@ -185,8 +185,27 @@ int cr_md_forces(cr_ctx *ctx);
  * BOND_BROKEN, CELL_OVERFLOW. */
 int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
 
-/* Fill the view (counts always; arrays when non-NULL) and synchronise. */
+/* Fill the view (counts always; arrays when non-NULL) and synchronise.
+ * Arrays are ordered by particle id. */
 int cr_state(cr_ctx *ctx, cr_state_view *out);
+
+/* Replace the configuration with n particles from host arrays (xyz [3n],
+ * vel [3n] or NULL, type [n], cls [n], state [n]; pinned memory gives
+ * asynchronous copies).  Particle ids become the indices.  Bonded and site
+ * particles must be those given to cr_init, at the same indices (the state
+ * arrays returned by cr_state qualify); ions may differ.  Cells are rebuilt
+ * on the device.  Errors: INVALID_ARG, NOT_NEUTRAL, CELL_OVERFLOW (at the
+ * next synchronising call). */
+int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type, const int32_t *cls,
+            const int8_t *state);
+
+/* Record CUDA events around every colour-phase and MD-force launch. */
+int cr_set_timing(cr_ctx *ctx, int32_t enable);
+
+/* Synchronise and report: ms[2] summed device time and launches[2] of the
+ * colour-phase kernel (0) and the MD force kernel (1) since the last reset,
+ * and the number of kernels this context launched.  reset != 0 zeroes them. */
+int cr_get_timing(cr_ctx *ctx, double *ms, int64_t *launches, int64_t *launches_total, int32_t reset);
 
 /* Geometry and schedule of the context. */
 int cr_get_info(const cr_ctx *ctx, cr_info *out);

@@ -367,6 +367,21 @@ static double pair_u(const Oracle *o, double qi, int ci, double qj, int cj, doub
   return u;
 }
 
+/* Gross magnitude of one pair's energy in a given state: the sum of the
+ * absolute values of the components that FP32 evaluation rounds, used as the
+ * scale of the FP32-vs-FP64 tolerance (the pair energies themselves cancel
+ * internally near the cutoffs). */
+static double gross_coul(const Oracle *o, double qi, double qj, double r) {
+  if (!(r < o->rc) || qi == 0.0 || qj == 0.0) return 0.0;
+  return fabs(o->lB * qi * qj) * (erfc(o->alpha * r) / r + o->phi_c1 + o->phi_c2 * fabs(r - o->rc));
+}
+static double gross_wca(const Oracle *o, int ci, int cj, double r) {
+  if (!o->on[ci][cj] || !(r < o->wcut[ci][cj])) return 0.0;
+  double s = r - o->del[ci][cj];
+  double sr6 = pow(o->sig[ci][cj] / s, 6.0);
+  return o->eps[ci][cj] * (4.0 * sr6 * sr6 + 4.0 * sr6 + 1.0);
+}
+
 typedef struct {
   int idx;              /* index of an existing particle, -1 for an inserted one */
   float x, y, z;
@@ -383,8 +398,9 @@ static double dist(const Oracle *o, float ax, float ay, float az, float bx, floa
 }
 
 /* Delta E = E_new - E_old, summed pair by pair over every pair that contains a
- * changed particle, plus the DSF self-energy change.  S = sum of |pair
- * changes|, the scale for the FP32 tolerance. */
+ * changed particle, plus the DSF self-energy change.  S = the gross
+ * magnitude of the summed terms (gross_coul / gross_wca of the states that
+ * differ, plus |self change|), the scale of the FP32 tolerance. */
 static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, double *S_out) {
   double dE = 0.0, S = 0.0;
   *overlap = 0;
@@ -401,7 +417,9 @@ static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, 
       double du = un - uo;
       if (ov || !(fabs(du) < BIG_TERM)) { *overlap = 1; continue; }
       dE += du;
-      S += fabs(du);
+      S += (c[a].pres_new ? gross_coul(o, c[a].q_new, qj, r) : 0.0) +
+           (c[a].pres_old ? gross_coul(o, c[a].q_old, qj, r) : 0.0);
+      if (c[a].pres_new != c[a].pres_old) S += gross_wca(o, c[a].cls, o->cls[j], r);
     }
   }
   /* pairs among the changed particles themselves */
@@ -416,7 +434,9 @@ static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, 
         double du = un - uo;
         if (ov || !(fabs(du) < BIG_TERM)) { *overlap = 1; continue; }
         dE += du;
-        S += fabs(du);
+        int pn = c[a].pres_new && c[b].pres_new, po = c[a].pres_old && c[b].pres_old;
+        S += (pn ? gross_coul(o, c[a].q_new, c[b].q_new, r) : 0.0) + (po ? gross_coul(o, c[a].q_old, c[b].q_old, r) : 0.0);
+        if (pn != po) S += gross_wca(o, c[a].cls, c[b].cls, r);
       }
   }
   if (o->dsf_self && g_plant != PLANT_DROP_SELF) {
@@ -815,16 +835,24 @@ static int forces_cons(const Oracle *o, double *F, double *fs) {
       double d[3] = {min_image((double)o->x[i] - o->x[j], o->L), min_image((double)o->y[i] - o->y[j], o->L),
                      min_image((double)o->z[i] - o->z[j], o->L)};
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      double f = 0.0; /* magnitude along (r_i - r_j)/r, positive = repulsive */
-      if (r < o->rc && qi != 0.0 && qj != 0.0) f += o->lB * qi * qj * dsf_force(o, r);
+      double f = 0.0, g = 0.0; /* along (r_i - r_j)/r, positive = repulsive; g: gross magnitude */
+      if (r < o->rc && qi != 0.0 && qj != 0.0) {
+        double ar = o->alpha * r;
+        f += o->lB * qi * qj * dsf_force(o, r);
+        g += fabs(o->lB * qi * qj) * (erfc(ar) / (r * r) + 2.0 * o->alpha / sqrt(M_PI) * exp(-ar * ar) / r + o->phi_c2);
+      }
       int ci = o->cls[i], cj = o->cls[j];
-      if (o->on[ci][cj] && r < o->wcut[ci][cj]) f += wca_f(o->eps[ci][cj], o->sig[ci][cj], r - o->del[ci][cj]);
+      if (o->on[ci][cj] && r < o->wcut[ci][cj]) {
+        double s = r - o->del[ci][cj], sr6 = pow(o->sig[ci][cj] / s, 6.0);
+        f += wca_f(o->eps[ci][cj], o->sig[ci][cj], s);
+        g += 24.0 * o->eps[ci][cj] * (2.0 * sr6 * sr6 + sr6) / s;
+      }
       if (f == 0.0) continue;
       for (int c = 0; c < 3; ++c) {
         double fc = f * d[c] / r;
         F[3 * i + c] += fc;
         F[3 * j + c] -= fc;
-        if (fs) { fs[3 * i + c] += fabs(fc); fs[3 * j + c] += fabs(fc); }
+        if (fs) { fs[3 * i + c] += g * fabs(d[c]) / r; fs[3 * j + c] += g * fabs(d[c]) / r; }
       }
     }
   }

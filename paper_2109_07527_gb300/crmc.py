@@ -71,7 +71,8 @@ TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id
 
 # every entry point of include/crmc.h
 EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
-           "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox")
+           "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
+           "cr_get_timing")
 
 _L = None
 
@@ -105,6 +106,12 @@ def _lib():
         lib.cr_destroy.argtypes = [P]
         lib.cr_strerror.restype = C.c_char_p
         lib.cr_strerror.argtypes = [C.c_int]
+        lib.cr_load.restype = C.c_int
+        lib.cr_load.argtypes = [P, C.c_int32, P, P, P, P, P]
+        lib.cr_set_timing.restype = C.c_int
+        lib.cr_set_timing.argtypes = [P, C.c_int32]
+        lib.cr_get_timing.restype = C.c_int
+        lib.cr_get_timing.argtypes = [P, P, P, P, C.c_int32]
         lib.cr_philox.restype = C.c_int
         lib.cr_philox.argtypes = [C.c_uint32] * 6 + [C.c_int32, P]
         _L = lib
@@ -216,6 +223,23 @@ class Context:
 
     def md_step(self, n_steps, dt, gamma, seed):
         _chk(self._lib.cr_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_md_step")
+
+    def load(self, n, xyz_ptr, vel_ptr, type_ptr, cls_ptr, state_ptr):
+        """Upload a configuration from host buffers given as raw pointers (ints) or numpy arrays."""
+        conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
+        _chk(self._lib.cr_load(self._h, int(n), conv(xyz_ptr), conv(vel_ptr), conv(type_ptr), conv(cls_ptr),
+                               conv(state_ptr)), "cr_load")
+
+    def set_timing(self, on=True):
+        _chk(self._lib.cr_set_timing(self._h, 1 if on else 0), "cr_set_timing")
+
+    def timing(self, reset=True):
+        ms = np.zeros(2)
+        la = np.zeros(2, np.int64)
+        tot = np.zeros(1, np.int64)
+        _chk(self._lib.cr_get_timing(self._h, _p(ms), _p(la), _p(tot), 1 if reset else 0), "cr_get_timing")
+        return dict(phase_ms=float(ms[0]), phase_launches=int(la[0]), md_ms=float(ms[1]), md_launches=int(la[1]),
+                    launches=int(tot[0]))
 
     def check(self):
         _chk(self._lib.cr_check(self._h), "cr_check")

@@ -43,11 +43,31 @@ struct cr_ctx {
   int *d_err = nullptr, *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr, *d_counter = nullptr;
   cr_trial *d_log = nullptr;
   size_t log_cap = 0;
+  // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
+  float *d_in_xyz = nullptr, *d_in_vel = nullptr;
+  int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
+  int8_t *d_in_state = nullptr;
+  float4 *d_dump_pos = nullptr, *d_dump_vel = nullptr, *d_dump_frc = nullptr;
+  unsigned long long *d_dump_pid = nullptr;
+  int *d_dump_info = nullptr;
+  float4 *h_dump_pos = nullptr, *h_dump_vel = nullptr, *h_dump_frc = nullptr;
+  unsigned long long *h_dump_pid = nullptr;
+  int *h_dump_info = nullptr;
   // MD
   double fene_K = 30.0, fene_R0 = 1.5;
   uint64_t sweep = 0;
   uint32_t md_eval = 0;
   bool f_valid = false, fcons_valid = false;
+  // input encoding kept for cr_load: type of every input particle, site index
+  std::vector<int> init_type, init_site;
+  // kernel timing (CUDA events on the context stream) and launch counters
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_pairs[2];  // [0] phase kernel, [1] MD force kernel
+  size_t ev_next = 0;
+  double ms[2] = {0.0, 0.0};
+  int64_t launches[2] = {0, 0};
+  int64_t launches_total = 0;
 };
 
 namespace {
@@ -113,16 +133,112 @@ static void free_ctx(cr_ctx *c) {
   if (!c) return;
   void *ptrs[] = {c->d_cnt, c->d_cnt2, c->d_info, c->d_info2, c->d_pos, c->d_pos2, c->d_vel, c->d_vel2,
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
-                  c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log};
+                  c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log,
+                  c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
+                  c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info};
+  for (void *p : hptrs)
+    if (p) cudaFreeHost(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
+}
+
+// CUDA-event timing of the two main kernels (kind 0: colour phase, 1: MD forces)
+static void tbegin(cr_ctx *c, int kind, int *idx) {
+  *idx = -1;
+  if (!c->timing) return;
+  while (c->ev_pool.size() < c->ev_next + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->ev_pool.push_back(e);
+  }
+  *idx = (int)c->ev_next;
+  c->ev_next += 2;
+  cudaEventRecord(c->ev_pool[*idx], c->stream);
+  (void)kind;
+}
+static void tend(cr_ctx *c, int kind, int idx) {
+  if (idx < 0) return;
+  cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+  c->ev_pairs[kind].push_back({idx, idx + 1});
+}
+static void tcollect(cr_ctx *c) {
+  for (int k = 0; k < 2; ++k) {
+    for (auto &pr : c->ev_pairs[k]) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, c->ev_pool[pr.first], c->ev_pool[pr.second]) == cudaSuccess) c->ms[k] += ms;
+      c->launches[k]++;
+    }
+    c->ev_pairs[k].clear();
+  }
+  c->ev_next = 0;
 }
 
 extern "C" void cr_destroy(cr_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   free_ctx(ctx);
+}
+
+// Lay n particles (input order = id order) into cell-major host arrays.
+struct Layout {
+  std::vector<int> cnt, perm;
+  std::vector<float4> pos, vel;
+  std::vector<unsigned long long> pid;
+  std::vector<int> info;
+  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
+  int max_occ = 0;
+};
+
+static int layout_particles(const SysParams &P, int n, const float *xyz, const float *vel, const int32_t *type,
+                            const int32_t *cls, const int8_t *state, const std::vector<int> &site_of, int cap,
+                            int n_perm, Layout &Lo) {
+  const int nc = P.nc;
+  std::vector<int> cell(n);
+  Lo.cnt.assign(P.ncell, 0);
+  for (int i = 0; i < n; ++i) {
+    const int cx = cell_of_host(xyz[3 * i], P.scf, nc), cy = cell_of_host(xyz[3 * i + 1], P.scf, nc),
+              cz = cell_of_host(xyz[3 * i + 2], P.scf, nc);
+    cell[i] = cx + nc * (cy + nc * cz);
+    Lo.cnt[cell[i]]++;
+  }
+  Lo.max_occ = n > 0 ? *std::max_element(Lo.cnt.begin(), Lo.cnt.end()) : 0;
+  if (cap <= 0) return CR_OK;  // occupancy only
+  if (Lo.max_occ > cap) return CR_ERR_CELL_OVERFLOW;
+  const size_t nslot = (size_t)P.ncell * cap;
+  std::fill(Lo.cnt.begin(), Lo.cnt.end(), 0);
+  Lo.pos.assign(nslot, make_float4(0, 0, 0, 0));
+  Lo.vel.assign(nslot, make_float4(0, 0, 0, 0));
+  Lo.pid.assign(nslot, 0ull);
+  Lo.info.assign(nslot, 0);
+  Lo.perm.assign(std::max(n_perm, 1), -1);
+  for (int i = 0; i < n; ++i) {  // ascending i == ascending id within every cell
+    const int cc = cell[i];
+    const int g = cc * cap + Lo.cnt[cc]++;
+    const int t = type[i];
+    const int ion = (t == CR_ACID || t == CR_BASE) && state[i] ? 1 : 0;
+    float q = 0.0f;
+    int cl = cls[i];
+    if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
+    else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
+    else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
+    else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+    Lo.pos[g] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], q);
+    if (vel) Lo.vel[g] = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0f);
+    Lo.pid[g] = (unsigned long long)i;
+    const int site = site_of[i] < 0 ? 0 : site_of[i];
+    Lo.info[g] = t | (cl << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
+    if (i < n_perm) Lo.perm[i] = g;
+    int kd = K_OTHER;
+    if (t == CR_ACID) kd = ion ? K_A1 : K_A0;
+    else if (t == CR_BASE) kd = ion ? K_B1 : K_B0;
+    else if (t == CR_XP) kd = K_XP;
+    else if (t == CR_XM) kd = K_XM;
+    Lo.kinds[kd]++;
+  }
+  return CR_OK;
 }
 
 extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const double *pK, cr_mu_ions mu, double lB,
@@ -172,6 +288,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.ncell = nc * nc * nc;
   P.Lf = Lf;
   P.invL = (float)(1.0 / L);
+  P.halfL = (float)(0.5 * L);
+  P.Ld = L;
+  P.halfLd = 0.5 * L;
   P.scf = (float)((double)nc / L);
   P.a = a;
   c->per_sweep = (int64_t)P.nd * P.nd * P.nd * P.m;
@@ -194,6 +313,10 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
       w.del = (float)sys->wca_del[4 * i + j];
       const double cut = sys->wca_del[4 * i + j] + std::pow(2.0, 1.0 / 6.0) * sys->wca_sig[4 * i + j];
       w.wcut2 = (float)(cut * cut);
+      w.eps_d = sys->wca_eps[4 * i + j];
+      w.sig_d = sys->wca_sig[4 * i + j];
+      w.del_d = sys->wca_del[4 * i + j];
+      w.wcut_d = cut;
       w.on = (i != CR_CLS_NONE && j != CR_CLS_NONE && sys->wca_on[4 * i + j]) ? 1 : 0;
     }
   if (sys->ion_cls < 0 || sys->ion_cls > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
@@ -237,48 +360,21 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   c->n_sites = (int)lnK.size();
   c->capacity = sys->capacity;
 
-  std::vector<int> cell(n);
-  std::vector<int> occ(P.ncell, 0);
-  for (int i = 0; i < n; ++i) {
-    const int cx = cell_of_host(sys->xyz[3 * i], P.scf, nc), cy = cell_of_host(sys->xyz[3 * i + 1], P.scf, nc),
-              cz = cell_of_host(sys->xyz[3 * i + 2], P.scf, nc);
-    cell[i] = cx + nc * (cy + nc * cz);
-    occ[cell[i]]++;
-  }
-  const int max_occ = n > 0 ? *std::max_element(occ.begin(), occ.end()) : 0;
+  Layout Lo;
+  layout_particles(P, n, sys->xyz, sys->vel, sys->type, sys->cls, sys->state, site_of, 0, n, Lo);
+  const int max_occ = Lo.max_occ;
   int cap = sys->cell_capacity > 0 ? sys->cell_capacity : std::max(32, ((2 * max_occ + 16) + 7) / 8 * 8);
   if (max_occ > cap) { free_ctx(c); return CR_ERR_CELL_OVERFLOW; }
   P.cap = cap;
   const size_t nslot = (size_t)P.ncell * cap;
-  std::vector<int> h_cnt(P.ncell, 0);
-  std::vector<float4> h_pos(nslot, make_float4(0, 0, 0, 0)), h_vel(nslot, make_float4(0, 0, 0, 0));
-  std::vector<unsigned long long> h_pid(nslot, 0);
-  std::vector<int> h_info(nslot, 0), h_perm(std::max(n, 1), -1);
-  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int i = 0; i < n; ++i) {  // ascending i == ascending id within every cell
-    const int cc = cell[i];
-    const int g = cc * cap + h_cnt[cc]++;
-    const int t = sys->type[i];
-    const int ion = (t == CR_ACID || t == CR_BASE) && sys->state[i] ? 1 : 0;
-    float q = 0.0f;
-    int cls = sys->cls[i];
-    if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
-    else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
-    else if (t == CR_XP) { q = P.ion_q; cls = P.ion_cls; }
-    else if (t == CR_XM) { q = -P.ion_q; cls = P.ion_cls; }
-    h_pos[g] = make_float4(sys->xyz[3 * i], sys->xyz[3 * i + 1], sys->xyz[3 * i + 2], q);
-    if (sys->vel) h_vel[g] = make_float4(sys->vel[3 * i], sys->vel[3 * i + 1], sys->vel[3 * i + 2], 0.0f);
-    h_pid[g] = (unsigned long long)i;
-    const int site = site_of[i] < 0 ? 0 : site_of[i];
-    h_info[g] = t | (cls << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
-    h_perm[i] = g;
-    int kd = K_OTHER;
-    if (t == CR_ACID) kd = ion ? K_A1 : K_A0;
-    else if (t == CR_BASE) kd = ion ? K_B1 : K_B0;
-    else if (t == CR_XP) kd = K_XP;
-    else if (t == CR_XM) kd = K_XM;
-    kinds[kd]++;
-  }
+  std::vector<int> occ = Lo.cnt;
+  layout_particles(P, n, sys->xyz, sys->vel, sys->type, sys->cls, sys->state, site_of, cap, n, Lo);
+  std::vector<int> &h_cnt = Lo.cnt, &h_info = Lo.info, &h_perm = Lo.perm;
+  std::vector<float4> &h_pos = Lo.pos, &h_vel = Lo.vel;
+  std::vector<unsigned long long> &h_pid = Lo.pid;
+  long long *kinds = Lo.kinds;
+  c->init_type.assign(sys->type, sys->type + n);
+  c->init_site = site_of;
   c->n_other = (int)kinds[K_OTHER];
 
   // ---- bonds (CSR by permanent particle)
@@ -379,7 +475,29 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_bond_off, n + 1);
   ALLOC(c->d_bond_nbr, std::max(2 * nb, 1));
   ALLOC(c->d_counter, 1);
+  ALLOC(c->d_in_xyz, 3 * (size_t)sys->capacity);
+  ALLOC(c->d_in_vel, 3 * (size_t)sys->capacity);
+  ALLOC(c->d_in_type, (size_t)sys->capacity);
+  ALLOC(c->d_in_cls, (size_t)sys->capacity);
+  ALLOC(c->d_in_state, (size_t)sys->capacity);
+  ALLOC(c->d_site_map, (size_t)std::max(n, 1));
+  ALLOC(c->d_dump_pos, (size_t)sys->capacity);
+  ALLOC(c->d_dump_vel, (size_t)sys->capacity);
+  ALLOC(c->d_dump_frc, (size_t)sys->capacity);
+  ALLOC(c->d_dump_pid, (size_t)sys->capacity);
+  ALLOC(c->d_dump_info, (size_t)sys->capacity);
 #undef ALLOC
+  {
+    const size_t cp = (size_t)std::max(sys->capacity, 1);
+    if (cudaHostAlloc((void **)&c->h_dump_pos, cp * sizeof(float4), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_dump_vel, cp * sizeof(float4), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_dump_frc, cp * sizeof(float4), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_dump_pid, cp * sizeof(unsigned long long), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_dump_info, cp * sizeof(int), 0) != cudaSuccess) {
+      free_ctx(c);
+      return CR_ERR_NOMEM;
+    }
+  }
 #define COPY(dst, src, n_)                                                                           \
   if ((rc_ = cuda_fail(cudaMemcpy((dst), (src), (n_) * sizeof(*(src)), cudaMemcpyHostToDevice))) != CR_OK) { \
     free_ctx(c);                                                                                     \
@@ -396,6 +514,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_bond_off, deg.data(), (size_t)n + 1);
   COPY(c->d_bond_nbr, nbr.data(), nbr.size());
   COPY(c->d_counts, kinds, (size_t)6);
+  if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
 #undef COPY
   cudaMemset(c->d_cnt2, 0, sizeof(int) * P.ncell);
   cudaMemset(c->d_frc, 0, sizeof(float4) * nslot);
@@ -478,7 +597,11 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
     const uint32_t swc = (uint32_t)ctx->sweep++;
     for (int col = 0; col < P.ncol; ++col) {
       P.log_base = base;
+      int ti;
+      tbegin(ctx, 0, &ti);
       CR_CUDA(launch_phase(P, ctx->R, log != nullptr, grid, ctx->threads, ctx->smem_phase, s, swc, col, k0, k1));
+      tend(ctx, 0, ti);
+      ctx->launches_total++;
       base += (long long)grid * P.m;
     }
   }
@@ -541,6 +664,7 @@ extern "C" int cr_md_forces(cr_ctx *ctx) {
   if (!ctx) return CR_ERR_INVALID_ARG;
   MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
   CR_CUDA(launch_md_forces(ctx->P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, ctx->stream));
+  ctx->launches_total++;
   ctx->fcons_valid = true;
   return cr_check(ctx);
 }
@@ -550,9 +674,13 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
+  int ti;
   if (!ctx->f_valid) {
     MdParams M = md_params(ctx, 1, dt, gamma, seed);
+    tbegin(ctx, 1, &ti);
     CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
+    tend(ctx, 1, ti);
+    ctx->launches_total++;
     ctx->md_eval++;
     ctx->f_valid = true;
   }
@@ -560,7 +688,10 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
     MdParams M = md_params(ctx, 2, dt, gamma, seed);
     CR_CUDA(launch_kick_drift(P, M, s));
     CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
+    tbegin(ctx, 1, &ti);
     CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
+    tend(ctx, 1, ti);
+    ctx->launches_total += 4;
     ctx->md_eval++;
   }
   ctx->fcons_valid = false;
@@ -585,37 +716,41 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state;
   if (!want) return cr_check(ctx);
   const int64_t n = out->n;
-  float4 *dpos = nullptr, *dvel = nullptr, *dfrc = nullptr;
-  unsigned long long *dpid = nullptr;
-  int *dinfo = nullptr;
-  int rc = CR_OK;
-  if ((rc = dalloc(&dpos, n)) || (rc = dalloc(&dvel, n)) || (rc = dalloc(&dfrc, n)) || (rc = dalloc(&dpid, n)) ||
-      (rc = dalloc(&dinfo, n))) {
-    cudaFree(dpos); cudaFree(dvel); cudaFree(dfrc); cudaFree(dpid); cudaFree(dinfo);
-    return rc;
-  }
-  DumpBufs D{ctx->d_counter, (int)n, dpos, dvel, dfrc, dpid, dinfo, ctx->d_vel,
-             ctx->fcons_valid ? ctx->d_fcons : nullptr};
-  std::vector<float4> hpos(n), hvel(n), hfrc(n, make_float4(0, 0, 0, 0));
-  std::vector<unsigned long long> hpid(n);
-  std::vector<int> hinfo(n);
+  if (n > ctx->capacity) return CR_ERR_CAPACITY;
+  DumpBufs D{ctx->d_counter, (int)n, ctx->d_dump_pos, ctx->d_dump_vel, ctx->d_dump_frc, ctx->d_dump_pid,
+             ctx->d_dump_info, ctx->d_vel, ctx->fcons_valid ? ctx->d_fcons : nullptr};
+  float4 *hpos = ctx->h_dump_pos, *hvel = ctx->h_dump_vel, *hfrc = ctx->h_dump_frc;
+  unsigned long long *hpid = ctx->h_dump_pid;
+  int *hinfo = ctx->h_dump_info;
   int got = 0;
-  cudaError_t e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = launch_dump(ctx->P, D, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&got, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hpos.data(), dpos, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hvel.data(), dvel, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && ctx->fcons_valid)
-    e = cudaMemcpyAsync(hfrc.data(), dfrc, sizeof(float4) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hpid.data(), dpid, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo.data(), dinfo, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(dpos); cudaFree(dvel); cudaFree(dfrc); cudaFree(dpid); cudaFree(dinfo);
-  if (e != cudaSuccess) return cuda_fail(e);
+  CR_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
+  CR_CUDA(launch_dump(ctx->P, D, s));
+  ctx->launches_total++;
+  CR_CUDA(cudaMemcpyAsync(&got, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (out->xyz) CR_CUDA(cudaMemcpyAsync(hpos, ctx->d_dump_pos, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
+  if (out->vel) CR_CUDA(cudaMemcpyAsync(hvel, ctx->d_dump_vel, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
+  if (out->force && ctx->fcons_valid)
+    CR_CUDA(cudaMemcpyAsync(hfrc, ctx->d_dump_frc, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaMemcpyAsync(hpid, ctx->d_dump_pid, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaMemcpyAsync(hinfo, ctx->d_dump_info, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaStreamSynchronize(s));
   if (got != n) return CR_ERR_CUDA;
-  std::vector<int64_t> ord(n);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return hpid[x] < hpid[y]; });
+  if (out->force && !ctx->fcons_valid)
+    for (int64_t i = 0; i < n; ++i) hfrc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  // order by id: input ids are dense (bucket them), inserted ions are sorted
+  std::vector<int64_t> ord;
+  ord.reserve(n);
+  {
+    std::vector<int64_t> at(ctx->n_input, -1), rest;
+    for (int64_t i = 0; i < n; ++i) {
+      if (hpid[i] < (unsigned long long)ctx->n_input) at[hpid[i]] = i;
+      else rest.push_back(i);
+    }
+    for (int64_t v : at)
+      if (v >= 0) ord.push_back(v);
+    std::sort(rest.begin(), rest.end(), [&](int64_t x, int64_t y) { return hpid[x] < hpid[y]; });
+    ord.insert(ord.end(), rest.begin(), rest.end());
+  }
   for (int64_t o = 0; o < n; ++o) {
     const int64_t i = ord[o];
     if (out->xyz) { out->xyz[3 * o] = hpos[i].x; out->xyz[3 * o + 1] = hpos[i].y; out->xyz[3 * o + 2] = hpos[i].z; }
@@ -642,4 +777,74 @@ extern "C" int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uin
   if (e == cudaSuccess) e = cudaMemcpy(out, d, sizeof(uint4) * n, cudaMemcpyDeviceToHost);
   cudaFree(d);
   return cuda_fail(e);
+}
+
+extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type,
+                       const int32_t *cls, const int8_t *state) {
+  if (!ctx || n < 0 || n > ctx->capacity) return CR_ERR_INVALID_ARG;
+  if (n > 0 && (!xyz || !type || !cls || !state)) return CR_ERR_INVALID_ARG;
+  const SysParams &P = ctx->P;
+  // the bonded / site particles must be those of cr_init, at the same indices
+  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
+  int qsum = 0, n_fixed = 0, n_fixed_init = 0;
+  for (int t : ctx->init_type) n_fixed_init += (t != CR_XP && t != CR_XM);
+  for (int i = 0; i < n; ++i) {
+    const int t = type[i];
+    if (t < CR_BEAD || t > CR_CORE || cls[i] < 0 || cls[i] > 3) return CR_ERR_INVALID_ARG;
+    const float X = xyz[3 * i], Y = xyz[3 * i + 1], Z = xyz[3 * i + 2];
+    if (!(X >= 0.0f && X < P.Lf && Y >= 0.0f && Y < P.Lf && Z >= 0.0f && Z < P.Lf)) return CR_ERR_INVALID_ARG;
+    if (t != CR_XP && t != CR_XM) {
+      if (i >= (int)ctx->init_type.size() || ctx->init_type[i] != t) return CR_ERR_INVALID_ARG;
+      n_fixed++;
+    }
+    const int ion = (t == CR_ACID || t == CR_BASE) && state[i] ? 1 : 0;
+    int kd = K_OTHER;
+    if (t == CR_ACID) { kd = ion ? K_A1 : K_A0; qsum -= ion; }
+    else if (t == CR_BASE) { kd = ion ? K_B1 : K_B0; qsum += ion; }
+    else if (t == CR_XP) { kd = K_XP; qsum += 1; }
+    else if (t == CR_XM) { kd = K_XM; qsum -= 1; }
+    kinds[kd]++;
+  }
+  if (n_fixed != n_fixed_init) return CR_ERR_INVALID_ARG;
+  if (qsum != 0) return CR_ERR_NOT_NEUTRAL;
+  cudaStream_t s = ctx->stream;
+  if (n > 0) {
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (vel) CR_CUDA(cudaMemcpyAsync(ctx->d_in_vel, vel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
+  }
+  CR_CUDA(cudaMemcpyAsync(ctx->d_counts, kinds, sizeof(long long) * 6, cudaMemcpyHostToDevice, s));
+  LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
+             ctx->d_in_state, n, ctx->n_input};
+  RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
+  CR_CUDA(launch_load(P, I, B, ctx->d_perm, ctx->n_input, s));
+  ctx->launches_total += 2;
+  ctx->f_valid = false;
+  ctx->fcons_valid = false;
+  return CR_OK;
+}
+
+extern "C" int cr_set_timing(cr_ctx *ctx, int32_t enable) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  ctx->timing = enable != 0;
+  return CR_OK;
+}
+
+extern "C" int cr_get_timing(cr_ctx *ctx, double *ms, int64_t *launches, int64_t *launches_total, int32_t reset) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  tcollect(ctx);
+  for (int k = 0; k < 2; ++k) {
+    if (ms) ms[k] = ctx->ms[k];
+    if (launches) launches[k] = ctx->launches[k];
+  }
+  if (launches_total) *launches_total = ctx->launches_total;
+  if (reset) {
+    ctx->ms[0] = ctx->ms[1] = 0.0;
+    ctx->launches[0] = ctx->launches[1] = 0;
+    ctx->launches_total = 0;
+  }
+  return CR_OK;
 }

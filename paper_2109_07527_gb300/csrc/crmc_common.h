@@ -30,15 +30,17 @@ constexpr float FIX_SCALE = 4294967296.0f;  // fixed-point scale 2^32 of the ene
 constexpr double FIX_INV = 1.0 / 4294967296.0;
 
 struct WcaEntry {
-  float eps, sig, del, wcut2;
+  float eps, sig, del, wcut2;  // FP32 (MD forces, range pre-check)
   int on;
+  double eps_d, sig_d, del_d, wcut_d;  // FP64 (WCA changes of inserted / deleted ions)
 };
 
 // Everything a phase (or MD) kernel needs, passed by value.
 struct SysParams {
   // geometry
   int nc, k, h, nd, ncol, m, cap, global, nr, ncell;
-  float Lf, invL, scf;  // box, 1/box, cells per unit length (FP32, decides cells)
+  float Lf, invL, scf, halfL;  // box, 1/box, cells per unit length (FP32, decides cells), L/2
+  double Ld, halfLd;
   double a;             // cell side in FP64 (insertion coordinates)
   // energy, FP32 pair constants
   float rc2, rcf, alpha, c1, c2, lBf;

@@ -73,48 +73,85 @@ __device__ __forceinline__ int kind_of(int info) {
   return idx < 12 ? (int)((tab >> (4 * idx)) & 15ull) : K_OTHER;
 }
 
-__device__ __forceinline__ float min_image(float d, float L, float invL) { return d - L * rintf(d * invL); }
+
+// Minimum-image difference a - b of two coordinates in [0, L) without the
+// large intermediate a - b ~ L: across the boundary the coordinate above L/2
+// is shifted by L first, which is exact (Sterbenz).
+__device__ __forceinline__ float wrap_diff(float a, float b, float L, float halfL) {
+  const float d = a - b;
+  if (d > halfL) return (a - L) - b;
+  if (d < -halfL) return a - (b - L);
+  return d;
+}
+__device__ __forceinline__ double wrap_diff_d(float a, float b, double L, double halfL) {
+  double d = (double)a - (double)b;
+  if (d > halfL) d -= L;
+  else if (d < -halfL) d += L;
+  return d;
+}
+
+// WCA change of an inserted (dp > 0) or deleted (dp < 0) particle against a
+// bystander, in FP64 from the exact float positions: the steep (sigma/s)^12
+// would amplify FP32 distance rounding twelvefold.  Returns the change and
+// its gross magnitude; flags an overlap when an inserted particle comes
+// closer than half a diameter.
+__device__ __forceinline__ bool wca_change_d(const WcaEntry &w, int dp, float cx, float cy, float cz, float xj,
+                                             float yj, float zj, double L, double halfL, double &du, double &gs,
+                                             int &ov) {
+  const double dx = wrap_diff_d(xj, cx, L, halfL), dy = wrap_diff_d(yj, cy, L, halfL),
+               dz = wrap_diff_d(zj, cz, L, halfL);
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  if (!(r < w.wcut_d)) return false;
+  const double s = r - w.del_d;
+  if (dp > 0 && s < 0.5 * w.sig_d) {
+    ov = 1;
+    return false;
+  }
+  const double t = w.sig_d / s;
+  const double t2 = t * t;
+  const double t6 = t2 * t2 * t2;
+  du = (double)dp * (4.0 * w.eps_d * (t6 * t6 - t6) + w.eps_d);
+  gs = w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
+  return true;
+}
 
 // One pair change of a changed particle c against a bystander j:
 //   du = lB dq_c q_j phi(r) [r < rc] + dp_c U_wca(r)
-// accumulated in 2^-32 kT fixed point.  Inserted particles (dp > 0) that come
-// closer than half a WCA diameter, and any |du| >= 2^20 kT, flag an overlap.
+// accumulated in 2^-32 kT fixed point: the Coulomb part in FP32, the WCA part
+// of inserted / deleted particles in FP64.  Inserted particles closer than
+// half a WCA diameter, and any |du| >= 2^20 kT, flag an overlap.
 template <bool WITH_S>
 __device__ __forceinline__ void pair_change(const SysParams &P, float cx, float cy, float cz, float dqlB, int dp,
                                             int ccls, float xj, float yj, float zj, float qj, int jcls,
                                             long long &acc, unsigned long long &sacc, int &ov) {
-  const float dx = min_image(xj - cx, P.Lf, P.invL);
-  const float dy = min_image(yj - cy, P.Lf, P.invL);
-  const float dz = min_image(zj - cz, P.Lf, P.invL);
+  const float dx = wrap_diff(xj, cx, P.Lf, P.halfL);
+  const float dy = wrap_diff(yj, cy, P.Lf, P.halfL);
+  const float dz = wrap_diff(zj, cz, P.Lf, P.halfL);
   const float r2 = dx * dx + dy * dy + dz * dz;
-  float du = 0.0f;
+  double du = 0.0, gs = 0.0;
   bool any = false;
   if (r2 < P.rc2 && dqlB != 0.0f && qj != 0.0f) {
     const float r = sqrtf(r2);
-    du = dqlB * qj * (erfcf(P.alpha * r) / r - P.c1 + P.c2 * (r - P.rcf));
+    const float e = erfcf(P.alpha * r) / r;
+    du = (double)(dqlB * qj * (e - P.c1 + P.c2 * (r - P.rcf)));
+    if (WITH_S) gs = (double)(fabsf(dqlB * qj) * (e + P.c1 + P.c2 * fabsf(r - P.rcf)));
     any = true;
   }
+  double dw = 0.0, gw = 0.0;
+  bool wany = false;
   if (dp != 0) {
     const WcaEntry &w = P.wca[ccls * 4 + jcls];
-    if (w.on && r2 < w.wcut2) {
-      const float s = sqrtf(r2) - w.del;
-      if (dp > 0 && s < 0.5f * w.sig) {
-        ov = 1;
-      } else {
-        const float t = w.sig / s;
-        const float t2 = t * t;
-        const float t6 = t2 * t2 * t2;
-        du += (float)dp * (4.0f * w.eps * (t6 * t6 - t6) + w.eps);
-        any = true;
-      }
-    }
+    if (w.on && r2 < 1.0001f * w.wcut2)
+      wany = wca_change_d(w, dp, cx, cy, cz, xj, yj, zj, P.Ld, P.halfLd, dw, gw, ov);
   }
-  if (any) {
-    if (!(fabsf(du) < BIG_TERM)) {
+  if (any || wany) {
+    if (!(fabs(du + dw) < (double)BIG_TERM)) {
       ov = 1;
     } else {
-      acc += __float2ll_rn(du * FIX_SCALE);
-      if (WITH_S) sacc += (unsigned long long)__float2ll_rn(fabsf(du) * FIX_SCALE);
+      // the FP32 Coulomb part and the FP64 WCA part enter the fixed-point sum separately
+      if (any) acc += __float2ll_rn((float)du * FIX_SCALE);
+      if (wany) acc += __double2ll_rn(dw * (double)FIX_SCALE);
+      if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin(gs + gw, (double)BIG_TERM) * (double)FIX_SCALE);
     }
   }
 }

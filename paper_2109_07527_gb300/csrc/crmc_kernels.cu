@@ -169,43 +169,55 @@ __device__ void warp_remove(DomList L, int n, int p) {
 
 __device__ __forceinline__ float dqlB_of(const SysParams &P, float dq) { return P.lBf * dq; }
 
-// pair change between the two changed particles: u_new - u_old (FP32 -> fixed)
+// pair change between the two changed particles: u_new - u_old, the Coulomb
+// part in FP32 and the WCA part in FP64 (as for bystanders), into fixed point
 __device__ void cc_change(const SysParams &P, const TrialCtl &t, float qa_o, float qa_n, float qb_o, float qb_n,
                           int pa_o, int pa_n, int pb_o, int pb_n, long long &acc, unsigned long long &sacc, int &ov) {
   const Desc &A = t.c[0], &B = t.c[1];
-  const float dx = min_image(B.x - A.x, P.Lf, P.invL);
-  const float dy = min_image(B.y - A.y, P.Lf, P.invL);
-  const float dz = min_image(B.z - A.z, P.Lf, P.invL);
+  const float dx = wrap_diff(B.x, A.x, P.Lf, P.halfL);
+  const float dy = wrap_diff(B.y, A.y, P.Lf, P.halfL);
+  const float dz = wrap_diff(B.z, A.z, P.Lf, P.halfL);
   const float r2 = dx * dx + dy * dy + dz * dz;
   const WcaEntry &w = P.wca[A.cls * 4 + B.cls];
-  float u[2] = {0.0f, 0.0f};  // old, new
+  float uc[2] = {0.0f, 0.0f};  // Coulomb, old / new
+  double uw[2] = {0.0, 0.0};   // WCA, old / new
+  double gs = 0.0;             // gross magnitude (tolerance scale)
   for (int s = 0; s < 2; ++s) {
     const bool pres = s ? (pa_n && pb_n) : (pa_o && pb_o);
     if (!pres) continue;
     const float qa = s ? qa_n : qa_o, qb = s ? qb_n : qb_o;
     if (r2 < P.rc2 && qa != 0.0f && qb != 0.0f) {
       const float r = sqrtf(r2);
-      u[s] += P.lBf * qa * qb * (erfcf(P.alpha * r) / r - P.c1 + P.c2 * (r - P.rcf));
+      const float e = erfcf(P.alpha * r) / r;
+      uc[s] = P.lBf * qa * qb * (e - P.c1 + P.c2 * (r - P.rcf));
+      gs += (double)(fabsf(P.lBf * qa * qb) * (e + P.c1 + P.c2 * fabsf(r - P.rcf)));
     }
-    if (w.on && r2 < w.wcut2) {
-      const float sv = sqrtf(r2) - w.del;
-      const bool inserted = s == 1 && ((pa_n && !pa_o) || (pb_n && !pb_o));
-      if (inserted && sv < 0.5f * w.sig) {
-        ov = 1;
-      } else {
-        const float tt = w.sig / sv;
-        const float t2 = tt * tt;
-        const float t6 = t2 * t2 * t2;
-        u[s] += 4.0f * w.eps * (t6 * t6 - t6) + w.eps;
+    if (w.on && r2 < 1.0001f * w.wcut2) {
+      const double ddx = wrap_diff_d(B.x, A.x, P.Ld, P.halfLd), ddy = wrap_diff_d(B.y, A.y, P.Ld, P.halfLd),
+                   ddz = wrap_diff_d(B.z, A.z, P.Ld, P.halfLd);
+      const double r = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+      if (r < w.wcut_d) {
+        const double sv = r - w.del_d;
+        const bool inserted = s == 1 && ((pa_n && !pa_o) || (pb_n && !pb_o));
+        if (inserted && sv < 0.5 * w.sig_d) {
+          ov = 1;
+        } else {
+          const double tt = w.sig_d / sv;
+          const double t2 = tt * tt;
+          const double t6 = t2 * t2 * t2;
+          uw[s] = 4.0 * w.eps_d * (t6 * t6 - t6) + w.eps_d;
+          gs += w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
+        }
       }
     }
   }
-  const float du = u[1] - u[0];
-  if (du != 0.0f) {
-    if (!(fabsf(du) < BIG_TERM)) ov = 1;
+  const float dc = uc[1] - uc[0];
+  const double dw = uw[1] - uw[0];
+  if (dc != 0.0f || dw != 0.0) {
+    if (!(fabs((double)dc + dw) < (double)BIG_TERM)) ov = 1;
     else {
-      acc += __float2ll_rn(du * FIX_SCALE);
-      sacc += (unsigned long long)__float2ll_rn(fabsf(du) * FIX_SCALE);
+      acc += __float2ll_rn(dc * FIX_SCALE) + __double2ll_rn(dw * (double)FIX_SCALE);
+      sacc += (unsigned long long)__double2ll_rn(fmin(gs, (double)BIG_TERM) * (double)FIX_SCALE);
     }
   }
 }
@@ -739,9 +751,9 @@ constexpr float FFIX_INV = 1.0f / 16777216.0f;
 __device__ __forceinline__ void force_pair(const SysParams &P, float xi, float yi, float zi, float qi, int ci,
                                            float xj, float yj, float zj, float qj, int cj, long long &fx,
                                            long long &fy, long long &fz) {
-  const float dx = min_image(xi - xj, P.Lf, P.invL);
-  const float dy = min_image(yi - yj, P.Lf, P.invL);
-  const float dz = min_image(zi - zj, P.Lf, P.invL);
+  const float dx = wrap_diff(xi, xj, P.Lf, P.halfL);
+  const float dy = wrap_diff(yi, yj, P.Lf, P.halfL);
+  const float dz = wrap_diff(zi, zj, P.Lf, P.halfL);
   const float r2 = dx * dx + dy * dy + dz * dz;
   float f = 0.0f;  // along (ri - rj) / r, positive = repulsive
   bool any = false;
@@ -851,9 +863,9 @@ __global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M, int 
       for (int bb = b0 + lane; bb < b1; bb += 32) {
         const int gj = M.perm_slot[M.bond_nbr[bb]];
         const float4 pj = P.pos[gj];
-        const float dx = min_image(pi.x - pj.x, P.Lf, P.invL);
-        const float dy = min_image(pi.y - pj.y, P.Lf, P.invL);
-        const float dz = min_image(pi.z - pj.z, P.Lf, P.invL);
+        const float dx = wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
+        const float dy = wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
+        const float dz = wrap_diff(pi.z, pj.z, P.Lf, P.halfL);
         const float x2 = (dx * dx + dy * dy + dz * dz) * M.inv_R02;
         if (x2 >= 1.0f) {
           atomicOr(P.err, ERRB_BOND);
@@ -995,6 +1007,35 @@ __global__ void k_dump(SysParams P, DumpBufs D) {
   if (D.frc_src) D.frc[o] = D.frc_src[g];
 }
 
+// load: place input particles (index = id) into cells, unordered
+__global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= I.n) return;
+  const float x = I.xyz[3 * i], y = I.xyz[3 * i + 1], z = I.xyz[3 * i + 2];
+  const int t = I.type[i];
+  const int ion = (t == CR_ACID || t == CR_BASE) && I.state[i] ? 1 : 0;
+  float q = 0.0f;
+  int cl = I.cls[i];
+  if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
+  else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
+  else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
+  else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+  const int site = (i < I.n_site_map && I.site[i] >= 0) ? I.site[i] : 0;
+  const int nc = P.nc;
+  const int cell = cell_of(x, P.scf, nc) + nc * (cell_of(y, P.scf, nc) + nc * cell_of(z, P.scf, nc));
+  const int s = atomicAdd(&B.cnt[cell], 1);
+  if (s >= P.cap) {
+    atomicOr(P.err, ERRB_CELL_OVERFLOW);
+    return;
+  }
+  const int o = cell * P.cap + s;
+  B.pos[o] = make_float4(x, y, z, q);
+  B.pid[o] = (unsigned long long)i;
+  B.info[o] = t | (cl << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
+  B.vel[o] = I.vel ? make_float4(I.vel[3 * i], I.vel[3 * i + 1], I.vel[3 * i + 2], 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  B.frc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                          uint4 *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1076,6 +1117,13 @@ cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_
 cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s) {
   const int n = P.ncell * P.cap;
   k_rebuild_scatter<<<(n + 255) / 256, 256, 0, s>>>(P, B);
+  k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
+                        cudaStream_t s) {
+  if (I.n > 0) k_load_scatter<<<(I.n + 255) / 256, 256, 0, s>>>(P, I, B);
   k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
   return cudaGetLastError();
 }

@@ -36,7 +36,16 @@ struct DumpBufs {
   const float4 *vel_src, *frc_src;
 };
 
+struct LoadBufs {
+  const float *xyz, *vel;
+  const int *type, *cls, *site;  // site: site index of input particle i (-1 none)
+  const int8_t *state;
+  int n, n_site_map;
+};
+
 size_t phase_smem_bytes(const SysParams &P);
+cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
+                        cudaStream_t s);
 size_t md_smem_bytes(int kb, int nrb, int rcap);
 cudaError_t launch_phase(const SysParams &P, int R, bool log, int grid, int threads, size_t smem, cudaStream_t s,
                          uint32_t sweep, int colour, uint32_t k0, uint32_t k1);

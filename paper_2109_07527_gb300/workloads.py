@@ -121,14 +121,17 @@ def _place(rng, grid, L, dmin, tag, tries=10000):
 
 
 def _chain(rng, grid, L, N, tag0, bond=0.97, dmin=1.0):
-    """Self-avoiding random walk: consecutive beads 0.97 sigma apart, all
-    non-bonded beads at least dmin apart."""
+    """Self-avoiding random walk: consecutive beads 0.97 sigma apart, every
+    non-bonded pair (within the chain and with everything placed before) at
+    least dmin apart."""
     for _attempt in range(200):
         pts = []
         start = _place_probe(rng, grid, L, WCA_CUT)
         if start is None:
             continue
+        own = _Grid(L, 1.2)
         pts.append(start)
+        own.add(start, 0)
         ok = True
         for i in range(1, N):
             placed = False
@@ -136,19 +139,10 @@ def _chain(rng, grid, L, N, tag0, bond=0.97, dmin=1.0):
                 v = rng.normal(size=3)
                 v /= np.linalg.norm(v)
                 p = _wrap(pts[-1].astype(np.float64) + bond * v, L)
-                if grid.too_close(p, dmin):
-                    continue
-                # within the new chain (not yet in the grid), skip the bonded predecessor
-                clash = False
-                for q in pts[:-1][-60:]:
-                    e = p.astype(np.float64) - q
-                    e -= L * np.round(e / L)
-                    if float(e @ e) < dmin * dmin:
-                        clash = True
-                        break
-                if clash:
+                if grid.too_close(p, dmin) or own.too_close(p, dmin, ignore=(i - 1,)):
                     continue
                 pts.append(p)
+                own.add(p, i)
                 placed = True
                 break
             if not placed:

@@ -2,8 +2,9 @@
 
 Protocol (tolerances written here, used by every parity test):
   * moves, chosen particle ids, no-eligible / edge / overlap flags: bit-exact;
-  * dE: |dE_gpu - dE_oracle| <= 1e-6 * max(|dE_oracle|, S) + 1e-9, where S is
-    the sum of |pair changes| (FP32 pair terms against FP64);
+  * dE: |dE_gpu - dE_oracle| <= 1e-6 * S + 1e-9, where S >= |dE| is the gross
+    magnitude of the summed terms (sum over pair terms of the absolute values
+    of their components), the condition scale of FP32 pair terms;
   * accept decisions: identical, except a "tie" where |ln u - lnA_oracle| is
     within tau = 1e-6 * S + 1e-12; the oracle is then re-run with the GPU's
     decision forced at that trial and the comparison continues;
@@ -18,7 +19,9 @@ STRUCT_FLAGS = oracle.F_NOELIG | oracle.F_EDGE | oracle.F_OVERLAP
 
 
 def de_tol(lo):
-    return DE_REL * np.maximum(np.abs(lo["dE"]), lo["S"]) + 1e-9
+    """1e-6 relative to S, the gross magnitude of the summed pair terms
+    (S >= |dE|; pair terms cancel internally near the cutoffs)."""
+    return DE_REL * lo["S"] + 1e-9
 
 
 def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8):
@@ -47,7 +50,10 @@ def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8):
     ok = (lo["flags"] & (oracle.F_NOELIG | oracle.F_EDGE | oracle.F_OVERLAP)) == 0
     err = np.abs(lg["dE"] - lo["dE"])
     tol = de_tol(lo)
-    assert np.all(err[ok] <= tol[ok]), f"dE out of tolerance at {np.flatnonzero(ok & (err > tol))[:5]}"
+    badi = np.flatnonzero(ok & (err > tol))
+    assert len(badi) == 0, "dE out of tolerance:\n" + "\n".join(
+        f"  trial {i}: move {lo['move'][i]} gpu dE {lg['dE'][i]!r} oracle dE {lo['dE'][i]!r} S {lo['S'][i]!r} "
+        f"gpu S {lg['S'][i]!r} err {err[i]:.3e} tol {tol[i]:.3e}" for i in badi[:8])
     lt = np.abs(lg["lnA"] - lo["lnA"])
     assert np.all(lt[ok] <= tol[ok] + 1e-12 * np.abs(lo["lnA"][ok])), "lnA out of tolerance"
     assert np.array_equal(lg["lnu"], lo["lnu"]) or np.allclose(lg["lnu"], lo["lnu"], rtol=1e-15, atol=0)

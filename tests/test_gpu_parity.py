@@ -173,3 +173,65 @@ def test_gpu_titration_matches_exact_closed_form(crmc):
             g.sweep(tps * 4, 2 + b)
             vals.append(g.counts()["n_Am"] / n)
         assert abs(np.mean(vals) - exact) < 0.005, (pH, np.mean(vals), exact)
+
+
+# ------------------------------------------------------------------ MD part
+F_REL = 4e-6  # FP32 force terms against FP64: relative to the gross magnitude of the summed terms
+
+
+def _wrapdiff(a, b, L):
+    d = a.astype(np.float64) - b.astype(np.float64)
+    return d - L * np.round(d / L)
+
+
+def test_md_forces_match_oracle(crmc):
+    w = W.config1(seed=5)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    n = g.trials_per_sweep * 4
+    g.sweep(n, 3)
+    o.sweep(n, 3)
+    g.md_forces()
+    st = g.state()
+    ids, F, S = o.forces()
+    assert np.array_equal(st["id"], ids)
+    err = np.abs(st["force"].astype(np.float64) - F)
+    tol = F_REL * S + 2e-6
+    assert np.all(err <= tol), (np.argmax(err / tol), err.max())
+    assert np.abs(F).max() > 1.0  # the check is not vacuous
+
+
+def test_md_forces_full_size_sampled(crmc):
+    """Forces of the full polyelectrolyte box: every particle vs the oracle's brute-force sum."""
+    w = W.config2(seed=1)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    g.md_forces()
+    st = g.state()
+    ids, F, S = o.forces()
+    assert np.array_equal(st["id"], ids)
+    err = np.abs(st["force"].astype(np.float64) - F)
+    assert np.all(err <= F_REL * S + 2e-6)
+
+
+def test_md_step_and_interleaved_cycles(crmc):
+    """CR-MC sweeps (bit-exact) alternating with MD steps (FP32 vs FP64 within
+    tolerance); the oracle is re-synchronised to the GPU positions after each MD step."""
+    w = W.config1(seed=6, n_pairs=32)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    L = float(np.float32(w.params["box_L"]))
+    n = g.trials_per_sweep * 2
+    for cyc in range(4):
+        lg = g.sweep(n, 10 + cyc, log=True)["log"]
+        lo = o.sweep(n, 10 + cyc, log=True)["log"]
+        assert np.array_equal(lg["flags"], lo["flags"]) and np.array_equal(lg["id_a"], lo["id_a"])
+        g.md_step(1, 0.005, 1.0, 77)
+        o.md_step(1, 0.005, 1.0, 77)
+        sg, so = g.state(), o.particles()
+        assert np.array_equal(sg["id"], so["id"])
+        assert np.abs(_wrapdiff(sg["xyz"], so["xyz"], L)).max() < 2e-5
+        assert np.abs(sg["vel"] - so["vel"]).max() < 2e-4
+        o.set_positions(sg["id"], sg["xyz"], sg["vel"])
+    g.md_step(20, 0.005, 1.0, 78)
+    g.check()
