@@ -496,14 +496,18 @@ static void domain_counts(const Oracle *o, const int off[3], int d, int64_t cnt[
   }
 }
 
-/* insertion coordinate: u = c0 + k*f (exact), wrapped into [0, nc), times the
- * cell side, rounded once to FP32; f carries the top 24 bits of w */
+/* insertion coordinate: the ion is placed uniformly in the trial's domain
+ * (Sec. II.C: an ion is taken from the reservoir and placed into the
+ * system).  The discretisation is in FP32: f = top 24 bits of w times 2^-24,
+ * u = fl32(c0 + k f) wrapped into [0, nc), x = fl32(u * fl32(L/nc)), wrapped
+ * into [0, L).  A point that rounds out of the domain is rejected. */
 static float insert_coord(const Oracle *o, int c0, uint32_t w) {
-  double f = (double)(w >> 8) * (1.0 / 16777216.0);
-  double u = (double)c0 + (double)o->k * f;
-  if (u >= (double)o->nc) u -= (double)o->nc;
-  double xd = u * o->a;
-  float xf = (float)xd;
+  float f = (float)(w >> 8) * (1.0f / 16777216.0f);
+  float kf = (float)o->k * f;
+  float u = (float)c0 + kf;
+  if (u >= (float)o->nc) u -= (float)o->nc;
+  float af = (float)(o->L / o->nc);
+  float xf = u * af;
   if (xf >= o->Lf) xf -= o->Lf;
   return xf;
 }
@@ -884,7 +888,7 @@ int32_t or_forces(const Oracle *o, double *F, double *fs) { return forces_cons(o
 
 /* Langevin part of the force, drawn per particle id and force evaluation:
  * -gamma v + sqrt(2 gamma T / dt) xi, xi ~ N(0,1) from Box-Muller on Philox
- * (key = seed, counter = (id_lo, id_hi, eval, 5)), uniforms (w + 0.5) 2^-32. */
+ * (key = seed, counter = (id_lo, id_hi, eval, 5)), uniforms ((w >> 8) + 0.5) 2^-24. */
 static void langevin(const Oracle *o, double *F, double gamma, double T, double dt, uint64_t seed, uint64_t ev) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   double amp = sqrt(2.0 * gamma * T / dt);
@@ -892,7 +896,7 @@ static void langevin(const Oracle *o, double *F, double gamma, double T, double 
     uint32_t c[4] = {(uint32_t)o->id[j], (uint32_t)(o->id[j] >> 32), (uint32_t)ev, 5u}, w[4];
     philox(c, key, w);
     double u[4];
-    for (int i = 0; i < 4; ++i) u[i] = ((double)w[i] + 0.5) * (1.0 / 4294967296.0);
+    for (int i = 0; i < 4; ++i) u[i] = (double)(((float)(w[i] >> 8) + 0.5f) * (1.0f / 16777216.0f));
     double r1 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
     double g[3] = {r1 * cos(2.0 * M_PI * u[1]), r1 * sin(2.0 * M_PI * u[1]), r2 * cos(2.0 * M_PI * u[3])};
     F[3 * j] += -gamma * o->vx[j] + amp * g[0];
