@@ -199,6 +199,15 @@ int cr_state(cr_ctx *ctx, cr_state_view *out);
 int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type, const int32_t *cls,
             const int8_t *state);
 
+/* Launch shape of the colour-phase kernel: threads per domain (128, 256 or
+ * 512) and halo particles held in registers per thread (1..8).  By default
+ * the first unlogged sweeps time every supported shape once and keep the
+ * fastest; the trial outcomes never depend on the shape (the energy sums are
+ * exact fixed point).  cr_set_launch_shape(ctx, 0, 0) restarts the tuning;
+ * an unsupported pair gives CR_ERR_INVALID_ARG. */
+int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs);
+int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t *regs);
+
 /* Record CUDA events around every colour-phase and MD-force launch. */
 int cr_set_timing(cr_ctx *ctx, int32_t enable);
 

@@ -72,7 +72,7 @@ TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id
 # every entry point of include/crmc.h
 EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
            "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
-           "cr_get_timing")
+           "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape")
 
 _L = None
 
@@ -112,6 +112,10 @@ def _lib():
         lib.cr_set_timing.argtypes = [P, C.c_int32]
         lib.cr_get_timing.restype = C.c_int
         lib.cr_get_timing.argtypes = [P, P, P, P, C.c_int32]
+        lib.cr_set_launch_shape.restype = C.c_int
+        lib.cr_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
+        lib.cr_get_launch_shape.restype = C.c_int
+        lib.cr_get_launch_shape.argtypes = [P, P, P]
         lib.cr_philox.restype = C.c_int
         lib.cr_philox.argtypes = [C.c_uint32] * 6 + [C.c_int32, P]
         _L = lib
@@ -229,6 +233,15 @@ class Context:
         conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
         _chk(self._lib.cr_load(self._h, int(n), conv(xyz_ptr), conv(vel_ptr), conv(type_ptr), conv(cls_ptr),
                                conv(state_ptr)), "cr_load")
+
+    def set_launch_shape(self, threads, regs):
+        _chk(self._lib.cr_set_launch_shape(self._h, int(threads), int(regs)), "cr_set_launch_shape")
+
+    def launch_shape(self):
+        t = C.c_int32()
+        r = C.c_int32()
+        _chk(self._lib.cr_get_launch_shape(self._h, C.byref(t), C.byref(r)), "cr_get_launch_shape")
+        return t.value, r.value
 
     def set_timing(self, on=True):
         _chk(self._lib.cr_set_timing(self._h, 1 if on else 0), "cr_set_timing")

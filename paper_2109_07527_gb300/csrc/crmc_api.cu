@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -25,10 +26,15 @@ struct cr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   SysParams P{};
-  // schedule / launch shape
-  int threads = 128, R = 4;
-  size_t smem_phase = 0;
-  int kb_md = 1, nb_md = 1, nr_md = 1, rcap_md = 1024, threads_md = 128;
+  // schedule / launch shape: (threads per CTA, halo registers per thread) of
+  // the phase kernel, chosen by timing real sweeps (the chain does not depend
+  // on it: the energy sums are exact fixed point)
+  int T = 128, R = 4;
+  int tune_next = 0;     // next candidate to time; >= count when done
+  bool tuning = true;
+  float tune_ms[16] = {};
+  PhaseShape S{};
+  SysParams *d_reps = nullptr;  // device copy of P (the phase kernel reads it)
   int64_t per_sweep = 0;
   // sizes
   int n_input = 0, n_sites = 0, n_other = 0;
@@ -38,11 +44,17 @@ struct cr_ctx {
   float4 *d_pos = nullptr, *d_pos2 = nullptr, *d_vel = nullptr, *d_vel2 = nullptr, *d_frc = nullptr,
          *d_frc2 = nullptr, *d_fcons = nullptr;
   unsigned long long *d_pid = nullptr, *d_pid2 = nullptr, *d_stats = nullptr;
-  double *d_lnK = nullptr, *d_lntab = nullptr;
+  long long *d_lnK = nullptr, *d_lntab = nullptr;
   long long *d_counts = nullptr;
   int *d_err = nullptr, *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr, *d_counter = nullptr;
   cr_trial *d_log = nullptr;
   size_t log_cap = 0;
+  // dense-domain scratch of the phase kernel and the MD particle list
+  float4 *d_gs_pos = nullptr, *d_gs_vel = nullptr;
+  unsigned long long *d_gs_id = nullptr;
+  long long *d_gs_lnk = nullptr;
+  int *d_gs_info = nullptr, *d_gs_rank = nullptr;
+  int *d_plist = nullptr, *d_nparts = nullptr;
   // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
@@ -94,6 +106,9 @@ double pIX_of(double pIS, double pH, double pOH) {
   return -std::log10(std::pow(10.0, -pIS) + std::pow(10.0, -m));
 }
 
+// value at the 2^-48 fixed-point scale of the Metropolis exponent
+long long to_lnfix(double v) { return std::llround(std::ldexp(v, 48)); }
+
 int cell_of_host(float x, float scf, int nc) {
   const float t = x * scf;  // single IEEE multiply
   int c = (int)std::floor(t);
@@ -135,7 +150,9 @@ static void free_ctx(cr_ctx *c) {
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log,
                   c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
-                  c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info};
+                  c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info,
+                  c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
+                  c->d_plist, c->d_nparts};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info};
@@ -293,6 +310,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.halfLd = 0.5 * L;
   P.scf = (float)((double)nc / L);
   P.a = a;
+  P.af = (float)(L / nc);
   c->per_sweep = (int64_t)P.nd * P.nd * P.nd * P.m;
 
   // ---- energy constants (FP64 -> FP32)
@@ -329,8 +347,11 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   if (mu.pIX_explicit) { pIXp = mu.pIX_plus; pIXm = mu.pIX_minus; }
   else { pIXp = pIX_of(mu.pI_S_plus, pH, pOH); pIXm = pIX_of(mu.pI_S_minus, pH, pOH); }
   const double D = global ? L : k * a;
-  P.ln_z1 = std::log(RHO0_NA * std::pow(D * sys->sigma_nm, 3.0));
-  P.ln_salt = -LN10 * (pIXp + pIXm);
+  const double ln_z1 = std::log(RHO0_NA * std::pow(D * sys->sigma_nm, 3.0));
+  const double ln_salt = -LN10 * (pIXp + pIXm);
+  P.lnz1_fx = to_lnfix(ln_z1);
+  P.lnsalt_fx = to_lnfix(ln_salt);
+  P.lBself_fx = to_lnfix(P.lB_self);
 
   // ---- particles: validate, classify, sort into cells
   std::vector<int> site_of(n, -1);
@@ -400,51 +421,63 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   c->fene_R0 = sys->fene_R0;
   if (nb > 0 && !(sys->fene_R0 > 0.0)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
 
-  // ---- launch shapes: CTA per domain; halo registers sized from the densest region
-  c->threads = 128;
+  // ---- launch shape: one CTA per active domain; the domain list of the
+  // densest domain (plus room for the phase's insertions) sized for shared
+  // memory, the halo of the densest region for registers
+  P.nact = global ? 1 : (P.nd / 2) * (P.nd / 2) * (P.nd / 2);
+  P.dcap_glob = k * k * k * cap + 2 * P.m;
+  int maxd = 0, maxh = 0;
   {
-    // halo of a domain whose first cell is (ox, oy, oz): region sum - domain sum
-    int maxh = 0;
     const int nr = P.nr;
-    if (!global) {
-      for (int oz = 0; oz < nc; ++oz)
-        for (int oy = 0; oy < nc; ++oy)
-          for (int ox = 0; ox < nc; ++ox) {
-            int sum = 0;
-            for (int iz = 0; iz < nr; ++iz)
-              for (int iy = 0; iy < nr; ++iy)
-                for (int ix = 0; ix < nr; ++ix) {
-                  if (ix < k && iy < k && iz < k) continue;
-                  auto rc_ = [&](int i, int o) {
-                    int cc = (i < k + h) ? o + i : o + i - nr;
-                    cc %= nc;
-                    if (cc < 0) cc += nc;
-                    return cc;
-                  };
-                  sum += occ[rc_(ix, ox) + nc * (rc_(iy, oy) + nc * rc_(iz, oz))];
-                }
-            maxh = std::max(maxh, sum);
-          }
-    }
-    const int want = (int)std::ceil(1.25 * maxh / c->threads);
-    int R = 1;
-    while (R < want && R < 16) R *= 2;
-    c->R = R;
+    auto rc_ = [&](int i, int o) {
+      int cc = (i < k + h) ? o + i : o + i - nr;
+      cc %= nc;
+      if (cc < 0) cc += nc;
+      return cc;
+    };
+    const int norg = global ? 1 : nc;
+    for (int oz = 0; oz < norg; ++oz)
+      for (int oy = 0; oy < norg; ++oy)
+        for (int ox = 0; ox < norg; ++ox) {
+          int dsum = 0, hsum = 0;
+          for (int iz = 0; iz < nr; ++iz)
+            for (int iy = 0; iy < nr; ++iy)
+              for (int ix = 0; ix < nr; ++ix) {
+                const int cnt = occ[rc_(ix, ox) + nc * (rc_(iy, oy) + nc * rc_(iz, oz))];
+                if (ix < k && iy < k && iz < k) dsum += cnt;
+                else hsum += cnt;
+              }
+          maxd = std::max(maxd, dsum);
+          maxh = std::max(maxh, hsum);
+        }
   }
-  P.dcap = (int)std::min<long long>((long long)k * k * k * cap, (long long)sys->capacity + 2);
-  P.lnmax = P.dcap + 2;
-  std::vector<double> h_lntab(P.lnmax);
-  h_lntab[0] = -INFINITY;
-  for (int i = 1; i < P.lnmax; ++i) h_lntab[i] = std::log((double)i);
-  c->smem_phase = phase_smem_bytes(P);
+  {
+    // starting shape before tuning: 128 threads, enough registers for the densest halo
+    const int want = (int)std::ceil(1.25 * maxh / 128.0);
+    int R = 2;
+    while (R < want && R < 8) R *= 2;
+    c->T = 128;
+    c->R = R;
+    c->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
+  }
+  P.lnmax = std::max(2 * k * k * k * cap, (int)std::min<long long>((long long)sys->capacity, 1 << 20)) + 2 * P.m + 4;
+  std::vector<long long> h_lntab(P.lnmax);
+  h_lntab[0] = LLONG_MIN / 4;  // never used: counts in a ratio are >= 1
+  for (int i = 1; i < P.lnmax; ++i) h_lntab[i] = to_lnfix(std::log((double)i));
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  if (c->smem_phase > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
-  // MD blocks: kb^3 cells per CTA
-  c->kb_md = (!global && nc % k == 0) ? k : 1;
-  c->nb_md = nc / c->kb_md;
-  c->nr_md = std::min(c->kb_md + 2 * h, nc);
-  c->rcap_md = 2048;
+  PhaseShape &S = c->S;
+  S.nr3 = P.nr * P.nr * P.nr;
+  S.kc3 = k * k * k;
+  S.dcs = std::min(P.dcap_glob, std::max(2 * maxd, maxd + 32) + 2 * P.m);
+  S.lns = std::min(P.lnmax, S.dcs + 4);
+  while (phase_smem_bytes(S) > (size_t)smem_max / 2 && S.dcs > 64) {
+    S.dcs /= 2;
+    S.lns = std::min(P.lnmax, S.dcs + 4);
+  }
+  if (phase_smem_bytes(S) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  P.per_sweep = c->per_sweep;
+  P.key_xor = 0u;
 
   // ---- device buffers
   int rc_ = CR_OK;
@@ -486,6 +519,18 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_dump_frc, (size_t)sys->capacity);
   ALLOC(c->d_dump_pid, (size_t)sys->capacity);
   ALLOC(c->d_dump_info, (size_t)sys->capacity);
+  {
+    const size_t ng = (size_t)P.nact * P.dcap_glob;
+    ALLOC(c->d_gs_pos, ng);
+    ALLOC(c->d_gs_vel, ng);
+    ALLOC(c->d_gs_id, ng);
+    ALLOC(c->d_gs_lnk, ng);
+    ALLOC(c->d_gs_info, ng);
+    ALLOC(c->d_gs_rank, ng);
+  }
+  ALLOC(c->d_reps, 1);
+  ALLOC(c->d_plist, (size_t)std::max(sys->capacity, 1));
+  ALLOC(c->d_nparts, 1);
 #undef ALLOC
   {
     const size_t cp = (size_t)std::max(sys->capacity, 1);
@@ -508,7 +553,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_vel, h_vel.data(), nslot);
   COPY(c->d_pid, h_pid.data(), nslot);
   COPY(c->d_info, h_info.data(), nslot);
-  if (!lnK.empty()) COPY(c->d_lnK, lnK.data(), lnK.size());
+  std::vector<long long> lnK_fx(lnK.size());
+  for (size_t i = 0; i < lnK.size(); ++i) lnK_fx[i] = to_lnfix(lnK[i]);
+  if (!lnK.empty()) COPY(c->d_lnK, lnK_fx.data(), lnK_fx.size());
   COPY(c->d_lntab, h_lntab.data(), (size_t)P.lnmax);
   COPY(c->d_perm, h_perm.data(), (size_t)std::max(n, 1));
   COPY(c->d_bond_off, deg.data(), (size_t)n + 1);
@@ -521,8 +568,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   cudaMemset(c->d_fcons, 0, sizeof(float4) * nslot);
   cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16);
   cudaMemset(c->d_err, 0, sizeof(int));
-  P.lnK = c->d_lnK;
-  P.lntab = c->d_lntab;
+  P.lnK_fx = c->d_lnK;
+  P.lntab_fx = c->d_lntab;
   P.cnt = c->d_cnt;
   P.pos = c->d_pos;
   P.vel = c->d_vel;
@@ -534,7 +581,16 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.counts = c->d_counts;
   P.err = c->d_err;
   P.log = nullptr;
-  P.log_base = 0;
+  P.gs_pos = c->d_gs_pos;
+  P.gs_vel = c->d_gs_vel;
+  P.gs_id = c->d_gs_id;
+  P.gs_lnk = c->d_gs_lnk;
+  P.gs_info = c->d_gs_info;
+  P.gs_rank = c->d_gs_rank;
+  if (cudaMemcpy(c->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_ctx(c);
+    return CR_ERR_CUDA;
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return CR_ERR_CUDA; }
   *out = c;
   return CR_OK;
@@ -590,20 +646,52 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
     P.log = ctx->d_log;
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  const int grid = P.global ? 1 : (P.nd / 2) * (P.nd / 2) * (P.nd / 2);
+  // the phase kernel reads the parameters from the device copy; the log
+  // pointer is set there only for logged calls
+  if (log) CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice, s));
   const uint64_t n_sweeps = n_trials / (uint64_t)ctx->per_sweep;
-  long long base = 0;
+  const uint32_t sweep0 = (uint32_t)ctx->sweep;
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)ctx->sweep++;
+    // online tuning: the first sweeps of unlogged calls time each launch shape once
+    const bool tune = ctx->tuning && !log && ctx->tune_next < phase_shape_count();
+    int T = ctx->T, R = ctx->R;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tune) {
+      phase_shape(ctx->tune_next, &T, &R);
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
     for (int col = 0; col < P.ncol; ++col) {
-      P.log_base = base;
       int ti;
       tbegin(ctx, 0, &ti);
-      CR_CUDA(launch_phase(P, ctx->R, log != nullptr, grid, ctx->threads, ctx->smem_phase, s, swc, col, k0, k1));
+      CR_CUDA(launch_phase(ctx->d_reps, 1, P.nact, ctx->S, T, R, log != nullptr, s, swc, sweep0, col, k0, k1));
       tend(ctx, 0, ti);
       ctx->launches_total++;
-      base += (long long)grid * P.m;
     }
+    if (tune) {
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ctx->tune_ms[ctx->tune_next++] = ms;
+      if (ctx->tune_next == phase_shape_count()) {
+        int best = 0;
+        for (int i = 1; i < phase_shape_count(); ++i)
+          if (ctx->tune_ms[i] < ctx->tune_ms[best]) best = i;
+        phase_shape(best, &ctx->T, &ctx->R);
+        ctx->tuning = false;
+      }
+    }
+  }
+  if (log) {
+    SysParams Q = ctx->P;
+    Q.log = nullptr;
+    CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &Q, sizeof(SysParams), cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaStreamSynchronize(s));
   }
   ctx->f_valid = false;
   ctx->fcons_valid = false;
@@ -656,15 +744,26 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
   M.n_perm = ctx->n_input;
   M.fene_K = (float)ctx->fene_K;
   M.inv_R02 = (float)(1.0 / (ctx->fene_R0 * ctx->fene_R0));
-  M.rcap = ctx->rcap_md;
+  M.plist = ctx->d_plist;
+  M.n_particles = ctx->d_nparts;
   return M;
+}
+
+// particle list, then one force evaluation
+static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
+  CR_CUDA(launch_plist(ctx->P, ctx->d_plist, ctx->d_nparts, ctx->stream));
+  int ti;
+  tbegin(ctx, 1, &ti);
+  CR_CUDA(launch_md_forces(ctx->P, M, (int)ctx->capacity, ctx->stream));
+  tend(ctx, 1, ti);
+  ctx->launches_total += 2;
+  return CR_OK;
 }
 
 extern "C" int cr_md_forces(cr_ctx *ctx) {
   if (!ctx) return CR_ERR_INVALID_ARG;
-  MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
-  CR_CUDA(launch_md_forces(ctx->P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, ctx->stream));
-  ctx->launches_total++;
+  int rc = md_force_eval(ctx, md_params(ctx, 0, 0.0, 0.0, 0));
+  if (rc != CR_OK) return rc;
   ctx->fcons_valid = true;
   return cr_check(ctx);
 }
@@ -674,13 +773,9 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
-  int ti;
+  int rc;
   if (!ctx->f_valid) {
-    MdParams M = md_params(ctx, 1, dt, gamma, seed);
-    tbegin(ctx, 1, &ti);
-    CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
-    tend(ctx, 1, ti);
-    ctx->launches_total++;
+    if ((rc = md_force_eval(ctx, md_params(ctx, 1, dt, gamma, seed))) != CR_OK) return rc;
     ctx->md_eval++;
     ctx->f_valid = true;
   }
@@ -688,10 +783,8 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
     MdParams M = md_params(ctx, 2, dt, gamma, seed);
     CR_CUDA(launch_kick_drift(P, M, s));
     CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
-    tbegin(ctx, 1, &ti);
-    CR_CUDA(launch_md_forces(P, M, ctx->kb_md, ctx->nb_md, ctx->nr_md, ctx->threads_md, s));
-    tend(ctx, 1, ti);
-    ctx->launches_total += 4;
+    ctx->launches_total += 3;
+    if ((rc = md_force_eval(ctx, M)) != CR_OK) return rc;
     ctx->md_eval++;
   }
   ctx->fcons_valid = false;
@@ -846,5 +939,32 @@ extern "C" int cr_get_timing(cr_ctx *ctx, double *ms, int64_t *launches, int64_t
     ctx->launches[0] = ctx->launches[1] = 0;
     ctx->launches_total = 0;
   }
+  return CR_OK;
+}
+
+extern "C" int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs) {
+  if (!ctx) return CR_ERR_INVALID_ARG;
+  if (threads == 0) {  // re-enable tuning
+    ctx->tuning = true;
+    ctx->tune_next = 0;
+    return CR_OK;
+  }
+  for (int i = 0; i < phase_shape_count(); ++i) {
+    int t, r;
+    phase_shape(i, &t, &r);
+    if (t == threads && r == regs) {
+      ctx->T = t;
+      ctx->R = r;
+      ctx->tuning = false;
+      return CR_OK;
+    }
+  }
+  return CR_ERR_INVALID_ARG;
+}
+
+extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t *regs) {
+  if (!ctx || !threads || !regs) return CR_ERR_INVALID_ARG;
+  *threads = ctx->T;
+  *regs = ctx->R;
   return CR_OK;
 }

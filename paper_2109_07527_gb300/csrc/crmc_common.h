@@ -28,6 +28,14 @@ constexpr int MAX_REGION_CELLS = 512;
 constexpr float BIG_TERM = 1048576.0f;  // 2^20 kT: larger pair changes count as overlaps
 constexpr float FIX_SCALE = 4294967296.0f;  // fixed-point scale 2^32 of the energy sums
 constexpr double FIX_INV = 1.0 / 4294967296.0;
+// The Metropolis exponent lnA is summed in 64-bit fixed point with scale 2^48
+// (integer adds, no FP64 on the trial's critical path).  |dE| is clamped at
+// 2^14 kT, where the decision no longer depends on it (ln u >= -37).
+constexpr double LNFIX = 281474976710656.0;  // 2^48
+constexpr long long DE_CLAMP32 = 1ll << 46;  // 2^14 kT at scale 2^32
+// an FP32 ln u decides directly when it is farther than this from lnA
+// (1e-4 at scale 2^48); inside the band ln u is recomputed in FP64
+constexpr long long LNU_BAND = 28147497671ll;
 
 struct WcaEntry {
   float eps, sig, del, wcut2;  // FP32 (MD forces, range pre-check)
@@ -35,26 +43,31 @@ struct WcaEntry {
   double eps_d, sig_d, del_d, wcut_d;  // FP64 (WCA changes of inserted / deleted ions)
 };
 
-// Everything a phase (or MD) kernel needs, passed by value.
+// Everything a phase (or MD) kernel needs about one system (one replica).
+// The phase kernel reads it from a device array (one entry per replica);
+// the MD kernels take it by value.
 struct SysParams {
   // geometry
   int nc, k, h, nd, ncol, m, cap, global, nr, ncell;
+  int nact;             // active domains per colour phase
   float Lf, invL, scf, halfL;  // box, 1/box, cells per unit length (FP32, decides cells), L/2
   double Ld, halfLd;
-  double a;             // cell side in FP64 (insertion coordinates)
+  double a;             // cell side in FP64
+  float af;             // cell side in FP32 (insertion coordinates)
   // energy, FP32 pair constants
   float rc2, rcf, alpha, c1, c2, lBf;
   double lB_self;       // lB * DSF self coefficient (0 when off)
   WcaEntry wca[16];
   int ion_cls;          // class of inserted ions (CR_CLS_NONE for ghosts)
   float ion_q;          // |effective charge| of inserted ions (0 for ghosts)
-  // chemistry (log form, FP64)
-  double ln_z1, ln_salt;
+  // chemistry (log form, fixed point 2^-48)
+  long long lnz1_fx, lnsalt_fx, lBself_fx;
   int n_react;
   int react[3];
-  const double *lnK;    // per site
-  const double *lntab;  // ln(i) for 0 < i < lnmax
+  const long long *lnK_fx;    // per site
+  const long long *lntab_fx;  // ln(i) for 0 < i < lnmax
   int lnmax;
+  uint32_t key_xor;     // XOR-ed into the high Philox key word (replica index)
   // state
   int *cnt;
   float4 *pos, *vel;
@@ -62,13 +75,27 @@ struct SysParams {
   int *info;
   int *perm_slot;  // slot of each permanent particle (bonded partners)
   int n_perm;
+  // domain lists that do not fit in shared memory (one region per CTA of a phase)
+  float4 *gs_pos, *gs_vel;
+  unsigned long long *gs_id;
+  long long *gs_lnk;
+  int *gs_info, *gs_rank;
+  int dcap_glob;        // entries per CTA region (k^3 * cap + 2 m)
   // bookkeeping
   unsigned long long *stats;  // [16]: attempts[6], accepts[6], no-elig, edge, overlap, trials
   long long *counts;          // [6] global counts per kind K_A0..K_XM
   int *err;                   // error bits
   cr_trial *log;              // trial records (device) or null
-  long long log_base;
-  int dcap;                   // capacity of the domain list in shared memory
+  long long per_sweep;        // trials per sweep (log indexing)
+};
+
+// Launch-wide shared-memory shape of a phase launch (the same for every CTA;
+// the maximum over the replicas of a batch).
+struct PhaseShape {
+  int dcs;     // domain-list entries held in shared memory
+  int lns;     // log-table entries held in shared memory
+  int nr3;     // region cells
+  int kc3;     // domain cells
 };
 
 // error bits in *err

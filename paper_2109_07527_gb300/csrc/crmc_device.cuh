@@ -51,16 +51,36 @@ __device__ __forceinline__ int cell_of(float x, float scf, int nc) {
   return min(max(c, 0), nc - 1);
 }
 
-// Insertion coordinate in a domain whose first cell is c0: u = c0 + k f
-// (exact), wrapped to [0, nc), times the FP64 cell side, rounded once to FP32.
-__device__ __forceinline__ float insert_coord(int c0, uint32_t w, int k, int nc, double a, float Lf) {
-  const double f = (double)(w >> 8) * (1.0 / 16777216.0);
-  double u = (double)c0 + (double)k * f;
-  if (u >= (double)nc) u -= (double)nc;
-  const double xd = __dmul_rn(u, a);
-  float xf = __double2float_rn(xd);
+// Insertion coordinate in a domain whose first cell is c0, in FP32 with
+// explicitly rounded operations: f = top 24 bits of w times 2^-24,
+// u = fl32(c0 + k f) wrapped into [0, nc), x = fl32(u * a) wrapped into [0, L).
+__device__ __forceinline__ float insert_coord(int c0, uint32_t w, int k, int nc, float af, float Lf) {
+  const float f = __fmul_rn((float)(w >> 8), 1.0f / 16777216.0f);
+  const float kf = __fmul_rn((float)k, f);
+  float u = __fadd_rn((float)c0, kf);
+  if (u >= (float)nc) u = __fsub_rn(u, (float)nc);
+  float xf = __fmul_rn(u, af);
   if (xf >= Lf) xf = __fsub_rn(xf, Lf);
   return xf;
+}
+
+// round(v * 2^32) as a 64-bit integer for |v| < 2^20, from two 32-bit
+// conversions (the direct float->int64 conversion is several times slower):
+// v = hi + lo with hi = trunc(v) and lo exact, lo * 2^31 rounded to int32.
+__device__ __forceinline__ long long fix32(float v) {
+  const float hi = truncf(v);
+  const float lo = v - hi;
+  const int l = __float2int_rn(lo * 2147483648.0f);
+  return ((long long)(int)hi << 32) + ((long long)l << 1);
+}
+
+// the same at scale 2^24 for |v| < 2^30 (MD forces)
+__device__ __forceinline__ long long fix24(float v) {
+  v = fminf(fmaxf(v, -1073741824.0f), 1073741824.0f);
+  const float hi = truncf(v);
+  const float lo = v - hi;
+  const int l = __float2int_rn(lo * 8388608.0f);
+  return ((long long)(int)hi << 24) + ((long long)l << 1);
 }
 
 // kind of a slot for the eligibility lists, from its info word
@@ -113,47 +133,6 @@ __device__ __forceinline__ bool wca_change_d(const WcaEntry &w, int dp, float cx
   du = (double)dp * (4.0 * w.eps_d * (t6 * t6 - t6) + w.eps_d);
   gs = w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
   return true;
-}
-
-// One pair change of a changed particle c against a bystander j:
-//   du = lB dq_c q_j phi(r) [r < rc] + dp_c U_wca(r)
-// accumulated in 2^-32 kT fixed point: the Coulomb part in FP32, the WCA part
-// of inserted / deleted particles in FP64.  Inserted particles closer than
-// half a WCA diameter, and any |du| >= 2^20 kT, flag an overlap.
-template <bool WITH_S>
-__device__ __forceinline__ void pair_change(const SysParams &P, float cx, float cy, float cz, float dqlB, int dp,
-                                            int ccls, float xj, float yj, float zj, float qj, int jcls,
-                                            long long &acc, unsigned long long &sacc, int &ov) {
-  const float dx = wrap_diff(xj, cx, P.Lf, P.halfL);
-  const float dy = wrap_diff(yj, cy, P.Lf, P.halfL);
-  const float dz = wrap_diff(zj, cz, P.Lf, P.halfL);
-  const float r2 = dx * dx + dy * dy + dz * dz;
-  double du = 0.0, gs = 0.0;
-  bool any = false;
-  if (r2 < P.rc2 && dqlB != 0.0f && qj != 0.0f) {
-    const float r = sqrtf(r2);
-    const float e = erfcf(P.alpha * r) / r;
-    du = (double)(dqlB * qj * (e - P.c1 + P.c2 * (r - P.rcf)));
-    if (WITH_S) gs = (double)(fabsf(dqlB * qj) * (e + P.c1 + P.c2 * fabsf(r - P.rcf)));
-    any = true;
-  }
-  double dw = 0.0, gw = 0.0;
-  bool wany = false;
-  if (dp != 0) {
-    const WcaEntry &w = P.wca[ccls * 4 + jcls];
-    if (w.on && r2 < 1.0001f * w.wcut2)
-      wany = wca_change_d(w, dp, cx, cy, cz, xj, yj, zj, P.Ld, P.halfLd, dw, gw, ov);
-  }
-  if (any || wany) {
-    if (!(fabs(du + dw) < (double)BIG_TERM)) {
-      ov = 1;
-    } else {
-      // the FP32 Coulomb part and the FP64 WCA part enter the fixed-point sum separately
-      if (any) acc += __float2ll_rn((float)du * FIX_SCALE);
-      if (wany) acc += __double2ll_rn(dw * (double)FIX_SCALE);
-      if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin(gs + gw, (double)BIG_TERM) * (double)FIX_SCALE);
-    }
-  }
 }
 
 template <typename T>

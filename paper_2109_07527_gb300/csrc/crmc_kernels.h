@@ -15,7 +15,8 @@ struct MdParams {
   const int *perm_slot, *bond_off, *bond_nbr;
   int n_perm;
   float fene_K, inv_R02;
-  int rcap;               // region particles staged in shared memory
+  const int *plist;       // occupied slots
+  const int *n_particles; // entries of plist
 };
 
 struct RebuildBufs {
@@ -43,16 +44,18 @@ struct LoadBufs {
   int n, n_site_map;
 };
 
-size_t phase_smem_bytes(const SysParams &P);
-cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
-                        cudaStream_t s);
-size_t md_smem_bytes(int kb, int nrb, int rcap);
-cudaError_t launch_phase(const SysParams &P, int R, bool log, int grid, int threads, size_t smem, cudaStream_t s,
-                         uint32_t sweep, int colour, uint32_t k0, uint32_t k1);
-cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int kb, int nb_dim, int nrb, int threads,
-                             cudaStream_t s);
+size_t phase_smem_bytes(const PhaseShape &S);
+int phase_shape_count();
+void phase_shape(int i, int *threads, int *regs);
+cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
+                         bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,
+                         uint32_t k1);
+cudaError_t launch_plist(const SysParams &P, int *plist, int *n_out, cudaStream_t s);
+cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int max_particles, cudaStream_t s);
 cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s);
 cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s);
+cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
+                        cudaStream_t s);
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
 cudaError_t launch_dump(const SysParams &P, const DumpBufs &D, cudaStream_t s);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,

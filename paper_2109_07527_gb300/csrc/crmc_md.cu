@@ -1,0 +1,340 @@
+// crmc_md.cu -- MD kernels (DSF + WCA + FENE forces, Langevin velocity Verlet),
+// the cell rebuild after particles move, configuration upload, state dump and
+// a Philox check kernel (sm_103a).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "crmc_device.cuh"
+#include "crmc_kernels.h"
+
+namespace crmc {
+
+// ---------------------------------------------------------------------------
+// MD forces: a group of 8 lanes per particle; the lanes of a group share the
+// (2h+1)^3 neighbour cells (cell side >= rc/h) and the group adds its pair
+// forces in 2^-24 fixed point, so the result does not depend on the launch
+// shape or the order of the particle list.  Mode 0: conservative forces into
+// fout; mode 1: + Langevin friction/noise; mode 2: + Langevin and the closing
+// half kick v += dt/2 f.
+// ---------------------------------------------------------------------------
+constexpr int MD_GROUP = 8;
+constexpr float FFIX_INV = 1.0f / 16777216.0f;
+
+__device__ __forceinline__ void force_pair(const SysParams &P, float xi, float yi, float zi, float qi, int ci,
+                                           float xj, float yj, float zj, float qj, int cj, long long &fx,
+                                           long long &fy, long long &fz) {
+  const float dx = wrap_diff(xi, xj, P.Lf, P.halfL);
+  const float dy = wrap_diff(yi, yj, P.Lf, P.halfL);
+  const float dz = wrap_diff(zi, zj, P.Lf, P.halfL);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  const WcaEntry &w = P.wca[ci * 4 + cj];
+  const bool coul = r2 < P.rc2 && qi != 0.0f && qj != 0.0f;
+  const bool wca = w.on && r2 < w.wcut2;
+  if (!coul && !wca) return;
+  const float rinv = rsqrtf(r2);
+  float g = 0.0f;  // force / r along (ri - rj), positive = repulsive
+  if (coul) {
+    const float r = r2 * rinv;
+    const float ar = P.alpha * r;
+    g = P.lBf * qi * qj * (erfcf(ar) * rinv * rinv + 1.1283791670955126f * P.alpha * __expf(-ar * ar) * rinv - P.c2) * rinv;
+  }
+  if (wca) {
+    const float s = r2 * rinv - w.del;
+    const float is = __fdividef(1.0f, s);
+    const float t = w.sig * is;
+    const float t2 = t * t;
+    const float t6 = t2 * t2 * t2;
+    g += 24.0f * w.eps * (2.0f * t6 * t6 - t6) * is * rinv;
+  }
+  fx += fix24(g * dx);
+  fy += fix24(g * dy);
+  fz += fix24(g * dz);
+}
+
+// compact list of occupied slots (order irrelevant)
+__global__ void k_plist(SysParams P, int *plist, int *n_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.ncell) return;
+  const int n = P.cnt[c];
+  if (n == 0) return;
+  const int o = atomicAdd(n_out, n);
+  for (int s = 0; s < n; ++s) plist[o + s] = c * P.cap + s;
+}
+
+__global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pi_idx = gt / MD_GROUP, sub = gt % MD_GROUP;
+  const int N = *M.n_particles;
+  const bool valid = pi_idx < N;
+  const int nc = P.nc, h = P.h, cap = P.cap;
+  long long fx = 0, fy = 0, fz = 0;
+  int gi = 0;
+  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    gi = M.plist[pi_idx];
+    pi = P.pos[gi];
+    const int ci = (P.info[gi] >> INFO_CLS_SHIFT) & 3;
+    const int cell = gi / cap;
+    const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+    // neighbour cells along each dimension: cx-h..cx+h, or every cell when
+    // the box has fewer than 2h+1 cells (no cell visited twice)
+    const int nb = min(2 * h + 1, nc);
+    const int nb3 = nb * nb * nb;
+    for (int o = sub; o < nb3; o += MD_GROUP) {
+      const int ox = o % nb, oy = (o / nb) % nb, oz = o / (nb * nb);
+      const int jx = nb == nc ? ox : (cx + ox - h + nc) % nc;
+      const int jy = nb == nc ? oy : (cy + oy - h + nc) % nc;
+      const int jz = nb == nc ? oz : (cz + oz - h + nc) % nc;
+      const int jc = jx + nc * (jy + nc * jz);
+      const int cnt = P.cnt[jc];
+      for (int s = 0; s < cnt; ++s) {
+        const int gj = jc * cap + s;
+        if (gj == gi) continue;
+        const float4 pj = P.pos[gj];
+        force_pair(P, pi.x, pi.y, pi.z, pi.w, ci, pj.x, pj.y, pj.z, pj.w, (P.info[gj] >> INFO_CLS_SHIFT) & 3, fx, fy,
+                   fz);
+      }
+    }
+  }
+  // FENE bonds of permanent particles, U = -K R0^2/2 ln(1 - (r/R0)^2), spread over the group
+  unsigned long long id = valid ? P.pid[gi] : ~0ull;
+  if (valid && id < (unsigned long long)M.n_perm) {
+    const int b0 = M.bond_off[id], b1 = M.bond_off[id + 1];
+    for (int bb = b0 + sub; bb < b1; bb += MD_GROUP) {
+      const float4 pj = P.pos[M.perm_slot[M.bond_nbr[bb]]];
+      const float dx = wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
+      const float dy = wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
+      const float dz = wrap_diff(pi.z, pj.z, P.Lf, P.halfL);
+      const float x2 = (dx * dx + dy * dy + dz * dz) * M.inv_R02;
+      if (x2 >= 1.0f) {
+        atomicOr(P.err, ERRB_BOND);
+        continue;
+      }
+      const float g = -M.fene_K / (1.0f - x2);
+      fx += fix24(g * dx);
+      fy += fix24(g * dy);
+      fz += fix24(g * dz);
+    }
+  }
+#pragma unroll
+  for (int o = MD_GROUP / 2; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+  }
+  if (!valid || sub != 0) return;
+  float4 f = make_float4((float)fx * FFIX_INV, (float)fy * FFIX_INV, (float)fz * FFIX_INV, 0.0f);
+  if (M.mode == 0) {
+    M.fout[gi] = f;
+    return;
+  }
+  // Langevin: -gamma v + sqrt(2 gamma kT / dt) xi, xi from Box-Muller on
+  // Philox(counter = (id_lo, id_hi, eval, 5), key = seed)
+  float4 v = M.vel[gi];
+  const uint4 w = philox10((uint32_t)id, (uint32_t)(id >> 32), M.eval, 5u, M.key0, M.key1);
+  const float u0 = ((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u1 = ((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = ((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u3 = ((float)(w.w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float r1 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s3, &c3);
+  f.x += -M.gamma * v.x + M.amp * r1 * c1;
+  f.y += -M.gamma * v.y + M.amp * r1 * s1;
+  f.z += -M.gamma * v.z + M.amp * r2 * c3;
+  M.fout[gi] = f;
+  if (M.mode == 2) {
+    v.x += 0.5f * M.dt * f.x;
+    v.y += 0.5f * M.dt * f.y;
+    v.z += 0.5f * M.dt * f.z;
+    M.vel[gi] = v;
+  }
+}
+
+// v += dt/2 f; x += dt v; wrap into [0, L)
+__global__ void k_md_kick_drift(SysParams P, MdParams M) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.ncell * P.cap) return;
+  const int c = g / P.cap;
+  if (g - c * P.cap >= P.cnt[c]) return;
+  float4 v = M.vel[g];
+  const float4 f = M.fout[g];
+  v.x += 0.5f * M.dt * f.x;
+  v.y += 0.5f * M.dt * f.y;
+  v.z += 0.5f * M.dt * f.z;
+  M.vel[g] = v;
+  float4 p = P.pos[g];
+  float x[3] = {p.x + M.dt * v.x, p.y + M.dt * v.y, p.z + M.dt * v.z};
+  for (int i = 0; i < 3; ++i) {
+    x[i] -= P.Lf * floorf(x[i] * P.invL);
+    if (x[i] >= P.Lf) x[i] -= P.Lf;
+    if (x[i] < 0.0f) x[i] = 0.0f;
+  }
+  P.pos[g] = make_float4(x[0], x[1], x[2], p.w);
+}
+
+// rebuild, step 1: scatter every particle into its new cell (unordered)
+__global__ void k_rebuild_scatter(SysParams P, RebuildBufs B) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.ncell * P.cap) return;
+  const int c = g / P.cap;
+  if (g - c * P.cap >= P.cnt[c]) return;
+  const float4 p = P.pos[g];
+  const int nc = P.nc;
+  const int cell = cell_of(p.x, P.scf, nc) + nc * (cell_of(p.y, P.scf, nc) + nc * cell_of(p.z, P.scf, nc));
+  const int s = atomicAdd(&B.cnt[cell], 1);
+  if (s >= P.cap) {
+    atomicOr(P.err, ERRB_CELL_OVERFLOW);
+    return;
+  }
+  const int o = cell * P.cap + s;
+  B.pos[o] = p;
+  B.pid[o] = P.pid[g];
+  B.info[o] = P.info[g];
+  B.vel[o] = B.vel_src[g];
+  B.frc[o] = B.frc_src[g];
+}
+
+// rebuild, step 2: one warp per cell sorts the cell by id into the primary arrays
+__global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n_perm) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P.ncell) return;
+  const int c = warp;
+  const int n = min(B.cnt[c], P.cap);
+  const int base = c * P.cap;
+  for (int e = lane; e < n; e += 32) {
+    const unsigned long long id = B.pid[base + e];
+    int rank = 0;
+    for (int o = 0; o < n; ++o) rank += B.pid[base + o] < id;
+    const int dst = base + rank;
+    P.pos[dst] = B.pos[base + e];
+    P.pid[dst] = id;
+    P.info[dst] = B.info[base + e];
+    B.vel_src[dst] = B.vel[base + e];
+    B.frc_src[dst] = B.frc[base + e];
+    if (id < (unsigned long long)n_perm) perm_slot[id] = dst;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    P.cnt[c] = n;
+    B.cnt[c] = 0;
+  }
+}
+
+// refresh the slot of every permanent particle
+__global__ void k_perm_slots(SysParams P, int *perm_slot, int n_perm) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.ncell * P.cap) return;
+  const int c = g / P.cap;
+  if (g - c * P.cap >= P.cnt[c]) return;
+  const unsigned long long id = P.pid[g];
+  if (id < (unsigned long long)n_perm) perm_slot[id] = g;
+}
+
+// dump every particle (unordered) for the state view
+__global__ void k_dump(SysParams P, DumpBufs D) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= P.ncell * P.cap) return;
+  const int c = g / P.cap;
+  if (g - c * P.cap >= P.cnt[c]) return;
+  const int o = atomicAdd(D.counter, 1);
+  if (o >= D.cap) return;
+  D.pos[o] = P.pos[g];
+  D.pid[o] = P.pid[g];
+  D.info[o] = P.info[g];
+  if (D.vel_src) D.vel[o] = D.vel_src[g];
+  if (D.frc_src) D.frc[o] = D.frc_src[g];
+}
+
+// load: place input particles (index = id) into cells, unordered
+__global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= I.n) return;
+  const float x = I.xyz[3 * i], y = I.xyz[3 * i + 1], z = I.xyz[3 * i + 2];
+  const int t = I.type[i];
+  const int ion = (t == CR_ACID || t == CR_BASE) && I.state[i] ? 1 : 0;
+  float q = 0.0f;
+  int cl = I.cls[i];
+  if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
+  else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
+  else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
+  else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+  const int site = (i < I.n_site_map && I.site[i] >= 0) ? I.site[i] : 0;
+  const int nc = P.nc;
+  const int cell = cell_of(x, P.scf, nc) + nc * (cell_of(y, P.scf, nc) + nc * cell_of(z, P.scf, nc));
+  const int s = atomicAdd(&B.cnt[cell], 1);
+  if (s >= P.cap) {
+    atomicOr(P.err, ERRB_CELL_OVERFLOW);
+    return;
+  }
+  const int o = cell * P.cap + s;
+  B.pos[o] = make_float4(x, y, z, q);
+  B.pid[o] = (unsigned long long)i;
+  B.info[o] = t | (cl << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
+  B.vel[o] = I.vel ? make_float4(I.vel[3 * i], I.vel[3 * i + 1], I.vel[3 * i + 2], 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
+  B.frc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
+                         uint4 *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox10(c0 + (uint32_t)i, c1, c2, c3, k0, k1);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_plist(const SysParams &P, int *plist, int *n_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(n_out, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_plist<<<(P.ncell + 255) / 256, 256, 0, s>>>(P, plist, n_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int max_particles, cudaStream_t s) {
+  const long long threads = (long long)max_particles * MD_GROUP;
+  k_md_forces<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s) {
+  const int n = P.ncell * P.cap;
+  k_md_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(P, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s) {
+  const int n = P.ncell * P.cap;
+  k_rebuild_scatter<<<(n + 255) / 256, 256, 0, s>>>(P, B);
+  k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
+                        cudaStream_t s) {
+  if (I.n > 0) k_load_scatter<<<(I.n + 255) / 256, 256, 0, s>>>(P, I, B);
+  k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s) {
+  const int n = P.ncell * P.cap;
+  k_perm_slots<<<(n + 255) / 256, 256, 0, s>>>(P, perm_slot, n_perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dump(const SysParams &P, const DumpBufs &D, cudaStream_t s) {
+  const int n = P.ncell * P.cap;
+  k_dump<<<(n + 255) / 256, 256, 0, s>>>(P, D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
+                          uint4 *out, cudaStream_t s) {
+  k_philox<<<(n + 255) / 256, 256, 0, s>>>(c0, c1, c2, c3, k0, k1, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace crmc

@@ -1,0 +1,915 @@
+// crmc_phase.cu -- the colour-phase kernel of the CR-MC stage (sm_103a).
+//
+// k_cr_phase: one CTA per active domain of one colour of the 8-colour
+// checkerboard, for one or several replicas (blockIdx.y) in one launch.
+// The CTA
+//   1. stages the domain's particles into a list kept in canonical order
+//      (in-domain cell rank, then id) -- in shared memory, or in a global
+//      scratch region when the domain is unusually dense -- and the halo
+//      particles around it into registers (they do not change in the phase);
+//   2. draws the phase's random numbers for a chunk of trials at once
+//      (Philox4x32-10, counter (trial, domain, phase, purpose));
+//   3. runs the m trials of the domain one after another: warp 0 selects the
+//      participants (ballot scans of the list); every thread sums its share of
+//      the pair changes -- FP32 Coulomb, FP64 WCA of inserted/deleted ions --
+//      into 64-bit fixed point, exact and therefore independent of the thread
+//      count; warp 0 takes the FP64 Metropolis decision and commits the move;
+//   4. writes the domain's cells back (id-sorted) and adds its count changes.
+// The move rules are those of Sec. II.C of the paper applied to the domain
+// (the domain's volume and counts).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "crmc_device.cuh"
+#include "crmc_kernels.h"
+
+namespace crmc {
+
+namespace {
+
+constexpr int MAX_WARPS = 16;  // up to 512 threads per CTA
+
+struct TrialPre {
+  uint32_t w0, w1, w2, w3;  // move, site choice, first ion, second ion
+  float ax, ay, az, bx, by, bz;
+  int rankA, rankB;  // in-domain cell rank of the insertion points, -1 = outside
+  uint32_t uhi, ulo; // the two words of the Metropolis uniform
+  float lnu_f;       // FP32 ln u (decides unless within LNU_BAND of lnA)
+  int pad;
+  double lnu;        // FP64 ln u (trial records only)
+};
+
+struct Desc {
+  float x, y, z, dqlB;  // position, lB * (q_new - q_old)
+  int dp, cls, skip;    // WCA presence change, class, list index (-1 inserted)
+};
+
+struct TrialCtl {
+  Desc c[2];
+  int nch;    // changed particles needing the energy sweep (0 = decided)
+  int flags;  // CR_TRIAL_* bits known before the sweep
+  int move;
+  int site, ionA, ionB;  // list indices (-1 none)
+  unsigned long long id_a, id_b, newid;
+  long long ln_ratio_fx, dself_fx;  // 2^-48 fixed point
+  float qa_o, qa_n, qb_o, qb_n;  // effective charges of the two changed particles
+  int pa_o, pa_n, pb_o, pb_n;    // presence before / after
+};
+
+struct DomList {
+  float4 *pos, *vel;
+  unsigned long long *id;
+  long long *lnk;  // site constant ln10 (pH - pK - pI_X) at 2^-48, 0 for non-sites
+  int *info, *rank;
+};
+
+// FP32 constants of the pair sweep, kept in registers
+struct PairK {
+  float Lf, halfL, rc2, alpha, c1, c2, rcf, lBf;
+  double Ld, halfLd;
+};
+
+__device__ __forceinline__ int region_coord(int i, int org, int k, int h, int nr, int nc) {
+  int c = (i < k + h) ? org + i : org + i - nr;
+  c %= nc;
+  if (c < 0) c += nc;
+  return c;
+}
+
+// Exclusive scan of n ints (shared memory) into pre[0..n]; all threads call.
+__device__ void block_scan(const int *vals, int n, int *pre, int *tmp) {
+  const int T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, nw = T >> 5;
+  const int per = (n + T - 1) / T;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += vals[i];
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = lane < nw ? tmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < nw) tmp[lane] = v;
+  }
+  __syncthreads();
+  int run = x - s + (w > 0 ? tmp[w - 1] : 0);
+  for (int i = lo; i < hi; ++i) {
+    pre[i] = run;
+    run += vals[i];
+  }
+  if (t == T - 1) pre[n] = run;
+  __syncthreads();
+}
+
+// largest i with pre[i] <= j (pre ascending, pre[0] = 0, j < pre[n])
+__device__ __forceinline__ int upper_idx(const int *pre, int n, int j) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pre[mid] <= j) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// warp: index of the kth (0-based) list entry of a kind, -1 if none
+__device__ __forceinline__ int warp_kth(const int *info, int n, int kind, int kth) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const bool m = j < n && kind_of(info[j]) == kind;
+    const unsigned b = __ballot_sync(0xffffffffu, m);
+    const int c = __popc(b);
+    if (kth < c) {
+      const unsigned lt = b & ((1u << lane) - 1u);
+      const unsigned hit = __ballot_sync(0xffffffffu, m && __popc(lt) == kth);
+      return base + __ffs(hit) - 1;
+    }
+    kth -= c;
+  }
+  return -1;
+}
+
+// warp: number of entries with rank < r and rank == r
+__device__ __forceinline__ void warp_rank_count(const int *rank, int n, int r, int &below, int &same) {
+  const int lane = threadIdx.x & 31;
+  below = 0;
+  same = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    const int rk = j < n ? rank[j] : INT_MAX;
+    below += __popc(__ballot_sync(0xffffffffu, rk < r));
+    same += __popc(__ballot_sync(0xffffffffu, rk == r));
+  }
+}
+
+// warp: open a hole at p (entries [p, n) move up by one)
+__device__ void warp_insert_gap(DomList L, int n, int p) {
+  const int lane = threadIdx.x & 31;
+  for (int hi = n; hi > p; hi -= 32) {
+    const int lo = max(p, hi - 32);
+    const int j = lo + lane;
+    const bool act = j < hi;
+    float4 a, v;
+    unsigned long long b = 0;
+    long long e = 0;
+    int c = 0, d = 0;
+    if (act) { a = L.pos[j]; v = L.vel[j]; b = L.id[j]; e = L.lnk[j]; c = L.info[j]; d = L.rank[j]; }
+    __syncwarp();
+    if (act) { L.pos[j + 1] = a; L.vel[j + 1] = v; L.id[j + 1] = b; L.lnk[j + 1] = e; L.info[j + 1] = c; L.rank[j + 1] = d; }
+    __syncwarp();
+  }
+}
+
+// warp: remove entry p (entries (p, n) move down by one)
+__device__ void warp_remove(DomList L, int n, int p) {
+  const int lane = threadIdx.x & 31;
+  for (int lo = p + 1; lo < n; lo += 32) {
+    const int j = lo + lane;
+    const bool act = j < n;
+    float4 a, v;
+    unsigned long long b = 0;
+    long long e = 0;
+    int c = 0, d = 0;
+    if (act) { a = L.pos[j]; v = L.vel[j]; b = L.id[j]; e = L.lnk[j]; c = L.info[j]; d = L.rank[j]; }
+    __syncwarp();
+    if (act) { L.pos[j - 1] = a; L.vel[j - 1] = v; L.id[j - 1] = b; L.lnk[j - 1] = e; L.info[j - 1] = c; L.rank[j - 1] = d; }
+    __syncwarp();
+  }
+}
+
+// WCA change (FP64) of an inserted / deleted particle against a bystander;
+// out of line because it is rare (pairs inside 2^(1/6) sigma) and long.
+// Returns (du, gross); gross < 0: no interaction; gross = -2: overlap.
+__device__ __noinline__ double2 wca_change_nl(const WcaEntry &w, int dp, float cx, float cy, float cz, float xj,
+                                              float yj, float zj, double L, double halfL) {
+  double du = 0.0, gs = 0.0;
+  int ov = 0;
+  const bool hit = wca_change_d(w, dp, cx, cy, cz, xj, yj, zj, L, halfL, du, gs, ov);
+  if (ov) return make_double2(0.0, -2.0);
+  if (!hit) return make_double2(0.0, -1.0);
+  return make_double2(du, gs);
+}
+
+// One pair change of a changed particle c against a bystander j: the FP32
+// Coulomb part lB dq_c q_j phi(r) [r < rc] and, for inserted / deleted c,
+// the FP64 WCA part, both into 2^-32 kT fixed point.  |du| >= 2^20 kT or an
+// inserted particle closer than half a diameter flags an overlap.
+template <bool WITH_S>
+__device__ __forceinline__ void pair_change(const PairK &K, const WcaEntry *wca, float cx, float cy, float cz,
+                                            float dqlB, int dp, int ccls, float xj, float yj, float zj, float qj,
+                                            int jcls, long long &acc, unsigned long long &sacc, int &ov) {
+  const float dx = wrap_diff(xj, cx, K.Lf, K.halfL);
+  const float dy = wrap_diff(yj, cy, K.Lf, K.halfL);
+  const float dz = wrap_diff(zj, cz, K.Lf, K.halfL);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  float du = 0.0f, gs = 0.0f;
+  bool any = false;
+  if (r2 < K.rc2 && dqlB != 0.0f && qj != 0.0f) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float e = erfcf(K.alpha * r) * rinv;
+    du = dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
+    if (WITH_S) gs = fabsf(dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
+    any = true;
+  }
+  if (dp != 0) {
+    const WcaEntry &w = wca[ccls * 4 + jcls];
+    if (w.on && r2 < 1.0001f * w.wcut2) {
+      const double2 res = wca_change_nl(w, dp, cx, cy, cz, xj, yj, zj, K.Ld, K.halfLd);
+      if (res.y == -2.0) {
+        ov = 1;
+      } else if (res.y >= 0.0) {
+        if (!(fabs((double)du + res.x) < (double)BIG_TERM)) {
+          ov = 1;
+        } else {
+          if (any) acc += fix32(du);
+          acc += __double2ll_rn(res.x * (double)FIX_SCALE);
+          if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + res.y, (double)BIG_TERM) * (double)FIX_SCALE);
+        }
+        return;
+      }
+    }
+  }
+  if (any) {
+    if (!(fabsf(du) < BIG_TERM)) {
+      ov = 1;
+    } else {
+      acc += fix32(du);
+      if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
+    }
+  }
+}
+
+// pair change between the two changed particles: u_new - u_old, Coulomb in
+// FP32 and WCA in FP64, into fixed point
+__device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
+                                       unsigned long long &sacc, int &ov) {
+  const Desc &A = t.c[0], &B = t.c[1];
+  const float dx = wrap_diff(B.x, A.x, K.Lf, K.halfL);
+  const float dy = wrap_diff(B.y, A.y, K.Lf, K.halfL);
+  const float dz = wrap_diff(B.z, A.z, K.Lf, K.halfL);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  const WcaEntry &w = wca[A.cls * 4 + B.cls];
+  float uc[2] = {0.0f, 0.0f};
+  double uw[2] = {0.0, 0.0};
+  double gs = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    const bool pres = s ? (t.pa_n && t.pb_n) : (t.pa_o && t.pb_o);
+    if (!pres) continue;
+    const float qa = s ? t.qa_n : t.qa_o, qb = s ? t.qb_n : t.qb_o;
+    if (r2 < K.rc2 && qa != 0.0f && qb != 0.0f) {
+      const float rinv = rsqrtf(r2);
+      const float r = r2 * rinv;
+      const float e = erfcf(K.alpha * r) * rinv;
+      uc[s] = K.lBf * qa * qb * (e - K.c1 + K.c2 * (r - K.rcf));
+      gs += (double)(fabsf(K.lBf * qa * qb) * (e + K.c1 + K.c2 * fabsf(r - K.rcf)));
+    }
+    if (w.on && r2 < 1.0001f * w.wcut2) {
+      const double ddx = wrap_diff_d(B.x, A.x, K.Ld, K.halfLd), ddy = wrap_diff_d(B.y, A.y, K.Ld, K.halfLd),
+                   ddz = wrap_diff_d(B.z, A.z, K.Ld, K.halfLd);
+      const double r = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+      if (r < w.wcut_d) {
+        const double sv = r - w.del_d;
+        const bool inserted = s == 1 && ((t.pa_n && !t.pa_o) || (t.pb_n && !t.pb_o));
+        if (inserted && sv < 0.5 * w.sig_d) {
+          ov = 1;
+        } else {
+          const double tt = w.sig_d / sv;
+          const double t2 = tt * tt;
+          const double t6 = t2 * t2 * t2;
+          uw[s] = 4.0 * w.eps_d * (t6 * t6 - t6) + w.eps_d;
+          gs += w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
+        }
+      }
+    }
+  }
+  const float dc = uc[1] - uc[0];
+  const double dw = uw[1] - uw[0];
+  if (dc != 0.0f || dw != 0.0) {
+    if (!(fabs((double)dc + dw) < (double)BIG_TERM)) {
+      ov = 1;
+    } else {
+      acc += fix32(dc) + __double2ll_rn(dw * (double)FIX_SCALE);
+      sacc += (unsigned long long)__double2ll_rn(fmin(gs, (double)BIG_TERM) * (double)FIX_SCALE);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the phase kernel
+// ---------------------------------------------------------------------------
+template <int T, int R, bool LOG>
+__global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
+    k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
+               uint32_t key0, uint32_t key1_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+
+  // ---- shared memory carve-up (launch-wide shape)
+  unsigned char *sp = smem;
+  SysParams &P = *(SysParams *)sp;
+  sp += (sizeof(SysParams) + 15) / 16 * 16;
+  DomList Ls;
+  Ls.pos = (float4 *)sp; sp += sizeof(float4) * S.dcs;
+  Ls.vel = (float4 *)sp; sp += sizeof(float4) * S.dcs;
+  Ls.id = (unsigned long long *)sp; sp += sizeof(unsigned long long) * S.dcs;
+  Ls.lnk = (long long *)sp; sp += sizeof(long long) * S.dcs;
+  Ls.info = (int *)sp; sp += sizeof(int) * S.dcs;
+  Ls.rank = (int *)sp; sp += sizeof(int) * S.dcs;
+  long long *lntab_s = (long long *)sp; sp += sizeof(long long) * S.lns;
+  TrialPre *tp = (TrialPre *)sp; sp += sizeof(TrialPre) * TRIAL_CHUNK;
+  TrialCtl *ctl = (TrialCtl *)sp; sp += (sizeof(TrialCtl) + 15) / 16 * 16;
+  long long *red = (long long *)sp; sp += sizeof(long long) * MAX_WARPS;
+  unsigned long long *reds = (unsigned long long *)sp; sp += sizeof(unsigned long long) * MAX_WARPS;
+  unsigned long long *st = (unsigned long long *)sp; sp += sizeof(unsigned long long) * 16;
+  int *redov = (int *)sp; sp += sizeof(int) * MAX_WARPS;
+  int *scan_tmp = (int *)sp; sp += sizeof(int) * 32;
+  int *misc = (int *)sp; sp += sizeof(int) * 16;  // [0] list size, [1..7] kind counts, [9..15] at start, [8] flags
+  int *hcnt = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
+  int *hcell = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
+  int *hpre = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
+  int *dcnt = (int *)sp; sp += sizeof(int) * (S.kc3 + 1);
+  int *dpre = (int *)sp; sp += sizeof(int) * (S.kc3 + 1);
+
+  {
+    const int *src = (const int *)&reps[blockIdx.y];
+    int *dst = (int *)&P;
+    for (int i = tid; i < (int)(sizeof(SysParams) / 4); i += T) dst[i] = src[i];
+  }
+  __syncthreads();
+  if ((int)blockIdx.x >= P.nact) return;  // uniform over the CTA
+  const int k = P.k, h = P.h, nc = P.nc, nr = P.nr, m = P.m;
+  const int KC = k * k * k, NR = nr * nr * nr;
+  const uint32_t key1 = key1_base ^ P.key_xor;
+  PairK K;
+  K.Lf = P.Lf; K.halfL = P.halfL; K.rc2 = P.rc2; K.alpha = P.alpha; K.c1 = P.c1; K.c2 = P.c2; K.rcf = P.rcf;
+  K.lBf = P.lBf; K.Ld = P.Ld; K.halfLd = P.halfLd;
+  const WcaEntry *wca = P.wca;
+
+  // ---- which domain
+  int dd[3];
+  if (P.global) {
+    dd[0] = dd[1] = dd[2] = 0;
+  } else {
+    const int hn = P.nd >> 1;
+    const int b = blockIdx.x;
+    dd[0] = 2 * (b % hn) + (colour & 1);
+    dd[1] = 2 * ((b / hn) % hn) + ((colour >> 1) & 1);
+    dd[2] = 2 * (b / (hn * hn)) + ((colour >> 2) & 1);
+  }
+  const int d = dd[0] + P.nd * (dd[1] + P.nd * dd[2]);
+  const uint32_t phi = sweep * (uint32_t)P.ncol + (uint32_t)colour;
+  int off[3] = {0, 0, 0};
+  if (!P.global) {
+    const uint4 w = philox10(0u, 0u, sweep, 4u, key0, key1);
+    off[0] = pick32(w.x, nc);
+    off[1] = pick32(w.y, nc);
+    off[2] = pick32(w.z, nc);
+  }
+  int org[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) org[i] = (off[i] + dd[i] * k) % nc;
+
+  // ---- cell counts of the domain and of its halo
+  for (int r = tid; r < KC; r += T) {
+    const int lx = r % k, ly = (r / k) % k, lz = r / (k * k);
+    dcnt[r] = P.cnt[(org[0] + lx) % nc + nc * ((org[1] + ly) % nc + nc * ((org[2] + lz) % nc))];
+  }
+  for (int i = tid; i < NR; i += T) {
+    const int ix = i % nr, iy = (i / nr) % nr, iz = i / (nr * nr);
+    int c = 0, cell = 0;
+    if (!(ix < k && iy < k && iz < k)) {
+      cell = region_coord(ix, org[0], k, h, nr, nc) +
+             nc * (region_coord(iy, org[1], k, h, nr, nc) + nc * region_coord(iz, org[2], k, h, nr, nc));
+      c = P.cnt[cell];
+    }
+    hcnt[i] = c;
+    hcell[i] = cell;
+  }
+  if (tid < 16) {
+    misc[tid] = 0;
+    st[tid] = 0ull;
+  }
+  __syncthreads();
+  block_scan(dcnt, KC, dpre, scan_tmp);
+  block_scan(hcnt, NR, hpre, scan_tmp);
+  const int ND = dpre[KC], NH = hpre[NR];
+  // the list lives in shared memory unless the domain is unusually dense
+  const bool in_smem = ND + 2 * m <= S.dcs;
+  DomList L = Ls;
+  if (!in_smem) {
+    const size_t o = (size_t)blockIdx.x * P.dcap_glob;
+    L.pos = P.gs_pos + o; L.vel = P.gs_vel + o; L.id = P.gs_id + o; L.lnk = P.gs_lnk + o;
+    L.info = P.gs_info + o; L.rank = P.gs_rank + o;
+    if (ND + 2 * m > P.dcap_glob) {  // cannot happen: a cell holds at most cap particles
+      if (tid == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
+      return;
+    }
+  }
+  const int lnmax_need = min(P.lnmax, ND + 2 * m + 2);
+  const bool ln_in_smem = lnmax_need <= S.lns;
+  const long long *lnt = ln_in_smem ? lntab_s : P.lntab_fx;
+  if (ln_in_smem)
+    for (int i = tid; i < lnmax_need; i += T) lntab_s[i] = P.lntab_fx[i];
+  for (int j = tid; j < ND; j += T) {
+    const int r = upper_idx(dpre, KC, j);
+    const int lx = r % k, ly = (r / k) % k, lz = r / (k * k);
+    const int cell = (org[0] + lx) % nc + nc * ((org[1] + ly) % nc + nc * ((org[2] + lz) % nc));
+    const int g = cell * P.cap + (j - dpre[r]);
+    const int info = P.info[g];
+    const int t = info & INFO_TYPE_MASK;
+    L.pos[j] = P.pos[g];
+    L.vel[j] = P.vel[g];
+    L.id[j] = P.pid[g];
+    L.lnk[j] = (t == CR_ACID || t == CR_BASE) ? P.lnK_fx[info >> INFO_SITE_SHIFT] : 0ll;
+    L.info[j] = info;
+    L.rank[j] = r;
+    atomicAdd(&misc[1 + min(kind_of(info), 6)], 1);
+  }
+  // halo particles into registers: w = q + 8 * cls
+  float4 hreg[R];
+  int nmine = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j = tid + r * T;
+    hreg[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < NH) {
+      const int i = upper_idx(hpre, NR, j);
+      const int g = hcell[i] * P.cap + (j - hpre[i]);
+      const float4 p = P.pos[g];
+      const int cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
+      hreg[r] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)cls);
+      nmine = r + 1;
+    }
+  }
+  if (tid == 0) misc[0] = ND;
+  __syncthreads();
+  if (tid < 7) misc[9 + tid] = misc[1 + tid];
+  const int cc_thread = nw > 1 ? 32 : 0;  // the thread that adds the changed-pair term
+  const long long log_dom = (long long)(sweep - sweep0) * P.per_sweep + (long long)colour * P.nact * m +
+                            (long long)blockIdx.x * m;
+
+  for (int k0 = 0; k0 < m; k0 += TRIAL_CHUNK) {
+    const int nchunk = min(TRIAL_CHUNK, m - k0);
+    // ---- random numbers of the chunk
+    for (int t = tid; t < nchunk; t += T) {
+      const uint32_t kk = (uint32_t)(k0 + t);
+      const uint4 a = philox10(kk, (uint32_t)d, phi, 0u, key0, key1);
+      const uint4 b = philox10(kk, (uint32_t)d, phi, 1u, key0, key1);
+      const uint4 c = philox10(kk, (uint32_t)d, phi, 2u, key0, key1);
+      TrialPre q;
+      q.w0 = a.x; q.w1 = a.y; q.w2 = a.z; q.w3 = a.w;
+      q.ax = insert_coord(org[0], b.x, k, nc, P.af, P.Lf);
+      q.ay = insert_coord(org[1], b.y, k, nc, P.af, P.Lf);
+      q.az = insert_coord(org[2], b.z, k, nc, P.af, P.Lf);
+      q.bx = insert_coord(org[0], b.w, k, nc, P.af, P.Lf);
+      q.by = insert_coord(org[1], c.x, k, nc, P.af, P.Lf);
+      q.bz = insert_coord(org[2], c.y, k, nc, P.af, P.Lf);
+      const float xs[2][3] = {{q.ax, q.ay, q.az}, {q.bx, q.by, q.bz}};
+      int rk[2];
+      for (int s = 0; s < 2; ++s) {
+        int l[3];
+        bool in = true;
+        for (int i = 0; i < 3; ++i) {
+          const int cc = cell_of(xs[s][i], P.scf, nc);
+          const int sh = ((cc - off[i]) % nc + nc) % nc;
+          in = in && (sh / k == dd[i]);
+          l[i] = sh % k;
+        }
+        rk[s] = in ? l[0] + k * (l[1] + k * l[2]) : -1;
+      }
+      q.rankA = rk[0];
+      q.rankB = rk[1];
+      q.uhi = c.z;
+      q.ulo = c.w;
+      q.lnu_f = logf((float)(c.z >> 5) * 7.450580596923828e-09f + ((float)(c.w >> 6) + 0.5f) * 1.1102230246251565e-16f);
+      q.pad = 0;
+      q.lnu = LOG ? log(unif53(c.z, c.w)) : 0.0;
+      tp[t] = q;
+    }
+    __syncthreads();
+
+    for (int t = 0; t < nchunk; ++t) {
+      const int kk = k0 + t;
+      // ---- warp 0: proposal and participants
+      if (warp == 0) {
+        const TrialPre q = tp[t];
+        const int n = misc[0];
+        const int mv = pick32(q.w0, 2 * P.n_react);
+        const int r = P.react[mv >> 1];
+        const bool fwd = (mv & 1) == 0;
+        int flags = 0, site = -1, ionA = -1, ionB = -1, nch = 0;
+        bool bad = false;
+        long long ln_ratio = 0;
+        const unsigned long long newid = ((unsigned long long)(phi + 1u) << 32) |
+                                         (unsigned long long)(2u * ((uint32_t)d * (uint32_t)m + (uint32_t)kk));
+        unsigned long long id_a = ~0ull, id_b = ~0ull;
+        Desc c0 = {}, c1 = {};
+        float qa_o = 0.f, qa_n = 0.f, qb_o = 0.f, qb_n = 0.f;
+        int pa_o = 0, pa_n = 0, pb_o = 0, pb_n = 0;
+        if (r == R_ACID || r == R_BASE) {
+          const int kn = r == R_ACID ? K_A0 : K_B0, ki = r == R_ACID ? K_A1 : K_B1;
+          const int kx = r == R_ACID ? K_XP : K_XM;
+          const float qs = r == R_ACID ? -1.0f : 1.0f;
+          const int n0 = misc[1 + kn], n1 = misc[1 + ki], nx = misc[1 + kx];
+          if (fwd) {
+            if (n0 == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+            else {
+              site = warp_kth(L.info, n, kn, pick32(q.w1, n0));
+              if (q.rankA < 0) flags |= CR_TRIAL_EDGE;
+              if (site < 0) { site = 0; bad = true; }
+              id_a = L.id[site];
+              id_b = newid;
+              const float4 sp4 = L.pos[site];
+              const int sinfo = L.info[site];
+              c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * qs, 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
+              c1 = Desc{q.ax, q.ay, q.az, P.lBf * (-qs * P.ion_q), 1, P.ion_cls, -1};
+              qa_o = 0.f; qa_n = qs; qb_o = 0.f; qb_n = -qs * P.ion_q;
+              pa_o = pa_n = 1; pb_o = 0; pb_n = 1;
+              nch = 2;
+              ln_ratio = lnt[n0] + P.lnz1_fx - lnt[n1 + 1];
+              ln_ratio -= lnt[nx + 1];
+              ln_ratio += L.lnk[site];
+            }
+          } else {
+            if (n1 == 0 || nx == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+            else {
+              site = warp_kth(L.info, n, ki, pick32(q.w1, n1));
+              ionA = warp_kth(L.info, n, kx, pick32(q.w2, nx));
+              if (site < 0 || ionA < 0) { site = max(site, 0); ionA = max(ionA, 0); bad = true; }
+              id_a = L.id[site];
+              id_b = L.id[ionA];
+              const float4 sp4 = L.pos[site], ip4 = L.pos[ionA];
+              const int sinfo = L.info[site], iinfo = L.info[ionA];
+              c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * (-qs), 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
+              c1 = Desc{ip4.x, ip4.y, ip4.z, P.lBf * (-ip4.w), -1, (iinfo >> INFO_CLS_SHIFT) & 3, ionA};
+              qa_o = qs; qa_n = 0.f; qb_o = ip4.w; qb_n = 0.f;
+              pa_o = pa_n = 1; pb_o = 1; pb_n = 0;
+              nch = 2;
+              ln_ratio = lnt[n1] - lnt[n0 + 1] - P.lnz1_fx;
+              ln_ratio += lnt[nx];
+              ln_ratio -= L.lnk[site];
+            }
+          }
+        } else {
+          const int nxp = misc[1 + K_XP], nxm = misc[1 + K_XM];
+          if (fwd) {
+            if (q.rankA < 0 || q.rankB < 0) flags |= CR_TRIAL_EDGE;
+            id_a = newid;
+            id_b = newid + 1u;
+            c0 = Desc{q.ax, q.ay, q.az, P.lBf * P.ion_q, 1, P.ion_cls, -1};
+            c1 = Desc{q.bx, q.by, q.bz, P.lBf * (-P.ion_q), 1, P.ion_cls, -1};
+            qa_o = 0.f; qa_n = P.ion_q; qb_o = 0.f; qb_n = -P.ion_q;
+            pa_o = 0; pa_n = 1; pb_o = 0; pb_n = 1;
+            nch = 2;
+            ln_ratio = 2 * P.lnz1_fx + P.lnsalt_fx;
+            ln_ratio -= lnt[nxp + 1] + lnt[nxm + 1];
+          } else {
+            if (nxp == 0 || nxm == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+            else {
+              ionA = warp_kth(L.info, n, K_XP, pick32(q.w2, nxp));
+              ionB = warp_kth(L.info, n, K_XM, pick32(q.w3, nxm));
+              if (ionA < 0 || ionB < 0) { ionA = max(ionA, 0); ionB = max(ionB, 0); bad = true; }
+              id_a = L.id[ionA];
+              id_b = L.id[ionB];
+              const float4 a4 = L.pos[ionA], b4 = L.pos[ionB];
+              c0 = Desc{a4.x, a4.y, a4.z, P.lBf * (-a4.w), -1, (L.info[ionA] >> INFO_CLS_SHIFT) & 3, ionA};
+              c1 = Desc{b4.x, b4.y, b4.z, P.lBf * (-b4.w), -1, (L.info[ionB] >> INFO_CLS_SHIFT) & 3, ionB};
+              qa_o = a4.w; qa_n = 0.f; qb_o = b4.w; qb_n = 0.f;
+              pa_o = 1; pa_n = 0; pb_o = 1; pb_n = 0;
+              nch = 2;
+              ln_ratio = -2 * P.lnz1_fx - P.lnsalt_fx;
+              ln_ratio += lnt[nxp] + lnt[nxm];
+            }
+          }
+        }
+        // a failed selection would mean the kind counts and the list disagree:
+        // record it and reject instead of touching memory outside the list
+        if (bad) {
+          flags |= CR_TRIAL_NO_ELIGIBLE;
+          if (lane == 0) atomicOr(P.err, ERRB_ARG);
+        }
+        if (lane == 0) {
+          TrialCtl &C = *ctl;
+          C.c[0] = c0;
+          C.c[1] = c1;
+          C.flags = flags;
+          C.nch = (flags & (CR_TRIAL_NO_ELIGIBLE | CR_TRIAL_EDGE)) ? 0 : nch;
+          C.move = 2 * r + (fwd ? 0 : 1);
+          C.site = site;
+          C.ionA = ionA;
+          C.ionB = ionB;
+          C.id_a = id_a;
+          C.id_b = id_b;
+          C.newid = newid;
+          C.ln_ratio_fx = ln_ratio;
+          C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
+          C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
+          // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
+          const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
+                         (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
+          C.dself_fx = P.lBself_fx * (long long)sq;
+        }
+      }
+      __syncthreads();
+      // ---- all threads: the pair-change sweep
+      const int nch = ctl->nch;
+      if (nch) {
+        long long acc = 0;
+        unsigned long long sacc = 0;
+        int ov = 0;
+        const Desc A = ctl->c[0], B = ctl->c[1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r < nmine) {
+            const float4 p = hreg[r];
+            const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+            const float q = p.w - 8.0f * (float)cls;
+            pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, q, cls, acc, sacc, ov);
+            pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, q, cls, acc, sacc, ov);
+          }
+        }
+        // halo beyond the registers (dense regions): straight from global memory
+        for (int j = R * T + tid; j < NH; j += T) {
+          const int i = upper_idx(hpre, NR, j);
+          const int g = hcell[i] * P.cap + (j - hpre[i]);
+          const float4 p = P.pos[g];
+          const int cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
+          pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+          pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+        }
+        const int n = misc[0];
+        for (int j = tid; j < n; j += T) {
+          if (j == A.skip || j == B.skip) continue;
+          const float4 p = L.pos[j];
+          const int cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
+          pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+          pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+        }
+        if (tid == cc_thread) cc_change(K, wca, *ctl, acc, sacc, ov);
+        acc = warp_sum(acc);
+        if (LOG) sacc = warp_sum(sacc);
+        ov = __any_sync(0xffffffffu, ov) ? 1 : 0;
+        if (lane == 0) {
+          red[warp] = acc;
+          reds[warp] = sacc;
+          redov[warp] = ov;
+        }
+      }
+      __syncthreads();
+      // ---- warp 0: decision and commit
+      if (warp == 0) {
+        const TrialCtl &C = *ctl;
+        const TrialPre &q = tp[t];
+        int flags = C.flags;
+        bool accept = false;
+        double dE = 0.0, Ssum = 0.0, lnA = -INFINITY;
+        if (C.nch) {
+          long long tot = 0;
+          unsigned long long stot = 0;
+          int anyov = 0;
+          for (int w = 0; w < nw; ++w) {
+            tot += red[w];
+            stot += reds[w];
+            anyov |= redov[w];
+          }
+          if (anyov) {
+            flags |= CR_TRIAL_OVERLAP;
+            dE = INFINITY;
+          } else {
+            const long long totc = tot > DE_CLAMP32 ? DE_CLAMP32 : (tot < -DE_CLAMP32 ? -DE_CLAMP32 : tot);
+            const long long lnA_fx = C.ln_ratio_fx - ((totc << 16) + C.dself_fx);
+            // FP32 ln u decides outside the band; inside it FP64 ln u does
+            const long long lnu_apx = (long long)__float2int_rn(q.lnu_f * 16777216.0f) << 24;
+            const long long diff = lnA_fx - lnu_apx;
+            if (diff > LNU_BAND) accept = true;
+            else if (diff < -LNU_BAND) accept = false;
+            else accept = __double2ll_rn(log(unif53(q.uhi, q.ulo)) * LNFIX) < lnA_fx;
+            if (LOG) {
+              dE = (double)tot * FIX_INV + (double)C.dself_fx / LNFIX;
+              Ssum = (double)stot * FIX_INV + fabs((double)C.dself_fx / LNFIX);
+              lnA = (double)C.ln_ratio_fx / LNFIX - dE;  // unclamped, for the record
+            }
+          }
+        }
+        const int r = C.move >> 1;
+        const bool fwd = (C.move & 1) == 0;
+        int n = misc[0];
+        // cell capacity for insertions (checked before committing anything)
+        if (accept && fwd) {
+          int below, same;
+          warp_rank_count(L.rank, n, q.rankA, below, same);
+          bool full = same + 1 > P.cap;
+          if (r == R_SALT) {
+            int below2, same2;
+            warp_rank_count(L.rank, n, q.rankB, below2, same2);
+            full = full || same2 + 1 + (q.rankB == q.rankA ? 1 : 0) > P.cap;
+          }
+          if (full || n + 2 > (in_smem ? S.dcs : P.dcap_glob)) {
+            accept = false;
+            if (lane == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
+          }
+        }
+        if (accept) {
+          flags |= CR_TRIAL_ACCEPTED;
+          if (r == R_ACID || r == R_BASE) {
+            const float qs = r == R_ACID ? -1.0f : 1.0f;
+            if (lane == 0) {
+              L.info[C.site] ^= INFO_ION_BIT;
+              L.pos[C.site].w = fwd ? qs : 0.0f;
+            }
+            __syncwarp();
+            if (fwd) {
+              int below, same;
+              warp_rank_count(L.rank, n, q.rankA, below, same);
+              const int p = below + same;
+              warp_insert_gap(L, n, p);
+              if (lane == 0) {
+                L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
+                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.id[p] = C.newid;
+                L.lnk[p] = 0;
+                L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
+                L.rank[p] = q.rankA;
+              }
+              n += 1;
+            } else {
+              warp_remove(L, n, C.ionA);
+              n -= 1;
+            }
+            if (lane == 0) {
+              const int kn = r == R_ACID ? K_A0 : K_B0, ki = kn + 1, kx = r == R_ACID ? K_XP : K_XM;
+              const int dlt = fwd ? 1 : -1;
+              misc[1 + kn] -= dlt;
+              misc[1 + ki] += dlt;
+              misc[1 + kx] += dlt;
+            }
+          } else {
+            if (fwd) {
+              int below, same;
+              warp_rank_count(L.rank, n, q.rankA, below, same);
+              int p = below + same;
+              warp_insert_gap(L, n, p);
+              if (lane == 0) {
+                L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
+                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.id[p] = C.newid;
+                L.lnk[p] = 0;
+                L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
+                L.rank[p] = q.rankA;
+              }
+              __syncwarp();
+              n += 1;
+              warp_rank_count(L.rank, n, q.rankB, below, same);
+              p = below + same;
+              warp_insert_gap(L, n, p);
+              if (lane == 0) {
+                L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
+                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.id[p] = C.newid + 1u;
+                L.lnk[p] = 0;
+                L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
+                L.rank[p] = q.rankB;
+              }
+              n += 1;
+            } else {
+              const int hi = max(C.ionA, C.ionB), lo = min(C.ionA, C.ionB);
+              warp_remove(L, n, hi);
+              n -= 1;
+              warp_remove(L, n, lo);
+              n -= 1;
+            }
+            if (lane == 0) {
+              const int dlt = fwd ? 1 : -1;
+              misc[1 + K_XP] += dlt;
+              misc[1 + K_XM] += dlt;
+            }
+          }
+          __syncwarp();
+        }
+        if (lane == 0) {
+          misc[0] = n;
+          st[C.move] += 1;
+          if (flags & CR_TRIAL_ACCEPTED) st[6 + C.move] += 1;
+          if (flags & CR_TRIAL_NO_ELIGIBLE) st[12] += 1;
+          if (flags & CR_TRIAL_EDGE) st[13] += 1;
+          if (flags & CR_TRIAL_OVERLAP) st[14] += 1;
+          st[15] += 1;
+          if (LOG && P.log) {
+            cr_trial rec;
+            rec.move = C.move;
+            rec.flags = flags;
+            rec.id_a = C.id_a;
+            rec.id_b = C.id_b;
+            rec.dE = dE;
+            rec.S = Ssum;
+            rec.lnA = lnA;
+            rec.lnu = q.lnu;
+            P.log[log_dom + kk] = rec;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- write the domain back (id-sorted cells) and publish counts
+  const int n = misc[0];
+  for (int r = tid; r < KC; r += T) {
+    int lo = 0, hi = n;  // first entry with rank >= r
+    while (lo < hi) { const int mid = (lo + hi) >> 1; if (L.rank[mid] < r) lo = mid + 1; else hi = mid; }
+    int lo2 = lo, hi2 = n;  // first entry with rank > r
+    while (lo2 < hi2) { const int mid = (lo2 + hi2) >> 1; if (L.rank[mid] <= r) lo2 = mid + 1; else hi2 = mid; }
+    dcnt[r] = lo;
+    const int lx = r % k, ly = (r / k) % k, lz = r / (k * k);
+    P.cnt[(org[0] + lx) % nc + nc * ((org[1] + ly) % nc + nc * ((org[2] + lz) % nc))] = lo2 - lo;
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += T) {
+    const int r = L.rank[j];
+    const int lx = r % k, ly = (r / k) % k, lz = r / (k * k);
+    const int cell = (org[0] + lx) % nc + nc * ((org[1] + ly) % nc + nc * ((org[2] + lz) % nc));
+    const int g = cell * P.cap + (j - dcnt[r]);
+    const unsigned long long id = L.id[j];
+    P.pos[g] = L.pos[j];
+    P.vel[g] = L.vel[j];
+    P.pid[g] = id;
+    P.info[g] = L.info[j];
+    if (id < (unsigned long long)P.n_perm) P.perm_slot[id] = g;
+  }
+  if (tid < 16 && st[tid]) atomicAdd(&P.stats[tid], st[tid]);
+  if (tid < 6 && misc[1 + tid] != misc[9 + tid])
+    atomicAdd((unsigned long long *)&P.counts[tid], (unsigned long long)(long long)(misc[1 + tid] - misc[9 + tid]));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t phase_smem_bytes(const PhaseShape &S) {
+  size_t b = (sizeof(SysParams) + 15) / 16 * 16;
+  b += (size_t)S.dcs * (2 * sizeof(float4) + sizeof(unsigned long long) + sizeof(long long) + 2 * sizeof(int));
+  b += sizeof(long long) * S.lns;
+  b += sizeof(TrialPre) * TRIAL_CHUNK;
+  b += (sizeof(TrialCtl) + 15) / 16 * 16;
+  b += (sizeof(long long) + sizeof(unsigned long long)) * MAX_WARPS + sizeof(unsigned long long) * 16;
+  b += sizeof(int) * MAX_WARPS + sizeof(int) * 32 + sizeof(int) * 16;
+  b += 3 * sizeof(int) * (S.nr3 + 1) + 2 * sizeof(int) * (S.kc3 + 1);
+  return b;
+}
+
+template <int T, int R, bool LOG>
+static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, cudaStream_t s,
+                                  uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0, uint32_t k1) {
+  static size_t attr_bytes = 0;
+  const size_t smem = phase_smem_bytes(S);
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_cr_phase<T, R, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  k_cr_phase<T, R, LOG><<<dim3(grid_x, n_rep), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
+  return cudaGetLastError();
+}
+
+// (threads per CTA, halo registers per thread) variants the autotuner picks from
+static const int kShapes[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+
+int phase_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+void phase_shape(int i, int *threads, int *regs) {
+  *threads = kShapes[i][0];
+  *regs = kShapes[i][1];
+}
+
+cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
+                         bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,
+                         uint32_t k1) {
+#define CRMC_CASE(TT, RR)                                                                                      \
+  if (threads == TT && R == RR)                                                                                \
+    return log ? launch_phase_t<TT, RR, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1)     \
+               : launch_phase_t<TT, RR, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
+  CRMC_CASE(128, 2)
+  CRMC_CASE(128, 4)
+  CRMC_CASE(128, 8)
+  CRMC_CASE(256, 1)
+  CRMC_CASE(256, 2)
+  CRMC_CASE(256, 4)
+  CRMC_CASE(512, 1)
+  CRMC_CASE(512, 2)
+#undef CRMC_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace crmc

@@ -235,3 +235,30 @@ def test_md_step_and_interleaved_cycles(crmc):
         o.set_positions(sg["id"], sg["xyz"], sg["vel"])
     g.md_step(20, 0.005, 1.0, 78)
     g.check()
+
+
+@pytest.mark.parametrize("threads,regs", [(128, 2), (128, 8), (256, 1), (256, 4), (512, 1), (512, 2)])
+def test_launch_shape_does_not_change_the_chain(crmc, threads, regs):
+    """Every (threads, halo registers) shape the autotuner may pick gives the
+    oracle's chain; (128, 2) also exercises the halo overflow path (halo of
+    ~400 particles > 256 register slots)."""
+    w = W.config2(seed=2, scale=0.5)
+    g = crmc.Context(w)
+    g.set_launch_shape(threads, regs)
+    assert g.launch_shape() == (threads, regs)
+    n = g.trials_per_sweep * 3
+    lg = g.sweep(n, 3, log=True)["log"]
+    o, lo, ties = compare_logs(w, lg, n, 3)
+    compare_states(g, o, w.n_sites)
+
+
+def test_autotuner_keeps_the_chain(crmc):
+    """Unlogged sweeps used for tuning (one shape per sweep) continue the same chain."""
+    w = W.config2(seed=3, scale=0.5)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    n = g.trials_per_sweep * 10
+    g.sweep(n, 5)
+    o.sweep(n, 5)
+    compare_states(g, o, w.n_sites)
+    assert g.launch_shape()[0] in (128, 256, 512)
