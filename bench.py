@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the CR-MC hot path on GB300 (prints one JSON line).
 
-Workload: the polyelectrolyte solution of the paper's method at the size the
-metric is quoted on -- 16 chains x 200 acid beads (pKa 4.5, pH 4.5), L = 120
-sigma, ~4000 ion pairs, r_c = 12 sigma, l_B = 2 sigma -- with synthetic,
-seeded coordinates.  One step = one MD/CR-MC cycle: 10^4 CR-MC trials (one
-sweep of 1000 domains x 10 trials) + one velocity-Verlet/Langevin MD step
-(dt = 0.005, gamma = 1); the full job is 100 steps (10^6 trials).  Inputs
-are resident in HBM; L2 is flushed (256 MB write) between timed steps.
+Workload: the polyelectrolyte solution the metric is quoted on -- 16 chains x
+200 acid beads (pKa 4.5), L = 120 sigma, ~4000 ion pairs, r_c = 12 sigma,
+l_B = 2 sigma -- titrated at pH 2.0, 2.5, ..., 8.0: 13 replicas advanced as one
+batch (one phase launch per colour covers all of them), synthetic seeded
+coordinates.  One step = one MD/CR-MC cycle of every replica: 10^4 CR-MC trials
+(one sweep of 1000 domains x 10 trials) + one velocity-Verlet/Langevin MD step
+(dt = 0.005, gamma = 1); the full job is 100 steps (10^6 trials per replica).
+The single-replica (pH 4.5) plain path is reported beside it.  Inputs are
+resident in HBM; L2 is flushed (256 MB write) between timed steps.
 
 --impl reference times the CPU oracle on the same workload (rank 0 only).
 Under torchrun each rank runs an independent replica (no collective on the
@@ -30,8 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CR-MC trials/s on 1 GB300 (plain vs surrogate-DA/batched) at |Δα|≤0.005"
-WORKLOAD = ("polyelectrolyte solution: 16 chains x 200 acid beads (pKa 4.5), pH 4.5, L=120 sigma, ~4000 ion pairs, "
-            "rc=12, lB=2, DSF alpha=0.2; step = 1e4 CR-MC trials (1000 domains x 10) + 1 MD step (dt 0.005, gamma 1)")
+WORKLOAD = ("polyelectrolyte solution, pH swept 2..8 in steps of 0.5 (13 replicas in one batch): 16 chains x 200 "
+            "acid beads (pKa 4.5), L=120 sigma, ~4000 ion pairs, rc=12, lB=2, DSF alpha=0.2; step = 1e4 CR-MC trials "
+            "per replica (1000 domains x 10) + 1 MD step (dt 0.005, gamma 1) per replica")
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -196,6 +199,34 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def ph_sweep_workloads(rank):
+    """The polyelectrolyte solution at pH 2.0, 2.5, ..., 8.0 (13 replicas of
+    the same seeded starting structure)."""
+    import copy
+    base = workload(rank)
+    out = []
+    for i in range(13):
+        w = copy.copy(base)
+        w.params = dict(base.params)
+        w.params["pH"] = 2.0 + 0.5 * i
+        out.append(w)
+    return out
+
+
+def time_steps(step_fn, steps, stream, flush):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        starts[s].record(stream)
+        step_fn(s)
+        ends[s].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    return sum(starts[s].elapsed_time(ends[s]) for s in range(steps))
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -205,113 +236,143 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2109_07527_gb300 import crmc
 
-    w = workload(rank)
-    g = crmc.Context(w)
-    info = g.info
-    per_step = g.trials_per_sweep
     dt, gamma = 0.005, 1.0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peak()
 
-    # launch-shape tuning: the first unlogged sweeps time each supported shape once
-    g.sweep(per_step * 8, 0xABC)
+    # ---- batched pH sweep (the timed workload)
+    ws = ph_sweep_workloads(rank)
+    ctxs = [crmc.Context(w) for w in ws]
+    batch = crmc.Batch(ctxs)
+    per_rep = ctxs[0].trials_per_sweep
+    per_step = per_rep * len(ctxs)
+    batch.sweep(8, 0xABC)  # launch-shape tuning (one shape per sweep)
     for s in range(args.warmup):
-        g.sweep(per_step, 1 + s)
-        g.md_step(1, dt, gamma, 1000 + s)
-    g.check()
-    torch.cuda.synchronize()
+        batch.sweep(1, 1 + s)
+        batch.md_step(1, dt, gamma, 1000 + s)
+    for g in ctxs:
+        g.check()
     if world > 1:
         torch.distributed.barrier()
+    g0 = ctxs[0]
     clocks = ClockSampler()
     clocks.start()
-    g.set_timing(True)
-    g.timing(reset=True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        starts[s].record(stream)
-        g.sweep(per_step, 100 + s)
-        g.md_step(1, dt, gamma, 5000 + s)
-        ends[s].record(stream)
-        flush.zero_()
-    torch.cuda.synchronize()
+    g0.set_timing(True)
+    g0.timing(reset=True)
+
+    def step(s):
+        batch.sweep(1, 100 + s)
+        batch.md_step(1, dt, gamma, 5000 + s)
+
+    ms = time_steps(step, args.steps, stream, flush)
     if world > 1:
         torch.distributed.barrier()
     cl = clocks.stop(local)
-    tm = g.timing(reset=True)
-    g.set_timing(False)
-    g.check()
-    ms = sum(starts[s].elapsed_time(ends[s]) for s in range(args.steps))
+    tm = g0.timing(reset=True)
+    g0.set_timing(False)
+    for g in ctxs:
+        g.check()
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    counts = g.counts()
-    total_trials = per_step * args.steps * world
-    value = total_trials / (ms / 1e3)
-
-    # roofline of the colour-phase kernel (the dominant kernel)
-    L = float(w.params["box_L"])
-    bpt = bytes_per_trial(L, float(w.params["rc"]), counts["n"])
-    trials_per_launch = per_step / 8
+    value = per_step * args.steps * world / (ms / 1e3)
+    counts = [g.counts() for g in ctxs]
+    L = float(ws[0].params["box_L"])
+    rc = float(ws[0].params["rc"])
+    info = g0.info
+    launches_per_step = info["ncol"]
+    trials_per_launch = per_rep / launches_per_step
+    bytes_launch = sum(trials_per_launch * bytes_per_trial(L, rc, c["n"]) for c in counts)
     avg_launch_s = tm["phase_ms"] / max(tm["phase_launches"], 1) / 1e3
-    achieved = bpt * trials_per_launch / avg_launch_s / 1e9
-    peak, peak_kind = measured_peak()
+    achieved = bytes_launch / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "k_cr_phase", "peak_source": peak_kind,
-                "bytes_per_trial": bpt, "trials_per_launch": trials_per_launch,
-                "avg_launch_us": avg_launch_s * 1e6, "phase_share_of_step": tm["phase_ms"] / ms,
-                "md_force_ms_per_step": tm["md_ms"] / args.steps}
+                "traffic": profiled_traffic(), "kernel": "k_cr_phase (13 replicas per launch)",
+                "peak_source": peak_kind, "bytes_per_trial_mean": bytes_launch / (trials_per_launch * len(ctxs)),
+                "trials_per_launch": trials_per_launch * len(ctxs), "avg_launch_us": avg_launch_s * 1e6,
+                "phase_share_of_step": tm["phase_ms"] / ms}
 
-    # end to end through the public API with host buffers: each step uploads
-    # the configuration from pinned host memory (cr_load), runs the cycle and
-    # reads the full state back (cr_state)
+    # ---- plain path: one replica (pH 4.5), same step definition
+    plain = None
+    if rank == 0:
+        w1 = workload(rank)
+        g1 = crmc.Context(w1)
+        g1.sweep(g1.trials_per_sweep * 8, 0xABC)
+        for s in range(3):
+            g1.sweep(g1.trials_per_sweep, 1 + s)
+            g1.md_step(1, dt, gamma, 1000 + s)
+        g1.set_timing(True)
+        g1.timing(reset=True)
+        n_plain = max(10, min(args.steps, 50))
+
+        def step1(s):
+            g1.sweep(g1.trials_per_sweep, 300 + s)
+            g1.md_step(1, dt, gamma, 7000 + s)
+
+        ms1 = time_steps(step1, n_plain, stream, flush)
+        tm1 = g1.timing(reset=True)
+        g1.check()
+        c1 = g1.counts()
+        al = tm1["phase_ms"] / max(tm1["phase_launches"], 1) / 1e3
+        ach1 = trials_per_launch * bytes_per_trial(L, rc, c1["n"]) / al / 1e9
+        plain = {"value": g1.trials_per_sweep * n_plain / (ms1 / 1e3), "unit": "trials/s", "steps": n_plain,
+                 "ms_per_step": ms1 / n_plain, "launch_shape": list(g1.launch_shape()),
+                 "roofline": {"achieved": ach1, "frac": ach1 / peak, "avg_launch_us": al * 1e6},
+                 "md_force_ms_per_step": tm1["md_ms"] / n_plain, "alpha_end": c1["alpha"]}
+        g1.close()
+
+    # ---- end to end through the public API with host buffers: each step
+    # uploads every replica's configuration from pinned host memory (cr_load),
+    # runs the batched cycle and reads every replica's state back (cr_state)
     e2e = None
     if not args.no_e2e and rank == 0:
-        st = g.state()
-        n = int(st["n"])
-        cls0 = np.ascontiguousarray(w.cls, np.int32)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        hx, hv, ht, hs = pin(st["xyz"]), pin(st["vel"]), pin(st["type"]), pin(st["state"])
-        ion = (st["type"] == 3) | (st["type"] == 4)
-        hc = pin(np.where(ion, 0, cls0[np.minimum(st["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32))
-        e2e_steps = max(3, min(args.steps, 20))
+        cls0 = np.ascontiguousarray(ws[0].cls, np.int32)
+
+        def host_state(st):
+            ion = (st["type"] == 3) | (st["type"] == 4)
+            cl = np.where(ion, 0, cls0[np.minimum(st["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32)
+            return (int(st["n"]), pin(st["xyz"]), pin(st["vel"]), pin(st["type"]), pin(cl), pin(st["state"]))
+
+        hs = [host_state(g.state()) for g in ctxs]
+        e2e_steps = 5
         h2d = d2h = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(e2e_steps):
-            g.load(n, hx.data_ptr(), hv.data_ptr(), ht.data_ptr(), hc.data_ptr(), hs.data_ptr())
-            h2d += n * (12 + 12 + 4 + 4 + 1)
-            g.sweep(per_step, 9000 + s)
-            g.md_step(1, dt, gamma, 9500 + s)
-            out = g.state()
-            d2h += int(out["n"]) * (16 + 16 + 8 + 4) + 64
-            n = int(out["n"])
-            ion = (out["type"] == 3) | (out["type"] == 4)
-            hx, hv, ht, hs = pin(out["xyz"]), pin(out["vel"]), pin(out["type"]), pin(out["state"])
-            hc = pin(np.where(ion, 0, cls0[np.minimum(out["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32))
+            for g, (n, hx, hv, ht, hc, hst) in zip(ctxs, hs):
+                g.load(n, hx.data_ptr(), hv.data_ptr(), ht.data_ptr(), hc.data_ptr(), hst.data_ptr())
+                h2d += n * (12 + 12 + 4 + 4 + 1)
+            batch.sweep(1, 9000 + s)
+            batch.md_step(1, dt, gamma, 9500 + s)
+            outs = [g.state() for g in ctxs]
+            d2h += sum(int(o["n"]) * (16 + 16 + 8 + 4) + 64 for o in outs)
+            hs = [host_state(o) for o in outs]
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
-               "note": "per step: cr_load from pinned host buffers + 1e4 trials + 1 MD step + cr_state readback"}
+               "note": "per step: cr_load of the 13 replicas from pinned host buffers + batched 1e4 trials per "
+                       "replica + batched MD step + cr_state readback of every replica"}
 
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 pair terms / i64 fixed-point sums / f64 Metropolis",
+           "vs_baseline": None, "dtype": "f32 pair terms / i64 fixed-point sums and exponent / f64 near ties",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "flushed (256 MB write) between timed steps",
-                      "trials_per_step": per_step, "md_steps_per_step": 1, "domains": info["nd"] ** 3,
-                      "cell_side": info["cell_side"], "launch_shape": list(g.launch_shape()),
-                      "alpha_end": counts["alpha"], "particles_end": counts["n"],
-                      "parallelism": f"{world} independent replica(s)"},
-           "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e,
+           "config": {"workload": WORKLOAD, "replicas": len(ctxs), "pH": [w.params["pH"] for w in ws],
+                      "l2": "flushed (256 MB write) between timed steps", "trials_per_step": per_step,
+                      "md_steps_per_step": 1, "domains_per_replica": info["nd"] ** 3,
+                      "cell_side": info["cell_side"], "launch_shape": list(batch.launch_shape()),
+                      "alpha_end": [round(c["alpha"], 4) for c in counts],
+                      "particles_end": [c["n"] for c in counts],
+                      "parallelism": f"{world} GPU(s), independent replica batches"},
+           "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e, "plain": plain,
            "md_cr_cycles_per_s": args.steps * world / (ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w)
+        out["cpu_baseline"] = cpu_baseline(workload(0))
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -228,6 +228,23 @@ int cr_check(cr_ctx *ctx);
 void cr_destroy(cr_ctx *ctx);
 const char *cr_strerror(int code);
 
+/* ---- batches of independent replicas (e.g. the points of a pH sweep) ----
+ * A batch advances n contexts together: one colour-phase launch per colour
+ * covers every domain of every replica.  Replica r uses the Philox key
+ * (seed_lo, seed_hi ^ r), so its chain equals cr_sweep on that context alone
+ * with seed ^ (r << 32).  The contexts stay owned by the caller, must outlive
+ * the batch, share one stream and sweep counter (e.g. freshly created) and
+ * the same schedule kind; their counts, states and errors are read per
+ * context (cr_state, cr_check). */
+typedef struct cr_batch cr_batch;
+int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n);
+/* n_sweeps sweeps on every replica (each replica runs its own trials per sweep). */
+int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed);
+/* cr_md_step on every replica, concurrently (replica r uses seed ^ (r << 32)). */
+int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed);
+int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);
+void cr_batch_destroy(cr_batch *b);
+
 /* Philox4x32-10 on the device for n consecutive counters (c0 + i, c1, c2, c3),
  * key (k0, k1); out: host array of 4n words.  Exposed for parity tests. */
 int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,

@@ -72,7 +72,8 @@ TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id
 # every entry point of include/crmc.h
 EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
            "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
-           "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape")
+           "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape", "cr_batch_create", "cr_batch_sweep",
+           "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy")
 
 _L = None
 
@@ -116,6 +117,16 @@ def _lib():
         lib.cr_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
         lib.cr_get_launch_shape.restype = C.c_int
         lib.cr_get_launch_shape.argtypes = [P, P, P]
+        lib.cr_batch_create.restype = C.c_int
+        lib.cr_batch_create.argtypes = [C.POINTER(P), P, C.c_int32]
+        lib.cr_batch_sweep.restype = C.c_int
+        lib.cr_batch_sweep.argtypes = [P, C.c_uint64, C.c_uint64]
+        lib.cr_batch_md_step.restype = C.c_int
+        lib.cr_batch_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        lib.cr_batch_get_launch_shape.restype = C.c_int
+        lib.cr_batch_get_launch_shape.argtypes = [P, P, P]
+        lib.cr_batch_destroy.restype = None
+        lib.cr_batch_destroy.argtypes = [P]
         lib.cr_philox.restype = C.c_int
         lib.cr_philox.argtypes = [C.c_uint32] * 6 + [C.c_int32, P]
         _L = lib
@@ -277,3 +288,35 @@ class Context:
         arr["site_state"] = arr["site_state"][: self.n_sites]
         c.update(arr)
         return c
+
+
+class Batch:
+    """Independent replicas advanced together (one phase launch per colour)."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = C.c_void_p()
+        _chk(_lib().cr_batch_create(C.byref(h), arr, len(self.contexts)), "cr_batch_create")
+        self._h = h
+        self._lib = _lib()
+
+    def sweep(self, n_sweeps, seed):
+        _chk(self._lib.cr_batch_sweep(self._h, int(n_sweeps), int(seed)), "cr_batch_sweep")
+
+    def md_step(self, n_steps, dt, gamma, seed):
+        _chk(self._lib.cr_batch_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_batch_md_step")
+
+    def launch_shape(self):
+        t = C.c_int32()
+        r = C.c_int32()
+        _chk(self._lib.cr_batch_get_launch_shape(self._h, C.byref(t), C.byref(r)), "cr_batch_get_launch_shape")
+        return t.value, r.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

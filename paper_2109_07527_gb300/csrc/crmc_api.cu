@@ -968,3 +968,160 @@ extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t 
   *regs = ctx->R;
   return CR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batches of replicas: one phase launch per colour for all replicas
+// ---------------------------------------------------------------------------
+struct cr_batch {
+  std::vector<cr_ctx *> ctx;
+  SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
+  PhaseShape S{};
+  int grid_x = 0, ncol = 8;
+  int T = 128, R = 4;
+  bool tuning = true;
+  int tune_next = 0;
+  float tune_ms[16] = {};
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaEvent_t fork = nullptr;
+};
+
+extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
+  if (!out || !ctxs || n <= 0) return CR_ERR_INVALID_ARG;
+  *out = nullptr;
+  cr_batch *b = new (std::nothrow) cr_batch();
+  if (!b) return CR_ERR_NOMEM;
+  b->ctx.assign(ctxs, ctxs + n);
+  std::vector<SysParams> reps(n);
+  int maxR = 1;
+  for (int r = 0; r < n; ++r) {
+    cr_ctx *c = ctxs[r];
+    if (!c || c->P.ncol != ctxs[0]->P.ncol || c->sweep != ctxs[0]->sweep || c->stream != ctxs[0]->stream) {
+      delete b;
+      return CR_ERR_INVALID_ARG;
+    }
+    reps[r] = c->P;
+    reps[r].key_xor = (uint32_t)r;
+    reps[r].log = nullptr;
+    b->S.dcs = std::max(b->S.dcs, c->S.dcs);
+    b->S.lns = std::max(b->S.lns, c->S.lns);
+    b->S.nr3 = std::max(b->S.nr3, c->S.nr3);
+    b->S.kc3 = std::max(b->S.kc3, c->S.kc3);
+    b->grid_x = std::max(b->grid_x, c->P.nact);
+    maxR = std::max(maxR, c->R);
+  }
+  b->ncol = ctxs[0]->P.ncol;
+  b->R = std::min(maxR, 8);
+  b->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctxs[0]->device);
+  if (phase_smem_bytes(b->S) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
+  if (cudaMalloc((void **)&b->d_reps, sizeof(SysParams) * n) != cudaSuccess) { delete b; return CR_ERR_NOMEM; }
+  if (cudaMemcpy(b->d_reps, reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(b->d_reps);
+    delete b;
+    return CR_ERR_CUDA;
+  }
+  b->streams.resize(n);
+  b->events.resize(n);
+  for (int r = 0; r < n; ++r) {
+    cudaStreamCreateWithFlags(&b->streams[r], cudaStreamNonBlocking);
+    cudaEventCreateWithFlags(&b->events[r], cudaEventDisableTiming);
+  }
+  cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  *out = b;
+  return CR_OK;
+}
+
+extern "C" void cr_batch_destroy(cr_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->ctx[0]->stream);
+  for (size_t r = 0; r < b->streams.size(); ++r) {
+    cudaStreamSynchronize(b->streams[r]);
+    cudaStreamDestroy(b->streams[r]);
+    cudaEventDestroy(b->events[r]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->d_reps) cudaFree(b->d_reps);
+  delete b;
+}
+
+extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
+  if (!b || n_sweeps == 0) return CR_ERR_INVALID_ARG;
+  cr_ctx *c0 = b->ctx[0];
+  cudaStream_t s = c0->stream;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int n = (int)b->ctx.size();
+  const uint32_t sweep0 = (uint32_t)c0->sweep;
+  for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
+    const uint32_t swc = (uint32_t)c0->sweep;
+    for (cr_ctx *c : b->ctx) {
+      c->sweep++;
+      c->f_valid = false;
+      c->fcons_valid = false;
+    }
+    const bool tune = b->tuning && b->tune_next < phase_shape_count();
+    int T = b->T, R = b->R;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (tune) {
+      phase_shape(b->tune_next, &T, &R);
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+    }
+    for (int col = 0; col < b->ncol; ++col) {
+      int ti;
+      tbegin(c0, 0, &ti);
+      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, b->S, T, R, false, s, swc, sweep0, col, k0, k1));
+      tend(c0, 0, ti);
+      c0->launches_total++;
+    }
+    if (tune) {
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      b->tune_ms[b->tune_next++] = ms;
+      if (b->tune_next == phase_shape_count()) {
+        int best = 0;
+        for (int i = 1; i < phase_shape_count(); ++i)
+          if (b->tune_ms[i] < b->tune_ms[best]) best = i;
+        phase_shape(best, &b->T, &b->R);
+        b->tuning = false;
+      }
+    }
+  }
+  return CR_OK;
+}
+
+extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+  if (!b) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = b->ctx[0]->stream;
+  CR_CUDA(cudaEventRecord(b->fork, s));
+  int rc = CR_OK;
+  for (size_t r = 0; r < b->ctx.size(); ++r) {
+    cr_ctx *c = b->ctx[r];
+    CR_CUDA(cudaStreamWaitEvent(b->streams[r], b->fork, 0));
+    c->stream = b->streams[r];
+    const bool timing = c->timing;
+    c->timing = false;
+    const int e = cr_md_step(c, n_steps, dt, gamma, seed ^ ((uint64_t)r << 32));
+    c->timing = timing;
+    c->stream = s;
+    if (e != CR_OK && rc == CR_OK) rc = e;
+    CR_CUDA(cudaEventRecord(b->events[r], b->streams[r]));
+    CR_CUDA(cudaStreamWaitEvent(s, b->events[r], 0));
+    b->ctx[0]->launches_total += (r > 0) ? c->launches_total : 0;
+    if (r > 0) c->launches_total = 0;
+  }
+  return rc;
+}
+
+extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs) {
+  if (!b || !threads || !regs) return CR_ERR_INVALID_ARG;
+  *threads = b->T;
+  *regs = b->R;
+  return CR_OK;
+}

@@ -62,6 +62,12 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out) {
   for (int s = 0; s < n; ++s) plist[o + s] = c * P.cap + s;
 }
 
+__device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+
+// NB = 2h+1 neighbour cells per dimension as a compile-time constant (rows of
+// NB cells along x, rows spread over the 8 lanes of a group); NB = 0 is the
+// generic form used when the box has fewer than 2h+1 cells per dimension
+template <int NB>
 __global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int pi_idx = gt / MD_GROUP, sub = gt % MD_GROUP;
@@ -77,23 +83,27 @@ __global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
     const int ci = (P.info[gi] >> INFO_CLS_SHIFT) & 3;
     const int cell = gi / cap;
     const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
-    // neighbour cells along each dimension: cx-h..cx+h, or every cell when
-    // the box has fewer than 2h+1 cells (no cell visited twice)
-    const int nb = min(2 * h + 1, nc);
-    const int nb3 = nb * nb * nb;
-    for (int o = sub; o < nb3; o += MD_GROUP) {
-      const int ox = o % nb, oy = (o / nb) % nb, oz = o / (nb * nb);
-      const int jx = nb == nc ? ox : (cx + ox - h + nc) % nc;
-      const int jy = nb == nc ? oy : (cy + oy - h + nc) % nc;
-      const int jz = nb == nc ? oz : (cz + oz - h + nc) % nc;
-      const int jc = jx + nc * (jy + nc * jz);
-      const int cnt = P.cnt[jc];
-      for (int s = 0; s < cnt; ++s) {
-        const int gj = jc * cap + s;
-        if (gj == gi) continue;
-        const float4 pj = P.pos[gj];
-        force_pair(P, pi.x, pi.y, pi.z, pi.w, ci, pj.x, pj.y, pj.z, pj.w, (P.info[gj] >> INFO_CLS_SHIFT) & 3, fx, fy,
-                   fz);
+    const int nb = NB > 0 ? NB : min(2 * h + 1, nc);
+    const bool all = NB == 0 && nb == nc;  // every cell of the dimension, once
+    for (int row = sub; row < nb * nb; row += MD_GROUP) {
+      const int oy = row % nb, oz = row / nb;
+      const int jy = all ? oy : wrap_cell(cy + oy - h, nc);
+      const int jz = all ? oz : wrap_cell(cz + oz - h, nc);
+      const int base = nc * (jy + nc * jz);
+#pragma unroll
+      for (int ox = 0; ox < (NB > 0 ? NB : 1); ++ox) {
+        for (int ox2 = (NB > 0 ? ox : 0); ox2 < (NB > 0 ? ox + 1 : nb); ++ox2) {
+          const int jx = all ? ox2 : wrap_cell(cx + ox2 - h, nc);
+          const int jc = base + jx;
+          const int cnt = P.cnt[jc];
+          for (int s = 0; s < cnt; ++s) {
+            const int gj = jc * cap + s;
+            if (gj == gi) continue;
+            const float4 pj = P.pos[gj];
+            force_pair(P, pi.x, pi.y, pi.z, pi.w, ci, pj.x, pj.y, pj.z, pj.w, (P.info[gj] >> INFO_CLS_SHIFT) & 3,
+                       fx, fy, fz);
+          }
+        }
       }
     }
   }
@@ -295,7 +305,10 @@ cudaError_t launch_plist(const SysParams &P, int *plist, int *n_out, cudaStream_
 
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int max_particles, cudaStream_t s) {
   const long long threads = (long long)max_particles * MD_GROUP;
-  k_md_forces<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, M);
+  const unsigned grid = (unsigned)((threads + 255) / 256);
+  if (P.h == 2 && P.nc >= 5) k_md_forces<5><<<grid, 256, 0, s>>>(P, M);
+  else if (P.h == 1 && P.nc >= 3) k_md_forces<3><<<grid, 256, 0, s>>>(P, M);
+  else k_md_forces<0><<<grid, 256, 0, s>>>(P, M);
   return cudaGetLastError();
 }
 

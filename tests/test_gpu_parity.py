@@ -262,3 +262,39 @@ def test_autotuner_keeps_the_chain(crmc):
     o.sweep(n, 5)
     compare_states(g, o, w.n_sites)
     assert g.launch_shape()[0] in (128, 256, 512)
+
+
+# ------------------------------------------------------------------ batches of replicas
+def _replica_seed(seed, r):
+    return seed ^ (r << 32)
+
+
+def test_batch_matches_independent_oracle_runs(crmc):
+    """A batch of replicas (different pH, different box sizes) advanced by
+    one launch per colour equals, replica by replica, the oracle run with the
+    replica's key."""
+    ws = [W.config2(seed=5, scale=0.5, pH=pH) for pH in (3.0, 4.5, 6.0)]
+    ws += W.config4(seed=2, n_rep=2, hi=300)
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(4, 77)
+    for r, (w, g) in enumerate(zip(ws, ctxs)):
+        o = oracle.Oracle(w)
+        o.sweep(o.trials_per_sweep * 4, _replica_seed(77, r))
+        compare_states(g, o, w.n_sites)
+
+
+def test_batch_md_equals_per_context_md(crmc):
+    ws = [W.config2(seed=7, scale=0.5, pH=pH) for pH in (3.0, 5.0)]
+    a = [crmc.Context(w) for w in ws]
+    c = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(a)
+    b.sweep(2, 9)
+    b.md_step(3, 0.005, 1.0, 11)
+    for r, g in enumerate(c):
+        g.sweep(g.trials_per_sweep * 2, _replica_seed(9, r))
+        g.md_step(3, 0.005, 1.0, _replica_seed(11, r))
+    for x, y in zip(a, c):
+        sx, sy = x.state(), y.state()
+        assert np.array_equal(sx["id"], sy["id"])
+        assert np.array_equal(sx["xyz"], sy["xyz"]) and np.array_equal(sx["vel"], sy["vel"])
