@@ -30,6 +30,7 @@ struct cr_ctx {
   // the phase kernel, chosen by timing real sweeps (the chain does not depend
   // on it: the energy sums are exact fixed point)
   int T = 128, R = 4;
+  int smem_max = 0;
   int tune_next = 0;     // next candidate to time; >= count when done
   bool tuning = true;
   float tune_ms[16] = {};
@@ -453,11 +454,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   }
   {
     // starting shape before tuning: 128 threads, enough registers for the densest halo
-    const int want = (int)std::ceil(1.25 * maxh / 128.0);
-    int R = 2;
-    while (R < want && R < 8) R *= 2;
     c->T = 128;
-    c->R = R;
+    c->R = 0;  // halo in shared memory until the tuner has timed the shapes
     c->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
   }
   P.lnmax = std::max(2 * k * k * k * cap, (int)std::min<long long>((long long)sys->capacity, 1 << 20)) + 2 * P.m + 4;
@@ -470,12 +468,15 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   S.nr3 = P.nr * P.nr * P.nr;
   S.kc3 = k * k * k;
   S.dcs = std::min(P.dcap_glob, std::max(2 * maxd, maxd + 32) + 2 * P.m);
+  S.hcs = std::min(maxh + maxh / 4 + 32, 4096);
   S.lns = std::min(P.lnmax, S.dcs + 4);
-  while (phase_smem_bytes(S) > (size_t)smem_max / 2 && S.dcs > 64) {
+  while (phase_smem_bytes(S, 512) > (size_t)smem_max / 2 && S.dcs > 64) {
     S.dcs /= 2;
+    S.hcs = std::max(S.hcs / 2, 64);
     S.lns = std::min(P.lnmax, S.dcs + 4);
   }
-  if (phase_smem_bytes(S) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  if (phase_smem_bytes(S, 512) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  c->smem_max = smem_max;
   P.per_sweep = c->per_sweep;
   P.key_xor = 0u;
 
@@ -654,6 +655,13 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)ctx->sweep++;
     // online tuning: the first sweeps of unlogged calls time each launch shape once
+    // shapes whose shared memory does not fit are skipped
+    while (ctx->tuning && !log && ctx->tune_next < phase_shape_count()) {
+      int t_, r_;
+      phase_shape(ctx->tune_next, &t_, &r_);
+      if (phase_shape_smem(ctx->S, t_, r_) <= (size_t)ctx->smem_max) break;
+      ctx->tune_ms[ctx->tune_next++] = 1e30f;
+    }
     const bool tune = ctx->tuning && !log && ctx->tune_next < phase_shape_count();
     int T = ctx->T, R = ctx->R;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -678,6 +686,12 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       ctx->tune_ms[ctx->tune_next++] = ms;
+      while (ctx->tune_next < phase_shape_count()) {  // skip trailing shapes that do not fit
+        int t_, r_;
+        phase_shape(ctx->tune_next, &t_, &r_);
+        if (phase_shape_smem(ctx->S, t_, r_) <= (size_t)ctx->smem_max) break;
+        ctx->tune_ms[ctx->tune_next++] = 1e30f;
+      }
       if (ctx->tune_next == phase_shape_count()) {
         int best = 0;
         for (int i = 1; i < phase_shape_count(); ++i)
@@ -978,6 +992,7 @@ struct cr_batch {
   PhaseShape S{};
   int grid_x = 0, ncol = 8;
   int T = 128, R = 4;
+  int smem_max = 0;
   bool tuning = true;
   int tune_next = 0;
   float tune_ms[16] = {};
@@ -1004,6 +1019,7 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     reps[r].key_xor = (uint32_t)r;
     reps[r].log = nullptr;
     b->S.dcs = std::max(b->S.dcs, c->S.dcs);
+    b->S.hcs = std::max(b->S.hcs, c->S.hcs);
     b->S.lns = std::max(b->S.lns, c->S.lns);
     b->S.nr3 = std::max(b->S.nr3, c->S.nr3);
     b->S.kc3 = std::max(b->S.kc3, c->S.kc3);
@@ -1011,11 +1027,13 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     maxR = std::max(maxR, c->R);
   }
   b->ncol = ctxs[0]->P.ncol;
-  b->R = std::min(maxR, 8);
+  b->R = 0;
+  (void)maxR;
   b->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctxs[0]->device);
-  if (phase_smem_bytes(b->S) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
+  if (phase_smem_bytes(b->S, 512) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
+  b->smem_max = smem_max;
   if (cudaMalloc((void **)&b->d_reps, sizeof(SysParams) * n) != cudaSuccess) { delete b; return CR_ERR_NOMEM; }
   if (cudaMemcpy(b->d_reps, reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(b->d_reps);
@@ -1060,6 +1078,12 @@ extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
       c->f_valid = false;
       c->fcons_valid = false;
     }
+    while (b->tuning && b->tune_next < phase_shape_count()) {
+      int t_, r_;
+      phase_shape(b->tune_next, &t_, &r_);
+      if (phase_shape_smem(b->S, t_, r_) <= (size_t)b->smem_max) break;
+      b->tune_ms[b->tune_next++] = 1e30f;
+    }
     const bool tune = b->tuning && b->tune_next < phase_shape_count();
     int T = b->T, R = b->R;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1084,6 +1108,12 @@ extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       b->tune_ms[b->tune_next++] = ms;
+      while (b->tune_next < phase_shape_count()) {
+        int t_, r_;
+        phase_shape(b->tune_next, &t_, &r_);
+        if (phase_shape_smem(b->S, t_, r_) <= (size_t)b->smem_max) break;
+        b->tune_ms[b->tune_next++] = 1e30f;
+      }
       if (b->tune_next == phase_shape_count()) {
         int best = 0;
         for (int i = 1; i < phase_shape_count(); ++i)

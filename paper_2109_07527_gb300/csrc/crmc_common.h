@@ -93,6 +93,7 @@ struct SysParams {
 // the maximum over the replicas of a batch).
 struct PhaseShape {
   int dcs;     // domain-list entries held in shared memory
+  int hcs;     // halo particles held in shared memory (shapes without halo registers)
   int lns;     // log-table entries held in shared memory
   int nr3;     // region cells
   int kc3;     // domain cells

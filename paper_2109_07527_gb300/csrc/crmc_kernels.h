@@ -44,8 +44,9 @@ struct LoadBufs {
   int n, n_site_map;
 };
 
-size_t phase_smem_bytes(const PhaseShape &S);
+size_t phase_smem_bytes(const PhaseShape &S, int threads);
 int phase_shape_count();
+size_t phase_shape_smem(const PhaseShape &S, int threads, int regs);
 void phase_shape(int i, int *threads, int *regs);
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,

@@ -306,43 +306,171 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
   }
 }
 
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int QCAP = 64;  // per-warp queue of Coulomb pair terms
+
+// DSF Coulomb change of one queued pair: qp * phi(r), qp = lB dq_c q_j
+template <bool WITH_S>
+__device__ __forceinline__ void coul_eval(const PairK &K, float r2, float qp, long long &acc,
+                                          unsigned long long &sacc, int &ov) {
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
+  const float e = erfcf(K.alpha * r) * rinv;
+  const float du = qp * (e - K.c1 + K.c2 * (r - K.rcf));
+  if (!(fabsf(du) < BIG_TERM)) {
+    ov = 1;
+  } else {
+    acc += fix32(du);
+    if (WITH_S) sacc += (unsigned long long)fix32(fminf(fabsf(qp) * (e + K.c1 + K.c2 * fabsf(r - K.rcf)), BIG_TERM));
+  }
+}
+
+// Warp step of the pair sweep: every lane offers at most one in-range Coulomb
+// pair; the warp appends the offers to its queue and, once 32 are waiting,
+// evaluates them with all lanes busy (the cheap distance tests of the
+// out-of-range majority never diverge into the expensive path).
+template <bool WITH_S>
+__device__ __forceinline__ void q_push(float *qr2, float *qqp, int &qn, bool in, float r2, float qp, const PairK &K,
+                                       long long &acc, unsigned long long &sacc, int &ov) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(FULL, in);
+  if (m == 0u) return;
+  const int pos = qn + __popc(m & ((1u << lane) - 1u));
+  if (in) {
+    qr2[pos] = r2;
+    qqp[pos] = qp;
+  }
+  qn += __popc(m);
+  if (qn >= 32) {
+    __syncwarp();
+    coul_eval<WITH_S>(K, qr2[lane], qqp[lane], acc, sacc, ov);
+    const int rest = qn - 32;
+    float a = 0.f, b = 0.f;
+    if (lane < rest) {
+      a = qr2[32 + lane];
+      b = qqp[32 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      qr2[lane] = a;
+      qqp[lane] = b;
+    }
+    __syncwarp();
+    qn = rest;
+  }
+}
+
+// One changed particle c against one candidate j (lane-parallel).  Pairs
+// within the WCA range of an inserted / deleted c are evaluated at once,
+// Coulomb in FP32 and WCA in FP64 (rare); other Coulomb pairs go to the queue.
+template <bool WITH_S>
+__device__ __forceinline__ void offer(const PairK &K, const WcaEntry *wca, const Desc &c, bool valid, float xj, float yj,
+                                      float zj, float qj, int jcls, float *qr2, float *qqp, int &qn, long long &acc,
+                                      unsigned long long &sacc, int &ov) {
+  const float dx = wrap_diff(xj, c.x, K.Lf, K.halfL);
+  const float dy = wrap_diff(yj, c.y, K.Lf, K.halfL);
+  const float dz = wrap_diff(zj, c.z, K.Lf, K.halfL);
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  bool near = false;
+  if (c.dp != 0 && valid) {  // warp-uniform dp
+    const WcaEntry &w = wca[c.cls * 4 + jcls];
+    near = w.on && r2 < 1.0001f * w.wcut2;
+    if (near) {
+      float du = 0.0f, gs = 0.0f;
+      const bool any = r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
+      if (any) {
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float e = erfcf(K.alpha * r) * rinv;
+        du = c.dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
+        if (WITH_S) gs = fabsf(c.dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
+      }
+      const double2 res = wca_change_nl(w, c.dp, c.x, c.y, c.z, xj, yj, zj, K.Ld, K.halfLd);
+      if (res.y == -2.0) {
+        ov = 1;
+      } else if (res.y >= 0.0) {
+        if (!(fabs((double)du + res.x) < (double)BIG_TERM)) {
+          ov = 1;
+        } else {
+          if (any) acc += fix32(du);
+          acc += __double2ll_rn(res.x * (double)FIX_SCALE);
+          if (WITH_S)
+            sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + res.y, (double)BIG_TERM) * (double)FIX_SCALE);
+        }
+      } else if (any) {  // beyond the WCA cutoff after all: Coulomb only
+        if (!(fabsf(du) < BIG_TERM)) ov = 1;
+        else {
+          acc += fix32(du);
+          if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
+        }
+      }
+    }
+  }
+  const bool in = valid && !near && r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
+  q_push<WITH_S>(qr2, qqp, qn, in, r2, c.dqlB * qj, K, acc, sacc, ov);
+}
+
+template <int T>
+__device__ __forceinline__ void cta_sync() {
+  if (T == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// int64 sum over the warp, result in every lane
+__device__ __forceinline__ long long warp_allsum(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // the phase kernel
+//   T threads per domain (T == 32: one warp, no block barriers);
+//   R > 0: halo particles in R registers per thread, R == 0: in shared memory
 // ---------------------------------------------------------------------------
 template <int T, int R, bool LOG>
-__global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
+__global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
     k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
                uint32_t key0, uint32_t key1_base) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  constexpr int NW = T / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  // ---- shared memory carve-up (launch-wide shape)
+  // ---- shared memory carve-up (launch-wide shape); every array starts on
+  // a 16-byte boundary (phase_smem_bytes mirrors this order and padding)
   unsigned char *sp = smem;
-  SysParams &P = *(SysParams *)sp;
-  sp += (sizeof(SysParams) + 15) / 16 * 16;
+  auto take = [&](size_t bytes) {
+    unsigned char *p = sp;
+    sp += (bytes + 15) / 16 * 16;
+    return p;
+  };
+  SysParams &P = *(SysParams *)take(sizeof(SysParams));
   DomList Ls;
-  Ls.pos = (float4 *)sp; sp += sizeof(float4) * S.dcs;
-  Ls.vel = (float4 *)sp; sp += sizeof(float4) * S.dcs;
-  Ls.id = (unsigned long long *)sp; sp += sizeof(unsigned long long) * S.dcs;
-  Ls.lnk = (long long *)sp; sp += sizeof(long long) * S.dcs;
-  Ls.info = (int *)sp; sp += sizeof(int) * S.dcs;
-  Ls.rank = (int *)sp; sp += sizeof(int) * S.dcs;
-  long long *lntab_s = (long long *)sp; sp += sizeof(long long) * S.lns;
-  TrialPre *tp = (TrialPre *)sp; sp += sizeof(TrialPre) * TRIAL_CHUNK;
-  TrialCtl *ctl = (TrialCtl *)sp; sp += (sizeof(TrialCtl) + 15) / 16 * 16;
-  long long *red = (long long *)sp; sp += sizeof(long long) * MAX_WARPS;
-  unsigned long long *reds = (unsigned long long *)sp; sp += sizeof(unsigned long long) * MAX_WARPS;
-  unsigned long long *st = (unsigned long long *)sp; sp += sizeof(unsigned long long) * 16;
-  int *redov = (int *)sp; sp += sizeof(int) * MAX_WARPS;
-  int *scan_tmp = (int *)sp; sp += sizeof(int) * 32;
-  int *misc = (int *)sp; sp += sizeof(int) * 16;  // [0] list size, [1..7] kind counts, [9..15] at start, [8] flags
-  int *hcnt = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
-  int *hcell = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
-  int *hpre = (int *)sp; sp += sizeof(int) * (S.nr3 + 1);
-  int *dcnt = (int *)sp; sp += sizeof(int) * (S.kc3 + 1);
-  int *dpre = (int *)sp; sp += sizeof(int) * (S.kc3 + 1);
+  Ls.pos = (float4 *)take(sizeof(float4) * S.dcs);
+  Ls.vel = (float4 *)take(sizeof(float4) * S.dcs);
+  Ls.id = (unsigned long long *)take(sizeof(unsigned long long) * S.dcs);
+  Ls.lnk = (long long *)take(sizeof(long long) * S.dcs);
+  Ls.info = (int *)take(sizeof(int) * S.dcs);
+  Ls.rank = (int *)take(sizeof(int) * S.dcs);
+  float4 *hpos = (float4 *)take(sizeof(float4) * S.hcs);  // halo (R == 0): x, y, z, q + 8 cls
+  long long *lntab_s = (long long *)take(sizeof(long long) * S.lns);
+  TrialPre *tp = (TrialPre *)take(sizeof(TrialPre) * TRIAL_CHUNK);
+  TrialCtl *ctl = (TrialCtl *)take(sizeof(TrialCtl));
+  long long *red = (long long *)take(sizeof(long long) * MAX_WARPS);
+  unsigned long long *reds = (unsigned long long *)take(sizeof(unsigned long long) * MAX_WARPS);
+  unsigned long long *st = (unsigned long long *)take(sizeof(unsigned long long) * 16);
+  float *qbuf = (float *)take(sizeof(float) * 2 * QCAP * NW);
+  int *redov = (int *)take(sizeof(int) * MAX_WARPS);
+  int *scan_tmp = (int *)take(sizeof(int) * 32);
+  int *misc = (int *)take(sizeof(int) * 16);  // [0] list size, [1..7] kind counts, [9..15] at start
+  int *hcnt = (int *)take(sizeof(int) * (S.nr3 + 1));
+  int *hcell = (int *)take(sizeof(int) * (S.nr3 + 1));
+  int *hpre = (int *)take(sizeof(int) * (S.nr3 + 1));
+  int *dcnt = (int *)take(sizeof(int) * (S.kc3 + 1));
+  int *dpre = (int *)take(sizeof(int) * (S.kc3 + 1));
+  float *qr2 = qbuf + warp * 2 * QCAP, *qqp = qr2 + QCAP;
 
   {
     const int *src = (const int *)&reps[blockIdx.y];
@@ -383,7 +511,7 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
 #pragma unroll
   for (int i = 0; i < 3; ++i) org[i] = (off[i] + dd[i] * k) % nc;
 
-  // ---- cell counts of the domain and of its halo
+  // ---- cell counts of the domain and of its halo (cell indices kept)
   for (int r = tid; r < KC; r += T) {
     const int lx = r % k, ly = (r / k) % k, lz = r / (k * k);
     dcnt[r] = P.cnt[(org[0] + lx) % nc + nc * ((org[1] + ly) % nc + nc * ((org[2] + lz) % nc))];
@@ -411,7 +539,7 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
   const bool in_smem = ND + 2 * m <= S.dcs;
   DomList L = Ls;
   if (!in_smem) {
-    const size_t o = (size_t)blockIdx.x * P.dcap_glob;
+    const size_t o = (size_t)blockIdx.x * P.dcap_glob;  // this replica's scratch
     L.pos = P.gs_pos + o; L.vel = P.gs_vel + o; L.id = P.gs_id + o; L.lnk = P.gs_lnk + o;
     L.info = P.gs_info + o; L.rank = P.gs_rank + o;
     if (ND + 2 * m > P.dcap_glob) {  // cannot happen: a cell holds at most cap particles
@@ -439,26 +567,36 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
     L.rank[j] = r;
     atomicAdd(&misc[1 + min(kind_of(info), 6)], 1);
   }
-  // halo particles into registers: w = q + 8 * cls
-  float4 hreg[R];
+  // halo particles (they do not change during the phase): w = q + 8 * cls
+  constexpr int RR = R > 0 ? R : 1;
+  float4 hreg[RR];
   int nmine = 0;
+  const int hcap = R > 0 ? R * T : S.hcs;  // halo entries held on chip
+  if (R > 0) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int j = tid + r * T;
-    hreg[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < NH) {
+    for (int r = 0; r < RR; ++r) {
+      const int j = tid + r * T;
+      hreg[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < NH) {
+        const int i = upper_idx(hpre, NR, j);
+        const int g = hcell[i] * P.cap + (j - hpre[i]);
+        const float4 p = P.pos[g];
+        hreg[r] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
+        nmine = r + 1;
+      }
+    }
+  } else {
+    for (int j = tid; j < min(NH, hcap); j += T) {
       const int i = upper_idx(hpre, NR, j);
       const int g = hcell[i] * P.cap + (j - hpre[i]);
       const float4 p = P.pos[g];
-      const int cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
-      hreg[r] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)cls);
-      nmine = r + 1;
+      hpos[j] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
     }
   }
   if (tid == 0) misc[0] = ND;
   __syncthreads();
   if (tid < 7) misc[9 + tid] = misc[1 + tid];
-  const int cc_thread = nw > 1 ? 32 : 0;  // the thread that adds the changed-pair term
+  const int cc_thread = NW > 1 ? 32 : 0;  // the thread that adds the changed-pair term
   const long long log_dom = (long long)(sweep - sweep0) * P.per_sweep + (long long)colour * P.nact * m +
                             (long long)blockIdx.x * m;
 
@@ -504,7 +642,10 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
 
     for (int t = 0; t < nchunk; ++t) {
       const int kk = k0 + t;
-      // ---- warp 0: proposal and participants
+      // ---- warp 0: proposal and participants (kept in warp 0's registers)
+      int s_move = 0, s_flags = 0, s_site = -1, s_ionA = -1, s_ionB = -1, s_nch = 0;
+      long long s_ln_ratio = 0, s_dself = 0;
+      unsigned long long s_id_a = ~0ull, s_id_b = ~0ull, s_newid = 0ull;
       if (warp == 0) {
         const TrialPre q = tp[t];
         const int n = misc[0];
@@ -602,96 +743,123 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
           flags |= CR_TRIAL_NO_ELIGIBLE;
           if (lane == 0) atomicOr(P.err, ERRB_ARG);
         }
+        nch = (flags & (CR_TRIAL_NO_ELIGIBLE | CR_TRIAL_EDGE)) ? 0 : nch;
+        // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
+        const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
+                       (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
+        s_move = 2 * r + (fwd ? 0 : 1);
+        s_flags = flags;
+        s_site = site;
+        s_ionA = ionA;
+        s_ionB = ionB;
+        s_nch = nch;
+        s_ln_ratio = ln_ratio;
+        s_dself = P.lBself_fx * (long long)sq;
+        s_id_a = id_a;
+        s_id_b = id_b;
+        s_newid = newid;
         if (lane == 0) {
           TrialCtl &C = *ctl;
           C.c[0] = c0;
           C.c[1] = c1;
-          C.flags = flags;
-          C.nch = (flags & (CR_TRIAL_NO_ELIGIBLE | CR_TRIAL_EDGE)) ? 0 : nch;
-          C.move = 2 * r + (fwd ? 0 : 1);
-          C.site = site;
-          C.ionA = ionA;
-          C.ionB = ionB;
-          C.id_a = id_a;
-          C.id_b = id_b;
-          C.newid = newid;
-          C.ln_ratio_fx = ln_ratio;
+          C.nch = nch;
           C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
           C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
-          // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
-          const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
-                         (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
-          C.dself_fx = P.lBself_fx * (long long)sq;
         }
       }
-      __syncthreads();
+      cta_sync<T>();
       // ---- all threads: the pair-change sweep
       const int nch = ctl->nch;
+      long long acc = 0;
+      unsigned long long sacc = 0;
+      int ov = 0;
       if (nch) {
-        long long acc = 0;
-        unsigned long long sacc = 0;
-        int ov = 0;
         const Desc A = ctl->c[0], B = ctl->c[1];
+        int qn = 0;
+        if (R > 0) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (r < nmine) {
+          for (int r = 0; r < RR; ++r) {
             const float4 p = hreg[r];
             const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
             const float q = p.w - 8.0f * (float)cls;
-            pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, q, cls, acc, sacc, ov);
-            pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, q, cls, acc, sacc, ov);
+            const bool v = r < nmine;
+            offer<LOG>(K, wca, A, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+            offer<LOG>(K, wca, B, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+          }
+        } else {
+          const int lim = min(NH, hcap);
+          for (int base = 0; base < lim; base += T) {
+            const int j = base + tid;
+            const bool v = j < lim;
+            const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+            const float q = p.w - 8.0f * (float)cls;
+            offer<LOG>(K, wca, A, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+            offer<LOG>(K, wca, B, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
           }
         }
-        // halo beyond the registers (dense regions): straight from global memory
-        for (int j = R * T + tid; j < NH; j += T) {
-          const int i = upper_idx(hpre, NR, j);
-          const int g = hcell[i] * P.cap + (j - hpre[i]);
-          const float4 p = P.pos[g];
-          const int cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
-          pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
-          pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+        // halo beyond what is held on chip (dense regions): straight from global memory
+        for (int base = hcap; base < NH; base += T) {
+          const int j = base + tid;
+          const bool v = j < NH;
+          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+          int cls = 0;
+          if (v) {
+            const int i = upper_idx(hpre, NR, j);
+            const int g = hcell[i] * P.cap + (j - hpre[i]);
+            p = P.pos[g];
+            cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
+          }
+          offer<LOG>(K, wca, A, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+          offer<LOG>(K, wca, B, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
         }
         const int n = misc[0];
-        for (int j = tid; j < n; j += T) {
-          if (j == A.skip || j == B.skip) continue;
-          const float4 p = L.pos[j];
-          const int cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
-          pair_change<LOG>(K, wca, A.x, A.y, A.z, A.dqlB, A.dp, A.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
-          pair_change<LOG>(K, wca, B.x, B.y, B.z, B.dqlB, B.dp, B.cls, p.x, p.y, p.z, p.w, cls, acc, sacc, ov);
+        for (int base = 0; base < n; base += T) {
+          const int j = base + tid;
+          const bool v = j < n && j != A.skip && j != B.skip;
+          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+          int cls = 0;
+          if (j < n) {
+            p = L.pos[j];
+            cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
+          }
+          offer<LOG>(K, wca, A, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+          offer<LOG>(K, wca, B, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
         }
+        __syncwarp();
+        if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
         if (tid == cc_thread) cc_change(K, wca, *ctl, acc, sacc, ov);
-        acc = warp_sum(acc);
-        if (LOG) sacc = warp_sum(sacc);
-        ov = __any_sync(0xffffffffu, ov) ? 1 : 0;
-        if (lane == 0) {
+        acc = warp_allsum(acc);
+        if (LOG) sacc = (unsigned long long)warp_allsum((long long)sacc);
+        ov = __any_sync(FULL, ov) ? 1 : 0;
+        if (NW > 1 && lane == 0) {
           red[warp] = acc;
           reds[warp] = sacc;
           redov[warp] = ov;
         }
       }
-      __syncthreads();
+      if (NW > 1) __syncthreads();
       // ---- warp 0: decision and commit
       if (warp == 0) {
-        const TrialCtl &C = *ctl;
         const TrialPre &q = tp[t];
-        int flags = C.flags;
+        int flags = s_flags;
         bool accept = false;
         double dE = 0.0, Ssum = 0.0, lnA = -INFINITY;
-        if (C.nch) {
-          long long tot = 0;
-          unsigned long long stot = 0;
-          int anyov = 0;
-          for (int w = 0; w < nw; ++w) {
-            tot += red[w];
-            stot += reds[w];
-            anyov |= redov[w];
+        if (s_nch) {
+          long long tot = acc;
+          unsigned long long stot = sacc;
+          int anyov = ov;
+          if (NW > 1) {
+            tot = warp_allsum(lane < NW ? red[lane] : 0ll);
+            if (LOG) stot = (unsigned long long)warp_allsum(lane < NW ? (long long)reds[lane] : 0ll);
+            anyov = __any_sync(FULL, lane < NW && redov[lane]) ? 1 : 0;
           }
           if (anyov) {
             flags |= CR_TRIAL_OVERLAP;
             dE = INFINITY;
           } else {
             const long long totc = tot > DE_CLAMP32 ? DE_CLAMP32 : (tot < -DE_CLAMP32 ? -DE_CLAMP32 : tot);
-            const long long lnA_fx = C.ln_ratio_fx - ((totc << 16) + C.dself_fx);
+            const long long lnA_fx = s_ln_ratio - ((totc << 16) + s_dself);
             // FP32 ln u decides outside the band; inside it FP64 ln u does
             const long long lnu_apx = (long long)__float2int_rn(q.lnu_f * 16777216.0f) << 24;
             const long long diff = lnA_fx - lnu_apx;
@@ -699,20 +867,20 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
             else if (diff < -LNU_BAND) accept = false;
             else accept = __double2ll_rn(log(unif53(q.uhi, q.ulo)) * LNFIX) < lnA_fx;
             if (LOG) {
-              dE = (double)tot * FIX_INV + (double)C.dself_fx / LNFIX;
-              Ssum = (double)stot * FIX_INV + fabs((double)C.dself_fx / LNFIX);
-              lnA = (double)C.ln_ratio_fx / LNFIX - dE;  // unclamped, for the record
+              dE = (double)tot * FIX_INV + (double)s_dself / LNFIX;
+              Ssum = (double)stot * FIX_INV + fabs((double)s_dself / LNFIX);
+              lnA = (double)s_ln_ratio / LNFIX - dE;  // unclamped, for the record
             }
           }
         }
-        const int r = C.move >> 1;
-        const bool fwd = (C.move & 1) == 0;
+        const int r = s_move >> 1;
+        const bool fwd = (s_move & 1) == 0;
         int n = misc[0];
         // cell capacity for insertions (checked before committing anything)
+        int belowA = 0, sameA = 0;
         if (accept && fwd) {
-          int below, same;
-          warp_rank_count(L.rank, n, q.rankA, below, same);
-          bool full = same + 1 > P.cap;
+          warp_rank_count(L.rank, n, q.rankA, belowA, sameA);
+          bool full = sameA + 1 > P.cap;
           if (r == R_SALT) {
             int below2, same2;
             warp_rank_count(L.rank, n, q.rankB, below2, same2);
@@ -728,26 +896,24 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
           if (r == R_ACID || r == R_BASE) {
             const float qs = r == R_ACID ? -1.0f : 1.0f;
             if (lane == 0) {
-              L.info[C.site] ^= INFO_ION_BIT;
-              L.pos[C.site].w = fwd ? qs : 0.0f;
+              L.info[s_site] ^= INFO_ION_BIT;
+              L.pos[s_site].w = fwd ? qs : 0.0f;
             }
             __syncwarp();
             if (fwd) {
-              int below, same;
-              warp_rank_count(L.rank, n, q.rankA, below, same);
-              const int p = below + same;
+              const int p = belowA + sameA;  // after every entry of its cell rank
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
                 L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                L.id[p] = C.newid;
+                L.id[p] = s_newid;
                 L.lnk[p] = 0;
                 L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
                 L.rank[p] = q.rankA;
               }
               n += 1;
             } else {
-              warp_remove(L, n, C.ionA);
+              warp_remove(L, n, s_ionA);
               n -= 1;
             }
             if (lane == 0) {
@@ -759,34 +925,33 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
             }
           } else {
             if (fwd) {
-              int below, same;
-              warp_rank_count(L.rank, n, q.rankA, below, same);
-              int p = below + same;
+              int p = belowA + sameA;
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
                 L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                L.id[p] = C.newid;
+                L.id[p] = s_newid;
                 L.lnk[p] = 0;
                 L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
                 L.rank[p] = q.rankA;
               }
               __syncwarp();
               n += 1;
+              int below, same;
               warp_rank_count(L.rank, n, q.rankB, below, same);
               p = below + same;
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
                 L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-                L.id[p] = C.newid + 1u;
+                L.id[p] = s_newid + 1u;
                 L.lnk[p] = 0;
                 L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
                 L.rank[p] = q.rankB;
               }
               n += 1;
             } else {
-              const int hi = max(C.ionA, C.ionB), lo = min(C.ionA, C.ionB);
+              const int hi = max(s_ionA, s_ionB), lo = min(s_ionA, s_ionB);
               warp_remove(L, n, hi);
               n -= 1;
               warp_remove(L, n, lo);
@@ -802,18 +967,18 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
         }
         if (lane == 0) {
           misc[0] = n;
-          st[C.move] += 1;
-          if (flags & CR_TRIAL_ACCEPTED) st[6 + C.move] += 1;
+          st[s_move] += 1;
+          if (flags & CR_TRIAL_ACCEPTED) st[6 + s_move] += 1;
           if (flags & CR_TRIAL_NO_ELIGIBLE) st[12] += 1;
           if (flags & CR_TRIAL_EDGE) st[13] += 1;
           if (flags & CR_TRIAL_OVERLAP) st[14] += 1;
           st[15] += 1;
           if (LOG && P.log) {
             cr_trial rec;
-            rec.move = C.move;
+            rec.move = s_move;
             rec.flags = flags;
-            rec.id_a = C.id_a;
-            rec.id_b = C.id_b;
+            rec.id_a = s_id_a;
+            rec.id_b = s_id_b;
             rec.dE = dE;
             rec.S = Ssum;
             rec.lnA = lnA;
@@ -822,11 +987,12 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
           }
         }
       }
-      __syncthreads();
+      cta_sync<T>();
     }
   }
 
   // ---- write the domain back (id-sorted cells) and publish counts
+  __syncthreads();
   const int n = misc[0];
   for (int r = tid; r < KC; r += T) {
     int lo = 0, hi = n;  // first entry with rank >= r
@@ -858,23 +1024,41 @@ __global__ void __launch_bounds__(T, (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t phase_smem_bytes(const PhaseShape &S) {
-  size_t b = (sizeof(SysParams) + 15) / 16 * 16;
-  b += (size_t)S.dcs * (2 * sizeof(float4) + sizeof(unsigned long long) + sizeof(long long) + 2 * sizeof(int));
-  b += sizeof(long long) * S.lns;
-  b += sizeof(TrialPre) * TRIAL_CHUNK;
-  b += (sizeof(TrialCtl) + 15) / 16 * 16;
-  b += (sizeof(long long) + sizeof(unsigned long long)) * MAX_WARPS + sizeof(unsigned long long) * 16;
-  b += sizeof(int) * MAX_WARPS + sizeof(int) * 32 + sizeof(int) * 16;
-  b += 3 * sizeof(int) * (S.nr3 + 1) + 2 * sizeof(int) * (S.kc3 + 1);
+size_t phase_smem_bytes(const PhaseShape &S, int threads) {
+  const size_t sizes[] = {sizeof(SysParams),
+                          sizeof(float4) * S.dcs,
+                          sizeof(float4) * S.dcs,
+                          sizeof(unsigned long long) * S.dcs,
+                          sizeof(long long) * S.dcs,
+                          sizeof(int) * S.dcs,
+                          sizeof(int) * S.dcs,
+                          sizeof(float4) * S.hcs,
+                          sizeof(long long) * S.lns,
+                          sizeof(TrialPre) * TRIAL_CHUNK,
+                          sizeof(TrialCtl),
+                          sizeof(long long) * MAX_WARPS,
+                          sizeof(unsigned long long) * MAX_WARPS,
+                          sizeof(unsigned long long) * 16,
+                          sizeof(float) * 2 * QCAP * (threads / 32),
+                          sizeof(int) * MAX_WARPS,
+                          sizeof(int) * 32,
+                          sizeof(int) * 16,
+                          sizeof(int) * (S.nr3 + 1),
+                          sizeof(int) * (S.nr3 + 1),
+                          sizeof(int) * (S.nr3 + 1),
+                          sizeof(int) * (S.kc3 + 1),
+                          sizeof(int) * (S.kc3 + 1)};
+  size_t b = 0;
+  for (size_t x : sizes) b += (x + 15) / 16 * 16;
   return b;
 }
 
 template <int T, int R, bool LOG>
-static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, cudaStream_t s,
+static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x, PhaseShape S, cudaStream_t s,
                                   uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0, uint32_t k1) {
+  if (R > 0) S.hcs = 0;  // halo in registers
   static size_t attr_bytes = 0;
-  const size_t smem = phase_smem_bytes(S);
+  const size_t smem = phase_smem_bytes(S, T);
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_cr_phase<T, R, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -884,13 +1068,20 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
   return cudaGetLastError();
 }
 
-// (threads per CTA, halo registers per thread) variants the autotuner picks from
-static const int kShapes[][2] = {{128, 2}, {128, 4}, {128, 8}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}};
+// (threads per CTA, halo registers per thread; 0 = halo in shared memory)
+// variants the autotuner picks from
+static const int kShapes[][2] = {{32, 0}, {64, 0}, {128, 0}, {128, 4}, {256, 0}, {256, 2}, {512, 0}, {512, 1}};
 
 int phase_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
 void phase_shape(int i, int *threads, int *regs) {
   *threads = kShapes[i][0];
   *regs = kShapes[i][1];
+}
+
+size_t phase_shape_smem(const PhaseShape &S, int threads, int regs) {
+  PhaseShape Q = S;
+  if (regs > 0) Q.hcs = 0;
+  return phase_smem_bytes(Q, threads);
 }
 
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
@@ -900,14 +1091,14 @@ cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const P
   if (threads == TT && R == RR)                                                                                \
     return log ? launch_phase_t<TT, RR, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1)     \
                : launch_phase_t<TT, RR, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
-  CRMC_CASE(128, 2)
+  CRMC_CASE(32, 0)
+  CRMC_CASE(64, 0)
+  CRMC_CASE(128, 0)
   CRMC_CASE(128, 4)
-  CRMC_CASE(128, 8)
-  CRMC_CASE(256, 1)
+  CRMC_CASE(256, 0)
   CRMC_CASE(256, 2)
-  CRMC_CASE(256, 4)
+  CRMC_CASE(512, 0)
   CRMC_CASE(512, 1)
-  CRMC_CASE(512, 2)
 #undef CRMC_CASE
   return cudaErrorInvalidValue;
 }
