@@ -55,7 +55,7 @@ struct cr_ctx {
   unsigned long long *d_gs_id = nullptr;
   long long *d_gs_lnk = nullptr;
   int *d_gs_info = nullptr, *d_gs_rank = nullptr;
-  int *d_plist = nullptr, *d_nparts = nullptr;
+  int *d_plist = nullptr, *d_nparts = nullptr;  // MD particle list
   // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
@@ -758,17 +758,14 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
   M.n_perm = ctx->n_input;
   M.fene_K = (float)ctx->fene_K;
   M.inv_R02 = (float)(1.0 / (ctx->fene_R0 * ctx->fene_R0));
-  M.plist = ctx->d_plist;
-  M.n_particles = ctx->d_nparts;
   return M;
 }
 
-// particle list, then one force evaluation
+// one force evaluation
 static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
-  CR_CUDA(launch_plist(ctx->P, ctx->d_plist, ctx->d_nparts, ctx->stream));
   int ti;
   tbegin(ctx, 1, &ti);
-  CR_CUDA(launch_md_forces(ctx->P, M, (int)ctx->capacity, ctx->stream));
+  CR_CUDA(launch_md_forces(ctx->P, M, ctx->d_plist, ctx->d_nparts, (int)ctx->capacity, ctx->stream));
   tend(ctx, 1, ti);
   ctx->launches_total += 2;
   return CR_OK;

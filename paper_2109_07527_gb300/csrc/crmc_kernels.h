@@ -15,8 +15,9 @@ struct MdParams {
   const int *perm_slot, *bond_off, *bond_nbr;
   int n_perm;
   float fene_K, inv_R02;
-  const int *plist;       // occupied slots
-  const int *n_particles; // entries of plist
+  const int *plist;        // occupied slots (filled by the launcher)
+  const int *n_particles;  // entries of plist
+  int max_particles;       // capacity of plist
 };
 
 struct RebuildBufs {
@@ -51,8 +52,10 @@ void phase_shape(int i, int *threads, int *regs);
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,
                          uint32_t k1);
-cudaError_t launch_plist(const SysParams &P, int *plist, int *n_out, cudaStream_t s);
-cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int max_particles, cudaStream_t s);
+// particle list (plist, n_particles: device scratch of max_particles + 1
+// ints), then the force kernel (one warp per particle)
+cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,
+                             cudaStream_t s);
 cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s);
 cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s);
 cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,

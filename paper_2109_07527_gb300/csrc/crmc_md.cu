@@ -18,7 +18,6 @@ namespace crmc {
 // fout; mode 1: + Langevin friction/noise; mode 2: + Langevin and the closing
 // half kick v += dt/2 f.
 // ---------------------------------------------------------------------------
-constexpr int MD_GROUP = 8;
 constexpr float FFIX_INV = 1.0f / 16777216.0f;
 
 __device__ __forceinline__ void force_pair(const SysParams &P, float xi, float yi, float zi, float qi, int ci,
@@ -52,66 +51,15 @@ __device__ __forceinline__ void force_pair(const SysParams &P, float xi, float y
   fz += fix24(g * dz);
 }
 
-// compact list of occupied slots (order irrelevant)
-__global__ void k_plist(SysParams P, int *plist, int *n_out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= P.ncell) return;
-  const int n = P.cnt[c];
-  if (n == 0) return;
-  const int o = atomicAdd(n_out, n);
-  for (int s = 0; s < n; ++s) plist[o + s] = c * P.cap + s;
-}
 
-__device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
-
-// NB = 2h+1 neighbour cells per dimension as a compile-time constant (rows of
-// NB cells along x, rows spread over the 8 lanes of a group); NB = 0 is the
-// generic form used when the box has fewer than 2h+1 cells per dimension
-template <int NB>
-__global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int pi_idx = gt / MD_GROUP, sub = gt % MD_GROUP;
-  const int N = *M.n_particles;
-  const bool valid = pi_idx < N;
-  const int nc = P.nc, h = P.h, cap = P.cap;
-  long long fx = 0, fy = 0, fz = 0;
-  int gi = 0;
-  float4 pi = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (valid) {
-    gi = M.plist[pi_idx];
-    pi = P.pos[gi];
-    const int ci = (P.info[gi] >> INFO_CLS_SHIFT) & 3;
-    const int cell = gi / cap;
-    const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
-    const int nb = NB > 0 ? NB : min(2 * h + 1, nc);
-    const bool all = NB == 0 && nb == nc;  // every cell of the dimension, once
-    for (int row = sub; row < nb * nb; row += MD_GROUP) {
-      const int oy = row % nb, oz = row / nb;
-      const int jy = all ? oy : wrap_cell(cy + oy - h, nc);
-      const int jz = all ? oz : wrap_cell(cz + oz - h, nc);
-      const int base = nc * (jy + nc * jz);
-#pragma unroll
-      for (int ox = 0; ox < (NB > 0 ? NB : 1); ++ox) {
-        for (int ox2 = (NB > 0 ? ox : 0); ox2 < (NB > 0 ? ox + 1 : nb); ++ox2) {
-          const int jx = all ? ox2 : wrap_cell(cx + ox2 - h, nc);
-          const int jc = base + jx;
-          const int cnt = P.cnt[jc];
-          for (int s = 0; s < cnt; ++s) {
-            const int gj = jc * cap + s;
-            if (gj == gi) continue;
-            const float4 pj = P.pos[gj];
-            force_pair(P, pi.x, pi.y, pi.z, pi.w, ci, pj.x, pj.y, pj.z, pj.w, (P.info[gj] >> INFO_CLS_SHIFT) & 3,
-                       fx, fy, fz);
-          }
-        }
-      }
-    }
-  }
-  // FENE bonds of permanent particles, U = -K R0^2/2 ln(1 - (r/R0)^2), spread over the group
-  unsigned long long id = valid ? P.pid[gi] : ~0ull;
-  if (valid && id < (unsigned long long)M.n_perm) {
+// FENE bonds, Langevin and the store of the total force, for one particle
+// (lane 0 of its warp)
+__device__ __forceinline__ void finish_particle(const SysParams &P, const MdParams &M, int gi, float4 pi,
+                                                long long fx, long long fy, long long fz) {
+  const unsigned long long id = P.pid[gi];
+  if (id < (unsigned long long)M.n_perm) {  // FENE, U = -K R0^2/2 ln(1 - (r/R0)^2)
     const int b0 = M.bond_off[id], b1 = M.bond_off[id + 1];
-    for (int bb = b0 + sub; bb < b1; bb += MD_GROUP) {
+    for (int bb = b0; bb < b1; ++bb) {
       const float4 pj = P.pos[M.perm_slot[M.bond_nbr[bb]]];
       const float dx = wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
       const float dy = wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
@@ -127,13 +75,6 @@ __global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
       fz += fix24(g * dz);
     }
   }
-#pragma unroll
-  for (int o = MD_GROUP / 2; o > 0; o >>= 1) {
-    fx += __shfl_xor_sync(0xffffffffu, fx, o);
-    fy += __shfl_xor_sync(0xffffffffu, fy, o);
-    fz += __shfl_xor_sync(0xffffffffu, fz, o);
-  }
-  if (!valid || sub != 0) return;
   float4 f = make_float4((float)fx * FFIX_INV, (float)fy * FFIX_INV, (float)fz * FFIX_INV, 0.0f);
   if (M.mode == 0) {
     M.fout[gi] = f;
@@ -161,6 +102,133 @@ __global__ void __launch_bounds__(256) k_md_forces(SysParams P, MdParams M) {
     v.z += 0.5f * M.dt * f.z;
     M.vel[gi] = v;
   }
+}
+
+constexpr int MD_THREADS = 128;
+constexpr int MD_NW = MD_THREADS / 32;
+constexpr int MD_QCAP = 64;
+constexpr int MD_CPL = 4;  // stencil cells per lane (125 cells of a 5^3 stencil over 32 lanes)
+
+__device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+
+// compact list of occupied slots; one atomic per warp of 32 cells
+__global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  const int n = c < P.ncell ? P.cnt[c] : 0;
+  int x = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  int base = 0;
+  if (lane == 31) base = atomicAdd(n_out, x);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  const int o = base + x - n;
+  if (o + n > max_out) {  // more particles than the context's capacity
+    if (n > 0) atomicOr(P.err, ERRB_CAPACITY);
+    return;
+  }
+  for (int s = 0; s < n; ++s) plist[o + s] = c * P.cap + s;
+}
+
+// MD forces: one warp per particle.  The lanes share the (2h+1)^3 stencil of
+// neighbour cells (cell side >= rc/h), up to MD_CPL cells each; every lane
+// tests its candidates (cheap), in-range partners are queued and their forces
+// evaluated with all lanes busy.  Pair forces are FP32 terms summed in 2^-24
+// fixed point, so the result does not depend on the order.
+template <int NBC>  // 2h+1 when the box has at least that many cells per dimension, 0 otherwise
+__global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams M) {
+  __shared__ int queue[MD_NW][MD_QCAP];
+  const int lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5;
+  const int w = blockIdx.x * MD_NW + wl;
+  if (w >= *M.n_particles || w >= M.max_particles) return;  // whole warp
+  const int nc = P.nc, h = P.h, cap = P.cap;
+  const int gi = M.plist[w];
+  const float4 pi = P.pos[gi];
+  const int clsi = (P.info[gi] >> INFO_CLS_SHIFT) & 3;
+  const int cell = gi / cap;
+  const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+  const int nb = NBC > 0 ? NBC : min(2 * h + 1, nc);
+  const bool all = NBC == 0 && nb == nc;  // every cell of the dimension, once
+  const int nb3 = nb * nb * nb;
+  // this lane's stencil cells and their counts
+  int cbase[MD_CPL], ccnt[MD_CPL], total = 0;
+#pragma unroll
+  for (int t = 0; t < MD_CPL; ++t) {
+    const int o = lane + 32 * t;
+    cbase[t] = 0;
+    ccnt[t] = 0;
+    if (o < nb3) {
+      const int ox = o % nb, oy = (o / nb) % nb, oz = o / (nb * nb);
+      const int jx = all ? ox : wrap_cell(cx + ox - h, nc);
+      const int jy = all ? oy : wrap_cell(cy + oy - h, nc);
+      const int jz = all ? oz : wrap_cell(cz + oz - h, nc);
+      const int jc = jx + nc * (jy + nc * jz);
+      cbase[t] = jc * cap;
+      ccnt[t] = P.cnt[jc];
+      total += ccnt[t];
+    }
+  }
+  const int iters = __reduce_max_sync(0xffffffffu, (unsigned)total);
+  int *q = queue[wl];
+  int qn = 0;
+  long long fx = 0, fy = 0, fz = 0;
+  for (int it = 0; it < iters; ++it) {
+    bool in = false;
+    int gj = -1;
+    if (it < total) {
+      int rem = it;
+#pragma unroll
+      for (int t = 0; t < MD_CPL; ++t) {
+        if (gj < 0) {
+          if (rem < ccnt[t]) gj = cbase[t] + rem;
+          else rem -= ccnt[t];
+        }
+      }
+      if (gj != gi) {
+        const float4 pj = P.pos[gj];
+        const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
+        const float dx = wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
+        const float dy = wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
+        const float dz = wrap_diff(pi.z, pj.z, P.Lf, P.halfL);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const WcaEntry &wc = P.wca[clsi * 4 + cj];
+        in = (r2 < P.rc2 && pi.w != 0.0f && pj.w != 0.0f) || (wc.on && r2 < wc.wcut2);
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) q[qn + __popc(m & ((1u << lane) - 1u))] = gj;
+    qn += __popc(m);
+    if (qn >= 32) {
+      __syncwarp();
+      const int g2 = q[lane];
+      const float4 pj = P.pos[g2];
+      force_pair(P, pi.x, pi.y, pi.z, pi.w, clsi, pj.x, pj.y, pj.z, pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy,
+                 fz);
+      const int rest = qn - 32;
+      int keep = 0;
+      if (lane < rest) keep = q[32 + lane];
+      __syncwarp();
+      if (lane < rest) q[lane] = keep;
+      __syncwarp();
+      qn = rest;
+    }
+  }
+  __syncwarp();
+  if (lane < qn) {
+    const int g2 = q[lane];
+    const float4 pj = P.pos[g2];
+    force_pair(P, pi.x, pi.y, pi.z, pi.w, clsi, pj.x, pj.y, pj.z, pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx += __shfl_xor_sync(0xffffffffu, fx, o);
+    fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    fz += __shfl_xor_sync(0xffffffffu, fz, o);
+  }
+  if (lane == 0) finish_particle(P, M, gi, pi, fx, fy, fz);
 }
 
 // v += dt/2 f; x += dt v; wrap into [0, L)
@@ -296,19 +364,20 @@ __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uin
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_plist(const SysParams &P, int *plist, int *n_out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(n_out, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  k_plist<<<(P.ncell + 255) / 256, 256, 0, s>>>(P, plist, n_out);
-  return cudaGetLastError();
-}
 
-cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int max_particles, cudaStream_t s) {
-  const long long threads = (long long)max_particles * MD_GROUP;
-  const unsigned grid = (unsigned)((threads + 255) / 256);
-  if (P.h == 2 && P.nc >= 5) k_md_forces<5><<<grid, 256, 0, s>>>(P, M);
-  else if (P.h == 1 && P.nc >= 3) k_md_forces<3><<<grid, 256, 0, s>>>(P, M);
-  else k_md_forces<0><<<grid, 256, 0, s>>>(P, M);
+cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,
+                             cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(n_particles, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  k_plist<<<(P.ncell + 255) / 256, 256, 0, s>>>(P, plist, n_particles, max_particles);
+  MdParams Q = M;
+  Q.plist = plist;
+  Q.n_particles = n_particles;
+  Q.max_particles = max_particles;
+  const unsigned grid = (unsigned)((max_particles + MD_NW - 1) / MD_NW);
+  if (P.h == 2 && P.nc >= 5) k_md_forces<5><<<grid, MD_THREADS, 0, s>>>(P, Q);
+  else if (P.h == 1 && P.nc >= 3) k_md_forces<3><<<grid, MD_THREADS, 0, s>>>(P, Q);
+  else k_md_forces<0><<<grid, MD_THREADS, 0, s>>>(P, Q);
   return cudaGetLastError();
 }
 
