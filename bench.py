@@ -151,7 +151,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def cpu_baseline(w, sample_sweeps=10):
+def cpu_baseline(w, sample_sweeps=20):
     """The oracle as it stands (single thread) on a bounded sample of the
     workload: sample_sweeps sweeps of 1000 trials (one trial per domain) and one
     MD step, i.e. the workload's 1 MD step : 1e4 trials mix."""
