@@ -125,11 +125,10 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
   if (lane == 31) base = atomicAdd(n_out, x);
   base = __shfl_sync(0xffffffffu, base, 31);
   const int o = base + x - n;
-  if (o + n > max_out) {  // more particles than the context's capacity
-    if (n > 0) atomicOr(P.err, ERRB_CAPACITY);
-    return;
-  }
-  for (int s = 0; s < n; ++s) plist[o + s] = c * P.cap + s;
+  if (o + n > max_out && n > 0) atomicOr(P.err, ERRB_CAPACITY);  // more particles than the context's capacity
+  // entries that fit are written even then, so every entry the force kernel
+  // reads (below min(count, max_out)) names a slot of this system
+  for (int s = 0; s < n && o + s < max_out; ++s) plist[o + s] = c * P.cap + s;
 }
 
 // MD forces: one warp per particle.  The lanes share the (2h+1)^3 stencil of
