@@ -185,6 +185,34 @@ int cr_md_forces(cr_ctx *ctx);
  * BOND_BROKEN, CELL_OVERFLOW. */
 int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
 
+/* The force evaluation of cr_md_forces, allocating nothing, with the results
+ * written to caller-owned device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device
+ * memory while they run, e.g. an MD engine that owns every device buffer
+ * through its own pool, or a time-critical loop in which a device allocation
+ * (which may synchronise the whole device) is not acceptable.
+ *
+ * force: device array of 4 * n_slots floats (16-byte aligned); slot g gets
+ *        (fx, fy, fz, 0) of the particle held in it, empty slots (0, 0, 0, 0).
+ * id:    device array of n_slots particle ids; UINT64_MAX marks an empty slot.
+ * n_slots must be at least nc^3 * cap (cr_get_info); slots beyond that are
+ * not written.  Both arrays stay owned by the caller.  The context's own
+ * force buffers (cr_state().force) are not touched.
+ *
+ * Scratch: the particle list lives in one fixed device array of the library,
+ * sized for CR_NOALLOC_MAX_PARTICLES particles and shared by every context
+ * on a device.  A context created with a capacity above that maximum gets
+ * CR_ERR_CAPACITY before anything is launched.  The call clears the scratch
+ * counter itself.  Calls whose work overlaps on the GPU (different streams or
+ * contexts without ordering between them) race on that scratch: order them
+ * on one stream or with events.  The first call on a device looks the
+ * scratch address up (cudaGetSymbolAddress) with the context's device
+ * current; make that first call before any stream capture.  Synchronises the
+ * context's stream.  Errors: INVALID_ARG (NULL or misaligned pointer, n_slots
+ * too small, context device not current), CAPACITY, CELL_OVERFLOW, CUDA. */
+#define CR_NOALLOC_MAX_PARTICLES 262144
+int cr_md_forces_noalloc(cr_ctx *ctx, float *force, uint64_t *id, int64_t n_slots);
+
 /* Fill the view (counts always; arrays when non-NULL) and synchronise.
  * Arrays are ordered by particle id. */
 int cr_state(cr_ctx *ctx, cr_state_view *out);

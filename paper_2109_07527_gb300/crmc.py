@@ -73,7 +73,7 @@ TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id
 EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
            "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
            "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape", "cr_batch_create", "cr_batch_sweep",
-           "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy")
+           "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy", "cr_md_forces_noalloc")
 
 _L = None
 
@@ -94,6 +94,8 @@ def _lib():
         lib.cr_md_forces.restype = C.c_int
         lib.cr_md_forces.argtypes = [P]
         lib.cr_md_step.restype = C.c_int
+        lib.cr_md_forces_noalloc.restype = C.c_int
+        lib.cr_md_forces_noalloc.argtypes = [P, P, P, C.c_int64]
         lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
         lib.cr_state.restype = C.c_int
         lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
@@ -235,6 +237,12 @@ class Context:
 
     def md_forces(self):
         _chk(self._lib.cr_md_forces(self._h), "cr_md_forces")
+
+    def md_forces_noalloc(self, force_ptr, id_ptr, n_slots):
+        """cr_md_forces_noalloc into caller-owned device memory given as raw
+        pointers: force [4 * n_slots] float32, id [n_slots] uint64."""
+        _chk(self._lib.cr_md_forces_noalloc(self._h, C.c_void_p(int(force_ptr)), C.c_void_p(int(id_ptr)),
+                                            int(n_slots)), "cr_md_forces_noalloc")
 
     def md_step(self, n_steps, dt, gamma, seed):
         _chk(self._lib.cr_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_md_step")

@@ -1152,3 +1152,27 @@ extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, in
   *regs = b->R;
   return CR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// context access for the allocation-free force entry point (crmc_noalloc.cu):
+// the force evaluation of cr_md_forces with the particle-list scratch and the
+// slot-indexed force output supplied by the caller; the context's own force
+// buffers and its validity flags are left alone.
+// ---------------------------------------------------------------------------
+namespace crmc {
+
+int ctx_md_forces_into(cr_ctx *ctx, float4 *fout, int *plist, int *n_particles, int max_particles) {
+  MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
+  M.fout = fout;
+  CR_CUDA(launch_md_forces(ctx->P, M, plist, n_particles, max_particles, ctx->stream));
+  ctx->launches_total += 2;
+  return CR_OK;
+}
+
+const SysParams &ctx_params(const cr_ctx *ctx) { return ctx->P; }
+cudaStream_t ctx_stream(const cr_ctx *ctx) { return ctx->stream; }
+int64_t ctx_capacity(const cr_ctx *ctx) { return ctx->capacity; }
+int ctx_device(const cr_ctx *ctx) { return ctx->device; }
+void ctx_count_launch(cr_ctx *ctx) { ctx->launches_total++; }
+
+}  // namespace crmc
