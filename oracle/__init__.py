@@ -3,7 +3,7 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``crmc_oracle.c`` (plain C,
 compiled with gcc here or on the GPU host by :func:`build`) and
-``mlp_oracle.py`` (numpy float64).  Nothing in it is shared with the CUDA path.
+``mlp_oracle.py`` (numpy float64, the surrogate's training step).  Nothing in it is shared with the CUDA path.
 
 Paper sections it follows: Sec. II.B (grouped reactions), Sec. II.C (moves and
 acceptance rules, Eq. QQ), App. A (ion grouping, Eq. mux), App. C (Eq. pIXgen).
@@ -22,7 +22,8 @@ _LIB = os.path.join(_HERE, "libcrmc_oracle.so")
 # trial-record flags
 F_ACC, F_NOELIG, F_EDGE, F_OVERLAP = 1, 2, 4, 8
 PLANT = {"none": 0, "drop_ion_count": 1, "dE_sign": 2, "drop_self": 3, "drop_pair_cc": 4,
-         "wrong_volume": 5}
+         "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7}
+N_FEAT, N_HID = 48, 128
 
 
 def build(force: bool = False) -> str:
@@ -53,6 +54,9 @@ class _Params(C.Structure):
 
 TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id_b", "<u8"),
                         ("dE", "<f8"), ("S", "<f8"), ("lnA", "<f8"), ("lnu", "<f8")])
+# delayed-acceptance record: surrogate dE~, stage (0 none, 1 stage-1 reject,
+# 2 passed stage 1), stage-2 log ratio dE~ - dE_pair, log of the stage-2 uniform
+DA_DTYPE = np.dtype([("dE_sur", "<f4"), ("stage", "<i4"), ("lnA2", "<f8"), ("lnu2", "<f8")])
 
 _lib = None
 
@@ -66,7 +70,15 @@ def _load():
         lib.or_create.argtypes = [C.POINTER(_Params), P, P, P, P, P, P, P, C.POINTER(C.c_int32)]
         lib.or_destroy.argtypes = [P]
         lib.or_sweep.restype = C.c_int32
-        lib.or_sweep.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, C.c_int32, P]
+        lib.or_sweep.argtypes = [P, C.c_int64, C.c_uint64, P, P, P, C.c_int32, P, P, P, P]
+        lib.or_set_surrogate.restype = C.c_int32
+        lib.or_set_surrogate.argtypes = [P, P, P, P, P, P, P, P, C.c_float]
+        lib.or_set_da.restype = C.c_int32
+        lib.or_set_da.argtypes = [P, C.c_int32]
+        lib.or_mlp.restype = C.c_float
+        lib.or_mlp.argtypes = [P, P]
+        lib.or_surrogate.restype = C.c_float
+        lib.or_surrogate.argtypes = [P, P]
         lib.or_trials_per_sweep.restype = C.c_int64
         lib.or_trials_per_sweep.argtypes = [P]
         lib.or_counts.argtypes = [P, P]
@@ -190,19 +202,48 @@ class Oracle:
         self._lib.or_chem(self._h, _ptr(c))
         return dict(pIX_plus=c[0], pIX_minus=c[1], ln_z1=c[2], ln_salt=c[3], a=c[4], self_coef=c[5], pOH=c[6])
 
-    def sweep(self, n_trials, seed, log=False, forced=None, hist_n=0, trans=False):
+    def set_surrogate(self, mlp):
+        """Surrogate weights: dict with W1 [128,48], W2, W3 [128,128], w4 [128]
+        as uint16 BF16 bit patterns and b1, b2, b3 [128] float32, b4 float."""
+        self._mlp = {k: np.ascontiguousarray(mlp[k], dtype=np.uint16) for k in ("W1", "W2", "W3", "w4")}
+        self._mlp.update({k: np.ascontiguousarray(mlp[k], dtype=np.float32) for k in ("b1", "b2", "b3")})
+        m = self._mlp
+        self._lib.or_set_surrogate(self._h, _ptr(m["W1"]), _ptr(m["b1"]), _ptr(m["W2"]), _ptr(m["b2"]),
+                                   _ptr(m["W3"]), _ptr(m["b3"]), _ptr(m["w4"]), float(mlp["b4"]))
+
+    def set_da(self, on=True):
+        if self._lib.or_set_da(self._h, 1 if on else 0) != 0:
+            raise ValueError("delayed acceptance needs a surrogate (set_surrogate)")
+
+    def mlp(self, F):
+        F = np.ascontiguousarray(F, dtype=np.float32)
+        return float(self._lib.or_mlp(self._h, _ptr(F)))
+
+    def surrogate(self, F):
+        F = np.ascontiguousarray(F, dtype=np.float32)
+        return float(self._lib.or_surrogate(self._h, _ptr(F)))
+
+    def sweep(self, n_trials, seed, log=False, forced=None, hist_n=0, trans=False, da_log=False, features=False):
         n_trials = int(n_trials)
         rec = np.zeros(n_trials, dtype=TRIAL_DTYPE) if log else None
         f = None if forced is None else np.ascontiguousarray(forced, dtype=np.int8)
         hist = np.zeros(1 << hist_n, dtype=np.int64) if hist_n else None
         tr = np.zeros((1 << hist_n) * hist_n, dtype=np.int64) if (trans and hist_n) else None
+        dl = np.zeros(n_trials, dtype=DA_DTYPE) if da_log else None
+        feat = np.zeros((n_trials, N_FEAT), dtype=np.float32) if features else None
+        dep = np.zeros(n_trials, dtype=np.float64) if features else None
         rc = self._lib.or_sweep(self._h, n_trials, C.c_uint64(seed), _ptr(rec), _ptr(f), _ptr(hist), hist_n,
-                                _ptr(tr))
+                                _ptr(tr), _ptr(dl), _ptr(feat), _ptr(dep))
         if rc != 0:
             raise RuntimeError(f"or_sweep failed with code {rc}")
         out = {}
         if log:
             out["log"] = rec
+        if da_log:
+            out["da"] = dl
+        if features:
+            out["features"] = feat
+            out["dE_pair"] = dep
         if hist_n:
             out["hist"] = hist
         if tr is not None:

@@ -54,7 +54,8 @@ enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 
 /* Planted mistakes, used only by the tests that show the pins catch them. */
 enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
-       PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5 };
+       PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5,
+       PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7 };
 
 /* ----------------------------------------------------------------------- */
 /* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
@@ -138,6 +139,10 @@ typedef struct {
   uint64_t sweep, md_evals;
   int64_t stats[16];
   int plant;
+  /* learned delayed acceptance: surrogate weights (BF16 values held as
+   * floats), on when has_mlp and da are set */
+  int has_mlp, da;
+  float *W1, *b1, *W2, *b2, *W3, *b3, *w4, b4;
 } Oracle;
 
 static int g_plant = PLANT_NONE;
@@ -236,6 +241,7 @@ void or_destroy(Oracle *o) {
   free(o->x); free(o->y); free(o->z); free(o->type); free(o->cls); free(o->site); free(o->st);
   free(o->id); free(o->vx); free(o->vy); free(o->vz); free(o->fx); free(o->fy); free(o->fz);
   free(o->lnK); free(o->bi); free(o->bj);
+  free(o->W1); free(o->b1); free(o->W2); free(o->b2); free(o->W3); free(o->b3); free(o->w4);
   free(o);
 }
 
@@ -547,9 +553,173 @@ static int net_charge(const Oracle *o) {
  *   purpose 1 -> w0..w2 position of ion A, w3 x of ion B
  *   purpose 2 -> w0, w1 y, z of ion B; w2, w3 the Metropolis uniform
  * New ion ids: (phi+1) << 32 | 2*(d*m + k) + b, b = 0 (ion A / X+) or 1 (X-). */
+/* ----------------------------------------------------------------------- */
+/* Learned delayed acceptance (Christen & Fox, J. Comput. Graph. Stat. 14,
+ * 795 (2005)) in front of the exact Metropolis test of Sec. II.C.  The paper
+ * itself evaluates every trial exactly; this stage is the surrogate fast path.
+ *   stage 1: accept with min(1, R exp(-(dE_self + dE~))), R the combinatorial
+ *            and chemical factor of the move, dE_self the exact DSF self-term
+ *            change and dE~ the surrogate estimate of the pair-energy change;
+ *            a stage-1 rejection ends the trial without the exact pair sum;
+ *   stage 2: accept with min(1, exp(-(dE_pair - dE~))).
+ * The two-stage acceptance satisfies detailed balance with respect to
+ * Eq. (QQ) when dE~(y -> x) = -dE~(x -> y): the features change sign under
+ * move reversal (the particles other than the two changed ones are the same
+ * in x and y) and the surrogate is antisymmetrised, dE~ = (mlp(F) - mlp(-F))/2.
+ *
+ * Features (48 integers) of a change of particles a (site, or cation of a
+ * salt move) and b (ion, or anion), over the cells of the 5^3 stencil of
+ * half-cutoff cells around each changed particle's cell, grouped into 8
+ * shells by the squared integer cell offset {0},{1},{2},{3},{4},{5},{6},{8,9,12}:
+ *   F[24 s +  0 + shell] += dq_s * (charge of each ion in those cells)
+ *   F[24 s +  8 + shell] += dq_s * (charge of each site in those cells)
+ *   F[24 s + 16 + shell] += eta_s  (for each particle in those cells)
+ * dq_s = change of s's effective charge, eta_s = +1 inserted, -1 deleted,
+ * 0 otherwise; every particle other than a and b counts.  The a-b pair adds
+ *   F[shell(b relative to a)] += q_a' q_b' - q_a q_b  (primes: after the move).
+ * MLP 48 -> 128 -> 128 -> 128 -> 1 with ReLU, BF16 weights and FP32 biases,
+ * evaluated in FP32: each output is its bias plus one fused multiply-add per
+ * weight in input order. */
+#define MLP_IN 48
+#define MLP_H 128
+
+static float bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  memcpy(&f, &u, sizeof f);
+  return f;
+}
+
+static float *bf16_array(const uint16_t *w, int n) {
+  float *f = malloc((size_t)n * sizeof(float));
+  for (int i = 0; i < n; ++i) f[i] = bf16_value(w[i]);
+  return f;
+}
+
+static float *f32_array(const float *w, int n) {
+  float *f = malloc((size_t)n * sizeof(float));
+  memcpy(f, w, (size_t)n * sizeof(float));
+  return f;
+}
+
+/* W1 [128][48], W2 and W3 [128][128] (out x in), w4 [128]: BF16 bit patterns */
+int32_t or_set_surrogate(Oracle *o, const uint16_t *W1, const float *b1, const uint16_t *W2, const float *b2,
+                         const uint16_t *W3, const float *b3, const uint16_t *w4, float b4) {
+  free(o->W1); free(o->b1); free(o->W2); free(o->b2); free(o->W3); free(o->b3); free(o->w4);
+  o->W1 = bf16_array(W1, MLP_H * MLP_IN); o->b1 = f32_array(b1, MLP_H);
+  o->W2 = bf16_array(W2, MLP_H * MLP_H); o->b2 = f32_array(b2, MLP_H);
+  o->W3 = bf16_array(W3, MLP_H * MLP_H); o->b3 = f32_array(b3, MLP_H);
+  o->w4 = bf16_array(w4, MLP_H); o->b4 = b4;
+  o->has_mlp = 1;
+  return OR_OK;
+}
+
+/* delayed acceptance on (1) or off (0); needs a surrogate */
+int32_t or_set_da(Oracle *o, int32_t on) {
+  if (on && !o->has_mlp) return OR_ERR_ARG;
+  o->da = on ? 1 : 0;
+  return OR_OK;
+}
+
+static void dense_relu(const float *W, const float *b, const float *x, int n_in, float *y) {
+  for (int i = 0; i < MLP_H; ++i) {
+    float a = b[i];
+    for (int k = 0; k < n_in; ++k) a = fmaf(W[i * n_in + k], x[k], a);
+    y[i] = a > 0.0f ? a : 0.0f;
+  }
+}
+
+static float mlp_forward(const Oracle *o, const float *F) {
+  float h1[MLP_H], h2[MLP_H], h3[MLP_H];
+  dense_relu(o->W1, o->b1, F, MLP_IN, h1);
+  dense_relu(o->W2, o->b2, h1, MLP_H, h2);
+  dense_relu(o->W3, o->b3, h2, MLP_H, h3);
+  float y = o->b4;
+  for (int k = 0; k < MLP_H; ++k) y = fmaf(o->w4[k], h3[k], y);
+  return y;
+}
+
+float or_mlp(const Oracle *o, const float *F) { return o->has_mlp ? mlp_forward(o, F) : NAN; }
+
+static float surrogate_dE(const Oracle *o, const float *F) {
+  float G[MLP_IN];
+  for (int k = 0; k < MLP_IN; ++k) G[k] = -F[k];
+  const float yp = mlp_forward(o, F);
+  if (g_plant == PLANT_DA_ONE_SIDED) return yp;
+  const float ym = mlp_forward(o, G);
+  return 0.5f * (yp - ym);
+}
+
+float or_surrogate(const Oracle *o, const float *F) { return o->has_mlp ? surrogate_dE(o, F) : NAN; }
+
+/* shell of a squared integer cell offset; -1 cannot occur in a 5^3 stencil */
+static const int SHELL_OF_N2[13] = {0, 1, 2, 3, 4, 5, 6, -1, 7, 7, -1, -1, 7};
+
+static int cell_delta(const Oracle *o, int cb, int ca) {
+  int d = ((cb - ca) % o->nc + o->nc) % o->nc;
+  if (d > o->nc / 2) d -= o->nc;
+  return d;
+}
+
+/* shell of the cell of b relative to the cell of a, -1 outside the stencil */
+static int shell_between(const Oracle *o, float ax, float ay, float az, float bx, float by, float bz) {
+  const int dx = cell_delta(o, cell_of(o, bx), cell_of(o, ax));
+  const int dy = cell_delta(o, cell_of(o, by), cell_of(o, ay));
+  const int dz = cell_delta(o, cell_of(o, bz), cell_of(o, az));
+  if (abs(dx) > 2 || abs(dy) > 2 || abs(dz) > 2) return -1;
+  return SHELL_OF_N2[dx * dx + dy * dy + dz * dz];
+}
+
+static int iround(double v) { return (int)lround(v); }
+
+static void da_features(const Oracle *o, const change_t *ch, float *F) {
+  int acc[MLP_IN];
+  memset(acc, 0, sizeof acc);
+  for (int s = 0; s < 2; ++s) {
+    const change_t *c = &ch[s];
+    const int dq = iround((c->pres_new ? c->q_new : 0.0) - (c->pres_old ? c->q_old : 0.0));
+    const int eta = c->pres_new - c->pres_old;
+    for (int j = 0; j < o->n; ++j) {
+      if (j == ch[0].idx || j == ch[1].idx) continue;
+      const int sh = shell_between(o, c->x, c->y, c->z, o->x[j], o->y[j], o->z[j]);
+      if (sh < 0) continue;
+      const int t = o->type[j];
+      const int q = iround(qeff(o, t, o->st[j]));
+      if (t == T_XP || t == T_XM) acc[24 * s + sh] += dq * q;
+      else if (t == T_ACID || t == T_BASE) acc[24 * s + 8 + sh] += dq * q;
+      acc[24 * s + 16 + sh] += eta;
+    }
+  }
+  const int sh = shell_between(o, ch[0].x, ch[0].y, ch[0].z, ch[1].x, ch[1].y, ch[1].z);
+  if (sh >= 0) {
+    const int qn = (ch[0].pres_new && ch[1].pres_new) ? iround(ch[0].q_new) * iround(ch[1].q_new) : 0;
+    const int qo = (ch[0].pres_old && ch[1].pres_old) ? iround(ch[0].q_old) * iround(ch[1].q_old) : 0;
+    acc[sh] += qn - qo;
+  }
+  for (int k = 0; k < MLP_IN; ++k) F[k] = (float)acc[k];
+}
+
+/* exact DSF self-term change of a set of changed particles (part of dE) */
+static double self_change(const Oracle *o, const change_t *c, int nc) {
+  if (!o->dsf_self || g_plant == PLANT_DROP_SELF) return 0.0;
+  double ds = 0.0;
+  for (int a = 0; a < nc; ++a)
+    ds += o->lB * o->self_coef *
+          ((c[a].pres_new ? c[a].q_new * c[a].q_new : 0.0) - (c[a].pres_old ? c[a].q_old * c[a].q_old : 0.0));
+  return ds;
+}
+
+/* extra per-trial record of the delayed-acceptance stages */
+typedef struct {
+  float dE_sur;    /* surrogate pair-energy change */
+  int32_t stage;   /* 0 no surrogate evaluated, 1 rejected at stage 1, 2 passed stage 1 */
+  double lnA2;     /* dE~ - dE_pair (NaN on overlap) */
+  double lnu2;     /* log of the stage-2 uniform */
+} or_trial_da;
+
 static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint32_t phi, int d, int k,
                         or_trial *rec, int forced, elig_t *buf, int64_t *hist, int hist_n,
-                        int64_t *trans) {
+                        int64_t *trans, or_trial_da *drec, float *feat, double *dEpair) {
   uint32_t c0[4] = {(uint32_t)k, (uint32_t)d, phi, 0u}, c1[4] = {(uint32_t)k, (uint32_t)d, phi, 1u},
            c2[4] = {(uint32_t)k, (uint32_t)d, phi, 2u};
   uint32_t P0[4], P1[4], P2[4];
@@ -647,11 +817,48 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
     }
   }
   int accept = 0;
+  or_trial_da td = {0.0f, 0, NAN, NAN};
+  if (feat) for (int q = 0; q < MLP_IN; ++q) feat[q] = 0.0f;
+  if (dEpair) *dEpair = NAN;
   if (noelig) t.flags |= F_NOELIG;
   else if (edge) t.flags |= F_EDGE;
-  else {
+  else if (o->da) {
+    /* delayed acceptance; forced: bit 1 forces stage 1 to bit 0, bit 3
+     * forces stage 2 to bit 2 (tie protocol of the parity tests) */
+    float F[MLP_IN];
+    da_features(o, ch, F);
+    const float sur = surrogate_dE(o, F);
+    const double dself = self_change(o, ch, nch);
     int ov = 0;
     double S = 0.0;
+    const double dE = delta_E(o, ch, nch, &ov, &S); /* recorded always, decisive only after stage 1 */
+    t.S = S;
+    t.lnA = ln_ratio - dself - (double)sur;
+    int s1 = t.lnu < t.lnA;
+    if (forced >= 0 && (forced & 2)) s1 = forced & 1;
+    uint32_t c3[4] = {(uint32_t)k, (uint32_t)d, phi, 3u}, P3[4];
+    philox(c3, key, P3);
+    td.dE_sur = sur;
+    td.stage = s1 ? 2 : 1;
+    td.lnu2 = log(unif53(P3[0], P3[1]));
+    if (feat) memcpy(feat, F, sizeof F);
+    if (ov) {
+      t.dE = INFINITY;
+      if (s1) t.flags |= F_OVERLAP;
+    } else {
+      t.dE = dE;
+      td.lnA2 = (double)sur - (dE - dself);
+      if (g_plant == PLANT_DA_STAGE2_FULL) td.lnA2 = ln_ratio - dE;
+      if (dEpair) *dEpair = dE - dself;
+      if (s1) {
+        accept = td.lnu2 < td.lnA2;
+        if (forced >= 0 && (forced & 8)) accept = (forced >> 2) & 1;
+      }
+    }
+  } else {
+    int ov = 0;
+    double S = 0.0;
+    if (feat) da_features(o, ch, feat);
     double dE = delta_E(o, ch, nch, &ov, &S);
     if (g_plant == PLANT_DE_SIGN) dE = -dE;
     t.S = S;
@@ -660,9 +867,11 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
       t.dE = dE;
       t.lnA = ln_ratio - dE;
       accept = t.lnu < t.lnA;
+      if (dEpair) *dEpair = dE - self_change(o, ch, nch);
     }
+    if (forced >= 0 && !(t.flags & (F_NOELIG | F_EDGE | F_OVERLAP))) accept = forced;
   }
-  if (forced >= 0 && !(t.flags & (F_NOELIG | F_EDGE | F_OVERLAP))) accept = forced;
+  if (drec) *drec = td;
   if (accept) {
     t.flags |= F_ACC;
     o->stats[6 + t.move]++;
@@ -711,9 +920,12 @@ int64_t or_trials_per_sweep(const Oracle *o) {
  * (colour phases in order, domains ascending, trials in the domain).
  * forced: optional per-trial decision override (-1 = none) used only to step
  * over a tie at the acceptance threshold.  hist/trans: optional state
- * histogram over the first hist_n sites and site-flip transition counts. */
+ * histogram over the first hist_n sites and site-flip transition counts.
+ * dlog / feat / dEpair: optional per-trial delayed-acceptance records, the
+ * 48 surrogate features and the exact pair-energy change (dE minus the self
+ * term; NaN when not evaluated or on overlap). */
 int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, const int8_t *forced,
-                 int64_t *hist, int32_t hist_n, int64_t *trans) {
+                 int64_t *hist, int32_t hist_n, int64_t *trans, or_trial_da *dlog, float *feat, double *dEpair) {
   int64_t per = or_trials_per_sweep(o);
   if (n_trials < 0 || n_trials % per != 0) return OR_ERR_ARG;
   if (hist_n < 0 || hist_n > 20) return OR_ERR_ARG;
@@ -739,7 +951,9 @@ int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, cons
         if (colour != col) continue;
         for (int k = 0; k < o->m && rc == OR_OK; ++k, ++t) {
           int f = forced ? forced[t] : -1;
-          rc = or_trial_one(o, key, off, phi, d, k, log ? &log[t] : NULL, f, buf, hist, hist_n, trans);
+          rc = or_trial_one(o, key, off, phi, d, k, log ? &log[t] : NULL, f, buf, hist, hist_n, trans,
+                            dlog ? &dlog[t] : NULL, feat ? feat + (size_t)t * MLP_IN : NULL,
+                            dEpair ? &dEpair[t] : NULL);
         }
       }
     }

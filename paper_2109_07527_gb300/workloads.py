@@ -371,3 +371,29 @@ def config5(seed=1, scale=1.0):
     params = default_params(box_L=L, rc=12.0, lB=2.0, pH=4.5, pIS_plus=1.226, pIS_minus=1.226)
     n = n_chains * 200 + 2 * n_pairs
     return _assemble("config5", [chains, ions], params, n + 8192, rng, bonds=bonds)
+
+
+# ---------------------------------------------------------------- surrogate weights
+def to_bf16_bits(x):
+    """BF16 bit patterns of float32 values (round to nearest, ties to even)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def bf16_to_f32(bits):
+    """float32 values of BF16 bit patterns (exact)."""
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def random_mlp(seed=1, gain=1.0, out_gain=1.0, n_in=48, n_hid=128):
+    """Seeded random surrogate weights in the layout the ABI takes: W1 [128, 48],
+    W2 and W3 [128, 128], w4 [128] as BF16 bit patterns, biases float32.
+    He-style scales times `gain`; `out_gain` scales the output layer."""
+    rng = np.random.default_rng(seed)
+    def layer(o, i, g):
+        return to_bf16_bits(rng.normal(0.0, g * math.sqrt(2.0 / i), (o, i)).astype(np.float32))
+    return dict(W1=layer(n_hid, n_in, gain * 0.25), b1=(0.05 * rng.normal(size=n_hid)).astype(np.float32),
+                W2=layer(n_hid, n_hid, gain), b2=(0.05 * rng.normal(size=n_hid)).astype(np.float32),
+                W3=layer(n_hid, n_hid, gain), b3=(0.05 * rng.normal(size=n_hid)).astype(np.float32),
+                w4=to_bf16_bits((out_gain * rng.normal(0.0, math.sqrt(1.0 / n_hid), n_hid)).astype(np.float32)),
+                b4=float(0.1 * rng.normal()))

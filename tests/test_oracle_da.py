@@ -1,0 +1,256 @@
+"""Pins of the oracle's learned delayed-acceptance (DA) stage.
+
+The surrogate is not in the paper (which evaluates every trial exactly); what
+must hold is fixed by the mathematics of delayed acceptance (Christen & Fox
+2005) and by the definitions written in the oracle:
+  * the MLP equals a numpy float64 evaluation within the FP32 rounding bound,
+    and a hand-built network gives its closed-form value exactly;
+  * the surrogate is exactly antisymmetric, dE~(-F) = -dE~(F);
+  * the features equal a brute-force numpy recount from the particles;
+  * the DA chain samples the exact distribution of Eq. (QQ) (exact
+    enumeration), whatever the surrogate, and planted mistakes in the stages
+    (a one-sided surrogate, a stage 2 that ignores the surrogate) fail it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_07527_gb300 import workloads as W
+from test_oracle_pins import enumeration_probs
+
+
+def _np_mlp(m, F):
+    """float64 evaluation of the same network (BF16 weights)."""
+    f = lambda k: W.bf16_to_f32(m[k]).astype(np.float64)
+    h = np.maximum(f("W1") @ F + m["b1"], 0.0)
+    h = np.maximum(f("W2") @ h + m["b2"], 0.0)
+    h = np.maximum(f("W3") @ h + m["b3"], 0.0)
+    return float(f("w4") @ h + m["b4"])
+
+
+def test_mlp_matches_float64_evaluation():
+    w = W.ideal(n_sites=4, n_pairs=2)
+    o = oracle.Oracle(w)
+    m = W.random_mlp(seed=3)
+    o.set_surrogate(m)
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        F = rng.integers(-20, 20, 48).astype(np.float32)
+        y32, y64 = o.mlp(F), _np_mlp(m, F.astype(np.float64))
+        # FP32 dot products: relative error bound ~ n u sum|terms| per layer
+        f = lambda k: np.abs(W.bf16_to_f32(m[k]).astype(np.float64))
+        g = np.abs(F.astype(np.float64))
+        for k in ("W1", "W2", "W3"):
+            g = f(k) @ g + 1.0
+        scale = float(f("w4") @ g) + 1.0
+        assert abs(y32 - y64) <= 4 * 128 * 2.0 ** -24 * scale, (y32, y64, scale)
+
+
+def test_mlp_closed_form():
+    """A network that passes feature 0 (and -feature 0) through the ReLUs:
+    mlp(F) = 2 F0 + 0.5 when F0 > 0, else 0.5; dE~ = F0."""
+    w = W.ideal(n_sites=4, n_pairs=2)
+    o = oracle.Oracle(w)
+    z = np.zeros
+    W1 = z((128, 48), np.float32); W1[0, 0] = 1.0
+    W2 = z((128, 128), np.float32); W2[0, 0] = 2.0
+    W3 = z((128, 128), np.float32); W3[0, 0] = 1.0
+    w4 = z(128, np.float32); w4[0] = 1.0
+    m = dict(W1=W.to_bf16_bits(W1), W2=W.to_bf16_bits(W2), W3=W.to_bf16_bits(W3), w4=W.to_bf16_bits(w4),
+             b1=z(128, np.float32), b2=z(128, np.float32), b3=z(128, np.float32), b4=0.5)
+    o.set_surrogate(m)
+    for v in (3.0, -7.0, 0.0, 11.0):
+        F = z(48, np.float32); F[0] = v
+        assert o.mlp(F) == (2 * v if v > 0 else 0.0) + 0.5
+        assert o.surrogate(F) == v
+
+
+def test_surrogate_is_exactly_antisymmetric():
+    w = W.ideal(n_sites=4, n_pairs=2)
+    o = oracle.Oracle(w)
+    o.set_surrogate(W.random_mlp(seed=5, gain=1.3))
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        F = rng.integers(-40, 40, 48).astype(np.float32)
+        assert o.surrogate(-F) == -o.surrogate(F)
+
+
+# ---------------------------------------------------------------- features: brute force
+def _cells(xyz, nc, L):
+    scf = np.float32(np.float64(nc) / np.float64(np.float32(L)))
+    c = np.floor(np.asarray(xyz, np.float32) * scf).astype(np.int64)
+    return np.clip(c, 0, nc - 1)
+
+
+def _shell(ca, cb, nc):
+    d = (cb - ca) % nc
+    d = np.where(d > nc // 2, d - nc, d)
+    if np.any(np.abs(d) > 2):
+        return -1
+    n2 = int(d @ d)
+    return n2 if n2 <= 6 else 7
+
+
+def _qeff(t, st, coupling):
+    if t == W.ACID:
+        return -1 if st else 0
+    if t == W.BASE:
+        return 1 if st else 0
+    if t == W.XP:
+        return 1 if coupling else 0
+    if t == W.XM:
+        return -1 if coupling else 0
+    return 0
+
+
+def _features(pre, changes, nc, L, coupling):
+    """48 features from the particles before a move; changes: two tuples
+    (id or None, xyz, q_old, q_new, pres_old, pres_new)."""
+    cells = _cells(pre["xyz"], nc, L)
+    F = np.zeros(48, np.int64)
+    skip = {c[0] for c in changes if c[0] is not None}
+    for s, (cid, xyz, qo, qn, po, pn) in enumerate(changes):
+        cs = _cells(np.array([xyz]), nc, L)[0]
+        dq = (qn if pn else 0) - (qo if po else 0)
+        eta = pn - po
+        for j in range(len(pre["id"])):
+            if int(pre["id"][j]) in skip:
+                continue
+            sh = _shell(cs, cells[j], nc)
+            if sh < 0:
+                continue
+            t = int(pre["type"][j])
+            q = _qeff(t, pre["state"][j], coupling)
+            if t in (W.XP, W.XM):
+                F[24 * s + sh] += dq * q
+            elif t in (W.ACID, W.BASE):
+                F[24 * s + 8 + sh] += dq * q
+            F[24 * s + 16 + sh] += eta
+    (ia, xa, qao, qan, pao, pan), (ib, xb, qbo, qbn, pbo, pbn) = changes
+    sh = _shell(_cells(np.array([xa]), nc, L)[0], _cells(np.array([xb]), nc, L)[0], nc)
+    if sh >= 0:
+        F[sh] += (qan * qbn if (pan and pbn) else 0) - (qao * qbo if (pao and pbo) else 0)
+    return F
+
+
+def test_features_match_brute_force_recount():
+    """Accepted trials (whose inserted ions appear in the next state) and every
+    site-flip / deletion trial, one trial per sweep on a small chain system."""
+    w = W.config1(seed=4, n_pairs=24, schedule=1, trials_per_domain=1)
+    o = oracle.Oracle(w)
+    o.set_surrogate(W.random_mlp(seed=2))
+    o.set_da(True)
+    g = o.geometry()
+    nc, L, coupling = g["nc"], w.params["box_L"], w.params["ion_coupling"]
+    checked = 0
+    for t in range(400):
+        pre = o.particles()
+        r = o.sweep(1, 100 + t, log=True, da_log=True, features=True)
+        rec, F = r["log"][0], r["features"][0]
+        if rec["flags"] & (oracle.F_NOELIG | oracle.F_EDGE):
+            assert not F.any()
+            continue
+        post = o.particles()
+        idx = {int(i): k for k, i in enumerate(pre["id"])}
+        pidx = {int(i): k for k, i in enumerate(post["id"])}
+        move = int(rec["move"])
+        react, fwd = move >> 1, (move & 1) == 0
+        ia, ib = int(rec["id_a"]), int(rec["id_b"])
+
+        def existing(i):
+            k = idx[i]
+            q = _qeff(int(pre["type"][k]), pre["state"][k], coupling)
+            return k, pre["xyz"][k], q
+
+        if react < 2:
+            ka, xa, qa = existing(ia)
+            qs = -1 if react == 0 else 1
+            if fwd:
+                if ib not in pidx:
+                    continue  # rejected insertion: its position is not observable here
+                xb = post["xyz"][pidx[ib]]
+                qb = -qs if coupling else 0
+                ch = [(ia, xa, 0, qs, 1, 1), (None, xb, 0, qb, 0, 1)]
+            else:
+                kb, xb, qb = existing(ib)
+                ch = [(ia, xa, qs, 0, 1, 1), (ib, xb, qb, 0, 1, 0)]
+        else:
+            if fwd:
+                if ia not in pidx:
+                    continue
+                q = 1 if coupling else 0
+                ch = [(None, post["xyz"][pidx[ia]], 0, q, 0, 1), (None, post["xyz"][pidx[ib]], 0, -q, 0, 1)]
+            else:
+                ka, xa, qa = existing(ia)
+                kb, xb, qb = existing(ib)
+                ch = [(ia, xa, qa, 0, 1, 0), (ib, xb, qb, 0, 1, 0)]
+        ref = _features(pre, ch, nc, L, coupling)
+        assert np.array_equal(F.astype(np.int64), ref), (t, move, F, ref)
+        checked += 1
+    assert checked > 100
+
+
+# ---------------------------------------------------------------- exactness of the two-stage chain
+def _da_enumeration(schedule, seed_mlp, gain, out_gain, plant=None, n_base=0):
+    n = 6
+    w = W.enum_sites(n_sites=n, L=24.0, rc=8.0, lB=2.0, pH=5.0, pKa=5.0, pIS=2.0, n_pairs=4, seed=3,
+                     n_base=n_base, schedule=schedule, trials_per_domain=64 if schedule == 1 else 2)
+    o = oracle.Oracle(w)
+    o.set_surrogate(W.random_mlp(seed=seed_mlp, gain=gain, out_gain=out_gain))
+    o.set_da(True)
+    if plant:
+        oracle.plant(plant)
+    P = enumeration_probs(w, n, o.chem())
+    tps = o.trials_per_sweep
+    o.sweep(tps * max(1, 8000 // tps), 1)
+    B, per = 16, 6144
+    H = []
+    for b in range(B):
+        h = o.sweep(tps * max(1, per // tps), 2000 + b, hist_n=n)["hist"]
+        H.append(h / h.sum())
+    H = np.array(H)
+    mean = H.mean(0)
+    se = H.std(0, ddof=1) / math.sqrt(B)
+    big = P > 0.01
+    z = np.abs(mean - P)[big] / np.maximum(se[big], 1e-4)
+    tv = 0.5 * np.abs(mean - P).sum()
+    tv_noise = 0.5 * float(np.sum(se)) * math.sqrt(2.0 / math.pi)
+    return z.max(), tv, tv_noise
+
+
+@pytest.mark.parametrize("schedule,seed_mlp,out_gain", [(1, 7, 3.0), (0, 8, 3.0), (0, 9, 0.0)])
+def test_da_chain_samples_the_exact_distribution(schedule, seed_mlp, out_gain):
+    """Whatever the surrogate (random weights of O(1) output, or zero), the
+    two-stage chain reproduces the exact enumeration of Eq. (QQ)."""
+    zmax, tv, tv_noise = _da_enumeration(schedule, seed_mlp, 1.0, out_gain)
+    assert zmax < 5.0 and tv < 3.0 * tv_noise + 0.005, (zmax, tv, tv_noise)
+
+
+@pytest.mark.parametrize("kind", ["da_one_sided", "da_stage2_full"])
+def test_planted_da_mistake_fails_exactness(kind):
+    zmax, tv, tv_noise = _da_enumeration(0, 8, 1.0, 3.0, plant=kind)
+    assert zmax >= 5.0 or tv >= 3.0 * tv_noise + 0.005, (kind, zmax, tv, tv_noise)
+
+
+def test_da_records_are_consistent():
+    """Stage bookkeeping: a stage-1 rejection is a rejection; an accepted trial
+    passed stage 1 with ln u2 < lnA2; lnA2 = dE~ - dE_pair."""
+    w = W.config1(seed=5)
+    o = oracle.Oracle(w)
+    o.set_surrogate(W.random_mlp(seed=4, out_gain=2.0))
+    o.set_da(True)
+    r = o.sweep(o.trials_per_sweep * 4, 9, log=True, da_log=True, features=True)
+    lg, da = r["log"], r["da"]
+    evald = (lg["flags"] & (oracle.F_NOELIG | oracle.F_EDGE)) == 0
+    assert np.all(da["stage"][~evald] == 0) and np.all(da["stage"][evald] > 0)
+    acc = (lg["flags"] & oracle.F_ACC) != 0
+    assert np.all(da["stage"][acc] == 2)
+    assert np.all(da["lnu2"][acc] < da["lnA2"][acc])
+    s1 = evald & (lg["lnu"] < lg["lnA"])
+    assert np.array_equal(s1, da["stage"] == 2)
+    ok = evald & np.isfinite(lg["dE"])
+    dpair = r["dE_pair"][ok]
+    assert np.allclose(da["lnA2"][ok], da["dE_sur"][ok].astype(np.float64) - dpair, rtol=0, atol=1e-12)
+    assert 0 < (da["stage"] == 1).sum() and 0 < acc.sum()
