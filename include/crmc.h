@@ -139,6 +139,47 @@ typedef struct {
   double lnu;    /* log of the Metropolis uniform */
 } cr_trial;
 
+/* ---- learned delayed acceptance (DA) ----
+ * A surrogate stage in front of the exact Metropolis test (Christen & Fox,
+ * 2005; the paper evaluates every trial exactly):
+ *   stage 1: accept with min(1, R exp(-(dE_self + dE~))), R the combinatorial
+ *            and chemical factor of the move (Sec. II.C), dE_self the exact
+ *            DSF self-term change, dE~ the surrogate pair-energy change; a
+ *            stage-1 rejection ends the trial without the exact pair sum;
+ *   stage 2: accept with min(1, exp(-(dE_pair - dE~))).
+ * The chain keeps the stationary distribution of Eq. (QQ) because dE~ is
+ * antisymmetric under move reversal: dE~ = (mlp(F) - mlp(-F)) / 2 with
+ * features F that change sign when the move is reversed.  Features (48): for
+ * each changed particle s (a = the site, or the cation of a salt move; b =
+ * the ion, or the anion) over the 5^3 half-cutoff cells around its cell,
+ * binned into 8 shells by the squared integer cell offset
+ * {0},{1},{2},{3},{4},{5},{6},{8,9,12}: dq_s x (ion charge), dq_s x (site
+ * charge) and eta_s x (particle count), every particle other than a and b
+ * counted (dq_s: charge change of s; eta_s: +1 inserted, -1 deleted, else 0);
+ * plus q_a' q_b' - q_a q_b added at the shell of b relative to a.
+ * MLP 48 -> 128 -> 128 -> 128 -> 1, ReLU, BF16 weights, FP32 biases and FP32
+ * arithmetic (one fused multiply-add per weight in input order).
+ * Needs the coloured schedule, cells_per_rc = 2 and nc >= domain_cells + 4. */
+typedef struct {
+  const uint16_t *W1;  /* [128][48] BF16 bit patterns (row = output) */
+  const float *b1;     /* [128] */
+  const uint16_t *W2;  /* [128][128] */
+  const float *b2;     /* [128] */
+  const uint16_t *W3;  /* [128][128] */
+  const float *b3;     /* [128] */
+  const uint16_t *w4;  /* [128] */
+  float b4;
+} cr_mlp;
+
+/* Per-trial record of the DA stages (alongside cr_trial, whose lnA is then
+ * the stage-1 log ratio). */
+typedef struct {
+  float dE_sur;  /* surrogate dE~ */
+  int32_t stage; /* 0 no surrogate evaluated, 1 rejected at stage 1, 2 passed stage 1 */
+  double lnA2;   /* dE~ - dE_pair (NaN on overlap) */
+  double lnu2;   /* log of the stage-2 uniform (Philox purpose 3) */
+} cr_trial_da;
+
 /* State view: counts always; arrays when non-NULL (sizes >= n, n_sites). */
 typedef struct {
   int64_t n, n_A, n_Am, n_B, n_Bp, n_Xp, n_Xm, net_charge;
@@ -174,6 +215,22 @@ int cr_sweep(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stat
 /* As cr_sweep, and writes one cr_trial per trial to the host array `log`
  * (n_trials entries).  Slower: used by the parity tests. */
 int cr_sweep_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log);
+
+/* Load the DA surrogate (host arrays, copied).  Errors: INVALID_ARG when the
+ * context's geometry does not support DA (see above). */
+int cr_set_surrogate(cr_ctx *ctx, const cr_mlp *mlp);
+
+/* As cr_sweep with delayed acceptance (needs cr_set_surrogate). */
+int cr_sweep_da(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats);
+
+/* As cr_sweep_da with per-trial records on the host: log [n_trials],
+ * dlog [n_trials] and, when non-NULL, features [48 n_trials] (the surrogate
+ * input of each trial, zeros when none was evaluated).  The exact pair sum
+ * is evaluated for every trial here (recorded in log.dE) but decides only
+ * after stage 1, as in cr_sweep_da.  Feature/energy pairs recorded here are
+ * the training data of the surrogate (dE_pair = dE~ - lnA2). */
+int cr_sweep_da_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log,
+                    cr_trial_da *dlog, float *features);
 
 /* Evaluate the conservative MD forces (DSF Coulomb + WCA + FENE) with the
  * current charges; they become readable through cr_state().force. */
@@ -268,6 +325,8 @@ typedef struct cr_batch cr_batch;
 int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n);
 /* n_sweeps sweeps on every replica (each replica runs its own trials per sweep). */
 int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed);
+/* The same with delayed acceptance (every context needs a surrogate). */
+int cr_batch_sweep_da(cr_batch *b, uint64_t n_sweeps, uint64_t seed);
 /* cr_md_step on every replica, concurrently (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed);
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);

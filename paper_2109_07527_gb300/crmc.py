@@ -68,12 +68,20 @@ class cr_info(C.Structure):
 
 TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id_b", "<u8"),
                         ("dE", "<f8"), ("S", "<f8"), ("lnA", "<f8"), ("lnu", "<f8")])
+DA_DTYPE = np.dtype([("dE_sur", "<f4"), ("stage", "<i4"), ("lnA2", "<f8"), ("lnu2", "<f8")])
+N_FEAT = 48
+
+
+class cr_mlp(C.Structure):
+    _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
+                ("W3", C.c_void_p), ("b3", C.c_void_p), ("w4", C.c_void_p), ("b4", C.c_float)]
 
 # every entry point of include/crmc.h
 EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", "cr_state", "cr_get_info",
            "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
            "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape", "cr_batch_create", "cr_batch_sweep",
-           "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy", "cr_md_forces_noalloc")
+           "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy", "cr_md_forces_noalloc",
+           "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da")
 
 _L = None
 
@@ -94,6 +102,14 @@ def _lib():
         lib.cr_md_forces.restype = C.c_int
         lib.cr_md_forces.argtypes = [P]
         lib.cr_md_step.restype = C.c_int
+        lib.cr_set_surrogate.restype = C.c_int
+        lib.cr_set_surrogate.argtypes = [P, C.POINTER(cr_mlp)]
+        lib.cr_sweep_da.restype = C.c_int
+        lib.cr_sweep_da.argtypes = [P, C.c_uint64, C.c_uint64, C.POINTER(cr_sweep_stats)]
+        lib.cr_sweep_da_log.restype = C.c_int
+        lib.cr_sweep_da_log.argtypes = [P, C.c_uint64, C.c_uint64, C.POINTER(cr_sweep_stats), P, P, P]
+        lib.cr_batch_sweep_da.restype = C.c_int
+        lib.cr_batch_sweep_da.argtypes = [P, C.c_uint64, C.c_uint64]
         lib.cr_md_forces_noalloc.restype = C.c_int
         lib.cr_md_forces_noalloc.argtypes = [P, P, P, C.c_int64]
         lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
@@ -235,6 +251,37 @@ class Context:
             out["log"] = rec
         return out
 
+    def set_surrogate(self, mlp):
+        """Surrogate weights: dict with W1 [128,48], W2, W3 [128,128], w4 [128]
+        (uint16 BF16 bit patterns), b1, b2, b3 [128] float32 and b4."""
+        k = {n: np.ascontiguousarray(mlp[n], dtype=np.uint16) for n in ("W1", "W2", "W3", "w4")}
+        k.update({n: np.ascontiguousarray(mlp[n], dtype=np.float32) for n in ("b1", "b2", "b3")})
+        m = cr_mlp(_p(k["W1"]), _p(k["b1"]), _p(k["W2"]), _p(k["b2"]), _p(k["W3"]), _p(k["b3"]), _p(k["w4"]),
+                   float(mlp["b4"]))
+        _chk(self._lib.cr_set_surrogate(self._h, C.byref(m)), "cr_set_surrogate")
+
+    def sweep_da(self, n_trials, seed, stats=False, log=False, features=False):
+        """Delayed-acceptance sweeps; log=True also returns the DA records
+        ("da") and, with features=True, the 48 surrogate inputs per trial."""
+        st = cr_sweep_stats() if stats else None
+        out = {}
+        if log:
+            n = int(n_trials)
+            rec = np.zeros(n, dtype=TRIAL_DTYPE)
+            drec = np.zeros(n, dtype=DA_DTYPE)
+            feat = np.zeros((n, N_FEAT), dtype=np.float32) if features else None
+            _chk(self._lib.cr_sweep_da_log(self._h, n, int(seed), C.byref(st) if st else None, _p(rec), _p(drec),
+                                           _p(feat)), "cr_sweep_da_log")
+            out.update(log=rec, da=drec)
+            if features:
+                out["features"] = feat
+        else:
+            _chk(self._lib.cr_sweep_da(self._h, int(n_trials), int(seed), C.byref(st) if st else None), "cr_sweep_da")
+        if st is not None:
+            out["stats"] = dict(trials=st.trials, attempts=np.array(st.attempts[:]), accepts=np.array(st.accepts[:]),
+                                no_eligible=st.no_eligible, edge=st.edge, overlap=st.overlap)
+        return out
+
     def md_forces(self):
         _chk(self._lib.cr_md_forces(self._h), "cr_md_forces")
 
@@ -311,6 +358,9 @@ class Batch:
 
     def sweep(self, n_sweeps, seed):
         _chk(self._lib.cr_batch_sweep(self._h, int(n_sweeps), int(seed)), "cr_batch_sweep")
+
+    def sweep_da(self, n_sweeps, seed):
+        _chk(self._lib.cr_batch_sweep_da(self._h, int(n_sweeps), int(seed)), "cr_batch_sweep_da")
 
     def md_step(self, n_steps, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_batch_md_step")

@@ -56,6 +56,16 @@ struct cr_ctx {
   long long *d_gs_lnk = nullptr;
   int *d_gs_info = nullptr, *d_gs_rank = nullptr;
   int *d_plist = nullptr, *d_nparts = nullptr;  // MD particle list
+  // delayed acceptance: surrogate on the device, records, its own launch-shape tuner
+  uint16_t *d_mlp_w = nullptr;
+  float *d_mlp_b = nullptr;
+  bool has_mlp = false;
+  cr_trial_da *d_dlog = nullptr;
+  float *d_feat = nullptr;
+  size_t dlog_cap = 0, feat_cap = 0;
+  int da_T = 128, da_R = 0, da_next = 0;
+  bool da_tuning = true;
+  float da_ms[4] = {};
   // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
@@ -153,7 +163,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
                   c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
-                  c->d_plist, c->d_nparts};
+                  c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info};
@@ -457,6 +467,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     c->T = 128;
     c->R = 0;  // halo in shared memory until the tuner has timed the shapes
     c->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
+    c->da_tuning = c->tuning;
   }
   P.lnmax = std::max(2 * k * k * k * cap, (int)std::min<long long>((long long)sys->capacity, 1 << 20)) + 2 * P.m + 4;
   std::vector<long long> h_lntab(P.lnmax);
@@ -470,12 +481,12 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   S.dcs = std::min(P.dcap_glob, std::max(2 * maxd, maxd + 32) + 2 * P.m);
   S.hcs = std::min(maxh + maxh / 4 + 32, 4096);
   S.lns = std::min(P.lnmax, S.dcs + 4);
-  while (phase_smem_bytes(S, 512) > (size_t)smem_max / 2 && S.dcs > 64) {
+  while (phase_smem_bytes(S, 512, false) > (size_t)smem_max / 2 && S.dcs > 64) {
     S.dcs /= 2;
     S.hcs = std::max(S.hcs / 2, 64);
     S.lns = std::min(P.lnmax, S.dcs + 4);
   }
-  if (phase_smem_bytes(S, 512) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  if (phase_smem_bytes(S, 512, false) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
   c->smem_max = smem_max;
   P.per_sweep = c->per_sweep;
   P.key_xor = 0u;
@@ -630,43 +641,85 @@ extern "C" int cr_check(cr_ctx *ctx) {
   return err_bits_to_code(bits);
 }
 
-static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log) {
+// grow a device record buffer to n entries (records of logged calls only)
+template <typename TT>
+static int grow(TT **p, size_t *cap, size_t n) {
+  if (*cap >= n) return CR_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  CR_CUDA(cudaMalloc((void **)p, sizeof(TT) * n));
+  *cap = n;
+  return CR_OK;
+}
+
+// Online launch-shape tuning (shared by plain and delayed-acceptance sweeps):
+// the first sweeps of unlogged calls time each shape of the set once (shapes
+// whose shared memory does not fit are skipped), then the fastest is kept.
+struct TuneRef {
+  int &T, &R, &next;
+  bool &on;
+  float *ms;
+};
+
+static void tune_skip(TuneRef t, const PhaseShape &S, int smem_max, bool da) {
+  while (t.on && t.next < phase_shape_count(da)) {
+    int t_, r_;
+    phase_shape(t.next, &t_, &r_, da);
+    if (phase_shape_smem(S, t_, r_, da) <= (size_t)smem_max) break;
+    t.ms[t.next++] = 1e30f;
+  }
+}
+
+static void tune_finish(TuneRef t, float ms, const PhaseShape &S, int smem_max, bool da) {
+  t.ms[t.next++] = ms;
+  tune_skip(t, S, smem_max, da);
+  if (t.next == phase_shape_count(da)) {
+    int best = 0;
+    for (int i = 1; i < phase_shape_count(da); ++i)
+      if (t.ms[i] < t.ms[best]) best = i;
+    phase_shape(best, &t.T, &t.R, da);
+    t.on = false;
+  }
+}
+
+static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log,
+                      bool da = false, cr_trial_da *dlog = nullptr, float *feat = nullptr) {
   if (!ctx) return CR_ERR_INVALID_ARG;
   if (n_trials == 0 || n_trials % (uint64_t)ctx->per_sweep != 0) return CR_ERR_INVALID_ARG;
+  if (da && !ctx->has_mlp) return CR_ERR_INVALID_ARG;
   SysParams P = ctx->P;
   cudaStream_t s = ctx->stream;
   if (stats) CR_CUDA(cudaMemsetAsync(ctx->d_stats, 0, sizeof(unsigned long long) * 16, s));
   if (log) {
-    if (ctx->log_cap < n_trials) {
-      if (ctx->d_log) cudaFree(ctx->d_log);
-      ctx->d_log = nullptr;
-      ctx->log_cap = 0;
-      CR_CUDA(cudaMalloc((void **)&ctx->d_log, sizeof(cr_trial) * n_trials));
-      ctx->log_cap = n_trials;
-    }
+    int rc = grow(&ctx->d_log, &ctx->log_cap, n_trials);
+    if (rc != CR_OK) return rc;
     P.log = ctx->d_log;
+    if (da) {
+      if ((rc = grow(&ctx->d_dlog, &ctx->dlog_cap, n_trials)) != CR_OK) return rc;
+      P.dlog = ctx->d_dlog;
+      if (feat) {
+        if ((rc = grow(&ctx->d_feat, &ctx->feat_cap, n_trials * MLP_IN)) != CR_OK) return rc;
+        P.feat_log = ctx->d_feat;
+      }
+    }
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   // the phase kernel reads the parameters from the device copy; the log
-  // pointer is set there only for logged calls
+  // pointers are set there only for logged calls
   if (log) CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice, s));
   const uint64_t n_sweeps = n_trials / (uint64_t)ctx->per_sweep;
   const uint32_t sweep0 = (uint32_t)ctx->sweep;
+  TuneRef tr = da ? TuneRef{ctx->da_T, ctx->da_R, ctx->da_next, ctx->da_tuning, ctx->da_ms}
+                  : TuneRef{ctx->T, ctx->R, ctx->tune_next, ctx->tuning, ctx->tune_ms};
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)ctx->sweep++;
-    // online tuning: the first sweeps of unlogged calls time each launch shape once
-    // shapes whose shared memory does not fit are skipped
-    while (ctx->tuning && !log && ctx->tune_next < phase_shape_count()) {
-      int t_, r_;
-      phase_shape(ctx->tune_next, &t_, &r_);
-      if (phase_shape_smem(ctx->S, t_, r_) <= (size_t)ctx->smem_max) break;
-      ctx->tune_ms[ctx->tune_next++] = 1e30f;
-    }
-    const bool tune = ctx->tuning && !log && ctx->tune_next < phase_shape_count();
-    int T = ctx->T, R = ctx->R;
+    if (!log) tune_skip(tr, ctx->S, ctx->smem_max, da);
+    const bool tune = tr.on && !log && tr.next < phase_shape_count(da);
+    int T = tr.T, R = tr.R;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
-      phase_shape(ctx->tune_next, &T, &R);
+      phase_shape(tr.next, &T, &R, da);
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
@@ -674,7 +727,7 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
     for (int col = 0; col < P.ncol; ++col) {
       int ti;
       tbegin(ctx, 0, &ti);
-      CR_CUDA(launch_phase(ctx->d_reps, 1, P.nact, ctx->S, T, R, log != nullptr, s, swc, sweep0, col, k0, k1));
+      CR_CUDA(launch_phase(ctx->d_reps, 1, P.nact, ctx->S, T, R, log != nullptr, da, s, swc, sweep0, col, k0, k1));
       tend(ctx, 0, ti);
       ctx->launches_total++;
     }
@@ -685,25 +738,14 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       cudaEventElapsedTime(&ms, e0, e1);
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      ctx->tune_ms[ctx->tune_next++] = ms;
-      while (ctx->tune_next < phase_shape_count()) {  // skip trailing shapes that do not fit
-        int t_, r_;
-        phase_shape(ctx->tune_next, &t_, &r_);
-        if (phase_shape_smem(ctx->S, t_, r_) <= (size_t)ctx->smem_max) break;
-        ctx->tune_ms[ctx->tune_next++] = 1e30f;
-      }
-      if (ctx->tune_next == phase_shape_count()) {
-        int best = 0;
-        for (int i = 1; i < phase_shape_count(); ++i)
-          if (ctx->tune_ms[i] < ctx->tune_ms[best]) best = i;
-        phase_shape(best, &ctx->T, &ctx->R);
-        ctx->tuning = false;
-      }
+      tune_finish(tr, ms, ctx->S, ctx->smem_max, da);
     }
   }
   if (log) {
     SysParams Q = ctx->P;
     Q.log = nullptr;
+    Q.dlog = nullptr;
+    Q.feat_log = nullptr;
     CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &Q, sizeof(SysParams), cudaMemcpyHostToDevice, s));
     CR_CUDA(cudaStreamSynchronize(s));
   }
@@ -711,6 +753,10 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
   ctx->fcons_valid = false;
   if (log) {
     CR_CUDA(cudaMemcpyAsync(log, ctx->d_log, sizeof(cr_trial) * n_trials, cudaMemcpyDeviceToHost, s));
+    if (da && dlog)
+      CR_CUDA(cudaMemcpyAsync(dlog, ctx->d_dlog, sizeof(cr_trial_da) * n_trials, cudaMemcpyDeviceToHost, s));
+    if (da && feat)
+      CR_CUDA(cudaMemcpyAsync(feat, ctx->d_feat, sizeof(float) * MLP_IN * n_trials, cudaMemcpyDeviceToHost, s));
   }
   if (stats) {
     unsigned long long st[16];
@@ -739,6 +785,57 @@ extern "C" int cr_sweep(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_
 extern "C" int cr_sweep_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log) {
   if (!log) return CR_ERR_INVALID_ARG;
   return sweep_impl(ctx, n_trials, seed, stats, log);
+}
+
+extern "C" int cr_sweep_da(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats) {
+  return sweep_impl(ctx, n_trials, seed, stats, nullptr, true);
+}
+
+extern "C" int cr_sweep_da_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stats *stats, cr_trial *log,
+                               cr_trial_da *dlog, float *features) {
+  if (!log || !dlog) return CR_ERR_INVALID_ARG;
+  return sweep_impl(ctx, n_trials, seed, stats, log, true, dlog, features);
+}
+
+extern "C" int cr_set_surrogate(cr_ctx *ctx, const cr_mlp *m) {
+  if (!ctx || !m || !m->W1 || !m->b1 || !m->W2 || !m->b2 || !m->W3 || !m->b3 || !m->w4) return CR_ERR_INVALID_ARG;
+  const SysParams &P0 = ctx->P;
+  // the features use the 5^3 stencil of half-cutoff cells inside the phase's region
+  if (P0.global || P0.h != 2 || P0.nc < P0.k + 4 || !std::isfinite(m->b4)) return CR_ERR_INVALID_ARG;
+  int smem_ok = 0;
+  for (int i = 0; i < phase_shape_count(true); ++i) {
+    int t, r;
+    phase_shape(i, &t, &r, true);
+    smem_ok |= phase_shape_smem(ctx->S, t, r, true) <= (size_t)ctx->smem_max;
+  }
+  if (!smem_ok) return CR_ERR_INVALID_ARG;
+  // transposed BF16 weights (WT[in][out]) and the biases
+  std::vector<uint16_t> w(MLPW_N);
+  for (int o = 0; o < MLP_H; ++o) {
+    for (int k = 0; k < MLP_IN; ++k) w[MLPW_W1 + k * MLP_H + o] = m->W1[o * MLP_IN + k];
+    for (int k = 0; k < MLP_H; ++k) {
+      w[MLPW_W2 + k * MLP_H + o] = m->W2[o * MLP_H + k];
+      w[MLPW_W3 + k * MLP_H + o] = m->W3[o * MLP_H + k];
+    }
+    w[MLPW_W4 + o] = m->w4[o];
+  }
+  std::vector<float> b(MLPB_N);
+  for (int o = 0; o < MLP_H; ++o) {
+    b[o] = m->b1[o];
+    b[MLP_H + o] = m->b2[o];
+    b[2 * MLP_H + o] = m->b3[o];
+  }
+  b[3 * MLP_H] = m->b4;
+  if (!ctx->d_mlp_w) CR_CUDA(cudaMalloc((void **)&ctx->d_mlp_w, sizeof(uint16_t) * MLPW_N));
+  if (!ctx->d_mlp_b) CR_CUDA(cudaMalloc((void **)&ctx->d_mlp_b, sizeof(float) * MLPB_N));
+  CR_CUDA(cudaMemcpyAsync(ctx->d_mlp_w, w.data(), sizeof(uint16_t) * MLPW_N, cudaMemcpyHostToDevice, ctx->stream));
+  CR_CUDA(cudaMemcpyAsync(ctx->d_mlp_b, b.data(), sizeof(float) * MLPB_N, cudaMemcpyHostToDevice, ctx->stream));
+  ctx->P.mlp_w = ctx->d_mlp_w;
+  ctx->P.mlp_b = ctx->d_mlp_b;
+  CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &ctx->P, sizeof(SysParams), cudaMemcpyHostToDevice, ctx->stream));
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->has_mlp = true;
+  return CR_OK;
 }
 
 static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64_t seed) {
@@ -958,19 +1055,32 @@ extern "C" int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs) {
   if (threads == 0) {  // re-enable tuning
     ctx->tuning = true;
     ctx->tune_next = 0;
+    ctx->da_tuning = true;
+    ctx->da_next = 0;
     return CR_OK;
   }
-  for (int i = 0; i < phase_shape_count(); ++i) {
+  bool found = false;
+  for (int i = 0; i < phase_shape_count(false); ++i) {
     int t, r;
-    phase_shape(i, &t, &r);
+    phase_shape(i, &t, &r, false);
     if (t == threads && r == regs) {
       ctx->T = t;
       ctx->R = r;
       ctx->tuning = false;
-      return CR_OK;
+      found = true;
     }
   }
-  return CR_ERR_INVALID_ARG;
+  for (int i = 0; i < phase_shape_count(true); ++i) {  // delayed-acceptance sweeps, where supported
+    int t, r;
+    phase_shape(i, &t, &r, true);
+    if (t == threads && r == regs) {
+      ctx->da_T = t;
+      ctx->da_R = r;
+      ctx->da_tuning = false;
+      found = true;
+    }
+  }
+  return found ? CR_OK : CR_ERR_INVALID_ARG;
 }
 
 extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t *regs) {
@@ -993,6 +1103,10 @@ struct cr_batch {
   bool tuning = true;
   int tune_next = 0;
   float tune_ms[16] = {};
+  int da_T = 128, da_R = 0, da_next = 0;
+  bool da_tuning = true;
+  float da_ms[4] = {};
+  std::vector<SysParams> reps;  // host copy of d_reps
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   cudaEvent_t fork = nullptr;
@@ -1027,9 +1141,11 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   b->R = 0;
   (void)maxR;
   b->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
+  b->da_tuning = b->tuning;
+  b->reps = reps;
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctxs[0]->device);
-  if (phase_smem_bytes(b->S, 512) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
+  if (phase_smem_bytes(b->S, 512, false) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
   b->smem_max = smem_max;
   if (cudaMalloc((void **)&b->d_reps, sizeof(SysParams) * n) != cudaSuccess) { delete b; return CR_ERR_NOMEM; }
   if (cudaMemcpy(b->d_reps, reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -1061,13 +1177,29 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   delete b;
 }
 
-extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
+static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool da) {
   if (!b || n_sweeps == 0) return CR_ERR_INVALID_ARG;
   cr_ctx *c0 = b->ctx[0];
   cudaStream_t s = c0->stream;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const int n = (int)b->ctx.size();
+  if (da) {  // every replica needs its surrogate; refresh the device copies of the parameters
+    bool changed = false;
+    for (int r = 0; r < n; ++r) {
+      cr_ctx *c = b->ctx[r];
+      if (!c->has_mlp) return CR_ERR_INVALID_ARG;
+      if (b->reps[r].mlp_w != c->P.mlp_w || b->reps[r].mlp_b != c->P.mlp_b) {
+        b->reps[r].mlp_w = c->P.mlp_w;
+        b->reps[r].mlp_b = c->P.mlp_b;
+        changed = true;
+      }
+    }
+    if (changed)
+      CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice, s));
+  }
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const uint32_t sweep0 = (uint32_t)c0->sweep;
+  TuneRef tr = da ? TuneRef{b->da_T, b->da_R, b->da_next, b->da_tuning, b->da_ms}
+                  : TuneRef{b->T, b->R, b->tune_next, b->tuning, b->tune_ms};
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)c0->sweep;
     for (cr_ctx *c : b->ctx) {
@@ -1075,17 +1207,12 @@ extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
       c->f_valid = false;
       c->fcons_valid = false;
     }
-    while (b->tuning && b->tune_next < phase_shape_count()) {
-      int t_, r_;
-      phase_shape(b->tune_next, &t_, &r_);
-      if (phase_shape_smem(b->S, t_, r_) <= (size_t)b->smem_max) break;
-      b->tune_ms[b->tune_next++] = 1e30f;
-    }
-    const bool tune = b->tuning && b->tune_next < phase_shape_count();
-    int T = b->T, R = b->R;
+    tune_skip(tr, b->S, b->smem_max, da);
+    const bool tune = tr.on && tr.next < phase_shape_count(da);
+    int T = tr.T, R = tr.R;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
-      phase_shape(b->tune_next, &T, &R);
+      phase_shape(tr.next, &T, &R, da);
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
@@ -1093,7 +1220,7 @@ extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
     for (int col = 0; col < b->ncol; ++col) {
       int ti;
       tbegin(c0, 0, &ti);
-      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, b->S, T, R, false, s, swc, sweep0, col, k0, k1));
+      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, b->S, T, R, false, da, s, swc, sweep0, col, k0, k1));
       tend(c0, 0, ti);
       c0->launches_total++;
     }
@@ -1104,23 +1231,18 @@ extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
       cudaEventElapsedTime(&ms, e0, e1);
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      b->tune_ms[b->tune_next++] = ms;
-      while (b->tune_next < phase_shape_count()) {
-        int t_, r_;
-        phase_shape(b->tune_next, &t_, &r_);
-        if (phase_shape_smem(b->S, t_, r_) <= (size_t)b->smem_max) break;
-        b->tune_ms[b->tune_next++] = 1e30f;
-      }
-      if (b->tune_next == phase_shape_count()) {
-        int best = 0;
-        for (int i = 1; i < phase_shape_count(); ++i)
-          if (b->tune_ms[i] < b->tune_ms[best]) best = i;
-        phase_shape(best, &b->T, &b->R);
-        b->tuning = false;
-      }
+      tune_finish(tr, ms, b->S, b->smem_max, da);
     }
   }
   return CR_OK;
+}
+
+extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
+  return batch_sweep_impl(b, n_sweeps, seed, false);
+}
+
+extern "C" int cr_batch_sweep_da(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
+  return batch_sweep_impl(b, n_sweeps, seed, true);
 }
 
 extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed) {

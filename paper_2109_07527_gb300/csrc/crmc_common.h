@@ -87,7 +87,23 @@ struct SysParams {
   int *err;                   // error bits
   cr_trial *log;              // trial records (device) or null
   long long per_sweep;        // trials per sweep (log indexing)
+  // delayed acceptance: surrogate weights (BF16, transposed: W1T [48][128],
+  // W2T, W3T [128][128], w4 [128]), biases (b1, b2, b3, b4), records
+  const uint16_t *mlp_w;
+  const float *mlp_b;
+  cr_trial_da *dlog;          // DA records (device) or null
+  float *feat_log;            // 48 features per trial (device) or null
 };
+
+// surrogate MLP sizes and the offsets of its parts in mlp_w / mlp_b
+constexpr int MLP_IN = 48;
+constexpr int MLP_H = 128;
+constexpr int MLPW_W1 = 0;
+constexpr int MLPW_W2 = MLP_IN * MLP_H;
+constexpr int MLPW_W3 = MLPW_W2 + MLP_H * MLP_H;
+constexpr int MLPW_W4 = MLPW_W3 + MLP_H * MLP_H;
+constexpr int MLPW_N = MLPW_W4 + MLP_H;
+constexpr int MLPB_N = 3 * MLP_H + 1;
 
 // Launch-wide shared-memory shape of a phase launch (the same for every CTA;
 // the maximum over the replicas of a batch).

@@ -45,13 +45,14 @@ struct LoadBufs {
   int n, n_site_map;
 };
 
-size_t phase_smem_bytes(const PhaseShape &S, int threads);
-int phase_shape_count();
-size_t phase_shape_smem(const PhaseShape &S, int threads, int regs);
-void phase_shape(int i, int *threads, int *regs);
+// phase kernel shapes (threads, halo registers); da: the delayed-acceptance set
+size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da);
+int phase_shape_count(bool da);
+size_t phase_shape_smem(const PhaseShape &S, int threads, int regs, bool da);
+void phase_shape(int i, int *threads, int *regs, bool da);
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
-                         bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,
-                         uint32_t k1);
+                         bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
+                         uint32_t k0, uint32_t k1);
 // particle list (plist, n_particles: device scratch of max_particles + 1
 // ints), then the force kernel (one warp per particle)
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,

@@ -39,6 +39,11 @@ struct TrialPre {
   float lnu_f;       // FP32 ln u (decides unless within LNU_BAND of lnA)
   int pad;
   double lnu;        // FP64 ln u (trial records only)
+  // delayed acceptance: the stage-2 uniform (Philox purpose 3)
+  uint32_t u2hi, u2lo;
+  float lnu2_f;
+  int pad2;
+  double lnu2;
 };
 
 struct Desc {
@@ -56,6 +61,9 @@ struct TrialCtl {
   long long ln_ratio_fx, dself_fx;  // 2^-48 fixed point
   float qa_o, qa_n, qb_o, qb_n;  // effective charges of the two changed particles
   int pa_o, pa_n, pb_o, pb_n;    // presence before / after
+  // delayed acceptance: in-domain cell ranks of a and b, charge and presence
+  // changes, feature group of a (0 ion, 8 site), stage-1 outcome
+  int rka, rkb, dqa, dqb, eta_a, eta_b, cat_a, go;
 };
 
 struct DomList {
@@ -309,6 +317,57 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 64;  // per-warp queue of Coulomb pair terms
 
+// Metropolis comparison ln u < lnA with lnA in 2^-48 fixed point: the FP32
+// ln u decides outside LNU_BAND, the FP64 ln u inside it
+__device__ __forceinline__ bool accept_fx(long long lnA_fx, float lnu_f, uint32_t uhi, uint32_t ulo) {
+  const long long lnu_apx = (long long)__float2int_rn(lnu_f * 16777216.0f) << 24;
+  const long long diff = lnA_fx - lnu_apx;
+  if (diff > LNU_BAND) return true;
+  if (diff < -LNU_BAND) return false;
+  return __double2ll_rn(log(unif53(uhi, ulo)) * LNFIX) < lnA_fx;
+}
+
+__device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000ll); }
+
+// ---- delayed-acceptance surrogate
+__device__ __forceinline__ float bf16_value(uint16_t w) { return __uint_as_float((uint32_t)w << 16); }
+
+// shell of a squared integer cell offset inside the 5^3 stencil:
+// {0},{1},{2},{3},{4},{5},{6},{8,9,12}
+__device__ __forceinline__ int shell_of_n2(int n2) { return n2 <= 6 ? n2 : 7; }
+
+// shell of in-domain cell rank rb relative to rank ra (-1 outside the stencil)
+__device__ __forceinline__ int shell_ranks(int ra, int rb, int k) {
+  const int dx = rb % k - ra % k, dy = (rb / k) % k - (ra / k) % k, dz = rb / (k * k) - ra / (k * k);
+  if (abs(dx) > 2 || abs(dy) > 2 || abs(dz) > 2) return -1;
+  return shell_of_n2(dx * dx + dy * dy + dz * dz);
+}
+
+// region cell of in-domain rank r shifted by (dx, dy, dz) in [-2, 2]^3
+__device__ __forceinline__ int region_of(int r, int dx, int dy, int dz, int k, int nr) {
+  int x = r % k + dx, y = (r / k) % k + dy, z = r / (k * k) + dz;
+  x += x < 0 ? nr : 0;
+  y += y < 0 ? nr : 0;
+  z += z < 0 ? nr : 0;
+  return x + nr * (y + nr * z);
+}
+
+// one dense layer with ReLU for the two input vectors x[2][n_in] -> y[2][128]:
+// each output is its bias plus one FP32 fused multiply-add per weight, in
+// input order (weights transposed, WT[k][o], so that a warp's loads coalesce)
+template <int T>
+__device__ __forceinline__ void mlp_layer(const uint16_t *__restrict__ WT, const float *__restrict__ b,
+                                          const float *x, int n_in, float *y) {
+  for (int o = threadIdx.x; o < 2 * MLP_H; o += T) {
+    const int v = o / MLP_H, i = o % MLP_H;
+    const float *xv = x + v * n_in;
+    float a = __ldg(&b[i]);
+#pragma unroll 8
+    for (int kk = 0; kk < n_in; ++kk) a = __fmaf_rn(bf16_value(__ldg(&WT[kk * MLP_H + i])), xv[kk], a);
+    y[o] = a > 0.0f ? a : 0.0f;
+  }
+}
+
 // DSF Coulomb change of one queued pair: qp * phi(r), qp = lB dq_c q_j
 template <bool WITH_S>
 __device__ __forceinline__ void coul_eval(const PairK &K, float r2, float qp, long long &acc,
@@ -430,7 +489,7 @@ __device__ __forceinline__ long long warp_allsum(long long v) {
 //   T threads per domain (T == 32: one warp, no block barriers);
 //   R > 0: halo particles in R registers per thread, R == 0: in shared memory
 // ---------------------------------------------------------------------------
-template <int T, int R, bool LOG>
+template <int T, int R, bool LOG, bool DA>
 __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
     k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
                uint32_t key0, uint32_t key1_base) {
@@ -471,6 +530,19 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   int *dcnt = (int *)take(sizeof(int) * (S.kc3 + 1));
   int *dpre = (int *)take(sizeof(int) * (S.kc3 + 1));
   float *qr2 = qbuf + warp * 2 * QCAP, *qqp = qr2 + QCAP;
+  // delayed acceptance: region cell aggregates (ion charge, site charge,
+  // particles), feature bins, the two surrogate inputs and hidden layers
+  int *aQi = nullptr, *aQs = nullptr, *aN = nullptr, *dfeat = nullptr;
+  float *fv = nullptr, *hb0 = nullptr, *hb1 = nullptr;
+  if (DA) {
+    aQi = (int *)take(sizeof(int) * (S.nr3 + 1));
+    aQs = (int *)take(sizeof(int) * (S.nr3 + 1));
+    aN = (int *)take(sizeof(int) * (S.nr3 + 1));
+    dfeat = (int *)take(sizeof(int) * MLP_IN);
+    fv = (float *)take(sizeof(float) * 2 * MLP_IN);
+    hb0 = (float *)take(sizeof(float) * 2 * MLP_H);
+    hb1 = (float *)take(sizeof(float) * 2 * MLP_H);
+  }
 
   {
     const int *src = (const int *)&reps[blockIdx.y];
@@ -593,6 +665,25 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       hpos[j] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
     }
   }
+  if (DA) {  // region cell aggregates at the start of the phase
+    for (int i = tid; i < NR; i += T) {
+      const int ix = i % nr, iy = (i / nr) % nr, iz = i / (nr * nr);
+      const int cell = region_coord(ix, org[0], k, h, nr, nc) +
+                       nc * (region_coord(iy, org[1], k, h, nr, nc) + nc * region_coord(iz, org[2], k, h, nr, nc));
+      const int cn = P.cnt[cell];
+      int qi = 0, qs = 0;
+      for (int sl = 0; sl < cn; ++sl) {
+        const int g = cell * P.cap + sl;
+        const int t = P.info[g] & INFO_TYPE_MASK;
+        const int q = __float2int_rn(P.pos[g].w);
+        if (t == CR_XP || t == CR_XM) qi += q;
+        else if (t == CR_ACID || t == CR_BASE) qs += q;
+      }
+      aQi[i] = qi;
+      aQs[i] = qs;
+      aN[i] = cn;
+    }
+  }
   if (tid == 0) misc[0] = ND;
   __syncthreads();
   if (tid < 7) misc[9 + tid] = misc[1 + tid];
@@ -636,6 +727,17 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       q.lnu_f = logf((float)(c.z >> 5) * 7.450580596923828e-09f + ((float)(c.w >> 6) + 0.5f) * 1.1102230246251565e-16f);
       q.pad = 0;
       q.lnu = LOG ? log(unif53(c.z, c.w)) : 0.0;
+      q.u2hi = q.u2lo = 0u;
+      q.lnu2_f = 0.0f;
+      q.pad2 = 0;
+      q.lnu2 = 0.0;
+      if (DA) {
+        const uint4 e = philox10(kk, (uint32_t)d, phi, 3u, key0, key1);
+        q.u2hi = e.x;
+        q.u2lo = e.y;
+        q.lnu2_f = logf((float)(e.x >> 5) * 7.450580596923828e-09f + ((float)(e.y >> 6) + 0.5f) * 1.1102230246251565e-16f);
+        q.lnu2 = LOG ? log(unif53(e.x, e.y)) : 0.0;
+      }
       tp[t] = q;
     }
     __syncthreads();
@@ -758,6 +860,16 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         s_id_a = id_a;
         s_id_b = id_b;
         s_newid = newid;
+        int rka = 0, rkb = 0;
+        if (DA && nch) {
+          if (r == R_SALT) {
+            rka = fwd ? q.rankA : L.rank[ionA];
+            rkb = fwd ? q.rankB : L.rank[ionB];
+          } else {
+            rka = L.rank[site];
+            rkb = fwd ? q.rankA : L.rank[ionA];
+          }
+        }
         if (lane == 0) {
           TrialCtl &C = *ctl;
           C.c[0] = c0;
@@ -765,11 +877,100 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
           C.nch = nch;
           C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
           C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
+          if (DA) {
+            C.rka = rka;
+            C.rkb = rkb;
+            C.dqa = (pa_n ? __float2int_rn(qa_n) : 0) - (pa_o ? __float2int_rn(qa_o) : 0);
+            C.dqb = (pb_n ? __float2int_rn(qb_n) : 0) - (pb_o ? __float2int_rn(qb_o) : 0);
+            C.eta_a = pa_n - pa_o;
+            C.eta_b = pb_n - pb_o;
+            C.cat_a = r == R_SALT ? 0 : 8;
+            C.go = 1;
+          }
         }
       }
       cta_sync<T>();
+      // ---- delayed acceptance, stage 1: surrogate features and MLP (all
+      // threads), decision in warp 0; a rejection skips the pair sweep
+      bool s1 = true;
+      float sur = 0.0f;
+      long long sur_fx = 0;
+      if (DA && ctl->nch) {
+        if (tid < MLP_IN) dfeat[tid] = 0;
+        cta_sync<T>();
+        const int rka = ctl->rka, rkb = ctl->rkb;
+        const int dqa = ctl->dqa, dqb = ctl->dqb, ea = ctl->eta_a, eb = ctl->eta_b;
+        for (int it = tid; it < 250; it += T) {  // 2 changed particles x 125 stencil cells
+          const int sb = it >= 125 ? 1 : 0;
+          const int c = it - 125 * sb;
+          const int dx = c % 5 - 2, dy = (c / 5) % 5 - 2, dz = c / 25 - 2;
+          const int ri = region_of(sb ? rkb : rka, dx, dy, dz, k, nr);
+          const int sh = shell_of_n2(dx * dx + dy * dy + dz * dz);
+          const int dq = sb ? dqb : dqa, eta = sb ? eb : ea;
+          if (dq != 0) {
+            const int qi = aQi[ri], qs = aQs[ri];
+            if (qi) atomicAdd(&dfeat[24 * sb + sh], dq * qi);
+            if (qs) atomicAdd(&dfeat[24 * sb + 8 + sh], dq * qs);
+          }
+          if (eta != 0 && aN[ri]) atomicAdd(&dfeat[24 * sb + 16 + sh], eta * aN[ri]);
+        }
+        cta_sync<T>();
+        if (tid == 0) {  // the changed particles themselves do not count; the a-b pair term
+          const TrialCtl &C = *ctl;
+          const int qao = __float2int_rn(C.qa_o), qan = __float2int_rn(C.qa_n);
+          const int qbo = __float2int_rn(C.qb_o), qbn = __float2int_rn(C.qb_n);
+          for (int sb = 0; sb < 2; ++sb) {
+            const int rs = sb ? rkb : rka, dq = sb ? dqb : dqa, eta = sb ? eb : ea;
+            for (int x = 0; x < 2; ++x) {
+              if (!(x ? C.pb_o : C.pa_o)) continue;
+              const int sh = shell_ranks(rs, x ? rkb : rka, k);
+              if (sh < 0) continue;
+              dfeat[24 * sb + (x ? 0 : C.cat_a) + sh] -= dq * (x ? qbo : qao);
+              dfeat[24 * sb + 16 + sh] -= eta;
+            }
+          }
+          const int sh = shell_ranks(rka, rkb, k);
+          if (sh >= 0) dfeat[sh] += (C.pa_n && C.pb_n ? qan * qbn : 0) - (C.pa_o && C.pb_o ? qao * qbo : 0);
+        }
+        cta_sync<T>();
+        if (tid < MLP_IN) {
+          const float f = (float)dfeat[tid];
+          fv[tid] = f;
+          fv[MLP_IN + tid] = -f;
+          if (LOG && P.feat_log) P.feat_log[(size_t)(log_dom + kk) * MLP_IN + tid] = f;
+        }
+        cta_sync<T>();
+        mlp_layer<T>(P.mlp_w + MLPW_W1, P.mlp_b, fv, MLP_IN, hb0);
+        cta_sync<T>();
+        mlp_layer<T>(P.mlp_w + MLPW_W2, P.mlp_b + MLP_H, hb0, MLP_H, hb1);
+        cta_sync<T>();
+        mlp_layer<T>(P.mlp_w + MLPW_W3, P.mlp_b + 2 * MLP_H, hb1, MLP_H, hb0);
+        cta_sync<T>();
+        if (warp == 0) {
+          float y = 0.0f;
+          if (lane < 2) {
+            y = __ldg(&P.mlp_b[3 * MLP_H]);
+            const uint16_t *w4 = P.mlp_w + MLPW_W4;
+            const float *hv = hb0 + lane * MLP_H;
+#pragma unroll 8
+            for (int kk2 = 0; kk2 < MLP_H; ++kk2) y = __fmaf_rn(bf16_value(__ldg(&w4[kk2])), hv[kk2], y);
+          }
+          const float y0 = __shfl_sync(FULL, y, 0), y1 = __shfl_sync(FULL, y, 1);
+          sur = 0.5f * (y0 - y1);
+          if (sur != sur) {
+            s1 = false;  // NaN: rejected, as a comparison with NaN is false
+          } else {
+            sur_fx = __double2ll_rn((double)fminf(fmaxf(sur, -16384.0f), 16384.0f) * LNFIX);
+            s1 = accept_fx(s_ln_ratio - s_dself - sur_fx, tp[t].lnu_f, tp[t].uhi, tp[t].ulo);
+          }
+          if (lane == 0) ctl->go = s1 ? 1 : 0;
+        }
+        cta_sync<T>();
+      } else if (DA && LOG && P.feat_log && tid < MLP_IN) {
+        P.feat_log[(size_t)(log_dom + kk) * MLP_IN + tid] = 0.0f;
+      }
       // ---- all threads: the pair-change sweep
-      const int nch = ctl->nch;
+      const int nch = (DA && !LOG && !ctl->go) ? 0 : ctl->nch;
       long long acc = 0;
       unsigned long long sacc = 0;
       int ov = 0;
@@ -844,8 +1045,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         const TrialPre &q = tp[t];
         int flags = s_flags;
         bool accept = false;
-        double dE = 0.0, Ssum = 0.0, lnA = -INFINITY;
-        if (s_nch) {
+        double dE = 0.0, Ssum = 0.0, lnA = -INFINITY, lnA2r = quiet_nan();
+        if (DA && LOG && s_nch) lnA = (double)s_ln_ratio / LNFIX - (double)s_dself / LNFIX - (double)sur;
+        if (s_nch && (!DA || LOG || s1)) {
           long long tot = acc;
           unsigned long long stot = sacc;
           int anyov = ov;
@@ -855,21 +1057,20 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             anyov = __any_sync(FULL, lane < NW && redov[lane]) ? 1 : 0;
           }
           if (anyov) {
-            flags |= CR_TRIAL_OVERLAP;
+            if (!DA || s1) flags |= CR_TRIAL_OVERLAP;  // DA: only an exact evaluation that decides
             dE = INFINITY;
           } else {
             const long long totc = tot > DE_CLAMP32 ? DE_CLAMP32 : (tot < -DE_CLAMP32 ? -DE_CLAMP32 : tot);
-            const long long lnA_fx = s_ln_ratio - ((totc << 16) + s_dself);
-            // FP32 ln u decides outside the band; inside it FP64 ln u does
-            const long long lnu_apx = (long long)__float2int_rn(q.lnu_f * 16777216.0f) << 24;
-            const long long diff = lnA_fx - lnu_apx;
-            if (diff > LNU_BAND) accept = true;
-            else if (diff < -LNU_BAND) accept = false;
-            else accept = __double2ll_rn(log(unif53(q.uhi, q.ulo)) * LNFIX) < lnA_fx;
+            if (DA) {  // stage 2: ln u2 < dE~ - dE_pair
+              if (s1) accept = accept_fx(sur_fx - (totc << 16), q.lnu2_f, q.u2hi, q.u2lo);
+            } else {
+              accept = accept_fx(s_ln_ratio - ((totc << 16) + s_dself), q.lnu_f, q.uhi, q.ulo);
+            }
             if (LOG) {
               dE = (double)tot * FIX_INV + (double)s_dself / LNFIX;
               Ssum = (double)stot * FIX_INV + fabs((double)s_dself / LNFIX);
-              lnA = (double)s_ln_ratio / LNFIX - dE;  // unclamped, for the record
+              if (!DA) lnA = (double)s_ln_ratio / LNFIX - dE;  // unclamped, for the record
+              else lnA2r = (double)sur - (double)tot * FIX_INV;
             }
           }
         }
@@ -893,6 +1094,21 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         }
         if (accept) {
           flags |= CR_TRIAL_ACCEPTED;
+          if (DA && lane == 0) {  // region aggregates follow the committed change
+            const TrialCtl &C = *ctl;
+            for (int x = 0; x < 2; ++x) {
+              const int ri = region_of(x ? C.rkb : C.rka, 0, 0, 0, k, nr);
+              int *aq = (x == 0 && C.cat_a == 8) ? aQs : aQi;
+              if (x ? C.pb_o : C.pa_o) {
+                aq[ri] -= __float2int_rn(x ? C.qb_o : C.qa_o);
+                aN[ri] -= 1;
+              }
+              if (x ? C.pb_n : C.pa_n) {
+                aq[ri] += __float2int_rn(x ? C.qb_n : C.qa_n);
+                aN[ri] += 1;
+              }
+            }
+          }
           if (r == R_ACID || r == R_BASE) {
             const float qs = r == R_ACID ? -1.0f : 1.0f;
             if (lane == 0) {
@@ -984,6 +1200,14 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             rec.lnA = lnA;
             rec.lnu = q.lnu;
             P.log[log_dom + kk] = rec;
+            if (DA && P.dlog) {
+              cr_trial_da dr;
+              dr.dE_sur = s_nch ? sur : 0.0f;
+              dr.stage = s_nch ? (s1 ? 2 : 1) : 0;
+              dr.lnA2 = lnA2r;
+              dr.lnu2 = s_nch ? q.lnu2 : quiet_nan();
+              P.dlog[log_dom + kk] = dr;
+            }
           }
         }
       }
@@ -1024,7 +1248,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-size_t phase_smem_bytes(const PhaseShape &S, int threads) {
+size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
   const size_t sizes[] = {sizeof(SysParams),
                           sizeof(float4) * S.dcs,
                           sizeof(float4) * S.dcs,
@@ -1050,21 +1274,28 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads) {
                           sizeof(int) * (S.kc3 + 1)};
   size_t b = 0;
   for (size_t x : sizes) b += (x + 15) / 16 * 16;
+  if (da) {
+    const size_t dsz[] = {sizeof(int) * (S.nr3 + 1), sizeof(int) * (S.nr3 + 1), sizeof(int) * (S.nr3 + 1),
+                          sizeof(int) * MLP_IN,      sizeof(float) * 2 * MLP_IN, sizeof(float) * 2 * MLP_H,
+                          sizeof(float) * 2 * MLP_H};
+    for (size_t x : dsz) b += (x + 15) / 16 * 16;
+  }
   return b;
 }
 
-template <int T, int R, bool LOG>
+template <int T, int R, bool LOG, bool DA>
 static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x, PhaseShape S, cudaStream_t s,
                                   uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0, uint32_t k1) {
   if (R > 0) S.hcs = 0;  // halo in registers
   static size_t attr_bytes = 0;
-  const size_t smem = phase_smem_bytes(S, T);
+  const size_t smem = phase_smem_bytes(S, T, DA);
   if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_cr_phase<T, R, LOG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_cr_phase<T, R, LOG, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  k_cr_phase<T, R, LOG><<<dim3(grid_x, n_rep), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
+  k_cr_phase<T, R, LOG, DA><<<dim3(grid_x, n_rep), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
   return cudaGetLastError();
 }
 
@@ -1072,25 +1303,34 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
 // variants the autotuner picks from
 static const int kShapes[][2] = {{32, 0}, {64, 0}, {128, 0}, {128, 4}, {256, 0}, {256, 2}, {512, 0}, {512, 1}};
 
-int phase_shape_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
-void phase_shape(int i, int *threads, int *regs) {
-  *threads = kShapes[i][0];
-  *regs = kShapes[i][1];
+// shapes with a delayed-acceptance variant (the surrogate runs on >= 128 threads)
+static const int kShapesDA[][2] = {{128, 0}, {256, 0}, {512, 0}};
+
+int phase_shape_count(bool da) {
+  return da ? (int)(sizeof(kShapesDA) / sizeof(kShapesDA[0])) : (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+}
+void phase_shape(int i, int *threads, int *regs, bool da) {
+  *threads = da ? kShapesDA[i][0] : kShapes[i][0];
+  *regs = da ? kShapesDA[i][1] : kShapes[i][1];
 }
 
-size_t phase_shape_smem(const PhaseShape &S, int threads, int regs) {
+size_t phase_shape_smem(const PhaseShape &S, int threads, int regs, bool da) {
   PhaseShape Q = S;
   if (regs > 0) Q.hcs = 0;
-  return phase_smem_bytes(Q, threads);
+  return phase_smem_bytes(Q, threads, da);
 }
 
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
-                         bool log, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0,
-                         uint32_t k1) {
+                         bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
+                         uint32_t k0, uint32_t k1) {
 #define CRMC_CASE(TT, RR)                                                                                      \
-  if (threads == TT && R == RR)                                                                                \
-    return log ? launch_phase_t<TT, RR, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1)     \
-               : launch_phase_t<TT, RR, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
+  if (!da && threads == TT && R == RR)                                                                         \
+    return log ? launch_phase_t<TT, RR, true, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1) \
+               : launch_phase_t<TT, RR, false, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
+#define CRMC_CASE_DA(TT, RR)                                                                                   \
+  if (da && threads == TT && R == RR)                                                                          \
+    return log ? launch_phase_t<TT, RR, true, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1)  \
+               : launch_phase_t<TT, RR, false, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
   CRMC_CASE(32, 0)
   CRMC_CASE(64, 0)
   CRMC_CASE(128, 0)
@@ -1099,7 +1339,11 @@ cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const P
   CRMC_CASE(256, 2)
   CRMC_CASE(512, 0)
   CRMC_CASE(512, 1)
+  CRMC_CASE_DA(128, 0)
+  CRMC_CASE_DA(256, 0)
+  CRMC_CASE_DA(512, 0)
 #undef CRMC_CASE
+#undef CRMC_CASE_DA
   return cudaErrorInvalidValue;
 }
 

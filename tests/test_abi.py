@@ -53,7 +53,7 @@ def test_struct_layouts_match_header(tmp_path):
     import subprocess
     from paper_2109_07527_gb300 import crmc
     structs = {"cr_system": crmc.cr_system, "cr_mu_ions": crmc.cr_mu_ions, "cr_sweep_stats": crmc.cr_sweep_stats,
-               "cr_state_view": crmc.cr_state_view, "cr_info": crmc.cr_info}
+               "cr_state_view": crmc.cr_state_view, "cr_info": crmc.cr_info, "cr_mlp": crmc.cr_mlp}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crmc.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
@@ -61,6 +61,9 @@ def test_struct_layouts_match_header(tmp_path):
             cf = "global" if f == "global_" else f
             lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {cf}));')
     lines.append('  printf("cr_trial %zu\\n", sizeof(cr_trial));')
+    lines.append('  printf("cr_trial_da %zu\\n", sizeof(cr_trial_da));')
+    for f in crmc.DA_DTYPE.names:
+        lines.append(f'  printf("cr_trial_da.{f} %zu\\n", offsetof(cr_trial_da, {f}));')
     lines.append("  return 0;\n}")
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -72,3 +75,6 @@ def test_struct_layouts_match_header(tmp_path):
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
     assert int(got["cr_trial"]) == crmc.TRIAL_DTYPE.itemsize
+    assert int(got["cr_trial_da"]) == crmc.DA_DTYPE.itemsize
+    for f in crmc.DA_DTYPE.names:
+        assert int(got[f"cr_trial_da.{f}"]) == crmc.DA_DTYPE.fields[f][1], f
