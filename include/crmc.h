@@ -332,6 +332,40 @@ int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);
 void cr_batch_destroy(cr_batch *b);
 
+/* ---- training of the DA surrogate (MSE on feature / pair-energy pairs, Adam) ----
+ * Every matrix product runs on the tensor cores (tcgen05.mma, BF16 operands,
+ * FP32 accumulation in tensor memory); masters, gradients and Adam moments are
+ * FP32, activations BF16.  Parameter vector order (FP32, N = 39425):
+ * W1 [128][48], b1 [128], W2 [128][128], b2, W3 [128][128], b3, w4 [128], b4. */
+typedef struct cr_trainer cr_trainer;
+typedef struct {
+  int32_t max_batch;  /* largest batch (a multiple of 128) */
+  double lr, beta1, beta2, eps;  /* Adam */
+  double target_clip; /* targets are clipped to [-clip, clip] (kT); <= 0: no clip */
+} cr_train_cfg;
+#define CR_TRAIN_N_PARAMS 39425
+int cr_train_create(cr_trainer **out, const cr_mlp *init, const cr_train_cfg *cfg);
+int cr_train_set_stream(cr_trainer *t, void *stream);
+/* One Adam step on `batch` rows (a multiple of 128, <= max_batch): X device
+ * [batch][48] FP32 features, target device [batch] FP32 pair-energy changes.
+ * loss (host, nullable): the batch's MSE before the step (synchronises). */
+int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss);
+/* Loss and gradients (host [CR_TRAIN_N_PARAMS], nullable) without an update. */
+int cr_train_gradients(cr_trainer *t, const float *X, const float *target, int32_t batch, float *grads, float *loss);
+/* Current parameters: FP32 masters (params, nullable) and the cr_mlp layout
+ * (BF16 of the masters; each pointer nullable). */
+int cr_train_get(cr_trainer *t, float *params, uint16_t *W1, float *b1, uint16_t *W2, float *b2, uint16_t *W3,
+                 float *b3, uint16_t *w4, float *b4);
+int cr_train_stats(const cr_trainer *t, int64_t *steps, int64_t *launches);
+void cr_train_destroy(cr_trainer *t);
+
+/* The tensor-core product used by the trainer, exposed for parity tests:
+ * D [M][N] (FP32, device) = A [M][K] B [N][K]^T (BF16 bit patterns, device,
+ * row-major, K a multiple of 8, N = 48 or 128); accumulate != 0 adds into D
+ * (split over K), else overwrites.  Synchronises the stream. */
+int cr_mma_bf16(const uint16_t *A, const uint16_t *B, float *D, int32_t M, int32_t N, int32_t K, int32_t accumulate,
+                void *stream);
+
 /* Philox4x32-10 on the device for n consecutive counters (c0 + i, c1, c2, c3),
  * key (k0, k1); out: host array of 4n words.  Exposed for parity tests. */
 int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,

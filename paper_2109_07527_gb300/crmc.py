@@ -81,7 +81,15 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_set_stream", "cr_check", "cr_destroy", "cr_strerror", "cr_philox", "cr_load", "cr_set_timing",
            "cr_get_timing", "cr_set_launch_shape", "cr_get_launch_shape", "cr_batch_create", "cr_batch_sweep",
            "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy", "cr_md_forces_noalloc",
-           "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da")
+           "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
+           "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
+           "cr_train_destroy", "cr_mma_bf16")
+N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
+
+
+class cr_train_cfg(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
+                ("eps", C.c_double), ("target_clip", C.c_double)]
 
 _L = None
 
@@ -102,6 +110,22 @@ def _lib():
         lib.cr_md_forces.restype = C.c_int
         lib.cr_md_forces.argtypes = [P]
         lib.cr_md_step.restype = C.c_int
+        lib.cr_train_create.restype = C.c_int
+        lib.cr_train_create.argtypes = [C.POINTER(P), C.POINTER(cr_mlp), C.POINTER(cr_train_cfg)]
+        lib.cr_train_set_stream.restype = C.c_int
+        lib.cr_train_set_stream.argtypes = [P, P]
+        lib.cr_train_step.restype = C.c_int
+        lib.cr_train_step.argtypes = [P, P, P, C.c_int32, P]
+        lib.cr_train_gradients.restype = C.c_int
+        lib.cr_train_gradients.argtypes = [P, P, P, C.c_int32, P, P]
+        lib.cr_train_get.restype = C.c_int
+        lib.cr_train_get.argtypes = [P] + [P] * 9
+        lib.cr_train_stats.restype = C.c_int
+        lib.cr_train_stats.argtypes = [P, P, P]
+        lib.cr_train_destroy.restype = None
+        lib.cr_train_destroy.argtypes = [P]
+        lib.cr_mma_bf16.restype = C.c_int
+        lib.cr_mma_bf16.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]
         lib.cr_set_surrogate.restype = C.c_int
         lib.cr_set_surrogate.argtypes = [P, C.POINTER(cr_mlp)]
         lib.cr_sweep_da.restype = C.c_int
@@ -378,3 +402,72 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def _mlp_struct(mlp):
+    k = {n: np.ascontiguousarray(mlp[n], dtype=np.uint16) for n in ("W1", "W2", "W3", "w4")}
+    k.update({n: np.ascontiguousarray(mlp[n], dtype=np.float32) for n in ("b1", "b2", "b3")})
+    m = cr_mlp(_p(k["W1"]), _p(k["b1"]), _p(k["W2"]), _p(k["b2"]), _p(k["W3"]), _p(k["b3"]), _p(k["w4"]),
+               float(mlp["b4"]))
+    return m, k
+
+
+class Trainer:
+    """Surrogate training on the tensor cores (owns one cr_trainer).  Batches
+    are device pointers (raw ints, e.g. torch tensors' data_ptr())."""
+
+    def __init__(self, mlp, max_batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, target_clip=20.0, stream=None):
+        self._lib = _lib()
+        m, keep = _mlp_struct(mlp)
+        cfg = cr_train_cfg(int(max_batch), lr, beta1, beta2, eps, target_clip)
+        h = C.c_void_p()
+        _chk(self._lib.cr_train_create(C.byref(h), C.byref(m), C.byref(cfg)), "cr_train_create")
+        self._h = h
+        st = stream if stream is not None else _torch_stream()
+        if st is not None:
+            _chk(self._lib.cr_train_set_stream(h, st), "cr_train_set_stream")
+
+    def step(self, X_ptr, t_ptr, batch, want_loss=False):
+        loss = C.c_float()
+        _chk(self._lib.cr_train_step(self._h, C.c_void_p(int(X_ptr)), C.c_void_p(int(t_ptr)), int(batch),
+                                     C.byref(loss) if want_loss else None), "cr_train_step")
+        return loss.value if want_loss else None
+
+    def gradients(self, X_ptr, t_ptr, batch):
+        g = np.zeros(N_PARAMS, np.float32)
+        loss = C.c_float()
+        _chk(self._lib.cr_train_gradients(self._h, C.c_void_p(int(X_ptr)), C.c_void_p(int(t_ptr)), int(batch),
+                                          _p(g), C.byref(loss)), "cr_train_gradients")
+        return loss.value, g
+
+    def get(self):
+        """(FP32 master vector, surrogate dict in the cr_mlp layout)."""
+        P = np.zeros(N_PARAMS, np.float32)
+        out = dict(W1=np.zeros((128, 48), np.uint16), W2=np.zeros((128, 128), np.uint16),
+                   W3=np.zeros((128, 128), np.uint16), w4=np.zeros(128, np.uint16), b1=np.zeros(128, np.float32),
+                   b2=np.zeros(128, np.float32), b3=np.zeros(128, np.float32))
+        b4 = C.c_float()
+        _chk(self._lib.cr_train_get(self._h, _p(P), _p(out["W1"]), _p(out["b1"]), _p(out["W2"]), _p(out["b2"]),
+                                    _p(out["W3"]), _p(out["b3"]), _p(out["w4"]), C.byref(b4)), "cr_train_get")
+        out["b4"] = b4.value
+        return P, out
+
+    def stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        _chk(self._lib.cr_train_stats(self._h, C.byref(a), C.byref(b)), "cr_train_stats")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cr_train_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def mma_bf16(A_ptr, B_ptr, D_ptr, M, N, K, accumulate=False, stream=None):
+    """D [M][N] = A [M][K] B [N][K]^T on the tensor cores (device pointers)."""
+    st = stream if stream is not None else _torch_stream()
+    _chk(_lib().cr_mma_bf16(C.c_void_p(int(A_ptr)), C.c_void_p(int(B_ptr)), C.c_void_p(int(D_ptr)), int(M), int(N),
+                            int(K), 1 if accumulate else 0, st), "cr_mma_bf16")

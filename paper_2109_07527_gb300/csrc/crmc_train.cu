@@ -1,0 +1,783 @@
+// crmc_train.cu -- training of the delayed-acceptance surrogate (MLP
+// 48 -> 128 -> 128 -> 128 -> 1, ReLU) by mean squared error with Adam, on the
+// fifth-generation tensor cores of sm_103a.
+//
+// Every matrix product of the forward and backward passes is one launch of
+// k_mma: D[M x N] = A[M x K] B[N x K]^T with BF16 operands that TMA stages
+// into 128-byte-swizzled shared memory (a 4-deep ring of 64-wide K slices),
+// tcgen05.mma (cta_group::1, M = 128) accumulating FP32 in tensor memory,
+// and an epilogue that reads the accumulator with tcgen05.ld and applies
+// bias + ReLU, the ReLU mask of the backward pass, the output layer and loss
+// (fused into the last forward product), or split-K atomic accumulation of
+// the weight gradients.  One warp issues the TMA copies, one thread the MMAs;
+// every wait on an mbarrier has an iteration limit after which the CTA
+// records an error, lets its copies and MMAs in flight finish (again with a
+// limit), frees its tensor memory and returns.
+//
+// Training step on a batch of B rows (B a multiple of 128), masters in FP32:
+//   H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), H3 = relu(H2 W3^T + b3)
+//   y = H3 w4 + b4, L = sum (y - t)^2 / (2B), dy = (y - t) / B
+//   G3 = dy w4^T * [H3 > 0]; gW3 = G3^T H2; G2 = (G3 W3) * [H2 > 0]; gW2 = G2^T H1
+//   G1 = (G2 W2) * [H1 > 0]; gW1 = G1^T X; gb = column sums; gw4 = H3^T dy
+//   Adam on every parameter; BF16 copies (and transposes) of the weights.
+// Activations and back-propagated errors are stored as BF16 between the
+// products (row-major and transposed, so that every operand is K-major).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "crmc.h"
+#include "crmc_common.h"
+
+namespace crmc {
+namespace {
+
+constexpr int GM = 128;          // tile rows (MMA M)
+constexpr int GK = 64;           // K per pipeline stage: one 128-byte swizzle row of BF16
+constexpr int GSTAGES = 4;
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+enum Epi { EPI_RELU = 0, EPI_MASK = 1, EPI_ATOMIC = 2, EPI_HEAD = 3, EPI_STORE = 4 };
+
+struct GemmEpi {
+  const float *bias;        // [N] (RELU, HEAD)
+  const uint16_t *mask;     // BF16 [M][ldm]: keep where > 0 (MASK)
+  int ldm;
+  uint16_t *out;            // BF16 [M][ldo] (RELU, MASK, HEAD)
+  int ldo;
+  uint16_t *outT;           // BF16 [N][ldt] (RELU, MASK, HEAD)
+  int ldt;
+  float *colsum;            // [N] column sums of the stored FP32 values (MASK)
+  float *outF;              // FP32 [M][ldf] (ATOMIC: += ; STORE: =)
+  int ldf;
+  // output layer and loss (HEAD): y = h3 . w4 + b4 per row
+  const uint16_t *w4;       // BF16 [128]
+  const float *b4;
+  const float *target;      // [M]
+  float inv_batch;
+  uint16_t *g3;             // BF16 [M][128] and [128][ldt3]: dy w4 [h3 > 0]
+  uint16_t *g3T;
+  int ldt3;
+  float *gb3, *gw4, *gb4, *loss;
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on a phase of an mbarrier: false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < SPIN_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzle layout: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;                   // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                             // descriptor version
+  d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's row (TMEM lane)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint16_t to_bf16(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float from_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int BN>
+__host__ __device__ constexpr int tmem_cols() {
+  return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+}
+
+template <int BN>
+constexpr size_t mma_smem_bytes() {
+  return 1024 + (size_t)GSTAGES * (GM * 128 + BN * 128) + 256;
+}
+
+// ---------------------------------------------------------------------------
+// D = A B^T on one 128 x BN tile (blockIdx.x, blockIdx.y) and one K range
+// (blockIdx.z) of k_split columns (a multiple of GK)
+// ---------------------------------------------------------------------------
+template <int BN, int EPI>
+__global__ void __launch_bounds__(128, 1)
+    k_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
+          int k_split, GemmEpi E) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + GSTAGES * GM * 128;
+  uint64_t *full = (uint64_t *)(sB + GSTAGES * BN * 128);
+  uint64_t *empty = full + GSTAGES;
+  uint64_t *done = empty + GSTAGES;
+  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  constexpr uint32_t TCOLS = tmem_cols<BN>();
+  constexpr uint32_t IDESC = idesc_bf16(GM, BN);
+  constexpr uint32_t STAGE_BYTES = (GM + BN) * 128;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * GM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * k_split;
+  const int kend = min(K, kbeg + k_split);
+  const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < GSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // the whole warp allocates the accumulator columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int fail = 0;
+  int issued = 0;  // producer: stages whose copies were issued
+  if (nk > 0 && warp == 0 && lane == 0) {  // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % GSTAGES;
+      if (kb >= GSTAGES && !mbar_wait(&empty[s], ((kb / GSTAGES) - 1) & 1)) {
+        fail = 1;
+        break;
+      }
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(&mapA, &full[s], sA + s * GM * 128, kbeg + kb * GK, m0);
+      tma_load_2d(&mapB, &full[s], sB + s * BN * 128, kbeg + kb * GK, n0);
+      issued = kb + 1;
+    }
+  } else if (nk > 0 && warp == 1 && lane == 0) {  // MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % GSTAGES;
+      if (!mbar_wait(&full[s], (kb / GSTAGES) & 1)) {
+        fail = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * GM * 128), b0 = smem_u32(sB + s * BN * 128);
+#pragma unroll
+      for (int kk = 0; kk < GK / 16; ++kk)
+        umma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), IDESC, (kb | kk) != 0 ? 1u : 0u);
+      umma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+    }
+    umma_commit(done);  // completes when every MMA issued above has finished
+  }
+  // everyone: wait for the accumulator (bounded), agree on failure
+  bool ok = nk == 0 || mbar_wait(done, 0);
+  fail = __syncthreads_or(fail || !ok);
+  tc_fence_after();
+
+  const int row = m0 + warp * 32 + lane;
+  const bool rv = row < M;
+  __syncwarp();
+  if (!fail && nk > 0) {
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    if constexpr (EPI == EPI_HEAD) {
+      // pass 1: h3 = relu(z3 + b3) (BF16, stored), y = h3 . w4 + b4
+      float y = 0.0f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        uint16_t hb[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          const float h = fmaxf(v[j] + E.bias[n], 0.0f);
+          hb[j] = to_bf16(h);
+          y = fmaf(from_bf16(hb[j]), from_bf16(E.w4[n]), y);
+        }
+        if (rv) {
+          uint4 *o = (uint4 *)(E.out + (size_t)row * E.ldo + n0 + c0);
+          o[0] = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16), hb[6] | (hb[7] << 16));
+          o[1] = make_uint4(hb[8] | (hb[9] << 16), hb[10] | (hb[11] << 16), hb[12] | (hb[13] << 16),
+                            hb[14] | (hb[15] << 16));
+        }
+      }
+      y += *E.b4;
+      const float diff = rv ? y - E.target[row] : 0.0f;
+      const float dy = diff * E.inv_batch;
+      const float l = warp_sum_f(0.5f * diff * diff * E.inv_batch);
+      if (lane == 0) atomicAdd(E.loss, l);
+      const float gb4 = warp_sum_f(dy);
+      if (lane == 0) atomicAdd(E.gb4, gb4);
+      // pass 2: g3 = dy w4 [h3 > 0]; column sums gb3 (of g3) and gw4 (of dy h3)
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint4 raw[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+        if (rv) {
+          const uint4 *src = (const uint4 *)(E.out + (size_t)row * E.ldo + n0 + c0);
+          raw[0] = src[0];
+          raw[1] = src[1];
+        }
+        const uint16_t *hb = (const uint16_t *)raw;
+        uint16_t gb[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          const float h = from_bf16(hb[j]);
+          const float g = h > 0.0f ? dy * from_bf16(E.w4[n]) : 0.0f;
+          gb[j] = to_bf16(g);
+          if (rv) E.g3T[(size_t)n * E.ldt3 + row] = gb[j];
+          const float sg = warp_sum_f(g), sw = warp_sum_f(dy * h);
+          if (lane == 0) {
+            atomicAdd(&E.gb3[n], sg);
+            atomicAdd(&E.gw4[n], sw);
+          }
+        }
+        if (rv) {
+          uint4 *o = (uint4 *)(E.g3 + (size_t)row * 128 + n0 + c0);
+          o[0] = make_uint4(gb[0] | (gb[1] << 16), gb[2] | (gb[3] << 16), gb[4] | (gb[5] << 16), gb[6] | (gb[7] << 16));
+          o[1] = make_uint4(gb[8] | (gb[9] << 16), gb[10] | (gb[11] << 16), gb[12] | (gb[13] << 16),
+                            gb[14] | (gb[15] << 16));
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        if constexpr (EPI == EPI_ATOMIC || EPI == EPI_STORE) {
+          if (rv) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < N) {
+                if (EPI == EPI_ATOMIC) atomicAdd(&E.outF[(size_t)row * E.ldf + n], v[j]);
+                else E.outF[(size_t)row * E.ldf + n] = v[j];
+              }
+            }
+          }
+        } else {
+        uint16_t hb[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = n0 + c0 + j;
+          float x;
+          if (EPI == EPI_RELU) {
+            x = fmaxf(v[j] + E.bias[n], 0.0f);
+          } else {  // EPI_MASK
+            const float mk = rv ? from_bf16(E.mask[(size_t)row * E.ldm + n]) : 0.0f;
+            x = mk > 0.0f ? v[j] : 0.0f;
+            const float cs = warp_sum_f(rv ? x : 0.0f);
+            if (lane == 0) atomicAdd(&E.colsum[n], cs);
+          }
+          hb[j] = to_bf16(x);
+          if (rv && E.outT) E.outT[(size_t)n * E.ldt + row] = hb[j];
+        }
+        if (rv && E.out) {
+          uint4 *o = (uint4 *)(E.out + (size_t)row * E.ldo + n0 + c0);
+          o[0] = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16), hb[6] | (hb[7] << 16));
+          o[1] = make_uint4(hb[8] | (hb[9] << 16), hb[10] | (hb[11] << 16), hb[12] | (hb[13] << 16),
+                            hb[14] | (hb[15] << 16));
+        }
+        }
+      }
+    }
+  }
+  if (fail) {
+    // let this CTA's copies in flight land before its shared memory goes away
+    if (warp == 0 && lane == 0)
+      for (int kb = max(0, issued - GSTAGES); kb < issued; ++kb) mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1);
+    if (threadIdx.x == 0) atomicOr(E.err, ERRB_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  __syncwarp();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+// X (FP32 [B][48]) -> BF16 Xb [B][64] (zero padded) and XbT [48][B]; targets clipped
+__global__ void k_prep(const float *X, const float *t, int B, float clip, uint16_t *Xb, uint16_t *XbT, float *tc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * 64) return;
+  const int r = i / 64, c = i % 64;
+  const uint16_t v = c < MLP_IN ? to_bf16(X[(size_t)r * MLP_IN + c]) : (uint16_t)0;
+  Xb[(size_t)r * 64 + c] = v;
+  if (c < MLP_IN) XbT[(size_t)c * B + r] = v;
+  if (c == 0) tc[r] = fminf(fmaxf(t[r], -clip), clip);
+}
+
+// parameter layout of the masters, gradients and Adam moments
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + MLP_H * MLP_IN, OFF_W2 = OFF_B1 + MLP_H, OFF_B2 = OFF_W2 + MLP_H * MLP_H,
+              OFF_W3 = OFF_B2 + MLP_H, OFF_B3 = OFF_W3 + MLP_H * MLP_H, OFF_W4 = OFF_B3 + MLP_H,
+              OFF_B4 = OFF_W4 + MLP_H, N_PARAMS = OFF_B4 + 1;
+
+struct Bf16Copies {
+  uint16_t *W1p;  // [128][64] (K padded)
+  uint16_t *W2, *W2T, *W3, *W3T, *w4;
+};
+
+// BF16 copies of the masters (and transposes), as the products take them
+__global__ void k_weights_bf16(const float *P, Bf16Copies C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < MLP_H * 64) {
+    const int o = i / 64, k = i % 64;
+    C.W1p[i] = k < MLP_IN ? to_bf16(P[OFF_W1 + o * MLP_IN + k]) : (uint16_t)0;
+  }
+  if (i < MLP_H * MLP_H) {
+    const int o = i / MLP_H, k = i % MLP_H;
+    const uint16_t a = to_bf16(P[OFF_W2 + i]), b = to_bf16(P[OFF_W3 + i]);
+    C.W2[i] = a;
+    C.W3[i] = b;
+    C.W2T[k * MLP_H + o] = a;
+    C.W3T[k * MLP_H + o] = b;
+  }
+  if (i < MLP_H) C.w4[i] = to_bf16(P[OFF_W4 + i]);
+}
+
+// Adam (bias-corrected) on every master parameter
+__global__ void k_adam(float *P, const float *G, float *Mm, float *Vv, int n, float lr, float beta1, float beta2,
+                       float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = G[i];
+  const float m = beta1 * Mm[i] + (1.0f - beta1) * g;
+  const float v = beta2 * Vv[i] + (1.0f - beta2) * g * g;
+  Mm[i] = m;
+  Vv[i] = v;
+  P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mutex;
+
+int get_encode() {
+  std::lock_guard<std::mutex> lock(g_encode_mutex);
+  if (g_encode) return CR_OK;
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn)
+    return CR_ERR_CUDA;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return CR_OK;
+}
+
+// 2D BF16 tensor [rows][cols] (cols contiguous), box of GK columns x box_rows
+int make_map(CUtensorMap *map, const uint16_t *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  if (((uintptr_t)base & 15) || (cols * 2) % 16) return CR_ERR_INVALID_ARG;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)GK, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? CR_OK : CR_ERR_INVALID_ARG;
+}
+
+template <int BN, int EPI>
+int launch_mma(const uint16_t *A, const uint16_t *Bm, int M, int N, int K, int lda, int ldb, int k_split,
+               const GemmEpi &E, cudaStream_t s) {
+  CUtensorMap ma, mb;
+  int rc = make_map(&ma, A, (uint64_t)M, (uint64_t)lda, GM);
+  if (rc == CR_OK) rc = make_map(&mb, Bm, (uint64_t)N, (uint64_t)ldb, BN);
+  if (rc != CR_OK) return rc;
+  static bool attr = false;
+  const size_t smem = mma_smem_bytes<BN>();
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_mma<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return CR_ERR_CUDA;
+    attr = true;
+  }
+  const int splits = (K + k_split - 1) / k_split;
+  dim3 grid((M + GM - 1) / GM, (N + BN - 1) / BN, splits);
+  k_mma<BN, EPI><<<grid, 128, smem, s>>>(ma, mb, M, N, K, k_split, E);
+  return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
+// split of a long K (weight gradients) over about one wave of CTAs
+int split_for(int K, int tiles) {
+  int per = (K + 151) / 152 * std::max(tiles, 1);
+  per = (per + GK - 1) / GK * GK;
+  return std::max(per, GK);
+}
+
+}  // namespace
+}  // namespace crmc
+
+using namespace crmc;
+
+struct cr_trainer {
+  int max_batch = 0;
+  double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8, clip = 20.0;
+  long long step = 0;
+  cudaStream_t stream = nullptr;
+  float *P = nullptr, *G = nullptr, *Mm = nullptr, *Vv = nullptr, *loss = nullptr, *tc = nullptr;
+  int *err = nullptr;
+  uint16_t *Xb = nullptr, *XbT = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1T = nullptr, *H2T = nullptr,
+           *G3 = nullptr, *G3T = nullptr, *G2 = nullptr, *G2T = nullptr, *G1T = nullptr;
+  uint16_t *wb = nullptr;  // BF16 weight copies (one block)
+  Bf16Copies C{};
+  int64_t launches = 0;
+};
+
+static void free_trainer(cr_trainer *t) {
+  if (!t) return;
+  void *ptrs[] = {t->P,  t->G,   t->Mm,  t->Vv, t->tc,  t->err, t->Xb, t->XbT, t->H1, t->H2,
+                  t->H3, t->H1T, t->H2T, t->G3, t->G3T, t->G2,  t->G2T, t->G1T, t->wb};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete t;
+}
+
+extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train_cfg *cfg) {
+  if (!out || !m || !cfg || cfg->max_batch <= 0 || cfg->max_batch % 128 || !m->W1 || !m->b1 || !m->W2 || !m->b2 ||
+      !m->W3 || !m->b3 || !m->w4)
+    return CR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (get_encode() != CR_OK) return CR_ERR_CUDA;
+  cr_trainer *t = new (std::nothrow) cr_trainer();
+  if (!t) return CR_ERR_NOMEM;
+  t->max_batch = cfg->max_batch;
+  t->lr = cfg->lr;
+  t->beta1 = cfg->beta1;
+  t->beta2 = cfg->beta2;
+  t->eps = cfg->eps;
+  t->clip = cfg->target_clip > 0.0 ? cfg->target_clip : 1e30;
+  const size_t B = (size_t)cfg->max_batch;
+  bool ok = true;
+  auto al = [&](auto **p, size_t n) {
+    if (ok && cudaMalloc((void **)p, n * sizeof(**p)) != cudaSuccess) ok = false;
+  };
+  al(&t->P, N_PARAMS);
+  al(&t->G, N_PARAMS + 1);  // + loss
+  al(&t->Mm, N_PARAMS);
+  al(&t->Vv, N_PARAMS);
+  al(&t->tc, B);
+  al(&t->err, 1);
+  al(&t->Xb, B * 64);
+  al(&t->XbT, B * MLP_IN);
+  for (uint16_t **p : {&t->H1, &t->H2, &t->H3, &t->H1T, &t->H2T, &t->G3, &t->G3T, &t->G2, &t->G2T, &t->G1T})
+    al(p, B * MLP_H);
+  al(&t->wb, (size_t)MLP_H * 64 + 4 * MLP_H * MLP_H + MLP_H);
+  if (!ok) {
+    free_trainer(t);
+    return CR_ERR_NOMEM;
+  }
+  t->loss = t->G + N_PARAMS;
+  t->C.W1p = t->wb;
+  t->C.W2 = t->C.W1p + MLP_H * 64;
+  t->C.W2T = t->C.W2 + MLP_H * MLP_H;
+  t->C.W3 = t->C.W2T + MLP_H * MLP_H;
+  t->C.W3T = t->C.W3 + MLP_H * MLP_H;
+  t->C.w4 = t->C.W3T + MLP_H * MLP_H;
+  // masters from the BF16 initial weights
+  std::vector<float> h(N_PARAMS);
+  auto bf = [](uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+  };
+  for (int i = 0; i < MLP_H * MLP_IN; ++i) h[OFF_W1 + i] = bf(m->W1[i]);
+  for (int i = 0; i < MLP_H * MLP_H; ++i) {
+    h[OFF_W2 + i] = bf(m->W2[i]);
+    h[OFF_W3 + i] = bf(m->W3[i]);
+  }
+  for (int i = 0; i < MLP_H; ++i) {
+    h[OFF_B1 + i] = m->b1[i];
+    h[OFF_B2 + i] = m->b2[i];
+    h[OFF_B3 + i] = m->b3[i];
+    h[OFF_W4 + i] = bf(m->w4[i]);
+  }
+  h[OFF_B4] = m->b4;
+  if (cudaMemcpy(t->P, h.data(), sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(t->Mm, 0, sizeof(float) * N_PARAMS) != cudaSuccess ||
+      cudaMemset(t->Vv, 0, sizeof(float) * N_PARAMS) != cudaSuccess || cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) {
+    free_trainer(t);
+    return CR_ERR_CUDA;
+  }
+  k_weights_bf16<<<(MLP_H * MLP_H + 255) / 256, 256>>>(t->P, t->C);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    free_trainer(t);
+    return CR_ERR_CUDA;
+  }
+  *out = t;
+  return CR_OK;
+}
+
+extern "C" void cr_train_destroy(cr_trainer *t) {
+  if (!t) return;
+  cudaStreamSynchronize(t->stream);
+  free_trainer(t);
+}
+
+extern "C" int cr_train_set_stream(cr_trainer *t, void *stream) {
+  if (!t) return CR_ERR_INVALID_ARG;
+  t->stream = (cudaStream_t)stream;
+  return CR_OK;
+}
+
+// forward + backward of one batch into t->G (and t->loss); device inputs
+static int train_grads(cr_trainer *t, const float *X, const float *target, int B) {
+  if (!t || !X || !target || B <= 0 || B % 128 || B > t->max_batch) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = t->stream;
+  if (cudaMemsetAsync(t->G, 0, sizeof(float) * (N_PARAMS + 1), s) != cudaSuccess) return CR_ERR_CUDA;
+  k_prep<<<(B * 64 + 255) / 256, 256, 0, s>>>(X, target, B, (float)t->clip, t->Xb, t->XbT, t->tc);
+  t->launches++;
+  const float *P = t->P;
+  float *G = t->G;
+  int rc;
+  GemmEpi E{};
+  E.err = t->err;
+  // H1 = relu(X W1^T + b1)
+  E.bias = P + OFF_B1;
+  E.out = t->H1;
+  E.ldo = MLP_H;
+  E.outT = t->H1T;
+  E.ldt = B;
+  if ((rc = launch_mma<128, EPI_RELU>(t->Xb, t->C.W1p, B, MLP_H, 64, 64, 64, 64, E, s)) != CR_OK) return rc;
+  // H2 = relu(H1 W2^T + b2)
+  E.bias = P + OFF_B2;
+  E.out = t->H2;
+  E.outT = t->H2T;
+  if ((rc = launch_mma<128, EPI_RELU>(t->H1, t->C.W2, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, E, s)) != CR_OK) return rc;
+  // H3 = relu(H2 W3^T + b3), then the output layer, the loss and G3 = dL/dz3
+  GemmEpi H{};
+  H.err = t->err;
+  H.bias = P + OFF_B3;
+  H.out = t->H3;
+  H.ldo = MLP_H;
+  H.w4 = t->C.w4;
+  H.b4 = P + OFF_B4;
+  H.target = t->tc;
+  H.inv_batch = 1.0f / (float)B;
+  H.g3 = t->G3;
+  H.g3T = t->G3T;
+  H.ldt3 = B;
+  H.gb3 = G + OFF_B3;
+  H.gw4 = G + OFF_W4;
+  H.gb4 = G + OFF_B4;
+  H.loss = t->loss;
+  if ((rc = launch_mma<128, EPI_HEAD>(t->H2, t->C.W3, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, H, s)) != CR_OK) return rc;
+  // gW3 = G3^T H2 (K = batch, split over the SMs)
+  GemmEpi A{};
+  A.err = t->err;
+  A.outF = G + OFF_W3;
+  A.ldf = MLP_H;
+  const int ks = split_for(B, 1);
+  if ((rc = launch_mma<128, EPI_ATOMIC>(t->G3T, t->H2T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  // G2 = (G3 W3) * [H2 > 0]; gb2
+  GemmEpi Mk{};
+  Mk.err = t->err;
+  Mk.mask = t->H2;
+  Mk.ldm = MLP_H;
+  Mk.out = t->G2;
+  Mk.ldo = MLP_H;
+  Mk.outT = t->G2T;
+  Mk.ldt = B;
+  Mk.colsum = G + OFF_B2;
+  if ((rc = launch_mma<128, EPI_MASK>(t->G3, t->C.W3T, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, Mk, s)) != CR_OK) return rc;
+  // gW2 = G2^T H1
+  A.outF = G + OFF_W2;
+  if ((rc = launch_mma<128, EPI_ATOMIC>(t->G2T, t->H1T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  // G1 = (G2 W2) * [H1 > 0] (transposed only); gb1
+  Mk.mask = t->H1;
+  Mk.out = nullptr;
+  Mk.outT = t->G1T;
+  Mk.colsum = G + OFF_B1;
+  if ((rc = launch_mma<128, EPI_MASK>(t->G2, t->C.W2T, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, Mk, s)) != CR_OK) return rc;
+  // gW1 = G1^T X
+  A.outF = G + OFF_W1;
+  A.ldf = MLP_IN;
+  if ((rc = launch_mma<48, EPI_ATOMIC>(t->G1T, t->XbT, MLP_H, MLP_IN, B, B, B, ks, A, s)) != CR_OK) return rc;
+  t->launches += 8;
+  return CR_OK;
+}
+
+static int train_check(cr_trainer *t) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, t->err, sizeof(int), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaStreamSynchronize(t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  return (e & ERRB_TIMEOUT) ? CR_ERR_TIMEOUT : CR_OK;
+}
+
+extern "C" int cr_train_gradients(cr_trainer *t, const float *X, const float *target, int32_t batch, float *grads,
+                                  float *loss) {
+  int rc = train_grads(t, X, target, batch);
+  if (rc != CR_OK) return rc;
+  if (grads && cudaMemcpyAsync(grads, t->G, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  if (loss && cudaMemcpyAsync(loss, t->loss, sizeof(float), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  return train_check(t);
+}
+
+extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss) {
+  int rc = train_grads(t, X, target, batch);
+  if (rc != CR_OK) return rc;
+  t->step++;
+  const double c1 = 1.0 - std::pow(t->beta1, (double)t->step), c2 = 1.0 - std::pow(t->beta2, (double)t->step);
+  k_adam<<<(N_PARAMS + 255) / 256, 256, 0, t->stream>>>(t->P, t->G, t->Mm, t->Vv, N_PARAMS, (float)t->lr,
+                                                         (float)t->beta1, (float)t->beta2, (float)t->eps, (float)c1,
+                                                         (float)c2);
+  k_weights_bf16<<<(MLP_H * MLP_H + 255) / 256, 256, 0, t->stream>>>(t->P, t->C);
+  t->launches += 2;
+  if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;
+  if (loss) {
+    if (cudaMemcpyAsync(loss, t->loss, sizeof(float), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+      return CR_ERR_CUDA;
+    return train_check(t);
+  }
+  return CR_OK;
+}
+
+extern "C" int cr_train_get(cr_trainer *t, float *params, uint16_t *W1, float *b1, uint16_t *W2, float *b2,
+                            uint16_t *W3, float *b3, uint16_t *w4, float *b4) {
+  if (!t) return CR_ERR_INVALID_ARG;
+  std::vector<float> h(N_PARAMS);
+  if (cudaMemcpyAsync(h.data(), t->P, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess ||
+      cudaStreamSynchronize(t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  if (params) std::memcpy(params, h.data(), sizeof(float) * N_PARAMS);
+  auto tb = [](float f) {  // round to nearest even BF16
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+  };
+  for (int i = 0; i < MLP_H * MLP_IN; ++i)
+    if (W1) W1[i] = tb(h[OFF_W1 + i]);
+  for (int i = 0; i < MLP_H * MLP_H; ++i) {
+    if (W2) W2[i] = tb(h[OFF_W2 + i]);
+    if (W3) W3[i] = tb(h[OFF_W3 + i]);
+  }
+  for (int i = 0; i < MLP_H; ++i) {
+    if (b1) b1[i] = h[OFF_B1 + i];
+    if (b2) b2[i] = h[OFF_B2 + i];
+    if (b3) b3[i] = h[OFF_B3 + i];
+    if (w4) w4[i] = tb(h[OFF_W4 + i]);
+  }
+  if (b4) *b4 = h[OFF_B4];
+  return CR_OK;
+}
+
+extern "C" int cr_train_stats(const cr_trainer *t, int64_t *steps, int64_t *launches) {
+  if (!t) return CR_ERR_INVALID_ARG;
+  if (steps) *steps = t->step;
+  if (launches) *launches = t->launches;
+  return CR_OK;
+}
+
+extern "C" int cr_mma_bf16(const uint16_t *A, const uint16_t *B, float *D, int32_t M, int32_t N, int32_t K,
+                           int32_t accumulate, void *stream) {
+  if (!A || !B || !D || M <= 0 || K <= 0 || K % 8 || !(N == 48 || N == 128)) return CR_ERR_INVALID_ARG;
+  if (get_encode() != CR_OK) return CR_ERR_CUDA;
+  static int *d_err = nullptr;
+  if (!d_err) {
+    if (cudaMalloc((void **)&d_err, sizeof(int)) != cudaSuccess) return CR_ERR_NOMEM;
+    cudaMemset(d_err, 0, sizeof(int));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  GemmEpi E{};
+  E.err = d_err;
+  E.outF = D;
+  E.ldf = N;
+  const int tiles = (M + GM - 1) / GM;
+  const int ks = accumulate ? split_for(K, tiles) : ((K + GK - 1) / GK) * GK;
+  int rc = N == 48 ? (accumulate ? launch_mma<48, EPI_ATOMIC>(A, B, M, N, K, K, K, ks, E, s)
+                                 : launch_mma<48, EPI_STORE>(A, B, M, N, K, K, K, ks, E, s))
+                   : (accumulate ? launch_mma<128, EPI_ATOMIC>(A, B, M, N, K, K, K, ks, E, s)
+                                 : launch_mma<128, EPI_STORE>(A, B, M, N, K, K, K, ks, E, s));
+  if (rc != CR_OK) return rc;
+  int e = 0;
+  if (cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CR_ERR_CUDA;
+  if (e) {
+    cudaMemset(d_err, 0, sizeof(int));
+    return CR_ERR_TIMEOUT;
+  }
+  return CR_OK;
+}
