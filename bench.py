@@ -8,7 +8,10 @@ batch (one phase launch per colour covers all of them), synthetic seeded
 coordinates.  One step = one MD/CR-MC cycle of every replica: 10^4 CR-MC trials
 (one sweep of 1000 domains x 10 trials) + one velocity-Verlet/Langevin MD step
 (dt = 0.005, gamma = 1); the full job is 100 steps (10^6 trials per replica).
-The single-replica (pH 4.5) plain path is reported beside it.  Inputs are
+The single-replica (pH 4.5) plain path is reported beside it, and the
+surrogate delayed-acceptance path ("surrogate_da"): training pairs recorded by
+logged DA sweeps, the MLP trained on the tensor cores (throughput against the
+BF16 tensor peak), then the same batched cycle with DA sweeps.  Inputs are
 resident in HBM; L2 is flushed (256 MB write) between timed steps.
 
 --impl reference times the CPU oracle on the same workload (rank 0 only).
@@ -36,6 +39,7 @@ WORKLOAD = ("polyelectrolyte solution, pH swept 2..8 in steps of 0.5 (13 replica
             "acid beads (pKa 4.5), L=120 sigma, ~4000 ion pairs, rc=12, lB=2, DSF alpha=0.2; step = 1e4 CR-MC trials "
             "per replica (1000 domains x 10) + 1 MD step (dt 0.005, gamma 1) per replica")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -46,6 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-da", action="store_true")
     return ap.parse_args()
 
 
@@ -213,6 +218,108 @@ def ph_sweep_workloads(rank):
     return out
 
 
+def measured_tensor_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("bf16_tflops", "bf16_TFLOPs"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except (OSError, ValueError):
+            pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
+
+
+# floating-point operations of one training row (algorithmic, K = 48 input):
+# forward 48x128 + 2 x 128x128, backward 4 x 128x128 + 128x48, 2 flops per MAC
+TRAIN_FLOPS_PER_ROW = 2 * (48 * 128 + 2 * 128 * 128) + 2 * (4 * 128 * 128 + 128 * 48)
+
+
+def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
+    """Surrogate delayed acceptance: record (feature, pair-energy) pairs with
+    logged DA sweeps (zero surrogate: stage 1 is the chemistry alone), train the
+    MLP on the tensor cores, then time the batched DA cycle with it."""
+    from paper_2109_07527_gb300 import workloads as W
+    rng = np.random.default_rng(0)
+    gd = crmc.Context(ws[5])  # pH 4.5
+    gd.set_surrogate(W.random_mlp(seed=5, out_gain=0.0))
+    X, y = [], []
+    for s in range(12):
+        r = gd.sweep_da(gd.trials_per_sweep, 40 + s, log=True, features=True)
+        ok = (r["da"]["stage"] > 0) & np.isfinite(r["da"]["lnA2"])
+        X.append(r["features"][ok])
+        y.append(r["da"]["dE_sur"][ok].astype(np.float64) - r["da"]["lnA2"][ok])
+        gd.md_step(1, dt, gamma, 60 + s)
+    X = np.concatenate(X)
+    y = np.concatenate(y).astype(np.float32)
+    n_hold = len(X) // 10
+    Xh, yh = X[:n_hold], y[:n_hold]
+    X, y = np.concatenate([X[n_hold:], -X[n_hold:]]), np.concatenate([y[n_hold:], -y[n_hold:]])
+    perm = rng.permutation(len(X))
+    X, y = X[perm], y[perm]
+    Bt = 8192
+    nb = len(X) // Bt
+    Xd = torch.from_numpy(np.ascontiguousarray(X[:nb * Bt])).cuda()
+    yd = torch.from_numpy(np.ascontiguousarray(y[:nb * Bt])).cuda()
+    tr = crmc.Trainer(W.random_mlp(seed=6, gain=0.5), max_batch=Bt, lr=1e-3, target_clip=20.0)
+    loss0 = tr.step(Xd.data_ptr(), yd.data_ptr(), Bt, want_loss=True)
+    n_train = 300
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(n_train):
+        b = k % nb
+        tr.step(Xd.data_ptr() + b * Bt * 48 * 4, yd.data_ptr() + b * Bt * 4, Bt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_ms = e0.elapsed_time(e1)
+    loss_end = tr.step(Xd.data_ptr(), yd.data_ptr(), Bt, want_loss=True)
+    _, mlp = tr.get()
+    tpeak, tkind = measured_tensor_peak()
+    tflops = n_train * Bt * TRAIN_FLOPS_PER_ROW / (t_ms / 1e3) / 1e12
+    # held-out error of the antisymmetrised surrogate (oracle-free: the library's own DA records)
+    gd.set_surrogate(mlp)
+    r = gd.sweep_da(gd.trials_per_sweep, 999, log=True, features=False)
+    ev = r["da"]["stage"] > 0
+    stage1_reject = float(np.mean(r["da"]["stage"][ev] == 1))
+    fin = ev & np.isfinite(r["da"]["lnA2"])
+    err = np.abs(r["da"]["lnA2"][fin])  # |dE~ - dE_pair|
+    sur_err = {"median_kT": float(np.median(err)), "frac_within_1kT": float(np.mean(err < 1.0))}
+    gd.close()
+    # batched DA cycle, same step definition as the plain batch
+    ctxs = [crmc.Context(w) for w in ws]
+    for c in ctxs:
+        c.set_surrogate(mlp)
+    b = crmc.Batch(ctxs)
+    b.sweep_da(3, 0xDA)  # launch-shape tuning of the DA variant
+    for s in range(3):
+        b.sweep_da(1, 1 + s)
+        b.md_step(1, dt, gamma, 1000 + s)
+
+    def step(s):
+        b.sweep_da(1, 200 + s)
+        b.md_step(1, dt, gamma, 6000 + s)
+
+    ms = time_steps(step, steps, stream, flush)
+    for c in ctxs:
+        c.check()
+    per_step = ctxs[0].trials_per_sweep * len(ctxs)
+    out = {"value": per_step * steps / (ms / 1e3), "unit": "trials/s", "steps": steps, "ms_per_step": ms / steps,
+           "launch_shape": None, "stage1_reject_frac": stage1_reject, "surrogate_error": sur_err,
+           "alpha_end": [round(c.counts()["alpha"], 4) for c in ctxs],
+           "train": {"rows": int(nb * Bt), "batch": Bt, "steps": n_train, "ms": t_ms,
+                     "rows_per_s": n_train * Bt / (t_ms / 1e3), "loss_first": loss0, "loss_end": loss_end,
+                     "held_out_pairs": int(n_hold),
+                     "roofline": {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+                                  "frac": tflops / tpeak, "peak_source": tkind,
+                                  "flops_per_row": TRAIN_FLOPS_PER_ROW}}}
+    b.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def time_steps(step_fn, steps, stream, flush):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -322,6 +429,10 @@ def run_ours(args):
                  "md_force_ms_per_step": tm1["md_ms"] / n_plain, "alpha_end": c1["alpha"]}
         g1.close()
 
+    da = None
+    if rank == 0 and not args.no_da:
+        da = run_da(crmc, torch, stream, flush, ws, dt, gamma, max(10, min(args.steps, 50)))
+
     # ---- end to end through the public API with host buffers: each step
     # uploads every replica's configuration from pinned host memory (cr_load),
     # runs the batched cycle and reads every replica's state back (cr_state)
@@ -370,6 +481,7 @@ def run_ours(args):
                       "particles_end": [c["n"] for c in counts],
                       "parallelism": f"{world} GPU(s), independent replica batches"},
            "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e, "plain": plain,
+           "surrogate_da": da,
            "md_cr_cycles_per_s": args.steps * world / (ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(workload(0))
