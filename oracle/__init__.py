@@ -97,6 +97,9 @@ def _load():
         lib.or_forces.argtypes = [P, P, P]
         lib.or_md_step.restype = C.c_int32
         lib.or_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        for f in ("or_md_begin", "or_md_end"):
+            getattr(lib, f).restype = C.c_int32
+            getattr(lib, f).argtypes = [P, C.c_double, C.c_double, C.c_uint64]
         lib.or_set_positions.restype = C.c_int32
         lib.or_set_positions.argtypes = [P, P, P, P, C.c_int32]
         lib.or_philox.argtypes = [P, P, P]
@@ -301,6 +304,18 @@ class Oracle:
         rc = self._lib.or_md_step(self._h, int(n_steps), float(dt), float(gamma), C.c_uint64(seed))
         if rc != 0:
             raise RuntimeError(f"or_md_step failed with code {rc}")
+
+    def md_begin(self, dt, gamma, seed):
+        """First half of an MD step (forces if stale, half kick, drift)."""
+        rc = self._lib.or_md_begin(self._h, float(dt), float(gamma), C.c_uint64(seed))
+        if rc != 0:
+            raise RuntimeError(f"or_md_begin failed with code {rc}")
+
+    def md_end(self, dt, gamma, seed):
+        """Second half of an MD step (forces with the current charges, half kick)."""
+        rc = self._lib.or_md_end(self._h, float(dt), float(gamma), C.c_uint64(seed))
+        if rc != 0:
+            raise RuntimeError(f"or_md_end failed with code {rc}")
 
     def set_positions(self, ids, xyz, vel=None):
         ids = np.ascontiguousarray(ids, dtype=np.uint64)

@@ -530,13 +530,28 @@ static void remove_particle(Oracle *o, int j) {
   o->n--;
 }
 
-static int add_ion(Oracle *o, int t, float x, float y, float z, uint64_t id) {
+/* Maxwell-Boltzmann velocity of an inserted ion (unit mass, kT = 1): three
+ * normal deviates by the Box-Muller transform of the four 24-bit uniforms of
+ * the Philox block (k, d, phase, purpose), purpose 6 for the first inserted
+ * ion of a trial and 7 for the second. */
+static void ion_velocity(const uint32_t key[2], int k, int d, uint32_t phi, uint32_t purpose, double v[3]) {
+  uint32_t c[4] = {(uint32_t)k, (uint32_t)d, phi, purpose}, w[4];
+  philox(c, key, w);
+  double u[4];
+  for (int i = 0; i < 4; ++i) u[i] = (double)(((float)(w[i] >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  double r1 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
+  v[0] = r1 * cos(2.0 * M_PI * u[1]);
+  v[1] = r1 * sin(2.0 * M_PI * u[1]);
+  v[2] = r2 * cos(2.0 * M_PI * u[3]);
+}
+
+static int add_ion(Oracle *o, int t, float x, float y, float z, uint64_t id, const double v[3]) {
   if (o->n >= o->cap) return OR_ERR_CAPACITY;
   int j = o->n++;
   o->x[j] = x; o->y[j] = y; o->z[j] = z;
   o->type[j] = t; o->cls[j] = o->ion_coupling ? o->ion_cls : CLS_NONE;
   o->site[j] = -1; o->st[j] = 0; o->id[j] = id;
-  o->vx[j] = o->vy[j] = o->vz[j] = 0.0;
+  o->vx[j] = v[0]; o->vy[j] = v[1]; o->vz[j] = v[2];
   o->fx[j] = o->fy[j] = o->fz[j] = 0.0;
   return OR_OK;
 }
@@ -877,18 +892,21 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
     o->stats[6 + t.move]++;
     int s_before = 0;
     if (hist_n > 0) for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0 && o->site[j] < hist_n && o->st[j]) s_before |= 1 << o->site[j];
+    double va[3], vb[3];
+    ion_velocity(key, k, d, phi, 6u, va);
+    ion_velocity(key, k, d, phi, 7u, vb);
     if (r == R_ACID || r == R_BASE) {
       if (fwd) {
         o->st[site] = 1;
-        if (add_ion(o, r == R_ACID ? T_XP : T_XM, pa[0], pa[1], pa[2], idA)) return OR_ERR_CAPACITY;
+        if (add_ion(o, r == R_ACID ? T_XP : T_XM, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
       } else {
         o->st[site] = 0;
         remove_particle(o, ionA);
       }
     } else {
       if (fwd) {
-        if (add_ion(o, T_XP, pa[0], pa[1], pa[2], idA)) return OR_ERR_CAPACITY;
-        if (add_ion(o, T_XM, pb[0], pb[1], pb[2], idB)) return OR_ERR_CAPACITY;
+        if (add_ion(o, T_XP, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
+        if (add_ion(o, T_XM, pb[0], pb[1], pb[2], idB, vb)) return OR_ERR_CAPACITY;
       } else {
         int hi = ionA > ionB ? ionA : ionB, lo = ionA > ionB ? ionB : ionA;
         remove_particle(o, hi);
@@ -1161,6 +1179,46 @@ int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t
 
 /* overwrite positions / velocities from id-sorted arrays (used to re-sync the
  * oracle to a state before a parity window) */
+/* The MD step split around a CR-MC call: or_md_begin evaluates the forces
+ * if a CR-MC call changed the system since the last evaluation, then does
+ * the first half kick and the drift; or_md_end evaluates the forces (with the
+ * charges after any CR-MC trials run in between) and does the closing half
+ * kick.  begin + end with nothing in between is or_md_step with one step. */
+int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
+  double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
+  int rc = OR_OK;
+  if (!o->f_valid) {
+    rc = forces_cons(o, F, NULL);
+    if (rc) { free(F); return rc; }
+    langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
+    for (int j = 0; j < o->n; ++j) { o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2]; }
+  }
+  for (int j = 0; j < o->n; ++j) {
+    o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
+    o->x[j] = wrapf(o, (double)o->x[j] + dt * o->vx[j]);
+    o->y[j] = wrapf(o, (double)o->y[j] + dt * o->vy[j]);
+    o->z[j] = wrapf(o, (double)o->z[j] + dt * o->vz[j]);
+  }
+  o->f_valid = 0;
+  free(F);
+  return rc;
+}
+
+int32_t or_md_end(Oracle *o, double dt, double gamma, uint64_t seed) {
+  double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
+  int rc = forces_cons(o, F, NULL);
+  if (!rc) {
+    langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
+    for (int j = 0; j < o->n; ++j) {
+      o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2];
+      o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
+    }
+    o->f_valid = 1;
+  }
+  free(F);
+  return rc;
+}
+
 int32_t or_set_positions(Oracle *o, const uint64_t *ids, const float *xyz, const float *vel, int32_t n) {
   if (n != o->n) return OR_ERR_ARG;
   for (int j = 0; j < o->n; ++j) {

@@ -78,3 +78,37 @@ def test_langevin_thermalises_ideal_gas():
         ke.append(float((v * v).mean()))
     T = float(np.mean(ke))
     assert abs(T - 1.0) < 0.05, T
+
+
+def test_split_step_equals_md_step():
+    """md_begin + md_end with nothing in between is exactly one md_step."""
+    w = W.config1(seed=9, n_pairs=16)
+    a, b = oracle.Oracle(w), oracle.Oracle(w)
+    for s in range(3):
+        a.md_step(1, 0.005, 1.0, 77)
+        b.md_begin(0.005, 1.0, 77)
+        b.md_end(0.005, 1.0, 77)
+    pa, pb = a.particles(), b.particles()
+    assert np.array_equal(pa["xyz"], pb["xyz"]) and np.array_equal(pa["vel"], pb["vel"])
+
+
+def test_cycles_with_trials_inside_the_step_keep_the_temperature():
+    """CR-MC trials between the drift and the force evaluation (one force
+    evaluation per cycle) leave the Langevin temperature at kT = 1."""
+    w = W.config1(seed=10, n_pairs=24)
+    o = oracle.Oracle(w, trials_per_domain=2)
+    n = o.trials_per_sweep
+    for s in range(150):
+        o.md_begin(0.005, 1.0, 5)
+        o.sweep(n, 100 + s)
+        o.md_end(0.005, 1.0, 5)
+    ke = []
+    for s in range(300):
+        o.md_begin(0.005, 1.0, 5)
+        o.sweep(n, 1000 + s)
+        o.md_end(0.005, 1.0, 5)
+        if s % 10 == 0:
+            v = o.particles()["vel"]
+            ke.append(float((v * v).mean()))
+    T = float(np.mean(ke))
+    assert abs(T - 1.0) < 0.08, T
