@@ -5,9 +5,11 @@ Workload: the polyelectrolyte solution the metric is quoted on -- 16 chains x
 200 acid beads (pKa 4.5), L = 120 sigma, ~4000 ion pairs, r_c = 12 sigma,
 l_B = 2 sigma -- titrated at pH 2.0, 2.5, ..., 8.0: 13 replicas advanced as one
 batch (one phase launch per colour covers all of them), synthetic seeded
-coordinates.  One step = one MD/CR-MC cycle of every replica: 10^4 CR-MC trials
-(one sweep of 1000 domains x 10 trials) + one velocity-Verlet/Langevin MD step
-(dt = 0.005, gamma = 1); the full job is 100 steps (10^6 trials per replica).
+coordinates.  One step = one MD/CR-MC cycle of every replica: one
+velocity-Verlet/Langevin MD step (dt = 0.005, gamma = 1) with 10^4 CR-MC trials
+(one sweep of 1000 domains x 10 trials) between its drift and its force
+evaluation, so that one force evaluation serves both; the full job is 100 steps
+(10^6 trials per replica).
 The single-replica (pH 4.5) plain path is reported beside it, and the
 surrogate delayed-acceptance path ("surrogate_da"): training pairs recorded by
 logged DA sweeps, the MLP trained on the tensor cores (throughput against the
@@ -37,7 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "CR-MC trials/s on 1 GB300 (plain vs surrogate-DA/batched) at |Δα|≤0.005"
 WORKLOAD = ("polyelectrolyte solution, pH swept 2..8 in steps of 0.5 (13 replicas in one batch): 16 chains x 200 "
             "acid beads (pKa 4.5), L=120 sigma, ~4000 ion pairs, rc=12, lB=2, DSF alpha=0.2; step = 1e4 CR-MC trials "
-            "per replica (1000 domains x 10) + 1 MD step (dt 0.005, gamma 1) per replica")
+            "per replica (1000 domains x 10) inside 1 MD step (dt 0.005, gamma 1; the trials run between the drift "
+            "and the force evaluation, one force evaluation per step) per replica")
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 
@@ -294,12 +297,14 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     b = crmc.Batch(ctxs)
     b.sweep_da(3, 0xDA)  # launch-shape tuning of the DA variant
     for s in range(3):
+        b.md_begin(dt, gamma, 1000 + s)
         b.sweep_da(1, 1 + s)
-        b.md_step(1, dt, gamma, 1000 + s)
+        b.md_end(dt, gamma, 1000 + s)
 
     def step(s):
+        b.md_begin(dt, gamma, 6000 + s)
         b.sweep_da(1, 200 + s)
-        b.md_step(1, dt, gamma, 6000 + s)
+        b.md_end(dt, gamma, 6000 + s)
 
     ms = time_steps(step, steps, stream, flush)
     for c in ctxs:
@@ -356,8 +361,9 @@ def run_ours(args):
     per_step = per_rep * len(ctxs)
     batch.sweep(8, 0xABC)  # launch-shape tuning (one shape per sweep)
     for s in range(args.warmup):
+        batch.md_begin(dt, gamma, 1000 + s)
         batch.sweep(1, 1 + s)
-        batch.md_step(1, dt, gamma, 1000 + s)
+        batch.md_end(dt, gamma, 1000 + s)
     for g in ctxs:
         g.check()
     if world > 1:
@@ -368,9 +374,10 @@ def run_ours(args):
     g0.set_timing(True)
     g0.timing(reset=True)
 
-    def step(s):
+    def step(s):  # one MD step with the replicas' trials between its drift and its force evaluation
+        batch.md_begin(dt, gamma, 5000 + s)
         batch.sweep(1, 100 + s)
-        batch.md_step(1, dt, gamma, 5000 + s)
+        batch.md_end(dt, gamma, 5000 + s)
 
     ms = time_steps(step, args.steps, stream, flush)
     if world > 1:
@@ -407,15 +414,17 @@ def run_ours(args):
         g1 = crmc.Context(w1)
         g1.sweep(g1.trials_per_sweep * 8, 0xABC)
         for s in range(3):
+            g1.md_begin(dt, gamma, 1000 + s)
             g1.sweep(g1.trials_per_sweep, 1 + s)
-            g1.md_step(1, dt, gamma, 1000 + s)
+            g1.md_end(dt, gamma, 1000 + s)
         g1.set_timing(True)
         g1.timing(reset=True)
         n_plain = max(10, min(args.steps, 50))
 
         def step1(s):
+            g1.md_begin(dt, gamma, 7000 + s)
             g1.sweep(g1.trials_per_sweep, 300 + s)
-            g1.md_step(1, dt, gamma, 7000 + s)
+            g1.md_end(dt, gamma, 7000 + s)
 
         ms1 = time_steps(step1, n_plain, stream, flush)
         tm1 = g1.timing(reset=True)
@@ -455,8 +464,9 @@ def run_ours(args):
             for g, (n, hx, hv, ht, hc, hst) in zip(ctxs, hs):
                 g.load(n, hx.data_ptr(), hv.data_ptr(), ht.data_ptr(), hc.data_ptr(), hst.data_ptr())
                 h2d += n * (12 + 12 + 4 + 4 + 1)
+            batch.md_begin(dt, gamma, 9500 + s)
             batch.sweep(1, 9000 + s)
-            batch.md_step(1, dt, gamma, 9500 + s)
+            batch.md_end(dt, gamma, 9500 + s)
             outs = [g.state() for g in ctxs]
             d2h += sum(int(o["n"]) * (16 + 16 + 8 + 4) + 64 for o in outs)
             hs = [host_state(o) for o in outs]

@@ -242,6 +242,17 @@ int cr_md_forces(cr_ctx *ctx);
  * BOND_BROKEN, CELL_OVERFLOW. */
 int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
 
+/* One MD step split around CR-MC calls, so that a cycle of trials and one MD
+ * step needs a single force evaluation: cr_md_begin evaluates the forces if
+ * CR-MC changed the system since the last evaluation, then does the first
+ * half kick and the drift (and rebuilds the cells); CR-MC calls may follow;
+ * cr_md_end evaluates the forces with the current charges (Langevin terms
+ * included) and does the closing half kick.  begin + end with nothing in
+ * between equals cr_md_step with one step.  Inserted ions carry
+ * Maxwell-Boltzmann velocities (unit mass, kT = 1). */
+int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
+int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
+
 /* The force evaluation of cr_md_forces, allocating nothing, with the results
  * written to caller-owned device memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot let a library allocate device
@@ -329,6 +340,9 @@ int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed);
 int cr_batch_sweep_da(cr_batch *b, uint64_t n_sweeps, uint64_t seed);
 /* cr_md_step on every replica, concurrently (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed);
+/* cr_md_begin / cr_md_end on every replica (replica r uses seed ^ (r << 32)). */
+int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed);
+int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);
 void cr_batch_destroy(cr_batch *b);
 

@@ -83,7 +83,8 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_batch_md_step", "cr_batch_get_launch_shape", "cr_batch_destroy", "cr_md_forces_noalloc",
            "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
-           "cr_train_destroy", "cr_mma_bf16")
+           "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
+           "cr_batch_md_end")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -110,6 +111,9 @@ def _lib():
         lib.cr_md_forces.restype = C.c_int
         lib.cr_md_forces.argtypes = [P]
         lib.cr_md_step.restype = C.c_int
+        for f in ("cr_md_begin", "cr_md_end", "cr_batch_md_begin", "cr_batch_md_end"):
+            getattr(lib, f).restype = C.c_int
+            getattr(lib, f).argtypes = [P, C.c_double, C.c_double, C.c_uint64]
         lib.cr_train_create.restype = C.c_int
         lib.cr_train_create.argtypes = [C.POINTER(P), C.POINTER(cr_mlp), C.POINTER(cr_train_cfg)]
         lib.cr_train_set_stream.restype = C.c_int
@@ -315,6 +319,12 @@ class Context:
         _chk(self._lib.cr_md_forces_noalloc(self._h, C.c_void_p(int(force_ptr)), C.c_void_p(int(id_ptr)),
                                             int(n_slots)), "cr_md_forces_noalloc")
 
+    def md_begin(self, dt, gamma, seed):
+        _chk(self._lib.cr_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_md_begin")
+
+    def md_end(self, dt, gamma, seed):
+        _chk(self._lib.cr_md_end(self._h, float(dt), float(gamma), int(seed)), "cr_md_end")
+
     def md_step(self, n_steps, dt, gamma, seed):
         _chk(self._lib.cr_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_md_step")
 
@@ -388,6 +398,12 @@ class Batch:
 
     def md_step(self, n_steps, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_step(self._h, int(n_steps), float(dt), float(gamma), int(seed)), "cr_batch_md_step")
+
+    def md_begin(self, dt, gamma, seed):
+        _chk(self._lib.cr_batch_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_begin")
+
+    def md_end(self, dt, gamma, seed):
+        _chk(self._lib.cr_batch_md_end(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_end")
 
     def launch_shape(self):
         t = C.c_int32()

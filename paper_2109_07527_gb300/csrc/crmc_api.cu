@@ -899,6 +899,35 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
   return CR_OK;
 }
 
+extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
+  if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  const SysParams &P = ctx->P;
+  RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
+  int rc;
+  if (!ctx->f_valid) {
+    if ((rc = md_force_eval(ctx, md_params(ctx, 1, dt, gamma, seed))) != CR_OK) return rc;
+    ctx->md_eval++;
+  }
+  MdParams M = md_params(ctx, 2, dt, gamma, seed);
+  CR_CUDA(launch_kick_drift(P, M, s));
+  CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
+  ctx->launches_total += 3;
+  ctx->f_valid = false;  // positions moved: the closing kick needs new forces
+  ctx->fcons_valid = false;
+  return CR_OK;
+}
+
+extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
+  if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = md_force_eval(ctx, md_params(ctx, 2, dt, gamma, seed))) != CR_OK) return rc;
+  ctx->md_eval++;
+  ctx->f_valid = true;
+  ctx->fcons_valid = false;
+  return CR_OK;
+}
+
 extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   if (!ctx || !out) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
@@ -1245,7 +1274,9 @@ extern "C" int cr_batch_sweep_da(cr_batch *b, uint64_t n_sweeps, uint64_t seed) 
   return batch_sweep_impl(b, n_sweeps, seed, true);
 }
 
-extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+// run an MD call on every replica of a batch, concurrently on per-replica streams
+template <typename Fn>
+static int batch_md(cr_batch *b, Fn fn) {
   if (!b) return CR_ERR_INVALID_ARG;
   cudaStream_t s = b->ctx[0]->stream;
   CR_CUDA(cudaEventRecord(b->fork, s));
@@ -1256,7 +1287,7 @@ extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double 
     c->stream = b->streams[r];
     const bool timing = c->timing;
     c->timing = false;
-    const int e = cr_md_step(c, n_steps, dt, gamma, seed ^ ((uint64_t)r << 32));
+    const int e = fn(c, (uint64_t)r);
     c->timing = timing;
     c->stream = s;
     if (e != CR_OK && rc == CR_OK) rc = e;
@@ -1266,6 +1297,18 @@ extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double 
     if (r > 0) c->launches_total = 0;
   }
   return rc;
+}
+
+extern "C" int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+  return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_step(c, n_steps, dt, gamma, seed ^ (r << 32)); });
+}
+
+extern "C" int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed) {
+  return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_begin(c, dt, gamma, seed ^ (r << 32)); });
+}
+
+extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed) {
+  return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
 }
 
 extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs) {

@@ -327,6 +327,23 @@ __device__ __forceinline__ bool accept_fx(long long lnA_fx, float lnu_f, uint32_
   return __double2ll_rn(log(unif53(uhi, ulo)) * LNFIX) < lnA_fx;
 }
 
+// Maxwell-Boltzmann velocity of an inserted ion (unit mass, kT = 1): Box-Muller
+// on the four 24-bit uniforms of Philox block (trial, domain, phase, purpose),
+// purpose 6 for the first inserted ion of a trial and 7 for the second
+__device__ __noinline__ float4 ion_velocity(uint32_t k, uint32_t d, uint32_t phi, uint32_t purpose, uint32_t key0,
+                                           uint32_t key1) {
+  const uint4 w = philox10(k, d, phi, purpose, key0, key1);
+  const float u0 = ((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u1 = ((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = ((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u3 = ((float)(w.w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float r1 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s3, &c3);
+  return make_float4(r1 * c1, r1 * s1, r2 * c3, 0.0f);
+}
+
 __device__ __forceinline__ double quiet_nan() { return __longlong_as_double(0x7ff8000000000000ll); }
 
 // ---- delayed-acceptance surrogate
@@ -1121,7 +1138,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
-                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
                 L.id[p] = s_newid;
                 L.lnk[p] = 0;
                 L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
@@ -1145,7 +1162,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
-                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
                 L.id[p] = s_newid;
                 L.lnk[p] = 0;
                 L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
@@ -1159,7 +1176,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               warp_insert_gap(L, n, p);
               if (lane == 0) {
                 L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
-                L.vel[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 7u, key0, key1);
                 L.id[p] = s_newid + 1u;
                 L.lnk[p] = 0;
                 L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);

@@ -1,0 +1,96 @@
+"""The MD step split around CR-MC calls (one force evaluation per MD/CR-MC
+cycle), through the C ABI, against the oracle's split step.
+
+  * md_begin + md_end with nothing in between equals md_step, bitwise;
+  * cycles begin -> CR-MC sweeps -> end match the oracle: the trials decision
+    by decision (the oracle is synchronised to the GPU positions after the
+    drift, where MD has rounded differently), then positions and velocities
+    within the MD tolerances after the closing kick;
+  * a batch of replicas equals the same calls on each context alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_07527_gb300 import workloads as W
+from parity_util import STRUCT_FLAGS, de_tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crmc():
+    from paper_2109_07527_gb300 import crmc as m
+    m._lib()
+    return m
+
+
+def _wrapdiff(a, b, L):
+    d = a.astype(np.float64) - b.astype(np.float64)
+    return d - L * np.round(d / L)
+
+
+def test_split_step_equals_md_step(crmc):
+    w = W.config1(seed=9, n_pairs=16)
+    a, b = crmc.Context(w), crmc.Context(w)
+    a.sweep(a.trials_per_sweep, 3)
+    b.sweep(b.trials_per_sweep, 3)
+    for s in range(3):
+        a.md_step(1, 0.005, 1.0, 77)
+        b.md_begin(0.005, 1.0, 77)
+        b.md_end(0.005, 1.0, 77)
+    sa, sb = a.state(), b.state()
+    for k in ("id", "xyz", "vel"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_cycles_match_oracle(crmc):
+    w = W.config1(seed=6, n_pairs=32)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    L = float(np.float32(w.params["box_L"]))
+    n = g.trials_per_sweep * 2
+    inserted = 0
+    for cyc in range(5):
+        g.md_begin(0.005, 1.0, 77)
+        o.md_begin(0.005, 1.0, 77)
+        sg, so = g.state(), o.particles()
+        assert np.array_equal(sg["id"], so["id"])
+        assert np.abs(_wrapdiff(sg["xyz"], so["xyz"], L)).max() < 2e-5
+        assert np.abs(sg["vel"] - so["vel"]).max() < 2e-4
+        o.set_positions(sg["id"], sg["xyz"], sg["vel"])
+        lg = g.sweep(n, 10 + cyc, log=True)["log"]
+        lo = o.sweep(n, 10 + cyc, log=True)["log"]
+        assert np.array_equal(lg["move"], lo["move"])
+        assert np.array_equal(lg["flags"] & STRUCT_FLAGS, lo["flags"] & STRUCT_FLAGS)
+        assert np.array_equal(lg["flags"], lo["flags"]), np.flatnonzero(lg["flags"] != lo["flags"])[:4]
+        assert np.array_equal(lg["id_a"], lo["id_a"]) and np.array_equal(lg["id_b"], lo["id_b"])
+        ok = (lo["flags"] & STRUCT_FLAGS) == 0
+        assert np.all(np.abs(lg["dE"][ok] - lo["dE"][ok]) <= de_tol(lo[ok]))
+        inserted += int(np.sum((lg["flags"] & oracle.F_ACC) != 0))
+        g.md_end(0.005, 1.0, 77)
+        o.md_end(0.005, 1.0, 77)
+        sg, so = g.state(), o.particles()
+        assert np.array_equal(sg["id"], so["id"])
+        assert np.abs(_wrapdiff(sg["xyz"], so["xyz"], L)).max() < 2e-5
+        assert np.abs(sg["vel"] - so["vel"]).max() < 2e-4  # includes inserted ions' drawn velocities
+    assert inserted > 0
+
+
+def test_batch_split_step_equals_single_contexts(crmc):
+    ws = [W.config2(seed=8, scale=0.5, pH=pH) for pH in (3.0, 6.0)]
+    single = [crmc.Context(w) for w in ws]
+    batched = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(batched)
+    for cyc in range(3):
+        b.md_begin(0.005, 1.0, 40 + cyc)
+        b.sweep(1, 50 + cyc)
+        b.md_end(0.005, 1.0, 40 + cyc)
+        for r, c in enumerate(single):
+            c.md_begin(0.005, 1.0, (40 + cyc) ^ (r << 32))
+            c.sweep(c.trials_per_sweep, (50 + cyc) ^ (r << 32))
+            c.md_end(0.005, 1.0, (40 + cyc) ^ (r << 32))
+    for c1, c2 in zip(single, batched):
+        s1, s2 = c1.state(), c2.state()
+        for k in ("id", "xyz", "vel", "state"):
+            assert np.array_equal(s1[k], s2[k]), k
