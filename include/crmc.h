@@ -107,6 +107,8 @@ typedef struct {
   int32_t schedule;        /* CR_SCHED_COLOURED or CR_SCHED_GLOBAL */
   int32_t nc;              /* cells per dimension; 0 = automatic */
   int32_t cell_capacity;   /* slots per cell; 0 = automatic */
+  int32_t list_capacity;   /* domain particles held in shared memory per CTA; 0 = automatic */
+  int32_t halo_capacity;   /* halo particles held on chip per CTA; 0 = automatic */
 } cr_system;
 
 /* Reservoir ions: pI_S of the symmetric salt per sign and pKw; with

@@ -39,7 +39,7 @@ class cr_system(C.Structure):
                 ("dsf_alpha", C.c_double), ("dsf_self", C.c_int32), ("ion_coupling", C.c_int32),
                 ("ion_cls", C.c_int32), ("cells_per_rc", C.c_int32), ("domain_cells", C.c_int32),
                 ("trials_per_domain", C.c_int32), ("schedule", C.c_int32), ("nc", C.c_int32),
-                ("cell_capacity", C.c_int32)]
+                ("cell_capacity", C.c_int32), ("list_capacity", C.c_int32), ("halo_capacity", C.c_int32)]
 
 
 class cr_mu_ions(C.Structure):
@@ -208,7 +208,8 @@ def _torch_stream():
 class Context:
     """A CR-MC system on the GPU (owns one cr_ctx)."""
 
-    def __init__(self, w, schedule=None, trials_per_domain=None, domain_cells=None, cell_capacity=0, stream=None):
+    def __init__(self, w, schedule=None, trials_per_domain=None, domain_cells=None, cell_capacity=0, stream=None,
+                 list_capacity=0, halo_capacity=0):
         lib = _lib()
         q = w.params
         s = cr_system()
@@ -232,6 +233,8 @@ class Context:
         s.schedule = int(schedule if schedule is not None else q["schedule"])
         s.nc = int(q.get("nc", 0))
         s.cell_capacity = int(cell_capacity)
+        s.list_capacity = int(list_capacity)
+        s.halo_capacity = int(halo_capacity)
         mu = cr_mu_ions(q["pIS_plus"], q["pIS_minus"], q["pKw"], int(q.get("pIX_explicit", 0)),
                         q.get("pIX_plus", 0.0), q.get("pIX_minus", 0.0))
         h = C.c_void_p()

@@ -478,8 +478,15 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   PhaseShape &S = c->S;
   S.nr3 = P.nr * P.nr * P.nr;
   S.kc3 = k * k * k;
-  S.dcs = std::min(P.dcap_glob, std::max(2 * maxd, maxd + 32) + 2 * P.m);
-  S.hcs = std::min(maxh + maxh / 4 + 32, 4096);
+  // Shared-memory list and halo capacities: the densest domain of the
+  // starting configuration with room for growth, and its densest halo (with
+  // a smaller capacity, denser domains keep their list in a global scratch
+  // region and read the halo beyond it from global memory: measured slower
+  // on the benchmark box, where several CTAs per SM do not hide the extra
+  // latency).  list_capacity / halo_capacity > 0 override the choice.
+  S.dcs = sys->list_capacity > 0 ? sys->list_capacity + 2 * P.m : std::max(2 * maxd, maxd + 32) + 2 * P.m;
+  S.dcs = std::min(P.dcap_glob, S.dcs);
+  S.hcs = sys->halo_capacity > 0 ? sys->halo_capacity : std::min(maxh + maxh / 4 + 32, 4096);
   S.lns = std::min(P.lnmax, S.dcs + 4);
   while (phase_smem_bytes(S, 512, false) > (size_t)smem_max / 2 && S.dcs > 64) {
     S.dcs /= 2;

@@ -117,3 +117,8 @@ def test_da_rejects_unsupported_geometry(crmc):
     g2 = crmc.Context(W.config1(seed=1))
     with pytest.raises(crmc.CrError):
         g2.sweep_da(g2.trials_per_sweep, 1)  # no surrogate loaded
+
+
+def test_da_parity_with_lists_beyond_shared_memory(crmc):
+    w = W.config2(seed=9, scale=0.5)
+    _da_parity(crmc, w, W.random_mlp(seed=18, out_gain=1.5), 2, 13, list_capacity=8, halo_capacity=64)

@@ -298,3 +298,11 @@ def test_batch_md_equals_per_context_md(crmc):
         sx, sy = x.state(), y.state()
         assert np.array_equal(sx["id"], sy["id"])
         assert np.array_equal(sx["xyz"], sy["xyz"]) and np.array_equal(sx["vel"], sy["vel"])
+
+
+@pytest.mark.parametrize("list_capacity,halo_capacity", [(8, 64), (4, 32)])
+def test_parity_with_lists_and_halos_beyond_shared_memory(crmc, list_capacity, halo_capacity):
+    """Small on-chip capacities force the global-memory paths: domain lists in
+    the global scratch region and halo particles read from global memory."""
+    w = W.config2(seed=3, scale=0.5)
+    _parity(crmc, w, 2, 31, list_capacity=list_capacity, halo_capacity=halo_capacity)
