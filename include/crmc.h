@@ -345,6 +345,8 @@ int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint
 /* cr_md_begin / cr_md_end on every replica (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed);
 int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
+/* Fix the batch's launch shape (as cr_set_launch_shape; 0, 0 restarts the tuning). */
+int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs);
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);
 void cr_batch_destroy(cr_batch *b);
 

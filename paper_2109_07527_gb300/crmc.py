@@ -84,7 +84,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
-           "cr_batch_md_end")
+           "cr_batch_md_end", "cr_batch_set_launch_shape")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -169,6 +169,8 @@ def _lib():
         lib.cr_batch_sweep.argtypes = [P, C.c_uint64, C.c_uint64]
         lib.cr_batch_md_step.restype = C.c_int
         lib.cr_batch_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        lib.cr_batch_set_launch_shape.restype = C.c_int
+        lib.cr_batch_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
         lib.cr_batch_get_launch_shape.restype = C.c_int
         lib.cr_batch_get_launch_shape.argtypes = [P, P, P]
         lib.cr_batch_destroy.restype = None
@@ -407,6 +409,9 @@ class Batch:
 
     def md_end(self, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_end(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_end")
+
+    def set_launch_shape(self, threads, regs):
+        _chk(self._lib.cr_batch_set_launch_shape(self._h, int(threads), int(regs)), "cr_batch_set_launch_shape")
 
     def launch_shape(self):
         t = C.c_int32()

@@ -1318,6 +1318,33 @@ extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t se
   return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
 }
 
+extern "C" int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs) {
+  if (!b) return CR_ERR_INVALID_ARG;
+  if (threads == 0) {  // re-enable tuning
+    b->tuning = b->da_tuning = true;
+    b->tune_next = b->da_next = 0;
+    return CR_OK;
+  }
+  bool found = false;
+  for (int da = 0; da < 2; ++da)
+    for (int i = 0; i < phase_shape_count(da != 0); ++i) {
+      int t, r;
+      phase_shape(i, &t, &r, da != 0);
+      if (t != threads || r != regs || phase_shape_smem(b->S, t, r, da != 0) > (size_t)b->smem_max) continue;
+      if (da) {
+        b->da_T = t;
+        b->da_R = r;
+        b->da_tuning = false;
+      } else {
+        b->T = t;
+        b->R = r;
+        b->tuning = false;
+      }
+      found = true;
+    }
+  return found ? CR_OK : CR_ERR_INVALID_ARG;
+}
+
 extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs) {
   if (!b || !threads || !regs) return CR_ERR_INVALID_ARG;
   *threads = b->T;

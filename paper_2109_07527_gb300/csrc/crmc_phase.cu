@@ -196,69 +196,6 @@ __device__ void warp_remove(DomList L, int n, int p) {
   }
 }
 
-// WCA change (FP64) of an inserted / deleted particle against a bystander;
-// out of line because it is rare (pairs inside 2^(1/6) sigma) and long.
-// Returns (du, gross); gross < 0: no interaction; gross = -2: overlap.
-__device__ __noinline__ double2 wca_change_nl(const WcaEntry &w, int dp, float cx, float cy, float cz, float xj,
-                                              float yj, float zj, double L, double halfL) {
-  double du = 0.0, gs = 0.0;
-  int ov = 0;
-  const bool hit = wca_change_d(w, dp, cx, cy, cz, xj, yj, zj, L, halfL, du, gs, ov);
-  if (ov) return make_double2(0.0, -2.0);
-  if (!hit) return make_double2(0.0, -1.0);
-  return make_double2(du, gs);
-}
-
-// One pair change of a changed particle c against a bystander j: the FP32
-// Coulomb part lB dq_c q_j phi(r) [r < rc] and, for inserted / deleted c,
-// the FP64 WCA part, both into 2^-32 kT fixed point.  |du| >= 2^20 kT or an
-// inserted particle closer than half a diameter flags an overlap.
-template <bool WITH_S>
-__device__ __forceinline__ void pair_change(const PairK &K, const WcaEntry *wca, float cx, float cy, float cz,
-                                            float dqlB, int dp, int ccls, float xj, float yj, float zj, float qj,
-                                            int jcls, long long &acc, unsigned long long &sacc, int &ov) {
-  const float dx = wrap_diff(xj, cx, K.Lf, K.halfL);
-  const float dy = wrap_diff(yj, cy, K.Lf, K.halfL);
-  const float dz = wrap_diff(zj, cz, K.Lf, K.halfL);
-  const float r2 = dx * dx + dy * dy + dz * dz;
-  float du = 0.0f, gs = 0.0f;
-  bool any = false;
-  if (r2 < K.rc2 && dqlB != 0.0f && qj != 0.0f) {
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float e = erfcf(K.alpha * r) * rinv;
-    du = dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
-    if (WITH_S) gs = fabsf(dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
-    any = true;
-  }
-  if (dp != 0) {
-    const WcaEntry &w = wca[ccls * 4 + jcls];
-    if (w.on && r2 < 1.0001f * w.wcut2) {
-      const double2 res = wca_change_nl(w, dp, cx, cy, cz, xj, yj, zj, K.Ld, K.halfLd);
-      if (res.y == -2.0) {
-        ov = 1;
-      } else if (res.y >= 0.0) {
-        if (!(fabs((double)du + res.x) < (double)BIG_TERM)) {
-          ov = 1;
-        } else {
-          if (any) acc += fix32(du);
-          acc += __double2ll_rn(res.x * (double)FIX_SCALE);
-          if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + res.y, (double)BIG_TERM) * (double)FIX_SCALE);
-        }
-        return;
-      }
-    }
-  }
-  if (any) {
-    if (!(fabsf(du) < BIG_TERM)) {
-      ov = 1;
-    } else {
-      acc += fix32(du);
-      if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
-    }
-  }
-}
-
 // pair change between the two changed particles: u_new - u_old, Coulomb in
 // FP32 and WCA in FP64, into fixed point
 __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
@@ -315,7 +252,7 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
 }
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int QCAP = 64;  // per-warp queue of Coulomb pair terms
+constexpr int QCAP = 96;  // per-warp queue of Coulomb pair terms (up to 31 waiting + 64 new)
 
 // Metropolis comparison ln u < lnA with lnA in 2^-48 fixed point: the FP32
 // ln u decides outside LNU_BAND, the FP64 ln u inside it
@@ -401,89 +338,120 @@ __device__ __forceinline__ void coul_eval(const PairK &K, float r2, float qp, lo
   }
 }
 
-// Warp step of the pair sweep: every lane offers at most one in-range Coulomb
-// pair; the warp appends the offers to its queue and, once 32 are waiting,
-// evaluates them with all lanes busy (the cheap distance tests of the
-// out-of-range majority never diverge into the expensive path).
-template <bool WITH_S>
-__device__ __forceinline__ void q_push(float *qr2, float *qqp, int &qn, bool in, float r2, float qp, const PairK &K,
-                                       long long &acc, unsigned long long &sacc, int &ov) {
-  const int lane = threadIdx.x & 31;
-  const unsigned m = __ballot_sync(FULL, in);
-  if (m == 0u) return;
-  const int pos = qn + __popc(m & ((1u << lane) - 1u));
-  if (in) {
-    qr2[pos] = r2;
-    qqp[pos] = qp;
+// WCA pre-check radii of a changed particle against the four classes
+// (1.0001 x squared cutoff, or -1 when it is not inserted / deleted or the
+// pair does not interact), kept in registers for the whole trial
+__device__ __forceinline__ float4 wca_radii(const WcaEntry *wca, const Desc &c) {
+  float r[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const WcaEntry &w = wca[c.cls * 4 + j];
+    r[j] = (c.dp != 0 && w.on) ? 1.0001f * w.wcut2 : -1.0f;
   }
-  qn += __popc(m);
-  if (qn >= 32) {
+  return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+__device__ __forceinline__ float sel4(const float4 v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// A pair within the WCA range of an inserted / deleted changed particle:
+// Coulomb in FP32 and WCA in FP64, evaluated at once (rare)
+template <bool WITH_S>
+__device__ __noinline__ void near_pair(const PairK &K, const WcaEntry &w, const Desc &c, float xj, float yj, float zj,
+                                       float qj, float r2, long long &acc, unsigned long long &sacc, int &ov) {
+  float du = 0.0f, gs = 0.0f;
+  const bool any = r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
+  if (any) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float e = erfcf(K.alpha * r) * rinv;
+    du = c.dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
+    if (WITH_S) gs = fabsf(c.dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
+  }
+  double du_w = 0.0, gs_w = 0.0;
+  int ovw = 0;
+  const bool hit = wca_change_d(w, c.dp, c.x, c.y, c.z, xj, yj, zj, K.Ld, K.halfLd, du_w, gs_w, ovw);
+  if (ovw) {
+    ov = 1;
+  } else if (hit) {
+    if (!(fabs((double)du + du_w) < (double)BIG_TERM)) {
+      ov = 1;
+    } else {
+      if (any) acc += fix32(du);
+      acc += __double2ll_rn(du_w * (double)FIX_SCALE);
+      if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + gs_w, (double)BIG_TERM) * (double)FIX_SCALE);
+    }
+  } else if (any) {  // beyond the WCA cutoff after all: Coulomb only
+    if (!(fabsf(du) < BIG_TERM)) ov = 1;
+    else {
+      acc += fix32(du);
+      if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
+    }
+  }
+}
+
+// Both changed particles A and B against one candidate j (lane-parallel):
+// the two distance tests are independent, pairs near an inserted / deleted
+// particle are evaluated at once, the in-range Coulomb pairs of A and B join
+// the warp's queue with one compaction step, and every full 32 queued pairs
+// are evaluated with all lanes busy.
+template <bool WITH_S>
+__device__ __forceinline__ void offer2(const PairK &K, const WcaEntry *wca, const Desc &A, const Desc &B,
+                                       const float4 wrA, const float4 wrB, bool valid, float xj, float yj, float zj,
+                                       float qj, int jcls, float *qr2, float *qqp, int &qn, long long &acc,
+                                       unsigned long long &sacc, int &ov) {
+  const int lane = threadIdx.x & 31;
+  const float ax = wrap_diff(xj, A.x, K.Lf, K.halfL), ay = wrap_diff(yj, A.y, K.Lf, K.halfL),
+              az = wrap_diff(zj, A.z, K.Lf, K.halfL);
+  const float bx = wrap_diff(xj, B.x, K.Lf, K.halfL), by = wrap_diff(yj, B.y, K.Lf, K.halfL),
+              bz = wrap_diff(zj, B.z, K.Lf, K.halfL);
+  const float rA = ax * ax + ay * ay + az * az, rB = bx * bx + by * by + bz * bz;
+  const bool nearA = valid && rA < sel4(wrA, jcls), nearB = valid && rB < sel4(wrB, jcls);
+  if (nearA) near_pair<WITH_S>(K, wca[A.cls * 4 + jcls], A, xj, yj, zj, qj, rA, acc, sacc, ov);
+  if (nearB) near_pair<WITH_S>(K, wca[B.cls * 4 + jcls], B, xj, yj, zj, qj, rB, acc, sacc, ov);
+  const bool inA = valid && !nearA && rA < K.rc2 && A.dqlB != 0.0f && qj != 0.0f;
+  const bool inB = valid && !nearB && rB < K.rc2 && B.dqlB != 0.0f && qj != 0.0f;
+  const unsigned mA = __ballot_sync(FULL, inA), mB = __ballot_sync(FULL, inB);
+  if ((mA | mB) == 0u) return;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nA = __popc(mA);
+  if (inA) {
+    const int p = qn + __popc(mA & lt);
+    qr2[p] = rA;
+    qqp[p] = A.dqlB * qj;
+  }
+  if (inB) {
+    const int p = qn + nA + __popc(mB & lt);
+    qr2[p] = rB;
+    qqp[p] = B.dqlB * qj;
+  }
+  qn += nA + __popc(mB);
+  while (qn >= 32) {
     __syncwarp();
     coul_eval<WITH_S>(K, qr2[lane], qqp[lane], acc, sacc, ov);
     const int rest = qn - 32;
-    float a = 0.f, b = 0.f;
+    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
     if (lane < rest) {
-      a = qr2[32 + lane];
-      b = qqp[32 + lane];
+      a0 = qr2[32 + lane];
+      b0 = qqp[32 + lane];
+    }
+    if (lane + 32 < rest) {
+      a1 = qr2[64 + lane];
+      b1 = qqp[64 + lane];
     }
     __syncwarp();
     if (lane < rest) {
-      qr2[lane] = a;
-      qqp[lane] = b;
+      qr2[lane] = a0;
+      qqp[lane] = b0;
+    }
+    if (lane + 32 < rest) {
+      qr2[32 + lane] = a1;
+      qqp[32 + lane] = b1;
     }
     __syncwarp();
     qn = rest;
   }
-}
-
-// One changed particle c against one candidate j (lane-parallel).  Pairs
-// within the WCA range of an inserted / deleted c are evaluated at once,
-// Coulomb in FP32 and WCA in FP64 (rare); other Coulomb pairs go to the queue.
-template <bool WITH_S>
-__device__ __forceinline__ void offer(const PairK &K, const WcaEntry *wca, const Desc &c, bool valid, float xj, float yj,
-                                      float zj, float qj, int jcls, float *qr2, float *qqp, int &qn, long long &acc,
-                                      unsigned long long &sacc, int &ov) {
-  const float dx = wrap_diff(xj, c.x, K.Lf, K.halfL);
-  const float dy = wrap_diff(yj, c.y, K.Lf, K.halfL);
-  const float dz = wrap_diff(zj, c.z, K.Lf, K.halfL);
-  const float r2 = dx * dx + dy * dy + dz * dz;
-  bool near = false;
-  if (c.dp != 0 && valid) {  // warp-uniform dp
-    const WcaEntry &w = wca[c.cls * 4 + jcls];
-    near = w.on && r2 < 1.0001f * w.wcut2;
-    if (near) {
-      float du = 0.0f, gs = 0.0f;
-      const bool any = r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
-      if (any) {
-        const float rinv = rsqrtf(r2);
-        const float r = r2 * rinv;
-        const float e = erfcf(K.alpha * r) * rinv;
-        du = c.dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
-        if (WITH_S) gs = fabsf(c.dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
-      }
-      const double2 res = wca_change_nl(w, c.dp, c.x, c.y, c.z, xj, yj, zj, K.Ld, K.halfLd);
-      if (res.y == -2.0) {
-        ov = 1;
-      } else if (res.y >= 0.0) {
-        if (!(fabs((double)du + res.x) < (double)BIG_TERM)) {
-          ov = 1;
-        } else {
-          if (any) acc += fix32(du);
-          acc += __double2ll_rn(res.x * (double)FIX_SCALE);
-          if (WITH_S)
-            sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + res.y, (double)BIG_TERM) * (double)FIX_SCALE);
-        }
-      } else if (any) {  // beyond the WCA cutoff after all: Coulomb only
-        if (!(fabsf(du) < BIG_TERM)) ov = 1;
-        else {
-          acc += fix32(du);
-          if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
-        }
-      }
-    }
-  }
-  const bool in = valid && !near && r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
-  q_push<WITH_S>(qr2, qqp, qn, in, r2, c.dqlB * qj, K, acc, sacc, ov);
 }
 
 template <int T>
@@ -993,6 +961,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       int ov = 0;
       if (nch) {
         const Desc A = ctl->c[0], B = ctl->c[1];
+        const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
         int qn = 0;
         if (R > 0) {
 #pragma unroll
@@ -1001,8 +970,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
             const float q = p.w - 8.0f * (float)cls;
             const bool v = r < nmine;
-            offer<LOG>(K, wca, A, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
-            offer<LOG>(K, wca, B, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+            offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
           }
         } else {
           const int lim = min(NH, hcap);
@@ -1012,8 +980,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
             const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
             const float q = p.w - 8.0f * (float)cls;
-            offer<LOG>(K, wca, A, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
-            offer<LOG>(K, wca, B, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+            offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
           }
         }
         // halo beyond what is held on chip (dense regions): straight from global memory
@@ -1028,8 +995,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             p = P.pos[g];
             cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
           }
-          offer<LOG>(K, wca, A, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-          offer<LOG>(K, wca, B, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+          offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
         }
         const int n = misc[0];
         for (int base = 0; base < n; base += T) {
@@ -1041,8 +1007,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             p = L.pos[j];
             cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
           }
-          offer<LOG>(K, wca, A, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-          offer<LOG>(K, wca, B, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+          offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
         }
         __syncwarp();
         if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
