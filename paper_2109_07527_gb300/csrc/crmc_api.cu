@@ -56,6 +56,7 @@ struct cr_ctx {
   long long *d_gs_lnk = nullptr;
   int *d_gs_info = nullptr, *d_gs_rank = nullptr;
   int *d_plist = nullptr, *d_nparts = nullptr;  // MD particle list
+  int *d_order = nullptr;                       // launch order of the domains of each colour
   // delayed acceptance: surrogate on the device, records, its own launch-shape tuner
   uint16_t *d_mlp_w = nullptr;
   float *d_mlp_b = nullptr;
@@ -163,7 +164,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
                   c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
-                  c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat};
+                  c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info};
@@ -606,6 +607,18 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.gs_lnk = c->d_gs_lnk;
   P.gs_info = c->d_gs_info;
   P.gs_rank = c->d_gs_rank;
+  P.order = nullptr;
+  if (!global && nc <= ORDER_MAX_NC && P.nact <= ORDER_MAX_NACT) {
+    // densest-first launch order, recomputed every sweep; starts as the identity
+    std::vector<int> ident((size_t)P.ncol * P.nact);
+    for (size_t i = 0; i < ident.size(); ++i) ident[i] = (int)(i % (size_t)P.nact);
+    if (cudaMalloc((void **)&c->d_order, sizeof(int) * ident.size()) != cudaSuccess ||
+        cudaMemcpy(c->d_order, ident.data(), sizeof(int) * ident.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_ctx(c);
+      return CR_ERR_NOMEM;
+    }
+    P.order = c->d_order;
+  }
   if (cudaMemcpy(c->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice) != cudaSuccess) {
     free_ctx(c);
     return CR_ERR_CUDA;
@@ -730,6 +743,10 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
+    }
+    if (P.order) {
+      CR_CUDA(launch_domain_order(ctx->d_reps, 1, P.nc, P.nact, s, swc, k0, k1));
+      ctx->launches_total++;
     }
     for (int col = 0; col < P.ncol; ++col) {
       int ti;
@@ -1143,6 +1160,7 @@ struct cr_batch {
   bool da_tuning = true;
   float da_ms[4] = {};
   std::vector<SysParams> reps;  // host copy of d_reps
+  int order_nc = 0, order_nact = 0;  // largest box and colour among replicas with a launch order (0: none)
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   cudaEvent_t fork = nullptr;
@@ -1179,6 +1197,11 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   b->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
   b->da_tuning = b->tuning;
   b->reps = reps;
+  for (int r = 0; r < n; ++r)
+    if (reps[r].order) {
+      b->order_nc = std::max(b->order_nc, reps[r].nc);
+      b->order_nact = std::max(b->order_nact, reps[r].nact);
+    }
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctxs[0]->device);
   if (phase_smem_bytes(b->S, 512, false) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
@@ -1252,6 +1275,10 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
+    }
+    if (b->order_nc > 0) {
+      CR_CUDA(launch_domain_order(b->d_reps, n, b->order_nc, b->order_nact, s, swc, k0, k1));
+      c0->launches_total++;
     }
     for (int col = 0; col < b->ncol; ++col) {
       int ti;

@@ -93,7 +93,15 @@ struct SysParams {
   const float *mlp_b;
   cr_trial_da *dlog;          // DA records (device) or null
   float *feat_log;            // 48 features per trial (device) or null
+  // launch order of each colour's domains, largest region first (ncol x nact),
+  // or null for the natural order
+  int *order;
 };
+
+// domain ordering is computed in shared memory for boxes of at most this many
+// cells per dimension and at most this many active domains per colour
+constexpr int ORDER_MAX_NC = 24;
+constexpr int ORDER_MAX_NACT = 512;
 
 // surrogate MLP sizes and the offsets of its parts in mlp_w / mlp_b
 constexpr int MLP_IN = 48;

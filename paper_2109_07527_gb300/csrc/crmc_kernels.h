@@ -53,6 +53,10 @@ void phase_shape(int i, int *threads, int *regs, bool da);
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
                          uint32_t k0, uint32_t k1);
+// launch order of every colour's domains for one sweep (densest region first);
+// does nothing for boxes or colours beyond the ordering limits
+cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int nc, int nact, cudaStream_t s, uint32_t sweep,
+                                uint32_t k0, uint32_t k1);
 // particle list (plist, n_particles: device scratch of max_particles + 1
 // ints), then the force kernel (one warp per particle)
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,

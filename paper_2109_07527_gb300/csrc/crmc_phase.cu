@@ -1,7 +1,10 @@
 // crmc_phase.cu -- the colour-phase kernel of the CR-MC stage (sm_103a).
 //
 // k_cr_phase: one CTA per active domain of one colour of the 8-colour
-// checkerboard, for one or several replicas (blockIdx.y) in one launch.
+// checkerboard, for one or several replicas (blockIdx.x) in one launch; the
+// domains of a colour are launched densest first (blockIdx.y is the rank in
+// the order k_domain_order computes at the start of every sweep), so that the
+// long CTAs do not form the tail of the launch.
 // The CTA
 //   1. stages the domain's particles into a list kept in canonical order
 //      (in-domain cell rank, then id) -- in shared memory, or in a global
@@ -530,12 +533,13 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   }
 
   {
-    const int *src = (const int *)&reps[blockIdx.y];
+    const int *src = (const int *)&reps[blockIdx.x];
     int *dst = (int *)&P;
     for (int i = tid; i < (int)(sizeof(SysParams) / 4); i += T) dst[i] = src[i];
   }
   __syncthreads();
-  if ((int)blockIdx.x >= P.nact) return;  // uniform over the CTA
+  if ((int)blockIdx.y >= P.nact) return;  // uniform over the CTA
+  const int bdom = P.order ? P.order[colour * P.nact + blockIdx.y] : (int)blockIdx.y;  // active-domain index
   const int k = P.k, h = P.h, nc = P.nc, nr = P.nr, m = P.m;
   const int KC = k * k * k, NR = nr * nr * nr;
   const uint32_t key1 = key1_base ^ P.key_xor;
@@ -550,7 +554,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
     dd[0] = dd[1] = dd[2] = 0;
   } else {
     const int hn = P.nd >> 1;
-    const int b = blockIdx.x;
+    const int b = bdom;
     dd[0] = 2 * (b % hn) + (colour & 1);
     dd[1] = 2 * ((b / hn) % hn) + ((colour >> 1) & 1);
     dd[2] = 2 * (b / (hn * hn)) + ((colour >> 2) & 1);
@@ -596,7 +600,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   const bool in_smem = ND + 2 * m <= S.dcs;
   DomList L = Ls;
   if (!in_smem) {
-    const size_t o = (size_t)blockIdx.x * P.dcap_glob;  // this replica's scratch
+    const size_t o = (size_t)blockIdx.y * P.dcap_glob;  // this replica's scratch
     L.pos = P.gs_pos + o; L.vel = P.gs_vel + o; L.id = P.gs_id + o; L.lnk = P.gs_lnk + o;
     L.info = P.gs_info + o; L.rank = P.gs_rank + o;
     if (ND + 2 * m > P.dcap_glob) {  // cannot happen: a cell holds at most cap particles
@@ -674,7 +678,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   if (tid < 7) misc[9 + tid] = misc[1 + tid];
   const int cc_thread = NW > 1 ? 32 : 0;  // the thread that adds the changed-pair term
   const long long log_dom = (long long)(sweep - sweep0) * P.per_sweep + (long long)colour * P.nact * m +
-                            (long long)blockIdx.x * m;
+                            (long long)bdom * m;
 
   for (int k0 = 0; k0 < m; k0 += TRIAL_CHUNK) {
     const int nchunk = min(TRIAL_CHUNK, m - k0);
@@ -1228,6 +1232,87 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
 }
 
 // ---------------------------------------------------------------------------
+// Launch order of the domains of every colour for one sweep: the particles in
+// each domain's region (its cells and the halo around them, counted at the
+// start of the sweep: box sums of the cell counts, separable over x, y, z with
+// periodic wrap) and, per colour, the domains ranked by decreasing count (ties
+// by index).  Only the order of independent CTAs changes, never a result.
+// One CTA per replica; boxes and colours above ORDER_MAX_NC / ORDER_MAX_NACT
+// keep the natural order (order is then not used: P.order is null).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_domain_order(const SysParams *__restrict__ reps, uint32_t sweep, uint32_t key0,
+                                                      uint32_t key1_base) {
+  const SysParams &P = reps[blockIdx.x];
+  if (!P.order) return;
+  extern __shared__ int osm[];
+  const int nc = P.nc, nr = P.nr, h = P.h, k = P.k, nact = P.nact, ncell = nc * nc * nc;
+  int *a = osm, *bsum = osm + ncell, *cost = osm + 2 * ncell;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const uint32_t key1 = key1_base ^ P.key_xor;
+  const uint4 w = philox10(0u, 0u, sweep, 4u, key0, key1);
+  const int off[3] = {pick32(w.x, nc), pick32(w.y, nc), pick32(w.z, nc)};
+  for (int i = tid; i < ncell; i += T) a[i] = P.cnt[i];
+  __syncthreads();
+  // window sums of nr cells along x, then y, then z (b = sum over [c, c + nr))
+  for (int i = tid; i < ncell; i += T) {
+    const int x = i % nc, yz = i - x;
+    int sum = 0;
+    for (int j = 0; j < nr; ++j) sum += a[yz + (x + j) % nc];
+    bsum[i] = sum;
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell; i += T) {
+    const int x = i % nc, y = (i / nc) % nc, z = i / (nc * nc);
+    int sum = 0;
+    for (int j = 0; j < nr; ++j) sum += bsum[x + nc * ((y + j) % nc + nc * z)];
+    a[i] = sum;
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell; i += T) {
+    const int x = i % nc, y = (i / nc) % nc, z = i / (nc * nc);
+    int sum = 0;
+    for (int j = 0; j < nr; ++j) sum += a[x + nc * (y + nc * ((z + j) % nc))];
+    bsum[i] = sum;
+  }
+  __syncthreads();
+  const int hn = P.nd >> 1;
+  for (int c = 0; c < P.ncol; ++c) {
+    for (int b = tid; b < nact; b += T) {
+      int o[3];
+      const int dd[3] = {2 * (b % hn) + (c & 1), 2 * ((b / hn) % hn) + ((c >> 1) & 1), 2 * (b / (hn * hn)) + ((c >> 2) & 1)};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) o[i] = ((off[i] + dd[i] * k - h) % nc + nc) % nc;  // region origin
+      cost[b] = bsum[o[0] + nc * (o[1] + nc * o[2])];
+    }
+    __syncthreads();
+    for (int b = tid; b < nact; b += T) {
+      const int cb = cost[b];
+      int rank = 0;
+      for (int j = 0; j < nact; ++j) {
+        const int cj = cost[j];
+        rank += (cj > cb || (cj == cb && j < b)) ? 1 : 0;
+      }
+      P.order[c * nact + rank] = b;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int nc, int nact, cudaStream_t s, uint32_t sweep,
+                                uint32_t k0, uint32_t k1) {
+  if (nc > ORDER_MAX_NC || nact > ORDER_MAX_NACT) return cudaSuccess;  // contexts keep P.order null then
+  const size_t smem = sizeof(int) * (2 * (size_t)nc * nc * nc + nact);
+  static size_t attr = 0;
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_domain_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
+  k_domain_order<<<n_rep, 512, smem, s>>>(d_reps, sweep, k0, k1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
@@ -1277,7 +1362,7 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  k_cr_phase<T, R, LOG, DA><<<dim3(grid_x, n_rep), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
+  k_cr_phase<T, R, LOG, DA><<<dim3(n_rep, grid_x), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
   return cudaGetLastError();
 }
 
