@@ -131,14 +131,18 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
   for (int s = 0; s < n && o + s < max_out; ++s) plist[o + s] = c * P.cap + s;
 }
 
-// MD forces: one warp per particle.  The lanes share the (2h+1)^3 stencil of
-// neighbour cells (cell side >= rc/h), up to MD_CPL cells each; every lane
-// tests its candidates (cheap), in-range partners are queued and their forces
+// MD forces: one warp per particle.  The candidates of the (2h+1)^3 stencil of
+// neighbour cells (cell side >= rc/h) are numbered consecutively over the
+// cells (a warp prefix sum of the cell counts), so the lanes take 32
+// consecutive candidates per round whatever the cells' occupancy; every lane
+// tests its candidate (cheap), in-range partners are queued and their forces
 // evaluated with all lanes busy.  Pair forces are FP32 terms summed in 2^-24
 // fixed point, so the result does not depend on the order.
 template <int NBC>  // 2h+1 when the box has at least that many cells per dimension, 0 otherwise
 __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams M) {
   __shared__ int queue[MD_NW][MD_QCAP];
+  __shared__ int cpre[MD_NW][MD_CPL * 32 + 1];  // exclusive prefix of the stencil cells' counts
+  __shared__ int cbs[MD_NW][MD_CPL * 32];       // first slot of each stencil cell
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * MD_NW + wl;
@@ -152,40 +156,51 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   const int nb = NBC > 0 ? NBC : min(2 * h + 1, nc);
   const bool all = NBC == 0 && nb == nc;  // every cell of the dimension, once
   const int nb3 = nb * nb * nb;
-  // this lane's stencil cells and their counts
-  int cbase[MD_CPL], ccnt[MD_CPL], total = 0;
+  // stencil cell o = lane + 32 t: its first slot and count; the candidates of
+  // all cells are then numbered consecutively (exclusive prefix over o)
+  int run = 0;
 #pragma unroll
   for (int t = 0; t < MD_CPL; ++t) {
     const int o = lane + 32 * t;
-    cbase[t] = 0;
-    ccnt[t] = 0;
+    int n = 0, base = 0;
     if (o < nb3) {
       const int ox = o % nb, oy = (o / nb) % nb, oz = o / (nb * nb);
       const int jx = all ? ox : wrap_cell(cx + ox - h, nc);
       const int jy = all ? oy : wrap_cell(cy + oy - h, nc);
       const int jz = all ? oz : wrap_cell(cz + oz - h, nc);
       const int jc = jx + nc * (jy + nc * jz);
-      cbase[t] = jc * cap;
-      ccnt[t] = P.cnt[jc];
-      total += ccnt[t];
+      base = jc * cap;
+      n = P.cnt[jc];
     }
+    int x = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    cpre[wl][o] = run + x - n;
+    cbs[wl][o] = base;
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
-  const int iters = __reduce_max_sync(0xffffffffu, (unsigned)total);
+  if (lane == 0) cpre[wl][MD_CPL * 32] = run;
+  __syncwarp();
+  const int total = run;
   int *q = queue[wl];
+  const int *pre = cpre[wl];
   int qn = 0;
   long long fx = 0, fy = 0, fz = 0;
-  for (int it = 0; it < iters; ++it) {
+  for (int c0 = 0; c0 < total; c0 += 32) {
+    const int c = c0 + lane;
     bool in = false;
     int gj = -1;
-    if (it < total) {
-      int rem = it;
-#pragma unroll
-      for (int t = 0; t < MD_CPL; ++t) {
-        if (gj < 0) {
-          if (rem < ccnt[t]) gj = cbase[t] + rem;
-          else rem -= ccnt[t];
-        }
+    if (c < total) {
+      int lo = 0, hi = MD_CPL * 32;  // last cell o with pre[o] <= c
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= c) lo = mid;
+        else hi = mid;
       }
+      gj = cbs[wl][lo] + (c - pre[lo]);
       if (gj != gi) {
         const float4 pj = P.pos[gj];
         const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
