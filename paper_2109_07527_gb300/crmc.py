@@ -368,6 +368,18 @@ class Context:
         return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
                     net_charge=v.net_charge, alpha=v.alpha)
 
+    def state_into(self, xyz=None, vel=None, id=None, type=None, state=None, site_state=None, force=None):
+        """cr_state into caller-owned host arrays (numpy arrays or raw pointers,
+        e.g. pinned buffers reused every step, each sized for the capacity);
+        returns the counts."""
+        conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
+        v = cr_state_view()
+        v.xyz, v.vel, v.force, v.id = conv(xyz), conv(vel), conv(force), conv(id)
+        v.type, v.state, v.site_state = conv(type), conv(state), conv(site_state)
+        _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
+        return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
+                    net_charge=v.net_charge, alpha=v.alpha)
+
     def state(self):
         """Counts and all particles sorted by id."""
         c = self.counts()

@@ -67,6 +67,8 @@ struct TrialCtl {
   // delayed acceptance: in-domain cell ranks of a and b, charge and presence
   // changes, feature group of a (0 ion, 8 site), stage-1 outcome
   int rka, rkb, dqa, dqb, eta_a, eta_b, cat_a, go;
+  float sur;             // surrogate dE~ (DA)
+  long long sur_fx;      // dE~ clamped, 2^-48 fixed point (DA)
 };
 
 struct DomList {
@@ -734,9 +736,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
     for (int t = 0; t < nchunk; ++t) {
       const int kk = k0 + t;
       // ---- warp 0: proposal and participants (kept in warp 0's registers)
-      int s_move = 0, s_flags = 0, s_site = -1, s_ionA = -1, s_ionB = -1, s_nch = 0;
-      long long s_ln_ratio = 0, s_dself = 0;
-      unsigned long long s_id_a = ~0ull, s_id_b = ~0ull, s_newid = 0ull;
+      // (the trial's selection lives in shared memory, *ctl, across the sweep)
       if (warp == 0) {
         const TrialPre q = tp[t];
         const int n = misc[0];
@@ -838,17 +838,6 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
         const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
                        (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
-        s_move = 2 * r + (fwd ? 0 : 1);
-        s_flags = flags;
-        s_site = site;
-        s_ionA = ionA;
-        s_ionB = ionB;
-        s_nch = nch;
-        s_ln_ratio = ln_ratio;
-        s_dself = P.lBself_fx * (long long)sq;
-        s_id_a = id_a;
-        s_id_b = id_b;
-        s_newid = newid;
         int rka = 0, rkb = 0;
         if (DA && nch) {
           if (r == R_SALT) {
@@ -864,6 +853,18 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
           C.c[0] = c0;
           C.c[1] = c1;
           C.nch = nch;
+          C.move = 2 * r + (fwd ? 0 : 1);
+          C.flags = flags;
+          C.site = site;
+          C.ionA = ionA;
+          C.ionB = ionB;
+          C.ln_ratio_fx = ln_ratio;
+          C.dself_fx = P.lBself_fx * (long long)sq;
+          C.id_a = id_a;
+          C.id_b = id_b;
+          C.newid = newid;
+          C.sur = 0.0f;
+          C.sur_fx = 0;
           C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
           C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
           if (DA) {
@@ -881,9 +882,6 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       cta_sync<T>();
       // ---- delayed acceptance, stage 1: surrogate features and MLP (all
       // threads), decision in warp 0; a rejection skips the pair sweep
-      bool s1 = true;
-      float sur = 0.0f;
-      long long sur_fx = 0;
       if (DA && ctl->nch) {
         if (tid < MLP_IN) dfeat[tid] = 0;
         cta_sync<T>();
@@ -945,14 +943,18 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
             for (int kk2 = 0; kk2 < MLP_H; ++kk2) y = __fmaf_rn(bf16_value(__ldg(&w4[kk2])), hv[kk2], y);
           }
           const float y0 = __shfl_sync(FULL, y, 0), y1 = __shfl_sync(FULL, y, 1);
-          sur = 0.5f * (y0 - y1);
-          if (sur != sur) {
-            s1 = false;  // NaN: rejected, as a comparison with NaN is false
-          } else {
+          const float sur = 0.5f * (y0 - y1);
+          bool s1 = false;  // NaN: rejected, as a comparison with NaN is false
+          long long sur_fx = 0;
+          if (sur == sur) {
             sur_fx = __double2ll_rn((double)fminf(fmaxf(sur, -16384.0f), 16384.0f) * LNFIX);
-            s1 = accept_fx(s_ln_ratio - s_dself - sur_fx, tp[t].lnu_f, tp[t].uhi, tp[t].ulo);
+            s1 = accept_fx(ctl->ln_ratio_fx - ctl->dself_fx - sur_fx, tp[t].lnu_f, tp[t].uhi, tp[t].ulo);
           }
-          if (lane == 0) ctl->go = s1 ? 1 : 0;
+          if (lane == 0) {
+            ctl->go = s1 ? 1 : 0;
+            ctl->sur = sur;
+            ctl->sur_fx = sur_fx;
+          }
         }
         cta_sync<T>();
       } else if (DA && LOG && P.feat_log && tid < MLP_IN) {
@@ -1029,7 +1031,13 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       // ---- warp 0: decision and commit
       if (warp == 0) {
         const TrialPre &q = tp[t];
-        int flags = s_flags;
+        const int s_move = ctl->move, s_site = ctl->site, s_ionA = ctl->ionA, s_ionB = ctl->ionB, s_nch = ctl->nch;
+        const long long s_ln_ratio = ctl->ln_ratio_fx, s_dself = ctl->dself_fx;
+        const unsigned long long s_id_a = ctl->id_a, s_id_b = ctl->id_b, s_newid = ctl->newid;
+        const bool s1 = !DA || ctl->go != 0;
+        const float sur = DA ? ctl->sur : 0.0f;
+        const long long sur_fx = DA ? ctl->sur_fx : 0ll;
+        int flags = ctl->flags;
         bool accept = false;
         double dE = 0.0, Ssum = 0.0, lnA = -INFINITY, lnA2r = quiet_nan();
         if (DA && LOG && s_nch) lnA = (double)s_ln_ratio / LNFIX - (double)s_dself / LNFIX - (double)sur;
