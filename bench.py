@@ -499,304 +499,6 @@ def run_ours(args):
 
     if rank != 0:
         return
-    import oracle
-    w = workload(0)
-    o = oracle.Oracle(w, trials_per_domain=1)
-    tps = o.trials_per_sweep
-    for s in range(args.warmup):
-        o.sweep(tps, 7 + s)
-    t0 = time.perf_counter()
-    n = 0
-    for s in range(args.steps):
-        o.sweep(tps, 100 + s)
-        n += tps
-        if s % 10 == 9:
-            o.md_step(1, 0.005, 1.0, 11)
-    dt = time.perf_counter() - t0
-    v = n / dt
-    sample = (f"{args.steps} steps of {tps} trials (1 trial per domain) with one MD step per 10 steps "
-              f"(the 1 MD : 1e4 trials mix), {dt:.1f} s, 1 host thread")
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
-           "cpu_baseline": {"value": v, "unit": "trials/s", "cores": 1, "kind": "oracle", "sample": sample},
-           "e2e": {"value": v, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
-
-
-def ph_sweep_workloads(rank):
-    """The polyelectrolyte solution at pH 2.0, 2.5, ..., 8.0 (13 replicas of
-    the same seeded starting structure)."""
-    import copy
-    base = workload(rank)
-    out = []
-    for i in range(13):
-        w = copy.copy(base)
-        w.params = dict(base.params)
-        w.params["pH"] = 2.0 + 0.5 * i
-        out.append(w)
-    return out
-
-
-def measured_tensor_peak():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        try:
-            d = json.load(open(p))
-            for k in ("bf16_tflops", "bf16_TFLOPs"):
-                if k in d:
-                    return float(d[k]), "measured"
-        except (OSError, ValueError):
-            pass
-    return FALLBACK_BF16_TFLOPS, "fallback"
-
-
-# floating-point operations of one training row (algorithmic, K = 48 input):
-# forward 48x128 + 2 x 128x128, backward 4 x 128x128 + 128x48, 2 flops per MAC
-TRAIN_FLOPS_PER_ROW = 2 * (48 * 128 + 2 * 128 * 128) + 2 * (4 * 128 * 128 + 128 * 48)
-
-
-def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
-    """Surrogate delayed acceptance: record (feature, pair-energy) pairs with
-    logged DA sweeps (zero surrogate: stage 1 is the chemistry alone), train the
-    MLP on the tensor cores, then time the batched DA cycle with it."""
-    from paper_2109_07527_gb300 import workloads as W
-    rng = np.random.default_rng(0)
-    gd = crmc.Context(ws[5])  # pH 4.5
-    gd.set_surrogate(W.random_mlp(seed=5, out_gain=0.0))
-    X, y = [], []
-    for s in range(12):
-        r = gd.sweep_da(gd.trials_per_sweep, 40 + s, log=True, features=True)
-        ok = (r["da"]["stage"] > 0) & np.isfinite(r["da"]["lnA2"])
-        X.append(r["features"][ok])
-        y.append(r["da"]["dE_sur"][ok].astype(np.float64) - r["da"]["lnA2"][ok])
-        gd.md_step(1, dt, gamma, 60 + s)
-    X = np.concatenate(X)
-    y = np.concatenate(y).astype(np.float32)
-    n_hold = len(X) // 10
-    Xh, yh = X[:n_hold], y[:n_hold]
-    X, y = np.concatenate([X[n_hold:], -X[n_hold:]]), np.concatenate([y[n_hold:], -y[n_hold:]])
-    perm = rng.permutation(len(X))
-    X, y = X[perm], y[perm]
-    Bt = 8192
-    nb = len(X) // Bt
-    Xd = torch.from_numpy(np.ascontiguousarray(X[:nb * Bt])).cuda()
-    yd = torch.from_numpy(np.ascontiguousarray(y[:nb * Bt])).cuda()
-    tr = crmc.Trainer(W.random_mlp(seed=6, gain=0.5), max_batch=Bt, lr=1e-3, target_clip=20.0)
-    loss0 = tr.step(Xd.data_ptr(), yd.data_ptr(), Bt, want_loss=True)
-    n_train = 300
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(n_train):
-        b = k % nb
-        tr.step(Xd.data_ptr() + b * Bt * 48 * 4, yd.data_ptr() + b * Bt * 4, Bt)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_ms = e0.elapsed_time(e1)
-    loss_end = tr.step(Xd.data_ptr(), yd.data_ptr(), Bt, want_loss=True)
-    _, mlp = tr.get()
-    tpeak, tkind = measured_tensor_peak()
-    tflops = n_train * Bt * TRAIN_FLOPS_PER_ROW / (t_ms / 1e3) / 1e12
-    # held-out error of the antisymmetrised surrogate (oracle-free: the library's own DA records)
-    gd.set_surrogate(mlp)
-    r = gd.sweep_da(gd.trials_per_sweep, 999, log=True, features=False)
-    ev = r["da"]["stage"] > 0
-    stage1_reject = float(np.mean(r["da"]["stage"][ev] == 1))
-    fin = ev & np.isfinite(r["da"]["lnA2"])
-    err = np.abs(r["da"]["lnA2"][fin])  # |dE~ - dE_pair|
-    sur_err = {"median_kT": float(np.median(err)), "frac_within_1kT": float(np.mean(err < 1.0))}
-    gd.close()
-    # batched DA cycle, same step definition as the plain batch
-    ctxs = [crmc.Context(w) for w in ws]
-    for c in ctxs:
-        c.set_surrogate(mlp)
-    b = crmc.Batch(ctxs)
-    b.sweep_da(3, 0xDA)  # launch-shape tuning of the DA variant
-    for s in range(3):
-        b.md_begin(dt, gamma, 1000 + s)
-        b.sweep_da(1, 1 + s)
-        b.md_end(dt, gamma, 1000 + s)
-
-    def step(s):
-        b.md_begin(dt, gamma, 6000 + s)
-        b.sweep_da(1, 200 + s)
-        b.md_end(dt, gamma, 6000 + s)
-
-    ms = time_steps(step, steps, stream, flush)
-    for c in ctxs:
-        c.check()
-    per_step = ctxs[0].trials_per_sweep * len(ctxs)
-    out = {"value": per_step * steps / (ms / 1e3), "unit": "trials/s", "steps": steps, "ms_per_step": ms / steps,
-           "launch_shape": None, "stage1_reject_frac": stage1_reject, "surrogate_error": sur_err,
-           "alpha_end": [round(c.counts()["alpha"], 4) for c in ctxs],
-           "train": {"rows": int(nb * Bt), "batch": Bt, "steps": n_train, "ms": t_ms,
-                     "rows_per_s": n_train * Bt / (t_ms / 1e3), "loss_first": loss0, "loss_end": loss_end,
-                     "held_out_pairs": int(n_hold),
-                     "roofline": {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
-                                  "frac": tflops / tpeak, "peak_source": tkind,
-                                  "flops_per_row": TRAIN_FLOPS_PER_ROW}}}
-    b.close()
-    for c in ctxs:
-        c.close()
-    return out
-
-
-def time_steps(step_fn, steps, stream, flush):
-    import torch
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    torch.cuda.synchronize()
-    for s in range(steps):
-        starts[s].record(stream)
-        step_fn(s)
-        ends[s].record(stream)
-        flush.zero_()
-    torch.cuda.synchronize()
-    return sum(starts[s].elapsed_time(ends[s]) for s in range(steps))
-
-
-def run_ours(args):
-    import torch
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    from paper_2109_07527_gb300 import crmc
-
-    dt, gamma = 0.005, 1.0
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-    peak, peak_kind = measured_peak()
-
-    # ---- batched pH sweep (the timed workload)
-    ws = ph_sweep_workloads(rank)
-    ctxs = [crmc.Context(w) for w in ws]
-    batch = crmc.Batch(ctxs)
-    per_rep = ctxs[0].trials_per_sweep
-    per_step = per_rep * len(ctxs)
-    batch.sweep(8, 0xABC)  # launch-shape tuning (one shape per sweep)
-    for s in range(args.warmup):
-        batch.md_begin(dt, gamma, 1000 + s)
-        batch.sweep(1, 1 + s)
-        batch.md_end(dt, gamma, 1000 + s)
-    for g in ctxs:
-        g.check()
-    if world > 1:
-        torch.distributed.barrier()
-    g0 = ctxs[0]
-    clocks = ClockSampler()
-    clocks.start()
-    g0.set_timing(True)
-    g0.timing(reset=True)
-
-    def step(s):  # one MD step with the replicas' trials between its drift and its force evaluation
-        batch.md_begin(dt, gamma, 5000 + s)
-        batch.sweep(1, 100 + s)
-        batch.md_end(dt, gamma, 5000 + s)
-
-    ms = time_steps(step, args.steps, stream, flush)
-    if world > 1:
-        torch.distributed.barrier()
-    cl = clocks.stop(local)
-    tm = g0.timing(reset=True)
-    g0.set_timing(False)
-    for g in ctxs:
-        g.check()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = per_step * args.steps * world / (ms / 1e3)
-    counts = [g.counts() for g in ctxs]
-    L = float(ws[0].params["box_L"])
-    rc = float(ws[0].params["rc"])
-    info = g0.info
-    launches_per_step = info["ncol"]
-    trials_per_launch = per_rep / launches_per_step
-    bytes_launch = sum(trials_per_launch * bytes_per_trial(L, rc, c["n"]) for c in counts)
-    avg_launch_s = tm["phase_ms"] / max(tm["phase_launches"], 1) / 1e3
-    achieved = bytes_launch / avg_launch_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "k_cr_phase (13 replicas per launch)",
-                "peak_source": peak_kind, "bytes_per_trial_mean": bytes_launch / (trials_per_launch * len(ctxs)),
-                "trials_per_launch": trials_per_launch * len(ctxs), "avg_launch_us": avg_launch_s * 1e6,
-                "phase_share_of_step": tm["phase_ms"] / ms}
-
-    # ---- plain path: one replica (pH 4.5), same step definition
-    plain = None
-    if rank == 0:
-        w1 = workload(rank)
-        g1 = crmc.Context(w1)
-        g1.sweep(g1.trials_per_sweep * 8, 0xABC)
-        for s in range(3):
-            g1.md_begin(dt, gamma, 1000 + s)
-            g1.sweep(g1.trials_per_sweep, 1 + s)
-            g1.md_end(dt, gamma, 1000 + s)
-        g1.set_timing(True)
-        g1.timing(reset=True)
-        n_plain = max(10, min(args.steps, 50))
-
-        def step1(s):
-            g1.md_begin(dt, gamma, 7000 + s)
-            g1.sweep(g1.trials_per_sweep, 300 + s)
-            g1.md_end(dt, gamma, 7000 + s)
-
-        ms1 = time_steps(step1, n_plain, stream, flush)
-        tm1 = g1.timing(reset=True)
-        g1.check()
-        c1 = g1.counts()
-        al = tm1["phase_ms"] / max(tm1["phase_launches"], 1) / 1e3
-        ach1 = trials_per_launch * bytes_per_trial(L, rc, c1["n"]) / al / 1e9
-        plain = {"value": g1.trials_per_sweep * n_plain / (ms1 / 1e3), "unit": "trials/s", "steps": n_plain,
-                 "ms_per_step": ms1 / n_plain, "launch_shape": list(g1.launch_shape()),
-                 "roofline": {"achieved": ach1, "frac": ach1 / peak, "avg_launch_us": al * 1e6},
-                 "md_force_ms_per_step": tm1["md_ms"] / n_plain, "alpha_end": c1["alpha"]}
-        g1.close()
-
-    da = None
-    if rank == 0 and not args.no_da:
-        da = run_da(crmc, torch, stream, flush, ws, dt, gamma, max(10, min(args.steps, 50)))
-
-    # ---- end to end through the public API with host buffers: each step
-    # uploads every replica's configuration from pinned host memory (cr_load),
-    # runs the batched cycle and reads every replica's state back (cr_state)
-    e2e = None
-    if not args.no_e2e and rank == 0:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        cls0 = np.ascontiguousarray(ws[0].cls, np.int32)
-
-        def host_state(st):
-            ion = (st["type"] == 3) | (st["type"] == 4)
-            cl = np.where(ion, 0, cls0[np.minimum(st["id"], len(cls0) - 1).astype(np.int64)]).astype(np.int32)
-            return (int(st["n"]), pin(st["xyz"]), pin(st["vel"]), pin(st["type"]), pin(cl), pin(st["state"]))
-
-        hs = [host_state(g.state()) for g in ctxs]
-        e2e_steps = 5
-        h2d = d2h = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for s in range(e2e_steps):
-            for g, (n, hx, hv, ht, hc, hst) in zip(ctxs, hs):
-                g.load(n, hx.data_ptr(), hv.data_ptr(), ht.data_ptr(), hc.data_ptr(), hst.data_ptr())
-                h2d += n * (12 + 12 + 4 + 4 + 1)
-            batch.md_begin(dt, gamma, 9500 + s)
-            batch.sweep(1, 9000 + s)
-            batch.md_end(dt, gamma, 9500 + s)
-            outs = [g.state() for g in ctxs]
-            d2h += sum(int(o["n"]) * (16 + 16 + 8 + 4) + 64 for o in outs)
-            hs = [host_state(o) for o in outs]
-        torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
-               "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
-               "note": "per step: cr_load of the 13 replicas from pinned host buffers + batched 1e4 trials per "
-                       "replica + batched MD step + cr_state readback of every replica"}
-
-    if rank != 0:
-        return
     out = {"metric": METRIC, "value": value, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 pair terms / i64 fixed-point sums and exponent / f64 near ties",
