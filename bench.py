@@ -295,7 +295,7 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     for c in ctxs:
         c.set_surrogate(mlp)
     b = crmc.Batch(ctxs)
-    b.sweep_da(3, 0xDA)  # launch-shape tuning of the DA variant
+    b.sweep_da(5, 0xDA)  # launch-shape tuning of the DA variant
     for s in range(3):
         b.md_begin(dt, gamma, 1000 + s)
         b.sweep_da(1, 1 + s)
@@ -359,7 +359,7 @@ def run_ours(args):
     batch = crmc.Batch(ctxs)
     per_rep = ctxs[0].trials_per_sweep
     per_step = per_rep * len(ctxs)
-    batch.sweep(8, 0xABC)  # launch-shape tuning (one shape per sweep)
+    batch.sweep(12, 0xABC)  # launch-shape tuning (one shape per sweep)
     for s in range(args.warmup):
         batch.md_begin(dt, gamma, 1000 + s)
         batch.sweep(1, 1 + s)
@@ -412,7 +412,7 @@ def run_ours(args):
     if rank == 0:
         w1 = workload(rank)
         g1 = crmc.Context(w1)
-        g1.sweep(g1.trials_per_sweep * 8, 0xABC)
+        g1.sweep(g1.trials_per_sweep * 12, 0xABC)
         for s in range(3):
             g1.md_begin(dt, gamma, 1000 + s)
             g1.sweep(g1.trials_per_sweep, 1 + s)

@@ -34,7 +34,9 @@ struct cr_ctx {
   int tune_next = 0;     // next candidate to time; >= count when done
   bool tuning = true;
   float tune_ms[16] = {};
-  PhaseShape S{};
+  PhaseShape S{};   // shared-memory capacities for the densest domain
+  PhaseShape Sc{};  // compact capacities (most domains; denser ones spill to global memory)
+  bool C = false, da_C = false;  // the tuned shapes use Sc
   SysParams *d_reps = nullptr;  // device copy of P (the phase kernel reads it)
   int64_t per_sweep = 0;
   // sizes
@@ -66,7 +68,7 @@ struct cr_ctx {
   size_t dlog_cap = 0, feat_cap = 0;
   int da_T = 128, da_R = 0, da_next = 0;
   bool da_tuning = true;
-  float da_ms[4] = {};
+  float da_ms[8] = {};
   // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
@@ -439,6 +441,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.nact = global ? 1 : (P.nd / 2) * (P.nd / 2) * (P.nd / 2);
   P.dcap_glob = k * k * k * cap + 2 * P.m;
   int maxd = 0, maxh = 0;
+  std::vector<int> dsums, hsums;
   {
     const int nr = P.nr;
     auto rc_ = [&](int i, int o) {
@@ -461,6 +464,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
               }
           maxd = std::max(maxd, dsum);
           maxh = std::max(maxh, hsum);
+          dsums.push_back(dsum);
+          hsums.push_back(hsum);
         }
   }
   {
@@ -480,11 +485,12 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   S.nr3 = P.nr * P.nr * P.nr;
   S.kc3 = k * k * k;
   // Shared-memory list and halo capacities: the densest domain of the
-  // starting configuration with room for growth, and its densest halo (with
-  // a smaller capacity, denser domains keep their list in a global scratch
-  // region and read the halo beyond it from global memory: measured slower
-  // on the benchmark box, where several CTAs per SM do not hide the extra
-  // latency).  list_capacity / halo_capacity > 0 override the choice.
+  // starting configuration with room for growth, and its densest halo.  The
+  // compact set (Sc) is sized for the 90th percentile instead, so that more
+  // CTAs fit on an SM; denser domains then keep their list in a global
+  // scratch region and read the halo beyond the capacity from global memory.
+  // The tuner times shapes with either set.  list_capacity / halo_capacity > 0
+  // fix the capacities (both sets).
   S.dcs = sys->list_capacity > 0 ? sys->list_capacity + 2 * P.m : std::max(2 * maxd, maxd + 32) + 2 * P.m;
   S.dcs = std::min(P.dcap_glob, S.dcs);
   S.hcs = sys->halo_capacity > 0 ? sys->halo_capacity : std::min(maxh + maxh / 4 + 32, 4096);
@@ -495,6 +501,21 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     S.lns = std::min(P.lnmax, S.dcs + 4);
   }
   if (phase_smem_bytes(S, 512, false) > (size_t)smem_max) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  {
+    auto pct90 = [](std::vector<int> v) {
+      if (v.empty()) return 0;
+      std::sort(v.begin(), v.end());
+      return v[(size_t)(0.9 * (double)(v.size() - 1))];
+    };
+    PhaseShape &Q = c->Sc;
+    Q = S;
+    if (sys->list_capacity <= 0 && sys->halo_capacity <= 0) {
+      const int pd = pct90(dsums), ph = pct90(hsums);
+      Q.dcs = std::min(S.dcs, std::max(32, (3 * pd) / 2 + 16) + 2 * P.m);
+      Q.hcs = std::min(S.hcs, ph + ph / 4 + 32);
+      Q.lns = std::min(P.lnmax, Q.dcs + 4);
+    }
+  }
   c->smem_max = smem_max;
   P.per_sweep = c->per_sweep;
   P.key_xor = 0u;
@@ -680,25 +701,28 @@ struct TuneRef {
   int &T, &R, &next;
   bool &on;
   float *ms;
+  bool &C;  // the chosen shape uses the compact capacities
 };
 
-static void tune_skip(TuneRef t, const PhaseShape &S, int smem_max, bool da) {
+static void tune_skip(TuneRef t, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
   while (t.on && t.next < phase_shape_count(da)) {
     int t_, r_;
     phase_shape(t.next, &t_, &r_, da);
-    if (phase_shape_smem(S, t_, r_, da) <= (size_t)smem_max) break;
+    const PhaseShape &Q = phase_shape_compact(t.next, da) ? Sc : S;
+    if (phase_shape_smem(Q, t_, r_, da) <= (size_t)smem_max) break;
     t.ms[t.next++] = 1e30f;
   }
 }
 
-static void tune_finish(TuneRef t, float ms, const PhaseShape &S, int smem_max, bool da) {
+static void tune_finish(TuneRef t, float ms, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
   t.ms[t.next++] = ms;
-  tune_skip(t, S, smem_max, da);
+  tune_skip(t, S, Sc, smem_max, da);
   if (t.next == phase_shape_count(da)) {
     int best = 0;
     for (int i = 1; i < phase_shape_count(da); ++i)
       if (t.ms[i] < t.ms[best]) best = i;
     phase_shape(best, &t.T, &t.R, da);
+    t.C = phase_shape_compact(best, da);
     t.on = false;
   }
 }
@@ -730,13 +754,15 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
   if (log) CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice, s));
   const uint64_t n_sweeps = n_trials / (uint64_t)ctx->per_sweep;
   const uint32_t sweep0 = (uint32_t)ctx->sweep;
-  TuneRef tr = da ? TuneRef{ctx->da_T, ctx->da_R, ctx->da_next, ctx->da_tuning, ctx->da_ms}
-                  : TuneRef{ctx->T, ctx->R, ctx->tune_next, ctx->tuning, ctx->tune_ms};
+  TuneRef tr = da ? TuneRef{ctx->da_T, ctx->da_R, ctx->da_next, ctx->da_tuning, ctx->da_ms, ctx->da_C}
+                  : TuneRef{ctx->T, ctx->R, ctx->tune_next, ctx->tuning, ctx->tune_ms, ctx->C};
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)ctx->sweep++;
-    if (!log) tune_skip(tr, ctx->S, ctx->smem_max, da);
+    if (!log) tune_skip(tr, ctx->S, ctx->Sc, ctx->smem_max, da);
     const bool tune = tr.on && !log && tr.next < phase_shape_count(da);
     int T = tr.T, R = tr.R;
+    const bool compact = tune ? phase_shape_compact(tr.next, da) : tr.C;
+    const PhaseShape &SS = compact ? ctx->Sc : ctx->S;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
       phase_shape(tr.next, &T, &R, da);
@@ -751,7 +777,7 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
     for (int col = 0; col < P.ncol; ++col) {
       int ti;
       tbegin(ctx, 0, &ti);
-      CR_CUDA(launch_phase(ctx->d_reps, 1, P.nact, ctx->S, T, R, log != nullptr, da, s, swc, sweep0, col, k0, k1));
+      CR_CUDA(launch_phase(ctx->d_reps, 1, P.nact, SS, T, R, log != nullptr, da, s, swc, sweep0, col, k0, k1));
       tend(ctx, 0, ti);
       ctx->launches_total++;
     }
@@ -762,7 +788,7 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       cudaEventElapsedTime(&ms, e0, e1);
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      tune_finish(tr, ms, ctx->S, ctx->smem_max, da);
+      tune_finish(tr, ms, ctx->S, ctx->Sc, ctx->smem_max, da);
     }
   }
   if (log) {
@@ -1119,6 +1145,7 @@ extern "C" int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs) {
     if (t == threads && r == regs) {
       ctx->T = t;
       ctx->R = r;
+      ctx->C = false;
       ctx->tuning = false;
       found = true;
     }
@@ -1129,6 +1156,7 @@ extern "C" int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs) {
     if (t == threads && r == regs) {
       ctx->da_T = t;
       ctx->da_R = r;
+      ctx->da_C = false;
       ctx->da_tuning = false;
       found = true;
     }
@@ -1149,7 +1177,8 @@ extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t 
 struct cr_batch {
   std::vector<cr_ctx *> ctx;
   SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
-  PhaseShape S{};
+  PhaseShape S{}, Sc{};
+  bool C = false, da_C = false;
   int grid_x = 0, ncol = 8;
   int T = 128, R = 4;
   int smem_max = 0;
@@ -1158,7 +1187,7 @@ struct cr_batch {
   float tune_ms[16] = {};
   int da_T = 128, da_R = 0, da_next = 0;
   bool da_tuning = true;
-  float da_ms[4] = {};
+  float da_ms[8] = {};
   std::vector<SysParams> reps;  // host copy of d_reps
   int order_nc = 0, order_nact = 0;  // largest box and colour among replicas with a launch order (0: none)
   std::vector<cudaStream_t> streams;
@@ -1188,6 +1217,11 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     b->S.lns = std::max(b->S.lns, c->S.lns);
     b->S.nr3 = std::max(b->S.nr3, c->S.nr3);
     b->S.kc3 = std::max(b->S.kc3, c->S.kc3);
+    b->Sc.dcs = std::max(b->Sc.dcs, c->Sc.dcs);
+    b->Sc.hcs = std::max(b->Sc.hcs, c->Sc.hcs);
+    b->Sc.lns = std::max(b->Sc.lns, c->Sc.lns);
+    b->Sc.nr3 = std::max(b->Sc.nr3, c->Sc.nr3);
+    b->Sc.kc3 = std::max(b->Sc.kc3, c->Sc.kc3);
     b->grid_x = std::max(b->grid_x, c->P.nact);
     maxR = std::max(maxR, c->R);
   }
@@ -1257,8 +1291,8 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const uint32_t sweep0 = (uint32_t)c0->sweep;
-  TuneRef tr = da ? TuneRef{b->da_T, b->da_R, b->da_next, b->da_tuning, b->da_ms}
-                  : TuneRef{b->T, b->R, b->tune_next, b->tuning, b->tune_ms};
+  TuneRef tr = da ? TuneRef{b->da_T, b->da_R, b->da_next, b->da_tuning, b->da_ms, b->da_C}
+                  : TuneRef{b->T, b->R, b->tune_next, b->tuning, b->tune_ms, b->C};
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)c0->sweep;
     for (cr_ctx *c : b->ctx) {
@@ -1266,9 +1300,11 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       c->f_valid = false;
       c->fcons_valid = false;
     }
-    tune_skip(tr, b->S, b->smem_max, da);
+    tune_skip(tr, b->S, b->Sc, b->smem_max, da);
     const bool tune = tr.on && tr.next < phase_shape_count(da);
     int T = tr.T, R = tr.R;
+    const bool compact = tune ? phase_shape_compact(tr.next, da) : tr.C;
+    const PhaseShape &SS = compact ? b->Sc : b->S;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
       phase_shape(tr.next, &T, &R, da);
@@ -1283,7 +1319,7 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
     for (int col = 0; col < b->ncol; ++col) {
       int ti;
       tbegin(c0, 0, &ti);
-      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, b->S, T, R, false, da, s, swc, sweep0, col, k0, k1));
+      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, SS, T, R, false, da, s, swc, sweep0, col, k0, k1));
       tend(c0, 0, ti);
       c0->launches_total++;
     }
@@ -1294,7 +1330,7 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       cudaEventElapsedTime(&ms, e0, e1);
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
-      tune_finish(tr, ms, b->S, b->smem_max, da);
+      tune_finish(tr, ms, b->S, b->Sc, b->smem_max, da);
     }
   }
   return CR_OK;
@@ -1361,10 +1397,12 @@ extern "C" int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t r
       if (da) {
         b->da_T = t;
         b->da_R = r;
+        b->da_C = false;
         b->da_tuning = false;
       } else {
         b->T = t;
         b->R = r;
+        b->C = false;
         b->tuning = false;
       }
       found = true;

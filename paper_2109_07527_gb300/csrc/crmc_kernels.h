@@ -50,6 +50,7 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da);
 int phase_shape_count(bool da);
 size_t phase_shape_smem(const PhaseShape &S, int threads, int regs, bool da);
 void phase_shape(int i, int *threads, int *regs, bool da);
+bool phase_shape_compact(int i, bool da);  // shape i uses the compact list and halo capacities
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
                          uint32_t k0, uint32_t k1);

@@ -1376,10 +1376,14 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
 
 // (threads per CTA, halo registers per thread; 0 = halo in shared memory)
 // variants the autotuner picks from
-static const int kShapes[][2] = {{32, 0}, {64, 0}, {128, 0}, {128, 4}, {256, 0}, {256, 2}, {512, 0}, {512, 1}};
+// (threads, halo registers, compact): compact variants size the shared-memory
+// list and halo for most domains rather than the densest (denser ones spill
+// to global memory), so that more CTAs fit on an SM
+static const int kShapes[][3] = {{32, 0, 0},  {64, 0, 0},  {128, 0, 0}, {128, 4, 0}, {256, 0, 0}, {256, 2, 0},
+                                 {512, 0, 0}, {512, 1, 0}, {32, 0, 1},  {64, 0, 1},  {128, 0, 1}, {256, 0, 1}};
 
 // shapes with a delayed-acceptance variant (the surrogate runs on >= 128 threads)
-static const int kShapesDA[][2] = {{128, 0}, {256, 0}, {512, 0}};
+static const int kShapesDA[][3] = {{128, 0, 0}, {256, 0, 0}, {512, 0, 0}, {128, 0, 1}, {256, 0, 1}};
 
 int phase_shape_count(bool da) {
   return da ? (int)(sizeof(kShapesDA) / sizeof(kShapesDA[0])) : (int)(sizeof(kShapes) / sizeof(kShapes[0]));
@@ -1388,6 +1392,7 @@ void phase_shape(int i, int *threads, int *regs, bool da) {
   *threads = da ? kShapesDA[i][0] : kShapes[i][0];
   *regs = da ? kShapesDA[i][1] : kShapes[i][1];
 }
+bool phase_shape_compact(int i, bool da) { return (da ? kShapesDA[i][2] : kShapes[i][2]) != 0; }
 
 size_t phase_shape_smem(const PhaseShape &S, int threads, int regs, bool da) {
   PhaseShape Q = S;
