@@ -261,7 +261,7 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     X, y = np.concatenate([X[n_hold:], -X[n_hold:]]), np.concatenate([y[n_hold:], -y[n_hold:]])
     perm = rng.permutation(len(X))
     X, y = X[perm], y[perm]
-    Bt = 8192
+    Bt = 32768 if len(X) >= 2 * 32768 else 8192
     nb = len(X) // Bt
     Xd = torch.from_numpy(np.ascontiguousarray(X[:nb * Bt])).cuda()
     yd = torch.from_numpy(np.ascontiguousarray(y[:nb * Bt])).cuda()

@@ -79,6 +79,9 @@ struct cr_ctx {
   float4 *h_dump_pos = nullptr, *h_dump_vel = nullptr, *h_dump_frc = nullptr;
   unsigned long long *h_dump_pid = nullptr;
   int *h_dump_info = nullptr;
+  long long *h_small = nullptr;           // pinned: kind counts [6], dump count, error word
+  std::vector<int64_t> ord_at, ord;           // host scratch of cr_state's id ordering
+  std::vector<std::pair<unsigned long long, int64_t>> ord_kv, ord_tmp;
   // MD
   double fene_K = 30.0, fene_R0 = 1.5;
   uint64_t sweep = 0;
@@ -169,7 +172,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info};
+  void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info, c->h_small};
   for (void *p : hptrs)
     if (p) cudaFreeHost(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -579,7 +582,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
         cudaHostAlloc((void **)&c->h_dump_vel, cp * sizeof(float4), 0) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_dump_frc, cp * sizeof(float4), 0) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_dump_pid, cp * sizeof(unsigned long long), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_dump_info, cp * sizeof(int), 0) != cudaSuccess) {
+        cudaHostAlloc((void **)&c->h_dump_info, cp * sizeof(int), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_small, 16 * sizeof(long long), 0) != cudaSuccess) {
       free_ctx(c);
       return CR_ERR_NOMEM;
     }
@@ -676,10 +680,10 @@ extern "C" int cr_get_info(const cr_ctx *ctx, cr_info *out) {
 
 extern "C" int cr_check(cr_ctx *ctx) {
   if (!ctx) return CR_ERR_INVALID_ARG;
-  int bits = 0;
-  CR_CUDA(cudaMemcpyAsync(&bits, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int *bits = (int *)(ctx->h_small + 7);  // pinned
+  CR_CUDA(cudaMemcpyAsync(bits, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CR_CUDA(cudaStreamSynchronize(ctx->stream));
-  return err_bits_to_code(bits);
+  return err_bits_to_code(*bits);
 }
 
 // grow a device record buffer to n entries (records of logged calls only)
@@ -981,20 +985,23 @@ extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
 extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   if (!ctx || !out) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
-  long long kinds[6];
-  CR_CUDA(cudaMemcpyAsync(kinds, ctx->d_counts, sizeof(kinds), cudaMemcpyDeviceToHost, s));
+  long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] dump count, [7] error word
+  int *herr = (int *)(hs + 7);
+  CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaMemcpyAsync(herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaStreamSynchronize(s));
-  out->n_A = kinds[K_A0] + kinds[K_A1];
-  out->n_Am = kinds[K_A1];
-  out->n_B = kinds[K_B0] + kinds[K_B1];
-  out->n_Bp = kinds[K_B1];
-  out->n_Xp = kinds[K_XP];
-  out->n_Xm = kinds[K_XM];
+  out->n_A = hs[K_A0] + hs[K_A1];
+  out->n_Am = hs[K_A1];
+  out->n_B = hs[K_B0] + hs[K_B1];
+  out->n_Bp = hs[K_B1];
+  out->n_Xp = hs[K_XP];
+  out->n_Xm = hs[K_XM];
   out->n = out->n_A + out->n_B + out->n_Xp + out->n_Xm + ctx->n_other;
   out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
   out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
+  const int err0 = err_bits_to_code(*herr);
   const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state;
-  if (!want) return cr_check(ctx);
+  if (!want || err0 != CR_OK) return err0;
   const int64_t n = out->n;
   if (n > ctx->capacity) return CR_ERR_CAPACITY;
   DumpBufs D{ctx->d_counter, (int)n, ctx->d_dump_pos, ctx->d_dump_vel, ctx->d_dump_frc, ctx->d_dump_pid,
@@ -1002,11 +1009,11 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   float4 *hpos = ctx->h_dump_pos, *hvel = ctx->h_dump_vel, *hfrc = ctx->h_dump_frc;
   unsigned long long *hpid = ctx->h_dump_pid;
   int *hinfo = ctx->h_dump_info;
-  int got = 0;
+  int *hgot = (int *)(hs + 6);
   CR_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
   CR_CUDA(launch_dump(ctx->P, D, s));
   ctx->launches_total++;
-  CR_CUDA(cudaMemcpyAsync(&got, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaMemcpyAsync(hgot, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (out->xyz) CR_CUDA(cudaMemcpyAsync(hpos, ctx->d_dump_pos, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
   if (out->vel) CR_CUDA(cudaMemcpyAsync(hvel, ctx->d_dump_vel, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
   if (out->force && ctx->fcons_valid)
@@ -1014,28 +1021,42 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   CR_CUDA(cudaMemcpyAsync(hpid, ctx->d_dump_pid, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaMemcpyAsync(hinfo, ctx->d_dump_info, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaStreamSynchronize(s));
-  if (got != n) return CR_ERR_CUDA;
-  if (out->force && !ctx->fcons_valid)
-    for (int64_t i = 0; i < n; ++i) hfrc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (*hgot != n) return CR_ERR_CUDA;
   // order by id: input ids are dense (bucket them), inserted ions are sorted
-  std::vector<int64_t> ord;
-  ord.reserve(n);
-  {
-    std::vector<int64_t> at(ctx->n_input, -1), rest;
-    for (int64_t i = 0; i < n; ++i) {
-      if (hpid[i] < (unsigned long long)ctx->n_input) at[hpid[i]] = i;
-      else rest.push_back(i);
-    }
-    for (int64_t v : at)
-      if (v >= 0) ord.push_back(v);
-    std::sort(rest.begin(), rest.end(), [&](int64_t x, int64_t y) { return hpid[x] < hpid[y]; });
-    ord.insert(ord.end(), rest.begin(), rest.end());
+  // by an LSD radix sort on their 64-bit ids (bytes that do not vary skipped)
+  std::vector<int64_t> &at = ctx->ord_at, &ord = ctx->ord;
+  auto &kv = ctx->ord_kv, &tmp = ctx->ord_tmp;
+  at.assign((size_t)ctx->n_input, -1);
+  ord.clear();
+  kv.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    if (hpid[i] < (unsigned long long)ctx->n_input) at[hpid[i]] = i;
+    else kv.emplace_back(hpid[i], i);
   }
+  for (int64_t v : at)
+    if (v >= 0) ord.push_back(v);
+  for (int shift = 0; shift < 64 && kv.size() > 1; shift += 8) {
+    size_t cnt[257] = {0};
+    for (const auto &p : kv) cnt[((p.first >> shift) & 255u) + 1]++;
+    bool one = false;
+    for (int d = 0; d < 256 && !one; ++d) one = cnt[d + 1] == kv.size();
+    if (one) continue;
+    for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
+    tmp.resize(kv.size());
+    for (const auto &p : kv) tmp[cnt[(p.first >> shift) & 255u]++] = p;
+    kv.swap(tmp);
+  }
+  for (const auto &p : kv) ord.push_back(p.second);
+  const bool frc_ok = ctx->fcons_valid;
   for (int64_t o = 0; o < n; ++o) {
     const int64_t i = ord[o];
     if (out->xyz) { out->xyz[3 * o] = hpos[i].x; out->xyz[3 * o + 1] = hpos[i].y; out->xyz[3 * o + 2] = hpos[i].z; }
     if (out->vel) { out->vel[3 * o] = hvel[i].x; out->vel[3 * o + 1] = hvel[i].y; out->vel[3 * o + 2] = hvel[i].z; }
-    if (out->force) { out->force[3 * o] = hfrc[i].x; out->force[3 * o + 1] = hfrc[i].y; out->force[3 * o + 2] = hfrc[i].z; }
+    if (out->force) {
+      out->force[3 * o] = frc_ok ? hfrc[i].x : 0.0f;
+      out->force[3 * o + 1] = frc_ok ? hfrc[i].y : 0.0f;
+      out->force[3 * o + 2] = frc_ok ? hfrc[i].z : 0.0f;
+    }
     if (out->id) out->id[o] = hpid[i];
     const int info = hinfo[i];
     const int t = info & INFO_TYPE_MASK;
@@ -1044,7 +1065,7 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
     if (out->state) out->state[o] = (int8_t)ion;
     if (out->site_state && (t == CR_ACID || t == CR_BASE)) out->site_state[info >> INFO_SITE_SHIFT] = (int8_t)ion;
   }
-  return cr_check(ctx);
+  return CR_OK;
 }
 
 extern "C" int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,
@@ -1095,7 +1116,8 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
   }
-  CR_CUDA(cudaMemcpyAsync(ctx->d_counts, kinds, sizeof(long long) * 6, cudaMemcpyHostToDevice, s));
+  (void)kinds;  // counted again on the device by the load kernel (no pageable copy)
+  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * 6, s));
   LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
              ctx->d_in_state, n, ctx->n_input};
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1189,6 +1211,7 @@ struct cr_batch {
   bool da_tuning = true;
   float da_ms[8] = {};
   std::vector<SysParams> reps;  // host copy of d_reps
+  cudaStream_t stream = nullptr;  // the contexts' shared stream (destroy does not touch the contexts)
   int order_nc = 0, order_nact = 0;  // largest box and colour among replicas with a launch order (0: none)
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
@@ -1226,6 +1249,7 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     maxR = std::max(maxR, c->R);
   }
   b->ncol = ctxs[0]->P.ncol;
+  b->stream = ctxs[0]->stream;
   b->R = 0;
   (void)maxR;
   b->tuning = std::getenv("CRMC_NO_TUNE") == nullptr;
@@ -1259,7 +1283,7 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
 
 extern "C" void cr_batch_destroy(cr_batch *b) {
   if (!b) return;
-  cudaStreamSynchronize(b->ctx[0]->stream);
+  cudaStreamSynchronize(b->stream);
   for (size_t r = 0; r < b->streams.size(); ++r) {
     cudaStreamSynchronize(b->streams[r]);
     cudaStreamDestroy(b->streams[r]);

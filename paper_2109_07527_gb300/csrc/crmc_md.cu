@@ -11,12 +11,10 @@
 namespace crmc {
 
 // ---------------------------------------------------------------------------
-// MD forces: a group of 8 lanes per particle; the lanes of a group share the
-// (2h+1)^3 neighbour cells (cell side >= rc/h) and the group adds its pair
-// forces in 2^-24 fixed point, so the result does not depend on the launch
-// shape or the order of the particle list.  Mode 0: conservative forces into
-// fout; mode 1: + Langevin friction/noise; mode 2: + Langevin and the closing
-// half kick v += dt/2 f.
+// MD force helpers: FP32 pair forces summed in 2^-24 fixed point, so the
+// result does not depend on the launch shape or the order of the particle
+// list.  Mode 0: conservative forces into fout; mode 1: + Langevin
+// friction/noise; mode 2: + Langevin and the closing half kick v += dt/2 f.
 // ---------------------------------------------------------------------------
 constexpr float FFIX_INV = 1.0f / 16777216.0f;
 
@@ -327,11 +325,17 @@ __global__ void k_perm_slots(SysParams P, int *perm_slot, int n_perm) {
 
 // dump every particle (unordered) for the state view
 __global__ void k_dump(SysParams P, DumpBufs D) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.ncell * P.cap) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
   const int c = g / P.cap;
-  if (g - c * P.cap >= P.cnt[c]) return;
-  const int o = atomicAdd(D.counter, 1);
+  const bool have = g < P.ncell * P.cap && g - c * P.cap < P.cnt[c];
+  const unsigned m = __ballot_sync(0xffffffffu, have);  // one atomic per warp
+  if (m == 0u) return;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(D.counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (!have) return;
+  const int o = base + __popc(m & ((1u << lane) - 1u));
   if (o >= D.cap) return;
   D.pos[o] = P.pos[g];
   D.pid[o] = P.pid[g];
@@ -353,6 +357,12 @@ __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
   else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
   else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
   else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+  {  // global kind counts (zeroed by the host before the launch)
+    const int kd = t == CR_ACID ? (ion ? K_A1 : K_A0)
+                   : t == CR_BASE ? (ion ? K_B1 : K_B0)
+                   : t == CR_XP ? K_XP : (t == CR_XM ? K_XM : K_OTHER);
+    if (kd < K_OTHER) atomicAdd((unsigned long long *)&P.counts[kd], 1ull);
+  }
   const int site = (i < I.n_site_map && I.site[i] >= 0) ? I.site[i] : 0;
   const int nc = P.nc;
   const int cell = cell_of(x, P.scf, nc) + nc * (cell_of(y, P.scf, nc) + nc * cell_of(z, P.scf, nc));
