@@ -633,7 +633,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.gs_info = c->d_gs_info;
   P.gs_rank = c->d_gs_rank;
   P.order = nullptr;
-  if (!global && nc <= ORDER_MAX_NC && P.nact <= ORDER_MAX_NACT) {
+  if (!global && P.nact <= ORDER_MAX_NACT) {
     // densest-first launch order, recomputed every sweep; starts as the identity
     std::vector<int> ident((size_t)P.ncol * P.nact);
     for (size_t i = 0; i < ident.size(); ++i) ident[i] = (int)(i % (size_t)P.nact);
@@ -775,7 +775,7 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       cudaEventRecord(e0, s);
     }
     if (P.order) {
-      CR_CUDA(launch_domain_order(ctx->d_reps, 1, P.nc, P.nact, s, swc, k0, k1));
+      CR_CUDA(launch_domain_order(ctx->d_reps, 1, P.ncol, P.nact, s, swc, k0, k1));
       ctx->launches_total++;
     }
     for (int col = 0; col < P.ncol; ++col) {
@@ -1337,7 +1337,7 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       cudaEventRecord(e0, s);
     }
     if (b->order_nc > 0) {
-      CR_CUDA(launch_domain_order(b->d_reps, n, b->order_nc, b->order_nact, s, swc, k0, k1));
+      CR_CUDA(launch_domain_order(b->d_reps, n, b->ncol, b->order_nact, s, swc, k0, k1));
       c0->launches_total++;
     }
     for (int col = 0; col < b->ncol; ++col) {

@@ -98,10 +98,8 @@ struct SysParams {
   int *order;
 };
 
-// domain ordering is computed in shared memory for boxes of at most this many
-// cells per dimension and at most this many active domains per colour
-constexpr int ORDER_MAX_NC = 24;
-constexpr int ORDER_MAX_NACT = 512;
+// domains are launched densest first for colours of at most this many domains
+constexpr int ORDER_MAX_NACT = 4096;
 
 // surrogate MLP sizes and the offsets of its parts in mlp_w / mlp_b
 constexpr int MLP_IN = 48;

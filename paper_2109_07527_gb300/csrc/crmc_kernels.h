@@ -55,8 +55,8 @@ cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const P
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
                          uint32_t k0, uint32_t k1);
 // launch order of every colour's domains for one sweep (densest region first);
-// does nothing for boxes or colours beyond the ordering limits
-cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int nc, int nact, cudaStream_t s, uint32_t sweep,
+// does nothing for colours beyond the ordering limit
+cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, int nact, cudaStream_t s, uint32_t sweep,
                                 uint32_t k0, uint32_t k1);
 // particle list (plist, n_particles: device scratch of max_particles + 1
 // ints), then the force kernel (one warp per particle)

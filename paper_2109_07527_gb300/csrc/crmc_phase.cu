@@ -1240,83 +1240,56 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
 }
 
 // ---------------------------------------------------------------------------
-// Launch order of the domains of every colour for one sweep: the particles in
+// Launch order of the domains of one colour for one sweep: the particles in
 // each domain's region (its cells and the halo around them, counted at the
-// start of the sweep: box sums of the cell counts, separable over x, y, z with
-// periodic wrap) and, per colour, the domains ranked by decreasing count (ties
-// by index).  Only the order of independent CTAs changes, never a result.
-// One CTA per replica; boxes and colours above ORDER_MAX_NC / ORDER_MAX_NACT
-// keep the natural order (order is then not used: P.order is null).
+// start of the sweep; one warp sums a region's cell counts) and the domains
+// ranked by decreasing count (ties by index).  Only the order of independent
+// CTAs changes, never a result.  One CTA per (replica, colour); colours of
+// more than ORDER_MAX_NACT domains keep the natural order (P.order is null).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_domain_order(const SysParams *__restrict__ reps, uint32_t sweep, uint32_t key0,
                                                       uint32_t key1_base) {
   const SysParams &P = reps[blockIdx.x];
   if (!P.order) return;
-  extern __shared__ int osm[];
-  const int nc = P.nc, nr = P.nr, h = P.h, k = P.k, nact = P.nact, ncell = nc * nc * nc;
-  int *a = osm, *bsum = osm + ncell, *cost = osm + 2 * ncell;
-  const int tid = threadIdx.x, T = blockDim.x;
+  __shared__ int cost[ORDER_MAX_NACT];
+  const int c = blockIdx.y;
+  if (c >= P.ncol) return;
+  const int nc = P.nc, nr = P.nr, h = P.h, k = P.k, nact = P.nact;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const uint32_t key1 = key1_base ^ P.key_xor;
   const uint4 w = philox10(0u, 0u, sweep, 4u, key0, key1);
   const int off[3] = {pick32(w.x, nc), pick32(w.y, nc), pick32(w.z, nc)};
-  for (int i = tid; i < ncell; i += T) a[i] = P.cnt[i];
-  __syncthreads();
-  // window sums of nr cells along x, then y, then z (b = sum over [c, c + nr))
-  for (int i = tid; i < ncell; i += T) {
-    const int x = i % nc, yz = i - x;
-    int sum = 0;
-    for (int j = 0; j < nr; ++j) sum += a[yz + (x + j) % nc];
-    bsum[i] = sum;
-  }
-  __syncthreads();
-  for (int i = tid; i < ncell; i += T) {
-    const int x = i % nc, y = (i / nc) % nc, z = i / (nc * nc);
-    int sum = 0;
-    for (int j = 0; j < nr; ++j) sum += bsum[x + nc * ((y + j) % nc + nc * z)];
-    a[i] = sum;
-  }
-  __syncthreads();
-  for (int i = tid; i < ncell; i += T) {
-    const int x = i % nc, y = (i / nc) % nc, z = i / (nc * nc);
-    int sum = 0;
-    for (int j = 0; j < nr; ++j) sum += a[x + nc * (y + nc * ((z + j) % nc))];
-    bsum[i] = sum;
-  }
-  __syncthreads();
-  const int hn = P.nd >> 1;
-  for (int c = 0; c < P.ncol; ++c) {
-    for (int b = tid; b < nact; b += T) {
-      int o[3];
-      const int dd[3] = {2 * (b % hn) + (c & 1), 2 * ((b / hn) % hn) + ((c >> 1) & 1), 2 * (b / (hn * hn)) + ((c >> 2) & 1)};
+  const int hn = P.nd >> 1, nr3 = nr * nr * nr;
+  for (int b = wid; b < nact; b += nwarp) {
+    const int dd[3] = {2 * (b % hn) + (c & 1), 2 * ((b / hn) % hn) + ((c >> 1) & 1), 2 * (b / (hn * hn)) + ((c >> 2) & 1)};
+    int o[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) o[i] = ((off[i] + dd[i] * k - h) % nc + nc) % nc;  // region origin
-      cost[b] = bsum[o[0] + nc * (o[1] + nc * o[2])];
+    for (int i = 0; i < 3; ++i) o[i] = ((off[i] + dd[i] * k - h) % nc + nc) % nc;  // region origin
+    int sum = 0;
+    for (int i = lane; i < nr3; i += 32) {
+      const int ix = i % nr, iy = (i / nr) % nr, iz = i / (nr * nr);
+      sum += P.cnt[(o[0] + ix) % nc + nc * ((o[1] + iy) % nc + nc * ((o[2] + iz) % nc))];
     }
-    __syncthreads();
-    for (int b = tid; b < nact; b += T) {
-      const int cb = cost[b];
-      int rank = 0;
-      for (int j = 0; j < nact; ++j) {
-        const int cj = cost[j];
-        rank += (cj > cb || (cj == cb && j < b)) ? 1 : 0;
-      }
-      P.order[c * nact + rank] = b;
+#pragma unroll
+    for (int x = 16; x > 0; x >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, x);
+    if (lane == 0) cost[b] = sum;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nact; b += blockDim.x) {
+    const int cb = cost[b];
+    int rank = 0;
+    for (int j = 0; j < nact; ++j) {
+      const int cj = cost[j];
+      rank += (cj > cb || (cj == cb && j < b)) ? 1 : 0;
     }
-    __syncthreads();
+    P.order[c * nact + rank] = b;
   }
 }
 
-cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int nc, int nact, cudaStream_t s, uint32_t sweep,
+cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, int nact, cudaStream_t s, uint32_t sweep,
                                 uint32_t k0, uint32_t k1) {
-  if (nc > ORDER_MAX_NC || nact > ORDER_MAX_NACT) return cudaSuccess;  // contexts keep P.order null then
-  const size_t smem = sizeof(int) * (2 * (size_t)nc * nc * nc + nact);
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_domain_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  k_domain_order<<<n_rep, 512, smem, s>>>(d_reps, sweep, k0, k1);
+  if (nact > ORDER_MAX_NACT) return cudaSuccess;  // contexts keep P.order null then
+  k_domain_order<<<dim3(n_rep, ncol), 512, 0, s>>>(d_reps, sweep, k0, k1);
   return cudaGetLastError();
 }
 
