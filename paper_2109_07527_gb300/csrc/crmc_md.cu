@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   __shared__ int queue[MD_NW][MD_QCAP];
   __shared__ int cpre[MD_NW][MD_CPL * 32 + 1];  // exclusive prefix of the stencil cells' counts
   __shared__ int cbs[MD_NW][MD_CPL * 32];       // first slot of each stencil cell
+  __shared__ int startcell[MD_NW][32];          // per round: the cell that starts at each candidate position
   const int lane = threadIdx.x & 31;
   const int wl = threadIdx.x >> 5;
   const int w = blockIdx.x * MD_NW + wl;
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   // stencil cell o = lane + 32 t: its first slot and count; the candidates of
   // all cells are then numbered consecutively (exclusive prefix over o)
   int run = 0;
+  int lpre[MD_CPL], lcnt[MD_CPL];  // this lane's cells: first candidate number and count
 #pragma unroll
   for (int t = 0; t < MD_CPL; ++t) {
     const int o = lane + 32 * t;
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     }
     cpre[wl][o] = run + x - n;
     cbs[wl][o] = base;
+    lpre[t] = run + x - n;
+    lcnt[t] = n;
     run += __shfl_sync(0xffffffffu, x, 31);
   }
   if (lane == 0) cpre[wl][MD_CPL * 32] = run;
@@ -187,18 +191,30 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   const int *pre = cpre[wl];
   int qn = 0;
   long long fx = 0, fy = 0, fz = 0;
+  int carry = 0;  // the cell that runs on past the previous round's last candidate
   for (int c0 = 0; c0 < total; c0 += 32) {
     const int c = c0 + lane;
+    // cell of candidate c: the last non-empty cell that starts at or before
+    // it; each lane marks where its own cells start inside this round
+    unsigned mk = 0u;
+#pragma unroll
+    for (int t = 0; t < MD_CPL; ++t) {
+      const int st = lpre[t] - c0;
+      if (lcnt[t] > 0 && st >= 0 && st < 32) {
+        mk |= 1u << st;
+        startcell[wl][st] = lane + 32 * t;
+      }
+    }
+    mk = __reduce_or_sync(0xffffffffu, mk);
+    __syncwarp();
+    const unsigned upto = mk & (0xffffffffu >> (31 - lane));
+    const int cell_o = upto ? startcell[wl][31 - __clz(upto)] : carry;
+    carry = __shfl_sync(0xffffffffu, cell_o, 31);
+    __syncwarp();
     bool in = false;
     int gj = -1;
     if (c < total) {
-      int lo = 0, hi = MD_CPL * 32;  // last cell o with pre[o] <= c
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (pre[mid] <= c) lo = mid;
-        else hi = mid;
-      }
-      gj = cbs[wl][lo] + (c - pre[lo]);
+      gj = cbs[wl][cell_o] + (c - pre[cell_o]);
       if (gj != gi) {
         const float4 pj = P.pos[gj];
         const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
