@@ -45,7 +45,10 @@ constexpr int GK = 64;           // K per pipeline stage: one 128-byte swizzle r
 constexpr int GSTAGES = 4;
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-enum Epi { EPI_RELU = 0, EPI_MASK = 1, EPI_ATOMIC = 2, EPI_HEAD = 3, EPI_STORE = 4 };
+// epilogues: bias + ReLU; backward ReLU mask with column sums; atomic add (split-K
+// into one output); output layer + loss; plain store; plain store of one split's
+// partial result (split-K into per-split slices, summed afterwards in split order)
+enum Epi { EPI_RELU = 0, EPI_MASK = 1, EPI_ATOMIC = 2, EPI_HEAD = 3, EPI_STORE = 4, EPI_PARTIAL = 5 };
 
 struct GemmEpi {
   const float *bias;        // [N] (RELU, HEAD)
@@ -164,8 +167,8 @@ __host__ __device__ constexpr int tmem_cols() {
 }
 
 template <int BN>
-constexpr size_t mma_smem_bytes() {
-  return 1024 + (size_t)GSTAGES * (GM * 128 + BN * 128) + 256;
+constexpr size_t mma_smem_bytes() {  // alignment slack, operand ring, barriers, column accumulators
+  return 1024 + (size_t)GSTAGES * (GM * 128 + BN * 128) + 256 + 2 * BN * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t *empty = full + GSTAGES;
   uint64_t *done = empty + GSTAGES;
   uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  float *colacc = (float *)(sB + GSTAGES * BN * 128 + 256);  // per-CTA column sums [2][BN]
   constexpr uint32_t TCOLS = tmem_cols<BN>();
   constexpr uint32_t IDESC = idesc_bf16(GM, BN);
   constexpr uint32_t STAGE_BYTES = (GM + BN) * 128;
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(128, 1)
   const int kend = min(K, kbeg + k_split);
   const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
 
+  for (int i = threadIdx.x; i < 2 * BN; i += blockDim.x) colacc[i] = 0.0f;
   if (threadIdx.x == 0) {
     for (int s = 0; s < GSTAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -302,8 +307,8 @@ __global__ void __launch_bounds__(128, 1)
           if (rv) E.g3T[(size_t)n * E.ldt3 + row] = gb[j];
           const float sg = warp_sum_f(g), sw = warp_sum_f(dy * h);
           if (lane == 0) {
-            atomicAdd(&E.gb3[n], sg);
-            atomicAdd(&E.gw4[n], sw);
+            atomicAdd(&colacc[n - n0], sg);
+            atomicAdd(&colacc[BN + n - n0], sw);
           }
         }
         if (rv) {
@@ -318,7 +323,15 @@ __global__ void __launch_bounds__(128, 1)
       for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
         tmem_ld16(tbase + c0, v);
-        if constexpr (EPI == EPI_ATOMIC || EPI == EPI_STORE) {
+        if constexpr (EPI == EPI_PARTIAL) {
+          if (rv && n0 + c0 + 16 <= N) {  // slice blockIdx.z of [splits][M][ldf], 16-byte stores
+            float4 *o = (float4 *)(E.outF + ((size_t)blockIdx.z * M + row) * E.ldf + n0 + c0);
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+            o[2] = make_float4(v[8], v[9], v[10], v[11]);
+            o[3] = make_float4(v[12], v[13], v[14], v[15]);
+          }
+        } else if constexpr (EPI == EPI_ATOMIC || EPI == EPI_STORE) {
           if (rv) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -331,6 +344,16 @@ __global__ void __launch_bounds__(128, 1)
           }
         } else {
         uint16_t hb[16];
+        uint16_t mrow[16];  // the mask row's 16 BF16 values (two 16-byte loads)
+        if (EPI == EPI_MASK) {
+          uint4 mr[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+          if (rv) {
+            const uint4 *src = (const uint4 *)(E.mask + (size_t)row * E.ldm + n0 + c0);
+            mr[0] = src[0];
+            mr[1] = src[1];
+          }
+          memcpy(mrow, mr, sizeof(mrow));
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c0 + j;
@@ -338,10 +361,10 @@ __global__ void __launch_bounds__(128, 1)
           if (EPI == EPI_RELU) {
             x = fmaxf(v[j] + E.bias[n], 0.0f);
           } else {  // EPI_MASK
-            const float mk = rv ? from_bf16(E.mask[(size_t)row * E.ldm + n]) : 0.0f;
+            const float mk = rv ? from_bf16(mrow[j]) : 0.0f;
             x = mk > 0.0f ? v[j] : 0.0f;
             const float cs = warp_sum_f(rv ? x : 0.0f);
-            if (lane == 0) atomicAdd(&E.colsum[n], cs);
+            if (lane == 0) atomicAdd(&colacc[n - n0], cs);
           }
           hb[j] = to_bf16(x);
           if (rv && E.outT) E.outT[(size_t)n * E.ldt + row] = hb[j];
@@ -364,6 +387,15 @@ __global__ void __launch_bounds__(128, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (!fail && nk > 0) {  // one global add per column and CTA
+    if (EPI == EPI_MASK)
+      for (int i = threadIdx.x; i < BN && n0 + i < N; i += blockDim.x) atomicAdd(&E.colsum[n0 + i], colacc[i]);
+    if (EPI == EPI_HEAD)
+      for (int i = threadIdx.x; i < BN && n0 + i < N; i += blockDim.x) {
+        atomicAdd(&E.gb3[n0 + i], colacc[i]);
+        atomicAdd(&E.gw4[n0 + i], colacc[BN + i]);
+      }
+  }
   __syncwarp();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
@@ -409,6 +441,15 @@ __global__ void k_weights_bf16(const float *P, Bf16Copies C) {
     C.W3T[k * MLP_H + o] = b;
   }
   if (i < MLP_H) C.w4[i] = to_bf16(P[OFF_W4 + i]);
+}
+
+// sum of the split-K slices [splits][count] in split order (deterministic)
+__global__ void k_sum_splits(const float *__restrict__ part, int splits, int count, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float acc = 0.0f;
+  for (int z = 0; z < splits; ++z) acc += part[(size_t)z * count + i];
+  out[i] = acc;
 }
 
 // Adam (bias-corrected) on every master parameter
@@ -497,6 +538,8 @@ struct cr_trainer {
   uint16_t *Xb = nullptr, *XbT = nullptr, *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1T = nullptr, *H2T = nullptr,
            *G3 = nullptr, *G3T = nullptr, *G2 = nullptr, *G2T = nullptr, *G1T = nullptr;
   uint16_t *wb = nullptr;  // BF16 weight copies (one block)
+  float *part = nullptr;   // split-K slices of a weight gradient [max_splits][128][128]
+  int max_splits = 0;
   Bf16Copies C{};
   int64_t launches = 0;
 };
@@ -504,7 +547,7 @@ struct cr_trainer {
 static void free_trainer(cr_trainer *t) {
   if (!t) return;
   void *ptrs[] = {t->P,  t->G,   t->Mm,  t->Vv, t->tc,  t->err, t->Xb, t->XbT, t->H1, t->H2,
-                  t->H3, t->H1T, t->H2T, t->G3, t->G3T, t->G2,  t->G2T, t->G1T, t->wb};
+                  t->H3, t->H1T, t->H2T, t->G3, t->G3T, t->G2,  t->G2T, t->G1T, t->wb, t->part};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -540,6 +583,11 @@ extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train
   for (uint16_t **p : {&t->H1, &t->H2, &t->H3, &t->H1T, &t->H2T, &t->G3, &t->G3T, &t->G2, &t->G2T, &t->G1T})
     al(p, B * MLP_H);
   al(&t->wb, (size_t)MLP_H * 64 + 4 * MLP_H * MLP_H + MLP_H);
+  {
+    const int ks = split_for(cfg->max_batch, 1);
+    t->max_splits = (cfg->max_batch + ks - 1) / ks;
+    al(&t->part, (size_t)t->max_splits * MLP_H * MLP_H);
+  }
   if (!ok) {
     free_trainer(t);
     return CR_ERR_NOMEM;
@@ -640,13 +688,22 @@ static int train_grads(cr_trainer *t, const float *X, const float *target, int B
   H.gb4 = G + OFF_B4;
   H.loss = t->loss;
   if ((rc = launch_mma<128, EPI_HEAD>(t->H2, t->C.W3, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, H, s)) != CR_OK) return rc;
-  // gW3 = G3^T H2 (K = batch, split over the SMs)
+  // weight gradients: K = batch split over about one wave of CTAs, each split
+  // storing its slice, the slices summed in split order
+  const int ks = split_for(B, 1);
+  const int splits = (B + ks - 1) / ks;
+  if (splits > t->max_splits) return CR_ERR_INVALID_ARG;
   GemmEpi A{};
   A.err = t->err;
-  A.outF = G + OFF_W3;
+  A.outF = t->part;
+  auto sum_into = [&](float *dst, int count) {
+    k_sum_splits<<<(count + 255) / 256, 256, 0, s>>>(t->part, splits, count, dst);
+    return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+  };
+  // gW3 = G3^T H2
   A.ldf = MLP_H;
-  const int ks = split_for(B, 1);
-  if ((rc = launch_mma<128, EPI_ATOMIC>(t->G3T, t->H2T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = launch_mma<128, EPI_PARTIAL>(t->G3T, t->H2T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = sum_into(G + OFF_W3, MLP_H * MLP_H)) != CR_OK) return rc;
   // G2 = (G3 W3) * [H2 > 0]; gb2
   GemmEpi Mk{};
   Mk.err = t->err;
@@ -659,8 +716,8 @@ static int train_grads(cr_trainer *t, const float *X, const float *target, int B
   Mk.colsum = G + OFF_B2;
   if ((rc = launch_mma<128, EPI_MASK>(t->G3, t->C.W3T, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, Mk, s)) != CR_OK) return rc;
   // gW2 = G2^T H1
-  A.outF = G + OFF_W2;
-  if ((rc = launch_mma<128, EPI_ATOMIC>(t->G2T, t->H1T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = launch_mma<128, EPI_PARTIAL>(t->G2T, t->H1T, MLP_H, MLP_H, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = sum_into(G + OFF_W2, MLP_H * MLP_H)) != CR_OK) return rc;
   // G1 = (G2 W2) * [H1 > 0] (transposed only); gb1
   Mk.mask = t->H1;
   Mk.out = nullptr;
@@ -668,9 +725,10 @@ static int train_grads(cr_trainer *t, const float *X, const float *target, int B
   Mk.colsum = G + OFF_B1;
   if ((rc = launch_mma<128, EPI_MASK>(t->G2, t->C.W2T, B, MLP_H, MLP_H, MLP_H, MLP_H, MLP_H, Mk, s)) != CR_OK) return rc;
   // gW1 = G1^T X
-  A.outF = G + OFF_W1;
   A.ldf = MLP_IN;
-  if ((rc = launch_mma<48, EPI_ATOMIC>(t->G1T, t->XbT, MLP_H, MLP_IN, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = launch_mma<48, EPI_PARTIAL>(t->G1T, t->XbT, MLP_H, MLP_IN, B, B, B, ks, A, s)) != CR_OK) return rc;
+  if ((rc = sum_into(G + OFF_W1, MLP_H * MLP_IN)) != CR_OK) return rc;
+  t->launches += 3;
   t->launches += 8;
   return CR_OK;
 }
