@@ -234,6 +234,9 @@ def measured_tensor_peak():
     return FALLBACK_BF16_TFLOPS, "fallback"
 
 
+# unlogged sweeps that time every launch shape once (the tuner has 12 plain shapes)
+TUNE_SWEEPS = 14
+
 # floating-point operations of one training row (algorithmic, K = 48 input):
 # forward 48x128 + 2 x 128x128, backward 4 x 128x128 + 128x48, 2 flops per MAC
 TRAIN_FLOPS_PER_ROW = 2 * (48 * 128 + 2 * 128 * 128) + 2 * (4 * 128 * 128 + 128 * 48)
@@ -359,7 +362,7 @@ def run_ours(args):
     batch = crmc.Batch(ctxs)
     per_rep = ctxs[0].trials_per_sweep
     per_step = per_rep * len(ctxs)
-    batch.sweep(12, 0xABC)  # launch-shape tuning (one shape per sweep)
+    batch.sweep(TUNE_SWEEPS, 0xABC)  # launch-shape tuning (one shape per sweep)
     for s in range(args.warmup):
         batch.md_begin(dt, gamma, 1000 + s)
         batch.sweep(1, 1 + s)
@@ -412,7 +415,7 @@ def run_ours(args):
     if rank == 0:
         w1 = workload(rank)
         g1 = crmc.Context(w1)
-        g1.sweep(g1.trials_per_sweep * 12, 0xABC)
+        g1.sweep(g1.trials_per_sweep * TUNE_SWEEPS, 0xABC)
         for s in range(3):
             g1.md_begin(dt, gamma, 1000 + s)
             g1.sweep(g1.trials_per_sweep, 1 + s)
@@ -451,7 +454,6 @@ def run_ours(args):
         # step (allocated once, as a caller coupling the library to its own
         # host-side code would): cr_load uploads it, the batched cycle runs,
         # cr_state reads the new configuration back into the same buffers
-        cls0 = np.ascontiguousarray(ws[0].cls, np.int32)
         bufs = []
         for g in ctxs:
             cap = g.capacity
@@ -465,14 +467,8 @@ def run_ours(args):
 
         def read_back(g, b):
             c = g.state_into(xyz=b["xyz"].data_ptr(), vel=b["vel"].data_ptr(), id=b["id"].data_ptr(),
-                             type=b["type"].data_ptr(), state=b["state"].data_ptr())
-            n = int(c["n"])
-            ids = b["id"].numpy()[:n].view(np.uint64)
-            t = b["type"].numpy()[:n]
-            ion = (t == 3) | (t == 4)
-            np.copyto(b["cls"].numpy()[:n], cls0[np.minimum(ids, len(cls0) - 1).astype(np.int64)])
-            b["cls"].numpy()[:n][ion] = 0
-            return n
+                             type=b["type"].data_ptr(), state=b["state"].data_ptr(), cls=b["cls"].data_ptr())
+            return int(c["n"])
 
         ns = [read_back(g, b) for g, b in zip(ctxs, bufs)]
         e2e_steps = 5
@@ -488,7 +484,7 @@ def run_ours(args):
             batch.sweep(1, 9000 + s)
             batch.md_end(dt, gamma, 9500 + s)
             ns = [read_back(g, b) for g, b in zip(ctxs, bufs)]
-            d2h += sum(n * (16 + 16 + 8 + 4) + 64 for n in ns)
+            d2h += sum(n * (12 + 12 + 8 + 4 + 1 + 4) + 64 for n in ns)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,

@@ -193,6 +193,7 @@ typedef struct {
   int32_t *type;         /* [n] */
   int8_t *state;         /* [n] 1 = ionised site */
   int8_t *site_state;    /* [n_sites] by site index (input order of the sites) */
+  int32_t *cls;          /* [n] interaction class (0..3), as cr_load takes it */
 } cr_state_view;
 
 typedef struct {
@@ -284,7 +285,9 @@ int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
 int cr_md_forces_noalloc(cr_ctx *ctx, float *force, uint64_t *id, int64_t n_slots);
 
 /* Fill the view (counts always; arrays when non-NULL) and synchronise.
- * Arrays are ordered by particle id. */
+ * Arrays are ordered by particle id (the ordering runs on the device: input
+ * ids by a prefix count, inserted ions by a radix sort), one device-to-host
+ * copy per array; pinned host arrays make those copies asynchronous DMA. */
 int cr_state(cr_ctx *ctx, cr_state_view *out);
 
 /* Replace the configuration with n particles from host arrays (xyz [3n],
@@ -297,12 +300,14 @@ int cr_state(cr_ctx *ctx, cr_state_view *out);
 int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type, const int32_t *cls,
             const int8_t *state);
 
-/* Launch shape of the colour-phase kernel: threads per domain (128, 256 or
- * 512) and halo particles held in registers per thread (1..8).  By default
- * the first unlogged sweeps time every supported shape once and keep the
- * fastest; the trial outcomes never depend on the shape (the energy sums are
- * exact fixed point).  cr_set_launch_shape(ctx, 0, 0) restarts the tuning;
- * an unsupported pair gives CR_ERR_INVALID_ARG. */
+/* Launch shape of the colour-phase kernel: threads per domain and halo
+ * particles held in registers per thread.  Supported pairs: (32|64|128|256|512,
+ * 0) halo in shared memory; (128, 4), (256, 2), (512, 1) halo in registers.
+ * By default the first unlogged sweeps time every supported shape once (with
+ * full and with compact shared-memory capacities) and keep the fastest; the
+ * trial outcomes never depend on the shape (the energy sums are exact fixed
+ * point).  cr_set_launch_shape(ctx, 0, 0) restarts the tuning; an unsupported
+ * pair gives CR_ERR_INVALID_ARG. */
 int cr_set_launch_shape(cr_ctx *ctx, int32_t threads, int32_t regs);
 int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t *regs);
 

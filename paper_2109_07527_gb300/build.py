@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcrmc.so")
-SOURCES = ["crmc_phase.cu", "crmc_md.cu", "crmc_api.cu", "crmc_noalloc.cu", "crmc_train.cu"]
+SOURCES = ["crmc_phase.cu", "crmc_md.cu", "crmc_api.cu", "crmc_noalloc.cu", "crmc_train.cu", "crmc_state.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -56,7 +56,8 @@ class cr_state_view(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_A", C.c_int64), ("n_Am", C.c_int64), ("n_B", C.c_int64),
                 ("n_Bp", C.c_int64), ("n_Xp", C.c_int64), ("n_Xm", C.c_int64), ("net_charge", C.c_int64),
                 ("alpha", C.c_double), ("xyz", C.c_void_p), ("vel", C.c_void_p), ("force", C.c_void_p),
-                ("id", C.c_void_p), ("type", C.c_void_p), ("state", C.c_void_p), ("site_state", C.c_void_p)]
+                ("id", C.c_void_p), ("type", C.c_void_p), ("state", C.c_void_p), ("site_state", C.c_void_p),
+                ("cls", C.c_void_p)]
 
 
 class cr_info(C.Structure):
@@ -368,14 +369,14 @@ class Context:
         return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
                     net_charge=v.net_charge, alpha=v.alpha)
 
-    def state_into(self, xyz=None, vel=None, id=None, type=None, state=None, site_state=None, force=None):
+    def state_into(self, xyz=None, vel=None, id=None, type=None, state=None, site_state=None, force=None, cls=None):
         """cr_state into caller-owned host arrays (numpy arrays or raw pointers,
         e.g. pinned buffers reused every step, each sized for the capacity);
         returns the counts."""
         conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
         v = cr_state_view()
         v.xyz, v.vel, v.force, v.id = conv(xyz), conv(vel), conv(force), conv(id)
-        v.type, v.state, v.site_state = conv(type), conv(state), conv(site_state)
+        v.type, v.state, v.site_state, v.cls = conv(type), conv(state), conv(site_state), conv(cls)
         _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
         return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
                     net_charge=v.net_charge, alpha=v.alpha)
@@ -386,10 +387,12 @@ class Context:
         n = int(c["n"])
         arr = dict(xyz=np.zeros((n, 3), np.float32), vel=np.zeros((n, 3), np.float32),
                    force=np.zeros((n, 3), np.float32), id=np.zeros(n, np.uint64), type=np.zeros(n, np.int32),
-                   state=np.zeros(n, np.int8), site_state=np.zeros(max(self.n_sites, 1), np.int8))
+                   state=np.zeros(n, np.int8), site_state=np.zeros(max(self.n_sites, 1), np.int8),
+                   cls=np.zeros(n, np.int32))
         v = cr_state_view()
         v.xyz, v.vel, v.force = _p(arr["xyz"]), _p(arr["vel"]), _p(arr["force"])
         v.id, v.type, v.state, v.site_state = _p(arr["id"]), _p(arr["type"]), _p(arr["state"]), _p(arr["site_state"])
+        v.cls = _p(arr["cls"])
         _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
         arr["site_state"] = arr["site_state"][: self.n_sites]
         c.update(arr)

@@ -69,19 +69,22 @@ struct cr_ctx {
   int da_T = 128, da_R = 0, da_next = 0;
   bool da_tuning = true;
   float da_ms[8] = {};
-  // cr_load inputs (capacity-sized) and cr_state dump buffers (device + pinned host)
+  // cr_load inputs (capacity-sized)
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
   int8_t *d_in_state = nullptr;
-  float4 *d_dump_pos = nullptr, *d_dump_vel = nullptr, *d_dump_frc = nullptr;
-  unsigned long long *d_dump_pid = nullptr;
-  int *d_dump_info = nullptr;
-  float4 *h_dump_pos = nullptr, *h_dump_vel = nullptr, *h_dump_frc = nullptr;
-  unsigned long long *h_dump_pid = nullptr;
-  int *h_dump_info = nullptr;
-  long long *h_small = nullptr;           // pinned: kind counts [6], dump count, error word
-  std::vector<int64_t> ord_at, ord;           // host scratch of cr_state's id ordering
-  std::vector<std::pair<unsigned long long, int64_t>> ord_kv, ord_tmp;
+  // cr_state: id ordering on the device and the output arrays in the
+  // caller's layouts (capacity-sized), one copy each to the caller
+  int *d_present = nullptr, *d_pre = nullptr;
+  unsigned long long *d_ion_key = nullptr, *d_ion_key2 = nullptr;
+  int *d_ion_val = nullptr, *d_ion_val2 = nullptr;
+  unsigned char *d_sort_tmp = nullptr;
+  size_t sort_tmp_bytes = 0;
+  float *d_out_xyz = nullptr, *d_out_vel = nullptr, *d_out_frc = nullptr;
+  unsigned long long *d_out_id = nullptr;
+  int *d_out_type = nullptr, *d_out_cls = nullptr;
+  int8_t *d_out_state = nullptr, *d_out_site = nullptr;
+  long long *h_small = nullptr;           // pinned: kind counts [6], ions found, error word
   // MD
   double fene_K = 30.0, fene_R0 = 1.5;
   uint64_t sweep = 0;
@@ -167,14 +170,14 @@ static void free_ctx(cr_ctx *c) {
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log,
                   c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
-                  c->d_dump_pos, c->d_dump_vel, c->d_dump_frc, c->d_dump_pid, c->d_dump_info,
+                  c->d_present, c->d_pre, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_sort_tmp,
+                  c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
+                  c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
                   c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
-  void *hptrs[] = {c->h_dump_pos, c->h_dump_vel, c->h_dump_frc, c->h_dump_pid, c->h_dump_info, c->h_small};
-  for (void *p : hptrs)
-    if (p) cudaFreeHost(p);
+  if (c->h_small) cudaFreeHost(c->h_small);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -558,11 +561,25 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_in_cls, (size_t)sys->capacity);
   ALLOC(c->d_in_state, (size_t)sys->capacity);
   ALLOC(c->d_site_map, (size_t)std::max(n, 1));
-  ALLOC(c->d_dump_pos, (size_t)sys->capacity);
-  ALLOC(c->d_dump_vel, (size_t)sys->capacity);
-  ALLOC(c->d_dump_frc, (size_t)sys->capacity);
-  ALLOC(c->d_dump_pid, (size_t)sys->capacity);
-  ALLOC(c->d_dump_info, (size_t)sys->capacity);
+  {
+    const size_t cp = (size_t)std::max(sys->capacity, 1);
+    ALLOC(c->d_present, (size_t)std::max(n, 1));
+    ALLOC(c->d_pre, (size_t)std::max(n, 1));
+    ALLOC(c->d_ion_key, cp);
+    ALLOC(c->d_ion_key2, cp);
+    ALLOC(c->d_ion_val, cp);
+    ALLOC(c->d_ion_val2, cp);
+    c->sort_tmp_bytes = std::max<size_t>(state_sort_temp_bytes((int)cp), 16);
+    ALLOC(c->d_sort_tmp, c->sort_tmp_bytes);
+    ALLOC(c->d_out_xyz, 3 * cp);
+    ALLOC(c->d_out_vel, 3 * cp);
+    ALLOC(c->d_out_frc, 3 * cp);
+    ALLOC(c->d_out_id, cp);
+    ALLOC(c->d_out_type, cp);
+    ALLOC(c->d_out_cls, cp);
+    ALLOC(c->d_out_state, cp);
+    ALLOC(c->d_out_site, (size_t)std::max(c->n_sites, 1));
+  }
   {
     const size_t ng = (size_t)P.nact * P.dcap_glob;
     ALLOC(c->d_gs_pos, ng);
@@ -577,13 +594,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_nparts, 1);
 #undef ALLOC
   {
-    const size_t cp = (size_t)std::max(sys->capacity, 1);
-    if (cudaHostAlloc((void **)&c->h_dump_pos, cp * sizeof(float4), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_dump_vel, cp * sizeof(float4), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_dump_frc, cp * sizeof(float4), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_dump_pid, cp * sizeof(unsigned long long), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_dump_info, cp * sizeof(int), 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_small, 16 * sizeof(long long), 0) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&c->h_small, 16 * sizeof(long long), 0) != cudaSuccess) {
       free_ctx(c);
       return CR_ERR_NOMEM;
     }
@@ -985,8 +996,37 @@ extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
 extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   if (!ctx || !out) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
-  long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] dump count, [7] error word
-  int *herr = (int *)(hs + 7);
+  long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] ions found, [7] error word
+  int *hions = (int *)(hs + 6), *herr = (int *)(hs + 7);
+  const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state ||
+                    out->cls;
+  StateBufs B{};
+  B.n_input = ctx->n_input;
+  B.cap = (int)ctx->capacity;
+  B.present = ctx->d_present;
+  B.pre = ctx->d_pre;
+  B.n_ions = ctx->d_counter;
+  B.ion_key = ctx->d_ion_key;
+  B.ion_key_alt = ctx->d_ion_key2;
+  B.ion_val = ctx->d_ion_val;
+  B.ion_val_alt = ctx->d_ion_val2;
+  B.sort_tmp = ctx->d_sort_tmp;
+  B.sort_tmp_bytes = ctx->sort_tmp_bytes;
+  B.vel_src = ctx->d_vel;
+  B.frc_src = ctx->fcons_valid ? ctx->d_fcons : nullptr;
+  B.xyz = out->xyz ? ctx->d_out_xyz : nullptr;
+  B.vel = out->vel ? ctx->d_out_vel : nullptr;
+  B.frc = out->force ? ctx->d_out_frc : nullptr;
+  B.id = out->id ? ctx->d_out_id : nullptr;
+  B.type = out->type ? ctx->d_out_type : nullptr;
+  B.cls = out->cls ? ctx->d_out_cls : nullptr;
+  B.state = out->state ? ctx->d_out_state : nullptr;
+  B.site = out->site_state ? ctx->d_out_site : nullptr;
+  if (want) {
+    CR_CUDA(launch_state_mark(ctx->P, B, s));
+    ctx->launches_total++;
+    CR_CUDA(cudaMemcpyAsync(hions, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+  }
   CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaMemcpyAsync(herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaStreamSynchronize(s));
@@ -1000,71 +1040,30 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
   out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
   const int err0 = err_bits_to_code(*herr);
-  const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state;
   if (!want || err0 != CR_OK) return err0;
   const int64_t n = out->n;
   if (n > ctx->capacity) return CR_ERR_CAPACITY;
-  DumpBufs D{ctx->d_counter, (int)n, ctx->d_dump_pos, ctx->d_dump_vel, ctx->d_dump_frc, ctx->d_dump_pid,
-             ctx->d_dump_info, ctx->d_vel, ctx->fcons_valid ? ctx->d_fcons : nullptr};
-  float4 *hpos = ctx->h_dump_pos, *hvel = ctx->h_dump_vel, *hfrc = ctx->h_dump_frc;
-  unsigned long long *hpid = ctx->h_dump_pid;
-  int *hinfo = ctx->h_dump_info;
-  int *hgot = (int *)(hs + 6);
-  CR_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
-  CR_CUDA(launch_dump(ctx->P, D, s));
-  ctx->launches_total++;
-  CR_CUDA(cudaMemcpyAsync(hgot, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
-  if (out->xyz) CR_CUDA(cudaMemcpyAsync(hpos, ctx->d_dump_pos, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
-  if (out->vel) CR_CUDA(cudaMemcpyAsync(hvel, ctx->d_dump_vel, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
-  if (out->force && ctx->fcons_valid)
-    CR_CUDA(cudaMemcpyAsync(hfrc, ctx->d_dump_frc, sizeof(float4) * n, cudaMemcpyDeviceToHost, s));
-  CR_CUDA(cudaMemcpyAsync(hpid, ctx->d_dump_pid, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s));
-  CR_CUDA(cudaMemcpyAsync(hinfo, ctx->d_dump_info, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  const int n_ions = *hions;
+  const int64_t n_present = n - n_ions;
+  if (n_ions < 0 || n_ions > ctx->capacity || n_present < 0 || n_present > ctx->n_input) return CR_ERR_CUDA;
+  // inserted ids are (phase + 1) << 32 | index with phase < sweeps * colours:
+  // the radix sort covers the bits that can be set
+  int end_bit = 33;
+  while (end_bit < 64 && (ctx->sweep * (uint64_t)ctx->P.ncol + 1) >> (end_bit - 32)) ++end_bit;
+  int nl = 0;
+  CR_CUDA(launch_state_emit(ctx->P, B, (int)n_present, n_ions, end_bit, s, &nl));
+  ctx->launches_total += nl;
+  const size_t nn = (size_t)n;
+  if (out->xyz) CR_CUDA(cudaMemcpyAsync(out->xyz, B.xyz, sizeof(float) * 3 * nn, cudaMemcpyDeviceToHost, s));
+  if (out->vel) CR_CUDA(cudaMemcpyAsync(out->vel, B.vel, sizeof(float) * 3 * nn, cudaMemcpyDeviceToHost, s));
+  if (out->force) CR_CUDA(cudaMemcpyAsync(out->force, B.frc, sizeof(float) * 3 * nn, cudaMemcpyDeviceToHost, s));
+  if (out->id) CR_CUDA(cudaMemcpyAsync(out->id, B.id, sizeof(uint64_t) * nn, cudaMemcpyDeviceToHost, s));
+  if (out->type) CR_CUDA(cudaMemcpyAsync(out->type, B.type, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, s));
+  if (out->cls) CR_CUDA(cudaMemcpyAsync(out->cls, B.cls, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, s));
+  if (out->state) CR_CUDA(cudaMemcpyAsync(out->state, B.state, nn, cudaMemcpyDeviceToHost, s));
+  if (out->site_state && ctx->n_sites > 0)
+    CR_CUDA(cudaMemcpyAsync(out->site_state, B.site, (size_t)ctx->n_sites, cudaMemcpyDeviceToHost, s));
   CR_CUDA(cudaStreamSynchronize(s));
-  if (*hgot != n) return CR_ERR_CUDA;
-  // order by id: input ids are dense (bucket them), inserted ions are sorted
-  // by an LSD radix sort on their 64-bit ids (bytes that do not vary skipped)
-  std::vector<int64_t> &at = ctx->ord_at, &ord = ctx->ord;
-  auto &kv = ctx->ord_kv, &tmp = ctx->ord_tmp;
-  at.assign((size_t)ctx->n_input, -1);
-  ord.clear();
-  kv.clear();
-  for (int64_t i = 0; i < n; ++i) {
-    if (hpid[i] < (unsigned long long)ctx->n_input) at[hpid[i]] = i;
-    else kv.emplace_back(hpid[i], i);
-  }
-  for (int64_t v : at)
-    if (v >= 0) ord.push_back(v);
-  for (int shift = 0; shift < 64 && kv.size() > 1; shift += 8) {
-    size_t cnt[257] = {0};
-    for (const auto &p : kv) cnt[((p.first >> shift) & 255u) + 1]++;
-    bool one = false;
-    for (int d = 0; d < 256 && !one; ++d) one = cnt[d + 1] == kv.size();
-    if (one) continue;
-    for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
-    tmp.resize(kv.size());
-    for (const auto &p : kv) tmp[cnt[(p.first >> shift) & 255u]++] = p;
-    kv.swap(tmp);
-  }
-  for (const auto &p : kv) ord.push_back(p.second);
-  const bool frc_ok = ctx->fcons_valid;
-  for (int64_t o = 0; o < n; ++o) {
-    const int64_t i = ord[o];
-    if (out->xyz) { out->xyz[3 * o] = hpos[i].x; out->xyz[3 * o + 1] = hpos[i].y; out->xyz[3 * o + 2] = hpos[i].z; }
-    if (out->vel) { out->vel[3 * o] = hvel[i].x; out->vel[3 * o + 1] = hvel[i].y; out->vel[3 * o + 2] = hvel[i].z; }
-    if (out->force) {
-      out->force[3 * o] = frc_ok ? hfrc[i].x : 0.0f;
-      out->force[3 * o + 1] = frc_ok ? hfrc[i].y : 0.0f;
-      out->force[3 * o + 2] = frc_ok ? hfrc[i].z : 0.0f;
-    }
-    if (out->id) out->id[o] = hpid[i];
-    const int info = hinfo[i];
-    const int t = info & INFO_TYPE_MASK;
-    const int ion = (info & INFO_ION_BIT) ? 1 : 0;
-    if (out->type) out->type[o] = t;
-    if (out->state) out->state[o] = (int8_t)ion;
-    if (out->site_state && (t == CR_ACID || t == CR_BASE)) out->site_state[info >> INFO_SITE_SHIFT] = (int8_t)ion;
-  }
   return CR_OK;
 }
 

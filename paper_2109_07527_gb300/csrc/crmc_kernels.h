@@ -29,13 +29,23 @@ struct RebuildBufs {
   float4 *vel_src, *frc_src;  // primary velocity / force arrays
 };
 
-struct DumpBufs {
-  int *counter;
-  int cap;
-  float4 *pos, *vel, *frc;
-  unsigned long long *pid;
-  int *info;
-  const float4 *vel_src, *frc_src;
+// the configuration read back in id order (crmc_state.cu); output arrays
+// that are null are not written
+struct StateBufs {
+  int n_input, cap;               // input ids are 0..n_input-1; ion list capacity
+  int *present;                   // [n_input] slot + 1 of each input id, 0 absent
+  int *pre;                       // [n_input] output position of each input id present
+  int *n_ions;                    // number of inserted ions found
+  unsigned long long *ion_key, *ion_key_alt;  // [cap] ion ids (sort double buffer)
+  int *ion_val, *ion_val_alt;                 // [cap] their slots
+  void *sort_tmp;
+  size_t sort_tmp_bytes;
+  const float4 *vel_src, *frc_src;  // velocities; forces (null: zeros)
+  float *xyz, *vel, *frc;           // [3n]
+  unsigned long long *id;           // [n]
+  int *type, *cls;                  // [n]
+  int8_t *state;                    // [n]
+  int8_t *site;                     // [n_sites] by site index
 };
 
 struct LoadBufs {
@@ -67,7 +77,13 @@ cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_s
 cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
                         cudaStream_t s);
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
-cudaError_t launch_dump(const SysParams &P, const DumpBufs &D, cudaStream_t s);
+// state read-back: mark the slots (ion count into *B.n_ions), then, with the
+// counts known, place the input ids, sort the ions (bits [0, end_bit) of the
+// ids) and write the arrays (adds the kernels it launched to *launches)
+cudaError_t launch_state_mark(const SysParams &P, const StateBufs &B, cudaStream_t s);
+cudaError_t launch_state_emit(const SysParams &P, const StateBufs &B, int n_present, int n_ions, int end_bit,
+                              cudaStream_t s, int *launches);
+size_t state_sort_temp_bytes(int cap);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                           uint4 *out, cudaStream_t s);
 

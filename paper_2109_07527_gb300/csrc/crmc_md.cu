@@ -1,6 +1,6 @@
 // crmc_md.cu -- MD kernels (DSF + WCA + FENE forces, Langevin velocity Verlet),
-// the cell rebuild after particles move, configuration upload, state dump and
-// a Philox check kernel (sm_103a).
+// the cell rebuild after particles move, configuration upload and a Philox
+// check kernel (sm_103a).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -339,27 +339,6 @@ __global__ void k_perm_slots(SysParams P, int *perm_slot, int n_perm) {
   if (id < (unsigned long long)n_perm) perm_slot[id] = g;
 }
 
-// dump every particle (unordered) for the state view
-__global__ void k_dump(SysParams P, DumpBufs D) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
-  const int c = g / P.cap;
-  const bool have = g < P.ncell * P.cap && g - c * P.cap < P.cnt[c];
-  const unsigned m = __ballot_sync(0xffffffffu, have);  // one atomic per warp
-  if (m == 0u) return;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(D.counter, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (!have) return;
-  const int o = base + __popc(m & ((1u << lane) - 1u));
-  if (o >= D.cap) return;
-  D.pos[o] = P.pos[g];
-  D.pid[o] = P.pid[g];
-  D.info[o] = P.info[g];
-  if (D.vel_src) D.vel[o] = D.vel_src[g];
-  if (D.frc_src) D.frc[o] = D.frc_src[g];
-}
-
 // load: place input particles (index = id) into cells, unordered
 __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -444,12 +423,6 @@ cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s) {
   const int n = P.ncell * P.cap;
   k_perm_slots<<<(n + 255) / 256, 256, 0, s>>>(P, perm_slot, n_perm);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dump(const SysParams &P, const DumpBufs &D, cudaStream_t s) {
-  const int n = P.ncell * P.cap;
-  k_dump<<<(n + 255) / 256, 256, 0, s>>>(P, D);
   return cudaGetLastError();
 }
 

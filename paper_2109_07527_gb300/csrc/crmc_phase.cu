@@ -202,9 +202,11 @@ __device__ void warp_remove(DomList L, int n, int p) {
 }
 
 // pair change between the two changed particles: u_new - u_old, Coulomb in
-// FP32 and WCA in FP64, into fixed point
-__device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
-                                       unsigned long long &sacc, int &ov) {
+// FP32 and WCA in FP64, into fixed point (without a WCA term the FP64 sum
+// reduces to the FP32 change, taken directly)
+template <bool WITH_S>
+__device__ __forceinline__ void cc_change(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
+                                          unsigned long long &sacc, int &ov) {
   const Desc &A = t.c[0], &B = t.c[1];
   const float dx = wrap_diff(B.x, A.x, K.Lf, K.halfL);
   const float dy = wrap_diff(B.y, A.y, K.Lf, K.halfL);
@@ -214,6 +216,7 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
   float uc[2] = {0.0f, 0.0f};
   double uw[2] = {0.0, 0.0};
   double gs = 0.0;
+  bool hit = false;
   for (int s = 0; s < 2; ++s) {
     const bool pres = s ? (t.pa_n && t.pb_n) : (t.pa_o && t.pb_o);
     if (!pres) continue;
@@ -223,7 +226,7 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
       const float r = r2 * rinv;
       const float e = erfcf(K.alpha * r) * rinv;
       uc[s] = K.lBf * qa * qb * (e - K.c1 + K.c2 * (r - K.rcf));
-      gs += (double)(fabsf(K.lBf * qa * qb) * (e + K.c1 + K.c2 * fabsf(r - K.rcf)));
+      if (WITH_S) gs += (double)(fabsf(K.lBf * qa * qb) * (e + K.c1 + K.c2 * fabsf(r - K.rcf)));
     }
     if (w.on && r2 < 1.0001f * w.wcut2) {
       const double ddx = wrap_diff_d(B.x, A.x, K.Ld, K.halfLd), ddy = wrap_diff_d(B.y, A.y, K.Ld, K.halfLd),
@@ -239,19 +242,31 @@ __device__ __noinline__ void cc_change(const PairK &K, const WcaEntry *wca, cons
           const double t2 = tt * tt;
           const double t6 = t2 * t2 * t2;
           uw[s] = 4.0 * w.eps_d * (t6 * t6 - t6) + w.eps_d;
-          gs += w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
+          if (WITH_S) gs += w.eps_d * (4.0 * t6 * t6 + 4.0 * t6 + 1.0);
+          hit = true;
         }
       }
     }
   }
   const float dc = uc[1] - uc[0];
+  if (!hit) {  // dw = 0: |dc| < 2^20 decides, fix32(dc) is the sum
+    if (dc != 0.0f) {
+      if (!(fabsf(dc) < BIG_TERM)) {
+        ov = 1;
+      } else {
+        acc += fix32(dc);
+        if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin(gs, (double)BIG_TERM) * (double)FIX_SCALE);
+      }
+    }
+    return;
+  }
   const double dw = uw[1] - uw[0];
   if (dc != 0.0f || dw != 0.0) {
     if (!(fabs((double)dc + dw) < (double)BIG_TERM)) {
       ov = 1;
     } else {
       acc += fix32(dc) + __double2ll_rn(dw * (double)FIX_SCALE);
-      sacc += (unsigned long long)__double2ll_rn(fmin(gs, (double)BIG_TERM) * (double)FIX_SCALE);
+      if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin(gs, (double)BIG_TERM) * (double)FIX_SCALE);
     }
   }
 }
@@ -396,6 +411,39 @@ __device__ __noinline__ void near_pair(const PairK &K, const WcaEntry &w, const 
   }
 }
 
+// every full 32 queued Coulomb pairs of the warp are evaluated with all lanes
+// busy; the rest (fewer than 32) stays queued
+template <bool WITH_S>
+__device__ __forceinline__ void queue_flush(const PairK &K, float *qr2, float *qqp, int &qn, long long &acc,
+                                            unsigned long long &sacc, int &ov) {
+  const int lane = threadIdx.x & 31;
+  while (qn >= 32) {
+    __syncwarp();
+    coul_eval<WITH_S>(K, qr2[lane], qqp[lane], acc, sacc, ov);
+    const int rest = qn - 32;
+    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
+    if (lane < rest) {
+      a0 = qr2[32 + lane];
+      b0 = qqp[32 + lane];
+    }
+    if (lane + 32 < rest) {
+      a1 = qr2[64 + lane];
+      b1 = qqp[64 + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      qr2[lane] = a0;
+      qqp[lane] = b0;
+    }
+    if (lane + 32 < rest) {
+      qr2[32 + lane] = a1;
+      qqp[32 + lane] = b1;
+    }
+    __syncwarp();
+    qn = rest;
+  }
+}
+
 // Both changed particles A and B against one candidate j (lane-parallel):
 // the two distance tests are independent, pairs near an inserted / deleted
 // particle are evaluated at once, the in-range Coulomb pairs of A and B join
@@ -432,32 +480,9 @@ __device__ __forceinline__ void offer2(const PairK &K, const WcaEntry *wca, cons
     qqp[p] = B.dqlB * qj;
   }
   qn += nA + __popc(mB);
-  while (qn >= 32) {
-    __syncwarp();
-    coul_eval<WITH_S>(K, qr2[lane], qqp[lane], acc, sacc, ov);
-    const int rest = qn - 32;
-    float a0 = 0.f, b0 = 0.f, a1 = 0.f, b1 = 0.f;
-    if (lane < rest) {
-      a0 = qr2[32 + lane];
-      b0 = qqp[32 + lane];
-    }
-    if (lane + 32 < rest) {
-      a1 = qr2[64 + lane];
-      b1 = qqp[64 + lane];
-    }
-    __syncwarp();
-    if (lane < rest) {
-      qr2[lane] = a0;
-      qqp[lane] = b0;
-    }
-    if (lane + 32 < rest) {
-      qr2[32 + lane] = a1;
-      qqp[32 + lane] = b1;
-    }
-    __syncwarp();
-    qn = rest;
-  }
+  queue_flush<WITH_S>(K, qr2, qqp, qn, acc, sacc, ov);
 }
+
 
 template <int T>
 __device__ __forceinline__ void cta_sync() {
@@ -470,6 +495,368 @@ __device__ __forceinline__ long long warp_allsum(long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
+}
+
+// Random numbers of a chunk of trials (Philox purposes 0-3; thread i0 of a
+// group of `stride` threads takes every stride-th trial): the move and its
+// choices, both insertion points with their in-domain cell ranks, the
+// Metropolis uniform and, for delayed acceptance, the stage-2 uniform.
+template <bool LOG, bool DA>
+__device__ __forceinline__ void draw_chunk(TrialPre *tp, int k0, int nchunk, int i0, int stride, int d, uint32_t phi,
+                                           const int *org, const int *off, const int *dd, int k, int nc, float af,
+                                           float Lf, float scf, uint32_t key0, uint32_t key1) {
+  for (int t = i0; t < nchunk; t += stride) {
+    const uint32_t kk = (uint32_t)(k0 + t);
+    const uint4 a = philox10(kk, (uint32_t)d, phi, 0u, key0, key1);
+    const uint4 b = philox10(kk, (uint32_t)d, phi, 1u, key0, key1);
+    const uint4 c = philox10(kk, (uint32_t)d, phi, 2u, key0, key1);
+    TrialPre q;
+    q.w0 = a.x; q.w1 = a.y; q.w2 = a.z; q.w3 = a.w;
+    q.ax = insert_coord(org[0], b.x, k, nc, af, Lf);
+    q.ay = insert_coord(org[1], b.y, k, nc, af, Lf);
+    q.az = insert_coord(org[2], b.z, k, nc, af, Lf);
+    q.bx = insert_coord(org[0], b.w, k, nc, af, Lf);
+    q.by = insert_coord(org[1], c.x, k, nc, af, Lf);
+    q.bz = insert_coord(org[2], c.y, k, nc, af, Lf);
+    const float xs[2][3] = {{q.ax, q.ay, q.az}, {q.bx, q.by, q.bz}};
+    int rk[2];
+    for (int s = 0; s < 2; ++s) {
+      int l[3];
+      bool in = true;
+      for (int i = 0; i < 3; ++i) {
+        const int cc = cell_of(xs[s][i], scf, nc);
+        const int sh = ((cc - off[i]) % nc + nc) % nc;
+        in = in && (sh / k == dd[i]);
+        l[i] = sh % k;
+      }
+      rk[s] = in ? l[0] + k * (l[1] + k * l[2]) : -1;
+    }
+    q.rankA = rk[0];
+    q.rankB = rk[1];
+    q.uhi = c.z;
+    q.ulo = c.w;
+    q.lnu_f = logf((float)(c.z >> 5) * 7.450580596923828e-09f + ((float)(c.w >> 6) + 0.5f) * 1.1102230246251565e-16f);
+    q.pad = 0;
+    q.lnu = LOG ? log(unif53(c.z, c.w)) : 0.0;
+    q.u2hi = q.u2lo = 0u;
+    q.lnu2_f = 0.0f;
+    q.pad2 = 0;
+    q.lnu2 = 0.0;
+    if (DA) {
+      const uint4 e = philox10(kk, (uint32_t)d, phi, 3u, key0, key1);
+      q.u2hi = e.x;
+      q.u2lo = e.y;
+      q.lnu2_f = logf((float)(e.x >> 5) * 7.450580596923828e-09f + ((float)(e.y >> 6) + 0.5f) * 1.1102230246251565e-16f);
+      q.lnu2 = LOG ? log(unif53(e.x, e.y)) : 0.0;
+    }
+    tp[t] = q;
+  }
+}
+
+// Proposal of trial kk on the current list (Sec. II.C applied to the domain):
+// the move, its participants, the log of the acceptance ratio without the
+// energy, the self-energy change and the two changed particles.  Every lane
+// of the calling warp computes the same values (the list scans are ballots).
+template <bool DA>
+__device__ __forceinline__ void select_trial(const SysParams &P, const DomList &L, const int *misc,
+                                             const long long *lnt, const TrialPre &q, int d, int m, int kk,
+                                             uint32_t phi, TrialCtl &C) {
+  const int lane = threadIdx.x & 31;
+  const int n = misc[0];
+  const int mv = pick32(q.w0, 2 * P.n_react);
+  const int r = P.react[mv >> 1];
+  const bool fwd = (mv & 1) == 0;
+  int flags = 0, site = -1, ionA = -1, ionB = -1, nch = 0;
+  bool bad = false;
+  long long ln_ratio = 0;
+  const unsigned long long newid = ((unsigned long long)(phi + 1u) << 32) |
+                                   (unsigned long long)(2u * ((uint32_t)d * (uint32_t)m + (uint32_t)kk));
+  unsigned long long id_a = ~0ull, id_b = ~0ull;
+  Desc c0 = {}, c1 = {};
+  float qa_o = 0.f, qa_n = 0.f, qb_o = 0.f, qb_n = 0.f;
+  int pa_o = 0, pa_n = 0, pb_o = 0, pb_n = 0;
+  if (r == R_ACID || r == R_BASE) {
+    const int kn = r == R_ACID ? K_A0 : K_B0, ki = r == R_ACID ? K_A1 : K_B1;
+    const int kx = r == R_ACID ? K_XP : K_XM;
+    const float qs = r == R_ACID ? -1.0f : 1.0f;
+    const int n0 = misc[1 + kn], n1 = misc[1 + ki], nx = misc[1 + kx];
+    if (fwd) {
+      if (n0 == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+      else {
+        site = warp_kth(L.info, n, kn, pick32(q.w1, n0));
+        if (q.rankA < 0) flags |= CR_TRIAL_EDGE;
+        if (site < 0) { site = 0; bad = true; }
+        id_a = L.id[site];
+        id_b = newid;
+        const float4 sp4 = L.pos[site];
+        const int sinfo = L.info[site];
+        c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * qs, 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
+        c1 = Desc{q.ax, q.ay, q.az, P.lBf * (-qs * P.ion_q), 1, P.ion_cls, -1};
+        qa_o = 0.f; qa_n = qs; qb_o = 0.f; qb_n = -qs * P.ion_q;
+        pa_o = pa_n = 1; pb_o = 0; pb_n = 1;
+        nch = 2;
+        ln_ratio = lnt[n0] + P.lnz1_fx - lnt[n1 + 1];
+        ln_ratio -= lnt[nx + 1];
+        ln_ratio += L.lnk[site];
+      }
+    } else {
+      if (n1 == 0 || nx == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+      else {
+        site = warp_kth(L.info, n, ki, pick32(q.w1, n1));
+        ionA = warp_kth(L.info, n, kx, pick32(q.w2, nx));
+        if (site < 0 || ionA < 0) { site = max(site, 0); ionA = max(ionA, 0); bad = true; }
+        id_a = L.id[site];
+        id_b = L.id[ionA];
+        const float4 sp4 = L.pos[site], ip4 = L.pos[ionA];
+        const int sinfo = L.info[site], iinfo = L.info[ionA];
+        c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * (-qs), 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
+        c1 = Desc{ip4.x, ip4.y, ip4.z, P.lBf * (-ip4.w), -1, (iinfo >> INFO_CLS_SHIFT) & 3, ionA};
+        qa_o = qs; qa_n = 0.f; qb_o = ip4.w; qb_n = 0.f;
+        pa_o = pa_n = 1; pb_o = 1; pb_n = 0;
+        nch = 2;
+        ln_ratio = lnt[n1] - lnt[n0 + 1] - P.lnz1_fx;
+        ln_ratio += lnt[nx];
+        ln_ratio -= L.lnk[site];
+      }
+    }
+  } else {
+    const int nxp = misc[1 + K_XP], nxm = misc[1 + K_XM];
+    if (fwd) {
+      if (q.rankA < 0 || q.rankB < 0) flags |= CR_TRIAL_EDGE;
+      id_a = newid;
+      id_b = newid + 1u;
+      c0 = Desc{q.ax, q.ay, q.az, P.lBf * P.ion_q, 1, P.ion_cls, -1};
+      c1 = Desc{q.bx, q.by, q.bz, P.lBf * (-P.ion_q), 1, P.ion_cls, -1};
+      qa_o = 0.f; qa_n = P.ion_q; qb_o = 0.f; qb_n = -P.ion_q;
+      pa_o = 0; pa_n = 1; pb_o = 0; pb_n = 1;
+      nch = 2;
+      ln_ratio = 2 * P.lnz1_fx + P.lnsalt_fx;
+      ln_ratio -= lnt[nxp + 1] + lnt[nxm + 1];
+    } else {
+      if (nxp == 0 || nxm == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
+      else {
+        ionA = warp_kth(L.info, n, K_XP, pick32(q.w2, nxp));
+        ionB = warp_kth(L.info, n, K_XM, pick32(q.w3, nxm));
+        if (ionA < 0 || ionB < 0) { ionA = max(ionA, 0); ionB = max(ionB, 0); bad = true; }
+        id_a = L.id[ionA];
+        id_b = L.id[ionB];
+        const float4 a4 = L.pos[ionA], b4 = L.pos[ionB];
+        c0 = Desc{a4.x, a4.y, a4.z, P.lBf * (-a4.w), -1, (L.info[ionA] >> INFO_CLS_SHIFT) & 3, ionA};
+        c1 = Desc{b4.x, b4.y, b4.z, P.lBf * (-b4.w), -1, (L.info[ionB] >> INFO_CLS_SHIFT) & 3, ionB};
+        qa_o = a4.w; qa_n = 0.f; qb_o = b4.w; qb_n = 0.f;
+        pa_o = 1; pa_n = 0; pb_o = 1; pb_n = 0;
+        nch = 2;
+        ln_ratio = -2 * P.lnz1_fx - P.lnsalt_fx;
+        ln_ratio += lnt[nxp] + lnt[nxm];
+      }
+    }
+  }
+  // a failed selection would mean the kind counts and the list disagree:
+  // record it and reject instead of touching memory outside the list
+  if (bad) {
+    flags |= CR_TRIAL_NO_ELIGIBLE;
+    if (lane == 0) atomicOr(P.err, ERRB_ARG);
+  }
+  nch = (flags & (CR_TRIAL_NO_ELIGIBLE | CR_TRIAL_EDGE)) ? 0 : nch;
+  // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
+  const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
+                 (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
+  C.c[0] = c0;
+  C.c[1] = c1;
+  C.nch = nch;
+  C.move = 2 * r + (fwd ? 0 : 1);
+  C.flags = flags;
+  C.site = site;
+  C.ionA = ionA;
+  C.ionB = ionB;
+  C.ln_ratio_fx = ln_ratio;
+  C.dself_fx = P.lBself_fx * (long long)sq;
+  C.id_a = id_a;
+  C.id_b = id_b;
+  C.newid = newid;
+  C.sur = 0.0f;
+  C.sur_fx = 0;
+  C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
+  C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
+  C.rka = C.rkb = C.dqa = C.dqb = C.eta_a = C.eta_b = C.cat_a = 0;
+  C.go = 1;
+  if (DA && nch) {
+    if (r == R_SALT) {
+      C.rka = fwd ? q.rankA : L.rank[ionA];
+      C.rkb = fwd ? q.rankB : L.rank[ionB];
+    } else {
+      C.rka = L.rank[site];
+      C.rkb = fwd ? q.rankA : L.rank[ionA];
+    }
+  }
+  if (DA) {
+    C.dqa = (pa_n ? __float2int_rn(qa_n) : 0) - (pa_o ? __float2int_rn(qa_o) : 0);
+    C.dqb = (pb_n ? __float2int_rn(qb_n) : 0) - (pb_o ? __float2int_rn(qb_o) : 0);
+    C.eta_a = pa_n - pa_o;
+    C.eta_b = pb_n - pb_o;
+    C.cat_a = r == R_SALT ? 0 : 8;
+  }
+}
+
+// The pair changes of the two changed particles A and B against the halo and
+// the domain list, summed by a group of threads (thread i0 of `stride`; each
+// thread keeps its part in acc / sacc / ov; the warp's queued Coulomb pairs
+// are evaluated at the end).  The pair between A and B is not included.
+template <bool LOG, int R, int RR>
+__device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca, const SysParams &P, const DomList &L,
+                                            const Desc &A, const Desc &B, const float4 (&hreg)[RR], int nmine,
+                                            const float4 *hpos, int NH, int hcap, const int *hpre, const int *hcell,
+                                            int NR, int n, int i0, int stride, float *qr2, float *qqp, long long &acc,
+                                            unsigned long long &sacc, int &ov) {
+  const int lane = threadIdx.x & 31;
+  const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
+  int qn = 0;
+  if (R > 0) {
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+      const float4 p = hreg[r];
+      const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+      const float q = p.w - 8.0f * (float)cls;
+      const bool v = r < nmine;
+      offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+    }
+  } else {
+    const int lim = min(NH, hcap);
+    for (int base = 0; base < lim; base += stride) {
+      const int j = base + i0;
+      const bool v = j < lim;
+      const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+      const float q = p.w - 8.0f * (float)cls;
+      offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+    }
+  }
+  // halo beyond what is held on chip (dense regions): straight from global memory
+  for (int base = hcap; base < NH; base += stride) {
+    const int j = base + i0;
+    const bool v = j < NH;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cls = 0;
+    if (v) {
+      const int i = upper_idx(hpre, NR, j);
+      const int g = hcell[i] * P.cap + (j - hpre[i]);
+      p = P.pos[g];
+      cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
+    }
+    offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+  }
+  for (int base = 0; base < n; base += stride) {
+    const int j = base + i0;
+    const bool v = j < n && j != A.skip && j != B.skip;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cls = 0;
+    if (j < n) {
+      p = L.pos[j];
+      cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
+    }
+    offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
+  }
+  __syncwarp();
+  if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
+}
+
+// room for the ions an accepted insertion adds: their cells below the cell
+// capacity and the list below its capacity (belowA / sameA: entries of the
+// list before and in the first ion's cell, where it goes)
+__device__ __forceinline__ bool insert_room(const SysParams &P, const DomList &L, int n, int list_cap, int r,
+                                            const TrialPre &q, int &belowA, int &sameA) {
+  warp_rank_count(L.rank, n, q.rankA, belowA, sameA);
+  bool full = sameA + 1 > P.cap;
+  if (r == R_SALT) {
+    int below2, same2;
+    warp_rank_count(L.rank, n, q.rankB, below2, same2);
+    full = full || same2 + 1 + (q.rankB == q.rankA ? 1 : 0) > P.cap;
+  }
+  return !(full || n + 2 > list_cap);
+}
+
+// Commit of an accepted trial by one warp: the site's charge state, the ion
+// inserted (after every entry of its cell, as new ids are the largest) or
+// deleted in the list, the kind counts.  Returns the new list size.
+__device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L, int *misc, const TrialCtl &C,
+                                            const TrialPre &q, int n, int belowA, int sameA, int kk, int d,
+                                            uint32_t phi, uint32_t key0, uint32_t key1) {
+  const int lane = threadIdx.x & 31;
+  const int r = C.move >> 1;
+  const bool fwd = (C.move & 1) == 0;
+  if (r == R_ACID || r == R_BASE) {
+    const float qs = r == R_ACID ? -1.0f : 1.0f;
+    const int s_site = C.site;
+    if (lane == 0) {
+      L.info[s_site] ^= INFO_ION_BIT;
+      L.pos[s_site].w = fwd ? qs : 0.0f;
+    }
+    __syncwarp();
+    if (fwd) {
+      const int p = belowA + sameA;  // after every entry of its cell rank
+      warp_insert_gap(L, n, p);
+      if (lane == 0) {
+        L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
+        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
+        L.id[p] = C.newid;
+        L.lnk[p] = 0;
+        L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
+        L.rank[p] = q.rankA;
+      }
+      n += 1;
+    } else {
+      warp_remove(L, n, C.ionA);
+      n -= 1;
+    }
+    if (lane == 0) {
+      const int kn = r == R_ACID ? K_A0 : K_B0, ki = kn + 1, kx = r == R_ACID ? K_XP : K_XM;
+      const int dlt = fwd ? 1 : -1;
+      misc[1 + kn] -= dlt;
+      misc[1 + ki] += dlt;
+      misc[1 + kx] += dlt;
+    }
+  } else {
+    if (fwd) {
+      int p = belowA + sameA;
+      warp_insert_gap(L, n, p);
+      if (lane == 0) {
+        L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
+        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
+        L.id[p] = C.newid;
+        L.lnk[p] = 0;
+        L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
+        L.rank[p] = q.rankA;
+      }
+      __syncwarp();
+      n += 1;
+      int below, same;
+      warp_rank_count(L.rank, n, q.rankB, below, same);
+      p = below + same;
+      warp_insert_gap(L, n, p);
+      if (lane == 0) {
+        L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
+        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 7u, key0, key1);
+        L.id[p] = C.newid + 1u;
+        L.lnk[p] = 0;
+        L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
+        L.rank[p] = q.rankB;
+      }
+      n += 1;
+    } else {
+      const int hi = max(C.ionA, C.ionB), lo = min(C.ionA, C.ionB);
+      warp_remove(L, n, hi);
+      n -= 1;
+      warp_remove(L, n, lo);
+      n -= 1;
+    }
+    if (lane == 0) {
+      const int dlt = fwd ? 1 : -1;
+      misc[1 + K_XP] += dlt;
+      misc[1 + K_XM] += dlt;
+    }
+  }
+  __syncwarp();
+  return n;
 }
 
 }  // namespace
@@ -685,199 +1072,17 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   for (int k0 = 0; k0 < m; k0 += TRIAL_CHUNK) {
     const int nchunk = min(TRIAL_CHUNK, m - k0);
     // ---- random numbers of the chunk
-    for (int t = tid; t < nchunk; t += T) {
-      const uint32_t kk = (uint32_t)(k0 + t);
-      const uint4 a = philox10(kk, (uint32_t)d, phi, 0u, key0, key1);
-      const uint4 b = philox10(kk, (uint32_t)d, phi, 1u, key0, key1);
-      const uint4 c = philox10(kk, (uint32_t)d, phi, 2u, key0, key1);
-      TrialPre q;
-      q.w0 = a.x; q.w1 = a.y; q.w2 = a.z; q.w3 = a.w;
-      q.ax = insert_coord(org[0], b.x, k, nc, P.af, P.Lf);
-      q.ay = insert_coord(org[1], b.y, k, nc, P.af, P.Lf);
-      q.az = insert_coord(org[2], b.z, k, nc, P.af, P.Lf);
-      q.bx = insert_coord(org[0], b.w, k, nc, P.af, P.Lf);
-      q.by = insert_coord(org[1], c.x, k, nc, P.af, P.Lf);
-      q.bz = insert_coord(org[2], c.y, k, nc, P.af, P.Lf);
-      const float xs[2][3] = {{q.ax, q.ay, q.az}, {q.bx, q.by, q.bz}};
-      int rk[2];
-      for (int s = 0; s < 2; ++s) {
-        int l[3];
-        bool in = true;
-        for (int i = 0; i < 3; ++i) {
-          const int cc = cell_of(xs[s][i], P.scf, nc);
-          const int sh = ((cc - off[i]) % nc + nc) % nc;
-          in = in && (sh / k == dd[i]);
-          l[i] = sh % k;
-        }
-        rk[s] = in ? l[0] + k * (l[1] + k * l[2]) : -1;
-      }
-      q.rankA = rk[0];
-      q.rankB = rk[1];
-      q.uhi = c.z;
-      q.ulo = c.w;
-      q.lnu_f = logf((float)(c.z >> 5) * 7.450580596923828e-09f + ((float)(c.w >> 6) + 0.5f) * 1.1102230246251565e-16f);
-      q.pad = 0;
-      q.lnu = LOG ? log(unif53(c.z, c.w)) : 0.0;
-      q.u2hi = q.u2lo = 0u;
-      q.lnu2_f = 0.0f;
-      q.pad2 = 0;
-      q.lnu2 = 0.0;
-      if (DA) {
-        const uint4 e = philox10(kk, (uint32_t)d, phi, 3u, key0, key1);
-        q.u2hi = e.x;
-        q.u2lo = e.y;
-        q.lnu2_f = logf((float)(e.x >> 5) * 7.450580596923828e-09f + ((float)(e.y >> 6) + 0.5f) * 1.1102230246251565e-16f);
-        q.lnu2 = LOG ? log(unif53(e.x, e.y)) : 0.0;
-      }
-      tp[t] = q;
-    }
+    draw_chunk<LOG, DA>(tp, k0, nchunk, tid, T, d, phi, org, off, dd, k, nc, P.af, P.Lf, P.scf, key0, key1);
     __syncthreads();
 
     for (int t = 0; t < nchunk; ++t) {
       const int kk = k0 + t;
-      // ---- warp 0: proposal and participants (kept in warp 0's registers)
-      // (the trial's selection lives in shared memory, *ctl, across the sweep)
+      // ---- warp 0: proposal and participants; the selection lives in
+      // shared memory (*ctl) across the sweep
       if (warp == 0) {
-        const TrialPre q = tp[t];
-        const int n = misc[0];
-        const int mv = pick32(q.w0, 2 * P.n_react);
-        const int r = P.react[mv >> 1];
-        const bool fwd = (mv & 1) == 0;
-        int flags = 0, site = -1, ionA = -1, ionB = -1, nch = 0;
-        bool bad = false;
-        long long ln_ratio = 0;
-        const unsigned long long newid = ((unsigned long long)(phi + 1u) << 32) |
-                                         (unsigned long long)(2u * ((uint32_t)d * (uint32_t)m + (uint32_t)kk));
-        unsigned long long id_a = ~0ull, id_b = ~0ull;
-        Desc c0 = {}, c1 = {};
-        float qa_o = 0.f, qa_n = 0.f, qb_o = 0.f, qb_n = 0.f;
-        int pa_o = 0, pa_n = 0, pb_o = 0, pb_n = 0;
-        if (r == R_ACID || r == R_BASE) {
-          const int kn = r == R_ACID ? K_A0 : K_B0, ki = r == R_ACID ? K_A1 : K_B1;
-          const int kx = r == R_ACID ? K_XP : K_XM;
-          const float qs = r == R_ACID ? -1.0f : 1.0f;
-          const int n0 = misc[1 + kn], n1 = misc[1 + ki], nx = misc[1 + kx];
-          if (fwd) {
-            if (n0 == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
-            else {
-              site = warp_kth(L.info, n, kn, pick32(q.w1, n0));
-              if (q.rankA < 0) flags |= CR_TRIAL_EDGE;
-              if (site < 0) { site = 0; bad = true; }
-              id_a = L.id[site];
-              id_b = newid;
-              const float4 sp4 = L.pos[site];
-              const int sinfo = L.info[site];
-              c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * qs, 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
-              c1 = Desc{q.ax, q.ay, q.az, P.lBf * (-qs * P.ion_q), 1, P.ion_cls, -1};
-              qa_o = 0.f; qa_n = qs; qb_o = 0.f; qb_n = -qs * P.ion_q;
-              pa_o = pa_n = 1; pb_o = 0; pb_n = 1;
-              nch = 2;
-              ln_ratio = lnt[n0] + P.lnz1_fx - lnt[n1 + 1];
-              ln_ratio -= lnt[nx + 1];
-              ln_ratio += L.lnk[site];
-            }
-          } else {
-            if (n1 == 0 || nx == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
-            else {
-              site = warp_kth(L.info, n, ki, pick32(q.w1, n1));
-              ionA = warp_kth(L.info, n, kx, pick32(q.w2, nx));
-              if (site < 0 || ionA < 0) { site = max(site, 0); ionA = max(ionA, 0); bad = true; }
-              id_a = L.id[site];
-              id_b = L.id[ionA];
-              const float4 sp4 = L.pos[site], ip4 = L.pos[ionA];
-              const int sinfo = L.info[site], iinfo = L.info[ionA];
-              c0 = Desc{sp4.x, sp4.y, sp4.z, P.lBf * (-qs), 0, (sinfo >> INFO_CLS_SHIFT) & 3, site};
-              c1 = Desc{ip4.x, ip4.y, ip4.z, P.lBf * (-ip4.w), -1, (iinfo >> INFO_CLS_SHIFT) & 3, ionA};
-              qa_o = qs; qa_n = 0.f; qb_o = ip4.w; qb_n = 0.f;
-              pa_o = pa_n = 1; pb_o = 1; pb_n = 0;
-              nch = 2;
-              ln_ratio = lnt[n1] - lnt[n0 + 1] - P.lnz1_fx;
-              ln_ratio += lnt[nx];
-              ln_ratio -= L.lnk[site];
-            }
-          }
-        } else {
-          const int nxp = misc[1 + K_XP], nxm = misc[1 + K_XM];
-          if (fwd) {
-            if (q.rankA < 0 || q.rankB < 0) flags |= CR_TRIAL_EDGE;
-            id_a = newid;
-            id_b = newid + 1u;
-            c0 = Desc{q.ax, q.ay, q.az, P.lBf * P.ion_q, 1, P.ion_cls, -1};
-            c1 = Desc{q.bx, q.by, q.bz, P.lBf * (-P.ion_q), 1, P.ion_cls, -1};
-            qa_o = 0.f; qa_n = P.ion_q; qb_o = 0.f; qb_n = -P.ion_q;
-            pa_o = 0; pa_n = 1; pb_o = 0; pb_n = 1;
-            nch = 2;
-            ln_ratio = 2 * P.lnz1_fx + P.lnsalt_fx;
-            ln_ratio -= lnt[nxp + 1] + lnt[nxm + 1];
-          } else {
-            if (nxp == 0 || nxm == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
-            else {
-              ionA = warp_kth(L.info, n, K_XP, pick32(q.w2, nxp));
-              ionB = warp_kth(L.info, n, K_XM, pick32(q.w3, nxm));
-              if (ionA < 0 || ionB < 0) { ionA = max(ionA, 0); ionB = max(ionB, 0); bad = true; }
-              id_a = L.id[ionA];
-              id_b = L.id[ionB];
-              const float4 a4 = L.pos[ionA], b4 = L.pos[ionB];
-              c0 = Desc{a4.x, a4.y, a4.z, P.lBf * (-a4.w), -1, (L.info[ionA] >> INFO_CLS_SHIFT) & 3, ionA};
-              c1 = Desc{b4.x, b4.y, b4.z, P.lBf * (-b4.w), -1, (L.info[ionB] >> INFO_CLS_SHIFT) & 3, ionB};
-              qa_o = a4.w; qa_n = 0.f; qb_o = b4.w; qb_n = 0.f;
-              pa_o = 1; pa_n = 0; pb_o = 1; pb_n = 0;
-              nch = 2;
-              ln_ratio = -2 * P.lnz1_fx - P.lnsalt_fx;
-              ln_ratio += lnt[nxp] + lnt[nxm];
-            }
-          }
-        }
-        // a failed selection would mean the kind counts and the list disagree:
-        // record it and reject instead of touching memory outside the list
-        if (bad) {
-          flags |= CR_TRIAL_NO_ELIGIBLE;
-          if (lane == 0) atomicOr(P.err, ERRB_ARG);
-        }
-        nch = (flags & (CR_TRIAL_NO_ELIGIBLE | CR_TRIAL_EDGE)) ? 0 : nch;
-        // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
-        const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
-                       (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
-        int rka = 0, rkb = 0;
-        if (DA && nch) {
-          if (r == R_SALT) {
-            rka = fwd ? q.rankA : L.rank[ionA];
-            rkb = fwd ? q.rankB : L.rank[ionB];
-          } else {
-            rka = L.rank[site];
-            rkb = fwd ? q.rankA : L.rank[ionA];
-          }
-        }
-        if (lane == 0) {
-          TrialCtl &C = *ctl;
-          C.c[0] = c0;
-          C.c[1] = c1;
-          C.nch = nch;
-          C.move = 2 * r + (fwd ? 0 : 1);
-          C.flags = flags;
-          C.site = site;
-          C.ionA = ionA;
-          C.ionB = ionB;
-          C.ln_ratio_fx = ln_ratio;
-          C.dself_fx = P.lBself_fx * (long long)sq;
-          C.id_a = id_a;
-          C.id_b = id_b;
-          C.newid = newid;
-          C.sur = 0.0f;
-          C.sur_fx = 0;
-          C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
-          C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
-          if (DA) {
-            C.rka = rka;
-            C.rkb = rkb;
-            C.dqa = (pa_n ? __float2int_rn(qa_n) : 0) - (pa_o ? __float2int_rn(qa_o) : 0);
-            C.dqb = (pb_n ? __float2int_rn(qb_n) : 0) - (pb_o ? __float2int_rn(qb_o) : 0);
-            C.eta_a = pa_n - pa_o;
-            C.eta_b = pb_n - pb_o;
-            C.cat_a = r == R_SALT ? 0 : 8;
-            C.go = 1;
-          }
-        }
+        TrialCtl C;
+        select_trial<DA>(P, L, misc, lnt, tp[t], d, m, kk, phi, C);
+        if (lane == 0) *ctl = C;
       }
       cta_sync<T>();
       // ---- delayed acceptance, stage 1: surrogate features and MLP (all
@@ -967,57 +1172,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       int ov = 0;
       if (nch) {
         const Desc A = ctl->c[0], B = ctl->c[1];
-        const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
-        int qn = 0;
-        if (R > 0) {
-#pragma unroll
-          for (int r = 0; r < RR; ++r) {
-            const float4 p = hreg[r];
-            const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-            const float q = p.w - 8.0f * (float)cls;
-            const bool v = r < nmine;
-            offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
-          }
-        } else {
-          const int lim = min(NH, hcap);
-          for (int base = 0; base < lim; base += T) {
-            const int j = base + tid;
-            const bool v = j < lim;
-            const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-            const float q = p.w - 8.0f * (float)cls;
-            offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
-          }
-        }
-        // halo beyond what is held on chip (dense regions): straight from global memory
-        for (int base = hcap; base < NH; base += T) {
-          const int j = base + tid;
-          const bool v = j < NH;
-          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-          int cls = 0;
-          if (v) {
-            const int i = upper_idx(hpre, NR, j);
-            const int g = hcell[i] * P.cap + (j - hpre[i]);
-            p = P.pos[g];
-            cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
-          }
-          offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-        }
-        const int n = misc[0];
-        for (int base = 0; base < n; base += T) {
-          const int j = base + tid;
-          const bool v = j < n && j != A.skip && j != B.skip;
-          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-          int cls = 0;
-          if (j < n) {
-            p = L.pos[j];
-            cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
-          }
-          offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-        }
-        __syncwarp();
-        if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
-        if (tid == cc_thread) cc_change(K, wca, *ctl, acc, sacc, ov);
+        sweep_pairs<LOG, R, RR>(K, wca, P, L, A, B, hreg, nmine, hpos, NH, hcap, hpre, hcell, NR, misc[0], tid, T,
+                                qr2, qqp, acc, sacc, ov);
+        if (tid == cc_thread) cc_change<LOG>(K, wca, *ctl, acc, sacc, ov);
         acc = warp_allsum(acc);
         if (LOG) sacc = (unsigned long long)warp_allsum((long long)sacc);
         ov = __any_sync(FULL, ov) ? 1 : 0;
@@ -1031,9 +1188,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       // ---- warp 0: decision and commit
       if (warp == 0) {
         const TrialPre &q = tp[t];
-        const int s_move = ctl->move, s_site = ctl->site, s_ionA = ctl->ionA, s_ionB = ctl->ionB, s_nch = ctl->nch;
+        const int s_move = ctl->move, s_nch = ctl->nch;
         const long long s_ln_ratio = ctl->ln_ratio_fx, s_dself = ctl->dself_fx;
-        const unsigned long long s_id_a = ctl->id_a, s_id_b = ctl->id_b, s_newid = ctl->newid;
+        const unsigned long long s_id_a = ctl->id_a, s_id_b = ctl->id_b;
         const bool s1 = !DA || ctl->go != 0;
         const float sur = DA ? ctl->sur : 0.0f;
         const long long sur_fx = DA ? ctl->sur_fx : 0ll;
@@ -1073,18 +1230,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         int n = misc[0];
         // cell capacity for insertions (checked before committing anything)
         int belowA = 0, sameA = 0;
-        if (accept && fwd) {
-          warp_rank_count(L.rank, n, q.rankA, belowA, sameA);
-          bool full = sameA + 1 > P.cap;
-          if (r == R_SALT) {
-            int below2, same2;
-            warp_rank_count(L.rank, n, q.rankB, below2, same2);
-            full = full || same2 + 1 + (q.rankB == q.rankA ? 1 : 0) > P.cap;
-          }
-          if (full || n + 2 > (in_smem ? S.dcs : P.dcap_glob)) {
-            accept = false;
-            if (lane == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
-          }
+        if (accept && fwd && !insert_room(P, L, n, in_smem ? S.dcs : P.dcap_glob, r, q, belowA, sameA)) {
+          accept = false;
+          if (lane == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
         }
         if (accept) {
           flags |= CR_TRIAL_ACCEPTED;
@@ -1103,77 +1251,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               }
             }
           }
-          if (r == R_ACID || r == R_BASE) {
-            const float qs = r == R_ACID ? -1.0f : 1.0f;
-            if (lane == 0) {
-              L.info[s_site] ^= INFO_ION_BIT;
-              L.pos[s_site].w = fwd ? qs : 0.0f;
-            }
-            __syncwarp();
-            if (fwd) {
-              const int p = belowA + sameA;  // after every entry of its cell rank
-              warp_insert_gap(L, n, p);
-              if (lane == 0) {
-                L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
-                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
-                L.id[p] = s_newid;
-                L.lnk[p] = 0;
-                L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
-                L.rank[p] = q.rankA;
-              }
-              n += 1;
-            } else {
-              warp_remove(L, n, s_ionA);
-              n -= 1;
-            }
-            if (lane == 0) {
-              const int kn = r == R_ACID ? K_A0 : K_B0, ki = kn + 1, kx = r == R_ACID ? K_XP : K_XM;
-              const int dlt = fwd ? 1 : -1;
-              misc[1 + kn] -= dlt;
-              misc[1 + ki] += dlt;
-              misc[1 + kx] += dlt;
-            }
-          } else {
-            if (fwd) {
-              int p = belowA + sameA;
-              warp_insert_gap(L, n, p);
-              if (lane == 0) {
-                L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
-                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
-                L.id[p] = s_newid;
-                L.lnk[p] = 0;
-                L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
-                L.rank[p] = q.rankA;
-              }
-              __syncwarp();
-              n += 1;
-              int below, same;
-              warp_rank_count(L.rank, n, q.rankB, below, same);
-              p = below + same;
-              warp_insert_gap(L, n, p);
-              if (lane == 0) {
-                L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
-                L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 7u, key0, key1);
-                L.id[p] = s_newid + 1u;
-                L.lnk[p] = 0;
-                L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
-                L.rank[p] = q.rankB;
-              }
-              n += 1;
-            } else {
-              const int hi = max(s_ionA, s_ionB), lo = min(s_ionA, s_ionB);
-              warp_remove(L, n, hi);
-              n -= 1;
-              warp_remove(L, n, lo);
-              n -= 1;
-            }
-            if (lane == 0) {
-              const int dlt = fwd ? 1 : -1;
-              misc[1 + K_XP] += dlt;
-              misc[1 + K_XM] += dlt;
-            }
-          }
-          __syncwarp();
+          n = commit_trial(P, L, misc, *ctl, q, n, belowA, sameA, kk, d, phi, key0, key1);
         }
         if (lane == 0) {
           misc[0] = n;
@@ -1208,7 +1286,6 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       cta_sync<T>();
     }
   }
-
   // ---- write the domain back (id-sorted cells) and publish counts
   __syncthreads();
   const int n = misc[0];
@@ -1347,11 +1424,10 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
   return cudaGetLastError();
 }
 
-// (threads per CTA, halo registers per thread; 0 = halo in shared memory)
-// variants the autotuner picks from
-// (threads, halo registers, compact): compact variants size the shared-memory
-// list and halo for most domains rather than the densest (denser ones spill
-// to global memory), so that more CTAs fit on an SM
+// variants the autotuner picks from: (threads per CTA, halo registers per
+// thread (0: the halo in shared memory), compact).  Compact variants size the
+// shared-memory list and halo for most domains rather than the densest
+// (denser ones spill to global memory), so that more CTAs fit on an SM.
 static const int kShapes[][3] = {{32, 0, 0},  {64, 0, 0},  {128, 0, 0}, {128, 4, 0}, {256, 0, 0}, {256, 2, 0},
                                  {512, 0, 0}, {512, 1, 0}, {32, 0, 1},  {64, 0, 1},  {128, 0, 1}, {256, 0, 1}};
 

@@ -240,8 +240,7 @@ def test_md_step_and_interleaved_cycles(crmc):
 @pytest.mark.parametrize("threads,regs", [(32, 0), (64, 0), (128, 0), (128, 4), (256, 0), (256, 2), (512, 0), (512, 1)])
 def test_launch_shape_does_not_change_the_chain(crmc, threads, regs):
     """Every (threads, halo registers) shape the autotuner may pick gives the
-    oracle's chain; (256, 2) and (512, 0)... cover registers, shared memory and
-    single-warp domains."""
+    oracle's chain: halo in registers or shared memory, single-warp domains."""
     w = W.config2(seed=2, scale=0.5)
     g = crmc.Context(w)
     g.set_launch_shape(threads, regs)

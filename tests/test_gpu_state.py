@@ -1,0 +1,99 @@
+"""cr_state (id order established on the device) and cr_load round trips,
+through the C ABI.
+
+  * arrays come out ordered by id -- input ids ascending, then inserted ions
+    (ids >= 2^32) ascending -- and equal the oracle's particles, with the
+    interaction classes cr_load takes;
+  * before any insertion (no ion to sort), after one sweep and after many;
+  * cr_load of a read-back reproduces the configuration (ids become the
+    indices) and its counts, and sweeps continue from it;
+  * pinned host buffers (raw pointers) give the same arrays as numpy arrays.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_07527_gb300 import workloads as W
+from parity_util import compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crmc():
+    from paper_2109_07527_gb300 import crmc as m
+    m._lib()
+    return m
+
+
+def _expected_cls(w, s):
+    ids, t = s["id"], s["type"]
+    ion = (t == W.XP) | (t == W.XM)
+    base = w.cls[np.minimum(ids, w.n - 1).astype(np.int64)]
+    return np.where(ion, int(w.params["ion_cls"]), base).astype(np.int32)
+
+
+@pytest.mark.parametrize("sweeps", [0, 1, 6])
+def test_state_is_id_ordered_and_matches_oracle(crmc, sweeps):
+    w = W.config2(seed=4, scale=0.5)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    if sweeps:
+        g.sweep(g.trials_per_sweep * sweeps, 21)
+        o.sweep(o.trials_per_sweep * sweeps, 21)
+    sg, _ = compare_states(g, o, w.n_sites)
+    ids = sg["id"]
+    assert np.all(ids[1:] > ids[:-1])
+    inserted = ids >= np.uint64(1 << 32)
+    if inserted.any():  # inserted ions after every input particle
+        assert np.all(inserted[int(np.argmax(inserted)):])
+    if sweeps == 0:
+        assert not inserted.any() and np.array_equal(ids, np.arange(w.n, dtype=np.uint64))
+    else:
+        assert inserted.sum() > 0
+    assert np.array_equal(sg["cls"], _expected_cls(w, sg))
+
+
+def test_load_round_trip(crmc):
+    w = W.config2(seed=5, scale=0.5, pH=6.0)
+    g = crmc.Context(w)
+    g.sweep(g.trials_per_sweep * 4, 3)
+    g.md_step(2, 0.005, 1.0, 9)
+    s = g.state()
+    n = int(s["n"])
+    h = crmc.Context(w)
+    h.load(n, np.ascontiguousarray(s["xyz"]), np.ascontiguousarray(s["vel"]), s["type"], s["cls"], s["state"])
+    t = h.state()
+    assert np.array_equal(t["id"], np.arange(n, dtype=np.uint64))
+    for k in ("xyz", "vel", "type", "state", "cls", "site_state"):
+        assert np.array_equal(t[k], s[k]), k
+    for k in ("n", "n_A", "n_Am", "n_B", "n_Bp", "n_Xp", "n_Xm", "net_charge"):
+        assert t[k] == s[k], k
+    h.sweep(h.trials_per_sweep * 2, 4)
+    h.check()
+    u = h.state()
+    assert u["net_charge"] == 0 and np.all(u["id"][1:] > u["id"][:-1])
+
+
+def test_state_into_pinned_buffers(crmc):
+    torch = pytest.importorskip("torch")
+    w = W.config2(seed=6, scale=0.5)
+    g = crmc.Context(w)
+    g.sweep(g.trials_per_sweep * 3, 8)
+    ref = g.state()
+    cap = w.capacity
+    b = dict(xyz=torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
+             vel=torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
+             id=torch.empty(cap, dtype=torch.int64).pin_memory(),
+             type=torch.empty(cap, dtype=torch.int32).pin_memory(),
+             state=torch.empty(cap, dtype=torch.int8).pin_memory(),
+             cls=torch.empty(cap, dtype=torch.int32).pin_memory())
+    c = g.state_into(**{k: v.data_ptr() for k, v in b.items()})
+    n = int(c["n"])
+    assert n == int(ref["n"])
+    assert np.array_equal(b["xyz"].numpy()[:n], ref["xyz"])
+    assert np.array_equal(b["vel"].numpy()[:n], ref["vel"])
+    assert np.array_equal(b["id"].numpy()[:n].view(np.uint64), ref["id"])
+    assert np.array_equal(b["type"].numpy()[:n], ref["type"])
+    assert np.array_equal(b["state"].numpy()[:n], ref["state"])
+    assert np.array_equal(b["cls"].numpy()[:n], ref["cls"])
