@@ -453,7 +453,7 @@ def run_ours(args):
         # every replica's configuration goes through pinned host buffers each
         # step (allocated once, as a caller coupling the library to its own
         # host-side code would): cr_load uploads it, the batched cycle runs,
-        # cr_state reads the new configuration back into the same buffers
+        # cr_batch_state reads every new configuration back into the same buffers
         bufs = []
         for g in ctxs:
             cap = g.capacity
@@ -465,13 +465,13 @@ def run_ours(args):
                      cls=torch.empty(cap, dtype=torch.int32).pin_memory())
             bufs.append(b)
 
-        def read_back(g, b):
-            c = g.state_into(xyz=b["xyz"].data_ptr(), vel=b["vel"].data_ptr(), id=b["id"].data_ptr(),
-                             type=b["type"].data_ptr(), state=b["state"].data_ptr(), cls=b["cls"].data_ptr())
-            return int(c["n"])
+        views = [{k: v.data_ptr() for k, v in b.items()} for b in bufs]
 
-        ns = [read_back(g, b) for g, b in zip(ctxs, bufs)]
-        e2e_steps = 5
+        def read_back():
+            return [int(c["n"]) for c in batch.state_into(views)]
+
+        ns = read_back()
+        e2e_steps = 20
         h2d = d2h = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -483,15 +483,15 @@ def run_ours(args):
             batch.md_begin(dt, gamma, 9500 + s)
             batch.sweep(1, 9000 + s)
             batch.md_end(dt, gamma, 9500 + s)
-            ns = [read_back(g, b) for g, b in zip(ctxs, bufs)]
+            ns = read_back()
             d2h += sum(n * (12 + 12 + 8 + 4 + 1 + 4) + 64 for n in ns)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "note": "per step: cr_load of the 13 replicas from pinned host buffers + the batched cycle (1e4 "
-                       "trials per replica inside one MD step) + cr_state readback of every replica into the same "
-                       "pinned buffers"}
+                       "trials per replica inside one MD step) + cr_batch_state readback of every replica into the "
+                       "same pinned buffers"}
 
     if rank != 0:
         return

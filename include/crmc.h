@@ -294,9 +294,13 @@ int cr_state(cr_ctx *ctx, cr_state_view *out);
  * vel [3n] or NULL, type [n], cls [n], state [n]; pinned memory gives
  * asynchronous copies).  Particle ids become the indices.  Bonded and site
  * particles must be those given to cr_init, at the same indices (the state
- * arrays returned by cr_state qualify); ions may differ.  Cells are rebuilt
- * on the device.  Errors: INVALID_ARG, NOT_NEUTRAL, CELL_OVERFLOW (at the
- * next synchronising call). */
+ * arrays returned by cr_state qualify); ions may differ.  The arrays are
+ * checked and the cells rebuilt on the device, asynchronously: INVALID_ARG
+ * for NULL arrays or n out of range at once; a particle of unknown type or
+ * class, outside [0, L), or a bonded / site particle missing or moved
+ * (INVALID_ARG), a configuration that is not neutral (NOT_NEUTRAL) and a full
+ * cell (CELL_OVERFLOW) at the next synchronising call (cr_check, cr_state);
+ * the context is then unusable. */
 int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type, const int32_t *cls,
             const int8_t *state);
 
@@ -350,6 +354,11 @@ int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint
 /* cr_md_begin / cr_md_end on every replica (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed);
 int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
+/* cr_state of every replica of the batch into views[0 .. n-1] (one view per
+ * context, in the order given to cr_batch_create); the replicas' reads run
+ * concurrently on the batch's streams with two synchronisations in all.
+ * Returns the first error of a replica. */
+int cr_batch_state(cr_batch *b, cr_state_view *views);
 /* Fix the batch's launch shape (as cr_set_launch_shape; 0, 0 restarts the tuning). */
 int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs);
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);

@@ -85,7 +85,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
-           "cr_batch_md_end", "cr_batch_set_launch_shape")
+           "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -144,6 +144,8 @@ def _lib():
         lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
         lib.cr_state.restype = C.c_int
         lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
+        lib.cr_batch_state.restype = C.c_int
+        lib.cr_batch_state.argtypes = [P, C.POINTER(cr_state_view)]
         lib.cr_get_info.restype = C.c_int
         lib.cr_get_info.argtypes = [P, C.POINTER(cr_info)]
         lib.cr_set_stream.restype = C.c_int
@@ -196,6 +198,19 @@ def philox(c0, c1, c2, c3, k0, k1, n):
     out = np.zeros((n, 4), dtype=np.uint32)
     _chk(_lib().cr_philox(c0, c1, c2, c3, k0, k1, n, _p(out)), "cr_philox")
     return out
+
+
+def _view(**arrays):
+    """A cr_state_view over caller arrays (numpy arrays or raw pointers; None = not wanted)."""
+    v = cr_state_view()
+    for k, a in arrays.items():
+        setattr(v, k, None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a)))
+    return v
+
+
+def _view_counts(v):
+    return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
+                net_charge=v.net_charge, alpha=v.alpha)
 
 
 def _torch_stream():
@@ -373,13 +388,9 @@ class Context:
         """cr_state into caller-owned host arrays (numpy arrays or raw pointers,
         e.g. pinned buffers reused every step, each sized for the capacity);
         returns the counts."""
-        conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
-        v = cr_state_view()
-        v.xyz, v.vel, v.force, v.id = conv(xyz), conv(vel), conv(force), conv(id)
-        v.type, v.state, v.site_state, v.cls = conv(type), conv(state), conv(site_state), conv(cls)
+        v = _view(xyz=xyz, vel=vel, id=id, type=type, state=state, site_state=site_state, force=force, cls=cls)
         _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
-        return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
-                    net_charge=v.net_charge, alpha=v.alpha)
+        return _view_counts(v)
 
     def state(self):
         """Counts and all particles sorted by id."""
@@ -421,6 +432,15 @@ class Batch:
 
     def md_begin(self, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_begin")
+
+    def state_into(self, arrays):
+        """cr_batch_state: one dict of caller arrays (as Context.state_into
+        takes them) per replica; returns the counts of every replica."""
+        views = (cr_state_view * len(self.contexts))()
+        for r, a in enumerate(arrays):
+            views[r] = _view(**a)
+        _chk(self._lib.cr_batch_state(self._h, views), "cr_batch_state")
+        return [_view_counts(views[r]) for r in range(len(self.contexts))]
 
     def md_end(self, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_end(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_end")

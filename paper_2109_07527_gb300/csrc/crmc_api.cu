@@ -92,6 +92,8 @@ struct cr_ctx {
   bool f_valid = false, fcons_valid = false;
   // input encoding kept for cr_load: type of every input particle, site index
   std::vector<int> init_type, init_site;
+  int *d_init_type = nullptr;  // init_type on the device (cr_load checks)
+  int n_fixed_end = 0;         // one past the last bonded / site particle of cr_init
   // kernel timing (CUDA events on the context stream) and launch counters
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -143,6 +145,7 @@ int err_bits_to_code(int bits) {
   if (bits & ERRB_BOND) return CR_ERR_BOND_BROKEN;
   if (bits & ERRB_TIMEOUT) return CR_ERR_TIMEOUT;
   if (bits & ERRB_ARG) return CR_ERR_INVALID_ARG;
+  if (bits & ERRB_NOT_NEUTRAL) return CR_ERR_NOT_NEUTRAL;
   return CR_OK;
 }
 
@@ -169,7 +172,7 @@ static void free_ctx(cr_ctx *c) {
   void *ptrs[] = {c->d_cnt, c->d_cnt2, c->d_info, c->d_info2, c->d_pos, c->d_pos2, c->d_vel, c->d_vel2,
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log,
-                  c->d_in_xyz, c->d_in_vel, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
+                  c->d_in_xyz, c->d_in_vel, c->d_init_type, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
                   c->d_present, c->d_pre, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_sort_tmp,
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
@@ -416,6 +419,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   long long *kinds = Lo.kinds;
   c->init_type.assign(sys->type, sys->type + n);
   c->init_site = site_of;
+  for (int i = 0; i < n; ++i)
+    if (sys->type[i] != CR_XP && sys->type[i] != CR_XM) c->n_fixed_end = i + 1;
   c->n_other = (int)kinds[K_OTHER];
 
   // ---- bonds (CSR by permanent particle)
@@ -561,6 +566,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_in_cls, (size_t)sys->capacity);
   ALLOC(c->d_in_state, (size_t)sys->capacity);
   ALLOC(c->d_site_map, (size_t)std::max(n, 1));
+  ALLOC(c->d_init_type, (size_t)std::max(n, 1));
   {
     const size_t cp = (size_t)std::max(sys->capacity, 1);
     ALLOC(c->d_present, (size_t)std::max(n, 1));
@@ -618,6 +624,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_bond_nbr, nbr.data(), nbr.size());
   COPY(c->d_counts, kinds, (size_t)6);
   if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
+  if (n > 0) COPY(c->d_init_type, sys->type, (size_t)n);
 #undef COPY
   cudaMemset(c->d_cnt2, 0, sizeof(int) * P.ncell);
   cudaMemset(c->d_frc, 0, sizeof(float4) * nslot);
@@ -993,14 +1000,14 @@ extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   return CR_OK;
 }
 
-extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
-  if (!ctx || !out) return CR_ERR_INVALID_ARG;
-  cudaStream_t s = ctx->stream;
+// A state read in two halves around one synchronisation of the stream:
+// state_begin queues the id marks (when arrays are wanted) and the copies of
+// the counts and the error word; state_arrays, with those on the host, fills
+// the counts of the view and queues the ordering and one copy per array.
+static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, StateBufs &B, bool &want) {
   long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] ions found, [7] error word
-  int *hions = (int *)(hs + 6), *herr = (int *)(hs + 7);
-  const bool want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state ||
-                    out->cls;
-  StateBufs B{};
+  want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state || out->cls;
+  B = StateBufs{};
   B.n_input = ctx->n_input;
   B.cap = (int)ctx->capacity;
   B.present = ctx->d_present;
@@ -1025,11 +1032,16 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   if (want) {
     CR_CUDA(launch_state_mark(ctx->P, B, s));
     ctx->launches_total++;
-    CR_CUDA(cudaMemcpyAsync(hions, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CR_CUDA(cudaMemcpyAsync(hs + 6, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
   }
   CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CR_CUDA(cudaMemcpyAsync(herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CR_CUDA(cudaStreamSynchronize(s));
+  CR_CUDA(cudaMemcpyAsync(hs + 7, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return CR_OK;
+}
+
+static int state_arrays(cr_ctx *ctx, cr_state_view *out, cudaStream_t s, const StateBufs &B, bool want) {
+  const long long *hs = ctx->h_small;
+  const int n_ions = *(const int *)(hs + 6), bits = *(const int *)(hs + 7);
   out->n_A = hs[K_A0] + hs[K_A1];
   out->n_Am = hs[K_A1];
   out->n_B = hs[K_B0] + hs[K_B1];
@@ -1039,11 +1051,10 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   out->n = out->n_A + out->n_B + out->n_Xp + out->n_Xm + ctx->n_other;
   out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
   out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
-  const int err0 = err_bits_to_code(*herr);
+  const int err0 = err_bits_to_code(bits);
   if (!want || err0 != CR_OK) return err0;
   const int64_t n = out->n;
   if (n > ctx->capacity) return CR_ERR_CAPACITY;
-  const int n_ions = *hions;
   const int64_t n_present = n - n_ions;
   if (n_ions < 0 || n_ions > ctx->capacity || n_present < 0 || n_present > ctx->n_input) return CR_ERR_CUDA;
   // inserted ids are (phase + 1) << 32 | index with phase < sweeps * colours:
@@ -1063,6 +1074,19 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   if (out->state) CR_CUDA(cudaMemcpyAsync(out->state, B.state, nn, cudaMemcpyDeviceToHost, s));
   if (out->site_state && ctx->n_sites > 0)
     CR_CUDA(cudaMemcpyAsync(out->site_state, B.site, (size_t)ctx->n_sites, cudaMemcpyDeviceToHost, s));
+  return CR_OK;
+}
+
+extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
+  if (!ctx || !out) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  StateBufs B;
+  bool want = false;
+  int rc = state_begin(ctx, out, s, B, want);
+  if (rc != CR_OK) return rc;
+  CR_CUDA(cudaStreamSynchronize(s));
+  rc = state_arrays(ctx, out, s, B, want);
+  if (rc != CR_OK || !want) return rc;
   CR_CUDA(cudaStreamSynchronize(s));
   return CR_OK;
 }
@@ -1083,30 +1107,10 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
                        const int32_t *cls, const int8_t *state) {
   if (!ctx || n < 0 || n > ctx->capacity) return CR_ERR_INVALID_ARG;
   if (n > 0 && (!xyz || !type || !cls || !state)) return CR_ERR_INVALID_ARG;
+  // every bonded / site particle of cr_init must be there (at its index; the
+  // load kernels check each particle and the neutrality on the device)
+  if (n < ctx->n_fixed_end) return CR_ERR_INVALID_ARG;
   const SysParams &P = ctx->P;
-  // the bonded / site particles must be those of cr_init, at the same indices
-  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
-  int qsum = 0, n_fixed = 0, n_fixed_init = 0;
-  for (int t : ctx->init_type) n_fixed_init += (t != CR_XP && t != CR_XM);
-  for (int i = 0; i < n; ++i) {
-    const int t = type[i];
-    if (t < CR_BEAD || t > CR_CORE || cls[i] < 0 || cls[i] > 3) return CR_ERR_INVALID_ARG;
-    const float X = xyz[3 * i], Y = xyz[3 * i + 1], Z = xyz[3 * i + 2];
-    if (!(X >= 0.0f && X < P.Lf && Y >= 0.0f && Y < P.Lf && Z >= 0.0f && Z < P.Lf)) return CR_ERR_INVALID_ARG;
-    if (t != CR_XP && t != CR_XM) {
-      if (i >= (int)ctx->init_type.size() || ctx->init_type[i] != t) return CR_ERR_INVALID_ARG;
-      n_fixed++;
-    }
-    const int ion = (t == CR_ACID || t == CR_BASE) && state[i] ? 1 : 0;
-    int kd = K_OTHER;
-    if (t == CR_ACID) { kd = ion ? K_A1 : K_A0; qsum -= ion; }
-    else if (t == CR_BASE) { kd = ion ? K_B1 : K_B0; qsum += ion; }
-    else if (t == CR_XP) { kd = K_XP; qsum += 1; }
-    else if (t == CR_XM) { kd = K_XM; qsum -= 1; }
-    kinds[kd]++;
-  }
-  if (n_fixed != n_fixed_init) return CR_ERR_INVALID_ARG;
-  if (qsum != 0) return CR_ERR_NOT_NEUTRAL;
   cudaStream_t s = ctx->stream;
   if (n > 0) {
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
@@ -1115,13 +1119,12 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
   }
-  (void)kinds;  // counted again on the device by the load kernel (no pageable copy)
   CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * 6, s));
   LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
-             ctx->d_in_state, n, ctx->n_input};
+             ctx->d_in_state, n, ctx->n_input, ctx->d_init_type};
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
   CR_CUDA(launch_load(P, I, B, ctx->d_perm, ctx->n_input, s));
-  ctx->launches_total += 2;
+  ctx->launches_total += 3;
   ctx->f_valid = false;
   ctx->fcons_valid = false;
   return CR_OK;
@@ -1402,6 +1405,32 @@ extern "C" int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t 
 
 extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed) {
   return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
+}
+
+// cr_state of every replica: the halves of all replicas run on the
+// replicas' streams, two synchronisations in all
+extern "C" int cr_batch_state(cr_batch *b, cr_state_view *views) {
+  if (!b || !views) return CR_ERR_INVALID_ARG;
+  const size_t n = b->ctx.size();
+  cudaStream_t s = b->ctx[0]->stream;
+  CR_CUDA(cudaEventRecord(b->fork, s));
+  std::vector<StateBufs> B(n);
+  std::vector<char> want(n, 0);
+  int rc = CR_OK;
+  for (size_t r = 0; r < n; ++r) {
+    CR_CUDA(cudaStreamWaitEvent(b->streams[r], b->fork, 0));
+    bool w = false;
+    const int e = state_begin(b->ctx[r], &views[r], b->streams[r], B[r], w);
+    want[r] = w;
+    if (e != CR_OK) return e;
+  }
+  for (size_t r = 0; r < n; ++r) CR_CUDA(cudaStreamSynchronize(b->streams[r]));
+  for (size_t r = 0; r < n; ++r) {
+    const int e = state_arrays(b->ctx[r], &views[r], b->streams[r], B[r], want[r] != 0);
+    if (e != CR_OK && rc == CR_OK) rc = e;
+  }
+  for (size_t r = 0; r < n; ++r) CR_CUDA(cudaStreamSynchronize(b->streams[r]));
+  return rc;
 }
 
 extern "C" int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs) {

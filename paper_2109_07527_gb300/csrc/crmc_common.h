@@ -127,5 +127,6 @@ constexpr int ERRB_CAPACITY = 2;
 constexpr int ERRB_BOND = 4;
 constexpr int ERRB_TIMEOUT = 8;
 constexpr int ERRB_ARG = 16;
+constexpr int ERRB_NOT_NEUTRAL = 32;
 
 }  // namespace crmc

@@ -53,6 +53,7 @@ struct LoadBufs {
   const int *type, *cls, *site;  // site: site index of input particle i (-1 none)
   const int8_t *state;
   int n, n_site_map;
+  const int *init_type;  // [n_site_map] types given to cr_init (bonded and site particles stay at their index)
 };
 
 // phase kernel shapes (threads, halo registers); da: the delayed-acceptance set

@@ -339,12 +339,29 @@ __global__ void k_perm_slots(SysParams P, int *perm_slot, int n_perm) {
   if (id < (unsigned long long)n_perm) perm_slot[id] = g;
 }
 
+// the loaded configuration must be neutral (kind counts of the load)
+__global__ void k_load_neutral(SysParams P) {
+  if (threadIdx.x != 0) return;
+  const long long q = P.counts[K_XP] - P.counts[K_XM] - P.counts[K_A1] + P.counts[K_B1];
+  if (q != 0) atomicOr(P.err, ERRB_NOT_NEUTRAL);
+}
+
 // load: place input particles (index = id) into cells, unordered
 __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= I.n) return;
   const float x = I.xyz[3 * i], y = I.xyz[3 * i + 1], z = I.xyz[3 * i + 2];
   const int t = I.type[i];
+  {  // the particle must be valid and a bonded / site particle of cr_init must keep its index and type
+    const int ti = i < I.n_site_map ? I.init_type[i] : CR_XP;
+    const bool fixed = ti != CR_XP && ti != CR_XM;
+    const bool ok = t >= CR_BEAD && t <= CR_CORE && I.cls[i] >= 0 && I.cls[i] <= 3 && x >= 0.0f && x < P.Lf &&
+                    y >= 0.0f && y < P.Lf && z >= 0.0f && z < P.Lf && (fixed ? t == ti : (t == CR_XP || t == CR_XM));
+    if (!ok) {
+      atomicOr(P.err, ERRB_ARG);
+      return;
+    }
+  }
   const int ion = (t == CR_ACID || t == CR_BASE) && I.state[i] ? 1 : 0;
   float q = 0.0f;
   int cl = I.cls[i];
@@ -417,6 +434,7 @@ cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs
                         cudaStream_t s) {
   if (I.n > 0) k_load_scatter<<<(I.n + 255) / 256, 256, 0, s>>>(P, I, B);
   k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
+  k_load_neutral<<<1, 32, 0, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -7,7 +7,10 @@ through the C ABI.
   * before any insertion (no ion to sort), after one sweep and after many;
   * cr_load of a read-back reproduces the configuration (ids become the
     indices) and its counts, and sweeps continue from it;
-  * pinned host buffers (raw pointers) give the same arrays as numpy arrays.
+  * pinned host buffers (raw pointers) give the same arrays as numpy arrays;
+  * a batch read (cr_batch_state) equals the contexts' own reads;
+  * cr_load checks on the device: a non-neutral configuration, a moved site
+    and a particle outside the box are reported at the next check.
 """
 import numpy as np
 import pytest
@@ -97,3 +100,49 @@ def test_state_into_pinned_buffers(crmc):
     assert np.array_equal(b["type"].numpy()[:n], ref["type"])
     assert np.array_equal(b["state"].numpy()[:n], ref["state"])
     assert np.array_equal(b["cls"].numpy()[:n], ref["cls"])
+
+
+def test_batch_state_equals_context_states(crmc):
+    ws = [W.config2(seed=9, scale=0.5, pH=pH) for pH in (3.0, 5.0, 7.0)]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(3, 5)
+    refs = [g.state() for g in ctxs]
+    arrs = []
+    for w in ws:
+        cap = w.capacity
+        arrs.append(dict(xyz=np.zeros((cap, 3), np.float32), vel=np.zeros((cap, 3), np.float32),
+                         id=np.zeros(cap, np.uint64), type=np.zeros(cap, np.int32), state=np.zeros(cap, np.int8),
+                         cls=np.zeros(cap, np.int32), site_state=np.zeros(max(w.n_sites, 1), np.int8)))
+    counts = b.state_into(arrs)
+    for ref, a, c, w in zip(refs, arrs, counts, ws):
+        n = int(c["n"])
+        assert n == int(ref["n"]) and c["n_Am"] == ref["n_Am"] and c["alpha"] == ref["alpha"]
+        for k in ("xyz", "vel", "id", "type", "state", "cls"):
+            assert np.array_equal(a[k][:n], ref[k]), k
+        assert np.array_equal(a["site_state"][:w.n_sites], ref["site_state"])
+
+
+@pytest.mark.parametrize("fault", ["not_neutral", "site_moved", "outside"])
+def test_load_errors_reported_at_the_next_check(crmc, fault):
+    w = W.config2(seed=10, scale=0.5)
+    g = crmc.Context(w)
+    s = g.state()
+    n = int(s["n"])
+    xyz, t, st = s["xyz"].copy(), s["type"].copy(), s["state"].copy()
+    if fault == "not_neutral":
+        k = int(np.flatnonzero(t == W.XP)[0])
+        t[k] = W.XM
+        code = "NOT_NEUTRAL"
+    elif fault == "site_moved":
+        k = int(np.flatnonzero(t == W.ACID)[0])
+        t[k] = W.BEAD
+        code = "INVALID_ARG"
+    else:
+        xyz[0, 0] = np.float32(w.params["box_L"]) * 2
+        code = "INVALID_ARG"
+    h = crmc.Context(w)
+    h.load(n, xyz, s["vel"], t, s["cls"], st)  # checked on the device
+    with pytest.raises(crmc.CrError) as e:
+        h.check()
+    assert crmc.ERRORS[e.value.code] == code
