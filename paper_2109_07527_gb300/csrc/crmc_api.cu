@@ -49,7 +49,10 @@ struct cr_ctx {
   unsigned long long *d_pid = nullptr, *d_pid2 = nullptr, *d_stats = nullptr;
   long long *d_lnK = nullptr, *d_lntab = nullptr;
   long long *d_counts = nullptr;
-  int *d_err = nullptr, *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr, *d_counter = nullptr;
+  int *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr;
+  // d_counts holds 8 words: [0..5] kind counts, [6] ions found by cr_state
+  // (an int), [7] the error word (an int), read back with one copy
+  int *d_err = nullptr, *d_counter = nullptr;
   cr_trial *d_log = nullptr;
   size_t log_cap = 0;
   // dense-domain scratch of the phase kernel and the MD particle list
@@ -75,7 +78,8 @@ struct cr_ctx {
   int8_t *d_in_state = nullptr;
   // cr_state: id ordering on the device and the output arrays in the
   // caller's layouts (capacity-sized), one copy each to the caller
-  int *d_present = nullptr, *d_pre = nullptr;
+  int *d_present = nullptr;
+  int ion_lo_bits = 32;  // the low words of inserted ids stay below 2^ion_lo_bits
   unsigned long long *d_ion_key = nullptr, *d_ion_key2 = nullptr;
   int *d_ion_val = nullptr, *d_ion_val2 = nullptr;
   unsigned char *d_sort_tmp = nullptr;
@@ -171,9 +175,9 @@ static void free_ctx(cr_ctx *c) {
   if (!c) return;
   void *ptrs[] = {c->d_cnt, c->d_cnt2, c->d_info, c->d_info2, c->d_pos, c->d_pos2, c->d_vel, c->d_vel2,
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
-                  c->d_counts, c->d_err, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_counter, c->d_log,
+                  c->d_counts, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_log,
                   c->d_in_xyz, c->d_in_vel, c->d_init_type, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
-                  c->d_present, c->d_pre, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_sort_tmp,
+                  c->d_present, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_sort_tmp,
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
@@ -555,11 +559,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_lnK, std::max<size_t>(lnK.size(), 1));
   ALLOC(c->d_lntab, P.lnmax);
   ALLOC(c->d_counts, 8);
-  ALLOC(c->d_err, 1);
   ALLOC(c->d_perm, std::max(n, 1));
   ALLOC(c->d_bond_off, n + 1);
   ALLOC(c->d_bond_nbr, std::max(2 * nb, 1));
-  ALLOC(c->d_counter, 1);
   ALLOC(c->d_in_xyz, 3 * (size_t)sys->capacity);
   ALLOC(c->d_in_vel, 3 * (size_t)sys->capacity);
   ALLOC(c->d_in_type, (size_t)sys->capacity);
@@ -570,13 +572,21 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   {
     const size_t cp = (size_t)std::max(sys->capacity, 1);
     ALLOC(c->d_present, (size_t)std::max(n, 1));
-    ALLOC(c->d_pre, (size_t)std::max(n, 1));
     ALLOC(c->d_ion_key, cp);
-    ALLOC(c->d_ion_key2, cp);
     ALLOC(c->d_ion_val, cp);
-    ALLOC(c->d_ion_val2, cp);
-    c->sort_tmp_bytes = std::max<size_t>(state_sort_temp_bytes((int)cp), 16);
-    ALLOC(c->d_sort_tmp, c->sort_tmp_bytes);
+    c->sort_tmp_bytes = state_sort_temp_bytes((int)cp);
+    if (c->sort_tmp_bytes > 0) {  // ion lists beyond the one-CTA sort
+      ALLOC(c->d_ion_key2, cp);
+      ALLOC(c->d_ion_val2, cp);
+      ALLOC(c->d_sort_tmp, c->sort_tmp_bytes);
+    }
+    // low word of an inserted id: 2 (domain * trials per domain + trial) + 0/1;
+    // ids from cr_load are indices below the capacity
+    const unsigned long long lo_max =
+        std::max<unsigned long long>(2ull * (unsigned long long)P.nd * P.nd * P.nd * (unsigned long long)P.m,
+                                     (unsigned long long)cp);
+    c->ion_lo_bits = 1;
+    while (c->ion_lo_bits < 32 && (lo_max >> c->ion_lo_bits) != 0) ++c->ion_lo_bits;
     ALLOC(c->d_out_xyz, 3 * cp);
     ALLOC(c->d_out_vel, 3 * cp);
     ALLOC(c->d_out_frc, 3 * cp);
@@ -622,6 +632,10 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_perm, h_perm.data(), (size_t)std::max(n, 1));
   COPY(c->d_bond_off, deg.data(), (size_t)n + 1);
   COPY(c->d_bond_nbr, nbr.data(), nbr.size());
+  c->d_counter = (int *)(c->d_counts + 6);
+  c->d_err = (int *)(c->d_counts + 7);
+  cudaMemset(c->d_counts, 0, sizeof(long long) * 8);
+  cudaMemset(c->d_present, 0, sizeof(int) * (size_t)std::max(n, 1));
   COPY(c->d_counts, kinds, (size_t)6);
   if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
   if (n > 0) COPY(c->d_init_type, sys->type, (size_t)n);
@@ -630,7 +644,6 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   cudaMemset(c->d_frc, 0, sizeof(float4) * nslot);
   cudaMemset(c->d_fcons, 0, sizeof(float4) * nslot);
   cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16);
-  cudaMemset(c->d_err, 0, sizeof(int));
   P.lnK_fx = c->d_lnK;
   P.lntab_fx = c->d_lntab;
   P.cnt = c->d_cnt;
@@ -1010,8 +1023,8 @@ static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, St
   B = StateBufs{};
   B.n_input = ctx->n_input;
   B.cap = (int)ctx->capacity;
+  B.lo_bits = ctx->ion_lo_bits;
   B.present = ctx->d_present;
-  B.pre = ctx->d_pre;
   B.n_ions = ctx->d_counter;
   B.ion_key = ctx->d_ion_key;
   B.ion_key_alt = ctx->d_ion_key2;
@@ -1032,10 +1045,9 @@ static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, St
   if (want) {
     CR_CUDA(launch_state_mark(ctx->P, B, s));
     ctx->launches_total++;
-    CR_CUDA(cudaMemcpyAsync(hs + 6, ctx->d_counter, sizeof(int), cudaMemcpyDeviceToHost, s));
   }
-  CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
-  CR_CUDA(cudaMemcpyAsync(hs + 7, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // kind counts, ions found and the error word: adjacent, one copy
+  CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
   return CR_OK;
 }
 
@@ -1052,17 +1064,26 @@ static int state_arrays(cr_ctx *ctx, cr_state_view *out, cudaStream_t s, const S
   out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
   out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
   const int err0 = err_bits_to_code(bits);
-  if (!want || err0 != CR_OK) return err0;
+  if (!want) return err0;
   const int64_t n = out->n;
-  if (n > ctx->capacity) return CR_ERR_CAPACITY;
   const int64_t n_present = n - n_ions;
-  if (n_ions < 0 || n_ions > ctx->capacity || n_present < 0 || n_present > ctx->n_input) return CR_ERR_CUDA;
-  // inserted ids are (phase + 1) << 32 | index with phase < sweeps * colours:
-  // the radix sort covers the bits that can be set
-  int end_bit = 33;
-  while (end_bit < 64 && (ctx->sweep * (uint64_t)ctx->P.ncol + 1) >> (end_bit - 32)) ++end_bit;
+  int rc = err0;
+  if (rc == CR_OK && n > ctx->capacity) rc = CR_ERR_CAPACITY;
+  if (rc == CR_OK && (n_ions < 0 || n_ions > ctx->capacity || n_present < 0 || n_present > ctx->n_input))
+    rc = CR_ERR_CUDA;
+  if (rc != CR_OK) {  // clear the marks for the next read
+    CR_CUDA(cudaMemsetAsync(ctx->d_present, 0, sizeof(int) * (size_t)std::max(ctx->n_input, 1), s));
+    CR_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
+    return rc;
+  }
+  // inserted ids are (phase + 1) << 32 | low word with phase < sweeps *
+  // colours: the sort keys (high word above the low word's bits) need
+  // ion_lo_bits + bits of the phase, plus one
+  const uint64_t hi_max = ctx->sweep * (uint64_t)ctx->P.ncol + 1;
+  int end_bit = ctx->ion_lo_bits + 1;
+  while (end_bit < 64 && (hi_max >> (end_bit - ctx->ion_lo_bits - 1)) != 0) ++end_bit;
   int nl = 0;
-  CR_CUDA(launch_state_emit(ctx->P, B, (int)n_present, n_ions, end_bit, s, &nl));
+  CR_CUDA(launch_state_order(ctx->P, B, (int)n_present, n_ions, end_bit, s, &nl));
   ctx->launches_total += nl;
   const size_t nn = (size_t)n;
   if (out->xyz) CR_CUDA(cudaMemcpyAsync(out->xyz, B.xyz, sizeof(float) * 3 * nn, cudaMemcpyDeviceToHost, s));

@@ -31,14 +31,15 @@ struct RebuildBufs {
 
 // the configuration read back in id order (crmc_state.cu); output arrays
 // that are null are not written
+constexpr int STATE_BLOCK_SORT_MAX = 16384;  // ions sorted inside one CTA; more: device-wide sort
 struct StateBufs {
   int n_input, cap;               // input ids are 0..n_input-1; ion list capacity
+  int lo_bits;                    // the low words of ion ids stay below 2^lo_bits
   int *present;                   // [n_input] slot + 1 of each input id, 0 absent
-  int *pre;                       // [n_input] output position of each input id present
   int *n_ions;                    // number of inserted ions found
-  unsigned long long *ion_key, *ion_key_alt;  // [cap] ion ids (sort double buffer)
+  unsigned long long *ion_key, *ion_key_alt;  // [cap] ion sort keys (the alternates for the device-wide sort)
   int *ion_val, *ion_val_alt;                 // [cap] their slots
-  void *sort_tmp;
+  void *sort_tmp;                 // device-wide sort scratch (capacities above STATE_BLOCK_SORT_MAX)
   size_t sort_tmp_bytes;
   const float4 *vel_src, *frc_src;  // velocities; forces (null: zeros)
   float *xyz, *vel, *frc;           // [3n]
@@ -79,11 +80,13 @@ cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs
                         cudaStream_t s);
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
 // state read-back: mark the slots (ion count into *B.n_ions), then, with the
-// counts known, place the input ids, sort the ions (bits [0, end_bit) of the
-// ids) and write the arrays (adds the kernels it launched to *launches)
+// counts known, place the input ids, sort the ions (bits [0, end_bit) of their
+// keys), write the arrays and clear the marks (adds the kernels it launched to
+// *launches); the device-wide sort needs state_sort_temp_bytes(cap) of scratch
+// (0 when every ion list fits the one-CTA sort)
 cudaError_t launch_state_mark(const SysParams &P, const StateBufs &B, cudaStream_t s);
-cudaError_t launch_state_emit(const SysParams &P, const StateBufs &B, int n_present, int n_ions, int end_bit,
-                              cudaStream_t s, int *launches);
+cudaError_t launch_state_order(const SysParams &P, const StateBufs &B, int n_present, int n_ions, int end_bit,
+                               cudaStream_t s, int *launches);
 size_t state_sort_temp_bytes(int cap);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                           uint4 *out, cudaStream_t s);

@@ -146,3 +146,19 @@ def test_load_errors_reported_at_the_next_check(crmc, fault):
     with pytest.raises(crmc.CrError) as e:
         h.check()
     assert crmc.ERRORS[e.value.code] == code
+
+
+def test_state_with_more_ions_than_one_cta_sorts(crmc):
+    """Past 16,384 inserted ions the ions are ordered by the device-wide radix
+    sort instead of the one-CTA sort: ghost ions at high salt (pI_S = 0.5) fill
+    an empty L = 120 box within three sweeps; the state still equals the
+    oracle's."""
+    import dataclasses
+    w = dataclasses.replace(W.ideal(n_sites=10, L=120.0, pIS=0.5, n_pairs=20, seed=3), capacity=48000)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    g.sweep(g.trials_per_sweep * 3, 11)
+    o.sweep(o.trials_per_sweep * 3, 11)
+    sg, _ = compare_states(g, o, w.n_sites)
+    assert int(np.sum(sg["id"] >= np.uint64(1 << 32))) > 16384
+    assert np.all(sg["id"][1:] > sg["id"][:-1])
