@@ -452,7 +452,7 @@ def run_ours(args):
     if not args.no_e2e and rank == 0:
         # every replica's configuration goes through pinned host buffers each
         # step (allocated once, as a caller coupling the library to its own
-        # host-side code would): cr_load uploads it, the batched cycle runs,
+        # host-side code would): cr_batch_load uploads it, the batched cycle runs,
         # cr_batch_state reads every new configuration back into the same buffers
         bufs = []
         for g in ctxs:
@@ -476,10 +476,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(e2e_steps):
-            for g, b, n in zip(ctxs, bufs, ns):
-                g.load(n, b["xyz"].data_ptr(), b["vel"].data_ptr(), b["type"].data_ptr(), b["cls"].data_ptr(),
-                       b["state"].data_ptr())
-                h2d += n * (12 + 12 + 4 + 4 + 1)
+            batch.load([dict(n=n, **{k: v for k, v in vw.items() if k in ("xyz", "vel", "type", "cls", "state")})
+                        for n, vw in zip(ns, views)])
+            h2d += sum(n * (12 + 12 + 4 + 4 + 1) for n in ns)
             batch.md_begin(dt, gamma, 9500 + s)
             batch.sweep(1, 9000 + s)
             batch.md_end(dt, gamma, 9500 + s)
@@ -489,7 +488,7 @@ def run_ours(args):
         te = time.perf_counter() - t0
         e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
-               "note": "per step: cr_load of the 13 replicas from pinned host buffers + the batched cycle (1e4 "
+               "note": "per step: cr_batch_load of the 13 replicas from pinned host buffers + the batched cycle (1e4 "
                        "trials per replica inside one MD step) + cr_batch_state readback of every replica into the "
                        "same pinned buffers"}
 

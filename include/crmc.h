@@ -354,6 +354,17 @@ int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint
 /* cr_md_begin / cr_md_end on every replica (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed);
 int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
+/* cr_load of every replica of the batch: args[0 .. n-1], one per context in
+ * the order given to cr_batch_create; the uploads and load kernels of the
+ * replicas run concurrently on the batch's streams.  Errors as cr_load's;
+ * returns the first. */
+typedef struct {
+  int32_t n;
+  const float *xyz, *vel;
+  const int32_t *type, *cls;
+  const int8_t *state;
+} cr_load_args;
+int cr_batch_load(cr_batch *b, const cr_load_args *args);
 /* cr_state of every replica of the batch into views[0 .. n-1] (one view per
  * context, in the order given to cr_batch_create); the replicas' reads run
  * concurrently on the batch's streams with two synchronisations in all.

@@ -60,6 +60,11 @@ class cr_state_view(C.Structure):
                 ("cls", C.c_void_p)]
 
 
+class cr_load_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("xyz", C.c_void_p), ("vel", C.c_void_p), ("type", C.c_void_p),
+                ("cls", C.c_void_p), ("state", C.c_void_p)]
+
+
 class cr_info(C.Structure):
     _fields_ = [("nc", C.c_int32), ("k", C.c_int32), ("h", C.c_int32), ("nd", C.c_int32), ("ncol", C.c_int32),
                 ("m", C.c_int32), ("cap", C.c_int32), ("global_", C.c_int32), ("trials_per_sweep", C.c_int64),
@@ -85,7 +90,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
-           "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state")
+           "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -146,6 +151,8 @@ def _lib():
         lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
         lib.cr_batch_state.restype = C.c_int
         lib.cr_batch_state.argtypes = [P, C.POINTER(cr_state_view)]
+        lib.cr_batch_load.restype = C.c_int
+        lib.cr_batch_load.argtypes = [P, C.POINTER(cr_load_args)]
         lib.cr_get_info.restype = C.c_int
         lib.cr_get_info.argtypes = [P, C.POINTER(cr_info)]
         lib.cr_set_stream.restype = C.c_int
@@ -432,6 +439,17 @@ class Batch:
 
     def md_begin(self, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_begin")
+
+    def load(self, loads):
+        """cr_batch_load: one dict per replica with n and the arrays xyz, vel,
+        type, cls, state (numpy arrays or raw pointers), as Context.load."""
+        args = (cr_load_args * len(self.contexts))()
+        conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
+        for r, a in enumerate(loads):
+            args[r].n = int(a["n"])
+            for k in ("xyz", "vel", "type", "cls", "state"):
+                setattr(args[r], k, conv(a.get(k)))
+        _chk(self._lib.cr_batch_load(self._h, args), "cr_batch_load")
 
     def state_into(self, arrays):
         """cr_batch_state: one dict of caller arrays (as Context.state_into

@@ -1428,6 +1428,14 @@ extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t se
   return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
 }
 
+extern "C" int cr_batch_load(cr_batch *b, const cr_load_args *args) {
+  if (!b || !args) return CR_ERR_INVALID_ARG;
+  return batch_md(b, [&](cr_ctx *c, uint64_t r) {
+    const cr_load_args &a = args[r];
+    return cr_load(c, a.n, a.xyz, a.vel, a.type, a.cls, a.state);
+  });
+}
+
 // cr_state of every replica: the halves of all replicas run on the
 // replicas' streams, two synchronisations in all
 extern "C" int cr_batch_state(cr_batch *b, cr_state_view *views) {

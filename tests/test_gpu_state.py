@@ -162,3 +162,26 @@ def test_state_with_more_ions_than_one_cta_sorts(crmc):
     sg, _ = compare_states(g, o, w.n_sites)
     assert int(np.sum(sg["id"] >= np.uint64(1 << 32))) > 16384
     assert np.all(sg["id"][1:] > sg["id"][:-1])
+
+
+def test_batch_load_equals_context_loads(crmc):
+    ws = [W.config2(seed=12, scale=0.5, pH=pH) for pH in (3.5, 6.5)]
+    src = [crmc.Context(w) for w in ws]
+    for r, g in enumerate(src):
+        g.sweep(g.trials_per_sweep * 2, 30 + r)
+    states = [g.state() for g in src]
+    single = [crmc.Context(w) for w in ws]
+    batched = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(batched)
+    loads = [dict(n=int(s["n"]), xyz=np.ascontiguousarray(s["xyz"]), vel=np.ascontiguousarray(s["vel"]),
+                  type=s["type"], cls=s["cls"], state=s["state"]) for s in states]
+    for g, a in zip(single, loads):
+        g.load(a["n"], a["xyz"], a["vel"], a["type"], a["cls"], a["state"])
+    b.load(loads)
+    for g1, g2 in zip(single, batched):
+        s1, s2 = g1.state(), g2.state()
+        for k in ("id", "xyz", "vel", "type", "state", "cls", "site_state"):
+            assert np.array_equal(s1[k], s2[k]), k
+    b.sweep(1, 7)
+    for g in batched:
+        g.check()
