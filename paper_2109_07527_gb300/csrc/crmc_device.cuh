@@ -135,6 +135,17 @@ __device__ __forceinline__ bool wca_change_d(const WcaEntry &w, int dp, float cx
   return true;
 }
 
+// int64 sum over the warp (mod 2^64, exact), result in every lane: v = a 2^42
+// + b 2^21 + c with b, c in [0, 2^21) and a in [-2^21, 2^21), each part
+// summed by one 32-bit warp reduction (partial sums below 2^26 in magnitude)
+__device__ __forceinline__ long long warp_sum_i64(long long v) {
+  const unsigned c = (unsigned)v & 0x1FFFFFu, b = (unsigned)(v >> 21) & 0x1FFFFFu;
+  const int a = (int)(v >> 42);
+  const unsigned sc = __reduce_add_sync(0xffffffffu, c), sb = __reduce_add_sync(0xffffffffu, b);
+  const int sa = (int)__reduce_add_sync(0xffffffffu, (unsigned)a);
+  return (long long)sa * (1ll << 42) + (long long)sb * (1ll << 21) + (long long)sc;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

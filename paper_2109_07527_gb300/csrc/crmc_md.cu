@@ -250,12 +250,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     const float4 pj = P.pos[g2];
     force_pair(P, pi.x, pi.y, pi.z, pi.w, clsi, pj.x, pj.y, pj.z, pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    fx += __shfl_xor_sync(0xffffffffu, fx, o);
-    fy += __shfl_xor_sync(0xffffffffu, fy, o);
-    fz += __shfl_xor_sync(0xffffffffu, fz, o);
-  }
+  fx = warp_sum_i64(fx);
+  fy = warp_sum_i64(fy);
+  fz = warp_sum_i64(fz);
   if (lane == 0) finish_particle(P, M, gi, pi, fx, fy, fz);
 }
 

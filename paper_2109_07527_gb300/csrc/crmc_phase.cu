@@ -491,21 +491,24 @@ __device__ __forceinline__ void cta_sync() {
 }
 
 // int64 sum over the warp, result in every lane
-__device__ __forceinline__ long long warp_allsum(long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
+__device__ __forceinline__ long long warp_allsum(long long v) { return warp_sum_i64(v); }
 
-// Random numbers of a chunk of trials (Philox purposes 0-3; thread i0 of a
-// group of `stride` threads takes every stride-th trial): the move and its
-// choices, both insertion points with their in-domain cell ranks, the
-// Metropolis uniform and, for delayed acceptance, the stage-2 uniform.
+// Random numbers of a chunk of trials (Philox purposes 0-3 and 6-7; thread i0
+// of a group of `stride` threads takes every stride-th task): the move and
+// its choices, both insertion points with their in-domain cell ranks, the
+// Metropolis uniform, for delayed acceptance the stage-2 uniform, and the
+// velocities of the ions an insertion would add.
 template <bool LOG, bool DA>
-__device__ __forceinline__ void draw_chunk(TrialPre *tp, int k0, int nchunk, int i0, int stride, int d, uint32_t phi,
-                                           const int *org, const int *off, const int *dd, int k, int nc, float af,
-                                           float Lf, float scf, uint32_t key0, uint32_t key1) {
-  for (int t = i0; t < nchunk; t += stride) {
+__device__ __forceinline__ void draw_chunk(TrialPre *tp, float4 *tvel, int k0, int nchunk, int i0, int stride, int d,
+                                           uint32_t phi, const int *org, const int *off, const int *dd, int k, int nc,
+                                           float af, float Lf, float scf, uint32_t key0, uint32_t key1) {
+  for (int u = i0; u < 3 * nchunk; u += stride) {
+    if (u >= nchunk) {  // the Maxwell-Boltzmann velocities an accepted insertion gives its ions (purposes 6, 7)
+      const int t = u % nchunk, which = u / nchunk - 1;
+      tvel[2 * t + which] = ion_velocity((uint32_t)(k0 + t), (uint32_t)d, phi, 6u + (uint32_t)which, key0, key1);
+      continue;
+    }
+    const int t = u;
     const uint32_t kk = (uint32_t)(k0 + t);
     const uint4 a = philox10(kk, (uint32_t)d, phi, 0u, key0, key1);
     const uint4 b = philox10(kk, (uint32_t)d, phi, 1u, key0, key1);
@@ -779,8 +782,7 @@ __device__ __forceinline__ bool insert_room(const SysParams &P, const DomList &L
 // inserted (after every entry of its cell, as new ids are the largest) or
 // deleted in the list, the kind counts.  Returns the new list size.
 __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L, int *misc, const TrialCtl &C,
-                                            const TrialPre &q, int n, int belowA, int sameA, int kk, int d,
-                                            uint32_t phi, uint32_t key0, uint32_t key1) {
+                                            const TrialPre &q, const float4 *vel, int n, int belowA, int sameA) {
   const int lane = threadIdx.x & 31;
   const int r = C.move >> 1;
   const bool fwd = (C.move & 1) == 0;
@@ -797,7 +799,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
       warp_insert_gap(L, n, p);
       if (lane == 0) {
         L.pos[p] = make_float4(q.ax, q.ay, q.az, -qs * P.ion_q);
-        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
+        L.vel[p] = vel[0];
         L.id[p] = C.newid;
         L.lnk[p] = 0;
         L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
@@ -821,7 +823,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
       warp_insert_gap(L, n, p);
       if (lane == 0) {
         L.pos[p] = make_float4(q.ax, q.ay, q.az, P.ion_q);
-        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 6u, key0, key1);
+        L.vel[p] = vel[0];
         L.id[p] = C.newid;
         L.lnk[p] = 0;
         L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
@@ -835,7 +837,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
       warp_insert_gap(L, n, p);
       if (lane == 0) {
         L.pos[p] = make_float4(q.bx, q.by, q.bz, -P.ion_q);
-        L.vel[p] = ion_velocity((uint32_t)kk, (uint32_t)d, phi, 7u, key0, key1);
+        L.vel[p] = vel[1];
         L.id[p] = C.newid + 1u;
         L.lnk[p] = 0;
         L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
@@ -893,6 +895,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   float4 *hpos = (float4 *)take(sizeof(float4) * S.hcs);  // halo (R == 0): x, y, z, q + 8 cls
   long long *lntab_s = (long long *)take(sizeof(long long) * S.lns);
   TrialPre *tp = (TrialPre *)take(sizeof(TrialPre) * TRIAL_CHUNK);
+  float4 *tvel = (float4 *)take(sizeof(float4) * 2 * TRIAL_CHUNK);  // velocities of inserted ions
   TrialCtl *ctl = (TrialCtl *)take(sizeof(TrialCtl));
   long long *red = (long long *)take(sizeof(long long) * MAX_WARPS);
   unsigned long long *reds = (unsigned long long *)take(sizeof(unsigned long long) * MAX_WARPS);
@@ -1072,7 +1075,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   for (int k0 = 0; k0 < m; k0 += TRIAL_CHUNK) {
     const int nchunk = min(TRIAL_CHUNK, m - k0);
     // ---- random numbers of the chunk
-    draw_chunk<LOG, DA>(tp, k0, nchunk, tid, T, d, phi, org, off, dd, k, nc, P.af, P.Lf, P.scf, key0, key1);
+    draw_chunk<LOG, DA>(tp, tvel, k0, nchunk, tid, T, d, phi, org, off, dd, k, nc, P.af, P.Lf, P.scf, key0, key1);
     __syncthreads();
 
     for (int t = 0; t < nchunk; ++t) {
@@ -1251,7 +1254,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               }
             }
           }
-          n = commit_trial(P, L, misc, *ctl, q, n, belowA, sameA, kk, d, phi, key0, key1);
+          n = commit_trial(P, L, misc, *ctl, q, tvel + 2 * t, n, belowA, sameA);
         }
         if (lane == 0) {
           misc[0] = n;
@@ -1384,6 +1387,7 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
                           sizeof(float4) * S.hcs,
                           sizeof(long long) * S.lns,
                           sizeof(TrialPre) * TRIAL_CHUNK,
+                          sizeof(float4) * 2 * TRIAL_CHUNK,
                           sizeof(TrialCtl),
                           sizeof(long long) * MAX_WARPS,
                           sizeof(unsigned long long) * MAX_WARPS,
