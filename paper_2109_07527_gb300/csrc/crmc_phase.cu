@@ -411,6 +411,15 @@ __device__ __noinline__ void near_pair(const PairK &K, const WcaEntry &w, const 
   }
 }
 
+// Flat frame of a region that spans less than half the box: along an axis
+// whose region wraps around the periodic boundary (bit i of strad), a
+// coordinate x >= L/2 becomes x - L (exact: L/2 <= x < L).  Between two points
+// of the region the plain difference in this frame then equals the
+// minimum-image difference bit for bit, whichever of the two had been shifted.
+__device__ __forceinline__ float frame_x(float x, int strad, int axis, float halfL, float L) {
+  return ((strad >> axis) & 1) && x >= halfL ? x - L : x;
+}
+
 // every full 32 queued Coulomb pairs of the warp are evaluated with all lanes
 // busy; the rest (fewer than 32) stays queued
 template <bool WITH_S>
@@ -449,20 +458,37 @@ __device__ __forceinline__ void queue_flush(const PairK &K, float *qr2, float *q
 // particle are evaluated at once, the in-range Coulomb pairs of A and B join
 // the warp's queue with one compaction step, and every full 32 queued pairs
 // are evaluated with all lanes busy.
-template <bool WITH_S>
+// FLAT: the candidate's coordinates and As, Bs (those of A and B) are in the
+// region's flat frame (below), where plain differences are the minimum-image
+// ones; the raw coordinates, for the FP64 WCA of a near pair, come back
+// exactly as x + L for a shifted (negative) x.
+template <bool WITH_S, bool FLAT = false>
 __device__ __forceinline__ void offer2(const PairK &K, const WcaEntry *wca, const Desc &A, const Desc &B,
                                        const float4 wrA, const float4 wrB, bool valid, float xj, float yj, float zj,
                                        float qj, int jcls, float *qr2, float *qqp, int &qn, long long &acc,
-                                       unsigned long long &sacc, int &ov) {
+                                       unsigned long long &sacc, int &ov, const float3 As = float3{},
+                                       const float3 Bs = float3{}) {
   const int lane = threadIdx.x & 31;
-  const float ax = wrap_diff(xj, A.x, K.Lf, K.halfL), ay = wrap_diff(yj, A.y, K.Lf, K.halfL),
-              az = wrap_diff(zj, A.z, K.Lf, K.halfL);
-  const float bx = wrap_diff(xj, B.x, K.Lf, K.halfL), by = wrap_diff(yj, B.y, K.Lf, K.halfL),
-              bz = wrap_diff(zj, B.z, K.Lf, K.halfL);
+  float ax, ay, az, bx, by, bz;
+  if (FLAT) {
+    ax = xj - As.x; ay = yj - As.y; az = zj - As.z;
+    bx = xj - Bs.x; by = yj - Bs.y; bz = zj - Bs.z;
+  } else {
+    ax = wrap_diff(xj, A.x, K.Lf, K.halfL); ay = wrap_diff(yj, A.y, K.Lf, K.halfL); az = wrap_diff(zj, A.z, K.Lf, K.halfL);
+    bx = wrap_diff(xj, B.x, K.Lf, K.halfL); by = wrap_diff(yj, B.y, K.Lf, K.halfL); bz = wrap_diff(zj, B.z, K.Lf, K.halfL);
+  }
   const float rA = ax * ax + ay * ay + az * az, rB = bx * bx + by * by + bz * bz;
   const bool nearA = valid && rA < sel4(wrA, jcls), nearB = valid && rB < sel4(wrB, jcls);
-  if (nearA) near_pair<WITH_S>(K, wca[A.cls * 4 + jcls], A, xj, yj, zj, qj, rA, acc, sacc, ov);
-  if (nearB) near_pair<WITH_S>(K, wca[B.cls * 4 + jcls], B, xj, yj, zj, qj, rB, acc, sacc, ov);
+  if (nearA || nearB) {
+    float xr = xj, yr = yj, zr = zj;
+    if (FLAT) {
+      xr = xj < 0.0f ? xj + K.Lf : xj;
+      yr = yj < 0.0f ? yj + K.Lf : yj;
+      zr = zj < 0.0f ? zj + K.Lf : zj;
+    }
+    if (nearA) near_pair<WITH_S>(K, wca[A.cls * 4 + jcls], A, xr, yr, zr, qj, rA, acc, sacc, ov);
+    if (nearB) near_pair<WITH_S>(K, wca[B.cls * 4 + jcls], B, xr, yr, zr, qj, rB, acc, sacc, ov);
+  }
   const bool inA = valid && !nearA && rA < K.rc2 && A.dqlB != 0.0f && qj != 0.0f;
   const bool inB = valid && !nearB && rB < K.rc2 && B.dqlB != 0.0f && qj != 0.0f;
   const unsigned mA = __ballot_sync(FULL, inA), mB = __ballot_sync(FULL, inB);
@@ -710,28 +736,54 @@ __device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca,
                                             const Desc &A, const Desc &B, const float4 (&hreg)[RR], int nmine,
                                             const float4 *hpos, int NH, int hcap, const int *hpre, const int *hcell,
                                             int NR, int n, int i0, int stride, float *qr2, float *qqp, long long &acc,
-                                            unsigned long long &sacc, int &ov) {
+                                            unsigned long long &sacc, int &ov, bool flat, int strad) {
   const int lane = threadIdx.x & 31;
   const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
   int qn = 0;
+  // the on-chip halo is stored in the flat frame when the region allows it
+  const float3 As = make_float3(frame_x(A.x, strad, 0, K.halfL, K.Lf), frame_x(A.y, strad, 1, K.halfL, K.Lf),
+                                frame_x(A.z, strad, 2, K.halfL, K.Lf));
+  const float3 Bs = make_float3(frame_x(B.x, strad, 0, K.halfL, K.Lf), frame_x(B.y, strad, 1, K.halfL, K.Lf),
+                                frame_x(B.z, strad, 2, K.halfL, K.Lf));
   if (R > 0) {
+    if (flat) {
 #pragma unroll
-    for (int r = 0; r < RR; ++r) {
-      const float4 p = hreg[r];
-      const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-      const float q = p.w - 8.0f * (float)cls;
-      const bool v = r < nmine;
-      offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+      for (int r = 0; r < RR; ++r) {
+        const float4 p = hreg[r];
+        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+        const float q = p.w - 8.0f * (float)cls;
+        offer2<LOG, true>(K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov,
+                          As, Bs);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const float4 p = hreg[r];
+        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+        const float q = p.w - 8.0f * (float)cls;
+        offer2<LOG>(K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+      }
     }
   } else {
     const int lim = min(NH, hcap);
-    for (int base = 0; base < lim; base += stride) {
-      const int j = base + i0;
-      const bool v = j < lim;
-      const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-      const float q = p.w - 8.0f * (float)cls;
-      offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+    if (flat) {
+      for (int base = 0; base < lim; base += stride) {
+        const int j = base + i0;
+        const bool v = j < lim;
+        const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+        const float q = p.w - 8.0f * (float)cls;
+        offer2<LOG, true>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov, As, Bs);
+      }
+    } else {
+      for (int base = 0; base < lim; base += stride) {
+        const int j = base + i0;
+        const bool v = j < lim;
+        const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+        const float q = p.w - 8.0f * (float)cls;
+        offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+      }
     }
   }
   // halo beyond what is held on chip (dense regions): straight from global memory
@@ -1020,6 +1072,13 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
     L.rank[j] = r;
     atomicAdd(&misc[1 + min(kind_of(info), 6)], 1);
   }
+  // flat frame (frame_x): a region spanning less than half the box along
+  // every axis is compared without minimum-image tests; strad marks the
+  // axes along which it wraps around the periodic boundary
+  const bool flat = !P.global && 2.5f * (float)nr * P.af < P.Lf;
+  int strad = 0;
+  if (flat)
+    for (int i = 0; i < 3; ++i) strad |= (org[i] < h || org[i] + k + h > nc) ? 1 << i : 0;
   // halo particles (they do not change during the phase): w = q + 8 * cls
   constexpr int RR = R > 0 ? R : 1;
   float4 hreg[RR];
@@ -1034,7 +1093,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         const int i = upper_idx(hpre, NR, j);
         const int g = hcell[i] * P.cap + (j - hpre[i]);
         const float4 p = P.pos[g];
-        hreg[r] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
+        hreg[r] = make_float4(frame_x(p.x, strad, 0, P.halfL, P.Lf), frame_x(p.y, strad, 1, P.halfL, P.Lf),
+                              frame_x(p.z, strad, 2, P.halfL, P.Lf),
+                              p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
         nmine = r + 1;
       }
     }
@@ -1043,7 +1104,9 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       const int i = upper_idx(hpre, NR, j);
       const int g = hcell[i] * P.cap + (j - hpre[i]);
       const float4 p = P.pos[g];
-      hpos[j] = make_float4(p.x, p.y, p.z, p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
+      hpos[j] = make_float4(frame_x(p.x, strad, 0, P.halfL, P.Lf), frame_x(p.y, strad, 1, P.halfL, P.Lf),
+                            frame_x(p.z, strad, 2, P.halfL, P.Lf),
+                            p.w + 8.0f * (float)((P.info[g] >> INFO_CLS_SHIFT) & 3));
     }
   }
   if (DA) {  // region cell aggregates at the start of the phase
@@ -1176,7 +1239,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       if (nch) {
         const Desc A = ctl->c[0], B = ctl->c[1];
         sweep_pairs<LOG, R, RR>(K, wca, P, L, A, B, hreg, nmine, hpos, NH, hcap, hpre, hcell, NR, misc[0], tid, T,
-                                qr2, qqp, acc, sacc, ov);
+                                qr2, qqp, acc, sacc, ov, flat, strad);
         if (tid == cc_thread) cc_change<LOG>(K, wca, *ctl, acc, sacc, ov);
         acc = warp_allsum(acc);
         if (LOG) sacc = (unsigned long long)warp_allsum((long long)sacc);
