@@ -306,3 +306,18 @@ def test_parity_with_lists_and_halos_beyond_shared_memory(crmc, list_capacity, h
     the global scratch region and halo particles read from global memory."""
     w = W.config2(seed=3, scale=0.5)
     _parity(crmc, w, 2, 31, list_capacity=list_capacity, halo_capacity=halo_capacity)
+
+
+@pytest.mark.parametrize("threads,regs", [(64, 0), (128, 4), (512, 1)])
+def test_flat_frame_full_box_launch_shapes(crmc, threads, regs):
+    """In the full-size box (L = 120, regions of 36 sigma) the halo is compared
+    in the region's flat frame, held in shared memory or in registers; regions
+    that wrap around the periodic boundary along one to three axes occur every
+    sweep.  The chain equals the oracle's trial by trial."""
+    w = W.config2(seed=11)
+    g = crmc.Context(w)
+    g.set_launch_shape(threads, regs)
+    n = g.trials_per_sweep
+    lg = g.sweep(n, 13, log=True)["log"]
+    o, lo, ties = compare_logs(w, lg, n, 13)
+    compare_states(g, o, w.n_sites)
