@@ -61,6 +61,7 @@ struct cr_ctx {
   long long *d_gs_lnk = nullptr;
   int *d_gs_info = nullptr, *d_gs_rank = nullptr;
   int *d_plist = nullptr, *d_nparts = nullptr;  // MD particle list
+  long long *d_fsum = nullptr;                    // MD pair-force sums per listed particle
   int *d_order = nullptr;                       // launch order of the domains of each colour
   // delayed acceptance: surrogate on the device, records, its own launch-shape tuner
   uint16_t *d_mlp_w = nullptr;
@@ -181,7 +182,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
-                  c->d_plist, c->d_nparts, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
+                  c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_small) cudaFreeHost(c->h_small);
@@ -608,6 +609,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_reps, 1);
   ALLOC(c->d_plist, (size_t)std::max(sys->capacity, 1));
   ALLOC(c->d_nparts, 1);
+  ALLOC(c->d_fsum, 3 * (size_t)std::max(sys->capacity, 1));
 #undef ALLOC
   {
     if (cudaHostAlloc((void **)&c->h_small, 16 * sizeof(long long), 0) != cudaSuccess) {
@@ -947,9 +949,11 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
 static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
   int ti;
   tbegin(ctx, 1, &ti);
-  CR_CUDA(launch_md_forces(ctx->P, M, ctx->d_plist, ctx->d_nparts, (int)ctx->capacity, ctx->stream));
+  MdParams Q = M;
+  Q.fsum = ctx->d_fsum;
+  CR_CUDA(launch_md_forces(ctx->P, Q, ctx->d_plist, ctx->d_nparts, (int)ctx->capacity, ctx->stream));
   tend(ctx, 1, ti);
-  ctx->launches_total += 2;
+  ctx->launches_total += 3;  // particle list, pair forces, per-particle finish
   return CR_OK;
 }
 

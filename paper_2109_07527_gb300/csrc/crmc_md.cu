@@ -136,7 +136,9 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
 // tests its candidate (cheap), in-range partners are queued and their forces
 // evaluated with all lanes busy.  Pair forces are FP32 terms summed in 2^-24
 // fixed point, so the result does not depend on the order.
-template <int NBC>  // 2h+1 when the box has at least that many cells per dimension, 0 otherwise
+// SPLIT: the warp stores its particle's pair-force sums for k_md_finish (one
+// thread per particle) instead of finishing it on lane 0 while 31 lanes idle.
+template <int NBC, bool SPLIT>  // NBC: 2h+1 when the box has at least that many cells per dimension, else 0
 __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams M) {
   __shared__ int queue[MD_NW][MD_QCAP];
   __shared__ int cpre[MD_NW][MD_CPL * 32 + 1];  // exclusive prefix of the stencil cells' counts
@@ -253,7 +255,20 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   fx = warp_sum_i64(fx);
   fy = warp_sum_i64(fy);
   fz = warp_sum_i64(fz);
-  if (lane == 0) finish_particle(P, M, gi, pi, fx, fy, fz);
+  if (SPLIT) {
+    if (lane < 3) M.fsum[3 * w + lane] = lane == 0 ? fx : (lane == 1 ? fy : fz);
+  } else if (lane == 0) {
+    finish_particle(P, M, gi, pi, fx, fy, fz);
+  }
+}
+
+// FENE bonds, Langevin and the store of every particle's force (and the
+// half kick), one thread per particle, after k_md_forces<., true>
+__global__ void k_md_finish(SysParams P, MdParams M) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= *M.n_particles || w >= M.max_particles) return;
+  const int gi = M.plist[w];
+  finish_particle(P, M, gi, P.pos[gi], M.fsum[3 * w], M.fsum[3 * w + 1], M.fsum[3 * w + 2]);
 }
 
 // v += dt/2 f; x += dt v; wrap into [0, L)
@@ -408,9 +423,16 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
   Q.n_particles = n_particles;
   Q.max_particles = max_particles;
   const unsigned grid = (unsigned)((max_particles + MD_NW - 1) / MD_NW);
-  if (P.h == 2 && P.nc >= 5) k_md_forces<5><<<grid, MD_THREADS, 0, s>>>(P, Q);
-  else if (P.h == 1 && P.nc >= 3) k_md_forces<3><<<grid, MD_THREADS, 0, s>>>(P, Q);
-  else k_md_forces<0><<<grid, MD_THREADS, 0, s>>>(P, Q);
+  if (Q.fsum) {
+    if (P.h == 2 && P.nc >= 5) k_md_forces<5, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    else if (P.h == 1 && P.nc >= 3) k_md_forces<3, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    else k_md_forces<0, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    k_md_finish<<<(unsigned)((max_particles + 255) / 256), 256, 0, s>>>(P, Q);
+  } else {
+    if (P.h == 2 && P.nc >= 5) k_md_forces<5, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    else if (P.h == 1 && P.nc >= 3) k_md_forces<3, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    else k_md_forces<0, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
+  }
   return cudaGetLastError();
 }
 
