@@ -18,12 +18,15 @@ namespace crmc {
 // ---------------------------------------------------------------------------
 constexpr float FFIX_INV = 1.0f / 16777216.0f;
 
+// FLAT: i and j are given in the stencil's flat frame (md_frame), where the
+// plain difference is the minimum-image one bit for bit
+template <bool FLAT = false>
 __device__ __forceinline__ void force_pair(const SysParams &P, float xi, float yi, float zi, float qi, int ci,
                                            float xj, float yj, float zj, float qj, int cj, long long &fx,
                                            long long &fy, long long &fz) {
-  const float dx = wrap_diff(xi, xj, P.Lf, P.halfL);
-  const float dy = wrap_diff(yi, yj, P.Lf, P.halfL);
-  const float dz = wrap_diff(zi, zj, P.Lf, P.halfL);
+  const float dx = FLAT ? xi - xj : wrap_diff(xi, xj, P.Lf, P.halfL);
+  const float dy = FLAT ? yi - yj : wrap_diff(yi, yj, P.Lf, P.halfL);
+  const float dz = FLAT ? zi - zj : wrap_diff(zi, zj, P.Lf, P.halfL);
   const float r2 = dx * dx + dy * dy + dz * dz;
   const WcaEntry &w = P.wca[ci * 4 + cj];
   const bool coul = r2 < P.rc2 && qi != 0.0f && qj != 0.0f;
@@ -109,6 +112,12 @@ constexpr int MD_CPL = 4;  // stencil cells per lane (125 cells of a 5^3 stencil
 
 __device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
 
+// Flat frame of a stencil narrower than 0.4 L: along an axis where the
+// stencil wraps around the periodic boundary (s), x >= L/2 becomes x - L
+// (exact for L/2 <= x < L); plain differences between points of the stencil
+// then equal the minimum-image ones bit for bit.
+__device__ __forceinline__ float md_frame(float x, bool s, float halfL, float L) { return s && x >= halfL ? x - L : x; }
+
 // compact list of occupied slots; one atomic per warp of 32 cells
 __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
@@ -138,7 +147,9 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
 // fixed point, so the result does not depend on the order.
 // SPLIT: the warp stores its particle's pair-force sums for k_md_finish (one
 // thread per particle) instead of finishing it on lane 0 while 31 lanes idle.
-template <int NBC, bool SPLIT>  // NBC: 2h+1 when the box has at least that many cells per dimension, else 0
+// FLAT (with NBC > 0): the stencil spans less than 0.4 L, distances are taken
+// in its flat frame (md_frame) without minimum-image tests.
+template <int NBC, bool SPLIT, bool FLAT = false>  // NBC: 2h+1 when the box has at least that many cells per dimension, else 0
 __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams M) {
   __shared__ int queue[MD_NW][MD_QCAP];
   __shared__ int cpre[MD_NW][MD_CPL * 32 + 1];  // exclusive prefix of the stencil cells' counts
@@ -157,6 +168,10 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   const int nb = NBC > 0 ? NBC : min(2 * h + 1, nc);
   const bool all = NBC == 0 && nb == nc;  // every cell of the dimension, once
   const int nb3 = nb * nb * nb;
+  const bool sx = FLAT && (cx < h || cx + h >= nc), sy = FLAT && (cy < h || cy + h >= nc),
+             sz = FLAT && (cz < h || cz + h >= nc);
+  const float xi = FLAT ? md_frame(pi.x, sx, P.halfL, P.Lf) : pi.x, yi = FLAT ? md_frame(pi.y, sy, P.halfL, P.Lf) : pi.y,
+              zi = FLAT ? md_frame(pi.z, sz, P.halfL, P.Lf) : pi.z;
   // stencil cell o = lane + 32 t: its first slot and count; the candidates of
   // all cells are then numbered consecutively (exclusive prefix over o)
   int run = 0;
@@ -220,9 +235,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
       if (gj != gi) {
         const float4 pj = P.pos[gj];
         const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
-        const float dx = wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
-        const float dy = wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
-        const float dz = wrap_diff(pi.z, pj.z, P.Lf, P.halfL);
+        const float dx = FLAT ? xi - md_frame(pj.x, sx, P.halfL, P.Lf) : wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
+        const float dy = FLAT ? yi - md_frame(pj.y, sy, P.halfL, P.Lf) : wrap_diff(pi.y, pj.y, P.Lf, P.halfL);
+        const float dz = FLAT ? zi - md_frame(pj.z, sz, P.halfL, P.Lf) : wrap_diff(pi.z, pj.z, P.Lf, P.halfL);
         const float r2 = dx * dx + dy * dy + dz * dz;
         const WcaEntry &wc = P.wca[clsi * 4 + cj];
         in = (r2 < P.rc2 && pi.w != 0.0f && pj.w != 0.0f) || (wc.on && r2 < wc.wcut2);
@@ -235,8 +250,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
       __syncwarp();
       const int g2 = q[lane];
       const float4 pj = P.pos[g2];
-      force_pair(P, pi.x, pi.y, pi.z, pi.w, clsi, pj.x, pj.y, pj.z, pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy,
-                 fz);
+      force_pair<FLAT>(P, xi, yi, zi, pi.w, clsi, FLAT ? md_frame(pj.x, sx, P.halfL, P.Lf) : pj.x,
+                       FLAT ? md_frame(pj.y, sy, P.halfL, P.Lf) : pj.y, FLAT ? md_frame(pj.z, sz, P.halfL, P.Lf) : pj.z,
+                       pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
       const int rest = qn - 32;
       int keep = 0;
       if (lane < rest) keep = q[32 + lane];
@@ -250,7 +266,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   if (lane < qn) {
     const int g2 = q[lane];
     const float4 pj = P.pos[g2];
-    force_pair(P, pi.x, pi.y, pi.z, pi.w, clsi, pj.x, pj.y, pj.z, pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
+    force_pair<FLAT>(P, xi, yi, zi, pi.w, clsi, FLAT ? md_frame(pj.x, sx, P.halfL, P.Lf) : pj.x,
+                     FLAT ? md_frame(pj.y, sy, P.halfL, P.Lf) : pj.y, FLAT ? md_frame(pj.z, sz, P.halfL, P.Lf) : pj.z,
+                     pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
   }
   fx = warp_sum_i64(fx);
   fy = warp_sum_i64(fy);
@@ -423,7 +441,11 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
   Q.n_particles = n_particles;
   Q.max_particles = max_particles;
   const unsigned grid = (unsigned)((max_particles + MD_NW - 1) / MD_NW);
-  if (Q.fsum) {
+  const bool flat = 2.5f * (float)(2 * P.h + 1) * P.af < P.Lf;  // stencil narrower than 0.4 L
+  if (Q.fsum && flat && P.h == 2 && P.nc >= 5) {
+    k_md_forces<5, true, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
+    k_md_finish<<<(unsigned)((max_particles + 255) / 256), 256, 0, s>>>(P, Q);
+  } else if (Q.fsum) {
     if (P.h == 2 && P.nc >= 5) k_md_forces<5, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
     else if (P.h == 1 && P.nc >= 3) k_md_forces<3, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
     else k_md_forces<0, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
