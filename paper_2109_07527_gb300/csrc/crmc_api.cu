@@ -978,9 +978,8 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
   }
   for (int st = 0; st < n_steps; ++st) {
     MdParams M = md_params(ctx, 2, dt, gamma, seed);
-    CR_CUDA(launch_kick_drift(P, M, s));
-    CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
-    ctx->launches_total += 3;
+    CR_CUDA(launch_kick_drift_rebuild(P, M, B, ctx->d_perm, ctx->n_input, s));
+    ctx->launches_total += 2;
     if ((rc = md_force_eval(ctx, M)) != CR_OK) return rc;
     ctx->md_eval++;
   }
@@ -999,9 +998,8 @@ extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) 
     ctx->md_eval++;
   }
   MdParams M = md_params(ctx, 2, dt, gamma, seed);
-  CR_CUDA(launch_kick_drift(P, M, s));
-  CR_CUDA(launch_rebuild(P, B, ctx->d_perm, ctx->n_input, s));
-  ctx->launches_total += 3;
+  CR_CUDA(launch_kick_drift_rebuild(P, M, B, ctx->d_perm, ctx->n_input, s));
+  ctx->launches_total += 2;
   ctx->f_valid = false;  // positions moved: the closing kick needs new forces
   ctx->fcons_valid = false;
   return CR_OK;

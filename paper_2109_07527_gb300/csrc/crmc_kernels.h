@@ -76,8 +76,10 @@ cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, in
 // ints), then the force kernel (one warp per particle)
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,
                              cudaStream_t s);
-cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s);
-cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s);
+// half kick, drift and wrap fused with the scatter into the new cells, then
+// the per-cell id sort back into the primary arrays
+cudaError_t launch_kick_drift_rebuild(const SysParams &P, const MdParams &M, const RebuildBufs &B, int *perm_slot,
+                                      int n_perm, cudaStream_t s);
 cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
                         cudaStream_t s);
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);

@@ -289,8 +289,9 @@ __global__ void k_md_finish(SysParams P, MdParams M) {
   finish_particle(P, M, gi, P.pos[gi], M.fsum[3 * w], M.fsum[3 * w + 1], M.fsum[3 * w + 2]);
 }
 
-// v += dt/2 f; x += dt v; wrap into [0, L)
-__global__ void k_md_kick_drift(SysParams P, MdParams M) {
+// v += dt/2 f; x += dt v; wrap into [0, L); the particle goes straight into
+// its new cell of the scratch arrays (unordered; k_rebuild_sort orders them)
+__global__ void k_md_kick_drift_scatter(SysParams P, MdParams M, RebuildBufs B) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= P.ncell * P.cap) return;
   const int c = g / P.cap;
@@ -300,40 +301,29 @@ __global__ void k_md_kick_drift(SysParams P, MdParams M) {
   v.x += 0.5f * M.dt * f.x;
   v.y += 0.5f * M.dt * f.y;
   v.z += 0.5f * M.dt * f.z;
-  M.vel[g] = v;
-  float4 p = P.pos[g];
+  const float4 p = P.pos[g];
   float x[3] = {p.x + M.dt * v.x, p.y + M.dt * v.y, p.z + M.dt * v.z};
   for (int i = 0; i < 3; ++i) {
     x[i] -= P.Lf * floorf(x[i] * P.invL);
     if (x[i] >= P.Lf) x[i] -= P.Lf;
     if (x[i] < 0.0f) x[i] = 0.0f;
   }
-  P.pos[g] = make_float4(x[0], x[1], x[2], p.w);
-}
-
-// rebuild, step 1: scatter every particle into its new cell (unordered)
-__global__ void k_rebuild_scatter(SysParams P, RebuildBufs B) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.ncell * P.cap) return;
-  const int c = g / P.cap;
-  if (g - c * P.cap >= P.cnt[c]) return;
-  const float4 p = P.pos[g];
   const int nc = P.nc;
-  const int cell = cell_of(p.x, P.scf, nc) + nc * (cell_of(p.y, P.scf, nc) + nc * cell_of(p.z, P.scf, nc));
+  const int cell = cell_of(x[0], P.scf, nc) + nc * (cell_of(x[1], P.scf, nc) + nc * cell_of(x[2], P.scf, nc));
   const int s = atomicAdd(&B.cnt[cell], 1);
   if (s >= P.cap) {
     atomicOr(P.err, ERRB_CELL_OVERFLOW);
     return;
   }
   const int o = cell * P.cap + s;
-  B.pos[o] = p;
+  B.pos[o] = make_float4(x[0], x[1], x[2], p.w);
   B.pid[o] = P.pid[g];
   B.info[o] = P.info[g];
-  B.vel[o] = B.vel_src[g];
-  B.frc[o] = B.frc_src[g];
+  B.vel[o] = v;
+  B.frc[o] = f;
 }
 
-// rebuild, step 2: one warp per cell sorts the cell by id into the primary arrays
+// rebuild: one warp per cell sorts the cell by id into the primary arrays
 __global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n_perm) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= P.ncell) return;
@@ -458,15 +448,10 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_kick_drift(const SysParams &P, const MdParams &M, cudaStream_t s) {
+cudaError_t launch_kick_drift_rebuild(const SysParams &P, const MdParams &M, const RebuildBufs &B, int *perm_slot,
+                                      int n_perm, cudaStream_t s) {
   const int n = P.ncell * P.cap;
-  k_md_kick_drift<<<(n + 255) / 256, 256, 0, s>>>(P, M);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_rebuild(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm, cudaStream_t s) {
-  const int n = P.ncell * P.cap;
-  k_rebuild_scatter<<<(n + 255) / 256, 256, 0, s>>>(P, B);
+  k_md_kick_drift_scatter<<<(n + 255) / 256, 256, 0, s>>>(P, M, B);
   k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
   return cudaGetLastError();
 }
