@@ -170,11 +170,29 @@ def cpu_baseline(w, sample_sweeps=20):
     for s in range(sample_sweeps):
         o.sweep(o.trials_per_sweep, 1000 + s)
         n += o.trials_per_sweep
+    co = o.counts()
+    alpha_o = co["n_Am"] / co["n_A"] if co["n_A"] > 0 else 0.0  # degree of ionisation of the acid sites
     o.md_step(1, 0.005, 1.0, 5)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "trials/s", "cores": 1, "kind": "oracle",
             "sample": f"{sample_sweeps} sweeps x {o.trials_per_sweep} trials (1 trial per domain) + 1 MD step "
-                      f"of the same workload, {dt:.1f} s on 1 host thread"}
+                      f"of the same workload, {dt:.1f} s on 1 host thread"}, alpha_o
+
+
+def alpha_check(crmc, w, alpha_o, sample_sweeps=20):
+    """The metric's accuracy condition on the same sample: the GPU path runs
+    the oracle's sweeps (same seeds, same workload) and its degree of
+    ionisation must be within 0.005 of the oracle's (the chains are the same
+    trial by trial, so the difference is 0 unless a decision fell within the
+    tie band)."""
+    g = crmc.Context(w, trials_per_domain=1)
+    for s in range(sample_sweeps):
+        g.sweep(g.trials_per_sweep, 1000 + s)
+    a = g.counts()["alpha"]
+    g.close()
+    return {"sample": f"pH {w.params['pH']} replica, {sample_sweeps} sweeps x 1000 trials, GPU vs oracle",
+            "alpha_gpu": a, "alpha_oracle": alpha_o, "abs_diff": abs(a - alpha_o), "bound": 0.005,
+            "within": abs(a - alpha_o) <= 0.005}
 
 
 def run_reference(args):
@@ -509,7 +527,8 @@ def run_ours(args):
            "surrogate_da": da,
            "md_cr_cycles_per_s": args.steps * world / (ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(workload(0))
+        out["cpu_baseline"], alpha_o = cpu_baseline(workload(0))
+        out["alpha_check"] = alpha_check(crmc, workload(0), alpha_o)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
