@@ -464,51 +464,46 @@ def run_ours(args):
         da = run_da(crmc, torch, stream, flush, ws, dt, gamma, max(10, min(args.steps, 50)))
 
     # ---- end to end through the public API with host buffers: each step
-    # uploads every replica's configuration from pinned host memory (cr_load),
-    # runs the batched cycle and reads every replica's state back (cr_state)
+    # uploads every replica's configuration from pinned host memory, runs the
+    # batched cycle and reads every replica's state back
     e2e = None
     if not args.no_e2e and rank == 0:
-        # every replica's configuration goes through pinned host buffers each
-        # step (allocated once, as a caller coupling the library to its own
-        # host-side code would): cr_batch_load uploads it, the batched cycle runs,
-        # cr_batch_state reads every new configuration back into the same buffers
-        bufs = []
-        for g in ctxs:
-            cap = g.capacity
-            b = dict(xyz=torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
-                     vel=torch.empty((cap, 3), dtype=torch.float32).pin_memory(),
-                     id=torch.empty(cap, dtype=torch.int64).pin_memory(),
-                     type=torch.empty(cap, dtype=torch.int32).pin_memory(),
-                     state=torch.empty(cap, dtype=torch.int8).pin_memory(),
-                     cls=torch.empty(cap, dtype=torch.int32).pin_memory())
-            bufs.append(b)
-
-        views = [{k: v.data_ptr() for k, v in b.items()} for b in bufs]
-
-        def read_back():
-            return [int(c["n"]) for c in batch.state_into(views)]
-
-        ns = read_back()
+        # the replicas' configurations live in packed pinned host arrays
+        # (replica r from r * stride; allocated once, as a caller coupling the
+        # library to its own host-side code would): cr_batch_load_packed
+        # uploads them, the batched cycle runs, cr_batch_state_packed reads
+        # every new configuration back into the same arrays
+        R = len(ctxs)
+        stride = max(g.capacity for g in ctxs)
+        pk = dict(xyz=torch.empty((R * stride, 3), dtype=torch.float32).pin_memory(),
+                  vel=torch.empty((R * stride, 3), dtype=torch.float32).pin_memory(),
+                  id=torch.empty(R * stride, dtype=torch.int64).pin_memory(),
+                  type=torch.empty(R * stride, dtype=torch.int32).pin_memory(),
+                  state=torch.empty(R * stride, dtype=torch.int8).pin_memory(),
+                  cls=torch.empty(R * stride, dtype=torch.int32).pin_memory())
+        nbuf = torch.zeros(R, dtype=torch.int64).pin_memory()
+        ptr = {k: v.data_ptr() for k, v in pk.items()}
+        load_ptr = {k: ptr[k] for k in ("xyz", "vel", "type", "cls", "state")}
+        batch.state_packed(stride, ptr, nbuf.data_ptr())
         e2e_steps = 20
         h2d = d2h = 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(e2e_steps):
-            batch.load([dict(n=n, **{k: v for k, v in vw.items() if k in ("xyz", "vel", "type", "cls", "state")})
-                        for n, vw in zip(ns, views)])
-            h2d += sum(n * (12 + 12 + 4 + 4 + 1) for n in ns)
+            batch.load_packed(stride, load_ptr, nbuf.data_ptr())
+            h2d += R * stride * (12 + 12 + 4 + 4 + 1) + 8 * R
             batch.md_begin(dt, gamma, 9500 + s)
             batch.sweep(1, 9000 + s)
             batch.md_end(dt, gamma, 9500 + s)
-            ns = read_back()
-            d2h += sum(n * (12 + 12 + 8 + 4 + 1 + 4) + 64 for n in ns)
+            batch.state_packed(stride, ptr, nbuf.data_ptr())
+            d2h += R * stride * (12 + 12 + 8 + 4 + 1 + 4) + 12 * R
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
-               "note": "per step: cr_batch_load of the 13 replicas from pinned host buffers + the batched cycle (1e4 "
-                       "trials per replica inside one MD step) + cr_batch_state readback of every replica into the "
-                       "same pinned buffers"}
+               "note": "per step: cr_batch_load_packed of the 13 replicas from packed pinned host arrays + the batched "
+                       "cycle (1e4 trials per replica inside one MD step) + cr_batch_state_packed readback of every "
+                       "replica into the same arrays (whole replica blocks are copied each way)"}
 
     if rank != 0:
         return

@@ -286,8 +286,9 @@ int cr_md_forces_noalloc(cr_ctx *ctx, float *force, uint64_t *id, int64_t n_slot
 
 /* Fill the view (counts always; arrays when non-NULL) and synchronise.
  * Arrays are ordered by particle id (the ordering runs on the device: input
- * ids by a prefix count, inserted ions by a radix sort), one device-to-host
- * copy per array; pinned host arrays make those copies asynchronous DMA. */
+ * ids by a prefix count, inserted ions by their rank among the ion ids, or a
+ * device-wide radix sort past 16,384 ions), one device-to-host copy per
+ * array; pinned host arrays make those copies asynchronous DMA. */
 int cr_state(cr_ctx *ctx, cr_state_view *out);
 
 /* Replace the configuration with n particles from host arrays (xyz [3n],
@@ -365,6 +366,30 @@ typedef struct {
   const int8_t *state;
 } cr_load_args;
 int cr_batch_load(cr_batch *b, const cr_load_args *args);
+/* Packed batch I/O: one host array per quantity for all replicas, replica
+ * r's entries starting at r * stride (stride >= the largest capacity; xyz and
+ * vel hold 3 floats per entry).  cr_batch_state_packed fills the arrays that
+ * are not NULL and n[r] (the particles of replica r, ordered by id as
+ * cr_state; entries past n[r] in a replica's block are unspecified) with two
+ * kernel launches, one copy per array and one synchronisation for the whole
+ * batch (contexts above 16,384 particles of capacity take the per-context
+ * path).  cr_batch_load_packed is cr_load of every replica from such arrays
+ * (n[r] in; vel may be NULL), checked on the device like cr_load; its
+ * per-particle errors come at the next synchronising call.  Arrays the GPU
+ * can address (device memory, pinned host memory) are written or read in
+ * place by the kernels, others go through device staging with one copy each;
+ * a load reads its arrays asynchronously, so they must not change before the
+ * stream has passed the load. */
+typedef struct {
+  int64_t stride;
+  float *xyz, *vel;
+  uint64_t *id;
+  int32_t *type, *cls;
+  int8_t *state;
+  int64_t *n;
+} cr_batch_packed;
+int cr_batch_state_packed(cr_batch *b, cr_batch_packed *p);
+int cr_batch_load_packed(cr_batch *b, const cr_batch_packed *p);
 /* cr_state of every replica of the batch into views[0 .. n-1] (one view per
  * context, in the order given to cr_batch_create); the replicas' reads run
  * concurrently on the batch's streams with two synchronisations in all.

@@ -65,6 +65,11 @@ class cr_load_args(C.Structure):
                 ("cls", C.c_void_p), ("state", C.c_void_p)]
 
 
+class cr_batch_packed(C.Structure):
+    _fields_ = [("stride", C.c_int64), ("xyz", C.c_void_p), ("vel", C.c_void_p), ("id", C.c_void_p),
+                ("type", C.c_void_p), ("cls", C.c_void_p), ("state", C.c_void_p), ("n", C.c_void_p)]
+
+
 class cr_info(C.Structure):
     _fields_ = [("nc", C.c_int32), ("k", C.c_int32), ("h", C.c_int32), ("nd", C.c_int32), ("ncol", C.c_int32),
                 ("m", C.c_int32), ("cap", C.c_int32), ("global_", C.c_int32), ("trials_per_sweep", C.c_int64),
@@ -90,7 +95,8 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_set_surrogate", "cr_sweep_da", "cr_sweep_da_log", "cr_batch_sweep_da", "cr_train_create",
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
-           "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load")
+           "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
+           "cr_batch_state_packed", "cr_batch_load_packed")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -153,6 +159,9 @@ def _lib():
         lib.cr_batch_state.argtypes = [P, C.POINTER(cr_state_view)]
         lib.cr_batch_load.restype = C.c_int
         lib.cr_batch_load.argtypes = [P, C.POINTER(cr_load_args)]
+        for f in ("cr_batch_state_packed", "cr_batch_load_packed"):
+            getattr(lib, f).restype = C.c_int
+            getattr(lib, f).argtypes = [P, C.POINTER(cr_batch_packed)]
         lib.cr_get_info.restype = C.c_int
         lib.cr_get_info.argtypes = [P, C.POINTER(cr_info)]
         lib.cr_set_stream.restype = C.c_int
@@ -450,6 +459,29 @@ class Batch:
             for k in ("xyz", "vel", "type", "cls", "state"):
                 setattr(args[r], k, conv(a.get(k)))
         _chk(self._lib.cr_batch_load(self._h, args), "cr_batch_load")
+
+    @staticmethod
+    def _packed(stride, arrays, n):
+        conv = lambda a: None if a is None else (C.c_void_p(a) if isinstance(a, int) else _p(a))
+        pk = cr_batch_packed()
+        pk.stride = int(stride)
+        for k in ("xyz", "vel", "id", "type", "cls", "state"):
+            setattr(pk, k, conv(arrays.get(k)))
+        pk.n = conv(n)
+        return pk
+
+    def state_packed(self, stride, arrays, n):
+        """cr_batch_state_packed: arrays (numpy arrays or raw pointers) hold all
+        replicas, replica r from r * stride; n (int64 [replicas], numpy array
+        or pointer) receives the particle counts."""
+        pk = self._packed(stride, arrays, n)
+        _chk(self._lib.cr_batch_state_packed(self._h, C.byref(pk)), "cr_batch_state_packed")
+
+    def load_packed(self, stride, arrays, n):
+        """cr_batch_load_packed: every replica from packed arrays (xyz, vel, type,
+        cls, state), n (int64 [replicas]) particles each."""
+        pk = self._packed(stride, arrays, n)
+        _chk(self._lib.cr_batch_load_packed(self._h, C.byref(pk)), "cr_batch_load_packed")
 
     def state_into(self, arrays):
         """cr_batch_state: one dict of caller arrays (as Context.state_into

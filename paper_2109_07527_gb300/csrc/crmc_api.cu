@@ -82,7 +82,7 @@ struct cr_ctx {
   int *d_present = nullptr;
   int ion_lo_bits = 32;  // the low words of inserted ids stay below 2^ion_lo_bits
   unsigned long long *d_ion_key = nullptr, *d_ion_key2 = nullptr;
-  int *d_ion_val = nullptr, *d_ion_val2 = nullptr;
+  int *d_ion_val = nullptr, *d_ion_val2 = nullptr, *d_ion_rank = nullptr;
   unsigned char *d_sort_tmp = nullptr;
   size_t sort_tmp_bytes = 0;
   float *d_out_xyz = nullptr, *d_out_vel = nullptr, *d_out_frc = nullptr;
@@ -178,7 +178,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_log,
                   c->d_in_xyz, c->d_in_vel, c->d_init_type, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
-                  c->d_present, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_sort_tmp,
+                  c->d_present, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_ion_rank, c->d_sort_tmp,
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
@@ -575,8 +575,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     ALLOC(c->d_present, (size_t)std::max(n, 1));
     ALLOC(c->d_ion_key, cp);
     ALLOC(c->d_ion_val, cp);
+    ALLOC(c->d_ion_rank, cp);
     c->sort_tmp_bytes = state_sort_temp_bytes((int)cp);
-    if (c->sort_tmp_bytes > 0) {  // ion lists beyond the one-CTA sort
+    if (c->sort_tmp_bytes > 0) {  // ion lists beyond the tile ranking: device-wide sort
       ALLOC(c->d_ion_key2, cp);
       ALLOC(c->d_ion_val2, cp);
       ALLOC(c->d_sort_tmp, c->sort_tmp_bytes);
@@ -1015,6 +1016,16 @@ extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   return CR_OK;
 }
 
+// the sort bits of a context's ion keys: inserted ids are (phase + 1) << 32 |
+// low word with phase < sweeps * colours, the keys put the high word above the
+// low word's ion_lo_bits bits; one spare bit keeps the sort's padding last
+static int ion_end_bit(const cr_ctx *ctx) {
+  const uint64_t hi_max = ctx->sweep * (uint64_t)ctx->P.ncol + 1;
+  int end_bit = ctx->ion_lo_bits + 1;
+  while (end_bit < 64 && (hi_max >> (end_bit - ctx->ion_lo_bits - 1)) != 0) ++end_bit;
+  return end_bit;
+}
+
 // A state read in two halves around one synchronisation of the stream:
 // state_begin queues the id marks (when arrays are wanted) and the copies of
 // the counts and the error word; state_arrays, with those on the host, fills
@@ -1032,6 +1043,7 @@ static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, St
   B.ion_key_alt = ctx->d_ion_key2;
   B.ion_val = ctx->d_ion_val;
   B.ion_val_alt = ctx->d_ion_val2;
+  B.ion_rank = ctx->d_ion_rank;
   B.sort_tmp = ctx->d_sort_tmp;
   B.sort_tmp_bytes = ctx->sort_tmp_bytes;
   B.vel_src = ctx->d_vel;
@@ -1078,12 +1090,7 @@ static int state_arrays(cr_ctx *ctx, cr_state_view *out, cudaStream_t s, const S
     CR_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int), s));
     return rc;
   }
-  // inserted ids are (phase + 1) << 32 | low word with phase < sweeps *
-  // colours: the sort keys (high word above the low word's bits) need
-  // ion_lo_bits + bits of the phase, plus one
-  const uint64_t hi_max = ctx->sweep * (uint64_t)ctx->P.ncol + 1;
-  int end_bit = ctx->ion_lo_bits + 1;
-  while (end_bit < 64 && (hi_max >> (end_bit - ctx->ion_lo_bits - 1)) != 0) ++end_bit;
+  const int end_bit = ion_end_bit(ctx);
   int nl = 0;
   CR_CUDA(launch_state_order(ctx->P, B, (int)n_present, n_ions, end_bit, s, &nl));
   ctx->launches_total += nl;
@@ -1241,7 +1248,77 @@ struct cr_batch {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   cudaEvent_t fork = nullptr;
+  // packed reads and loads: per-replica descriptors (pinned host + device),
+  // the replicas' counts and error words, staging arrays of stride entries
+  // per replica
+  StateBufs *h_sbufs = nullptr, *d_sbufs = nullptr;
+  LoadJob *h_jobs = nullptr, *d_jobs = nullptr;
+  long long *h_nout = nullptr, *d_nout = nullptr;  // h_nout[n] also holds the error words (as ints)
+  int *d_errout = nullptr;
+  int64_t pk_stride = 0;
+  float *d_pk_xyz = nullptr, *d_pk_vel = nullptr;
+  unsigned long long *d_pk_id = nullptr;
+  int *d_pk_type = nullptr, *d_pk_cls = nullptr;
+  int8_t *d_pk_state = nullptr;
 };
+
+// The device address of caller memory the GPU can access directly (device
+// memory, or pinned host memory: on GB300 host writes and reads go over
+// NVLink-C2C), else null (pageable memory goes through the staging arrays).
+template <typename TT>
+static TT *device_view(TT *p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<TT *>(a.devicePointer);
+  return nullptr;
+}
+
+static void free_packed_staging(cr_batch *b) {
+  void *p[] = {b->d_pk_xyz, b->d_pk_vel, b->d_pk_id, b->d_pk_type, b->d_pk_cls, b->d_pk_state};
+  for (void *x : p)
+    if (x) cudaFree(x);
+  b->d_pk_xyz = b->d_pk_vel = nullptr;
+  b->d_pk_id = nullptr;
+  b->d_pk_type = b->d_pk_cls = nullptr;
+  b->d_pk_state = nullptr;
+  b->pk_stride = 0;
+}
+
+// device staging of stride entries per replica for the packed calls, and the
+// per-replica descriptors; allocated on first use, grown with the stride
+static int ensure_packed(cr_batch *b, int64_t stride) {
+  const size_t n = b->ctx.size();
+  if (!b->h_sbufs) {
+    if (cudaHostAlloc((void **)&b->h_sbufs, n * sizeof(StateBufs), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->h_jobs, n * sizeof(LoadJob), 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->h_nout, 2 * n * sizeof(long long), 0) != cudaSuccess)
+      return CR_ERR_NOMEM;
+    if (cudaMalloc((void **)&b->d_sbufs, n * sizeof(StateBufs)) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_jobs, n * sizeof(LoadJob)) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_nout, n * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_errout, n * sizeof(int)) != cudaSuccess)
+      return CR_ERR_NOMEM;
+  }
+  if (stride <= b->pk_stride) return CR_OK;
+  free_packed_staging(b);
+  const size_t m = n * (size_t)stride;
+  if (cudaMalloc((void **)&b->d_pk_xyz, 3 * m * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_pk_vel, 3 * m * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_pk_id, m * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_pk_type, m * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_pk_cls, m * sizeof(int)) != cudaSuccess ||
+      cudaMalloc((void **)&b->d_pk_state, m) != cudaSuccess) {
+    free_packed_staging(b);
+    return CR_ERR_NOMEM;
+  }
+  b->pk_stride = stride;
+  return CR_OK;
+}
 
 extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   if (!out || !ctxs || n <= 0) return CR_ERR_INVALID_ARG;
@@ -1316,6 +1393,13 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_reps) cudaFree(b->d_reps);
+  free_packed_staging(b);
+  void *dp[] = {b->d_sbufs, b->d_jobs, b->d_nout, b->d_errout};
+  for (void *x : dp)
+    if (x) cudaFree(x);
+  void *hp[] = {b->h_sbufs, b->h_jobs, b->h_nout};
+  for (void *x : hp)
+    if (x) cudaFreeHost(x);
   delete b;
 }
 
@@ -1462,6 +1546,134 @@ extern "C" int cr_batch_state(cr_batch *b, cr_state_view *views) {
   }
   for (size_t r = 0; r < n; ++r) CR_CUDA(cudaStreamSynchronize(b->streams[r]));
   return rc;
+}
+
+extern "C" int cr_batch_state_packed(cr_batch *b, cr_batch_packed *p) {
+  if (!b || !p || !p->n) return CR_ERR_INVALID_ARG;
+  const size_t R = b->ctx.size();
+  int64_t capmax = 0;
+  int max_slots = 0;
+  for (cr_ctx *c : b->ctx) {
+    capmax = std::max<int64_t>(capmax, c->capacity);
+    max_slots = std::max(max_slots, c->P.ncell * c->P.cap);
+  }
+  if (p->stride < capmax) return CR_ERR_INVALID_ARG;
+  const int64_t S = p->stride;
+  if (capmax > STATE_BLOCK_SORT_MAX) {  // ion lists beyond the tile ranking: per-context reads
+    std::vector<cr_state_view> v(R);
+    for (size_t r = 0; r < R; ++r) {
+      v[r] = cr_state_view{};
+      v[r].xyz = p->xyz ? p->xyz + 3 * r * S : nullptr;
+      v[r].vel = p->vel ? p->vel + 3 * r * S : nullptr;
+      v[r].id = p->id ? p->id + r * S : nullptr;
+      v[r].type = p->type ? p->type + r * S : nullptr;
+      v[r].state = p->state ? p->state + r * S : nullptr;
+      v[r].cls = p->cls ? p->cls + r * S : nullptr;
+    }
+    const int rc = cr_batch_state(b, v.data());
+    for (size_t r = 0; r < R; ++r) p->n[r] = v[r].n;
+    return rc;
+  }
+  int rc = ensure_packed(b, S);
+  if (rc != CR_OK) return rc;
+  cudaStream_t s = b->ctx[0]->stream;
+  // arrays the GPU can address are written in place (no staging, no copy)
+  float *zx = device_view(p->xyz), *zv = device_view(p->vel);
+  uint64_t *zi = device_view(p->id);
+  int32_t *zt = device_view(p->type), *zc = device_view(p->cls);
+  int8_t *zs = device_view(p->state);
+  for (size_t r = 0; r < R; ++r) {
+    cr_ctx *c = b->ctx[r];
+    StateBufs &B = b->h_sbufs[r];
+    B = StateBufs{};
+    B.n_input = c->n_input;
+    B.cap = (int)c->capacity;
+    B.lo_bits = c->ion_lo_bits;
+    B.present = c->d_present;
+    B.n_ions = c->d_counter;
+    B.ion_key = c->d_ion_key;
+    B.ion_val = c->d_ion_val;
+    B.ion_rank = c->d_ion_rank;
+    B.vel_src = c->d_vel;
+    B.counts = c->d_counts;
+    B.n_other = c->n_other;
+    B.end_bit = ion_end_bit(c);
+    B.xyz = p->xyz ? (zx ? zx : b->d_pk_xyz) + 3 * r * S : nullptr;
+    B.vel = p->vel ? (zv ? zv : b->d_pk_vel) + 3 * r * S : nullptr;
+    B.id = p->id ? (zi ? (unsigned long long *)zi : b->d_pk_id) + r * S : nullptr;
+    B.type = p->type ? (zt ? zt : b->d_pk_type) + r * S : nullptr;
+    B.cls = p->cls ? (zc ? zc : b->d_pk_cls) + r * S : nullptr;
+    B.state = p->state ? (zs ? zs : b->d_pk_state) + r * S : nullptr;
+  }
+  CR_CUDA(cudaMemcpyAsync(b->d_sbufs, b->h_sbufs, R * sizeof(StateBufs), cudaMemcpyHostToDevice, s));
+  CR_CUDA(launch_state_batch(b->d_reps, b->d_sbufs, (int)R, max_slots, (int)capmax, b->d_nout, b->d_errout, s));
+  b->ctx[0]->launches_total += 3;
+  CR_CUDA(cudaMemcpyAsync(b->h_nout, b->d_nout, R * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  int *herr = (int *)(b->h_nout + R);
+  CR_CUDA(cudaMemcpyAsync(herr, b->d_errout, R * sizeof(int), cudaMemcpyDeviceToHost, s));
+  const size_t m = R * (size_t)S;
+  if (p->xyz && !zx) CR_CUDA(cudaMemcpyAsync(p->xyz, b->d_pk_xyz, 3 * m * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (p->vel && !zv) CR_CUDA(cudaMemcpyAsync(p->vel, b->d_pk_vel, 3 * m * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (p->id && !zi) CR_CUDA(cudaMemcpyAsync(p->id, b->d_pk_id, m * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  if (p->type && !zt) CR_CUDA(cudaMemcpyAsync(p->type, b->d_pk_type, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (p->cls && !zc) CR_CUDA(cudaMemcpyAsync(p->cls, b->d_pk_cls, m * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (p->state && !zs) CR_CUDA(cudaMemcpyAsync(p->state, b->d_pk_state, m, cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaStreamSynchronize(s));
+  rc = CR_OK;
+  for (size_t r = 0; r < R; ++r) {
+    p->n[r] = b->h_nout[r];
+    const int e = err_bits_to_code(herr[r]);
+    if (rc == CR_OK && e != CR_OK) rc = e;
+    if (rc == CR_OK && b->h_nout[r] < 0) rc = CR_ERR_CUDA;
+  }
+  return rc;
+}
+
+extern "C" int cr_batch_load_packed(cr_batch *b, const cr_batch_packed *p) {
+  if (!b || !p || !p->n || !p->xyz || !p->type || !p->cls || !p->state) return CR_ERR_INVALID_ARG;
+  const size_t R = b->ctx.size();
+  int64_t capmax = 0, max_n = 0;
+  int max_cells = 0;
+  for (size_t r = 0; r < R; ++r) {
+    cr_ctx *c = b->ctx[r];
+    if (p->n[r] < c->n_fixed_end || p->n[r] > c->capacity) return CR_ERR_INVALID_ARG;
+    capmax = std::max<int64_t>(capmax, c->capacity);
+    max_n = std::max<int64_t>(max_n, p->n[r]);
+    max_cells = std::max(max_cells, c->P.ncell);
+  }
+  if (p->stride < capmax) return CR_ERR_INVALID_ARG;
+  const int64_t S = p->stride;
+  int rc = ensure_packed(b, S);
+  if (rc != CR_OK) return rc;
+  cudaStream_t s = b->ctx[0]->stream;
+  const size_t m = R * (size_t)S;
+  // arrays the GPU can address are read in place; the others are staged
+  const float *zx = device_view(p->xyz), *zv = device_view(p->vel);
+  const int32_t *zt = device_view(p->type), *zc = device_view(p->cls);
+  const int8_t *zs = device_view(p->state);
+  if (!zx) CR_CUDA(cudaMemcpyAsync(b->d_pk_xyz, p->xyz, 3 * m * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (p->vel && !zv) CR_CUDA(cudaMemcpyAsync(b->d_pk_vel, p->vel, 3 * m * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (!zt) CR_CUDA(cudaMemcpyAsync(b->d_pk_type, p->type, m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!zc) CR_CUDA(cudaMemcpyAsync(b->d_pk_cls, p->cls, m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (!zs) CR_CUDA(cudaMemcpyAsync(b->d_pk_state, p->state, m, cudaMemcpyHostToDevice, s));
+  const float *ix = zx ? zx : b->d_pk_xyz, *iv = p->vel ? (zv ? zv : b->d_pk_vel) : nullptr;
+  const int32_t *it = zt ? zt : b->d_pk_type, *ic = zc ? zc : b->d_pk_cls;
+  const int8_t *is = zs ? zs : b->d_pk_state;
+  for (size_t r = 0; r < R; ++r) {
+    cr_ctx *c = b->ctx[r];
+    LoadJob &J = b->h_jobs[r];
+    J.I = LoadBufs{ix + 3 * r * S, iv ? iv + 3 * r * S : nullptr, it + r * S, ic + r * S, c->d_site_map,
+                   is + r * S, (int)p->n[r], c->n_input, c->d_init_type};
+    J.B = RebuildBufs{c->d_cnt2, c->d_pos2, c->d_pid2, c->d_info2, c->d_vel2, c->d_frc2, c->d_vel, c->d_frc};
+    J.perm_slot = c->d_perm;
+    J.n_perm = c->n_input;
+    c->f_valid = false;
+    c->fcons_valid = false;
+  }
+  CR_CUDA(cudaMemcpyAsync(b->d_jobs, b->h_jobs, R * sizeof(LoadJob), cudaMemcpyHostToDevice, s));
+  CR_CUDA(launch_load_batch(b->d_reps, b->d_jobs, (int)R, (int)max_n, max_cells, s));
+  b->ctx[0]->launches_total += 4;
+  return CR_OK;
 }
 
 extern "C" int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs) {

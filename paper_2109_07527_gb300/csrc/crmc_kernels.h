@@ -33,7 +33,7 @@ struct RebuildBufs {
 
 // the configuration read back in id order (crmc_state.cu); output arrays
 // that are null are not written
-constexpr int STATE_BLOCK_SORT_MAX = 16384;  // ions sorted inside one CTA; more: device-wide sort
+constexpr int STATE_BLOCK_SORT_MAX = 16384;  // ions ranked by tile counting; more: device-wide sort
 struct StateBufs {
   int n_input, cap;               // input ids are 0..n_input-1; ion list capacity
   int lo_bits;                    // the low words of ion ids stay below 2^lo_bits
@@ -41,9 +41,12 @@ struct StateBufs {
   int *n_ions;                    // number of inserted ions found
   unsigned long long *ion_key, *ion_key_alt;  // [cap] ion sort keys (the alternates for the device-wide sort)
   int *ion_val, *ion_val_alt;                 // [cap] their slots
+  int *ion_rank;                              // [cap] rank of each ion among the ion ids
   void *sort_tmp;                 // device-wide sort scratch (capacities above STATE_BLOCK_SORT_MAX)
   size_t sort_tmp_bytes;
   const float4 *vel_src, *frc_src;  // velocities; forces (null: zeros)
+  const long long *counts;          // the context's kind counts (batch reads take n from them)
+  int n_other, end_bit;             // particles of no kind; sort bits (batch reads)
   float *xyz, *vel, *frc;           // [3n]
   unsigned long long *id;           // [n]
   int *type, *cls;                  // [n]
@@ -57,6 +60,14 @@ struct LoadBufs {
   const int8_t *state;
   int n, n_site_map;
   const int *init_type;  // [n_site_map] types given to cr_init (bonded and site particles stay at their index)
+};
+
+// one replica's load in a batched load
+struct LoadJob {
+  LoadBufs I;
+  RebuildBufs B;
+  int *perm_slot;
+  int n_perm;
 };
 
 // phase kernel shapes (threads, halo registers); da: the delayed-acceptance set
@@ -82,6 +93,10 @@ cudaError_t launch_kick_drift_rebuild(const SysParams &P, const MdParams &M, con
                                       int n_perm, cudaStream_t s);
 cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int *perm_slot, int n_perm,
                         cudaStream_t s);
+// loads of every replica of a batch (counts zeroed, scatter, cell sort,
+// neutrality), four launches
+cudaError_t launch_load_batch(const SysParams *d_reps, const LoadJob *d_jobs, int n_rep, int max_n, int max_cells,
+                              cudaStream_t s);
 cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
 // state read-back: mark the slots (ion count into *B.n_ions), then, with the
 // counts known, place the input ids, sort the ions (bits [0, end_bit) of their
@@ -92,6 +107,11 @@ cudaError_t launch_state_mark(const SysParams &P, const StateBufs &B, cudaStream
 cudaError_t launch_state_order(const SysParams &P, const StateBufs &B, int n_present, int n_ions, int end_bit,
                                cudaStream_t s, int *launches);
 size_t state_sort_temp_bytes(int cap);
+// every replica of a batch in two launches (marks, ordering), the counts read
+// on the device; n_out[r] = particles of replica r, -1 when its read needs the
+// per-context path; err_out[r] its error word
+cudaError_t launch_state_batch(const SysParams *d_reps, const StateBufs *d_bufs, int n_rep, int max_slots,
+                               int max_cap, long long *d_n_out, int *d_err_out, cudaStream_t s);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                           uint4 *out, cudaStream_t s);
 

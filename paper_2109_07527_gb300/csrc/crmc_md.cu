@@ -324,29 +324,49 @@ __global__ void k_md_kick_drift_scatter(SysParams P, MdParams M, RebuildBufs B) 
 }
 
 // rebuild: one warp per cell sorts the cell by id into the primary arrays
-__global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n_perm) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void rebuild_sort_cell(const SysParams &P, const RebuildBufs &B, int *perm_slot, int n_perm,
+                                                  int warp) {
+  const int lane = threadIdx.x & 31;
   if (warp >= P.ncell) return;
   const int c = warp;
   const int n = min(B.cnt[c], P.cap);
   const int base = c * P.cap;
-  for (int e = lane; e < n; e += 32) {
-    const unsigned long long id = B.pid[base + e];
+  if (n <= 32) {  // the cell's ids in the lanes, ranks by shuffles
+    const unsigned long long id = lane < n ? B.pid[base + lane] : ~0ull;
     int rank = 0;
-    for (int o = 0; o < n; ++o) rank += B.pid[base + o] < id;
-    const int dst = base + rank;
-    P.pos[dst] = B.pos[base + e];
-    P.pid[dst] = id;
-    P.info[dst] = B.info[base + e];
-    B.vel_src[dst] = B.vel[base + e];
-    B.frc_src[dst] = B.frc[base + e];
-    if (id < (unsigned long long)n_perm) perm_slot[id] = dst;
+    for (int o = 0; o < n; ++o) rank += __shfl_sync(0xffffffffu, id, o) < id ? 1 : 0;
+    if (lane < n) {
+      const int dst = base + rank;
+      P.pos[dst] = B.pos[base + lane];
+      P.pid[dst] = id;
+      P.info[dst] = B.info[base + lane];
+      B.vel_src[dst] = B.vel[base + lane];
+      B.frc_src[dst] = B.frc[base + lane];
+      if (id < (unsigned long long)n_perm) perm_slot[id] = dst;
+    }
+  } else {
+    for (int e = lane; e < n; e += 32) {
+      const unsigned long long id = B.pid[base + e];
+      int rank = 0;
+      for (int o = 0; o < n; ++o) rank += B.pid[base + o] < id;
+      const int dst = base + rank;
+      P.pos[dst] = B.pos[base + e];
+      P.pid[dst] = id;
+      P.info[dst] = B.info[base + e];
+      B.vel_src[dst] = B.vel[base + e];
+      B.frc_src[dst] = B.frc[base + e];
+      if (id < (unsigned long long)n_perm) perm_slot[id] = dst;
+    }
   }
   __syncwarp();
   if (lane == 0) {
     P.cnt[c] = n;
     B.cnt[c] = 0;
   }
+}
+
+__global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n_perm) {
+  rebuild_sort_cell(P, B, perm_slot, n_perm, (blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 }
 
 // refresh the slot of every permanent particle
@@ -367,8 +387,7 @@ __global__ void k_load_neutral(SysParams P) {
 }
 
 // load: place input particles (index = id) into cells, unordered
-__global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs &I, const RebuildBufs &B, int i) {
   if (i >= I.n) return;
   const float x = I.xyz[3 * i], y = I.xyz[3 * i + 1], z = I.xyz[3 * i + 2];
   const int t = I.type[i];
@@ -409,6 +428,30 @@ __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
   B.info[o] = t | (cl << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
   B.vel[o] = I.vel ? make_float4(I.vel[3 * i], I.vel[3 * i + 1], I.vel[3 * i + 2], 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
   B.frc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
+  load_particle(P, I, B, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Loads of every replica of a batch (blockIdx.y = replica): counts zeroed,
+// particles placed, cells sorted, neutrality checked, one launch per step.
+__global__ void k_load_zero_batch(const SysParams *__restrict__ reps) {
+  if (threadIdx.x < 6) reps[blockIdx.x].counts[threadIdx.x] = 0;
+}
+__global__ void k_load_scatter_batch(const SysParams *__restrict__ reps, const LoadJob *__restrict__ jobs) {
+  const LoadJob &J = jobs[blockIdx.y];
+  load_particle(reps[blockIdx.y], J.I, J.B, blockIdx.x * blockDim.x + threadIdx.x);
+}
+__global__ void k_rebuild_sort_batch(const SysParams *__restrict__ reps, const LoadJob *__restrict__ jobs) {
+  const LoadJob &J = jobs[blockIdx.y];
+  rebuild_sort_cell(reps[blockIdx.y], J.B, J.perm_slot, J.n_perm, (blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+}
+__global__ void k_load_neutral_batch(const SysParams *__restrict__ reps) {
+  if (threadIdx.x != 0) return;
+  const SysParams &P = reps[blockIdx.x];
+  const long long q = P.counts[K_XP] - P.counts[K_XM] - P.counts[K_A1] + P.counts[K_B1];
+  if (q != 0) atomicOr(P.err, ERRB_NOT_NEUTRAL);
 }
 
 __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
@@ -461,6 +504,15 @@ cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs
   if (I.n > 0) k_load_scatter<<<(I.n + 255) / 256, 256, 0, s>>>(P, I, B);
   k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
   k_load_neutral<<<1, 32, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_batch(const SysParams *d_reps, const LoadJob *d_jobs, int n_rep, int max_n, int max_cells,
+                              cudaStream_t s) {
+  k_load_zero_batch<<<n_rep, 32, 0, s>>>(d_reps);
+  if (max_n > 0) k_load_scatter_batch<<<dim3((max_n + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
+  k_rebuild_sort_batch<<<dim3((max_cells * 32 + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
+  k_load_neutral_batch<<<n_rep, 32, 0, s>>>(d_reps);
   return cudaGetLastError();
 }
 

@@ -1,14 +1,14 @@
 // crmc_state.cu -- the configuration read back in particle-id order, on the
 // device (sm_103a): the occupied cell slots are mapped to ids, input particles
 // (ids below n_input, dense) are placed by a prefix count over the ids present,
-// inserted ions (ids >= 2^32) by a radix sort of their ids, and every requested
-// array is written in the caller's layout, ready for one copy each.
+// inserted ions (ids >= 2^32) by their rank among the ion ids (counted in
+// 1024 x 1024 tiles over many CTAs; a device-wide radix sort past 16,384
+// ions), and every requested array is written in the caller's layout.
 //
 // Between two reads the id marks (present[]) and the ion counter are zero:
 // the ordering kernel clears what the mark kernel set.
 #include <cuda_runtime.h>
 
-#include <cub/block/block_radix_sort.cuh>
 #include <cub/device/device_radix_sort.cuh>
 
 #include <cstdint>
@@ -21,15 +21,14 @@ namespace crmc {
 namespace {
 
 constexpr int ORDER_THREADS = 1024;
-constexpr int ORDER_ITEMS = 16;  // ions sorted inside one CTA: up to 16,384
-using IonSort = cub::BlockRadixSort<unsigned long long, ORDER_THREADS, ORDER_ITEMS, int>;
+constexpr int RANK_TILE = 1024;  // ion keys per rank-counting tile
 
 // every occupied slot: input ids mark their slot (slot + 1), inserted ions
 // append (key, slot) to the ion list (one atomic per warp); the key keeps the
 // order of the ids: (id >> 32) << lo_bits | (id & 0xffffffff), as the low
 // word of an inserted id stays below 2^lo_bits
-__global__ void k_state_mark(SysParams P, StateBufs B) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+__device__ __forceinline__ void mark_slot(const SysParams &P, const StateBufs &B, int g) {
+  const int lane = threadIdx.x & 31;
   const int c = g / P.cap;
   const bool have = g < P.ncell * P.cap && g - c * P.cap < P.cnt[c];
   unsigned long long id = 0;
@@ -47,7 +46,34 @@ __global__ void k_state_mark(SysParams P, StateBufs B) {
   if (o >= B.cap) return;  // more ions than slots: the host sees the count and reports it
   B.ion_key[o] = ((id >> 32) << B.lo_bits) | (id & 0xffffffffull);
   B.ion_val[o] = g;
+  B.ion_rank[o] = 0;
 }
+
+// rank of every ion key among the n ion keys (the keys are distinct): CTA
+// (x, y) adds, for the keys of tile x, how many keys of tile y are smaller
+__device__ __forceinline__ void rank_tile(const StateBufs &B, int n) {
+  __shared__ unsigned long long ks[RANK_TILE];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * RANK_TILE + t, j0 = blockIdx.y * RANK_TILE;
+  if (j0 >= n || (int)blockIdx.x * RANK_TILE >= n) return;  // the whole CTA
+  ks[t] = j0 + t < n ? B.ion_key[j0 + t] : ~0ull;
+  __syncthreads();
+  if (i >= n) return;
+  const unsigned long long k = B.ion_key[i];
+  const int m = min(RANK_TILE, n - j0);
+  int c = 0;
+#pragma unroll 8
+  for (int j = 0; j < m; ++j) c += ks[j] < k ? 1 : 0;
+  if (c) atomicAdd(&B.ion_rank[i], c);
+}
+
+__global__ void __launch_bounds__(RANK_TILE) k_ion_rank(StateBufs B, int n) { rank_tile(B, n); }
+__global__ void __launch_bounds__(RANK_TILE) k_ion_rank_batch(const StateBufs *__restrict__ bufs) {
+  const StateBufs &B = bufs[blockIdx.z];
+  rank_tile(B, min(*B.n_ions, STATE_BLOCK_SORT_MAX));
+}
+
+__global__ void k_state_mark(SysParams P, StateBufs B) { mark_slot(P, B, blockIdx.x * blockDim.x + threadIdx.x); }
 
 __device__ __forceinline__ void emit(const SysParams &P, const StateBufs &B, int g, int o) {
   const float4 p = P.pos[g];
@@ -70,70 +96,101 @@ __device__ __forceinline__ void emit(const SysParams &P, const StateBufs &B, int
   if (B.site && (t == CR_ACID || t == CR_BASE)) B.site[info >> INFO_SITE_SHIFT] = (int8_t)ionised;
 }
 
-// CTA 0: the input ids present, by an exclusive prefix count (each thread a
-// contiguous range), written and unmarked.  CTA 1: the ions after them, in
-// id order -- sorted here (block radix sort of the keys) or, for more than
-// one CTA holds, already sorted by the device-wide sort (sorted_slot).
-__global__ void __launch_bounds__(ORDER_THREADS) k_state_order(SysParams P, StateBufs B, int n_present, int n_ions,
-                                                               int end_bit, const int *sorted_slot) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// The input ids present, by an exclusive prefix count (each thread a
+// contiguous range), written and unmarked (one CTA).
+__device__ __forceinline__ void order_inputs(const SysParams &P, const StateBufs &B, int *part) {
   const int t = threadIdx.x;
-  if (blockIdx.x == 0) {
-    int *part = (int *)smem;
-    const int lane = t & 31, w = t >> 5;
-    const int n = B.n_input;
-    const int per = (n + ORDER_THREADS - 1) / ORDER_THREADS;
-    const int lo = min(n, t * per), hi = min(n, lo + per);
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += B.present[i] != 0;
-    int x = s;
+  const int lane = t & 31, w = t >> 5;
+  const int n = B.n_input;
+  const int per = (n + ORDER_THREADS - 1) / ORDER_THREADS;
+  const int lo = min(n, t * per), hi = min(n, lo + per);
+  int s = 0;
+  for (int i = lo; i < hi; ++i) s += B.present[i] != 0;
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) part[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int v = part[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
     }
-    if (lane == 31) part[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      int v = part[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-      }
-      part[lane] = v;
+    part[lane] = v;
+  }
+  __syncthreads();
+  int run = x - s + (w > 0 ? part[w - 1] : 0);
+  for (int i = lo; i < hi; ++i) {
+    const int g = B.present[i] - 1;
+    if (g >= 0) {
+      emit(P, B, g, run++);
+      B.present[i] = 0;
     }
-    __syncthreads();
-    int run = x - s + (w > 0 ? part[w - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-      const int g = B.present[i] - 1;
-      if (g >= 0) {
-        emit(P, B, g, run++);
-        B.present[i] = 0;
-      }
+  }
+}
+
+// The ions after the input ids, in id order: at their ranks, or in the
+// order of the device-wide sort (sorted_slot).
+__device__ __forceinline__ void order_ions(const SysParams &P, const StateBufs &B, int n_present, int n_ions,
+                                           const int *sorted_slot) {
+  for (int r = threadIdx.x; r < n_ions; r += ORDER_THREADS)
+    emit(P, B, sorted_slot ? sorted_slot[r] : B.ion_val[r], n_present + (sorted_slot ? r : B.ion_rank[r]));
+}
+
+// CTA 0 the input ids, CTA 1 the ions (counts from the host)
+__global__ void __launch_bounds__(ORDER_THREADS) k_state_order(SysParams P, StateBufs B, int n_present, int n_ions,
+                                                               const int *sorted_slot) {
+  __shared__ int part[ORDER_THREADS / 32];
+  if (blockIdx.x == 0) {
+    order_inputs(P, B, part);
+    return;
+  }
+  if (threadIdx.x == 0) *B.n_ions = 0;  // the count came to the host as n_ions
+  order_ions(P, B, n_present, n_ions, sorted_slot);
+}
+
+// Every replica of a batch (blockIdx.y) at once, the counts read on the
+// device: n from the kind counts, n_ions from the mark kernel.  A replica
+// whose ions exceed the tile ranking (or whose counts are inconsistent) gets
+// n_out = -1 and only its marks cleared.  n_out and err_out receive each
+// replica's particle count and error word.
+__global__ void k_state_mark_batch(const SysParams *__restrict__ reps, const StateBufs *__restrict__ bufs) {
+  mark_slot(reps[blockIdx.y], bufs[blockIdx.y], blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(ORDER_THREADS) k_state_order_batch(const SysParams *__restrict__ reps,
+                                                                     const StateBufs *__restrict__ bufs,
+                                                                     long long *n_out, int *err_out) {
+  __shared__ int part[ORDER_THREADS / 32];
+  const int r = blockIdx.y;
+  const SysParams &P = reps[r];
+  const StateBufs &B = bufs[r];
+  const long long *cn = B.counts;
+  const long long n = cn[K_A0] + cn[K_A1] + cn[K_B0] + cn[K_B1] + cn[K_XP] + cn[K_XM] + B.n_other;
+  const int n_ions = *B.n_ions;
+  const long long n_present = n - n_ions;
+  const bool ok = n_ions >= 0 && n_ions <= STATE_BLOCK_SORT_MAX && n <= B.cap && n_present >= 0 &&
+                  n_present <= B.n_input && *P.err == 0;
+  __syncthreads();  // every thread has read the ion count
+  if (blockIdx.x == 0) {
+    if (ok) {
+      order_inputs(P, B, part);
+    } else {
+      for (int i = threadIdx.x; i < B.n_input; i += ORDER_THREADS) B.present[i] = 0;
+    }
+    if (threadIdx.x == 0) {
+      n_out[r] = ok ? n : -1;
+      err_out[r] = *P.err;
     }
     return;
   }
-  if (t == 0) *B.n_ions = 0;  // the count came to the host as n_ions
-  if (sorted_slot) {
-    for (int r = t; r < n_ions; r += ORDER_THREADS) emit(P, B, sorted_slot[r], n_present + r);
-    return;
-  }
-  if (n_ions == 0) return;
-  unsigned long long key[ORDER_ITEMS];
-  int val[ORDER_ITEMS];
-#pragma unroll
-  for (int i = 0; i < ORDER_ITEMS; ++i) {  // blocked arrangement, padded with the largest key
-    const int r = t * ORDER_ITEMS + i;
-    key[i] = r < n_ions ? B.ion_key[r] : ~0ull;
-    val[i] = r < n_ions ? B.ion_val[r] : -1;
-  }
-  IonSort(*(typename IonSort::TempStorage *)smem).Sort(key, val, 0, end_bit);
-#pragma unroll
-  for (int i = 0; i < ORDER_ITEMS; ++i) {
-    const int r = t * ORDER_ITEMS + i;
-    if (r < n_ions) emit(P, B, val[i], n_present + r);
-  }
+  if (threadIdx.x == 0) *B.n_ions = 0;
+  if (ok) order_ions(P, B, (int)n_present, n_ions, nullptr);
 }
 
 }  // namespace
@@ -155,18 +212,9 @@ size_t state_sort_temp_bytes(int cap) {
 
 cudaError_t launch_state_order(const SysParams &P, const StateBufs &B, int n_present, int n_ions, int end_bit,
                                cudaStream_t s, int *launches) {
-  static_assert(ORDER_THREADS * ORDER_ITEMS == STATE_BLOCK_SORT_MAX, "block sort capacity");
-  const size_t smem = sizeof(typename IonSort::TempStorage) > sizeof(int) * 32 ? sizeof(typename IonSort::TempStorage)
-                                                                               : sizeof(int) * 32;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_state_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   int n_launch = 1;
   const int *sorted = nullptr;
-  if (n_ions > STATE_BLOCK_SORT_MAX) {  // beyond one CTA: device-wide radix sort first
+  if (n_ions > STATE_BLOCK_SORT_MAX) {  // many ions: device-wide radix sort
     if (!B.sort_tmp || !B.ion_key_alt || !B.ion_val_alt) return cudaErrorInvalidValue;
     cub::DoubleBuffer<unsigned long long> k(B.ion_key, B.ion_key_alt);
     cub::DoubleBuffer<int> v(B.ion_val, B.ion_val_alt);
@@ -175,9 +223,22 @@ cudaError_t launch_state_order(const SysParams &P, const StateBufs &B, int n_pre
     if (e != cudaSuccess) return e;
     sorted = v.Current();
     n_launch += (end_bit + 7) / 8 + 2;  // histogram, scan and one pass per 8 bits
+  } else if (n_ions > 1) {
+    const unsigned nt = (unsigned)((n_ions + RANK_TILE - 1) / RANK_TILE);
+    k_ion_rank<<<dim3(nt, nt), RANK_TILE, 0, s>>>(B, n_ions);
+    ++n_launch;
   }
-  k_state_order<<<2, ORDER_THREADS, smem, s>>>(P, B, n_present, n_ions, end_bit, sorted);
+  k_state_order<<<2, ORDER_THREADS, 0, s>>>(P, B, n_present, n_ions, sorted);
   if (launches) *launches += n_launch;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_batch(const SysParams *d_reps, const StateBufs *d_bufs, int n_rep, int max_slots,
+                               int max_cap, long long *d_n_out, int *d_err_out, cudaStream_t s) {
+  if (max_slots > 0) k_state_mark_batch<<<dim3((max_slots + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_bufs);
+  const unsigned nt = (unsigned)((min(max_cap, STATE_BLOCK_SORT_MAX) + RANK_TILE - 1) / RANK_TILE);
+  if (nt > 0) k_ion_rank_batch<<<dim3(nt, nt, n_rep), RANK_TILE, 0, s>>>(d_bufs);
+  k_state_order_batch<<<dim3(2, n_rep), ORDER_THREADS, 0, s>>>(d_reps, d_bufs, d_n_out, d_err_out);
   return cudaGetLastError();
 }
 

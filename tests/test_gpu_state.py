@@ -185,3 +185,88 @@ def test_batch_load_equals_context_loads(crmc):
     b.sweep(1, 7)
     for g in batched:
         g.check()
+
+
+def test_packed_batch_state_and_load(crmc):
+    """cr_batch_state_packed equals the contexts' own reads (replica r's
+    block at r * stride); cr_batch_load_packed of those arrays equals the
+    per-context loads; the batch then sweeps on."""
+    ws = [W.config2(seed=13, scale=0.5, pH=pH) for pH in (3.0, 5.0, 7.0)]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(3, 21)
+    refs = [g.state() for g in ctxs]
+    R, S = len(ws), max(w.capacity for w in ws) + 5
+    arr = dict(xyz=np.zeros((R * S, 3), np.float32), vel=np.zeros((R * S, 3), np.float32),
+               id=np.zeros(R * S, np.uint64), type=np.zeros(R * S, np.int32), cls=np.zeros(R * S, np.int32),
+               state=np.zeros(R * S, np.int8))
+    n = np.zeros(R, np.int64)
+    b.state_packed(S, arr, n)
+    for r, ref in enumerate(refs):
+        k = int(n[r])
+        assert k == int(ref["n"])
+        for key in ("xyz", "vel", "id", "type", "cls", "state"):
+            assert np.array_equal(arr[key][r * S:r * S + k], ref[key]), (r, key)
+    fresh = [crmc.Context(w) for w in ws]
+    single = [crmc.Context(w) for w in ws]
+    bf = crmc.Batch(fresh)
+    bf.load_packed(S, {k: arr[k] for k in ("xyz", "vel", "type", "cls", "state")}, n)
+    for r, g in enumerate(single):
+        k = int(n[r])
+        g.load(k, arr["xyz"][r * S:r * S + k].copy(), arr["vel"][r * S:r * S + k].copy(),
+               arr["type"][r * S:r * S + k].copy(), arr["cls"][r * S:r * S + k].copy(),
+               arr["state"][r * S:r * S + k].copy())
+    for g1, g2 in zip(single, fresh):
+        s1, s2 = g1.state(), g2.state()
+        for key in ("id", "xyz", "vel", "type", "state", "cls", "site_state"):
+            assert np.array_equal(s1[key], s2[key]), key
+    bf.sweep(1, 8)
+    for g in fresh:
+        g.check()
+    n2 = np.zeros(R, np.int64)
+    bf.state_packed(S, {"id": np.zeros(R * S, np.uint64)}, n2)
+    assert np.all(n2 > 0)
+
+
+def test_packed_batch_io_in_place_on_pinned_memory(crmc):
+    """Pinned host arrays are written and read by the kernels in place (no
+    staging copies); the results equal those through pageable arrays."""
+    torch = pytest.importorskip("torch")
+    ws = [W.config2(seed=14, scale=0.5, pH=pH) for pH in (4.0, 6.0)]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(2, 17)
+    R, S = len(ws), max(w.capacity for w in ws)
+    ref = dict(xyz=np.zeros((R * S, 3), np.float32), vel=np.zeros((R * S, 3), np.float32),
+               id=np.zeros(R * S, np.uint64), type=np.zeros(R * S, np.int32), cls=np.zeros(R * S, np.int32),
+               state=np.zeros(R * S, np.int8))
+    nref = np.zeros(R, np.int64)
+    b.state_packed(S, ref, nref)
+    pk = dict(xyz=torch.zeros((R * S, 3), dtype=torch.float32).pin_memory(),
+              vel=torch.zeros((R * S, 3), dtype=torch.float32).pin_memory(),
+              id=torch.zeros(R * S, dtype=torch.int64).pin_memory(),
+              type=torch.zeros(R * S, dtype=torch.int32).pin_memory(),
+              cls=torch.zeros(R * S, dtype=torch.int32).pin_memory(),
+              state=torch.zeros(R * S, dtype=torch.int8).pin_memory())
+    n = torch.zeros(R, dtype=torch.int64).pin_memory()
+    b.state_packed(S, {k: v.data_ptr() for k, v in pk.items()}, n.data_ptr())
+    assert np.array_equal(n.numpy(), nref)
+    for r in range(R):
+        k = int(nref[r])
+        for key in ref:
+            got = pk[key].numpy()[r * S:r * S + k]
+            if key == "id":
+                got = got.view(np.uint64)
+            assert np.array_equal(got, ref[key][r * S:r * S + k]), (r, key)
+    # load in place from the pinned arrays into fresh contexts, read back again
+    fresh = [crmc.Context(w) for w in ws]
+    bf = crmc.Batch(fresh)
+    bf.load_packed(S, {k: pk[k].data_ptr() for k in ("xyz", "vel", "type", "cls", "state")}, n.data_ptr())
+    back = dict(xyz=np.zeros((R * S, 3), np.float32), type=np.zeros(R * S, np.int32), state=np.zeros(R * S, np.int8))
+    nb = np.zeros(R, np.int64)
+    bf.state_packed(S, back, nb)
+    assert np.array_equal(nb, nref)
+    for r in range(R):
+        k = int(nref[r])
+        for key in back:
+            assert np.array_equal(back[key][r * S:r * S + k], ref[key][r * S:r * S + k]), (r, key)
