@@ -375,11 +375,11 @@ int cr_batch_load(cr_batch *b, const cr_load_args *args);
  * batch (contexts above 16,384 particles of capacity take the per-context
  * path).  cr_batch_load_packed is cr_load of every replica from such arrays
  * (n[r] in; vel may be NULL), checked on the device like cr_load; its
- * per-particle errors come at the next synchronising call.  Arrays the GPU
- * can address (device memory, pinned host memory) are written or read in
- * place by the kernels, others go through device staging with one copy each;
- * a load reads its arrays asynchronously, so they must not change before the
- * stream has passed the load. */
+ * per-particle errors come at the next synchronising call.  A load reads
+ * arrays the GPU can address (device memory, pinned host memory) in place,
+ * others through device staging with one copy each; it reads them
+ * asynchronously, so they must not change before the stream has passed the
+ * load.  A read writes through device staging and one copy per array. */
 typedef struct {
   int64_t stride;
   float *xyz, *vel;

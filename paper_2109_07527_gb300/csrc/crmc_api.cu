@@ -1577,11 +1577,13 @@ extern "C" int cr_batch_state_packed(cr_batch *b, cr_batch_packed *p) {
   int rc = ensure_packed(b, S);
   if (rc != CR_OK) return rc;
   cudaStream_t s = b->ctx[0]->stream;
-  // arrays the GPU can address are written in place (no staging, no copy)
-  float *zx = device_view(p->xyz), *zv = device_view(p->vel);
-  uint64_t *zi = device_view(p->id);
-  int32_t *zt = device_view(p->type), *zc = device_view(p->cls);
-  int8_t *zs = device_view(p->state);
+  // outputs go through the device staging and one bulk copy per array (the
+  // kernels' scattered small records written straight into pinned host
+  // memory measured slower than the staging and the copy)
+  float *zx = nullptr, *zv = nullptr;
+  uint64_t *zi = nullptr;
+  int32_t *zt = nullptr, *zc = nullptr;
+  int8_t *zs = nullptr;
   for (size_t r = 0; r < R; ++r) {
     cr_ctx *c = b->ctx[r];
     StateBufs &B = b->h_sbufs[r];

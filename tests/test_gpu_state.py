@@ -228,9 +228,9 @@ def test_packed_batch_state_and_load(crmc):
     assert np.all(n2 > 0)
 
 
-def test_packed_batch_io_in_place_on_pinned_memory(crmc):
-    """Pinned host arrays are written and read by the kernels in place (no
-    staging copies); the results equal those through pageable arrays."""
+def test_packed_batch_io_on_pinned_memory(crmc):
+    """Pinned host arrays (read in place by the load kernels) give the same
+    results as pageable arrays, both ways."""
     torch = pytest.importorskip("torch")
     ws = [W.config2(seed=14, scale=0.5, pH=pH) for pH in (4.0, 6.0)]
     ctxs = [crmc.Context(w) for w in ws]
