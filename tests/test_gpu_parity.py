@@ -37,8 +37,11 @@ def _parity(crmc, w, sweeps, seed, **kw):
 
 def test_philox_device_matches_oracle(crmc):
     out = crmc.philox(0, 7, 11, 3, 0xDEADBEEF, 0x12345678, 4096)
-    for i in (0, 1, 17, 4095):
+    for i in range(4096):  # every block of the range, bit for bit
         assert out[i].tolist() == oracle.philox([i, 7, 11, 3], [0xDEADBEEF, 0x12345678]).tolist()
+    hi = crmc.philox(0xFFFFF000, 0xFFFFFFFF, 0x80000000, 6, 0xFFFFFFFF, 0, 4096)  # counter words near overflow
+    for i in range(0, 4096, 7):
+        assert hi[i].tolist() == oracle.philox([0xFFFFF000 + i, 0xFFFFFFFF, 0x80000000, 6], [0xFFFFFFFF, 0]).tolist()
     kat = crmc.philox(0, 0, 0, 0, 0, 0, 1)[0]
     assert kat.tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
 
