@@ -943,6 +943,13 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
   M.n_perm = ctx->n_input;
   M.fene_K = (float)ctx->fene_K;
   M.inv_R02 = (float)(1.0 / (ctx->fene_R0 * ctx->fene_R0));
+  // the longest pair range (Coulomb cutoff or WCA cutoff), with a margin far
+  // above the FP32 rounding of positions and cell boxes
+  double reach2 = (double)ctx->P.rc2;
+  for (int i = 0; i < 16; ++i)
+    if (ctx->P.wca[i].on) reach2 = std::max(reach2, (double)ctx->P.wca[i].wcut2);
+  const double reach = std::sqrt(reach2) * 1.001 + 1e-3;
+  M.reach2 = (float)(reach * reach);
   return M;
 }
 

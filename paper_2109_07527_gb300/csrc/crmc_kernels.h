@@ -18,6 +18,7 @@ struct MdParams {
   const int *plist;        // occupied slots (filled by the launcher)
   const int *n_particles;  // entries of plist
   int max_particles;       // capacity of plist
+  float reach2;            // squared interaction reach with a margin (cells beyond it are skipped)
   long long *fsum;         // [3 max_particles] pair-force sums (2^-24 fixed point) handed to the
                            // per-particle finish kernel; null: the force kernel finishes itself
 };

@@ -188,6 +188,14 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
       const int jc = jx + nc * (jy + nc * jz);
       base = jc * cap;
       n = P.cnt[jc];
+      if (FLAT && n > 0) {  // a cell whose box lies beyond the interaction reach holds no partner
+        const float x0 = (float)(cx + ox - h) * P.af, y0 = (float)(cy + oy - h) * P.af,
+                    z0 = (float)(cz + oz - h) * P.af;
+        const float ex = fmaxf(0.0f, fmaxf(x0 - pi.x, pi.x - (x0 + P.af)));
+        const float ey = fmaxf(0.0f, fmaxf(y0 - pi.y, pi.y - (y0 + P.af)));
+        const float ez = fmaxf(0.0f, fmaxf(z0 - pi.z, pi.z - (z0 + P.af)));
+        if (ex * ex + ey * ey + ez * ez > M.reach2) n = 0;
+      }
     }
     int x = n;
 #pragma unroll
