@@ -155,6 +155,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ uint16_t to_bf16(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float from_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
+// Column sums of a warp's 32 x 16 chunk (row = lane) through the warp's
+// shared-memory tile tb (32 x 17 floats, conflict-free): every lane stores its
+// 16 values, lanes l and l + 16 add rows 0-15 and 16-31 of column l & 15, one
+// shuffle joins the halves.  The sums are valid in lanes 0-15.
+__device__ __forceinline__ float chunk_colsum(float *tb, const float (&x)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = x[j];
+  __syncwarp();
+  const int col = lane & 15, r0 = (lane >> 4) * 16;
+  float sum = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) sum += tb[(r0 + r) * 17 + col];
+  sum += __shfl_down_sync(0xffffffffu, sum, 16);
+  __syncwarp();  // the tile is reused by the next chunk
+  return sum;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -255,6 +273,9 @@ __global__ void __launch_bounds__(128, 1)
 
   const int row = m0 + warp * 32 + lane;
   const bool rv = row < M;
+  // the epilogue's column-sum tile of this warp: in the operand ring, whose
+  // copies and MMAs have all completed once the accumulator is ready
+  float *tbuf = (float *)sA + warp * 32 * 17;
   __syncwarp();
   if (!fail && nk > 0) {
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
@@ -298,6 +319,7 @@ __global__ void __launch_bounds__(128, 1)
         }
         const uint16_t *hb = (const uint16_t *)raw;
         uint16_t gb[16];
+        float gv[16], wv[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c0 + j;
@@ -305,10 +327,14 @@ __global__ void __launch_bounds__(128, 1)
           const float g = h > 0.0f ? dy * from_bf16(E.w4[n]) : 0.0f;
           gb[j] = to_bf16(g);
           if (rv) E.g3T[(size_t)n * E.ldt3 + row] = gb[j];
-          const float sg = warp_sum_f(g), sw = warp_sum_f(dy * h);
-          if (lane == 0) {
-            atomicAdd(&colacc[n - n0], sg);
-            atomicAdd(&colacc[BN + n - n0], sw);
+          gv[j] = g;
+          wv[j] = dy * h;
+        }
+        {  // column sums of g3 (gb3) and of dy h3 (gw4)
+          const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
+          if (lane < 16) {
+            atomicAdd(&colacc[c0 + lane], sg);
+            atomicAdd(&colacc[BN + c0 + lane], sw);
           }
         }
         if (rv) {
@@ -354,6 +380,7 @@ __global__ void __launch_bounds__(128, 1)
           }
           memcpy(mrow, mr, sizeof(mrow));
         }
+        float xs[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = n0 + c0 + j;
@@ -363,11 +390,14 @@ __global__ void __launch_bounds__(128, 1)
           } else {  // EPI_MASK
             const float mk = rv ? from_bf16(mrow[j]) : 0.0f;
             x = mk > 0.0f ? v[j] : 0.0f;
-            const float cs = warp_sum_f(rv ? x : 0.0f);
-            if (lane == 0) atomicAdd(&colacc[n - n0], cs);
           }
+          xs[j] = rv ? x : 0.0f;
           hb[j] = to_bf16(x);
           if (rv && E.outT) E.outT[(size_t)n * E.ldt + row] = hb[j];
+        }
+        if (EPI == EPI_MASK) {  // column sums of the masked values
+          const float cs = chunk_colsum(tbuf, xs);
+          if (lane < 16) atomicAdd(&colacc[c0 + lane], cs);
         }
         if (rv && E.out) {
           uint4 *o = (uint4 *)(E.out + (size_t)row * E.ldo + n0 + c0);
