@@ -173,6 +173,31 @@ __device__ __forceinline__ float chunk_colsum(float *tb, const float (&x)[16]) {
   return sum;
 }
 
+// Transposed BF16 store of a warp's 32 x 16 chunk (row = lane): out^T rows
+// n .. n + 15, columns row0 .. row0 + 31, through the warp's shared-memory tile
+// tb (16 x 40 halves): two 16-byte stores per lane instead of 16 two-byte
+// stores.  A warp with rows past M stores element by element.
+__device__ __forceinline__ void store_chunk_T(uint16_t *tb, const uint16_t (&h)[16], uint16_t *outT, int ldt, int n,
+                                              int row0, int M) {
+  const int lane = threadIdx.x & 31;
+  if (row0 + 32 > M) {
+    const int row = row0 + lane;
+    if (row < M)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) outT[(size_t)(n + j) * ldt + row] = h[j];
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) tb[j * 40 + lane] = h[j];
+  __syncwarp();
+  const int j = lane >> 1, half = lane & 1;
+  const uint4 *src = (const uint4 *)(tb + j * 40 + half * 16);
+  uint4 *dst = (uint4 *)(outT + (size_t)(n + j) * ldt + row0 + half * 16);
+  dst[0] = src[0];
+  dst[1] = src[1];
+  __syncwarp();  // the tile is reused by the next chunk
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -276,6 +301,7 @@ __global__ void __launch_bounds__(128, 1)
   // the epilogue's column-sum tile of this warp: in the operand ring, whose
   // copies and MMAs have all completed once the accumulator is ready
   float *tbuf = (float *)sA + warp * 32 * 17;
+  uint16_t *tb16 = (uint16_t *)((float *)sA + 4 * 32 * 17) + warp * 16 * 40;
   __syncwarp();
   if (!fail && nk > 0) {
     const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
@@ -326,10 +352,10 @@ __global__ void __launch_bounds__(128, 1)
           const float h = from_bf16(hb[j]);
           const float g = h > 0.0f ? dy * from_bf16(E.w4[n]) : 0.0f;
           gb[j] = to_bf16(g);
-          if (rv) E.g3T[(size_t)n * E.ldt3 + row] = gb[j];
           gv[j] = g;
           wv[j] = dy * h;
         }
+        store_chunk_T(tb16, gb, E.g3T, E.ldt3, n0 + c0, m0 + warp * 32, M);
         {  // column sums of g3 (gb3) and of dy h3 (gw4)
           const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
           if (lane < 16) {
@@ -393,8 +419,8 @@ __global__ void __launch_bounds__(128, 1)
           }
           xs[j] = rv ? x : 0.0f;
           hb[j] = to_bf16(x);
-          if (rv && E.outT) E.outT[(size_t)n * E.ldt + row] = hb[j];
         }
+        if (E.outT) store_chunk_T(tb16, hb, E.outT, E.ldt, n0 + c0, m0 + warp * 32, M);
         if (EPI == EPI_MASK) {  // column sums of the masked values
           const float cs = chunk_colsum(tbuf, xs);
           if (lane < 16) atomicAdd(&colacc[c0 + lane], cs);
