@@ -98,7 +98,6 @@ cudaError_t launch_load(const SysParams &P, const LoadBufs &I, const RebuildBufs
 // neutrality), four launches
 cudaError_t launch_load_batch(const SysParams *d_reps, const LoadJob *d_jobs, int n_rep, int max_n, int max_cells,
                               cudaStream_t s);
-cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s);
 // state read-back: mark the slots (ion count into *B.n_ions), then, with the
 // counts known, place the input ids, sort the ions (bits [0, end_bit) of their
 // keys), write the arrays and clear the marks (adds the kernels it launched to

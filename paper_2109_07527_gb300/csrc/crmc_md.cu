@@ -377,16 +377,6 @@ __global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n
   rebuild_sort_cell(P, B, perm_slot, n_perm, (blockIdx.x * blockDim.x + threadIdx.x) >> 5);
 }
 
-// refresh the slot of every permanent particle
-__global__ void k_perm_slots(SysParams P, int *perm_slot, int n_perm) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= P.ncell * P.cap) return;
-  const int c = g / P.cap;
-  if (g - c * P.cap >= P.cnt[c]) return;
-  const unsigned long long id = P.pid[g];
-  if (id < (unsigned long long)n_perm) perm_slot[id] = g;
-}
-
 // the loaded configuration must be neutral (kind counts of the load)
 __global__ void k_load_neutral(SysParams P) {
   if (threadIdx.x != 0) return;
@@ -521,12 +511,6 @@ cudaError_t launch_load_batch(const SysParams *d_reps, const LoadJob *d_jobs, in
   if (max_n > 0) k_load_scatter_batch<<<dim3((max_n + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
   k_rebuild_sort_batch<<<dim3((max_cells * 32 + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
   k_load_neutral_batch<<<n_rep, 32, 0, s>>>(d_reps);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_perm_slots(const SysParams &P, int *perm_slot, int n_perm, cudaStream_t s) {
-  const int n = P.ncell * P.cap;
-  k_perm_slots<<<(n + 255) / 256, 256, 0, s>>>(P, perm_slot, n_perm);
   return cudaGetLastError();
 }
 
