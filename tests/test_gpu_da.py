@@ -122,3 +122,15 @@ def test_da_rejects_unsupported_geometry(crmc):
 def test_da_parity_with_lists_beyond_shared_memory(crmc):
     w = W.config2(seed=9, scale=0.5)
     _da_parity(crmc, w, W.random_mlp(seed=18, out_gain=1.5), 2, 13, list_capacity=8, halo_capacity=64)
+
+
+def test_da_parity_config5_full_size(crmc):
+    """The large delayed-acceptance system at full size (100 chains x 200, L =
+    250, ~70 000 particles), one sweep of one trial per domain (8000 trials):
+    features, dE~, stage decisions and charge states against the oracle."""
+    w = W.config5(seed=3)
+    w.params["trials_per_domain"] = 1
+    g, r, do, ties = _da_parity(crmc, w, W.random_mlp(seed=31, out_gain=1.0), 1, 5)
+    st = r["da"]["stage"]
+    assert (st == 1).sum() > 0 and (st == 2).sum() > 0
+    assert ties <= 2
