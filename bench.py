@@ -17,8 +17,10 @@ BF16 tensor peak), then the same batched cycle with DA sweeps.  Inputs are
 resident in HBM; L2 is flushed (256 MB write) between timed steps.
 
 --impl reference times the CPU oracle on the same workload (rank 0 only).
-Under torchrun each rank runs an independent replica (no collective on the
-data path; scaling "weak").
+Under torchrun each rank runs its own 13-replica batch of the same workload
+with its own seeded structure (no collective on the data path; scaling
+"weak"); the timed regions are bracketed by barriers and the slowest rank's
+time divides the units of all ranks.
 """
 import argparse
 import hashlib
@@ -62,6 +64,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, device):
+    """The largest value of x over all ranks (every rank must call it); x
+    itself when no process group is initialised or it has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed (each rank does the
+    same fixed work, weak scaling) over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def workload(rank):
@@ -408,11 +428,8 @@ def run_ours(args):
     g0.set_timing(False)
     for g in ctxs:
         g.check()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = per_step * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms, "cuda")
+    value = job_rate(per_step * args.steps, world, ms / 1e3)
     counts = [g.counts() for g in ctxs]
     L = float(ws[0].params["box_L"])
     rc = float(ws[0].params["rc"])
@@ -467,7 +484,7 @@ def run_ours(args):
     # uploads every replica's configuration from pinned host memory, runs the
     # batched cycle and reads every replica's state back
     e2e = None
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e:
         # the replicas' configurations live in packed pinned host arrays
         # (replica r from r * stride; allocated once, as a caller coupling the
         # library to its own host-side code would): cr_batch_load_packed
@@ -488,6 +505,8 @@ def run_ours(args):
         e2e_steps = 20
         h2d = d2h = 0
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t0 = time.perf_counter()
         for s in range(e2e_steps):
             batch.load_packed(stride, load_ptr, nbuf.data_ptr())
@@ -498,8 +517,8 @@ def run_ours(args):
             batch.state_packed(stride, ptr, nbuf.data_ptr())
             d2h += R * stride * (12 + 12 + 8 + 4 + 1 + 4) + 12 * R
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        e2e = {"value": per_step * e2e_steps / te, "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
+        te = max_over_ranks(time.perf_counter() - t0, "cuda")
+        e2e = {"value": job_rate(per_step * e2e_steps, world, te), "unit": "trials/s", "h2d_bytes_per_step": h2d // e2e_steps,
                "d2h_bytes_per_step": d2h // e2e_steps, "steps": e2e_steps,
                "note": "per step: cr_batch_load_packed of the 13 replicas from packed pinned host arrays + the batched "
                        "cycle (1e4 trials per replica inside one MD step) + cr_batch_state_packed readback of every "
@@ -520,7 +539,7 @@ def run_ours(args):
                       "parallelism": f"{world} GPU(s), independent replica batches"},
            "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e, "plain": plain,
            "surrogate_da": da,
-           "md_cr_cycles_per_s": args.steps * world / (ms / 1e3)}
+           "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"], alpha_o = cpu_baseline(workload(0))
         out["alpha_check"] = alpha_check(crmc, workload(0), alpha_o)
