@@ -51,13 +51,16 @@ def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8):
     with np.errstate(invalid="ignore"):
         err = np.abs(lg["dE"] - lo["dE"])
     tol = de_tol(lo)
-    badi = np.flatnonzero(ok & (err > tol))
+    # written as "not within" so that a NaN or an infinity where the oracle
+    # has a finite value (every counted trial) fails
+    badi = np.flatnonzero(ok & ~(err <= tol))
     assert len(badi) == 0, "dE out of tolerance:\n" + "\n".join(
         f"  trial {i}: move {lo['move'][i]} gpu dE {lg['dE'][i]!r} oracle dE {lo['dE'][i]!r} S {lo['S'][i]!r} "
         f"gpu S {lg['S'][i]!r} err {err[i]:.3e} tol {tol[i]:.3e}" for i in badi[:8])
-    lt = np.abs(lg["lnA"] - lo["lnA"])
+    with np.errstate(invalid="ignore"):
+        lt = np.abs(lg["lnA"] - lo["lnA"])
     ltol = tol + 1e-12 * np.abs(lo["lnA"])
-    badl = np.flatnonzero(ok & (lt > ltol))
+    badl = np.flatnonzero(ok & ~(lt <= ltol))
     assert len(badl) == 0, "lnA out of tolerance:\n" + "\n".join(
         f"  trial {i}: move {lo['move'][i]} gpu lnA {lg['lnA'][i]!r} oracle lnA {lo['lnA'][i]!r} "
         f"dE {lg['dE'][i]!r}/{lo['dE'][i]!r} tol {ltol[i]:.3e}" for i in badl[:8])
