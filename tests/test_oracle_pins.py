@@ -164,6 +164,44 @@ def test_henderson_hasselbalch_limit_at_high_salt():
     assert abs(mean - a_ex) <= 4.0 * se, (mean, se, a_ex)
 
 
+def two_state_ratio(lnK, zp, zm, m_max=400):
+    """P(ionised) / P(neutral) of one acid site with ideal reservoir ions,
+    summed term by term from the grand-canonical weights of Eq. (QQ) with
+    E = 0: K^k * sum over anion numbers m of zp^(m+k) zm^m / ((m+k)! m!),
+    neutrality fixing the cation number at m + k."""
+    def lse(k):
+        t = [(m + k) * math.log(zp) + m * math.log(zm) - math.lgamma(m + k + 1) - math.lgamma(m + 1)
+             for m in range(m_max)]
+        mx = max(t)
+        return mx + math.log(sum(math.exp(x - mx) for x in t))
+    return math.exp(lnK + lse(1) - lse(0))
+
+
+@pytest.mark.parametrize("pH,pIS_minus", [(5.0, 2.0), (4.5, 2.5), (5.5, 1.5)])
+def test_one_site_two_state_ratio(pH, pIS_minus):
+    """A single acid site with ghost ions: the time fraction spent ionised
+    against the exact two-state ratio (the ion sums done term by term, not
+    through a Bessel function), also with an asymmetric reservoir."""
+    L, sig = 40.0, 0.355
+    w = W.ideal(n_sites=1, L=L, pH=pH, pKa=5.0, pIS=2.0, n_pairs=20, seed=6, schedule=1, trials_per_domain=256)
+    w.params["pIS_minus"] = pIS_minus
+    o = oracle.Oracle(w)
+    ch = o.chem()
+    v = 0.602214076 * (L * sig) ** 3
+    r = two_state_ratio(math.log(10.0) * (pH - 5.0), v * 10 ** -ch["pIX_plus"], v * 10 ** -ch["pIX_minus"])
+    p_ex = r / (1.0 + r)
+    tps = o.trials_per_sweep
+    o.sweep(tps * 40, 1)
+    B, per = 30, 16384
+    f = []
+    for b in range(B):
+        h = o.sweep(tps * (per // tps), 500 + b, hist_n=1)["hist"]
+        f.append(h[1] / h.sum())
+    mean, se = float(np.mean(f)), float(np.std(f, ddof=1) / math.sqrt(B))
+    assert abs(mean - p_ex) <= max(4.0 * se, 0.003), (mean, se, p_ex)
+    assert abs(mean - p_ex) <= 0.01
+
+
 @pytest.mark.parametrize("pH,expect", [(1.0, 0.0), (10.0, 1.0)])
 def test_titration_limits(pH, expect):
     w = W.ideal(n_sites=20, pH=pH, pKa=5.0, n_pairs=10, seed=4, schedule=1, trials_per_domain=256)
