@@ -245,6 +245,7 @@ class Context:
     def __init__(self, w, schedule=None, trials_per_domain=None, domain_cells=None, cell_capacity=0, stream=None,
                  list_capacity=0, halo_capacity=0):
         lib = _lib()
+        self._nbatch = 0  # live batches that hold this context (it must outlive them)
         q = w.params
         s = cr_system()
         self._keep = dict(xyz=np.ascontiguousarray(w.xyz, np.float32), type=np.ascontiguousarray(w.type, np.int32),
@@ -282,12 +283,15 @@ class Context:
         self.capacity = w.capacity
 
     def close(self):
+        if getattr(self, "_nbatch", 0):
+            raise RuntimeError("the context is part of a live Batch: close the batch first")
         if getattr(self, "_h", None):
             self._lib.cr_destroy(self._h)
             self._h = None
 
     def __del__(self):
-        self.close()
+        if not getattr(self, "_nbatch", 0):
+            self.close()
 
     @property
     def info(self):
@@ -436,6 +440,8 @@ class Batch:
         _chk(_lib().cr_batch_create(C.byref(h), arr, len(self.contexts)), "cr_batch_create")
         self._h = h
         self._lib = _lib()
+        for c in self.contexts:
+            c._nbatch += 1
 
     def sweep(self, n_sweeps, seed):
         _chk(self._lib.cr_batch_sweep(self._h, int(n_sweeps), int(seed)), "cr_batch_sweep")
@@ -508,6 +514,8 @@ class Batch:
         if getattr(self, "_h", None):
             self._lib.cr_batch_destroy(self._h)
             self._h = None
+            for c in self.contexts:
+                c._nbatch -= 1
 
     def __del__(self):
         self.close()
