@@ -134,28 +134,40 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    def __init__(self):
+    """nvidia-smi samples of the SM clock and the throttle reasons every
+    `period_ms`; stop() summarises the samples received inside [t0, t1]
+    (host perf_counter times bracketing the timed region)."""
+
+    def __init__(self, period_ms=50, smi="nvidia-smi"):
         self.proc = None
         self.rows = []
+        self.period_ms = period_ms
+        self.smi = smi
 
-    def start(self):
+    def start(self, wait_s=5.0):
+        """Start sampling and wait (at most wait_s) for the first sample, so
+        that the sampler is live when the timed region begins."""
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen([self.smi, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", str(self.period_ms)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        end = time.perf_counter() + wait_s
+        while not self.rows and time.perf_counter() < end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
-    def stop(self, gpu_index):
+    def stop(self, gpu_index, t0=None, t1=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -164,7 +176,11 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        rows = [r for r in self.rows if len(r) >= 9 and r[0] == str(gpu_index)]
+        mine = [(t, r) for t, r in self.rows if len(r) >= 9 and r[0] == str(gpu_index)]
+        inside = [r for t, r in mine if (t0 is None or t >= t0) and (t1 is None or t <= t1)]
+        # a region shorter than the period: the first sample after its start
+        after = [r for t, r in mine if t0 is not None and t >= t0][:1]
+        rows = inside or after
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -176,7 +192,8 @@ class ClockSampler:
                 if v.strip().lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(rows), "samples_in_region": len(inside),
+                "period_ms": self.period_ms}
 
 
 def cpu_baseline(w, sample_sweeps=20):
@@ -407,11 +424,11 @@ def run_ours(args):
         batch.md_end(dt, gamma, 1000 + s)
     for g in ctxs:
         g.check()
+    clocks = ClockSampler()
+    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     g0 = ctxs[0]
-    clocks = ClockSampler()
-    clocks.start()
     g0.set_timing(True)
     g0.timing(reset=True)
 
@@ -420,10 +437,12 @@ def run_ours(args):
         batch.sweep(1, 100 + s)
         batch.md_end(dt, gamma, 5000 + s)
 
+    t_region0 = time.perf_counter()
     ms = time_steps(step, args.steps, stream, flush)
+    t_region1 = time.perf_counter()
     if world > 1:
         torch.distributed.barrier()
-    cl = clocks.stop(local)
+    cl = clocks.stop(local, t_region0, t_region1)
     tm = g0.timing(reset=True)
     g0.set_timing(False)
     for g in ctxs:
