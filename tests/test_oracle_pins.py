@@ -223,6 +223,28 @@ def test_pIX_grouping_formula():
     assert ch["pIX_plus"] == 7.0 and ch["pIX_minus"] == 7.0
 
 
+@pytest.mark.parametrize("pH,pIS", [(2.0, 2.0), (4.0, 1.0), (7.0, 2.0), (9.5, 3.0), (12.0, 1.5)])
+def test_pIX_from_reservoir_species(pH, pIS):
+    """The combined ion activities from the reservoir's species (App. C): salt
+    S+/S- at 10^-pIS, H+ and OH- at 10^-pH and 10^-pOH, and the acid anion
+    (or base cation) that the reservoir's neutrality requires at a
+    non-neutral pH.  Grouping species into one type adds their activities
+    (App. B, Eq. mux), so X+ = everything positive and X- = everything
+    negative.  The oracle's pI_X+ and pI_X- must be those activities."""
+    pOH = 14.0 - pH
+    s, h, oh = 10 ** -pIS, 10 ** -pH, 10 ** -pOH
+    extra_anion = max(h - oh, 0.0)   # e.g. Cl- of HCl at pH < 7
+    extra_cation = max(oh - h, 0.0)  # e.g. Na+ of NaOH at pH > 7
+    pos = [s, h, extra_cation]
+    neg = [s, oh, extra_anion]
+    assert abs(sum(pos) - sum(neg)) <= 1e-15 * sum(pos)  # the reservoir is neutral
+    a_plus, a_minus = sum(pos), sum(neg)
+    w = W.ideal(n_sites=4, pH=pH, pIS=pIS, n_pairs=2, seed=1, schedule=1, trials_per_domain=4)
+    ch = oracle.Oracle(w).chem()
+    assert abs(ch["pIX_plus"] + math.log10(a_plus)) < 1e-12
+    assert abs(ch["pIX_minus"] + math.log10(a_minus)) < 1e-12
+
+
 # ---------------------------------------------------------------- exact enumeration
 def dsf_energy_states(w, n):
     """E(s) for all 2^n site states from the DSF definition (scipy erfc)."""
