@@ -87,6 +87,29 @@ def test_wca_values():
     assert oracle.wca_u(1.0, 1.0, 0.0, 0.5) > 16000.0
 
 
+def test_expanded_wca_shifts_follow_table_II():
+    """The nanoparticle workload's expanded-WCA table against the stored Table
+    II rules, and the oracle's potential with those shifts: U = eps at
+    r = Delta + sigma, zero from r_c* = Delta + 2^(1/6) sigma on."""
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "table2_expanded_wca.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    R, r_ion = 5.0, 0.5
+    rule = {(a, b): eval(f, {"__builtins__": {}}, dict(R=R, r=r_ion)) for a, b, f in rows}
+    w = W.config3(separation=12.0, seed=1, L=60.0, n_sites=50)
+    p = w.params
+    cls = {"ion": 0, "particle": 1}  # short-range classes of free ions and cores
+    c = 2.0 ** (1.0 / 6.0)
+    for (a, b), delta in rule.items():
+        for i, j in ((cls[a], cls[b]), (cls[b], cls[a])):
+            assert p["wca_del"][4 * i + j] == delta, (a, b)
+            assert p["wca_on"][4 * i + j] == 1
+            eps, sig = p["wca_eps"][4 * i + j], p["wca_sig"][4 * i + j]
+            assert abs(oracle.wca_u(eps, sig, delta, delta + sig) - eps) < 1e-12
+            assert oracle.wca_u(eps, sig, delta, delta + c * sig + 1e-9) == 0.0
+            assert oracle.wca_u(eps, sig, delta, delta + c * sig - 1e-3) > 0.0
+    assert rule[("particle", "particle")] == 9.0 and rule[("particle", "ion")] == 4.5
+
+
 # ---------------------------------------------------------------- closed forms
 def exact_alpha(n, lnK, ln_zp, ln_zm):
     """<k>/n for P(k) ~ C(n,k) K^k (zp/zm)^(k/2) I_k(2 sqrt(zp zm))."""
