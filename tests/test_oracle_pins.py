@@ -225,6 +225,48 @@ def test_one_site_two_state_ratio(pH, pIS_minus):
     assert abs(mean - p_ex) <= 0.01
 
 
+@pytest.mark.parametrize("schedule", [1, 0])
+def test_ideal_salt_pair_distribution(schedule):
+    """A box of ghost ions without sites: only the salt moves (Eqs. MCsaltf,
+    MCmetro2) act, and the pair number N follows P(N) ~ (z+ z-)^N / (N!)^2
+    (Eq. QQ with E = 0 and N+ = N- = N), with an asymmetric reservoir.  Under
+    the coloured schedule the domain-local rule must give the same global
+    distribution."""
+    L, sig = 40.0, 0.355
+    w = W.ideal(n_sites=0, L=L, pH=7.0, pIS=2.0, n_pairs=10, seed=3, schedule=schedule,
+                trials_per_domain=256 if schedule == 1 else 4)
+    w.params["pIS_minus"] = 2.3
+    o = oracle.Oracle(w)
+    ch = o.chem()
+    v = 0.602214076 * (L * sig) ** 3
+    ln_zz = math.log(v * 10 ** -ch["pIX_plus"]) + math.log(v * 10 ** -ch["pIX_minus"])
+    N = np.arange(80)
+    logP = N * ln_zz - 2.0 * gammaln(N + 1)
+    P = np.exp(logP - logP.max())
+    P /= P.sum()
+    tps = o.trials_per_sweep
+    o.sweep(tps * 20, 1)
+    B, per = 30, 16384
+    H = []
+    for b in range(B):
+        c = []
+        for r in range(per // tps):
+            o.sweep(tps, 100 + 1000 * b + r)
+            k = o.counts()
+            assert k["n_Xp"] == k["n_Xm"]
+            c.append(k["n_Xm"])
+        H.append(np.bincount(c, minlength=len(N))[:len(N)] / len(c))
+    H = np.array(H)
+    mean_N = (H * N).sum(1)
+    m, se = mean_N.mean(), mean_N.std(ddof=1) / math.sqrt(B)
+    m_ex = float((P * N).sum())
+    assert abs(m - m_ex) <= max(4.0 * se, 0.05), (m, se, m_ex)
+    hm, hse = H.mean(0), H.std(0, ddof=1) / math.sqrt(B)
+    big = P > 0.02
+    z = np.abs(hm - P)[big] / np.maximum(hse[big], 2e-3)
+    assert z.max() < 5.0, (z.max(), hm[big], P[big])
+
+
 @pytest.mark.parametrize("pH,expect", [(1.0, 0.0), (10.0, 1.0)])
 def test_titration_limits(pH, expect):
     w = W.ideal(n_sites=20, pH=pH, pKa=5.0, n_pairs=10, seed=4, schedule=1, trials_per_domain=256)
