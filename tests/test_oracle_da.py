@@ -284,7 +284,32 @@ def _stage_stats(w, mlp, sweeps, seed):
     return dict(stage1_reject=float(np.mean(st[ev] == 1)), exact=int(np.sum(st[ev] == 2)), trials=int(ev.sum()))
 
 
-def test_trained_surrogate_gain():
+CLIP = 5.0
+
+
+@pytest.fixture(scope="module")
+def recorded_pairs():
+    """Training pairs from one half-size polyelectrolyte box (32 sweeps) and
+    held-out pairs from a second (8 sweeps), targets clipped at 5 kT; both
+    recorded with a zero surrogate (stage 1 = the chemical factor alone)."""
+    zero = W.random_mlp(seed=23, out_gain=0.0)
+    X, y = _da_pairs(W.config2(seed=6, scale=0.5), zero, 32, 17)
+    Xh, yh = _da_pairs(W.config2(seed=7, scale=0.5), zero, 8, 19)
+    return X, np.clip(y, -CLIP, CLIP), Xh, np.clip(yh, -CLIP, CLIP)
+
+
+def _train(X, y, n_hid=128, steps=100):
+    from oracle import mlp_oracle as M
+    X2, y2 = np.concatenate([X, -X]).astype(np.float64), np.concatenate([y, -y])
+    p = M.params_from_bf16(W.random_mlp(seed=24, gain=0.5, n_hid=n_hid), W.bf16_to_f32)
+    st = M.adam_init(p)
+    for _ in range(steps):
+        _, g = M.loss_and_grads(p, X2, y2)
+        p = M.adam_step(p, g, st, lr=2e-3)
+    return p
+
+
+def test_trained_surrogate_gain(recorded_pairs):
     """What a trained network gains over the method without it (a zero
     surrogate, whose stage 1 is the chemical factor alone).  Trained by the
     float64 reference on ~12,000 pairs recorded in one polyelectrolyte box
@@ -297,27 +322,39 @@ def test_trained_surrogate_gain():
     (within the sampling noise, so it is only checked not to grow).  Both
     chains stay exact; the delayed acceptance only changes how often the
     exact sum runs."""
-    from oracle import mlp_oracle as M
-    clip = 5.0
-    zero = W.random_mlp(seed=23, out_gain=0.0)
-    X, y = _da_pairs(W.config2(seed=6, scale=0.5), zero, 32, 17)
-    y = np.clip(y, -clip, clip)
-    X2, y2 = np.concatenate([X, -X]).astype(np.float64), np.concatenate([y, -y])
-    p = M.params_from_bf16(W.random_mlp(seed=24, gain=0.5), W.bf16_to_f32)
-    st = M.adam_init(p)
-    for _ in range(100):
-        _, g = M.loss_and_grads(p, X2, y2)
-        p = M.adam_step(p, g, st, lr=2e-3)
-    trained = _mlp_from_params(p)
+    X, y, Xh, yh = recorded_pairs
+    trained = _mlp_from_params(_train(X, y))
     w2 = W.config2(seed=7, scale=0.5)
-    Xh, yh = _da_pairs(w2, zero, 8, 19)
-    yh = np.clip(yh, -clip, clip)
     o = oracle.Oracle(w2)
     o.set_surrogate(trained)
     pred = np.array([o.surrogate(f) for f in Xh])
     mse_trained, mse_zero = float(np.mean((yh - pred) ** 2)), float(np.mean(yh ** 2))
     assert mse_trained < 0.95 * mse_zero, (mse_trained, mse_zero)
     assert np.corrcoef(pred, yh)[0, 1] > 0.2
+    zero = W.random_mlp(seed=23, out_gain=0.0)
     s0 = _stage_stats(w2, zero, 16, 21)
     s1 = _stage_stats(w2, trained, 16, 21)
     assert s1["exact"] / s1["trials"] <= s0["exact"] / s0["trials"] + 0.02, (s0, s1)
+
+
+def test_surrogate_error_is_set_by_the_features(recorded_pairs):
+    """On the same pairs, a network of width 32 and an antisymmetric linear
+    least-squares fit of the 48 features reach the held-out error of the
+    width-128 network (within 0.03 kT^2, all below no surrogate): the
+    features, not the width, limit what the surrogate can predict."""
+    from oracle import mlp_oracle as M
+    X, y, Xh, yh = recorded_pairs
+    Xh64 = Xh.astype(np.float64)
+
+    def mse(p):
+        a, _ = M.forward(p, Xh64)
+        b, _ = M.forward(p, -Xh64)
+        return float(np.mean((yh - 0.5 * (a - b)) ** 2))
+
+    m128, m32 = mse(_train(X, y, 128)), mse(_train(X, y, 32))
+    X2, y2 = np.concatenate([X, -X]).astype(np.float64), np.concatenate([y, -y])
+    coef, *_ = np.linalg.lstsq(X2, y2, rcond=None)
+    mlin = float(np.mean((yh - Xh64 @ coef) ** 2))
+    m0 = float(np.mean(yh ** 2))
+    assert max(m128, m32, mlin) < 0.95 * m0, (m128, m32, mlin, m0)
+    assert abs(m32 - m128) < 0.03 and abs(mlin - m128) < 0.03, (m128, m32, mlin)
