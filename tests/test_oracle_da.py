@@ -9,7 +9,9 @@ must hold is fixed by the mathematics of delayed acceptance (Christen & Fox
   * the features equal a brute-force numpy recount from the particles;
   * the DA chain samples the exact distribution of Eq. (QQ) (exact
     enumeration), whatever the surrogate, and planted mistakes in the stages
-    (a one-sided surrogate, a stage 2 that ignores the surrogate) fail it.
+    (a one-sided surrogate, a stage 2 that ignores the surrogate) fail it;
+  * what a trained surrogate gains over none (held-out error, exact sums
+    avoided), and that the features, not the network width, limit it.
 """
 import math
 
