@@ -19,7 +19,7 @@
  *     the base pair, (MCsaltf), (MCmetro2), written in log form.
  *   - App. C, Eq. (pIXgen): 10^-pI_X = 10^-pI_S + 10^-min(pH, pOH).
  *   - Eq. (LJe)/(LJ): WCA with an optional expanded distance Delta.
- * Readings where the paper is silent (all stated in the design notes):
+ * Readings where the paper is silent:
  *   - The energy model is a damped-shifted-force (DSF) Coulomb cutoff sum plus
  *     WCA (the paper uses PPPM), with the DSF self term.
  *   - Moves are domain-local under an 8-colour checkerboard schedule: the
