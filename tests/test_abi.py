@@ -79,3 +79,17 @@ def test_struct_layouts_match_header(tmp_path):
     assert int(got["cr_trial_da"]) == crmc.DA_DTYPE.itemsize
     for f in crmc.DA_DTYPE.names:
         assert int(got[f"cr_trial_da.{f}"]) == crmc.DA_DTYPE.fields[f][1], f
+
+
+def test_header_is_plain_c_and_cpp():
+    """The boundary header compiles warning-free as strict C99 and as C++11
+    (no C++-only constructs, no torch or CUDA types in the signatures)."""
+    import subprocess
+    h = os.path.join(ROOT, "include", "crmc.h")
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c", h])
+    subprocess.check_call(["g++", "-std=c++11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", "c++",
+                           h])
+    import re
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S))
+    for banned in ("torch", "at::", "cudaStream_t", "#include <cuda"):
+        assert banned not in code, banned
