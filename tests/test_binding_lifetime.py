@@ -1,7 +1,8 @@
-"""Host-side lifetime rules of the Python binding, on CPU with a stand-in for
+"""Host-side rules of the Python binding, on CPU with a stand-in for
 the library: a context must outlive every batch that holds it (the C ABI's
 contract), so closing it while a batch is live raises, and each handle is
-destroyed exactly once, the batch before its contexts."""
+destroyed exactly once, the batch before its contexts; without the built
+library every call raises (no CPU fallback)."""
 import ctypes as C
 
 import pytest
@@ -84,3 +85,14 @@ def test_failed_batch_creation_leaves_contexts_free(fake):
         crmc.Batch([a])
     a.close()
     assert fake.calls == [("destroy", 0x40)]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every call raises; nothing falls back to a
+    CPU path."""
+    monkeypatch.setattr(crmc, "_L", None)
+    monkeypatch.setattr(crmc, "LIB_PATH", str(tmp_path / "libcrmc.so"))
+    with pytest.raises(ImportError, match="not built"):
+        crmc._lib()
+    with pytest.raises(ImportError):
+        crmc.philox(0, 0, 0, 0, 0, 0, 1)
