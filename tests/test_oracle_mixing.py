@@ -17,21 +17,30 @@ import oracle
 from paper_2109_07527_gb300 import workloads as W
 
 
-def tau_trials(schedule, m, domain_cells=None, samples=1500, every=512, workload=None):
+def tau_trials(schedule, m, domain_cells=None, samples=1500, every=512, workload=None, md=False):
     """Integrated autocorrelation time of the ionised-site count, in trials
     (FFT autocorrelation, self-consistent window of five times tau), for
     config 1 or the given workload.  The half-size polyelectrolyte figures
     quoted beside this test's come from workload=W.config2(seed=2, scale=0.5),
-    samples=1200, every=640 (1.3 x 10^6 trials each, a few minutes)."""
+    samples=1200, every=640 (1.3 x 10^6 trials each, a few minutes).  md=True
+    adds one velocity-Verlet/Langevin step (dt 0.005, gamma 1) after every
+    sweep, as in the hybrid MD/CR-MC cycle."""
     w = workload if workload is not None else W.config1(seed=1)
     o = oracle.Oracle(w, schedule=schedule, trials_per_domain=m, domain_cells=domain_cells)
     tps = o.trials_per_sweep
     reps = max(1, every // tps)
-    o.sweep(tps * max(1, 200000 // tps), 1)
+    if md:
+        for i in range(max(1, 200000 // tps)):
+            o.sweep(tps, 1 + i)
+            o.md_step(1, 0.005, 1.0, 7 + i)
+    else:
+        o.sweep(tps * max(1, 200000 // tps), 1)
     x = []
     for i in range(samples):
         for r in range(reps):
             o.sweep(tps, 1000 + 100 * i + r)
+            if md:
+                o.md_step(1, 0.005, 1.0, 50000 + 100 * i + r)
         x.append(o.counts()["n_Am"])
     x = np.asarray(x, float) - np.mean(x)
     n = len(x)
