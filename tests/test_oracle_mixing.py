@@ -8,7 +8,10 @@ makes the degree of ionisation decorrelate much more slowly per trial with
 domains of two half-cutoff cells than with the global rule, and domains of
 four cells (2 r_c, one per colour) recover most of the difference.  Both
 schedules sample the same distribution (pinned elsewhere); this test records
-the cost in trials, which a trials/s figure does not show."""
+the cost in trials, which a trials/s figure does not show.  (With an MD step
+after every sweep, as in the hybrid cycle, the chains' relaxation under MD is
+slower still and sets the pace for both schedules; tau_trials(md=True) measures
+that, too slowly for this suite.)"""
 import math
 
 import numpy as np
