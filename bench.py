@@ -196,38 +196,86 @@ class ClockSampler:
                 "period_ms": self.period_ms}
 
 
-def cpu_baseline(w, sample_sweeps=20):
-    """The oracle as it stands (single thread) on a bounded sample of the
-    workload: sample_sweeps sweeps of 1000 trials (one trial per domain) and one
-    MD step, i.e. the workload's 1 MD step : 1e4 trials mix."""
+def host_cpu():
+    """(model name, logical CPUs) of the host, from lscpu or /proc/cpuinfo."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def oracle_step(oracles, seed, md_seed, threads):
+    """One step of the workload on the oracle: a sweep (10^4 trials at 10
+    trials per domain, the GPU's chain) and one MD step of every replica, the
+    replicas spread over `threads` host threads (each replica's chain is the
+    sequential oracle's; the C calls release the GIL).  Returns the trials."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(o):
+        o.sweep(o.trials_per_sweep, seed)
+        o.md_step(1, 0.005, 1.0, md_seed)
+        return o.trials_per_sweep
+
+    if threads <= 1:
+        return sum(one(o) for o in oracles)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return sum(ex.map(one, oracles))
+
+
+def cpu_baseline(ws):
+    """The oracle as it stands, on a bounded sample of the workload: one step
+    (one 10^4-trial sweep at 10 trials per domain + one MD step) of the pH 4.5
+    replica on one host thread, and one step of all 13 replicas with one
+    replica per host thread."""
     import oracle
-    o = oracle.Oracle(w, trials_per_domain=1)
+    model, ncpu = host_cpu()
+    o1 = oracle.Oracle(ws[5])
     t0 = time.perf_counter()
-    n = 0
-    for s in range(sample_sweeps):
-        o.sweep(o.trials_per_sweep, 1000 + s)
-        n += o.trials_per_sweep
-    co = o.counts()
+    n1 = oracle_step([o1], 1000, 5, 1)
+    dt1 = time.perf_counter() - t0
+    co = o1.counts()
     alpha_o = co["n_Am"] / co["n_A"] if co["n_A"] > 0 else 0.0  # degree of ionisation of the acid sites
-    o.md_step(1, 0.005, 1.0, 5)
+    threads = max(1, min(ncpu, len(ws)))
+    os_ = [oracle.Oracle(w) for w in ws]
+    t0 = time.perf_counter()
+    n = oracle_step(os_, 1000, 5, threads)
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "trials/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample_sweeps} sweeps x {o.trials_per_sweep} trials (1 trial per domain) + 1 MD step "
-                      f"of the same workload, {dt:.1f} s on 1 host thread"}, alpha_o
+    return {"value": n / dt, "unit": "trials/s", "cores": threads, "kind": "oracle",
+            "sample": f"one step of the 13-replica workload ({len(ws)} x {os_[0].trials_per_sweep} trials at 10 "
+                      f"trials per domain + 1 MD step each, the GPU's chain), one replica per host thread, "
+                      f"{dt:.1f} s",
+            "cpu_model": model, "nproc": ncpu,
+            "single_thread": {"value": n1 / dt1, "unit": "trials/s", "cores": 1,
+                              "sample": f"one step of the pH {ws[5].params['pH']} replica ({n1} trials + 1 MD step), "
+                                        f"{dt1:.1f} s"}}, alpha_o
 
 
-def alpha_check(crmc, w, alpha_o, sample_sweeps=20):
+def alpha_check(crmc, w, alpha_o):
     """The metric's accuracy condition on the same sample: the GPU path runs
-    the oracle's sweeps (same seeds, same workload) and its degree of
+    the oracle's step (same seeds, same workload) and its degree of
     ionisation must be within 0.005 of the oracle's (the chains are the same
     trial by trial, so the difference is 0 unless a decision fell within the
     tie band)."""
-    g = crmc.Context(w, trials_per_domain=1)
-    for s in range(sample_sweeps):
-        g.sweep(g.trials_per_sweep, 1000 + s)
+    g = crmc.Context(w)
+    tps = g.trials_per_sweep
+    g.sweep(tps, 1000)
     a = g.counts()["alpha"]
     g.close()
-    return {"sample": f"pH {w.params['pH']} replica, {sample_sweeps} sweeps x 1000 trials, GPU vs oracle",
+    return {"sample": f"pH {w.params['pH']} replica, one sweep of {tps} trials, GPU vs oracle",
             "alpha_gpu": a, "alpha_oracle": alpha_o, "abs_diff": abs(a - alpha_o), "bound": 0.005,
             "within": abs(a - alpha_o) <= 0.005}
 
@@ -237,27 +285,27 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    w = workload(0)
-    o = oracle.Oracle(w, trials_per_domain=1)
-    tps = o.trials_per_sweep
+    ws = ph_sweep_workloads(0)
+    model, ncpu = host_cpu()
+    threads = max(1, min(ncpu, len(ws)))
+    os_ = [oracle.Oracle(w) for w in ws]
     for s in range(args.warmup):
-        o.sweep(tps, 7 + s)
+        oracle_step(os_, 7 + s, 3 + s, threads)
     t0 = time.perf_counter()
     n = 0
     for s in range(args.steps):
-        o.sweep(tps, 100 + s)
-        n += tps
-        if s % 10 == 9:
-            o.md_step(1, 0.005, 1.0, 11)
+        n += oracle_step(os_, 100 + s, 5000 + s, threads)
     dt = time.perf_counter() - t0
     v = n / dt
-    sample = (f"{args.steps} steps of {tps} trials (1 trial per domain) with one MD step per 10 steps "
-              f"(the 1 MD : 1e4 trials mix), {dt:.1f} s, 1 host thread")
+    sample = (f"{args.steps} steps of the 13-replica workload, each a sweep of {os_[0].trials_per_sweep} trials "
+              f"(10 per domain, the GPU's chain) + 1 MD step per replica, one replica per host thread "
+              f"({threads} threads on {ncpu} CPUs, {model}), {dt:.1f} s")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "trials/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
-           "cpu_baseline": {"value": v, "unit": "trials/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle", "replicas": len(ws)},
+           "cpu_baseline": {"value": v, "unit": "trials/s", "cores": threads, "kind": "oracle", "sample": sample,
+                            "cpu_model": model, "nproc": ncpu},
            "e2e": {"value": v, "unit": "trials/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -560,8 +608,8 @@ def run_ours(args):
            "surrogate_da": da,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"], alpha_o = cpu_baseline(workload(0))
-        out["alpha_check"] = alpha_check(crmc, workload(0), alpha_o)
+        out["cpu_baseline"], alpha_o = cpu_baseline(ph_sweep_workloads(0))
+        out["alpha_check"] = alpha_check(crmc, ph_sweep_workloads(0)[5], alpha_o)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -236,17 +236,28 @@ int cr_sweep_da_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_stat
                     cr_trial_da *dlog, float *features);
 
 /* Evaluate the conservative MD forces (DSF Coulomb + WCA + FENE) with the
- * current charges; they become readable through cr_state().force. */
+ * current charges; they become readable through cr_state().force.  The paper
+ * couples CR-MC to MD whose every step needs a full force evaluation with the
+ * regulated charges (Sec. II.D); the pair forces are -dU/dr of the same DSF
+ * and WCA / expanded-WCA (Eqs. LJ, LJe) energies the trials use, the bonds
+ * FENE, U = -K R0^2/2 ln(1 - (r/R0)^2) (the paper's own chain model, Eq.
+ * bond, is harmonic).  FP32 pair terms summed in exact 2^-24 fixed point. */
 int cr_md_forces(cr_ctx *ctx);
 
 /* n_steps of velocity Verlet with Langevin friction gamma and noise at kT = 1
- * (unit mass), time step dt, noise key seed.  Forces are re-evaluated first
+ * (unit mass), time step dt, noise key seed: the integrator and thermostat of
+ * the paper's MD (Sec. III.A: velocity Verlet, Langevin damping time tau,
+ * dt = 0.005 tau), CR-MC trials running between MD steps (Sec. II.D).  The
+ * noise is applied at each force evaluation (BBK form), Box-Muller normals
+ * from Philox purpose 5 counted by particle id and force evaluation.  Forces are re-evaluated first
  * when CR-MC changed the system since the last evaluation.  Errors:
  * BOND_BROKEN, CELL_OVERFLOW. */
 int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed);
 
-/* One MD step split around CR-MC calls, so that a cycle of trials and one MD
- * step needs a single force evaluation: cr_md_begin evaluates the forces if
+/* One MD step split around CR-MC calls (Sec. III.A's velocity Verlet and
+ * Langevin thermostat, with the MC trials of Sec. II.C inside the step; the
+ * paper interleaves n_MC trials with n_MD steps, Sec. II.D), so that a cycle
+ * of trials and one MD step needs a single force evaluation: cr_md_begin evaluates the forces if
  * CR-MC changed the system since the last evaluation, then does the first
  * half kick and the drift (and rebuilds the cells); CR-MC calls may follow;
  * cr_md_end evaluates the forces with the current charges (Langevin terms
@@ -276,15 +287,21 @@ int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
  * CR_ERR_CAPACITY before anything is launched.  The call clears the scratch
  * counter itself.  Calls whose work overlaps on the GPU (different streams or
  * contexts without ordering between them) race on that scratch: order them
- * on one stream or with events.  The first call on a device looks the
- * scratch address up (cudaGetSymbolAddress) with the context's device
- * current; make that first call before any stream capture.  Synchronises the
- * context's stream.  Errors: INVALID_ARG (NULL or misaligned pointer, n_slots
- * too small, context device not current), CAPACITY, CELL_OVERFLOW, CUDA. */
+ * on one stream or with events.  Every call looks the scratch's device
+ * address up (cudaGetSymbolAddress) with the context's device current.  The
+ * forces equal cr_md_forces' bit for bit; this entry finishes each particle
+ * on one lane of its warp (cr_md_forces hands the sums to a per-particle
+ * kernel through a context buffer), so it is slower on large systems.
+ * Synchronises the context's stream.  Errors: INVALID_ARG (NULL or
+ * misaligned pointer, n_slots too small, context device not current),
+ * CAPACITY, CELL_OVERFLOW, CUDA. */
 #define CR_NOALLOC_MAX_PARTICLES 262144
 int cr_md_forces_noalloc(cr_ctx *ctx, float *force, uint64_t *id, int64_t n_slots);
 
-/* Fill the view (counts always; arrays when non-NULL) and synchronise.
+/* Fill the view (counts always; arrays when non-NULL) and synchronise.  The
+ * counts are the particle numbers of Eq. (QQ) (n_A-, n_B+, n_X+, n_X-); alpha
+ * is the instantaneous degree of dissociation n_A- / n_A whose average is the
+ * paper's observable alpha = <n_A-> / n_A (Sec. II.D).
  * Arrays are ordered by particle id (the ordering runs on the device: input
  * ids by a prefix count, inserted ions by their rank among the ion ids, or a
  * device-wide radix sort past 16,384 ions), one device-to-host copy per
@@ -305,6 +322,33 @@ int cr_state(cr_ctx *ctx, cr_state_view *out);
 int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type, const int32_t *cls,
             const int8_t *state);
 
+/* ---- checkpoint / resume ----
+ * A run split into a checkpoint and a restore into a fresh context (created
+ * by cr_init from the same system, pH and parameters) continues the unsplit
+ * chain bit for bit: the trials' random numbers are Philox counters of the
+ * sweep number (Sec. II.C's moves drawn per phase), the Langevin noise of the
+ * force-evaluation number, and the cells stay ordered by particle id.
+ * cr_counters carries those counters and whether the integrator holds the
+ * forces of the next half kick (after cr_md_end / cr_md_step, not after
+ * cr_md_begin or a sweep). */
+typedef struct {
+  uint64_t sweep;       /* sweeps run so far */
+  uint32_t md_eval;     /* force evaluations so far */
+  int32_t forces_valid; /* 1: the checkpoint's forces feed the next half kick */
+} cr_counters;
+/* cr_state (same arrays, ordered by id), except that out->force receives the
+ * integrator's forces (Langevin terms included) when they are valid, zeros
+ * otherwise; and the counters.  Synchronises. */
+int cr_checkpoint(cr_ctx *ctx, cr_state_view *out, cr_counters *counters);
+/* cr_load with the particle ids (input ids below 2^32 as given to cr_init,
+ * inserted ions at or above 2^32), the integrator forces (read when
+ * counters->forces_valid; may be NULL otherwise) and the counters of a
+ * checkpoint.  The ids are checked on the host (unique; every bonded and
+ * site particle of cr_init present; INVALID_ARG otherwise), the particles
+ * on the device as by cr_load. */
+int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const float *force, const uint64_t *id,
+               const int32_t *type, const int32_t *cls, const int8_t *state, const cr_counters *counters);
+
 /* Launch shape of the colour-phase kernel: threads per domain and halo
  * particles held in registers per thread.  Supported pairs: (32|64|128|256|512,
  * 0) halo in shared memory; (128, 4), (256, 2), (512, 1) halo in registers.
@@ -323,6 +367,29 @@ int cr_set_timing(cr_ctx *ctx, int32_t enable);
  * colour-phase kernel (0) and the MD force kernel (1) since the last reset,
  * and the number of kernels this context launched.  reset != 0 zeroes them. */
 int cr_get_timing(cr_ctx *ctx, double *ms, int64_t *launches, int64_t *launches_total, int32_t reset);
+
+/* A new reservoir pH from the next trial on: the paper's implementation
+ * accepts a variable (time-dependent) pH, e.g. to follow a system's response
+ * to a pH increase (App. B).  Recomputes pOH = pKw - pH, the grouped pI_X+-
+ * of Eq. (pIXgen) (unless they were given explicitly) and the equilibrium
+ * constants K_A = 10^(pH - pKa - pI_X+), K_B = 10^(pOH - pKb - pI_X-) and
+ * K_ion = 10^(-pI_X+ - pI_X-) (Sec. II.D) exactly as cr_init does, in stream
+ * order (trials queued before the call keep the old pH).  Batches holding the
+ * context pick the change up at their next sweep.  Synchronises. */
+int cr_set_pH(cr_ctx *ctx, double pH);
+
+/* Ungrouping of the combined ions (Sec. II.D, last paragraph): a grouped ion
+ * belongs to subspecies i with probability p_i = 10^(-pI_i + pI_X), exact in
+ * equilibrium.  p_S_plus, p_H: salt cation and H+ in X+; p_S_minus, p_OH:
+ * salt anion and OH- in X-; the remainder of each group (1 - the two) is the
+ * counter-ion of the acid or base that sets a non-neutral pH (App. C).  n_*:
+ * those fractions of the current n_X+ / n_X- (reads the counts;
+ * synchronises). */
+typedef struct {
+  double p_S_plus, p_H, p_S_minus, p_OH;
+  double n_S_plus, n_H, n_S_minus, n_OH;
+} cr_ungrouped;
+int cr_ungroup(cr_ctx *ctx, cr_ungrouped *out);
 
 /* Geometry and schedule of the context. */
 int cr_get_info(const cr_ctx *ctx, cr_info *out);
@@ -420,6 +487,15 @@ int cr_train_set_stream(cr_trainer *t, void *stream);
 int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss);
 /* Loss and gradients (host [CR_TRAIN_N_PARAMS], nullable) without an update. */
 int cr_train_gradients(cr_trainer *t, const float *X, const float *target, int32_t batch, float *grads, float *loss);
+/* One Adam step (Kingma & Ba, 2015: bias-corrected first and second moments;
+ * the hyperparameters of cr_train_cfg applied in FP32) with caller-supplied
+ * gradients instead of a batch's: host grads [CR_TRAIN_N_PARAMS] in the
+ * parameter vector order above.  The update of cr_train_step alone (it counts
+ * as a step of the trainer).  Synchronises. */
+int cr_train_apply(cr_trainer *t, const float *grads);
+/* Adam's first and second moments (host [CR_TRAIN_N_PARAMS] each, nullable),
+ * in the parameter vector order.  Synchronises. */
+int cr_train_moments(cr_trainer *t, float *m, float *v);
 /* Current parameters: FP32 masters (params, nullable) and the cr_mlp layout
  * (BF16 of the masters; each pointer nullable). */
 int cr_train_get(cr_trainer *t, float *params, uint16_t *W1, float *b1, uint16_t *W2, float *b2, uint16_t *W3,
@@ -433,6 +509,17 @@ void cr_train_destroy(cr_trainer *t);
  * (split over K), else overwrites.  Synchronises the stream. */
 int cr_mma_bf16(const uint16_t *A, const uint16_t *B, float *D, int32_t M, int32_t N, int32_t K, int32_t accumulate,
                 void *stream);
+
+/* Failure-detection self-test of the tensor-core product's bounded waits (no
+ * counterpart in the paper): one 128 x 128 x 64 product of cr_mma_bf16's kind
+ * whose only operand copy is withheld, so that the MMA issuer's wait for it,
+ * and every thread's wait for the accumulator, run out after `polls` polls;
+ * the CTA then records the timeout, frees its tensor memory and returns
+ * without touching D.  Returns CR_ERR_TIMEOUT when that path worked (the
+ * device stays usable; nothing faults or hangs), CR_OK if the wait did not
+ * run out.  A [128][64], B [128][64] BF16 and D [128][128] FP32: device
+ * buffers as for cr_mma_bf16.  Synchronises the stream. */
+int cr_selftest_mma_timeout(const uint16_t *A, const uint16_t *B, float *D, uint32_t polls, void *stream);
 
 /* Philox4x32-10 on the device for n consecutive counters (c0 + i, c1, c2, c3),
  * key (k0, k1); out: host array of 4n words.  Exposed for parity tests. */

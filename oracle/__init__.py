@@ -87,6 +87,8 @@ def _load():
         lib.or_n.argtypes = [P]
         lib.or_geometry.argtypes = [P, P]
         lib.or_chem.argtypes = [P, P]
+        lib.or_set_pH.argtypes = [P, C.c_double]
+        lib.or_ungroup.argtypes = [P, P]
         lib.or_particles.argtypes = [P, P, P, P, P, P]
         lib.or_site_states.argtypes = [P, P]
         lib.or_energy.restype = C.c_double
@@ -204,6 +206,17 @@ class Oracle:
         c = np.zeros(7)
         self._lib.or_chem(self._h, _ptr(c))
         return dict(pIX_plus=c[0], pIX_minus=c[1], ln_z1=c[2], ln_salt=c[3], a=c[4], self_coef=c[5], pOH=c[6])
+
+    def set_pH(self, pH):
+        """A new reservoir pH from the next trial on (chemistry recomputed)."""
+        self._lib.or_set_pH(self._h, float(pH))
+
+    def ungroup(self):
+        """Subspecies fractions of the grouped ions: p_S+, p_H+ (in X+),
+        p_S-, p_OH- (in X-)."""
+        c = np.zeros(4)
+        self._lib.or_ungroup(self._h, _ptr(c))
+        return dict(p_Sp=c[0], p_H=c[1], p_Sm=c[2], p_OH=c[3])
 
     def set_surrogate(self, mlp):
         """Surrogate weights: dict with W1 [128,48], W2, W3 [128,128], w4 [128]

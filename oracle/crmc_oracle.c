@@ -121,8 +121,12 @@ typedef struct {
   int on[4][4];
   /* chemistry (log form) */
   double pH, pOH, pIXp, pIXm, ln_z1, ln_salt;
+  double pKw, pIS_plus, pIS_minus;
+  int pIX_explicit;
   int n_sites;
   double *lnK; /* per site: ln10*(pH-pKa-pI_X+) for acids, ln10*(pOH-pKb-pI_X-) for bases */
+  double *pK;  /* per site: pKa or pKb as given */
+  int *site_type; /* per site: T_ACID or T_BASE */
   int react[3], n_react;
   /* particles */
   int n, cap;
@@ -240,7 +244,7 @@ void or_destroy(Oracle *o) {
   if (!o) return;
   free(o->x); free(o->y); free(o->z); free(o->type); free(o->cls); free(o->site); free(o->st);
   free(o->id); free(o->vx); free(o->vy); free(o->vz); free(o->fx); free(o->fy); free(o->fz);
-  free(o->lnK); free(o->bi); free(o->bj);
+  free(o->lnK); free(o->pK); free(o->site_type); free(o->bi); free(o->bj);
   free(o->W1); free(o->b1); free(o->W2); free(o->b2); free(o->W3); free(o->b3); free(o->w4);
   free(o);
 }
@@ -298,6 +302,10 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   o->m = p->trials_per_domain > 0 ? p->trials_per_domain : 1;
   /* chemistry */
   o->pH = p->pH;
+  o->pKw = p->pKw;
+  o->pIS_plus = p->pIS_plus;
+  o->pIS_minus = p->pIS_minus;
+  o->pIX_explicit = p->pIX_explicit;
   o->pOH = p->pKw - p->pH;
   if (p->pIX_explicit) { o->pIXp = p->pIX_plus; o->pIXm = p->pIX_minus; }
   else { o->pIXp = pIX_of(p->pIS_plus, o->pH, o->pOH); o->pIXm = pIX_of(p->pIS_minus, o->pH, o->pOH); }
@@ -316,6 +324,8 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   int ns = 0, nA = 0, nB = 0;
   for (int i = 0; i < p->n; ++i) if (type[i] == T_ACID || type[i] == T_BASE) ns++;
   o->lnK = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(double));
+  o->pK = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(double));
+  o->site_type = malloc((size_t)(ns > 0 ? ns : 1) * sizeof(int));
   int qsum = 0;
   ns = 0;
   for (int i = 0; i < p->n; ++i) {
@@ -331,6 +341,8 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
     if (type[i] == T_ACID || type[i] == T_BASE) {
       o->site[i] = ns;
       o->st[i] = state[i] ? 1 : 0;
+      o->pK[ns] = pK[i];
+      o->site_type[ns] = type[i];
       if (type[i] == T_ACID) { o->lnK[ns] = LN10 * ((o->pH - pK[i]) - o->pIXp); nA++; }
       else { o->lnK[ns] = LN10 * ((o->pOH - pK[i]) - o->pIXm); nB++; }
       ns++;
@@ -1004,6 +1016,36 @@ int32_t or_geometry(const Oracle *o, int32_t *out) {
   out[0] = o->nc; out[1] = o->k; out[2] = o->nd; out[3] = o->ncol; out[4] = o->m; out[5] = o->global;
   return OR_OK;
 }
+/* A new reservoir pH between sweeps (the paper's implementation accepts a
+ * time-dependent pH, App. B): pOH = pKw - pH, the grouped pI_X of Eq.
+ * (pIXgen) unless given explicitly, and the equilibrium constants
+ * K_A = 10^(pH - pKa - pI_X+), K_B = 10^(pOH - pKb - pI_X-) and
+ * K_ion = 10^(-pI_X+ - pI_X-) of every site, recomputed as at creation. */
+void or_set_pH(Oracle *o, double pH) {
+  o->pH = pH;
+  o->pOH = o->pKw - pH;
+  if (!o->pIX_explicit) {
+    o->pIXp = pIX_of(o->pIS_plus, o->pH, o->pOH);
+    o->pIXm = pIX_of(o->pIS_minus, o->pH, o->pOH);
+  }
+  o->ln_salt = -LN10 * (o->pIXp + o->pIXm);
+  for (int s = 0; s < o->n_sites; ++s)
+    o->lnK[s] = o->site_type[s] == T_ACID ? LN10 * ((o->pH - o->pK[s]) - o->pIXp)
+                                          : LN10 * ((o->pOH - o->pK[s]) - o->pIXm);
+}
+
+/* Ungrouping of the combined ions (Sec. II.D, last paragraph): a grouped
+ * ion belongs to subspecies i with probability p_i = 10^(-pI_i + pI_X).
+ * out[0] = p of S+ in X+, out[1] = p of H+ in X+, out[2] = p of S- in X-,
+ * out[3] = p of OH- in X-; the rest of each group (1 - the two) is the
+ * counter-ion of the acid or base that sets a non-neutral pH (App. C). */
+void or_ungroup(const Oracle *o, double *out) {
+  out[0] = pow(10.0, -o->pIS_plus + o->pIXp);
+  out[1] = pow(10.0, -o->pH + o->pIXp);
+  out[2] = pow(10.0, -o->pIS_minus + o->pIXm);
+  out[3] = pow(10.0, -o->pOH + o->pIXm);
+}
+
 void or_chem(const Oracle *o, double *out) {
   out[0] = o->pIXp; out[1] = o->pIXm; out[2] = o->ln_z1; out[3] = o->ln_salt; out[4] = o->a;
   out[5] = o->self_coef; out[6] = o->pOH;

@@ -96,8 +96,18 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_train_set_stream", "cr_train_step", "cr_train_gradients", "cr_train_get", "cr_train_stats",
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
            "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
-           "cr_batch_state_packed", "cr_batch_load_packed")
+           "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
+           "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
+
+
+class cr_counters(C.Structure):
+    _fields_ = [("sweep", C.c_uint64), ("md_eval", C.c_uint32), ("forces_valid", C.c_int32)]
+
+
+class cr_ungrouped(C.Structure):
+    _fields_ = [(f, C.c_double) for f in ("p_S_plus", "p_H", "p_S_minus", "p_OH", "n_S_plus", "n_H", "n_S_minus",
+                                          "n_OH")]
 
 
 class cr_train_cfg(C.Structure):
@@ -136,10 +146,16 @@ def _lib():
         lib.cr_train_gradients.argtypes = [P, P, P, C.c_int32, P, P]
         lib.cr_train_get.restype = C.c_int
         lib.cr_train_get.argtypes = [P] + [P] * 9
+        lib.cr_train_apply.restype = C.c_int
+        lib.cr_train_apply.argtypes = [P, P]
+        lib.cr_train_moments.restype = C.c_int
+        lib.cr_train_moments.argtypes = [P, P, P]
         lib.cr_train_stats.restype = C.c_int
         lib.cr_train_stats.argtypes = [P, P, P]
         lib.cr_train_destroy.restype = None
         lib.cr_train_destroy.argtypes = [P]
+        lib.cr_selftest_mma_timeout.restype = C.c_int
+        lib.cr_selftest_mma_timeout.argtypes = [P, P, P, C.c_uint32, P]
         lib.cr_mma_bf16.restype = C.c_int
         lib.cr_mma_bf16.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]
         lib.cr_set_surrogate.restype = C.c_int
@@ -172,6 +188,14 @@ def _lib():
         lib.cr_destroy.argtypes = [P]
         lib.cr_strerror.restype = C.c_char_p
         lib.cr_strerror.argtypes = [C.c_int]
+        lib.cr_set_pH.restype = C.c_int
+        lib.cr_set_pH.argtypes = [P, C.c_double]
+        lib.cr_ungroup.restype = C.c_int
+        lib.cr_ungroup.argtypes = [P, C.POINTER(cr_ungrouped)]
+        lib.cr_checkpoint.restype = C.c_int
+        lib.cr_checkpoint.argtypes = [P, C.POINTER(cr_state_view), C.POINTER(cr_counters)]
+        lib.cr_restore.restype = C.c_int
+        lib.cr_restore.argtypes = [P, C.c_int32, P, P, P, P, P, P, P, C.POINTER(cr_counters)]
         lib.cr_load.restype = C.c_int
         lib.cr_load.argtypes = [P, C.c_int32, P, P, P, P, P]
         lib.cr_set_timing.restype = C.c_int
@@ -430,6 +454,38 @@ class Context:
         return c
 
 
+    def set_pH(self, pH):
+        """cr_set_pH: a new reservoir pH from the next trial on."""
+        _chk(self._lib.cr_set_pH(self._h, float(pH)), "cr_set_pH")
+
+    def ungroup(self):
+        """cr_ungroup: subspecies fractions of X+ / X- and their expected numbers."""
+        u = cr_ungrouped()
+        _chk(self._lib.cr_ungroup(self._h, C.byref(u)), "cr_ungroup")
+        return {f: getattr(u, f) for f, _ in cr_ungrouped._fields_}
+
+    def checkpoint(self):
+        """cr_checkpoint: the state arrays (ordered by id; force = the
+        integrator's forces when valid) and the counters, as one dict."""
+        c = self.counts()
+        n = int(c["n"])
+        arr = dict(xyz=np.zeros((n, 3), np.float32), vel=np.zeros((n, 3), np.float32),
+                   force=np.zeros((n, 3), np.float32), id=np.zeros(n, np.uint64), type=np.zeros(n, np.int32),
+                   state=np.zeros(n, np.int8), cls=np.zeros(n, np.int32))
+        v = _view(**arr)
+        k = cr_counters()
+        _chk(self._lib.cr_checkpoint(self._h, C.byref(v), C.byref(k)), "cr_checkpoint")
+        arr.update(n=n, sweep=int(k.sweep), md_eval=int(k.md_eval), forces_valid=int(k.forces_valid))
+        return arr
+
+    def restore(self, ck):
+        """cr_restore from a dict as checkpoint() returns it."""
+        k = cr_counters(int(ck["sweep"]), int(ck["md_eval"]), int(ck["forces_valid"]))
+        a = {x: np.ascontiguousarray(ck[x]) for x in ("xyz", "vel", "force", "id", "type", "cls", "state")}
+        _chk(self._lib.cr_restore(self._h, int(ck["n"]), _p(a["xyz"]), _p(a["vel"]), _p(a["force"]), _p(a["id"]),
+                                  _p(a["type"]), _p(a["cls"]), _p(a["state"]), C.byref(k)), "cr_restore")
+
+
 class Batch:
     """Independent replicas advanced together (one phase launch per colour)."""
 
@@ -557,6 +613,20 @@ class Trainer:
                                           _p(g), C.byref(loss)), "cr_train_gradients")
         return loss.value, g
 
+    def apply(self, grads):
+        """cr_train_apply: one Adam step with the given gradient vector."""
+        g = np.ascontiguousarray(grads, dtype=np.float32)
+        if g.shape != (N_PARAMS,):
+            raise ValueError("gradient vector of CR_TRAIN_N_PARAMS floats expected")
+        _chk(self._lib.cr_train_apply(self._h, _p(g)), "cr_train_apply")
+
+    def moments(self):
+        """(first, second) Adam moments, FP32 vectors in the parameter order."""
+        m = np.zeros(N_PARAMS, np.float32)
+        v = np.zeros(N_PARAMS, np.float32)
+        _chk(self._lib.cr_train_moments(self._h, _p(m), _p(v)), "cr_train_moments")
+        return m, v
+
     def get(self):
         """(FP32 master vector, surrogate dict in the cr_mlp layout)."""
         P = np.zeros(N_PARAMS, np.float32)
@@ -581,6 +651,14 @@ class Trainer:
 
     def __del__(self):
         self.close()
+
+
+def selftest_mma_timeout(A_ptr, B_ptr, D_ptr, polls, stream=None):
+    """cr_selftest_mma_timeout: the status code (CR_ERR_TIMEOUT = -5 when the
+    bounded-wait expiry path worked)."""
+    st = stream if stream is not None else _torch_stream()
+    return int(_lib().cr_selftest_mma_timeout(C.c_void_p(int(A_ptr)), C.c_void_p(int(B_ptr)),
+                                              C.c_void_p(int(D_ptr)), int(polls), st))
 
 
 def mma_bf16(A_ptr, B_ptr, D_ptr, M, N, K, accumulate=False, stream=None):

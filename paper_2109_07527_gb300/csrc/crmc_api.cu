@@ -77,6 +77,8 @@ struct cr_ctx {
   float *d_in_xyz = nullptr, *d_in_vel = nullptr;
   int *d_in_type = nullptr, *d_in_cls = nullptr, *d_site_map = nullptr;
   int8_t *d_in_state = nullptr;
+  unsigned long long *d_in_id = nullptr;  // cr_restore inputs (allocated on first use)
+  float *d_in_frc = nullptr;
   // cr_state: id ordering on the device and the output arrays in the
   // caller's layouts (capacity-sized), one copy each to the caller
   int *d_present = nullptr;
@@ -90,6 +92,14 @@ struct cr_ctx {
   int *d_out_type = nullptr, *d_out_cls = nullptr;
   int8_t *d_out_state = nullptr, *d_out_site = nullptr;
   long long *h_small = nullptr;           // pinned: kind counts [6], ions found, error word
+  // chemistry kept for cr_set_pH: reservoir, per-site pK and kind, the
+  // current pH and pI_X, and a version that batches compare against
+  double pH = 7.0, pIXp = 0.0, pIXm = 0.0;
+  cr_mu_ions mu{};
+  std::vector<double> site_pK;
+  std::vector<char> site_is_acid;
+  std::vector<long long> h_lnK_fx;
+  int chem_version = 0;
   // MD
   double fene_K = 30.0, fene_R0 = 1.5;
   uint64_t sweep = 0;
@@ -178,7 +188,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_log,
                   c->d_in_xyz, c->d_in_vel, c->d_init_type, c->d_in_type, c->d_in_cls, c->d_site_map, c->d_in_state,
-                  c->d_present, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_ion_rank, c->d_sort_tmp,
+                  c->d_in_id, c->d_in_frc, c->d_present, c->d_ion_key, c->d_ion_key2, c->d_ion_val, c->d_ion_val2, c->d_ion_rank, c->d_sort_tmp,
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
@@ -380,6 +390,10 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.lnz1_fx = to_lnfix(ln_z1);
   P.lnsalt_fx = to_lnfix(ln_salt);
   P.lBself_fx = to_lnfix(P.lB_self);
+  c->pH = pH;
+  c->mu = mu;
+  c->pIXp = pIXp;
+  c->pIXm = pIXm;
 
   // ---- particles: validate, classify, sort into cells
   std::vector<int> site_of(n, -1);
@@ -392,6 +406,8 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     if (t < CR_BEAD || t > CR_CORE || sys->cls[i] < 0 || sys->cls[i] > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
     if (t == CR_ACID || t == CR_BASE) {
       site_of[i] = (int)lnK.size();
+      c->site_pK.push_back(pK[i]);
+      c->site_is_acid.push_back(t == CR_ACID ? 1 : 0);
       if (t == CR_ACID) { lnK.push_back(LN10 * ((pH - pK[i]) - pIXp)); nA++; }
       else { lnK.push_back(LN10 * ((pOH - pK[i]) - pIXm)); nB++; }
       const int ion = sys->state[i] ? 1 : 0;
@@ -684,6 +700,48 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   }
   if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return CR_ERR_CUDA; }
   *out = c;
+  return CR_OK;
+}
+
+extern "C" int cr_set_pH(cr_ctx *ctx, double pH) {
+  if (!ctx || !std::isfinite(pH)) return CR_ERR_INVALID_ARG;
+  const cr_mu_ions &mu = ctx->mu;
+  const double pOH = mu.pKw - pH;
+  double pIXp, pIXm;
+  if (mu.pIX_explicit) { pIXp = mu.pIX_plus; pIXm = mu.pIX_minus; }
+  else { pIXp = pIX_of(mu.pI_S_plus, pH, pOH); pIXm = pIX_of(mu.pI_S_minus, pH, pOH); }
+  const size_t ns = ctx->site_pK.size();
+  ctx->h_lnK_fx.resize(ns);
+  for (size_t i = 0; i < ns; ++i)
+    ctx->h_lnK_fx[i] = to_lnfix(ctx->site_is_acid[i] ? LN10 * ((pH - ctx->site_pK[i]) - pIXp)
+                                                     : LN10 * ((pOH - ctx->site_pK[i]) - pIXm));
+  // in stream order: the trials queued before this call keep the old constants
+  if (ns) CR_CUDA(cudaMemcpyAsync(ctx->d_lnK, ctx->h_lnK_fx.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+  ctx->P.lnsalt_fx = to_lnfix(-LN10 * (pIXp + pIXm));
+  CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &ctx->P, sizeof(SysParams), cudaMemcpyHostToDevice, ctx->stream));
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->pH = pH;
+  ctx->pIXp = pIXp;
+  ctx->pIXm = pIXm;
+  ctx->chem_version++;
+  return CR_OK;
+}
+
+extern "C" int cr_ungroup(cr_ctx *ctx, cr_ungrouped *out) {
+  if (!ctx || !out) return CR_ERR_INVALID_ARG;
+  const double pOH = ctx->mu.pKw - ctx->pH;
+  out->p_S_plus = std::pow(10.0, -ctx->mu.pI_S_plus + ctx->pIXp);
+  out->p_H = std::pow(10.0, -ctx->pH + ctx->pIXp);
+  out->p_S_minus = std::pow(10.0, -ctx->mu.pI_S_minus + ctx->pIXm);
+  out->p_OH = std::pow(10.0, -pOH + ctx->pIXm);
+  cr_state_view v{};
+  const int rc = cr_state(ctx, &v);
+  if (rc != CR_OK) return rc;
+  out->n_S_plus = out->p_S_plus * (double)v.n_Xp;
+  out->n_H = out->p_H * (double)v.n_Xp;
+  out->n_S_minus = out->p_S_minus * (double)v.n_Xm;
+  out->n_OH = out->p_OH * (double)v.n_Xm;
   return CR_OK;
 }
 
@@ -1037,7 +1095,8 @@ static int ion_end_bit(const cr_ctx *ctx) {
 // state_begin queues the id marks (when arrays are wanted) and the copies of
 // the counts and the error word; state_arrays, with those on the host, fills
 // the counts of the view and queues the ordering and one copy per array.
-static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, StateBufs &B, bool &want) {
+static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, StateBufs &B, bool &want,
+                       bool integrator_forces = false) {
   long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] ions found, [7] error word
   want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state || out->cls;
   B = StateBufs{};
@@ -1054,7 +1113,8 @@ static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, St
   B.sort_tmp = ctx->d_sort_tmp;
   B.sort_tmp_bytes = ctx->sort_tmp_bytes;
   B.vel_src = ctx->d_vel;
-  B.frc_src = ctx->fcons_valid ? ctx->d_fcons : nullptr;
+  if (integrator_forces) B.frc_src = ctx->f_valid ? ctx->d_frc : nullptr;  // a checkpoint: the next half kick's forces
+  else B.frc_src = ctx->fcons_valid ? ctx->d_fcons : nullptr;
   B.xyz = out->xyz ? ctx->d_out_xyz : nullptr;
   B.vel = out->vel ? ctx->d_out_vel : nullptr;
   B.frc = out->force ? ctx->d_out_frc : nullptr;
@@ -1128,6 +1188,23 @@ extern "C" int cr_state(cr_ctx *ctx, cr_state_view *out) {
   return CR_OK;
 }
 
+extern "C" int cr_checkpoint(cr_ctx *ctx, cr_state_view *out, cr_counters *counters) {
+  if (!ctx || !out || !counters) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  StateBufs B;
+  bool want = false;
+  int rc = state_begin(ctx, out, s, B, want, true);
+  if (rc != CR_OK) return rc;
+  CR_CUDA(cudaStreamSynchronize(s));
+  rc = state_arrays(ctx, out, s, B, want);
+  if (rc != CR_OK) return rc;
+  if (want) CR_CUDA(cudaStreamSynchronize(s));
+  counters->sweep = ctx->sweep;
+  counters->md_eval = ctx->md_eval;
+  counters->forces_valid = ctx->f_valid ? 1 : 0;
+  return CR_OK;
+}
+
 extern "C" int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int32_t n,
                          uint32_t *out) {
   if (n < 0 || (n > 0 && !out)) return CR_ERR_INVALID_ARG;
@@ -1163,6 +1240,61 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
   CR_CUDA(launch_load(P, I, B, ctx->d_perm, ctx->n_input, s));
   ctx->launches_total += 3;
   ctx->f_valid = false;
+  ctx->fcons_valid = false;
+  return CR_OK;
+}
+
+extern "C" int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const float *force,
+                          const uint64_t *id, const int32_t *type, const int32_t *cls, const int8_t *state,
+                          const cr_counters *counters) {
+  if (!ctx || !counters || n < 0 || n > ctx->capacity) return CR_ERR_INVALID_ARG;
+  if (n > 0 && (!xyz || !type || !cls || !state || !id)) return CR_ERR_INVALID_ARG;
+  if (counters->forces_valid && n > 0 && !force) return CR_ERR_INVALID_ARG;
+  if (counters->sweep > (uint64_t)UINT32_MAX / (uint64_t)std::max(ctx->P.ncol, 1)) return CR_ERR_INVALID_ARG;
+  // ids: unique; every bonded / site particle of cr_init present; the others
+  // input ions (below the input count) or inserted ions (at least 2^32)
+  {
+    std::vector<char> seen((size_t)std::max(ctx->n_input, 1), 0);
+    std::vector<uint64_t> ions;
+    for (int32_t i = 0; i < n; ++i) {
+      const uint64_t d = id[i];
+      if (d < (uint64_t)ctx->n_input) {
+        if (seen[d]) return CR_ERR_INVALID_ARG;
+        seen[d] = 1;
+      } else if (d >> 32) {
+        ions.push_back(d);
+      } else {
+        return CR_ERR_INVALID_ARG;
+      }
+    }
+    for (int i = 0; i < ctx->n_input; ++i)
+      if (!seen[i] && ctx->init_type[i] != CR_XP && ctx->init_type[i] != CR_XM) return CR_ERR_INVALID_ARG;
+    std::sort(ions.begin(), ions.end());
+    if (std::adjacent_find(ions.begin(), ions.end()) != ions.end()) return CR_ERR_INVALID_ARG;
+  }
+  if (!ctx->d_in_id) CR_CUDA(cudaMalloc((void **)&ctx->d_in_id, sizeof(unsigned long long) * (size_t)ctx->capacity));
+  if (!ctx->d_in_frc) CR_CUDA(cudaMalloc((void **)&ctx->d_in_frc, sizeof(float) * 3 * (size_t)ctx->capacity));
+  const SysParams &P = ctx->P;
+  cudaStream_t s = ctx->stream;
+  const bool with_f = counters->forces_valid != 0;
+  if (n > 0) {
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (vel) CR_CUDA(cudaMemcpyAsync(ctx->d_in_vel, vel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    if (with_f) CR_CUDA(cudaMemcpyAsync(ctx->d_in_frc, force, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_id, id, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_type, type, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
+  }
+  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * 6, s));
+  LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
+             ctx->d_in_state, n, ctx->n_input, ctx->d_init_type, ctx->d_in_id, with_f ? ctx->d_in_frc : nullptr};
+  RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
+  CR_CUDA(launch_load(P, I, B, ctx->d_perm, ctx->n_input, s));
+  ctx->launches_total += 3;
+  ctx->sweep = counters->sweep;
+  ctx->md_eval = counters->md_eval;
+  ctx->f_valid = with_f;
   ctx->fcons_valid = false;
   return CR_OK;
 }
@@ -1237,6 +1369,7 @@ extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t 
 // ---------------------------------------------------------------------------
 struct cr_batch {
   std::vector<cr_ctx *> ctx;
+  std::vector<int> chem_seen;  // each context's chemistry version in d_reps
   SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
   PhaseShape S{}, Sc{};
   bool C = false, da_C = false;
@@ -1333,6 +1466,7 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   cr_batch *b = new (std::nothrow) cr_batch();
   if (!b) return CR_ERR_NOMEM;
   b->ctx.assign(ctxs, ctxs + n);
+  for (int r = 0; r < n; ++r) b->chem_seen.push_back(ctxs[r] ? ctxs[r]->chem_version : 0);
   std::vector<SysParams> reps(n);
   int maxR = 1;
   for (int r = 0; r < n; ++r) {
@@ -1426,6 +1560,17 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
         changed = true;
       }
     }
+    if (changed)
+      CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice, s));
+  }
+  {  // a context's pH changed (cr_set_pH): its copy in the batch follows
+    bool changed = false;
+    for (int r = 0; r < n; ++r)
+      if (b->chem_seen[r] != b->ctx[r]->chem_version) {
+        b->reps[r].lnsalt_fx = b->ctx[r]->P.lnsalt_fx;
+        b->chem_seen[r] = b->ctx[r]->chem_version;
+        changed = true;
+      }
     if (changed)
       CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice, s));
   }

@@ -61,6 +61,8 @@ struct LoadBufs {
   const int8_t *state;
   int n, n_site_map;
   const int *init_type;  // [n_site_map] types given to cr_init (bonded and site particles stay at their index)
+  const unsigned long long *id;  // [n] particle ids (a restore), or null: the ids are the indices
+  const float *frc;              // [3n] integrator forces (a restore), or null: zero
 };
 
 // one replica's load in a batched load

@@ -389,8 +389,11 @@ __device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs
   if (i >= I.n) return;
   const float x = I.xyz[3 * i], y = I.xyz[3 * i + 1], z = I.xyz[3 * i + 2];
   const int t = I.type[i];
-  {  // the particle must be valid and a bonded / site particle of cr_init must keep its index and type
-    const int ti = i < I.n_site_map ? I.init_type[i] : CR_XP;
+  // particle id: given (a restore; the host checked that the ids are unique
+  // and complete) or the index
+  const unsigned long long pid = I.id ? I.id[i] : (unsigned long long)i;
+  {  // the particle must be valid and a bonded / site particle of cr_init must keep its id and type
+    const int ti = pid < (unsigned long long)I.n_site_map ? I.init_type[pid] : CR_XP;
     const bool fixed = ti != CR_XP && ti != CR_XM;
     const bool ok = t >= CR_BEAD && t <= CR_CORE && I.cls[i] >= 0 && I.cls[i] <= 3 && x >= 0.0f && x < P.Lf &&
                     y >= 0.0f && y < P.Lf && z >= 0.0f && z < P.Lf && (fixed ? t == ti : (t == CR_XP || t == CR_XM));
@@ -412,7 +415,7 @@ __device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs
                    : t == CR_XP ? K_XP : (t == CR_XM ? K_XM : K_OTHER);
     if (kd < K_OTHER) atomicAdd((unsigned long long *)&P.counts[kd], 1ull);
   }
-  const int site = (i < I.n_site_map && I.site[i] >= 0) ? I.site[i] : 0;
+  const int site = (pid < (unsigned long long)I.n_site_map && I.site[pid] >= 0) ? I.site[pid] : 0;
   const int nc = P.nc;
   const int cell = cell_of(x, P.scf, nc) + nc * (cell_of(y, P.scf, nc) + nc * cell_of(z, P.scf, nc));
   const int s = atomicAdd(&B.cnt[cell], 1);
@@ -422,10 +425,10 @@ __device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs
   }
   const int o = cell * P.cap + s;
   B.pos[o] = make_float4(x, y, z, q);
-  B.pid[o] = (unsigned long long)i;
+  B.pid[o] = pid;
   B.info[o] = t | (cl << INFO_CLS_SHIFT) | (ion ? INFO_ION_BIT : 0) | (site << INFO_SITE_SHIFT);
   B.vel[o] = I.vel ? make_float4(I.vel[3 * i], I.vel[3 * i + 1], I.vel[3 * i + 2], 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
-  B.frc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+  B.frc[o] = I.frc ? make_float4(I.frc[3 * i], I.frc[3 * i + 1], I.frc[3 * i + 2], 0.0f) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {

@@ -3,12 +3,17 @@
 // a library allocate device memory while they run (an MD engine that owns
 // every device buffer through its own pool; a time-critical loop in which a
 // device allocation, which may synchronise the whole device, is not
-// acceptable).  The paper has no counterpart; the forces are those of
-// cr_md_forces (same kernels, same exact fixed-point sums).
+// acceptable).  The paper has no counterpart.  The forces are those of
+// cr_md_forces bit for bit: the same pair terms summed in the same exact
+// 2^-24 fixed point.  This entry runs the force kernel's variant that
+// finishes each particle on lane 0 of its warp (no per-particle sum buffer,
+// no flat-frame distances), which is slower than the split form
+// cr_md_forces uses but needs no scratch beyond the particle list; the
+// flat-frame differences equal the minimum-image ones exactly, so the two
+// variants agree to the bit.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "crmc.h"
 #include "crmc_common.h"
@@ -35,21 +40,16 @@ static __device__ __align__(256) int g_md_scratch[CR_NOALLOC_SCRATCH_HEAD + CR_N
 namespace {
 
 constexpr int SCRATCH_HEAD = CR_NOALLOC_SCRATCH_HEAD;
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-int *g_scratch_ptr[MAX_DEVICES] = {};
 
-// Address of the scratch on the current device, looked up once per device.
-int scratch_on_device(int device, int **out) {
-  if (device < 0 || device >= MAX_DEVICES) return CR_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[device]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_md_scratch);
-    if (e != cudaSuccess || !p) return e == cudaErrorMemoryAllocation ? CR_ERR_NOMEM : CR_ERR_CUDA;
-    g_scratch_ptr[device] = static_cast<int *>(p);
-  }
-  *out = g_scratch_ptr[device];
+// Address of the scratch on the current device.  Host code sees the array's
+// name only as a host-side stand-in, so the device address is looked up on
+// every call (cheap next to the call's synchronisation); a cached address
+// would go stale after a device reset.
+int scratch_on_device(int **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_md_scratch);
+  if (e != cudaSuccess || !p) return e == cudaErrorMemoryAllocation ? CR_ERR_NOMEM : CR_ERR_CUDA;
+  *out = static_cast<int *>(p);
   return CR_OK;
 }
 
@@ -81,7 +81,7 @@ extern "C" int cr_md_forces_noalloc(cr_ctx *ctx, float *force, uint64_t *id, int
   if (cudaGetDevice(&current) != cudaSuccess) return CR_ERR_CUDA;
   if (current != ctx_device(ctx)) return CR_ERR_INVALID_ARG;  // the context's device must be current
   int *scratch = nullptr;
-  int rc = scratch_on_device(current, &scratch);
+  int rc = scratch_on_device(&scratch);
   if (rc != CR_OK) return rc;
   float4 *f4 = reinterpret_cast<float4 *>(force);
   rc = ctx_md_forces_into(ctx, f4, scratch + SCRATCH_HEAD, scratch, (int)ctx_capacity(ctx));

@@ -8,8 +8,10 @@
 // tcgen05.mma (cta_group::1, M = 128) accumulating FP32 in tensor memory,
 // and an epilogue that reads the accumulator with tcgen05.ld and applies
 // bias + ReLU, the ReLU mask of the backward pass, the output layer and loss
-// (fused into the last forward product), or split-K atomic accumulation of
-// the weight gradients.  One warp issues the TMA copies, one thread the MMAs;
+// (fused into the last forward product), or, for the weight gradients, one
+// slice per split of K (the batch) that a second kernel sums in split order
+// (deterministic; only the exposed product cr_mma_bf16 accumulates with
+// atomics).  One warp issues the TMA copies, one thread the MMAs;
 // every wait on an mbarrier has an iteration limit after which the CTA
 // records an error, lets its copies and MMAs in flight finish (again with a
 // limit), frees its tensor memory and returns.
@@ -71,6 +73,8 @@ struct GemmEpi {
   int ldt3;
   float *gb3, *gw4, *gb4, *loss;
   int *err;
+  uint32_t spin;      // polls of every bounded mbarrier wait (0: SPIN_LIMIT)
+  int withhold_first; // self-test only: the producer issues no copy for the first K slice
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,8 +95,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 // bounded wait on a phase of an mbarrier: false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < SPIN_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -261,12 +265,16 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  const uint32_t lim = E.spin ? E.spin : SPIN_LIMIT;
   int fail = 0;
   int issued = 0;  // producer: stages whose copies were issued
+  // the self-test withholds the first slice (its MMA issuer's wait runs out;
+  // nothing of that slice is in flight, so the drain below skips it)
+  const int first_issued = E.withhold_first ? 1 : 0;
   if (nk > 0 && warp == 0 && lane == 0) {  // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
+    for (int kb = first_issued; kb < nk; ++kb) {
       const int s = kb % GSTAGES;
-      if (kb >= GSTAGES && !mbar_wait(&empty[s], ((kb / GSTAGES) - 1) & 1)) {
+      if (kb >= GSTAGES && !mbar_wait(&empty[s], ((kb / GSTAGES) - 1) & 1, lim)) {
         fail = 1;
         break;
       }
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(128, 1)
   } else if (nk > 0 && warp == 1 && lane == 0) {  // MMA issuer
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % GSTAGES;
-      if (!mbar_wait(&full[s], (kb / GSTAGES) & 1)) {
+      if (!mbar_wait(&full[s], (kb / GSTAGES) & 1, lim)) {
         fail = 1;
         break;
       }
@@ -292,7 +300,7 @@ __global__ void __launch_bounds__(128, 1)
     umma_commit(done);  // completes when every MMA issued above has finished
   }
   // everyone: wait for the accumulator (bounded), agree on failure
-  bool ok = nk == 0 || mbar_wait(done, 0);
+  bool ok = nk == 0 || mbar_wait(done, 0, lim);
   fail = __syncthreads_or(fail || !ok);
   tc_fence_after();
 
@@ -438,7 +446,8 @@ __global__ void __launch_bounds__(128, 1)
   if (fail) {
     // let this CTA's copies in flight land before its shared memory goes away
     if (warp == 0 && lane == 0)
-      for (int kb = max(0, issued - GSTAGES); kb < issued; ++kb) mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1);
+      for (int kb = max(first_issued, issued - GSTAGES); kb < issued; ++kb)
+        mbar_wait(&full[kb % GSTAGES], (kb / GSTAGES) & 1, lim);
     if (threadIdx.x == 0) atomicOr(E.err, ERRB_TIMEOUT);
   }
   tc_fence_before();
@@ -808,9 +817,8 @@ extern "C" int cr_train_gradients(cr_trainer *t, const float *X, const float *ta
   return train_check(t);
 }
 
-extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss) {
-  int rc = train_grads(t, X, target, batch);
-  if (rc != CR_OK) return rc;
+// Adam on the masters from the gradients in t->G, then the BF16 copies
+static int adam_update(cr_trainer *t) {
   t->step++;
   const double c1 = 1.0 - std::pow(t->beta1, (double)t->step), c2 = 1.0 - std::pow(t->beta2, (double)t->step);
   k_adam<<<(N_PARAMS + 255) / 256, 256, 0, t->stream>>>(t->P, t->G, t->Mm, t->Vv, N_PARAMS, (float)t->lr,
@@ -818,13 +826,37 @@ extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target,
                                                          (float)c2);
   k_weights_bf16<<<(MLP_H * MLP_H + 255) / 256, 256, 0, t->stream>>>(t->P, t->C);
   t->launches += 2;
-  if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
+extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss) {
+  int rc = train_grads(t, X, target, batch);
+  if (rc != CR_OK) return rc;
+  if ((rc = adam_update(t)) != CR_OK) return rc;
   if (loss) {
     if (cudaMemcpyAsync(loss, t->loss, sizeof(float), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
       return CR_ERR_CUDA;
     return train_check(t);
   }
   return CR_OK;
+}
+
+extern "C" int cr_train_apply(cr_trainer *t, const float *grads) {
+  if (!t || !grads) return CR_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(t->G, grads, sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice, t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  const int rc = adam_update(t);
+  if (rc != CR_OK) return rc;
+  return cudaStreamSynchronize(t->stream) == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
+extern "C" int cr_train_moments(cr_trainer *t, float *m, float *v) {
+  if (!t) return CR_ERR_INVALID_ARG;
+  if (m && cudaMemcpyAsync(m, t->Mm, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  if (v && cudaMemcpyAsync(v, t->Vv, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
+    return CR_ERR_CUDA;
+  return cudaStreamSynchronize(t->stream) == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
 extern "C" int cr_train_get(cr_trainer *t, float *params, uint16_t *W1, float *b1, uint16_t *W2, float *b2,
@@ -864,15 +896,60 @@ extern "C" int cr_train_stats(const cr_trainer *t, int64_t *steps, int64_t *laun
   return CR_OK;
 }
 
+// error word of the exposed products (cr_mma_bf16, cr_selftest_mma_timeout)
+static int *mma_err_word() {
+  static int *d_err = nullptr;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!d_err) {
+    if (cudaMalloc((void **)&d_err, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(d_err, 0, sizeof(int)) != cudaSuccess) {
+      cudaFree(d_err);
+      d_err = nullptr;
+    }
+  }
+  return d_err;
+}
+
+// read and clear the error word after a product: CR_ERR_TIMEOUT when a
+// bounded wait ran out
+static int mma_status(int *d_err, cudaStream_t s) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CR_ERR_CUDA;
+  if (e) {
+    if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return CR_ERR_CUDA;
+    return CR_ERR_TIMEOUT;
+  }
+  return CR_OK;
+}
+
+extern "C" int cr_selftest_mma_timeout(const uint16_t *A, const uint16_t *B, float *D, uint32_t polls, void *stream) {
+  if (!A || !B || !D || polls == 0) return CR_ERR_INVALID_ARG;
+  if (get_encode() != CR_OK) return CR_ERR_CUDA;
+  int *d_err = mma_err_word();
+  if (!d_err) return CR_ERR_NOMEM;
+  cudaStream_t s = (cudaStream_t)stream;
+  GemmEpi E{};
+  E.err = d_err;
+  E.outF = D;
+  E.ldf = 128;
+  E.spin = polls;
+  E.withhold_first = 1;
+  // one 128 x 128 tile, K = 64: a single slice, the one withheld
+  const int rc = launch_mma<128, EPI_STORE>(A, B, 128, 128, 64, 64, 64, 64, E, s);
+  if (rc != CR_OK) return rc;
+  return mma_status(d_err, s);
+}
+
 extern "C" int cr_mma_bf16(const uint16_t *A, const uint16_t *B, float *D, int32_t M, int32_t N, int32_t K,
                            int32_t accumulate, void *stream) {
   if (!A || !B || !D || M <= 0 || K <= 0 || K % 8 || !(N == 48 || N == 128)) return CR_ERR_INVALID_ARG;
   if (get_encode() != CR_OK) return CR_ERR_CUDA;
-  static int *d_err = nullptr;
-  if (!d_err) {
-    if (cudaMalloc((void **)&d_err, sizeof(int)) != cudaSuccess) return CR_ERR_NOMEM;
-    cudaMemset(d_err, 0, sizeof(int));
-  }
+  int *d_err = mma_err_word();
+  if (!d_err) return CR_ERR_NOMEM;
   cudaStream_t s = (cudaStream_t)stream;
   GemmEpi E{};
   E.err = d_err;
@@ -885,13 +962,5 @@ extern "C" int cr_mma_bf16(const uint16_t *A, const uint16_t *B, float *D, int32
                    : (accumulate ? launch_mma<128, EPI_ATOMIC>(A, B, M, N, K, K, K, ks, E, s)
                                  : launch_mma<128, EPI_STORE>(A, B, M, N, K, K, K, ks, E, s));
   if (rc != CR_OK) return rc;
-  int e = 0;
-  if (cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return CR_ERR_CUDA;
-  if (e) {
-    cudaMemset(d_err, 0, sizeof(int));
-    return CR_ERR_TIMEOUT;
-  }
-  return CR_OK;
+  return mma_status(d_err, s);
 }

@@ -24,14 +24,18 @@ def de_tol(lo):
     return DE_REL * lo["S"] + 1e-9
 
 
-def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8):
+def compare_logs(w, lg, n_trials, seed, oracle_kw=None, max_ties=8, prep=None):
     """Run the oracle over the same trials (forcing tie decisions) and
-    compare with the GPU trial log.  Returns (oracle, oracle log, ties)."""
+    compare with the GPU trial log.  prep (optional) brings every fresh
+    oracle to the state the GPU log starts from (earlier calls, a pH change).
+    Returns (oracle, oracle log, ties)."""
     oracle_kw = oracle_kw or {}
     forced = np.full(n_trials, -1, np.int8)
     ties = 0
     while True:
         o = oracle.Oracle(w, **oracle_kw)
+        if prep is not None:
+            prep(o)
         lo = o.sweep(n_trials, seed, log=True, forced=forced)["log"]
         assert np.array_equal(lg["move"], lo["move"]), _first(lg, lo, "move")
         bad = np.flatnonzero((lg["flags"] & STRUCT_FLAGS) != (lo["flags"] & STRUCT_FLAGS))

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "crmc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(cr_[a-z0-9_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(cr_[A-Za-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -54,7 +54,9 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_2109_07527_gb300 import crmc
     structs = {"cr_system": crmc.cr_system, "cr_mu_ions": crmc.cr_mu_ions, "cr_sweep_stats": crmc.cr_sweep_stats,
                "cr_state_view": crmc.cr_state_view, "cr_info": crmc.cr_info, "cr_mlp": crmc.cr_mlp,
-               "cr_load_args": crmc.cr_load_args, "cr_batch_packed": crmc.cr_batch_packed}
+               "cr_load_args": crmc.cr_load_args, "cr_batch_packed": crmc.cr_batch_packed,
+               "cr_counters": crmc.cr_counters, "cr_train_cfg": crmc.cr_train_cfg,
+               "cr_ungrouped": crmc.cr_ungrouped}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crmc.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')

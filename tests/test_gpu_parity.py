@@ -84,6 +84,19 @@ def test_parity_config3_nanoparticles(crmc):
     _parity(crmc, w, 8, 4)
 
 
+def test_parity_config3_full_size_nanoparticles(crmc):
+    """The nanoparticle pair at full size: two R = 5 cores with 1000 surface
+    sites each (acids on one, bases on the other), L = 100, 20 mM salt, at the
+    closest separation of the sweep (10.5: the cores' surfaces 0.5 sigma
+    apart), trial by trial."""
+    w = W.config3(separation=10.5, seed=2)
+    assert w.n_sites == 2000 and float(w.params["box_L"]) == 100.0
+    g, o, lg, lo, ties = _parity(crmc, w, 3, 6)
+    acc = lg["flags"] & 1
+    moves = set(np.unique(lg["move"][acc == 1]).tolist())
+    assert {0, 1, 2, 3} <= moves  # acid and base sites both change, both ways
+
+
 def test_parity_full_size_polyelectrolyte(crmc):
     """The benchmark workload itself (L = 120, 3200 sites, ~4000 ion pairs), two sweeps."""
     w = W.config2(seed=1)
@@ -285,6 +298,25 @@ def test_batch_matches_independent_oracle_runs(crmc):
         o = oracle.Oracle(w)
         o.sweep(o.trials_per_sweep * 4, _replica_seed(77, r))
         compare_states(g, o, w.n_sites)
+
+
+def test_batch_of_64_uneven_replicas_matches_oracle(crmc):
+    """The batched titration at full size: 64 replicas with chain lengths
+    log-uniform in [50, 1000], pH uniform in [2, 10] and boxes from 36.8 to
+    100 sigma (1 to 64 domains per colour) advanced together, one launch per
+    colour; every replica's final state equals the oracle run with its key."""
+    ws = W.config4(seed=1)
+    assert len(ws) == 64
+    ctxs = [crmc.Context(w) for w in ws]
+    nact = sorted({g.info["nd"] ** 3 // 8 for g in ctxs})
+    assert nact[0] == 1 and nact[-1] == 64
+    b = crmc.Batch(ctxs)
+    b.sweep(3, 91)
+    for r, (w, g) in enumerate(zip(ws, ctxs)):
+        o = oracle.Oracle(w)
+        o.sweep(o.trials_per_sweep * 3, _replica_seed(91, r))
+        compare_states(g, o, w.n_sites)
+    b.close()
 
 
 def test_batch_md_equals_per_context_md(crmc):

@@ -310,6 +310,49 @@ def test_pIX_from_reservoir_species(pH, pIS):
     assert abs(ch["pIX_minus"] + math.log10(a_minus)) < 1e-12
 
 
+@pytest.mark.parametrize("pH,pIS", [(2.0, 2.0), (4.0, 1.0), (7.0, 2.0), (9.5, 3.0), (12.0, 1.5)])
+def test_ungrouped_fractions_from_reservoir_species(pH, pIS):
+    """Ungrouping (Sec. II.D): the share of a subspecies in its group is its
+    activity over the group's summed activity (the reservoir species of App. C
+    as in the test above); reached both at creation and through set_pH."""
+    pOH = 14.0 - pH
+    s, h, oh = 10 ** -pIS, 10 ** -pH, 10 ** -pOH
+    a_plus = s + h + max(oh - h, 0.0)
+    a_minus = s + oh + max(h - oh, 0.0)
+    want = dict(p_Sp=s / a_plus, p_H=h / a_plus, p_Sm=s / a_minus, p_OH=oh / a_minus)
+    w = W.ideal(n_sites=4, pH=pH, pIS=pIS, n_pairs=2, seed=1, schedule=1, trials_per_domain=4)
+    o = oracle.Oracle(w)
+    w2 = W.ideal(n_sites=4, pH=7.5 if pH != 7.5 else 3.0, pIS=pIS, n_pairs=2, seed=1, schedule=1,
+                 trials_per_domain=4)
+    o2 = oracle.Oracle(w2)
+    o2.set_pH(pH)
+    for u in (o.ungroup(), o2.ungroup()):
+        for k, v in want.items():
+            assert abs(u[k] - v) <= 1e-12 * v, (k, u[k], v)
+        assert u["p_Sp"] + u["p_H"] <= 1.0 + 1e-12 and u["p_Sm"] + u["p_OH"] <= 1.0 + 1e-12
+
+
+@pytest.mark.parametrize("pH0,pH1", [(3.0, 6.0), (6.5, 4.5)])
+def test_set_pH_moves_the_titration_to_its_exact_value(pH0, pH1):
+    """A time-dependent pH (App. B): an ideal box equilibrated at pH0 and then
+    switched to pH1 titrates to the exact finite-box value at pH1 (and pI_X
+    follows Eq. pIXgen at the new pH)."""
+    n, L, pIS, sig = 50, 40.0, 2.0, 0.355
+    w = W.ideal(n_sites=n, L=L, pH=pH0, pKa=5.0, pIS=pIS, n_pairs=20, seed=12, schedule=1, trials_per_domain=256)
+    o = oracle.Oracle(w)
+    o.sweep(o.trials_per_sweep * 40, 3)
+    o.set_pH(pH1)
+    ch = o.chem()
+    ref = -math.log10(10 ** -pIS + 10 ** -min(pH1, 14.0 - pH1))
+    assert abs(ch["pIX_plus"] - ref) < 1e-12 and abs(ch["pOH"] - (14.0 - pH1)) < 1e-12
+    ln10 = math.log(10.0)
+    lnV = math.log(0.602214076 * (L * sig) ** 3)
+    a_ex = exact_alpha(n, ln10 * (pH1 - 5.0), lnV - ln10 * ch["pIX_plus"], lnV - ln10 * ch["pIX_minus"])
+    mean, se = run_alpha(o, n, 40, 4096, seed=200 + int(10 * pH1))
+    assert abs(mean - a_ex) <= max(4.0 * se, 0.002), (mean, se, a_ex)
+    assert abs(mean - a_ex) <= 0.005
+
+
 # ---------------------------------------------------------------- exact enumeration
 def dsf_energy_states(w, n):
     """E(s) for all 2^n site states from the DSF definition (scipy erfc)."""
