@@ -337,8 +337,10 @@ def measured_tensor_peak():
     return FALLBACK_BF16_TFLOPS, "fallback"
 
 
-# unlogged sweeps that time every launch shape once (the tuner has 12 plain shapes)
+# unlogged sweeps that time every launch shape once: 12 plain shapes for a
+# context; for a batch each of them also as a persistent sweep (24)
 TUNE_SWEEPS = 14
+BATCH_TUNE_SWEEPS = 26
 
 # floating-point operations of one training row (algorithmic, K = 48 input):
 # forward 48x128 + 2 x 128x128, backward 4 x 128x128 + 128x48, 2 flops per MAC
@@ -401,7 +403,7 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     for c in ctxs:
         c.set_surrogate(mlp)
     b = crmc.Batch(ctxs)
-    b.sweep_da(5, 0xDA)  # launch-shape tuning of the DA variant
+    b.sweep_da(12, 0xDA)  # launch-shape tuning of the DA variant (5 shapes, each in both launch forms)
     for s in range(3):
         b.md_begin(dt, gamma, 1000 + s)
         b.sweep_da(1, 1 + s)
@@ -465,7 +467,7 @@ def run_ours(args):
     batch = crmc.Batch(ctxs)
     per_rep = ctxs[0].trials_per_sweep
     per_step = per_rep * len(ctxs)
-    batch.sweep(TUNE_SWEEPS, 0xABC)  # launch-shape tuning (one shape per sweep)
+    batch.sweep(BATCH_TUNE_SWEEPS, 0xABC)  # launch-shape tuning (one shape and launch form per sweep)
     for s in range(args.warmup):
         batch.md_begin(dt, gamma, 1000 + s)
         batch.sweep(1, 1 + s)
@@ -501,16 +503,20 @@ def run_ours(args):
     L = float(ws[0].params["box_L"])
     rc = float(ws[0].params["rc"])
     info = g0.info
-    launches_per_step = info["ncol"]
-    trials_per_launch = per_rep / launches_per_step
+    # the batch's sweep kernel: one persistent launch per sweep (every colour
+    # of every replica), or one launch per colour
+    launches_per_step = tm["phase_launches"] / args.steps
+    trials_per_launch = per_rep / launches_per_step  # per replica
     bytes_launch = sum(trials_per_launch * bytes_per_trial(L, rc, c["n"]) for c in counts)
     avg_launch_s = tm["phase_ms"] / max(tm["phase_launches"], 1) / 1e3
     achieved = bytes_launch / avg_launch_s / 1e9
+    kname = ("k_cr_sweep (persistent: all colours of the 13 replicas per launch)" if launches_per_step < 1.5
+             else "k_cr_phase (one colour of the 13 replicas per launch)")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "kernel": "k_cr_phase (13 replicas per launch)",
+                "traffic": profiled_traffic(), "kernel": kname,
                 "peak_source": peak_kind, "bytes_per_trial_mean": bytes_launch / (trials_per_launch * len(ctxs)),
-                "trials_per_launch": trials_per_launch * len(ctxs), "avg_launch_us": avg_launch_s * 1e6,
-                "phase_share_of_step": tm["phase_ms"] / ms}
+                "trials_per_launch": trials_per_launch * len(ctxs), "launches_per_step": launches_per_step,
+                "avg_launch_us": avg_launch_s * 1e6, "phase_share_of_step": tm["phase_ms"] / ms}
 
     # ---- plain path: one replica (pH 4.5), same step definition
     plain = None
@@ -536,7 +542,8 @@ def run_ours(args):
         g1.check()
         c1 = g1.counts()
         al = tm1["phase_ms"] / max(tm1["phase_launches"], 1) / 1e3
-        ach1 = trials_per_launch * bytes_per_trial(L, rc, c1["n"]) / al / 1e9
+        tpl1 = g1.trials_per_sweep / (tm1["phase_launches"] / n_plain)
+        ach1 = tpl1 * bytes_per_trial(L, rc, c1["n"]) / al / 1e9
         plain = {"value": g1.trials_per_sweep * n_plain / (ms1 / 1e3), "unit": "trials/s", "steps": n_plain,
                  "ms_per_step": ms1 / n_plain, "launch_shape": list(g1.launch_shape()),
                  "roofline": {"achieved": ach1, "frac": ach1 / peak, "avg_launch_us": al * 1e6},

@@ -462,6 +462,31 @@ int cr_batch_load_packed(cr_batch *b, const cr_batch_packed *p);
  * concurrently on the batch's streams with two synchronisations in all.
  * Returns the first error of a replica. */
 int cr_batch_state(cr_batch *b, cr_state_view *views);
+/* Persistent sweeps (mode 1): a batch sweep is one launch in
+ * which CTAs claim (colour, replica, domain) tasks in that order and a domain
+ * of colour c > 0 starts once its neighbouring domains of lower colours have
+ * finished (a domain's phase reads only its own and its neighbours' cells,
+ * Sec. II.C's moves being local to it) -- so colours overlap within and
+ * across replicas and no colour phase waits for the slowest domain of the
+ * batch.  Mode 2: a domain waits for its replica's whole previous colour
+ * (also what mode 1 does when a replica's halo reaches past its neighbouring
+ * domains).  Mode 0: one launch per colour.  Mode -1 (the default): the
+ * launch-shape tuner times every shape in both forms (mode 1 and mode 0) and
+ * keeps the fastest; fixing a shape with cr_batch_set_launch_shape then
+ * selects mode 0 unless a mode was set.  ctas_per_sm > 0 caps the
+ * resident CTAs per SM of a persistent launch (0: as many as fit).  Every
+ * wait is bounded in time; one that runs out sets CR_ERR_TIMEOUT on its
+ * replica and the rest of the sweep is skipped.  The chain is the same in
+ * every mode. */
+int cr_batch_set_persistent(cr_batch *b, int32_t mode, int32_t ctas_per_sm);
+/* Failure-detection self-test of those waits (no counterpart in the paper):
+ * one persistent sweep in which `replica` never reports that it finished
+ * colour 0, so the tasks of its colour 1 wait until timeout_ms (at most
+ * 10 s) runs out; the wait then records the timeout and the launch skips
+ * its remaining tasks and ends.  Returns CR_ERR_TIMEOUT when that path
+ * worked.  The replicas' chains are then incomplete (their contexts keep the
+ * error); the device stays usable.  Synchronises. */
+int cr_batch_selftest_wait_timeout(cr_batch *b, int32_t replica, double timeout_ms);
 /* Fix the batch's launch shape (as cr_set_launch_shape; 0, 0 restarts the tuning). */
 int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t regs);
 int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, int32_t *regs);

@@ -97,7 +97,8 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_train_destroy", "cr_mma_bf16", "cr_md_begin", "cr_md_end", "cr_batch_md_begin",
            "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
            "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
-           "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup")
+           "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup",
+           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -212,6 +213,10 @@ def _lib():
         lib.cr_batch_sweep.argtypes = [P, C.c_uint64, C.c_uint64]
         lib.cr_batch_md_step.restype = C.c_int
         lib.cr_batch_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        lib.cr_batch_set_persistent.restype = C.c_int
+        lib.cr_batch_set_persistent.argtypes = [P, C.c_int32, C.c_int32]
+        lib.cr_batch_selftest_wait_timeout.restype = C.c_int
+        lib.cr_batch_selftest_wait_timeout.argtypes = [P, C.c_int32, C.c_double]
         lib.cr_batch_set_launch_shape.restype = C.c_int
         lib.cr_batch_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
         lib.cr_batch_get_launch_shape.restype = C.c_int
@@ -559,6 +564,16 @@ class Batch:
 
     def set_launch_shape(self, threads, regs):
         _chk(self._lib.cr_batch_set_launch_shape(self._h, int(threads), int(regs)), "cr_batch_set_launch_shape")
+
+    def set_persistent(self, mode=1, ctas_per_sm=0):
+        """cr_batch_set_persistent: mode 1 per-domain dependencies (default), 2
+        per-colour ones, 0 (or False) one launch per colour."""
+        _chk(self._lib.cr_batch_set_persistent(self._h, int(mode), int(ctas_per_sm)), "cr_batch_set_persistent")
+
+    def selftest_wait_timeout(self, replica, timeout_ms):
+        """cr_batch_selftest_wait_timeout: the status code (CR_ERR_TIMEOUT = -5
+        when the bounded-wait path worked)."""
+        return int(self._lib.cr_batch_selftest_wait_timeout(self._h, int(replica), float(timeout_ms)))
 
     def launch_shape(self):
         t = C.c_int32()

@@ -516,6 +516,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   PhaseShape &S = c->S;
   S.nr3 = P.nr * P.nr * P.nr;
   S.kc3 = k * k * k;
+  S.chunk = std::min(P.m, TRIAL_CHUNK);
   // Shared-memory list and halo capacities: the densest domain of the
   // starting configuration with room for growth, and its densest halo.  The
   // compact set (Sc) is sized for the 90th percentile instead, so that more
@@ -615,7 +616,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     ALLOC(c->d_out_site, (size_t)std::max(c->n_sites, 1));
   }
   {
-    const size_t ng = (size_t)P.nact * P.dcap_glob;
+    // one region per (colour, active domain): a persistent batch sweep may run
+    // domains of several colours of one replica at the same time
+    const size_t ng = (size_t)P.ncol * P.nact * P.dcap_glob;
     ALLOC(c->d_gs_pos, ng);
     ALLOC(c->d_gs_vel, ng);
     ALLOC(c->d_gs_id, ng);
@@ -793,18 +796,25 @@ static int grow(TT **p, size_t *cap, size_t n) {
 // Online launch-shape tuning (shared by plain and delayed-acceptance sweeps):
 // the first sweeps of unlogged calls time each shape of the set once (shapes
 // whose shared memory does not fit are skipped), then the fastest is kept.
+// For batches whose persistent mode is left to the tuner (pers != null), the
+// candidates are every shape with one launch per colour, then every shape as
+// a persistent sweep; *pers receives the chosen mode.
 struct TuneRef {
   int &T, &R, &next;
   bool &on;
   float *ms;
   bool &C;  // the chosen shape uses the compact capacities
+  bool *pers = nullptr;
 };
 
+static int tune_count(const TuneRef &t, bool da) { return phase_shape_count(da) * (t.pers ? 2 : 1); }
+
 static void tune_skip(TuneRef t, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
-  while (t.on && t.next < phase_shape_count(da)) {
+  const int nshape = phase_shape_count(da);
+  while (t.on && t.next < tune_count(t, da)) {
     int t_, r_;
-    phase_shape(t.next, &t_, &r_, da);
-    const PhaseShape &Q = phase_shape_compact(t.next, da) ? Sc : S;
+    phase_shape(t.next % nshape, &t_, &r_, da);
+    const PhaseShape &Q = phase_shape_compact(t.next % nshape, da) ? Sc : S;
     if (phase_shape_smem(Q, t_, r_, da) <= (size_t)smem_max) break;
     t.ms[t.next++] = 1e30f;
   }
@@ -813,12 +823,14 @@ static void tune_skip(TuneRef t, const PhaseShape &S, const PhaseShape &Sc, int 
 static void tune_finish(TuneRef t, float ms, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
   t.ms[t.next++] = ms;
   tune_skip(t, S, Sc, smem_max, da);
-  if (t.next == phase_shape_count(da)) {
+  const int nshape = phase_shape_count(da);
+  if (t.next == tune_count(t, da)) {
     int best = 0;
-    for (int i = 1; i < phase_shape_count(da); ++i)
+    for (int i = 1; i < tune_count(t, da); ++i)
       if (t.ms[i] < t.ms[best]) best = i;
-    phase_shape(best, &t.T, &t.R, da);
-    t.C = phase_shape_compact(best, da);
+    phase_shape(best % nshape, &t.T, &t.R, da);
+    t.C = phase_shape_compact(best % nshape, da);
+    if (t.pers) *t.pers = best >= nshape;
     t.on = false;
   }
 }
@@ -1370,6 +1382,20 @@ extern "C" int cr_get_launch_shape(const cr_ctx *ctx, int32_t *threads, int32_t 
 struct cr_batch {
   std::vector<cr_ctx *> ctx;
   std::vector<int> chem_seen;  // each context's chemistry version in d_reps
+  // persistent sweeps (k_cr_sweep): on by default; the replicas' prefix of
+  // active domains per colour and the launch's device words (task counter,
+  // abort flag, per-(replica, colour) completion counters), zeroed per launch
+  int pmode = -1;              // persistent mode: -1 chosen by the tuner, 0 off, 1 per-domain, 2 per-colour
+  bool persistent = true;      // the mode in use (auto: the tuner's choice once it finished)
+  bool da_persistent = true;
+  bool fine = false;           // per-domain dependencies (every replica's halo within its neighbouring domains)
+  bool fine_ok = false;        // the geometry allows them
+  int ctas_per_sm = 0;         // resident CTAs per SM of a persistent sweep (0: as many as fit)
+  int *d_rep_first = nullptr;  // [n + 1] active domains per colour, then [n + 1] domains (prefix sums)
+  unsigned *d_words = nullptr;
+  size_t words = 0, flag_words = 0;
+  int tasks_per_colour = 0;
+  int sms = 0;
   SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
   PhaseShape S{}, Sc{};
   bool C = false, da_C = false;
@@ -1378,10 +1404,10 @@ struct cr_batch {
   int smem_max = 0;
   bool tuning = true;
   int tune_next = 0;
-  float tune_ms[16] = {};
+  float tune_ms[32] = {};
   int da_T = 128, da_R = 0, da_next = 0;
   bool da_tuning = true;
-  float da_ms[8] = {};
+  float da_ms[16] = {};
   std::vector<SysParams> reps;  // host copy of d_reps
   cudaStream_t stream = nullptr;  // the contexts' shared stream (destroy does not touch the contexts)
   int order_nc = 0, order_nact = 0;  // largest box and colour among replicas with a launch order (0: none)
@@ -1483,11 +1509,13 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     b->S.lns = std::max(b->S.lns, c->S.lns);
     b->S.nr3 = std::max(b->S.nr3, c->S.nr3);
     b->S.kc3 = std::max(b->S.kc3, c->S.kc3);
+    b->S.chunk = std::max(b->S.chunk, c->S.chunk);
     b->Sc.dcs = std::max(b->Sc.dcs, c->Sc.dcs);
     b->Sc.hcs = std::max(b->Sc.hcs, c->Sc.hcs);
     b->Sc.lns = std::max(b->Sc.lns, c->Sc.lns);
     b->Sc.nr3 = std::max(b->Sc.nr3, c->Sc.nr3);
     b->Sc.kc3 = std::max(b->Sc.kc3, c->Sc.kc3);
+    b->Sc.chunk = std::max(b->Sc.chunk, c->Sc.chunk);
     b->grid_x = std::max(b->grid_x, c->P.nact);
     maxR = std::max(maxR, c->R);
   }
@@ -1507,6 +1535,7 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctxs[0]->device);
   if (phase_smem_bytes(b->S, 512, false) > (size_t)smem_max) { delete b; return CR_ERR_INVALID_ARG; }
   b->smem_max = smem_max;
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, ctxs[0]->device);
   if (cudaMalloc((void **)&b->d_reps, sizeof(SysParams) * n) != cudaSuccess) { delete b; return CR_ERR_NOMEM; }
   if (cudaMemcpy(b->d_reps, reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(b->d_reps);
@@ -1520,6 +1549,27 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     cudaEventCreateWithFlags(&b->events[r], cudaEventDisableTiming);
   }
   cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  {  // persistent-sweep schedule: per-domain dependencies when every
+     // replica's region (its domain and h cells around it) lies within the
+     // 3^3 block of domains around it (h <= k) and the schedule is coloured
+    std::vector<int> first(2 * (n + 1), 0);
+    bool fine = true;
+    for (int r = 0; r < n; ++r) {
+      first[r + 1] = first[r] + reps[r].nact;
+      first[n + 1 + r + 1] = first[n + 1 + r] + reps[r].nd * reps[r].nd * reps[r].nd;
+      fine = fine && !reps[r].global && reps[r].h <= reps[r].k && reps[r].nd >= 2;
+    }
+    b->fine = b->fine_ok = fine;
+    b->tasks_per_colour = first[n];
+    b->flag_words = (size_t)first[2 * n + 1];
+    b->words = 2 + (size_t)n * b->ncol + b->flag_words;
+    if (cudaMalloc((void **)&b->d_rep_first, sizeof(int) * 2 * (n + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_words, sizeof(unsigned) * b->words) != cudaSuccess ||
+        cudaMemcpy(b->d_rep_first, first.data(), sizeof(int) * 2 * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cr_batch_destroy(b);
+      return CR_ERR_NOMEM;
+    }
+  }
   *out = b;
   return CR_OK;
 }
@@ -1534,6 +1584,8 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_reps) cudaFree(b->d_reps);
+  if (b->d_rep_first) cudaFree(b->d_rep_first);
+  if (b->d_words) cudaFree(b->d_words);
   free_packed_staging(b);
   void *dp[] = {b->d_sbufs, b->d_jobs, b->d_nout, b->d_errout};
   for (void *x : dp)
@@ -1542,6 +1594,35 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   for (void *x : hp)
     if (x) cudaFreeHost(x);
   delete b;
+}
+
+// one persistent sweep launch of every replica (words zeroed first)
+static int batch_launch_persistent(cr_batch *b, const PhaseShape &SS, int T, int R, bool da, uint32_t swc,
+                                   uint32_t sweep0, uint32_t k0, uint32_t k1, int withhold = -1,
+                                   unsigned long long wait_ns = 2000000000ull) {
+  cr_ctx *c0 = b->ctx[0];
+  cudaStream_t s = c0->stream;
+  CR_CUDA(cudaMemsetAsync(b->d_words, 0, sizeof(unsigned) * b->words, s));
+  SweepSched Q{};
+  Q.n_rep = (int)b->ctx.size();
+  Q.ncol = b->ncol;
+  Q.tasks_total = b->tasks_per_colour * b->ncol;
+  Q.fine = b->fine ? 1 : 0;
+  Q.rep_first = b->d_rep_first;
+  Q.dom_first = b->d_rep_first + b->ctx.size() + 1;
+  Q.next = b->d_words;
+  Q.abort = (int *)(b->d_words + 1);
+  Q.done = b->d_words + 2;
+  Q.flags = Q.done + b->ctx.size() * b->ncol;
+  Q.wait_ns = wait_ns;
+  Q.withhold_rep = withhold;
+  int ti;
+  tbegin(c0, 0, &ti);
+  const int sms = b->sms > 0 ? b->sms : 1;
+  CR_CUDA(launch_sweep(b->d_reps, SS, T, R, da, s, swc, sweep0, k0, k1, Q, b->ctas_per_sm * sms));
+  tend(c0, 0, ti);
+  c0->launches_total++;
+  return CR_OK;
 }
 
 static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool da) {
@@ -1576,8 +1657,12 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const uint32_t sweep0 = (uint32_t)c0->sweep;
+  bool &pers_choice = da ? b->da_persistent : b->persistent;
   TuneRef tr = da ? TuneRef{b->da_T, b->da_R, b->da_next, b->da_tuning, b->da_ms, b->da_C}
                   : TuneRef{b->T, b->R, b->tune_next, b->tuning, b->tune_ms, b->C};
+  if (b->pmode < 0) tr.pers = &pers_choice;
+  else pers_choice = b->pmode != 0;
+  const int nshape = phase_shape_count(da);
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)c0->sweep;
     for (cr_ctx *c : b->ctx) {
@@ -1586,13 +1671,15 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       c->fcons_valid = false;
     }
     tune_skip(tr, b->S, b->Sc, b->smem_max, da);
-    const bool tune = tr.on && tr.next < phase_shape_count(da);
+    const bool tune = tr.on && tr.next < tune_count(tr, da);
     int T = tr.T, R = tr.R;
-    const bool compact = tune ? phase_shape_compact(tr.next, da) : tr.C;
+    bool persistent = pers_choice;
+    const bool compact = tune ? phase_shape_compact(tr.next % nshape, da) : tr.C;
     const PhaseShape &SS = compact ? b->Sc : b->S;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
-      phase_shape(tr.next, &T, &R, da);
+      phase_shape(tr.next % nshape, &T, &R, da);
+      if (tr.pers) persistent = tr.next >= nshape;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
@@ -1601,12 +1688,17 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       CR_CUDA(launch_domain_order(b->d_reps, n, b->ncol, b->order_nact, s, swc, k0, k1));
       c0->launches_total++;
     }
-    for (int col = 0; col < b->ncol; ++col) {
-      int ti;
-      tbegin(c0, 0, &ti);
-      CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, SS, T, R, false, da, s, swc, sweep0, col, k0, k1));
-      tend(c0, 0, ti);
-      c0->launches_total++;
+    if (persistent) {
+      const int rc = batch_launch_persistent(b, SS, T, R, da, swc, sweep0, k0, k1);
+      if (rc != CR_OK) return rc;
+    } else {
+      for (int col = 0; col < b->ncol; ++col) {
+        int ti;
+        tbegin(c0, 0, &ti);
+        CR_CUDA(launch_phase(b->d_reps, n, b->grid_x, SS, T, R, false, da, s, swc, sweep0, col, k0, k1));
+        tend(c0, 0, ti);
+        c0->launches_total++;
+      }
     }
     if (tune) {
       cudaEventRecord(e1, s);
@@ -1623,6 +1715,47 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
 
 extern "C" int cr_batch_sweep(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
   return batch_sweep_impl(b, n_sweeps, seed, false);
+}
+
+extern "C" int cr_batch_set_persistent(cr_batch *b, int32_t mode, int32_t ctas_per_sm) {
+  if (!b || mode < -1 || mode > 2 || ctas_per_sm < 0) return CR_ERR_INVALID_ARG;
+  b->pmode = mode;
+  b->persistent = b->da_persistent = mode != 0;
+  b->fine = mode != 2 && b->fine_ok;
+  b->ctas_per_sm = ctas_per_sm;
+  return CR_OK;
+}
+
+extern "C" int cr_batch_selftest_wait_timeout(cr_batch *b, int32_t replica, double timeout_ms) {
+  if (!b || replica < 0 || replica >= (int)b->ctx.size() || !(timeout_ms > 0.0) || timeout_ms > 10000.0)
+    return CR_ERR_INVALID_ARG;
+  cr_ctx *c0 = b->ctx[0];
+  const uint32_t swc = (uint32_t)c0->sweep;
+  for (cr_ctx *c : b->ctx) {
+    c->sweep++;
+    c->f_valid = false;
+    c->fcons_valid = false;
+  }
+  int T = b->T, R = b->R;
+  const PhaseShape &SS = b->C ? b->Sc : b->S;
+  if (b->tuning) {  // a shape every context supports
+    T = 128;
+    R = 0;
+  }
+  if (b->order_nc > 0) {
+    CR_CUDA(launch_domain_order(b->d_reps, (int)b->ctx.size(), b->ncol, b->order_nact, c0->stream, swc, 1u, 0u));
+    c0->launches_total++;
+  }
+  const int rc = batch_launch_persistent(b, b->tuning ? b->S : SS, T, R, false, swc, swc, 1u, 0u, replica,
+                                         (unsigned long long)(timeout_ms * 1e6));
+  if (rc != CR_OK) return rc;
+  CR_CUDA(cudaStreamSynchronize(c0->stream));
+  int worst = CR_OK;
+  for (cr_ctx *c : b->ctx) {
+    const int e = cr_check(c);
+    if (e != CR_OK && worst == CR_OK) worst = e;
+  }
+  return worst;
 }
 
 extern "C" int cr_batch_sweep_da(cr_batch *b, uint64_t n_sweeps, uint64_t seed) {
@@ -1837,6 +1970,7 @@ extern "C" int cr_batch_set_launch_shape(cr_batch *b, int32_t threads, int32_t r
     b->tune_next = b->da_next = 0;
     return CR_OK;
   }
+  if (b->pmode < 0) b->persistent = b->da_persistent = false;  // a fixed shape without a fixed mode: per colour
   bool found = false;
   for (int da = 0; da < 2; ++da)
     for (int i = 0; i < phase_shape_count(da != 0); ++i) {

@@ -119,6 +119,7 @@ struct PhaseShape {
   int lns;     // log-table entries held in shared memory
   int nr3;     // region cells
   int kc3;     // domain cells
+  int chunk;   // trials whose random numbers are drawn at once (min(m, TRIAL_CHUNK))
 };
 
 // error bits in *err

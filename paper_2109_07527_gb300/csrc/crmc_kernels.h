@@ -82,6 +82,25 @@ bool phase_shape_compact(int i, bool da);  // shape i uses the compact list and 
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
                          uint32_t k0, uint32_t k1);
+// Schedule of a persistent sweep (k_cr_sweep): tasks (colour, replica, rank)
+// claimed in that order; next, done and abort are device words zeroed before
+// every launch.
+struct SweepSched {
+  int n_rep, ncol, tasks_total;
+  int fine;               // 1: per-domain dependencies (flags); 0: per-(replica, colour) counters (done)
+  const int *rep_first;   // [n_rep + 1] prefix sums of the replicas' active domains per colour
+  const int *dom_first;   // [n_rep + 1] prefix sums of the replicas' domain counts (flags)
+  unsigned *next;         // task counter
+  unsigned *done;         // [n_rep * ncol] finished tasks of each (replica, colour)
+  unsigned *flags;        // [dom_first[n_rep]] finished domains
+  int *abort;             // set when a wait ran out: the remaining tasks are skipped
+  unsigned long long wait_ns;  // limit of one dependency wait (ns)
+  int withhold_rep;       // self-test of the waits: this replica never reports colour 0 (-1: none)
+};
+// one sweep of every replica in one persistent launch; max_ctas > 0 caps the grid
+cudaError_t launch_sweep(const SysParams *d_reps, const PhaseShape &S, int threads, int R, bool da, cudaStream_t s,
+                         uint32_t sweep, uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q,
+                         int max_ctas);
 // launch order of every colour's domains for one sweep (densest region first);
 // does nothing for colours beyond the ordering limit
 cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, int nact, cudaStream_t s, uint32_t sweep,

@@ -22,6 +22,7 @@
 // (the domain's volume and counts).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -205,8 +206,8 @@ __device__ void warp_remove(DomList L, int n, int p) {
 // FP32 and WCA in FP64, into fixed point (without a WCA term the FP64 sum
 // reduces to the FP32 change, taken directly)
 template <bool WITH_S>
-__device__ __forceinline__ void cc_change(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
-                                          unsigned long long &sacc, int &ov) {
+__device__ __forceinline__ void cc_change_impl(const PairK &K, const WcaEntry *wca, const TrialCtl &t, long long &acc,
+                                               unsigned long long &sacc, int &ov) {
   const Desc &A = t.c[0], &B = t.c[1];
   const float dx = wrap_diff(B.x, A.x, K.Lf, K.halfL);
   const float dy = wrap_diff(B.y, A.y, K.Lf, K.halfL);
@@ -271,17 +272,29 @@ __device__ __forceinline__ void cc_change(const PairK &K, const WcaEntry *wca, c
   }
 }
 
+// Sums of pair terms returned by value from the out-of-line helpers, so that
+// the callers' accumulators stay in registers.
+struct PairSum {
+  long long acc;
+  unsigned long long sacc;
+  int ov;
+};
+
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int QCAP = 96;  // per-warp queue of Coulomb pair terms (up to 31 waiting + 64 new)
 
 // Metropolis comparison ln u < lnA with lnA in 2^-48 fixed point: the FP32
 // ln u decides outside LNU_BAND, the FP64 ln u inside it
+// (the FP64 logarithm of the band is out of line: rare, and large)
+__device__ __noinline__ bool accept_band(long long lnA_fx, uint32_t uhi, uint32_t ulo) {
+  return __double2ll_rn(log(unif53(uhi, ulo)) * LNFIX) < lnA_fx;
+}
 __device__ __forceinline__ bool accept_fx(long long lnA_fx, float lnu_f, uint32_t uhi, uint32_t ulo) {
   const long long lnu_apx = (long long)__float2int_rn(lnu_f * 16777216.0f) << 24;
   const long long diff = lnA_fx - lnu_apx;
   if (diff > LNU_BAND) return true;
   if (diff < -LNU_BAND) return false;
-  return __double2ll_rn(log(unif53(uhi, ulo)) * LNFIX) < lnA_fx;
+  return accept_band(lnA_fx, uhi, ulo);
 }
 
 // Maxwell-Boltzmann velocity of an inserted ion (unit mass, kT = 1): Box-Muller
@@ -376,39 +389,55 @@ __device__ __forceinline__ float sel4(const float4 v, int i) {
 }
 
 // A pair within the WCA range of an inserted / deleted changed particle:
-// Coulomb in FP32 and WCA in FP64, evaluated at once (rare)
+// Coulomb in FP32 and WCA in FP64, evaluated at once (rare).  Not inlined, to
+// keep the sweep's loop small; everything it needs comes by value or from
+// shared memory (P, w), and its sums come back by value.
 template <bool WITH_S>
-__device__ __noinline__ void near_pair(const PairK &K, const WcaEntry &w, const Desc &c, float xj, float yj, float zj,
-                                       float qj, float r2, long long &acc, unsigned long long &sacc, int &ov) {
+__device__ __noinline__ PairSum near_pair(const SysParams &P, const WcaEntry &w, float cx, float cy, float cz,
+                                          float cdq, int cdp, float xj, float yj, float zj, float qj, float r2) {
+  PairSum out{0, 0ull, 0};
   float du = 0.0f, gs = 0.0f;
-  const bool any = r2 < K.rc2 && c.dqlB != 0.0f && qj != 0.0f;
+  const bool any = r2 < P.rc2 && cdq != 0.0f && qj != 0.0f;
   if (any) {
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    const float e = erfcf(K.alpha * r) * rinv;
-    du = c.dqlB * qj * (e - K.c1 + K.c2 * (r - K.rcf));
-    if (WITH_S) gs = fabsf(c.dqlB * qj) * (e + K.c1 + K.c2 * fabsf(r - K.rcf));
+    const float e = erfcf(P.alpha * r) * rinv;
+    du = cdq * qj * (e - P.c1 + P.c2 * (r - P.rcf));
+    if (WITH_S) gs = fabsf(cdq * qj) * (e + P.c1 + P.c2 * fabsf(r - P.rcf));
   }
   double du_w = 0.0, gs_w = 0.0;
   int ovw = 0;
-  const bool hit = wca_change_d(w, c.dp, c.x, c.y, c.z, xj, yj, zj, K.Ld, K.halfLd, du_w, gs_w, ovw);
+  const bool hit = wca_change_d(w, cdp, cx, cy, cz, xj, yj, zj, P.Ld, P.halfLd, du_w, gs_w, ovw);
   if (ovw) {
-    ov = 1;
+    out.ov = 1;
   } else if (hit) {
     if (!(fabs((double)du + du_w) < (double)BIG_TERM)) {
-      ov = 1;
+      out.ov = 1;
     } else {
-      if (any) acc += fix32(du);
-      acc += __double2ll_rn(du_w * (double)FIX_SCALE);
-      if (WITH_S) sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + gs_w, (double)BIG_TERM) * (double)FIX_SCALE);
+      if (any) out.acc += fix32(du);
+      out.acc += __double2ll_rn(du_w * (double)FIX_SCALE);
+      if (WITH_S) out.sacc += (unsigned long long)__double2ll_rn(fmin((double)gs + gs_w, (double)BIG_TERM) * (double)FIX_SCALE);
     }
   } else if (any) {  // beyond the WCA cutoff after all: Coulomb only
-    if (!(fabsf(du) < BIG_TERM)) ov = 1;
+    if (!(fabsf(du) < BIG_TERM)) out.ov = 1;
     else {
-      acc += fix32(du);
-      if (WITH_S) sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
+      out.acc += fix32(du);
+      if (WITH_S) out.sacc += (unsigned long long)fix32(fminf(gs, BIG_TERM));
     }
   }
+  return out;
+}
+
+// the pair between the two changed particles (one thread per trial; out of
+// line, with its FP64 WCA branch)
+template <bool WITH_S>
+__device__ __noinline__ PairSum cc_change(const SysParams &P, const TrialCtl &t) {
+  PairK K;
+  K.Lf = P.Lf; K.halfL = P.halfL; K.rc2 = P.rc2; K.alpha = P.alpha; K.c1 = P.c1; K.c2 = P.c2; K.rcf = P.rcf;
+  K.lBf = P.lBf; K.Ld = P.Ld; K.halfLd = P.halfLd;
+  PairSum out{0, 0ull, 0};
+  cc_change_impl<WITH_S>(K, P.wca, t, out.acc, out.sacc, out.ov);
+  return out;
 }
 
 // Flat frame of a region that spans less than half the box: along an axis
@@ -463,7 +492,8 @@ __device__ __forceinline__ void queue_flush(const PairK &K, float *qr2, float *q
 // ones; the raw coordinates, for the FP64 WCA of a near pair, come back
 // exactly as x + L for a shifted (negative) x.
 template <bool WITH_S, bool FLAT = false>
-__device__ __forceinline__ void offer2(const PairK &K, const WcaEntry *wca, const Desc &A, const Desc &B,
+__device__ __forceinline__ void offer2(const SysParams &P, const PairK &K, const WcaEntry *wca, const Desc &A,
+                                       const Desc &B,
                                        const float4 wrA, const float4 wrB, bool valid, float xj, float yj, float zj,
                                        float qj, int jcls, float *qr2, float *qqp, int &qn, long long &acc,
                                        unsigned long long &sacc, int &ov, const float3 As = float3{},
@@ -486,8 +516,18 @@ __device__ __forceinline__ void offer2(const PairK &K, const WcaEntry *wca, cons
       yr = yj < 0.0f ? yj + K.Lf : yj;
       zr = zj < 0.0f ? zj + K.Lf : zj;
     }
-    if (nearA) near_pair<WITH_S>(K, wca[A.cls * 4 + jcls], A, xr, yr, zr, qj, rA, acc, sacc, ov);
-    if (nearB) near_pair<WITH_S>(K, wca[B.cls * 4 + jcls], B, xr, yr, zr, qj, rB, acc, sacc, ov);
+    if (nearA) {
+      const PairSum p = near_pair<WITH_S>(P, wca[A.cls * 4 + jcls], A.x, A.y, A.z, A.dqlB, A.dp, xr, yr, zr, qj, rA);
+      acc += p.acc;
+      sacc += p.sacc;
+      ov |= p.ov;
+    }
+    if (nearB) {
+      const PairSum p = near_pair<WITH_S>(P, wca[B.cls * 4 + jcls], B.x, B.y, B.z, B.dqlB, B.dp, xr, yr, zr, qj, rB);
+      acc += p.acc;
+      sacc += p.sacc;
+      ov |= p.ov;
+    }
   }
   const bool inA = valid && !nearA && rA < K.rc2 && A.dqlB != 0.0f && qj != 0.0f;
   const bool inB = valid && !nearB && rB < K.rc2 && B.dqlB != 0.0f && qj != 0.0f;
@@ -525,9 +565,11 @@ __device__ __forceinline__ long long warp_allsum(long long v) { return warp_sum_
 // Metropolis uniform, for delayed acceptance the stage-2 uniform, and the
 // velocities of the ions an insertion would add.
 template <bool LOG, bool DA>
-__device__ __forceinline__ void draw_chunk(TrialPre *tp, float4 *tvel, int k0, int nchunk, int i0, int stride, int d,
-                                           uint32_t phi, const int *org, const int *off, const int *dd, int k, int nc,
-                                           float af, float Lf, float scf, uint32_t key0, uint32_t key1) {
+__device__ __noinline__ void draw_chunk(TrialPre *tp, float4 *tvel, int k0, int nchunk, int i0, int stride, int d,
+                                        uint32_t phi, int org0, int org1, int org2, int off0, int off1, int off2,
+                                        int dd0, int dd1, int dd2, int k, int nc, float af, float Lf, float scf,
+                                        uint32_t key0, uint32_t key1) {
+  const int org[3] = {org0, org1, org2}, off[3] = {off0, off1, off2}, dd[3] = {dd0, dd1, dd2};
   for (int u = i0; u < 3 * nchunk; u += stride) {
     if (u >= nchunk) {  // the Maxwell-Boltzmann velocities an accepted insertion gives its ions (purposes 6, 7)
       const int t = u % nchunk, which = u / nchunk - 1;
@@ -690,53 +732,144 @@ __device__ __forceinline__ void select_trial(const SysParams &P, const DomList &
   // self-energy change: lB s_self (sum of q_new^2 - q_old^2), an integer multiple
   const int sq = (pa_n ? (int)(qa_n * qa_n) : 0) - (pa_o ? (int)(qa_o * qa_o) : 0) +
                  (pb_n ? (int)(qb_n * qb_n) : 0) - (pb_o ? (int)(qb_o * qb_o) : 0);
-  C.c[0] = c0;
-  C.c[1] = c1;
-  C.nch = nch;
-  C.move = 2 * r + (fwd ? 0 : 1);
-  C.flags = flags;
-  C.site = site;
-  C.ionA = ionA;
-  C.ionB = ionB;
-  C.ln_ratio_fx = ln_ratio;
-  C.dself_fx = P.lBself_fx * (long long)sq;
-  C.id_a = id_a;
-  C.id_b = id_b;
-  C.newid = newid;
-  C.sur = 0.0f;
-  C.sur_fx = 0;
-  C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
-  C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
-  C.rka = C.rkb = C.dqa = C.dqb = C.eta_a = C.eta_b = C.cat_a = 0;
-  C.go = 1;
+  // lane 0 publishes the selection (C lives in shared memory; every lane
+  // holds the same values)
+  int rka = 0, rkb = 0;
   if (DA && nch) {
     if (r == R_SALT) {
-      C.rka = fwd ? q.rankA : L.rank[ionA];
-      C.rkb = fwd ? q.rankB : L.rank[ionB];
+      rka = fwd ? q.rankA : L.rank[ionA];
+      rkb = fwd ? q.rankB : L.rank[ionB];
     } else {
-      C.rka = L.rank[site];
-      C.rkb = fwd ? q.rankA : L.rank[ionA];
+      rka = L.rank[site];
+      rkb = fwd ? q.rankA : L.rank[ionA];
     }
   }
-  if (DA) {
-    C.dqa = (pa_n ? __float2int_rn(qa_n) : 0) - (pa_o ? __float2int_rn(qa_o) : 0);
-    C.dqb = (pb_n ? __float2int_rn(qb_n) : 0) - (pb_o ? __float2int_rn(qb_o) : 0);
-    C.eta_a = pa_n - pa_o;
-    C.eta_b = pb_n - pb_o;
-    C.cat_a = r == R_SALT ? 0 : 8;
+  if (lane == 0) {
+    C.c[0] = c0;
+    C.c[1] = c1;
+    C.nch = nch;
+    C.move = 2 * r + (fwd ? 0 : 1);
+    C.flags = flags;
+    C.site = site;
+    C.ionA = ionA;
+    C.ionB = ionB;
+    C.ln_ratio_fx = ln_ratio;
+    C.dself_fx = P.lBself_fx * (long long)sq;
+    C.id_a = id_a;
+    C.id_b = id_b;
+    C.newid = newid;
+    C.sur = 0.0f;
+    C.sur_fx = 0;
+    C.qa_o = qa_o; C.qa_n = qa_n; C.qb_o = qb_o; C.qb_n = qb_n;
+    C.pa_o = pa_o; C.pa_n = pa_n; C.pb_o = pb_o; C.pb_n = pb_n;
+    C.rka = rka;
+    C.rkb = rkb;
+    C.dqa = C.dqb = C.eta_a = C.eta_b = C.cat_a = 0;
+    C.go = 1;
+    if (DA) {
+      C.dqa = (pa_n ? __float2int_rn(qa_n) : 0) - (pa_o ? __float2int_rn(qa_o) : 0);
+      C.dqb = (pb_n ? __float2int_rn(qb_n) : 0) - (pb_o ? __float2int_rn(qb_o) : 0);
+      C.eta_a = pa_n - pa_o;
+      C.eta_b = pb_n - pb_o;
+      C.cat_a = r == R_SALT ? 0 : 8;
+    }
   }
+}
+
+// One candidate of the merged stream of a region's particles that are not
+// held in registers: u < nhc the on-chip halo (shared memory, already in the
+// flat frame when the region is flat, w = q + 8 cls), u < NH the halo beyond
+// it (global memory), then the domain list.  FLAT: coordinates are returned
+// in the region's flat frame.
+template <bool FLAT>
+__device__ __forceinline__ bool stream_cand(const SysParams &P, const DomList &L, const Desc &A, const Desc &B,
+                                            const float4 *hpos, int nhc, int NH, int n, const int *hpre,
+                                            const int *hcell, int NR, int strad, int u, float &x, float &y,
+                                            float &z, float &q, int &cls) {
+  if (u < nhc) {
+    const float4 p = hpos[u];
+    cls = __float2int_rd((p.w + 2.0f) * 0.125f);
+    q = p.w - 8.0f * (float)cls;
+    x = p.x;
+    y = p.y;
+    z = p.z;
+    return true;
+  }
+  float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool v = false;
+  cls = 0;
+  if (u < NH) {  // halo beyond what is held on chip (dense regions): straight from global memory
+    const int i = upper_idx(hpre, NR, u);
+    const int g = hcell[i] * P.cap + (u - hpre[i]);
+    p = P.pos[g];
+    cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
+    v = true;
+  } else if (u < NH + n) {
+    const int j = u - NH;
+    p = L.pos[j];
+    cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
+    v = j != A.skip && j != B.skip;
+  }
+  q = p.w;
+  if (FLAT) {
+    x = frame_x(p.x, strad, 0, P.halfL, P.Lf);
+    y = frame_x(p.y, strad, 1, P.halfL, P.Lf);
+    z = frame_x(p.z, strad, 2, P.halfL, P.Lf);
+  } else {
+    x = p.x;
+    y = p.y;
+    z = p.z;
+  }
+  return v;
+}
+
+// The region's stream (all of it, or from `from` on) against A and B without
+// the flat frame: regions wider than 0.4 L, i.e. small boxes.  Out of line,
+// so that the flat loop is the only pair sweep in the trial loop's code; its
+// sums come back by value.
+template <bool LOG>
+__device__ __noinline__ PairSum sweep_general(const SysParams &P, const TrialCtl &C, const float4 *lpos,
+                                              const int *linfo, const float4 *hpos, int nhc, int NH, int n,
+                                              const int *hpre, const int *hcell, int NR, int from, int i0, int stride,
+                                              float *qr2, float *qqp) {
+  const Desc A = C.c[0], B = C.c[1];
+  DomList L{};
+  L.pos = const_cast<float4 *>(lpos);
+  L.info = const_cast<int *>(linfo);
+  PairK K;
+  K.Lf = P.Lf; K.halfL = P.halfL; K.rc2 = P.rc2; K.alpha = P.alpha; K.c1 = P.c1; K.c2 = P.c2; K.rcf = P.rcf;
+  K.lBf = P.lBf; K.Ld = P.Ld; K.halfLd = P.halfLd;
+  const WcaEntry *wca = P.wca;
+  const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
+  const int lane = threadIdx.x & 31;
+  PairSum out{0, 0ull, 0};
+  int qn = 0;
+  for (int base = from; base < NH + n; base += stride) {
+    float x, y, z, q;
+    int cls;
+    const int u = base + i0;
+    const bool v = stream_cand<false>(P, L, A, B, hpos, nhc, NH, n, hpre, hcell, NR, 0, u, x, y, z, q, cls);
+    offer2<LOG>(P, K, wca, A, B, wrA, wrB, v, x, y, z, q, cls, qr2, qqp, qn, out.acc, out.sacc, out.ov);
+  }
+  __syncwarp();
+  if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], out.acc, out.sacc, out.ov);
+  return out;
 }
 
 // The pair changes of the two changed particles A and B against the halo and
 // the domain list, summed by a group of threads (thread i0 of `stride`; each
 // thread keeps its part in acc / sacc / ov; the warp's queued Coulomb pairs
 // are evaluated at the end).  The pair between A and B is not included.
+// Flat regions (the common case) take every candidate in the flat frame in
+// one loop over the merged stream; halo particles held in registers come
+// first.
 template <bool LOG, int R, int RR>
 __device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca, const SysParams &P, const DomList &L,
                                             const Desc &A, const Desc &B, const float4 (&hreg)[RR], int nmine,
                                             const float4 *hpos, int NH, int hcap, const int *hpre, const int *hcell,
                                             int NR, int n, int i0, int stride, float *qr2, float *qqp, long long &acc,
-                                            unsigned long long &sacc, int &ov, bool flat, int strad) {
+                                            unsigned long long &sacc, int &ov, bool flat, int strad,
+                                            const TrialCtl *ctl) {
   const int lane = threadIdx.x & 31;
   const float4 wrA = wca_radii(wca, A), wrB = wca_radii(wca, B);
   int qn = 0;
@@ -752,7 +885,7 @@ __device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca,
         const float4 p = hreg[r];
         const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
         const float q = p.w - 8.0f * (float)cls;
-        offer2<LOG, true>(K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov,
+        offer2<LOG, true>(P, K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov,
                           As, Bs);
       }
     } else {
@@ -761,58 +894,33 @@ __device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca,
         const float4 p = hreg[r];
         const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
         const float q = p.w - 8.0f * (float)cls;
-        offer2<LOG>(K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
+        offer2<LOG>(P, K, wca, A, B, wrA, wrB, r < nmine, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
       }
     }
+  }
+  // the rest of the stream: for R == 0 the halo in shared memory from 0, for
+  // R > 0 the part of the halo beyond the registers, then the list
+  const int nhc = R > 0 ? 0 : min(NH, hcap);
+  const int from = R > 0 ? min(NH, hcap) : 0;
+  if (flat) {
+    for (int base = from; base < NH + n; base += stride) {
+      float x, y, z, q;
+      int cls;
+      const bool v = stream_cand<true>(P, L, A, B, hpos, nhc, NH, n, hpre, hcell, NR, strad, base + i0, x, y, z, q,
+                                       cls);
+      offer2<LOG, true>(P, K, wca, A, B, wrA, wrB, v, x, y, z, q, cls, qr2, qqp, qn, acc, sacc, ov, As, Bs);
+    }
+    __syncwarp();
+    if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
   } else {
-    const int lim = min(NH, hcap);
-    if (flat) {
-      for (int base = 0; base < lim; base += stride) {
-        const int j = base + i0;
-        const bool v = j < lim;
-        const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-        const float q = p.w - 8.0f * (float)cls;
-        offer2<LOG, true>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov, As, Bs);
-      }
-    } else {
-      for (int base = 0; base < lim; base += stride) {
-        const int j = base + i0;
-        const bool v = j < lim;
-        const float4 p = v ? hpos[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int cls = __float2int_rd((p.w + 2.0f) * 0.125f);
-        const float q = p.w - 8.0f * (float)cls;
-        offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, q, cls, qr2, qqp, qn, acc, sacc, ov);
-      }
-    }
+    __syncwarp();
+    if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);  // the registers' queue
+    const PairSum g =
+        sweep_general<LOG>(P, *ctl, L.pos, L.info, hpos, nhc, NH, n, hpre, hcell, NR, from, i0, stride, qr2, qqp);
+    acc += g.acc;
+    sacc += g.sacc;
+    ov |= g.ov;
   }
-  // halo beyond what is held on chip (dense regions): straight from global memory
-  for (int base = hcap; base < NH; base += stride) {
-    const int j = base + i0;
-    const bool v = j < NH;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    int cls = 0;
-    if (v) {
-      const int i = upper_idx(hpre, NR, j);
-      const int g = hcell[i] * P.cap + (j - hpre[i]);
-      p = P.pos[g];
-      cls = (P.info[g] >> INFO_CLS_SHIFT) & 3;
-    }
-    offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-  }
-  for (int base = 0; base < n; base += stride) {
-    const int j = base + i0;
-    const bool v = j < n && j != A.skip && j != B.skip;
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    int cls = 0;
-    if (j < n) {
-      p = L.pos[j];
-      cls = (L.info[j] >> INFO_CLS_SHIFT) & 3;
-    }
-    offer2<LOG>(K, wca, A, B, wrA, wrB, v, p.x, p.y, p.z, p.w, cls, qr2, qqp, qn, acc, sacc, ov);
-  }
-  __syncwarp();
-  if (lane < qn) coul_eval<LOG>(K, qr2[lane], qqp[lane], acc, sacc, ov);
 }
 
 // room for the ions an accepted insertion adds: their cells below the cell
@@ -913,18 +1021,31 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
   return n;
 }
 
+// An accepted trial, by warp 0: room for the ions an insertion adds (else
+// -1 and nothing changes), then the commit; returns the new list size.  Out
+// of line: it runs only for accepted trials and is large.
+__device__ __noinline__ int try_commit(const SysParams &P, float4 *lpos, float4 *lvel, unsigned long long *lid,
+                                       long long *llnk, int *linfo, int *lrank, int *misc, const TrialCtl &C,
+                                       const TrialPre &q, const float4 *vel, int n, int list_cap) {
+  DomList L;
+  L.pos = lpos; L.vel = lvel; L.id = lid; L.lnk = llnk; L.info = linfo; L.rank = lrank;
+  const int r = C.move >> 1;
+  const bool fwd = (C.move & 1) == 0;
+  int belowA = 0, sameA = 0;
+  if (fwd && !insert_room(P, L, n, list_cap, r, q, belowA, sameA)) return -1;
+  return commit_trial(P, L, misc, C, q, vel, n, belowA, sameA);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// the phase kernel
-//   T threads per domain (T == 32: one warp, no block barriers);
-//   R > 0: halo particles in R registers per thread, R == 0: in shared memory
-// ---------------------------------------------------------------------------
+// One domain of one colour phase of replica `rep`: `rank` is its place in
+// the colour's launch order.  Every thread of the CTA calls it; smem is the
+// CTA's dynamic shared memory, carved up as phase_smem_bytes describes.
 template <int T, int R, bool LOG, bool DA>
-__global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
-    k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
-               uint32_t key0, uint32_t key1_base) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams *__restrict__ reps,
+                                           const PhaseShape &S, uint32_t sweep, uint32_t sweep0, int colour,
+                                           uint32_t key0, uint32_t key1_base, int rep, int rank) {
   constexpr int NW = T / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -946,8 +1067,8 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   Ls.rank = (int *)take(sizeof(int) * S.dcs);
   float4 *hpos = (float4 *)take(sizeof(float4) * S.hcs);  // halo (R == 0): x, y, z, q + 8 cls
   long long *lntab_s = (long long *)take(sizeof(long long) * S.lns);
-  TrialPre *tp = (TrialPre *)take(sizeof(TrialPre) * TRIAL_CHUNK);
-  float4 *tvel = (float4 *)take(sizeof(float4) * 2 * TRIAL_CHUNK);  // velocities of inserted ions
+  TrialPre *tp = (TrialPre *)take(sizeof(TrialPre) * S.chunk);
+  float4 *tvel = (float4 *)take(sizeof(float4) * 2 * S.chunk);  // velocities of inserted ions
   TrialCtl *ctl = (TrialCtl *)take(sizeof(TrialCtl));
   long long *red = (long long *)take(sizeof(long long) * MAX_WARPS);
   unsigned long long *reds = (unsigned long long *)take(sizeof(unsigned long long) * MAX_WARPS);
@@ -977,13 +1098,13 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   }
 
   {
-    const int *src = (const int *)&reps[blockIdx.x];
+    const int *src = (const int *)&reps[rep];
     int *dst = (int *)&P;
     for (int i = tid; i < (int)(sizeof(SysParams) / 4); i += T) dst[i] = src[i];
   }
   __syncthreads();
-  if ((int)blockIdx.y >= P.nact) return;  // uniform over the CTA
-  const int bdom = P.order ? P.order[colour * P.nact + blockIdx.y] : (int)blockIdx.y;  // active-domain index
+  if (rank >= P.nact) return;  // uniform over the CTA
+  const int bdom = P.order ? P.order[colour * P.nact + rank] : rank;  // active-domain index
   const int k = P.k, h = P.h, nc = P.nc, nr = P.nr, m = P.m;
   const int KC = k * k * k, NR = nr * nr * nr;
   const uint32_t key1 = key1_base ^ P.key_xor;
@@ -1044,7 +1165,7 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   const bool in_smem = ND + 2 * m <= S.dcs;
   DomList L = Ls;
   if (!in_smem) {
-    const size_t o = (size_t)blockIdx.y * P.dcap_glob;  // this replica's scratch
+    const size_t o = (size_t)(colour * P.nact + rank) * P.dcap_glob;  // this domain's region of the replica's scratch
     L.pos = P.gs_pos + o; L.vel = P.gs_vel + o; L.id = P.gs_id + o; L.lnk = P.gs_lnk + o;
     L.info = P.gs_info + o; L.rank = P.gs_rank + o;
     if (ND + 2 * m > P.dcap_glob) {  // cannot happen: a cell holds at most cap particles
@@ -1135,21 +1256,18 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   const long long log_dom = (long long)(sweep - sweep0) * P.per_sweep + (long long)colour * P.nact * m +
                             (long long)bdom * m;
 
-  for (int k0 = 0; k0 < m; k0 += TRIAL_CHUNK) {
-    const int nchunk = min(TRIAL_CHUNK, m - k0);
+  for (int k0 = 0; k0 < m; k0 += S.chunk) {
+    const int nchunk = min(S.chunk, m - k0);
     // ---- random numbers of the chunk
-    draw_chunk<LOG, DA>(tp, tvel, k0, nchunk, tid, T, d, phi, org, off, dd, k, nc, P.af, P.Lf, P.scf, key0, key1);
+    draw_chunk<LOG, DA>(tp, tvel, k0, nchunk, tid, T, d, phi, org[0], org[1], org[2], off[0], off[1], off[2], dd[0],
+                        dd[1], dd[2], k, nc, P.af, P.Lf, P.scf, key0, key1);
     __syncthreads();
 
     for (int t = 0; t < nchunk; ++t) {
       const int kk = k0 + t;
       // ---- warp 0: proposal and participants; the selection lives in
       // shared memory (*ctl) across the sweep
-      if (warp == 0) {
-        TrialCtl C;
-        select_trial<DA>(P, L, misc, lnt, tp[t], d, m, kk, phi, C);
-        if (lane == 0) *ctl = C;
-      }
+      if (warp == 0) select_trial<DA>(P, L, misc, lnt, tp[t], d, m, kk, phi, *ctl);
       cta_sync<T>();
       // ---- delayed acceptance, stage 1: surrogate features and MLP (all
       // threads), decision in warp 0; a rejection skips the pair sweep
@@ -1239,8 +1357,13 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
       if (nch) {
         const Desc A = ctl->c[0], B = ctl->c[1];
         sweep_pairs<LOG, R, RR>(K, wca, P, L, A, B, hreg, nmine, hpos, NH, hcap, hpre, hcell, NR, misc[0], tid, T,
-                                qr2, qqp, acc, sacc, ov, flat, strad);
-        if (tid == cc_thread) cc_change<LOG>(K, wca, *ctl, acc, sacc, ov);
+                                qr2, qqp, acc, sacc, ov, flat, strad, ctl);
+        if (tid == cc_thread) {
+          const PairSum cc = cc_change<LOG>(P, *ctl);
+          acc += cc.acc;
+          sacc += cc.sacc;
+          ov |= cc.ov;
+        }
         acc = warp_allsum(acc);
         if (LOG) sacc = (unsigned long long)warp_allsum((long long)sacc);
         ov = __any_sync(FULL, ov) ? 1 : 0;
@@ -1294,12 +1417,18 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
         const int r = s_move >> 1;
         const bool fwd = (s_move & 1) == 0;
         int n = misc[0];
-        // cell capacity for insertions (checked before committing anything)
-        int belowA = 0, sameA = 0;
-        if (accept && fwd && !insert_room(P, L, n, in_smem ? S.dcs : P.dcap_glob, r, q, belowA, sameA)) {
-          accept = false;
-          if (lane == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
+        if (accept) {  // commit, unless an insertion finds no room (checked before anything changes)
+          const int n2 = try_commit(P, L.pos, L.vel, L.id, L.lnk, L.info, L.rank, misc, *ctl, q, tvel + 2 * t, n,
+                                    in_smem ? S.dcs : P.dcap_glob);
+          if (n2 < 0) {
+            accept = false;
+            if (lane == 0) atomicOr(P.err, ERRB_CELL_OVERFLOW);
+          } else {
+            n = n2;
+          }
         }
+        (void)r;
+        (void)fwd;
         if (accept) {
           flags |= CR_TRIAL_ACCEPTED;
           if (DA && lane == 0) {  // region aggregates follow the committed change
@@ -1317,7 +1446,6 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
               }
             }
           }
-          n = commit_trial(P, L, misc, *ctl, q, tvel + 2 * t, n, belowA, sameA);
         }
         if (lane == 0) {
           misc[0] = n;
@@ -1380,6 +1508,196 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
   if (tid < 16 && st[tid]) atomicAdd(&P.stats[tid], st[tid]);
   if (tid < 6 && misc[1 + tid] != misc[9 + tid])
     atomicAdd((unsigned long long *)&P.counts[tid], (unsigned long long)(long long)(misc[1 + tid] - misc[9 + tid]));
+}
+
+// ---------------------------------------------------------------------------
+// the phase kernel: one CTA per active domain of one colour
+//   T threads per domain (T == 32: one warp, no block barriers);
+//   R > 0: halo particles in R registers per thread, R == 0: in shared memory
+// ---------------------------------------------------------------------------
+template <int T, int R, bool LOG, bool DA>
+__global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
+    k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
+               uint32_t key0, uint32_t key1_base) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  phase_task<T, R, LOG, DA>(smem, reps, S, sweep, sweep0, colour, key0, key1_base, (int)blockIdx.x,
+                            (int)blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// The persistent sweep: every colour of every replica of a batch in one
+// launch.  CTAs claim tasks (colour c, replica r, domain rank i) in that
+// order from a counter.  A domain's phase reads its region -- its own cells
+// and the halo, which lies inside its 26 neighbouring domains -- and writes
+// only its own cells, so the colour-by-colour schedule is reproduced exactly
+// when each task starts after its neighbours of lower colours have finished
+// (per-domain completion flags; Q.fine) or, for geometries whose halo reaches
+// beyond the neighbouring domains, after its replica's whole previous colour
+// (per-(replica, colour) counters).  Tasks of later colours thus start while
+// distant domains of earlier colours still run, and no colour waits for the
+// slowest domain of the batch.  A task is claimed only after every task it
+// depends on was claimed, so the claims always make progress; each wait is
+// nevertheless bounded in time, and a wait that runs out marks the replica's
+// error word (ERRB_TIMEOUT), raises the launch's abort flag and skips the
+// task, after which every remaining task is skipped without waiting.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// linear index of the domain of active rank i in colour c of replica P
+__device__ __forceinline__ int task_domain(const SysParams &P, int c, int i, int (&dd)[3]) {
+  const int b = P.order ? P.order[c * P.nact + i] : i;
+  const int hn = P.nd >> 1;
+  dd[0] = 2 * (b % hn) + (c & 1);
+  dd[1] = 2 * ((b / hn) % hn) + ((c >> 1) & 1);
+  dd[2] = 2 * (b / (hn * hn)) + ((c >> 2) & 1);
+  return dd[0] + P.nd * (dd[1] + P.nd * dd[2]);
+}
+
+// bounded wait of one lane until *p >= need; false when the time ran out or
+// the launch was aborted
+__device__ __forceinline__ bool wait_at_least(const unsigned *p, unsigned need, const SweepSched &Q, int &timed_out) {
+  const unsigned long long t0 = global_ns();
+  while (ld_acquire_u32(p) < need) {
+    if (*(volatile int *)Q.abort) return false;
+    if (global_ns() - t0 > Q.wait_ns) {
+      timed_out = 1;
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <int T, int R, bool DA>
+__global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
+    k_cr_sweep(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, uint32_t key0,
+               uint32_t key1_base, SweepSched Q) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_task, s_run, s_dom;
+  const int lane = threadIdx.x & 31;
+  const int per_colour = Q.rep_first[Q.n_rep];
+  const int total = per_colour * Q.ncol;
+  for (;;) {
+    if (threadIdx.x < 32) {  // warp 0: claim a task and wait for what it depends on
+      int t = 0;
+      if (lane == 0) t = (int)atomicAdd(Q.next, 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      int run = 0, dom = -1;
+      if (t < total) {
+        const int c = t / per_colour, q = t - c * per_colour;
+        int r = 0;
+        while (Q.rep_first[r + 1] <= q) ++r;
+        const SysParams &P = reps[r];
+        int dd[3] = {0, 0, 0};
+        if (Q.fine) dom = task_domain(P, c, q - Q.rep_first[r], dd);
+        int ok = *(volatile int *)Q.abort ? 0 : 1, timed_out = 0;
+        if (ok && c > 0) {
+          if (Q.fine) {  // lane l < 26: neighbour l of the 3^3 block around the domain
+            const int nd = P.nd;
+            if (lane < 26) {
+              const int o = lane < 13 ? lane : lane + 1;
+              const int nx = (dd[0] + o % 3 - 1 + nd) % nd, ny = (dd[1] + (o / 3) % 3 - 1 + nd) % nd,
+                        nz = (dd[2] + o / 9 - 1 + nd) % nd;
+              const int col = (nx & 1) | ((ny & 1) << 1) | ((nz & 1) << 2);
+              if (col < c) ok = wait_at_least(Q.flags + Q.dom_first[r] + nx + nd * (ny + nd * nz), 1u, Q, timed_out);
+            }
+          } else if (lane == 0) {  // the replica's whole previous colour
+            const unsigned need = (unsigned)(Q.rep_first[r + 1] - Q.rep_first[r]);
+            ok = wait_at_least(Q.done + r * Q.ncol + (c - 1), need, Q, timed_out);
+          }
+          ok = __all_sync(0xffffffffu, ok);
+          if (__any_sync(0xffffffffu, timed_out) && lane == 0) {
+            atomicOr(P.err, ERRB_TIMEOUT);
+            atomicExch(Q.abort, 1);
+          }
+        }
+        run = ok;
+      }
+      if (lane == 0) {
+        s_task = t;
+        s_run = run;
+        s_dom = dom;
+      }
+    }
+    __syncthreads();
+    const int t = s_task;
+    if (t >= total) break;
+    const int c = t / per_colour, q = t - c * per_colour;
+    int r = 0;
+    while (Q.rep_first[r + 1] <= q) ++r;
+    if (s_run)
+      phase_task<T, R, false, DA>(smem, reps, S, sweep, sweep0, c, key0, key1_base, r, q - Q.rep_first[r]);
+    __syncthreads();  // the task's stores are done, its shared memory is free
+    if (threadIdx.x == 0 && !(r == Q.withhold_rep && c == 0)) {
+      __threadfence();
+      if (Q.fine) st_release_u32(Q.flags + Q.dom_first[r] + s_dom, 1u);
+      else atomicAdd(Q.done + r * Q.ncol + c, 1u);
+    }
+  }
+}
+
+template <int T, int R, bool DA>
+static cudaError_t launch_sweep_t(const SysParams *d_reps, PhaseShape S, cudaStream_t s, uint32_t sweep,
+                                  uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q, int max_ctas) {
+  if (R > 0) S.hcs = 0;  // halo in registers
+  static size_t attr_bytes = 0;
+  static int per_sm = 0;
+  static size_t per_sm_bytes = ~(size_t)0;
+  const size_t smem = phase_smem_bytes(S, T, DA);
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_cr_sweep<T, R, DA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  if (smem != per_sm_bytes) {  // resident CTAs per SM at this shared-memory size
+    int nb = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cr_sweep<T, R, DA>, T, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(nb, 1);
+    per_sm_bytes = smem;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int total = Q.tasks_total;
+  int grid = std::min(total, per_sm * std::max(sms, 1));
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
+  if (grid <= 0) return cudaSuccess;
+  k_cr_sweep<T, R, DA><<<grid, T, smem, s>>>(d_reps, S, sweep, sweep0, k0, k1, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const SysParams *d_reps, const PhaseShape &S, int threads, int R, bool da, cudaStream_t s,
+                         uint32_t sweep, uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q,
+                         int max_ctas) {
+#define CRMC_SW(TT, RR, DD)                                                                   \
+  if (da == DD && threads == TT && R == RR)                                                    \
+    return launch_sweep_t<TT, RR, DD>(d_reps, S, s, sweep, sweep0, k0, k1, Q, max_ctas);
+  CRMC_SW(32, 0, false)
+  CRMC_SW(64, 0, false)
+  CRMC_SW(128, 0, false)
+  CRMC_SW(128, 4, false)
+  CRMC_SW(256, 0, false)
+  CRMC_SW(256, 2, false)
+  CRMC_SW(512, 0, false)
+  CRMC_SW(512, 1, false)
+  CRMC_SW(128, 0, true)
+  CRMC_SW(256, 0, true)
+  CRMC_SW(512, 0, true)
+#undef CRMC_SW
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -1449,8 +1767,8 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
                           sizeof(int) * S.dcs,
                           sizeof(float4) * S.hcs,
                           sizeof(long long) * S.lns,
-                          sizeof(TrialPre) * TRIAL_CHUNK,
-                          sizeof(float4) * 2 * TRIAL_CHUNK,
+                          sizeof(TrialPre) * S.chunk,
+                          sizeof(float4) * 2 * S.chunk,
                           sizeof(TrialCtl),
                           sizeof(long long) * MAX_WARPS,
                           sizeof(unsigned long long) * MAX_WARPS,

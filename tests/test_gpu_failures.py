@@ -5,6 +5,10 @@
     CR_ERR_TIMEOUT, the output is untouched, and the next product on the same
     stream is correct -- the CTA freed its tensor memory and the context
     stayed usable;
+  * the bounded dependency waits of the persistent batch sweep run out when
+    one replica withholds its colour-0 completion
+    (cr_batch_selftest_wait_timeout): CR_ERR_TIMEOUT within about the given
+    limit, and the device runs a following batch sweep exactly;
   * a FENE bond stretched to R0 by a loaded configuration is reported as
     CR_ERR_BOND_BROKEN by the next force evaluation (the error word of the
     force kernel), not as a NaN force.
@@ -73,3 +77,30 @@ def test_stretched_bond_is_reported(env):
     h.md_forces()
     assert np.isfinite(h.state()["force"]).all()
     h.close()
+
+
+def test_persistent_sweep_wait_expires_and_the_device_recovers(env):
+    import time
+
+    import oracle
+    from parity_util import compare_states
+    torch, crmc = env
+    ws = [W.config2(seed=13, scale=0.5, pH=p) for p in (3.0, 5.0, 7.0)]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    t0 = time.perf_counter()
+    assert b.selftest_wait_timeout(1, 50.0) == CR_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0  # one bounded wait, then the rest skipped
+    with pytest.raises(crmc.CrError) as e:
+        ctxs[1].check()
+    assert e.value.code == CR_ERR_TIMEOUT
+    b.close()
+    # a new batch on the same device runs the oracle's chain
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(2, 8)
+    for r, (w, g) in enumerate(zip(ws, ctxs)):
+        o = oracle.Oracle(w)
+        o.sweep(o.trials_per_sweep * 2, 8 ^ (r << 32))
+        compare_states(g, o, w.n_sites)
+    b.close()

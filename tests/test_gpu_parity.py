@@ -319,6 +319,34 @@ def test_batch_of_64_uneven_replicas_matches_oracle(crmc):
     b.close()
 
 
+@pytest.mark.parametrize("threads,regs,cap", [(64, 0, 0), (128, 4, 0), (256, 0, 0), (64, 0, 8)])
+def test_persistent_sweep_equals_colour_launches(crmc, threads, regs, cap):
+    """The persistent batch sweep (a domain starts when its neighbours of
+    lower colours are done, so colours overlap within and across replicas)
+    and one launch per colour give the same states bit for bit, and both the
+    oracle's; cap = 8 puts dense domains' lists in the global scratch, one
+    region per (colour, domain), while domains of several colours run."""
+    ws = [W.config2(seed=12, scale=0.5, pH=p) for p in (3.0, 4.5, 6.0)] + W.config4(seed=3, n_rep=3, hi=400)
+    kw = dict(list_capacity=cap, halo_capacity=64) if cap else {}
+    runs = []
+    for persistent in (True, False):
+        ctxs = [crmc.Context(w, **kw) for w in ws]
+        b = crmc.Batch(ctxs)
+        b.set_persistent(persistent)
+        b.set_launch_shape(threads, regs)
+        b.sweep(3, 55)
+        runs.append([g.state() for g in ctxs])
+        if persistent:
+            for r, (w, g) in enumerate(zip(ws, ctxs)):
+                o = oracle.Oracle(w)
+                o.sweep(o.trials_per_sweep * 3, _replica_seed(55, r))
+                compare_states(g, o, w.n_sites)
+        b.close()
+    for a, c in zip(*runs):
+        for k in ("id", "xyz", "vel", "state"):
+            assert np.array_equal(a[k], c[k]), k
+
+
 def test_batch_md_equals_per_context_md(crmc):
     ws = [W.config2(seed=7, scale=0.5, pH=pH) for pH in (3.0, 5.0)]
     a = [crmc.Context(w) for w in ws]
