@@ -405,14 +405,10 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     b = crmc.Batch(ctxs)
     b.sweep_da(12, 0xDA)  # launch-shape tuning of the DA variant (5 shapes, each in both launch forms)
     for s in range(3):
-        b.md_begin(dt, gamma, 1000 + s)
-        b.sweep_da(1, 1 + s)
-        b.md_end(dt, gamma, 1000 + s)
+        b.cycle(1, dt, gamma, 1 + s, 1000 + s, da=True)
 
     def step(s):
-        b.md_begin(dt, gamma, 6000 + s)
-        b.sweep_da(1, 200 + s)
-        b.md_end(dt, gamma, 6000 + s)
+        b.cycle(1, dt, gamma, 200 + s, 6000 + s, da=True)
 
     ms = time_steps(step, steps, stream, flush)
     for c in ctxs:
@@ -468,24 +464,20 @@ def run_ours(args):
     per_rep = ctxs[0].trials_per_sweep
     per_step = per_rep * len(ctxs)
     batch.sweep(BATCH_TUNE_SWEEPS, 0xABC)  # launch-shape tuning (one shape and launch form per sweep)
+    g0 = ctxs[0]
+    g0.set_timing(True)  # before the warm-up, so that the captured cycle already records the phase kernel's events
     for s in range(args.warmup):
-        batch.md_begin(dt, gamma, 1000 + s)
-        batch.sweep(1, 1 + s)
-        batch.md_end(dt, gamma, 1000 + s)
+        batch.cycle(1, dt, gamma, 1 + s, 1000 + s)
     for g in ctxs:
         g.check()
     clocks = ClockSampler()
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
-    g0 = ctxs[0]
-    g0.set_timing(True)
     g0.timing(reset=True)
 
-    def step(s):  # one MD step with the replicas' trials between its drift and its force evaluation
-        batch.md_begin(dt, gamma, 5000 + s)
-        batch.sweep(1, 100 + s)
-        batch.md_end(dt, gamma, 5000 + s)
+    def step(s):  # one MD step with the replicas' trials between its drift and its force evaluation (one graph)
+        batch.cycle(1, dt, gamma, 100 + s, 5000 + s)
 
     t_region0 = time.perf_counter()
     ms = time_steps(step, args.steps, stream, flush)
@@ -585,9 +577,7 @@ def run_ours(args):
         for s in range(e2e_steps):
             batch.load_packed(stride, load_ptr, nbuf.data_ptr())
             h2d += R * stride * (12 + 12 + 4 + 4 + 1) + 8 * R
-            batch.md_begin(dt, gamma, 9500 + s)
-            batch.sweep(1, 9000 + s)
-            batch.md_end(dt, gamma, 9500 + s)
+            batch.cycle(1, dt, gamma, 9000 + s, 9500 + s)
             batch.state_packed(stride, ptr, nbuf.data_ptr())
             d2h += R * stride * (12 + 12 + 8 + 4 + 1 + 4) + 12 * R
         torch.cuda.synchronize()
@@ -611,7 +601,9 @@ def run_ours(args):
                       "alpha_end": [round(c["alpha"], 4) for c in counts],
                       "particles_end": [c["n"] for c in counts],
                       "parallelism": f"{world} GPU(s), independent replica batches"},
-           "roofline": roofline, "gpu_launches": tm["launches"], "clocks": cl, "e2e": e2e, "plain": plain,
+           "roofline": roofline, "gpu_launches": tm["launches"],
+           "graph_launches_per_step": 1, "kernels_per_step": tm["launches"] / args.steps,
+           "clocks": cl, "e2e": e2e, "plain": plain,
            "surrogate_da": da,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:

@@ -422,6 +422,19 @@ int cr_batch_md_step(cr_batch *b, int32_t n_steps, double dt, double gamma, uint
 /* cr_md_begin / cr_md_end on every replica (replica r uses seed ^ (r << 32)). */
 int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t seed);
 int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
+/* n_steps MD/CR-MC cycles of every replica: step s is cr_batch_md_begin,
+ * one sweep (cr_batch_sweep, or cr_batch_sweep_da when da != 0) and
+ * cr_batch_md_end, with seeds sweep_seed0 + s and md_seed0 + s -- the
+ * hybrid scheme of the paper with the trials of Sec. II.C between the drift
+ * and the force evaluation of a velocity-Verlet/Langevin step (Sec. III.A).
+ * Once the launch-shape tuner has finished and every replica holds the
+ * forces of a completed step, each step is one launch of a CUDA graph
+ * captured from those calls (captured again when dt, gamma, the launch form
+ * or timing change); its kernels read the step's seeds and counters from
+ * device memory.  Earlier steps run call by call.  The chain is the same as
+ * the calls made one by one. */
+int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t sweep_seed0, uint64_t md_seed0,
+                   int32_t da);
 /* cr_load of every replica of the batch: args[0 .. n-1], one per context in
  * the order given to cr_batch_create; the uploads and load kernels of the
  * replicas run concurrently on the batch's streams.  Errors as cr_load's;

@@ -98,7 +98,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
            "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
            "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup",
-           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout")
+           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -213,6 +213,8 @@ def _lib():
         lib.cr_batch_sweep.argtypes = [P, C.c_uint64, C.c_uint64]
         lib.cr_batch_md_step.restype = C.c_int
         lib.cr_batch_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
+        lib.cr_batch_cycle.restype = C.c_int
+        lib.cr_batch_cycle.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_int32]
         lib.cr_batch_set_persistent.restype = C.c_int
         lib.cr_batch_set_persistent.argtypes = [P, C.c_int32, C.c_int32]
         lib.cr_batch_selftest_wait_timeout.restype = C.c_int
@@ -561,6 +563,12 @@ class Batch:
 
     def md_end(self, dt, gamma, seed):
         _chk(self._lib.cr_batch_md_end(self._h, float(dt), float(gamma), int(seed)), "cr_batch_md_end")
+
+    def cycle(self, n_steps, dt, gamma, sweep_seed0, md_seed0, da=False):
+        """cr_batch_cycle: n_steps MD/CR-MC cycles (one CUDA graph launch per
+        step once tuned); step s uses seeds sweep_seed0 + s and md_seed0 + s."""
+        _chk(self._lib.cr_batch_cycle(self._h, int(n_steps), float(dt), float(gamma), int(sweep_seed0),
+                                      int(md_seed0), 1 if da else 0), "cr_batch_cycle")
 
     def set_launch_shape(self, threads, regs):
         _chk(self._lib.cr_batch_set_launch_shape(self._h, int(threads), int(regs)), "cr_batch_set_launch_shape")

@@ -114,6 +114,7 @@ struct cr_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_pairs[2];  // [0] phase kernel, [1] MD force kernel
   size_t ev_next = 0;
+  size_t ev_reserved = 0;  // events recorded by a batch's captured cycle (kept out of the pool's reuse)
   double ms[2] = {0.0, 0.0};
   int64_t launches[2] = {0, 0};
   int64_t launches_total = 0;
@@ -200,7 +201,16 @@ static void free_ctx(cr_ctx *c) {
   delete c;
 }
 
-// CUDA-event timing of the two main kernels (kind 0: colour phase, 1: MD forces)
+// CUDA-event timing of the two main kernels (kind 0: colour phase, 1: MD forces).
+// Under stream capture a record is external, so that it becomes an
+// event-record node of the graph, read after each of its launches.
+static void trecord(cr_ctx *c, cudaEvent_t e) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, c->stream);
+}
 static void tbegin(cr_ctx *c, int kind, int *idx) {
   *idx = -1;
   if (!c->timing) return;
@@ -211,12 +221,12 @@ static void tbegin(cr_ctx *c, int kind, int *idx) {
   }
   *idx = (int)c->ev_next;
   c->ev_next += 2;
-  cudaEventRecord(c->ev_pool[*idx], c->stream);
+  trecord(c, c->ev_pool[*idx]);
   (void)kind;
 }
 static void tend(cr_ctx *c, int kind, int idx) {
   if (idx < 0) return;
-  cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+  trecord(c, c->ev_pool[idx + 1]);
   c->ev_pairs[kind].push_back({idx, idx + 1});
 }
 static void tcollect(cr_ctx *c) {
@@ -228,7 +238,7 @@ static void tcollect(cr_ctx *c) {
     }
     c->ev_pairs[k].clear();
   }
-  c->ev_next = 0;
+  c->ev_next = c->ev_reserved;
 }
 
 extern "C" void cr_destroy(cr_ctx *ctx) {
@@ -1083,10 +1093,19 @@ extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) 
   return CR_OK;
 }
 
+// cr_md_end's force evaluation; in a captured cycle (dyn) the key and the
+// evaluation counter come from the step parameters in device memory
+static int md_end_impl(cr_ctx *ctx, double dt, double gamma, uint64_t seed, const StepDyn *dyn, unsigned rep) {
+  MdParams M = md_params(ctx, 2, dt, gamma, seed);
+  M.dyn = dyn;
+  M.rep = rep;
+  return md_force_eval(ctx, M);
+}
+
 extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
   int rc;
-  if ((rc = md_force_eval(ctx, md_params(ctx, 2, dt, gamma, seed))) != CR_OK) return rc;
+  if ((rc = md_end_impl(ctx, dt, gamma, seed, nullptr, 0)) != CR_OK) return rc;
   ctx->md_eval++;
   ctx->f_valid = true;
   ctx->fcons_valid = false;
@@ -1396,6 +1415,16 @@ struct cr_batch {
   size_t words = 0, flag_words = 0;
   int tasks_per_colour = 0;
   int sms = 0;
+  // captured MD/CR-MC cycle (cr_batch_cycle): the step parameters in device
+  // memory, the instantiated graph and what it was captured with
+  StepDyn *d_dyn = nullptr;
+  cudaStream_t cstream = nullptr;  // capture stream
+  cudaGraphExec_t graph = nullptr;
+  double g_dt = 0.0, g_gamma = 0.0;
+  int g_T = 0, g_R = 0, g_da = -1;
+  bool g_C = false, g_pers = false, g_fine = false, g_timing = false;
+  int64_t g_kernels = 0;                      // kernels per graph launch
+  std::vector<std::pair<int, int>> g_pairs;  // phase-kernel event pairs recorded by the graph (timing)
   SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
   PhaseShape S{}, Sc{};
   bool C = false, da_C = false;
@@ -1586,6 +1615,12 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   if (b->d_reps) cudaFree(b->d_reps);
   if (b->d_rep_first) cudaFree(b->d_rep_first);
   if (b->d_words) cudaFree(b->d_words);
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->ctx[0]->ev_reserved = 0;
+  }
+  if (b->d_dyn) cudaFree(b->d_dyn);
+  if (b->cstream) cudaStreamDestroy(b->cstream);
   free_packed_staging(b);
   void *dp[] = {b->d_sbufs, b->d_jobs, b->d_nout, b->d_errout};
   for (void *x : dp)
@@ -1599,7 +1634,7 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
 // one persistent sweep launch of every replica (words zeroed first)
 static int batch_launch_persistent(cr_batch *b, const PhaseShape &SS, int T, int R, bool da, uint32_t swc,
                                    uint32_t sweep0, uint32_t k0, uint32_t k1, int withhold = -1,
-                                   unsigned long long wait_ns = 2000000000ull) {
+                                   unsigned long long wait_ns = 2000000000ull, const StepDyn *dyn = nullptr) {
   cr_ctx *c0 = b->ctx[0];
   cudaStream_t s = c0->stream;
   CR_CUDA(cudaMemsetAsync(b->d_words, 0, sizeof(unsigned) * b->words, s));
@@ -1619,7 +1654,7 @@ static int batch_launch_persistent(cr_batch *b, const PhaseShape &SS, int T, int
   int ti;
   tbegin(c0, 0, &ti);
   const int sms = b->sms > 0 ? b->sms : 1;
-  CR_CUDA(launch_sweep(b->d_reps, SS, T, R, da, s, swc, sweep0, k0, k1, Q, b->ctas_per_sm * sms));
+  CR_CUDA(launch_sweep(b->d_reps, SS, T, R, da, s, swc, sweep0, k0, k1, Q, b->ctas_per_sm * sms, dyn));
   tend(c0, 0, ti);
   c0->launches_total++;
   return CR_OK;
@@ -1797,6 +1832,201 @@ extern "C" int cr_batch_md_begin(cr_batch *b, double dt, double gamma, uint64_t 
 
 extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed) {
   return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
+}
+
+// a context's pH changed (cr_set_pH): its copy in the batch follows
+static int batch_refresh_chem(cr_batch *b) {
+  bool changed = false;
+  const int n = (int)b->ctx.size();
+  for (int r = 0; r < n; ++r)
+    if (b->chem_seen[r] != b->ctx[r]->chem_version) {
+      b->reps[r].lnsalt_fx = b->ctx[r]->P.lnsalt_fx;
+      b->chem_seen[r] = b->ctx[r]->chem_version;
+      changed = true;
+    }
+  if (changed)
+    CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice,
+                            b->ctx[0]->stream));
+  return CR_OK;
+}
+
+// Capture one cycle of every replica -- MD begin (kick, drift, cell
+// rebuild), one sweep with the tuned launch form, MD end (forces with the
+// new charges, closing kick), step advance -- as a CUDA graph whose kernels
+// read the step's seeds and counters from b->d_dyn.  The contexts' host-side
+// counters are left as they were (the caller advances them per launch).
+static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
+  cr_ctx *c0 = b->ctx[0];
+  const int n = (int)b->ctx.size();
+  // captured on the batch's own stream (the caller's may be the legacy
+  // default stream, which cannot be captured); launched on the caller's
+  if (!b->cstream && cudaStreamCreateWithFlags(&b->cstream, cudaStreamNonBlocking) != cudaSuccess) return CR_ERR_CUDA;
+  const cudaStream_t user = c0->stream;
+  for (cr_ctx *c : b->ctx) c->stream = b->cstream;
+  cudaStream_t s = b->cstream;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  c0->ev_reserved = 0;
+  if (!c0->ev_pairs[0].empty() || !c0->ev_pairs[1].empty()) tcollect(c0);
+  std::vector<uint64_t> sweeps(n);
+  std::vector<uint32_t> evals(n);
+  std::vector<int64_t> launches(n);
+  for (int r = 0; r < n; ++r) {
+    sweeps[r] = b->ctx[r]->sweep;
+    evals[r] = b->ctx[r]->md_eval;
+    launches[r] = b->ctx[r]->launches_total;
+  }
+  const int T = da ? b->da_T : b->T, R = da ? b->da_R : b->R;
+  const bool C = da ? b->da_C : b->C, pers = da ? b->da_persistent : b->persistent;
+  const PhaseShape &SS = C ? b->Sc : b->S;
+  const StepDyn *dyn = b->d_dyn;
+  int rc = CR_OK;
+  while (c0->ev_pool.size() < c0->ev_next + 2 * (size_t)(b->ncol + 2)) {  // no event creation while capturing
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (cr_ctx *c : b->ctx) c->stream = user;
+      return CR_ERR_CUDA;
+    }
+    c0->ev_pool.push_back(e);
+  }
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    for (cr_ctx *c : b->ctx) c->stream = user;
+    return CR_ERR_CUDA;
+  }
+  {
+    rc = batch_md(b, [&](cr_ctx *c, uint64_t) { return cr_md_begin(c, dt, gamma, 0); });
+    if (rc == CR_OK && b->order_nc > 0) {
+      if (launch_domain_order(b->d_reps, n, b->ncol, b->order_nact, s, 0, 0, 0, dyn) != cudaSuccess) rc = CR_ERR_CUDA;
+      c0->launches_total++;
+    }
+    if (rc == CR_OK) {
+      if (pers) {
+        rc = batch_launch_persistent(b, SS, T, R, da, 0, 0, 0, 0, -1, 2000000000ull, dyn);
+      } else {
+        for (int col = 0; col < b->ncol && rc == CR_OK; ++col) {
+          int ti;
+          tbegin(c0, 0, &ti);
+          if (launch_phase(b->d_reps, n, b->grid_x, SS, T, R, false, da, s, 0, 0, col, 0, 0, dyn) != cudaSuccess)
+            rc = CR_ERR_CUDA;
+          tend(c0, 0, ti);
+          c0->launches_total++;
+        }
+      }
+    }
+    if (rc == CR_OK)
+      rc = batch_md(b, [&](cr_ctx *c, uint64_t r) { return md_end_impl(c, dt, gamma, 0, dyn, (unsigned)r); });
+    if (rc == CR_OK && launch_step_advance(b->d_dyn, s) != cudaSuccess) rc = CR_ERR_CUDA;
+    c0->launches_total++;
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &g);
+  if (rc == CR_OK && ec != cudaSuccess) rc = CR_ERR_CUDA;
+  if (rc == CR_OK && cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
+    b->graph = nullptr;
+    rc = CR_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  // the phase-kernel events the graph records, and the kernels it launches
+  b->g_pairs = c0->ev_pairs[0];
+  c0->ev_pairs[0].clear();
+  c0->ev_pairs[1].clear();
+  c0->ev_reserved = c0->ev_next;
+  int64_t kernels = 0;
+  for (int r = 0; r < n; ++r) {
+    kernels += b->ctx[r]->launches_total - launches[r];
+    b->ctx[r]->launches_total = launches[r];
+    b->ctx[r]->sweep = sweeps[r];
+    b->ctx[r]->md_eval = evals[r];
+    b->ctx[r]->f_valid = true;
+    b->ctx[r]->fcons_valid = false;
+  }
+  for (cr_ctx *c : b->ctx) c->stream = user;
+  b->g_kernels = kernels;
+  b->g_dt = dt;
+  b->g_gamma = gamma;
+  b->g_T = T;
+  b->g_R = R;
+  b->g_C = C;
+  b->g_pers = pers;
+  b->g_fine = b->fine;
+  b->g_da = da ? 1 : 0;
+  b->g_timing = c0->timing;
+  return rc;
+}
+
+extern "C" int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t sweep_seed0,
+                              uint64_t md_seed0, int32_t da) {
+  if (!b || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  cr_ctx *c0 = b->ctx[0];
+  cudaStream_t s = c0->stream;
+  if (da)
+    for (cr_ctx *c : b->ctx)
+      if (!c->has_mlp) return CR_ERR_INVALID_ARG;
+  // a step runs from the graph once the tuner has finished and every replica
+  // holds the forces of a completed step (same counters); earlier steps run
+  // call by call
+  auto graphable = [&]() {
+    if (da ? b->da_tuning : b->tuning) return false;
+    for (cr_ctx *c : b->ctx)
+      if (!c->f_valid || c->md_eval != c0->md_eval || c->sweep != c0->sweep || c->stream != s) return false;
+    return true;
+  };
+  int step = 0;
+  int rc = CR_OK;
+  for (; step < n_steps && !graphable(); ++step) {
+    if ((rc = cr_batch_md_begin(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
+    if ((rc = batch_sweep_impl(b, 1, sweep_seed0 + (uint64_t)step, da != 0)) != CR_OK) return rc;
+    if ((rc = cr_batch_md_end(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
+  }
+  if (step == n_steps) return CR_OK;
+  if ((rc = batch_refresh_chem(b)) != CR_OK) return rc;
+  if (da) {  // the surrogates' device copies
+    bool changed = false;
+    for (size_t r = 0; r < b->ctx.size(); ++r)
+      if (b->reps[r].mlp_w != b->ctx[r]->P.mlp_w || b->reps[r].mlp_b != b->ctx[r]->P.mlp_b) {
+        b->reps[r].mlp_w = b->ctx[r]->P.mlp_w;
+        b->reps[r].mlp_b = b->ctx[r]->P.mlp_b;
+        changed = true;
+      }
+    if (changed)
+      CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * b->ctx.size(), cudaMemcpyHostToDevice, s));
+  }
+  if (!b->d_dyn) CR_CUDA(cudaMalloc((void **)&b->d_dyn, sizeof(StepDyn)));
+  const int T = da ? b->da_T : b->T, R = da ? b->da_R : b->R;
+  const bool C = da ? b->da_C : b->C, pers = da ? b->da_persistent : b->persistent;
+  if (!b->graph || b->g_dt != dt || b->g_gamma != gamma || b->g_T != T || b->g_R != R || b->g_C != C ||
+      b->g_pers != pers || b->g_fine != b->fine || b->g_da != (da ? 1 : 0) || b->g_timing != c0->timing) {
+    if ((rc = batch_capture_cycle(b, dt, gamma, da != 0)) != CR_OK) return rc;
+  }
+  // this call's seeds and counters (a pageable source: staged before the call returns)
+  StepDyn d{};
+  d.step = 0;
+  d.sweep_seed0 = sweep_seed0 + (uint64_t)step;
+  d.md_seed0 = md_seed0 + (uint64_t)step;
+  d.sweep0 = (uint32_t)c0->sweep;
+  d.eval0 = c0->md_eval;
+  CR_CUDA(cudaMemcpyAsync(b->d_dyn, &d, sizeof(StepDyn), cudaMemcpyHostToDevice, s));
+  for (; step < n_steps; ++step) {
+    CR_CUDA(cudaGraphLaunch(b->graph, s));
+    for (cr_ctx *c : b->ctx) {
+      c->sweep++;
+      c->md_eval++;
+      c->f_valid = true;
+      c->fcons_valid = false;
+    }
+    c0->launches_total += b->g_kernels;
+    if (c0->timing) {  // the phase kernels' event pairs of this launch
+      CR_CUDA(cudaStreamSynchronize(s));
+      for (auto &pr : b->g_pairs) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c0->ev_pool[pr.first], c0->ev_pool[pr.second]) == cudaSuccess) c0->ms[0] += ms;
+        c0->launches[0]++;
+      }
+    }
+  }
+  return CR_OK;
 }
 
 extern "C" int cr_batch_load(cr_batch *b, const cr_load_args *args) {

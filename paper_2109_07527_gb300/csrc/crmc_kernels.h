@@ -7,6 +7,16 @@
 
 namespace crmc {
 
+// Per-step values of a captured MD/CR-MC cycle (cr_batch_cycle), read by the
+// kernels from device memory so that one CUDA graph serves every step: step s
+// of a call uses the seeds seed0 + s, the sweep counter sweep0 + s and the
+// force-evaluation counter eval0 + s; the graph's last node advances step.
+struct StepDyn {
+  unsigned long long step;
+  unsigned long long sweep_seed0, md_seed0;
+  unsigned int sweep0, eval0;
+};
+
 struct MdParams {
   float dt, gamma, amp;   // time step, friction, sqrt(2 gamma kT / dt)
   uint32_t key0, key1, eval;
@@ -21,6 +31,8 @@ struct MdParams {
   float reach2;            // squared interaction reach with a margin (cells beyond it are skipped)
   long long *fsum;         // [3 max_particles] pair-force sums (2^-24 fixed point) handed to the
                            // per-particle finish kernel; null: the force kernel finishes itself
+  const StepDyn *dyn;      // non-null in a captured cycle: key = (md_seed0 + step) ^ (rep << 32), eval = eval0 + step
+  unsigned int rep;
 };
 
 struct RebuildBufs {
@@ -81,7 +93,7 @@ void phase_shape(int i, int *threads, int *regs, bool da);
 bool phase_shape_compact(int i, bool da);  // shape i uses the compact list and halo capacities
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
-                         uint32_t k0, uint32_t k1);
+                         uint32_t k0, uint32_t k1, const StepDyn *dyn = nullptr);
 // Schedule of a persistent sweep (k_cr_sweep): tasks (colour, replica, rank)
 // claimed in that order; next, done and abort are device words zeroed before
 // every launch.
@@ -100,11 +112,13 @@ struct SweepSched {
 // one sweep of every replica in one persistent launch; max_ctas > 0 caps the grid
 cudaError_t launch_sweep(const SysParams *d_reps, const PhaseShape &S, int threads, int R, bool da, cudaStream_t s,
                          uint32_t sweep, uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q,
-                         int max_ctas);
+                         int max_ctas, const StepDyn *dyn = nullptr);
+// the step counter of a captured cycle (the graph's last node)
+cudaError_t launch_step_advance(StepDyn *dyn, cudaStream_t s);
 // launch order of every colour's domains for one sweep (densest region first);
 // does nothing for colours beyond the ordering limit
 cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, int nact, cudaStream_t s, uint32_t sweep,
-                                uint32_t k0, uint32_t k1);
+                                uint32_t k0, uint32_t k1, const StepDyn *dyn = nullptr);
 // particle list (plist, n_particles: device scratch of max_particles + 1
 // ints), then the force kernel (one warp per particle)
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,

@@ -84,7 +84,14 @@ __device__ __forceinline__ void finish_particle(const SysParams &P, const MdPara
   // Langevin: -gamma v + sqrt(2 gamma kT / dt) xi, xi from Box-Muller on
   // Philox(counter = (id_lo, id_hi, eval, 5), key = seed)
   float4 v = M.vel[gi];
-  const uint4 w = philox10((uint32_t)id, (uint32_t)(id >> 32), M.eval, 5u, M.key0, M.key1);
+  uint32_t key0 = M.key0, key1 = M.key1, eval = M.eval;
+  if (M.dyn) {  // a captured cycle: this step's key and evaluation counter
+    const unsigned long long step = M.dyn->step, seed = M.dyn->md_seed0 + step;
+    key0 = (uint32_t)seed;
+    key1 = (uint32_t)(seed >> 32) ^ M.rep;
+    eval = M.dyn->eval0 + (uint32_t)step;
+  }
+  const uint4 w = philox10((uint32_t)id, (uint32_t)(id >> 32), eval, 5u, key0, key1);
   const float u0 = ((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
   const float u1 = ((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
   const float u2 = ((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
@@ -464,6 +471,15 @@ __global__ void k_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uin
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
+
+__global__ void k_step_advance(StepDyn *dyn) {
+  if (threadIdx.x == 0) dyn->step += 1;
+}
+
+cudaError_t launch_step_advance(StepDyn *dyn, cudaStream_t s) {
+  k_step_advance<<<1, 32, 0, s>>>(dyn);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, int *n_particles, int max_particles,
                              cudaStream_t s) {

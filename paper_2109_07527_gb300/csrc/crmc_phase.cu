@@ -1518,8 +1518,14 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
 template <int T, int R, bool LOG, bool DA>
 __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
     k_cr_phase(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, int colour,
-               uint32_t key0, uint32_t key1_base) {
+               uint32_t key0, uint32_t key1_base, const StepDyn *dyn) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (dyn) {  // a captured cycle: this step's sweep counter and key
+    const unsigned long long step = dyn->step, seed = dyn->sweep_seed0 + step;
+    sweep = dyn->sweep0 + (uint32_t)step;
+    key0 = (uint32_t)seed;
+    key1_base = (uint32_t)(seed >> 32);
+  }
   phase_task<T, R, LOG, DA>(smem, reps, S, sweep, sweep0, colour, key0, key1_base, (int)blockIdx.x,
                             (int)blockIdx.y);
 }
@@ -1583,8 +1589,14 @@ __device__ __forceinline__ bool wait_at_least(const unsigned *p, unsigned need, 
 template <int T, int R, bool DA>
 __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 4 : (T <= 256 ? 2 : 1)))))
     k_cr_sweep(const SysParams *__restrict__ reps, PhaseShape S, uint32_t sweep, uint32_t sweep0, uint32_t key0,
-               uint32_t key1_base, SweepSched Q) {
+               uint32_t key1_base, SweepSched Q, const StepDyn *dyn) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (dyn) {  // a captured cycle: this step's sweep counter and key
+    const unsigned long long step = dyn->step, seed = dyn->sweep_seed0 + step;
+    sweep = dyn->sweep0 + (uint32_t)step;
+    key0 = (uint32_t)seed;
+    key1_base = (uint32_t)(seed >> 32);
+  }
   __shared__ int s_task, s_run, s_dom;
   const int lane = threadIdx.x & 31;
   const int per_colour = Q.rep_first[Q.n_rep];
@@ -1650,7 +1662,8 @@ __global__ void __launch_bounds__(T, (T <= 32 ? 16 : (T <= 64 ? 8 : (T <= 128 ? 
 
 template <int T, int R, bool DA>
 static cudaError_t launch_sweep_t(const SysParams *d_reps, PhaseShape S, cudaStream_t s, uint32_t sweep,
-                                  uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q, int max_ctas) {
+                                  uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q, int max_ctas,
+                                  const StepDyn *dyn) {
   if (R > 0) S.hcs = 0;  // halo in registers
   static size_t attr_bytes = 0;
   static int per_sm = 0;
@@ -1675,16 +1688,16 @@ static cudaError_t launch_sweep_t(const SysParams *d_reps, PhaseShape S, cudaStr
   int grid = std::min(total, per_sm * std::max(sms, 1));
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (grid <= 0) return cudaSuccess;
-  k_cr_sweep<T, R, DA><<<grid, T, smem, s>>>(d_reps, S, sweep, sweep0, k0, k1, Q);
+  k_cr_sweep<T, R, DA><<<grid, T, smem, s>>>(d_reps, S, sweep, sweep0, k0, k1, Q, dyn);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const SysParams *d_reps, const PhaseShape &S, int threads, int R, bool da, cudaStream_t s,
                          uint32_t sweep, uint32_t sweep0, uint32_t k0, uint32_t k1, const SweepSched &Q,
-                         int max_ctas) {
+                         int max_ctas, const StepDyn *dyn) {
 #define CRMC_SW(TT, RR, DD)                                                                   \
   if (da == DD && threads == TT && R == RR)                                                    \
-    return launch_sweep_t<TT, RR, DD>(d_reps, S, s, sweep, sweep0, k0, k1, Q, max_ctas);
+    return launch_sweep_t<TT, RR, DD>(d_reps, S, s, sweep, sweep0, k0, k1, Q, max_ctas, dyn);
   CRMC_SW(32, 0, false)
   CRMC_SW(64, 0, false)
   CRMC_SW(128, 0, false)
@@ -1709,7 +1722,13 @@ cudaError_t launch_sweep(const SysParams *d_reps, const PhaseShape &S, int threa
 // more than ORDER_MAX_NACT domains keep the natural order (P.order is null).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_domain_order(const SysParams *__restrict__ reps, uint32_t sweep, uint32_t key0,
-                                                      uint32_t key1_base) {
+                                                      uint32_t key1_base, const StepDyn *dyn) {
+  if (dyn) {  // a captured cycle: this step's sweep counter and key
+    const unsigned long long step = dyn->step, seed = dyn->sweep_seed0 + step;
+    sweep = dyn->sweep0 + (uint32_t)step;
+    key0 = (uint32_t)seed;
+    key1_base = (uint32_t)(seed >> 32);
+  }
   const SysParams &P = reps[blockIdx.x];
   if (!P.order) return;
   __shared__ int cost[ORDER_MAX_NACT];
@@ -1748,9 +1767,9 @@ __global__ void __launch_bounds__(512) k_domain_order(const SysParams *__restric
 }
 
 cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, int nact, cudaStream_t s, uint32_t sweep,
-                                uint32_t k0, uint32_t k1) {
+                                uint32_t k0, uint32_t k1, const StepDyn *dyn) {
   if (nact > ORDER_MAX_NACT) return cudaSuccess;  // contexts keep P.order null then
-  k_domain_order<<<dim3(n_rep, ncol), 512, 0, s>>>(d_reps, sweep, k0, k1);
+  k_domain_order<<<dim3(n_rep, ncol), 512, 0, s>>>(d_reps, sweep, k0, k1, dyn);
   return cudaGetLastError();
 }
 
@@ -1795,7 +1814,8 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
 
 template <int T, int R, bool LOG, bool DA>
 static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x, PhaseShape S, cudaStream_t s,
-                                  uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0, uint32_t k1) {
+                                  uint32_t sweep, uint32_t sweep0, int colour, uint32_t k0, uint32_t k1,
+                                  const StepDyn *dyn) {
   if (R > 0) S.hcs = 0;  // halo in registers
   static size_t attr_bytes = 0;
   const size_t smem = phase_smem_bytes(S, T, DA);
@@ -1805,7 +1825,7 @@ static cudaError_t launch_phase_t(const SysParams *d_reps, int n_rep, int grid_x
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  k_cr_phase<T, R, LOG, DA><<<dim3(n_rep, grid_x), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1);
+  k_cr_phase<T, R, LOG, DA><<<dim3(n_rep, grid_x), T, smem, s>>>(d_reps, S, sweep, sweep0, colour, k0, k1, dyn);
   return cudaGetLastError();
 }
 
@@ -1836,15 +1856,15 @@ size_t phase_shape_smem(const PhaseShape &S, int threads, int regs, bool da) {
 
 cudaError_t launch_phase(const SysParams *d_reps, int n_rep, int grid_x, const PhaseShape &S, int threads, int R,
                          bool log, bool da, cudaStream_t s, uint32_t sweep, uint32_t sweep0, int colour,
-                         uint32_t k0, uint32_t k1) {
+                         uint32_t k0, uint32_t k1, const StepDyn *dyn) {
 #define CRMC_CASE(TT, RR)                                                                                      \
   if (!da && threads == TT && R == RR)                                                                         \
-    return log ? launch_phase_t<TT, RR, true, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1) \
-               : launch_phase_t<TT, RR, false, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
+    return log ? launch_phase_t<TT, RR, true, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1, dyn) \
+               : launch_phase_t<TT, RR, false, false>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1, dyn);
 #define CRMC_CASE_DA(TT, RR)                                                                                   \
   if (da && threads == TT && R == RR)                                                                          \
-    return log ? launch_phase_t<TT, RR, true, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1)  \
-               : launch_phase_t<TT, RR, false, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1);
+    return log ? launch_phase_t<TT, RR, true, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1, dyn)  \
+               : launch_phase_t<TT, RR, false, true>(d_reps, n_rep, grid_x, S, s, sweep, sweep0, colour, k0, k1, dyn);
   CRMC_CASE(32, 0)
   CRMC_CASE(64, 0)
   CRMC_CASE(128, 0)

@@ -94,3 +94,36 @@ def test_batch_split_step_equals_single_contexts(crmc):
         s1, s2 = c1.state(), c2.state()
         for k in ("id", "xyz", "vel", "state"):
             assert np.array_equal(s1[k], s2[k]), k
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_cycle_equals_calls(crmc, mode):
+    """cr_batch_cycle (one CUDA graph launch per step once tuned, the step's
+    seeds and counters read from device memory) equals the same cycles made
+    call by call -- md_begin, sweep, md_end with seeds seed0 + s -- bit for
+    bit, for per-colour and persistent sweeps, and across two calls (the graph
+    reused with new seeds)."""
+    ws = [W.config2(seed=14, scale=0.5, pH=p) for p in (3.0, 4.5, 6.0)]
+    runs = []
+    for graph in (True, False):
+        ctxs = [crmc.Context(w) for w in ws]
+        b = crmc.Batch(ctxs)
+        b.set_persistent(mode)
+        b.set_launch_shape(64, 0)
+        if graph:
+            b.cycle(2, 0.005, 1.0, 100, 500)  # the first step runs call by call (no forces yet)
+            ctxs[0].timing(reset=True)
+            b.cycle(4, 0.005, 1.0, 102, 502)
+            assert ctxs[0].timing(reset=True)["launches"] > 0  # the graph's kernels are counted
+        else:
+            for s in range(6):
+                b.md_begin(0.005, 1.0, 500 + s)
+                b.sweep(1, 100 + s)
+                b.md_end(0.005, 1.0, 500 + s)
+        for g in ctxs:
+            g.check()
+        runs.append([g.state() for g in ctxs])
+        b.close()
+    for a, c in zip(*runs):
+        for k in ("id", "xyz", "vel", "state"):
+            assert np.array_equal(a[k], c[k]), k
