@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-da", action="store_true")
+    ap.add_argument("--no-config4", action="store_true")
     return ap.parse_args()
 
 
@@ -342,6 +343,9 @@ def measured_tensor_peak():
 TUNE_SWEEPS = 14
 BATCH_TUNE_SWEEPS = 26
 
+# exact (feature, pair energy) pairs recorded for the surrogate's training
+TRAIN_PAIRS = 1_000_000
+
 # floating-point operations of one training row (algorithmic, K = 48 input):
 # forward 48x128 + 2 x 128x128, backward 4 x 128x128 + 128x48, 2 flops per MAC
 TRAIN_FLOPS_PER_ROW = 2 * (48 * 128 + 2 * 128 * 128) + 2 * (4 * 128 * 128 + 128 * 48)
@@ -356,12 +360,15 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     gd = crmc.Context(ws[5])  # pH 4.5
     gd.set_surrogate(W.random_mlp(seed=5, out_gain=0.0))
     X, y = [], []
-    for s in range(12):
+    n_rec, s = 0, 0
+    while n_rec < TRAIN_PAIRS:  # exact (feature, pair dE) pairs of the polyelectrolyte box, one MD step between sweeps
         r = gd.sweep_da(gd.trials_per_sweep, 40 + s, log=True, features=True)
         ok = (r["da"]["stage"] > 0) & np.isfinite(r["da"]["lnA2"])
         X.append(r["features"][ok])
         y.append(r["da"]["dE_sur"][ok].astype(np.float64) - r["da"]["lnA2"][ok])
+        n_rec += int(ok.sum())
         gd.md_step(1, dt, gamma, 60 + s)
+        s += 1
     X = np.concatenate(X)
     y = np.concatenate(y).astype(np.float32)
     n_hold = len(X) // 10
@@ -417,7 +424,8 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     out = {"value": per_step * steps / (ms / 1e3), "unit": "trials/s", "steps": steps, "ms_per_step": ms / steps,
            "launch_shape": None, "stage1_reject_frac": stage1_reject, "surrogate_error": sur_err,
            "alpha_end": [round(c.counts()["alpha"], 4) for c in ctxs],
-           "train": {"rows": int(nb * Bt), "batch": Bt, "steps": n_train, "ms": t_ms,
+           "train": {"pairs_recorded": int(n_rec), "recording_sweeps": s, "rows": int(nb * Bt), "batch": Bt,
+                     "steps": n_train, "ms": t_ms,
                      "rows_per_s": n_train * Bt / (t_ms / 1e3), "loss_first": loss0, "loss_end": loss_end,
                      "held_out_pairs": int(n_hold),
                      "roofline": {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
@@ -426,6 +434,71 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     b.close()
     for c in ctxs:
         c.close()
+    out["config5"] = run_config5(crmc, torch, stream, flush, mlp, steps)
+    return out
+
+
+def run_config5(crmc, torch, stream, flush, mlp, steps):
+    """The large box of the learned stage: 100 x 200 acid beads (pKa 4.5, pH
+    4.5), L = 250, ~25,000 ion pairs, with the surrogate trained on the
+    polyelectrolyte pairs: plain sweeps against delayed-acceptance sweeps,
+    each timed after its own launch-shape tuning (L2 flushed between
+    sweeps), and the stage-1 rejection rate of a logged DA sweep."""
+    from paper_2109_07527_gb300 import workloads as W
+    w5 = W.config5(seed=1)
+    g = crmc.Context(w5)
+    tps = g.trials_per_sweep
+    g.sweep(tps * TUNE_SWEEPS, 0x55)
+    ms_plain = time_steps(lambda s: g.sweep(tps, 300 + s), steps, stream, flush)
+    a_plain = g.counts()["alpha"]
+    g.close()
+    h = crmc.Context(w5)
+    h.set_surrogate(mlp)
+    h.sweep_da(tps * 6, 0x55)  # DA shapes
+    ms_da = time_steps(lambda s: h.sweep_da(tps, 300 + s), steps, stream, flush)
+    a_da = h.counts()["alpha"]
+    r = h.sweep_da(tps, 999, log=True, features=False)
+    ev = r["da"]["stage"] > 0
+    rej = float(np.mean(r["da"]["stage"][ev] == 1))
+    counted = float(np.mean(ev))
+    h.close()
+    v_plain, v_da = tps * steps / (ms_plain / 1e3), tps * steps / (ms_da / 1e3)
+    return {"workload": f"100 x 200 acid beads, L=250, {w5.n} particles, {w5.n_sites} sites, pH 4.5; "
+                        f"{tps} trials per sweep", "steps": steps,
+            "plain": {"value": v_plain, "unit": "trials/s", "ms_per_sweep": ms_plain / steps, "alpha_end": a_plain},
+            "surrogate_da": {"value": v_da, "unit": "trials/s", "ms_per_sweep": ms_da / steps, "alpha_end": a_da,
+                             "stage1_reject_frac": rej, "evaluated_frac": counted},
+            "da_over_plain": v_da / v_plain}
+
+
+def run_config4(crmc, torch, stream, flush, steps):
+    """The batched titration: 64 replicas, chain lengths log-uniform in
+    [50, 1000], pH uniform in [2, 10], boxes at 10^-3 monomers per sigma^3
+    (36.8 to 100 sigma), one batch; each step one MD/CR-MC cycle of every
+    replica (one sweep inside one MD step), through the captured cycle."""
+    from paper_2109_07527_gb300 import workloads as W
+    ws = W.config4(seed=1)
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(BATCH_TUNE_SWEEPS, 0x44)
+    g0 = ctxs[0]
+    g0.set_timing(True)
+    for s in range(3):
+        b.cycle(1, 0.005, 1.0, 1 + s, 1000 + s)
+    g0.timing(reset=True)
+    ms = time_steps(lambda s: b.cycle(1, 0.005, 1.0, 100 + s, 5000 + s), steps, stream, flush)
+    tm = g0.timing(reset=True)
+    for g in ctxs:
+        g.check()
+    per_step = sum(g.trials_per_sweep for g in ctxs)
+    out = {"workload": "64 replicas, N log-uniform in [50, 1000], pH uniform in [2, 10], pKa 5, "
+                       "1e-3 monomers per sigma^3, 10 mM", "replicas": len(ctxs), "trials_per_step": per_step,
+           "value": per_step * steps / (ms / 1e3), "unit": "trials/s", "steps": steps, "ms_per_step": ms / steps,
+           "sweep_launches_per_step": tm["phase_launches"] / steps,
+           "sweep_kernel_ms_per_step": tm["phase_ms"] / steps, "launch_shape": list(b.launch_shape())}
+    b.close()
+    for g in ctxs:
+        g.close()
     return out
 
 
@@ -545,6 +618,9 @@ def run_ours(args):
     da = None
     if rank == 0 and not args.no_da:
         da = run_da(crmc, torch, stream, flush, ws, dt, gamma, max(10, min(args.steps, 50)))
+    cfg4 = None
+    if rank == 0 and not args.no_config4:
+        cfg4 = run_config4(crmc, torch, stream, flush, max(10, min(args.steps, 50)))
 
     # ---- end to end through the public API with host buffers: each step
     # uploads every replica's configuration from pinned host memory, runs the
@@ -604,7 +680,7 @@ def run_ours(args):
            "roofline": roofline, "gpu_launches": tm["launches"],
            "graph_launches_per_step": 1, "kernels_per_step": tm["launches"] / args.steps,
            "clocks": cl, "e2e": e2e, "plain": plain,
-           "surrogate_da": da,
+           "surrogate_da": da, "batched_titration": cfg4,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"], alpha_o = cpu_baseline(ph_sweep_workloads(0))
