@@ -508,13 +508,16 @@ void cr_batch_destroy(cr_batch *b);
 /* ---- training of the DA surrogate (MSE on feature / pair-energy pairs, Adam) ----
  * Every matrix product runs on the tensor cores (tcgen05.mma, BF16 operands,
  * FP32 accumulation in tensor memory); masters, gradients and Adam moments are
- * FP32, activations BF16.  Parameter vector order (FP32, N = 39425):
+ * FP32, activations BF16.  X must be 16-byte aligned.  Parameter vector order (FP32, N = 39425):
  * W1 [128][48], b1 [128], W2 [128][128], b2, W3 [128][128], b3, w4 [128], b4. */
 typedef struct cr_trainer cr_trainer;
 typedef struct {
   int32_t max_batch;  /* largest batch (a multiple of 128) */
   double lr, beta1, beta2, eps;  /* Adam */
   double target_clip; /* targets are clipped to [-clip, clip] (kT); <= 0: no clip */
+  int32_t unfused;    /* 0: the fused step (one kernel per SM runs each 128-row tile's forward,
+                         loss, backward and weight-gradient products on the tensor cores with
+                         every operand in shared memory); 1: one product per launch */
 } cr_train_cfg;
 #define CR_TRAIN_N_PARAMS 39425
 int cr_train_create(cr_trainer **out, const cr_mlp *init, const cr_train_cfg *cfg);

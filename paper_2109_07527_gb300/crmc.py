@@ -113,7 +113,7 @@ class cr_ungrouped(C.Structure):
 
 class cr_train_cfg(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
-                ("eps", C.c_double), ("target_clip", C.c_double)]
+                ("eps", C.c_double), ("target_clip", C.c_double), ("unfused", C.c_int32)]
 
 _L = None
 
@@ -612,10 +612,11 @@ class Trainer:
     """Surrogate training on the tensor cores (owns one cr_trainer).  Batches
     are device pointers (raw ints, e.g. torch tensors' data_ptr())."""
 
-    def __init__(self, mlp, max_batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, target_clip=20.0, stream=None):
+    def __init__(self, mlp, max_batch, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, target_clip=20.0, stream=None,
+                 unfused=False):
         self._lib = _lib()
         m, keep = _mlp_struct(mlp)
-        cfg = cr_train_cfg(int(max_batch), lr, beta1, beta2, eps, target_clip)
+        cfg = cr_train_cfg(int(max_batch), lr, beta1, beta2, eps, target_clip, 1 if unfused else 0)
         h = C.c_void_p()
         _chk(self._lib.cr_train_create(C.byref(h), C.byref(m), C.byref(cfg)), "cr_train_create")
         self._h = h

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -531,6 +532,386 @@ __global__ void k_adam(float *P, const float *G, float *Mm, float *Vv, int n, fl
 }
 
 // ---------------------------------------------------------------------------
+// The fused training step (k_train_fused): each CTA (one per SM, 128 threads,
+// thread = row of a 128-row tile) runs, tile after tile, the three forward
+// products, the output layer and loss, the two backward data products and the
+// three weight-gradient products.  Operands never leave the SM: the threads
+// write X, h1, h2 and the back-propagated errors G3, G2, G1 as BF16 into
+// 128-byte-swizzled K-major tiles in shared memory (the layout TMA gives the
+// products of k_mma), the weights stay resident there, the products
+// accumulate in tensor memory -- the weight gradients across all of the CTA's
+// tiles -- and each CTA writes its partial gradients once.  The weight-
+// gradient products (K = the tile's rows) and the backward data products
+// (B = W, K = W's output index) read the same stored tiles as MN-major
+// operands (transpose bits of the instruction descriptor; LBO = the 64-column
+// slice stride, SBO = 8 rows), so no transposed copy is written.  The bias
+// and output-layer gradients are column sums in shared memory, the loss a
+// block sum.  A second kernel sums the CTAs' partials in CTA order
+// (deterministic).  Every mbarrier wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int FT_THREADS = 128;
+constexpr uint32_t FT_TILE = 16384;         // one 128-row x 64-column BF16 slice
+constexpr uint32_t FT_G3 = 0;               // G3, then G1 [128 x 128] (read as MN-major operands)
+constexpr uint32_t FT_H2 = 2 * FT_TILE;     // h2, then G2 [128 x 128]
+constexpr uint32_t FT_H1 = 4 * FT_TILE;     // h1 [128 x 128]
+constexpr uint32_t FT_X = 6 * FT_TILE;      // X [128 x 64]: 48 features, zero padding
+constexpr uint32_t FT_W1 = 7 * FT_TILE;     // W1 [128 out x 64 in]
+constexpr uint32_t FT_W2 = 8 * FT_TILE;     // W2 [128 x 128]
+constexpr uint32_t FT_W3 = 10 * FT_TILE;    // W3 [128 x 128]
+constexpr uint32_t FT_MISC = 12 * FT_TILE;  // column-sum tiles, accumulators, barrier, tensor-memory slot
+constexpr uint32_t FT_ACC = FT_MISC + 4 * 32 * 17 * 4;     // [4][128] gb1, gb2, gb3, gw4; [4] gb4, loss
+constexpr uint32_t FT_BAR = FT_ACC + (4 * 128 + 4) * 4;
+constexpr size_t FT_SMEM = 1024 + FT_BAR + 64;
+// tensor-memory columns: the products' accumulator, then the weight gradients
+constexpr uint32_t TM_Z = 0, TM_GW3 = 128, TM_GW2 = 256, TM_GW1 = 384;
+
+// byte offset of 16-byte chunk j (of 8) of row r in a K-major 128-byte-swizzled slice
+__device__ __forceinline__ uint32_t sw128(int r, int j) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((j ^ (r & 7)) << 4));
+}
+// 16 BF16 values of row r, columns c .. c + 15 (c a multiple of 16), into / from a tile of slices
+__device__ __forceinline__ void st_row16(uint8_t *tile, int r, int c, const uint16_t (&h)[16]) {
+  uint8_t *sl = tile + (uint32_t)(c >> 6) * FT_TILE;
+  const int j = (c & 63) >> 3;
+  *(uint4 *)(sl + sw128(r, j)) =
+      make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+  *(uint4 *)(sl + sw128(r, j + 1)) =
+      make_uint4(h[8] | (h[9] << 16), h[10] | (h[11] << 16), h[12] | (h[13] << 16), h[14] | (h[15] << 16));
+}
+__device__ __forceinline__ void ld_row16(const uint8_t *tile, int r, int c, uint16_t (&h)[16]) {
+  const uint8_t *sl = tile + (uint32_t)(c >> 6) * FT_TILE;
+  const int j = (c & 63) >> 3;
+  const uint4 a = *(const uint4 *)(sl + sw128(r, j)), b = *(const uint4 *)(sl + sw128(r, j + 1));
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    h[2 * i] = (uint16_t)(w[i] & 0xFFFFu);
+    h[2 * i + 1] = (uint16_t)(w[i] >> 16);
+  }
+}
+
+// Shared-memory descriptor of an MN-major operand read from K-major-stored
+// 128-byte-swizzled slices: the 64-element blocks along M (or N) are the
+// slices (LBO = slice stride), the 8-deep groups along K are 8 stored rows
+// (SBO = 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(FT_TILE >> 4) << 16;  // leading byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+constexpr uint32_t IDESC_TA = 1u << 15, IDESC_TB = 1u << 16;  // A / B MN-major
+
+// D = A B^T with both K-major (K = 64 * kslices), by thread 0
+__device__ __forceinline__ void ft_mma_kk(uint32_t d, uint32_t a, uint32_t b, int kslices, uint32_t idesc) {
+  for (int kk = 0; kk < 4 * kslices; ++kk)
+    umma_bf16(d, sdesc_sw128(a + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32),
+              sdesc_sw128(b + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32), idesc, kk ? 1u : 0u);
+}
+// D (+)= A^T B over the tile's 128 rows (K = stored rows; A and B MN-major views)
+__device__ __forceinline__ void ft_mma_mn(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc, bool acc) {
+  for (int kk = 0; kk < 8; ++kk)
+    umma_bf16(d, sdesc_mn128(a + kk * 2048), sdesc_mn128(b + kk * 2048), idesc, (acc || kk) ? 1u : 0u);
+}
+// D = A W with A K-major (K = W's stored rows) and W read as an MN-major operand
+__device__ __forceinline__ void ft_mma_kmn(uint32_t d, uint32_t a, uint32_t w, uint32_t idesc) {
+  for (int kk = 0; kk < 8; ++kk)
+    umma_bf16(d, sdesc_sw128(a + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32), sdesc_mn128(w + kk * 2048), idesc,
+              kk ? 1u : 0u);
+}
+
+struct FusedArgs {
+  const float *X, *t;  // [B][48] features, [B] targets
+  int B;
+  float clip, inv_batch;
+  const uint16_t *W1p, *W2, *W3, *w4;  // BF16 copies of the masters
+  const float *P;                      // FP32 masters (biases)
+  float *part;                         // [gridDim.x][N_PARAMS + 1] partial gradients and loss
+  int *err;
+  uint32_t spin;
+};
+
+// rows of a [rows x cols] BF16 matrix in global memory into a swizzled tile
+__device__ __forceinline__ void ft_stage_weights(uint8_t *tile, const uint16_t *W, int rows, int cols) {
+  const int chunks = cols / 8;  // 16-byte chunks per row
+  for (int i = threadIdx.x; i < rows * chunks; i += blockDim.x) {
+    const int r = i / chunks, c = i % chunks;
+    const uint4 v = *(const uint4 *)(W + (size_t)r * cols + c * 8);
+    *(uint4 *)(tile + (uint32_t)(c >> 3) * FT_TILE + sw128(r, c & 7)) = v;
+  }
+}
+
+__global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float *tbuf_all = (float *)(sm + FT_MISC);
+  float *acc = (float *)(sm + FT_ACC);  // [0..127] gb1, [128..] gb2, [256..] gb3, [384..] gw4, [512] gb4, [513] loss
+  uint64_t *bar = (uint64_t *)(sm + FT_BAR);
+  uint32_t *tmem_slot = (uint32_t *)(sm + FT_BAR + 16);
+  int *fail_s = (int *)(sm + FT_BAR + 32);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r = threadIdx.x;
+  float *tbuf = tbuf_all + warp * 32 * 17;
+  const uint32_t lim = A.spin ? A.spin : SPIN_LIMIT;
+  const uint32_t sbase = smem_u32(sm);
+  constexpr uint32_t ID_KK = idesc_bf16(128, 128), ID_MN = idesc_bf16(128, 128) | IDESC_TA | IDESC_TB,
+                     ID_MN48 = idesc_bf16(128, 48) | IDESC_TA | IDESC_TB, ID_KMN = idesc_bf16(128, 128) | IDESC_TB;
+
+  for (int i = threadIdx.x; i < 4 * 128 + 4; i += blockDim.x) acc[i] = 0.0f;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    *fail_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  ft_stage_weights(sm + FT_W1, A.W1p, 128, 64);
+  ft_stage_weights(sm + FT_W2, A.W2, 128, 128);
+  ft_stage_weights(sm + FT_W3, A.W3, 128, 128);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
+  const float *b1 = A.P + OFF_B1, *b2 = A.P + OFF_B2, *b3 = A.P + OFF_B3;
+  const float b4 = A.P[OFF_B4];
+  uint32_t phase = 0;
+  int tiles_done = 0;
+
+  // every thread: wait for the last commit (bounded); false when it ran out
+  auto wait_mma = [&]() -> bool {
+    const bool ok = mbar_wait(bar, phase, lim);
+    phase ^= 1u;
+    const int f = __syncthreads_or(!ok);
+    tc_fence_after();
+    return f == 0;
+  };
+  // after the threads wrote operand tiles: visible to the tensor cores
+  auto publish = [&]() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  };
+
+  const int n_tiles = A.B / 128;
+  bool ok = true;
+  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const size_t row = (size_t)tile * 128 + r;
+    // ---- X (BF16, zero padded to 64) and the clipped target of this row
+    {
+      const float4 *xr = (const float4 *)(A.X + row * 48);
+#pragma unroll
+      for (int c = 0; c < 64; c += 16) {
+        uint16_t h[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4 v = c + 4 * q < 48 ? xr[(c >> 2) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+          h[4 * q] = to_bf16(v.x); h[4 * q + 1] = to_bf16(v.y); h[4 * q + 2] = to_bf16(v.z); h[4 * q + 3] = to_bf16(v.w);
+        }
+        st_row16(sm + FT_X, r, c, h);
+      }
+    }
+    const float tgt = fminf(fmaxf(A.t[row], -A.clip), A.clip);
+    publish();
+    // ---- z1 = X W1^T; h1 = relu(z1 + b1)
+    if (threadIdx.x == 0) {
+      ft_mma_kk(tmem + TM_Z, sbase + FT_X, sbase + FT_W1, 1, ID_KK);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(trow + TM_Z + c, v);
+      uint16_t h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) h[j] = to_bf16(fmaxf(v[j] + __ldg(&b1[c + j]), 0.0f));
+      st_row16(sm + FT_H1, r, c, h);
+    }
+    publish();
+    // ---- z2 = h1 W2^T; h2 = relu(z2 + b2)
+    if (threadIdx.x == 0) {
+      ft_mma_kk(tmem + TM_Z, sbase + FT_H1, sbase + FT_W2, 2, ID_KK);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(trow + TM_Z + c, v);
+      uint16_t h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) h[j] = to_bf16(fmaxf(v[j] + __ldg(&b2[c + j]), 0.0f));
+      st_row16(sm + FT_H2, r, c, h);
+    }
+    publish();
+    // ---- z3 = h2 W3^T; h3 = relu(z3 + b3) (BF16); y = h3 . w4 + b4; loss; G3 = dy w4 [h3 > 0]
+    if (threadIdx.x == 0) {
+      ft_mma_kk(tmem + TM_Z, sbase + FT_H2, sbase + FT_W3, 2, ID_KK);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+    float y = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(trow + TM_Z + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        y = fmaf(from_bf16(to_bf16(fmaxf(v[j] + __ldg(&b3[c + j]), 0.0f))), from_bf16(__ldg(&A.w4[c + j])), y);
+    }
+    y += b4;
+    const float diff = y - tgt, dy = diff * A.inv_batch;
+    {
+      const float l = warp_sum_f(0.5f * diff * diff * A.inv_batch), g4 = warp_sum_f(dy);
+      if (lane == 0) {
+        atomicAdd(&acc[513], l);
+        atomicAdd(&acc[512], g4);
+      }
+    }
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16], gv[16], wv[16];
+      uint16_t gb[16];
+      tmem_ld16(trow + TM_Z + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float h = from_bf16(to_bf16(fmaxf(v[j] + __ldg(&b3[c + j]), 0.0f)));
+        const float g = h > 0.0f ? dy * from_bf16(__ldg(&A.w4[c + j])) : 0.0f;
+        gv[j] = g;
+        wv[j] = dy * h;
+        gb[j] = to_bf16(g);
+      }
+      st_row16(sm + FT_G3, r, c, gb);
+      const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
+      if (lane < 16) {
+        atomicAdd(&acc[256 + c + lane], sg);
+        atomicAdd(&acc[384 + c + lane], sw);
+      }
+    }
+    publish();
+    // ---- gW3 += G3^T h2; q2 = G3 W3
+    if (threadIdx.x == 0) {
+      ft_mma_mn(tmem + TM_GW3, sbase + FT_G3, sbase + FT_H2, ID_MN, tiles_done > 0);
+      ft_mma_kmn(tmem + TM_Z, sbase + FT_G3, sbase + FT_W3, ID_KMN);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+    // ---- G2 = q2 [h2 > 0], written over h2
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16], gv[16];
+      uint16_t hm[16], gb[16];
+      tmem_ld16(trow + TM_Z + c, v);
+      ld_row16(sm + FT_H2, r, c, hm);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        gv[j] = from_bf16(hm[j]) > 0.0f ? v[j] : 0.0f;
+        gb[j] = to_bf16(gv[j]);
+      }
+      st_row16(sm + FT_H2, r, c, gb);
+      const float sg = chunk_colsum(tbuf, gv);
+      if (lane < 16) atomicAdd(&acc[128 + c + lane], sg);
+    }
+    publish();
+    // ---- gW2 += G2^T h1; q1 = G2 W2
+    if (threadIdx.x == 0) {
+      ft_mma_mn(tmem + TM_GW2, sbase + FT_H2, sbase + FT_H1, ID_MN, tiles_done > 0);
+      ft_mma_kmn(tmem + TM_Z, sbase + FT_H2, sbase + FT_W2, ID_KMN);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+    // ---- G1 = q1 [h1 > 0], written over G3
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16], gv[16];
+      uint16_t hm[16], gb[16];
+      tmem_ld16(trow + TM_Z + c, v);
+      ld_row16(sm + FT_H1, r, c, hm);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        gv[j] = from_bf16(hm[j]) > 0.0f ? v[j] : 0.0f;
+        gb[j] = to_bf16(gv[j]);
+      }
+      st_row16(sm + FT_G3, r, c, gb);
+      const float sg = chunk_colsum(tbuf, gv);
+      if (lane < 16) atomicAdd(&acc[c + lane], sg);
+    }
+    publish();
+    // ---- gW1 += G1^T X (the next tile overwrites X and G1 only after this)
+    if (threadIdx.x == 0) {
+      ft_mma_mn(tmem + TM_GW1, sbase + FT_G3, sbase + FT_X, ID_MN48, tiles_done > 0);
+      umma_commit(bar);
+    }
+    if (!(ok = wait_mma())) break;
+    ++tiles_done;
+  }
+  if (!ok) {  // a wait ran out: let the products in flight finish (bounded) before the memory goes
+    if (threadIdx.x == 0) {
+      mbar_wait(bar, phase ^ 1u, lim);  // the phase the failed wait was waiting for
+      atomicOr(A.err, ERRB_TIMEOUT);
+    }
+    __syncthreads();
+  }
+  // ---- this CTA's partial gradients and loss
+  float *out = A.part + (size_t)blockIdx.x * (N_PARAMS + 1);
+  if (ok && tiles_done > 0) {
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(trow + TM_GW3 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[OFF_W3 + r * 128 + c + j] = v[j];
+      tmem_ld16(trow + TM_GW2 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[OFF_W2 + r * 128 + c + j] = v[j];
+    }
+#pragma unroll 1
+    for (int c = 0; c < 48; c += 16) {
+      float v[16];
+      tmem_ld16(trow + TM_GW1 + c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[OFF_W1 + r * 48 + c + j] = v[j];
+    }
+  } else {
+    for (int i = threadIdx.x; i < 128 * 128; i += blockDim.x) {
+      out[OFF_W3 + i] = 0.0f;
+      out[OFF_W2 + i] = 0.0f;
+    }
+    for (int i = threadIdx.x; i < 128 * 48; i += blockDim.x) out[OFF_W1 + i] = 0.0f;
+  }
+  __syncthreads();
+  out[OFF_B1 + r] = acc[r];
+  out[OFF_B2 + r] = acc[128 + r];
+  out[OFF_B3 + r] = acc[256 + r];
+  out[OFF_W4 + r] = acc[384 + r];
+  if (r == 0) {
+    out[OFF_B4] = acc[512];
+    out[N_PARAMS] = acc[513];
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+}
+
+// G[i] = sum over the CTAs' partials in CTA order (deterministic)
+__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > N_PARAMS) return;
+  float s = 0.0f;
+  for (int c = 0; c < n_parts; ++c) s += part[(size_t)c * (N_PARAMS + 1) + i];
+  G[i] = s;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -605,6 +986,9 @@ struct cr_trainer {
   uint16_t *wb = nullptr;  // BF16 weight copies (one block)
   float *part = nullptr;   // split-K slices of a weight gradient [max_splits][128][128]
   int max_splits = 0;
+  bool unfused = false;     // one product per launch (k_mma) instead of the fused step
+  float *part_f = nullptr;  // fused step: per-CTA partial gradients and loss [sms][N_PARAMS + 1]
+  int sms = 1;
   Bf16Copies C{};
   int64_t launches = 0;
 };
@@ -612,7 +996,7 @@ struct cr_trainer {
 static void free_trainer(cr_trainer *t) {
   if (!t) return;
   void *ptrs[] = {t->P,  t->G,   t->Mm,  t->Vv, t->tc,  t->err, t->Xb, t->XbT, t->H1, t->H2,
-                  t->H3, t->H1T, t->H2T, t->G3, t->G3T, t->G2,  t->G2T, t->G1T, t->wb, t->part};
+                  t->H3, t->H1T, t->H2T, t->G3, t->G3T, t->G2,  t->G2T, t->G1T, t->wb, t->part, t->part_f};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete t;
@@ -632,6 +1016,13 @@ extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train
   t->beta2 = cfg->beta2;
   t->eps = cfg->eps;
   t->clip = cfg->target_clip > 0.0 ? cfg->target_clip : 1e30;
+  t->unfused = cfg->unfused != 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&t->sms, cudaDevAttrMultiProcessorCount, dev);
+    t->sms = std::max(t->sms, 1);
+  }
   const size_t B = (size_t)cfg->max_batch;
   bool ok = true;
   auto al = [&](auto **p, size_t n) {
@@ -653,6 +1044,7 @@ extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train
     t->max_splits = (cfg->max_batch + ks - 1) / ks;
     al(&t->part, (size_t)t->max_splits * MLP_H * MLP_H);
   }
+  al(&t->part_f, (size_t)std::min(t->sms, cfg->max_batch / 128) * (N_PARAMS + 1));
   if (!ok) {
     free_trainer(t);
     return CR_ERR_NOMEM;
@@ -711,9 +1103,40 @@ extern "C" int cr_train_set_stream(cr_trainer *t, void *stream) {
   return CR_OK;
 }
 
+// the fused step (k_train_fused, then the CTAs' partials summed in order)
+static int train_grads_fused(cr_trainer *t, const float *X, const float *target, int B) {
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return CR_ERR_INVALID_ARG;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_train_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT_SMEM) != cudaSuccess)
+      return CR_ERR_CUDA;
+    attr = true;
+  }
+  const int grid = std::min(B / 128, t->sms);
+  FusedArgs A{};
+  A.X = X;
+  A.t = target;
+  A.B = B;
+  A.clip = (float)t->clip;
+  A.inv_batch = 1.0f / (float)B;
+  A.W1p = t->C.W1p;
+  A.W2 = t->C.W2;
+  A.W3 = t->C.W3;
+  A.w4 = t->C.w4;
+  A.P = t->P;
+  A.part = t->part_f;
+  A.err = t->err;
+  A.spin = 0;
+  k_train_fused<<<grid, FT_THREADS, FT_SMEM, t->stream>>>(A);
+  k_sum_parts<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(t->part_f, grid, t->G);
+  t->launches += 2;
+  return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
 // forward + backward of one batch into t->G (and t->loss); device inputs
 static int train_grads(cr_trainer *t, const float *X, const float *target, int B) {
   if (!t || !X || !target || B <= 0 || B % 128 || B > t->max_batch) return CR_ERR_INVALID_ARG;
+  if (!t->unfused) return train_grads_fused(t, X, target, B);
   cudaStream_t s = t->stream;
   if (cudaMemsetAsync(t->G, 0, sizeof(float) * (N_PARAMS + 1), s) != cudaSuccess) return CR_ERR_CUDA;
   k_prep<<<(B * 64 + 255) / 256, 256, 0, s>>>(X, target, B, (float)t->clip, t->Xb, t->XbT, t->tc);

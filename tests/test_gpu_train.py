@@ -5,6 +5,7 @@
     operands within FP32 accumulation error (tiles, a ragged M, a K that is not
     a multiple of the 64-wide stage, split-K accumulation, N = 48 and 128);
   * the loss and every gradient element match the reference within a bound
+    (both the fused step and the one-product-per-launch path)
     derived from where the kernels round (activations and back-propagated
     errors stored in BF16 between the products, FP32 accumulation), carried
     through the network layer by layer (_gradient_bounds);
@@ -149,12 +150,16 @@ def _gradient_bounds(p, X, t):
     return ref_loss, ref, e_loss, bnd
 
 
-def test_gradients_match_reference(env):
+@pytest.mark.parametrize("unfused", [False, True])
+def test_gradients_match_reference(env, unfused):
+    """The fused step (every product of a 128-row tile in one kernel, weight
+    gradients accumulated in tensor memory) and the one-product-per-launch
+    path both meet the derived elementwise bound."""
     torch, crmc = env
     mlp = W.random_mlp(seed=21, out_gain=1.0)
     rng = np.random.default_rng(3)
     X, t = _batch(rng, 1024)
-    tr = crmc.Trainer(mlp, max_batch=1024)
+    tr = crmc.Trainer(mlp, max_batch=1024, unfused=unfused)
     Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
     torch.cuda.synchronize()
     loss, g = tr.gradients(Xd.data_ptr(), td.data_ptr(), 1024)
@@ -271,7 +276,7 @@ def test_adam_steps_reduce_the_loss_like_the_reference(env):
     assert abs(l0 - ref_losses[0]) <= 2e-2 * ref_losses[0]
     assert l_end <= 3.0 * ref_losses[-1] + 1e-3, (l_end, ref_losses[-1])
     steps, launches = tr.stats()
-    assert steps == 150 and launches == 150 * 14
+    assert steps == 150 and launches == 150 * 4  # fused step, partial sums, Adam, BF16 copies
 
 
 def test_trained_surrogate_keeps_da_parity(env):
@@ -305,3 +310,31 @@ def test_trained_surrogate_keeps_da_parity(env):
     r2 = h.sweep_da(m, 19, log=True, features=True)
     o, lo, do, ties = compare_logs_da(w2, mlp, r2["log"], r2["da"], r2["features"], m, 19)
     compare_states(h, o, w2.n_sites)
+
+
+def test_fused_step_over_many_tiles_per_cta(env):
+    """A batch of more 128-row tiles than SMs (each CTA accumulates several
+    tiles' weight gradients in tensor memory) gives the one-product-per-launch
+    gradients within the sum of both paths' rounding (the derived bound
+    against float64, applied to each)."""
+    torch, crmc = env
+    mlp = W.random_mlp(seed=25, out_gain=1.0)
+    rng = np.random.default_rng(9)
+    B = 128 * 400
+    X, t = _batch(rng, B)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    torch.cuda.synchronize()
+    p = MO.params_from_bf16(mlp, W.bf16_to_f32)
+    Xq = W.bf16_to_f32(W.to_bf16_bits(X)).astype(np.float64)
+    ref_loss, ref, e_loss, bnd = _gradient_bounds(p, Xq, t.astype(np.float64))
+    for unfused in (False, True):
+        tr = crmc.Trainer(mlp, max_batch=B, unfused=unfused)
+        loss, g = tr.gradients(Xd.data_ptr(), td.data_ptr(), B)
+        assert abs(loss - ref_loss) <= e_loss
+        G = _split(g)
+        for name in MO.NAMES:
+            a = np.atleast_1d(np.asarray(G[name], np.float64)).ravel()
+            b = np.atleast_1d(np.asarray(ref[name], np.float64)).ravel()
+            e = np.atleast_1d(np.asarray(bnd[name], np.float64)).ravel()
+            assert np.all(np.abs(a - b) <= e), (unfused, name)
+        tr.close()
