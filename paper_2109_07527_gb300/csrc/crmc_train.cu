@@ -157,6 +157,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive FP32 accumulator columns of this thread's row, one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint16_t to_bf16(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float from_bf16(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
@@ -228,7 +244,9 @@ __global__ void __launch_bounds__(128, 1)
     k_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N, int K,
           int k_split, GemmEpi E) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array itself, so that the compiler
+  // keeps shared-memory (not generic) accesses
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sA = smem;
   uint8_t *sB = smem + GSTAGES * GM * 128;
   uint64_t *full = (uint64_t *)(sB + GSTAGES * BN * 128);
@@ -549,7 +567,7 @@ __global__ void k_adam(float *P, const float *G, float *Mm, float *Vv, int n, fl
 // block sum.  A second kernel sums the CTAs' partials in CTA order
 // (deterministic).  Every mbarrier wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int FT_THREADS = 128;
+constexpr int FT_THREADS = 256;  // two warps per tensor-memory lane quarter: columns 0-63 and 64-127
 constexpr uint32_t FT_TILE = 16384;         // one 128-row x 64-column BF16 slice
 constexpr uint32_t FT_G3 = 0;               // G3, then G1 [128 x 128] (read as MN-major operands)
 constexpr uint32_t FT_H2 = 2 * FT_TILE;     // h2, then G2 [128 x 128]
@@ -559,8 +577,10 @@ constexpr uint32_t FT_W1 = 7 * FT_TILE;     // W1 [128 out x 64 in]
 constexpr uint32_t FT_W2 = 8 * FT_TILE;     // W2 [128 x 128]
 constexpr uint32_t FT_W3 = 10 * FT_TILE;    // W3 [128 x 128]
 constexpr uint32_t FT_MISC = 12 * FT_TILE;  // column-sum tiles, accumulators, barrier, tensor-memory slot
-constexpr uint32_t FT_ACC = FT_MISC + 4 * 32 * 17 * 4;     // [4][128] gb1, gb2, gb3, gw4; [4] gb4, loss
-constexpr uint32_t FT_BAR = FT_ACC + (4 * 128 + 4) * 4;
+constexpr uint32_t FT_ACC = FT_MISC + 8 * 32 * 17 * 4;     // [4][128] gb1, gb2, gb3, gw4; [4] gb4, loss
+constexpr uint32_t FT_BIAS = FT_ACC + (4 * 128 + 4) * 4;  // [4][128] b1, b2, b3 and w4 (FP32), staged once
+constexpr uint32_t FT_YP = FT_BIAS + 4 * 128 * 4;          // [2][128] the output layer's two half sums
+constexpr uint32_t FT_BAR = FT_YP + 2 * 128 * 4;
 constexpr size_t FT_SMEM = 1024 + FT_BAR + 64;
 // tensor-memory columns: the products' accumulator, then the weight gradients
 constexpr uint32_t TM_Z = 0, TM_GW3 = 128, TM_GW2 = 256, TM_GW1 = 384;
@@ -645,13 +665,18 @@ __device__ __forceinline__ void ft_stage_weights(uint8_t *tile, const uint16_t *
 
 __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *sm = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // aligned by an offset from the shared array itself, so that the compiler
+  // keeps shared-memory (not generic) accesses
+  uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   float *tbuf_all = (float *)(sm + FT_MISC);
   float *acc = (float *)(sm + FT_ACC);  // [0..127] gb1, [128..] gb2, [256..] gb3, [384..] gw4, [512] gb4, [513] loss
+  float *yp = (float *)(sm + FT_YP);
   uint64_t *bar = (uint64_t *)(sm + FT_BAR);
   uint32_t *tmem_slot = (uint32_t *)(sm + FT_BAR + 16);
-  int *fail_s = (int *)(sm + FT_BAR + 32);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r = threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int r = quarter * 32 + lane;  // this thread's row of the tile (its tensor-memory lane)
+  const int c0 = half * 64;           // and its 64 columns
   float *tbuf = tbuf_all + warp * 32 * 17;
   const uint32_t lim = A.spin ? A.spin : SPIN_LIMIT;
   const uint32_t sbase = smem_u32(sm);
@@ -661,7 +686,6 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   for (int i = threadIdx.x; i < 4 * 128 + 4; i += blockDim.x) acc[i] = 0.0f;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    *fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -673,13 +697,20 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   ft_stage_weights(sm + FT_W1, A.W1p, 128, 64);
   ft_stage_weights(sm + FT_W2, A.W2, 128, 128);
   ft_stage_weights(sm + FT_W3, A.W3, 128, 128);
+  float *bias = (float *)(sm + FT_BIAS);  // the epilogues read these as broadcasts
+  if (threadIdx.x < 128) {
+    bias[threadIdx.x] = A.P[OFF_B1 + threadIdx.x];
+    bias[128 + threadIdx.x] = A.P[OFF_B2 + threadIdx.x];
+    bias[256 + threadIdx.x] = A.P[OFF_B3 + threadIdx.x];
+    bias[384 + threadIdx.x] = from_bf16(A.w4[threadIdx.x]);
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's lanes
-  const float *b1 = A.P + OFF_B1, *b2 = A.P + OFF_B2, *b3 = A.P + OFF_B3;
+  const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);  // this warp's lanes
+  const float *b1 = bias, *b2 = bias + 128, *b3 = bias + 256, *w4f = bias + 384;
   const float b4 = A.P[OFF_B4];
   uint32_t phase = 0;
   int tiles_done = 0;
@@ -699,6 +730,44 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     __syncthreads();
     tc_fence_after();
   };
+  // relu(z + bias) of this thread's 64 columns as BF16 into a tile
+  auto relu_out = [&](const float *bb, uint8_t *tile) {
+#pragma unroll 1
+    for (int c = c0; c < c0 + 64; c += 32) {
+      float v[32];
+      tmem_ld32(trow + TM_Z + c, v);
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        uint16_t h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[j] = to_bf16(fmaxf(v[16 * hh + j] + bb[c + 16 * hh + j], 0.0f));
+        st_row16(tile, r, c + 16 * hh, h);
+      }
+    }
+  };
+  // G = q [h > 0] of this thread's 64 columns into a tile (BF16), the FP32
+  // column sums into the bias gradient
+  auto mask_out = [&](const uint8_t *hmask, uint8_t *tile, float *gbias) {
+#pragma unroll 1
+    for (int c = c0; c < c0 + 64; c += 32) {
+      float v[32];
+      tmem_ld32(trow + TM_Z + c, v);
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float gv[16];
+        uint16_t hm[16], gb[16];
+        ld_row16(hmask, r, c + 16 * hh, hm);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          gv[j] = from_bf16(hm[j]) > 0.0f ? v[16 * hh + j] : 0.0f;
+          gb[j] = to_bf16(gv[j]);
+        }
+        st_row16(tile, r, c + 16 * hh, gb);
+        const float sg = chunk_colsum(tbuf, gv);
+        if (lane < 16) atomicAdd(&gbias[c + 16 * hh + lane], sg);
+      }
+    }
+  };
 
   const int n_tiles = A.B / 128;
   bool ok = true;
@@ -708,7 +777,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     {
       const float4 *xr = (const float4 *)(A.X + row * 48);
 #pragma unroll
-      for (int c = 0; c < 64; c += 16) {
+      for (int c = 32 * half; c < 32 * half + 32; c += 16) {
         uint16_t h[16];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -726,15 +795,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-#pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(trow + TM_Z + c, v);
-      uint16_t h[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) h[j] = to_bf16(fmaxf(v[j] + __ldg(&b1[c + j]), 0.0f));
-      st_row16(sm + FT_H1, r, c, h);
-    }
+    relu_out(b1, sm + FT_H1);
     publish();
     // ---- z2 = h1 W2^T; h2 = relu(z2 + b2)
     if (threadIdx.x == 0) {
@@ -742,15 +803,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-#pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(trow + TM_Z + c, v);
-      uint16_t h[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) h[j] = to_bf16(fmaxf(v[j] + __ldg(&b2[c + j]), 0.0f));
-      st_row16(sm + FT_H2, r, c, h);
-    }
+    relu_out(b2, sm + FT_H2);
     publish();
     // ---- z3 = h2 W3^T; h3 = relu(z3 + b3) (BF16); y = h3 . w4 + b4; loss; G3 = dy w4 [h3 > 0]
     if (threadIdx.x == 0) {
@@ -758,18 +811,21 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-    float y = 0.0f;
-#pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(trow + TM_Z + c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        y = fmaf(from_bf16(to_bf16(fmaxf(v[j] + __ldg(&b3[c + j]), 0.0f))), from_bf16(__ldg(&A.w4[c + j])), y);
-    }
-    y += b4;
-    const float diff = y - tgt, dy = diff * A.inv_batch;
     {
+      float y = 0.0f;
+#pragma unroll 1
+      for (int c = c0; c < c0 + 64; c += 32) {
+        float v[32];
+        tmem_ld32(trow + TM_Z + c, v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) y = fmaf(from_bf16(to_bf16(fmaxf(v[j] + b3[c + j], 0.0f))), w4f[c + j], y);
+      }
+      yp[half * 128 + r] = y;
+    }
+    __syncthreads();
+    const float y = (yp[r] + yp[128 + r]) + b4;
+    const float diff = y - tgt, dy = diff * A.inv_batch;
+    if (half == 0) {
       const float l = warp_sum_f(0.5f * diff * diff * A.inv_batch), g4 = warp_sum_f(dy);
       if (lane == 0) {
         atomicAdd(&acc[513], l);
@@ -777,23 +833,28 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       }
     }
 #pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16], gv[16], wv[16];
-      uint16_t gb[16];
-      tmem_ld16(trow + TM_Z + c, v);
+    for (int c = c0; c < c0 + 64; c += 32) {
+      float v[32];
+      tmem_ld32(trow + TM_Z + c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float h = from_bf16(to_bf16(fmaxf(v[j] + __ldg(&b3[c + j]), 0.0f)));
-        const float g = h > 0.0f ? dy * from_bf16(__ldg(&A.w4[c + j])) : 0.0f;
-        gv[j] = g;
-        wv[j] = dy * h;
-        gb[j] = to_bf16(g);
-      }
-      st_row16(sm + FT_G3, r, c, gb);
-      const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
-      if (lane < 16) {
-        atomicAdd(&acc[256 + c + lane], sg);
-        atomicAdd(&acc[384 + c + lane], sw);
+      for (int hh = 0; hh < 2; ++hh) {
+        float gv[16], wv[16];
+        uint16_t gb[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c + 16 * hh + j;
+          const float h = from_bf16(to_bf16(fmaxf(v[16 * hh + j] + b3[n], 0.0f)));
+          const float g = h > 0.0f ? dy * w4f[n] : 0.0f;
+          gv[j] = g;
+          wv[j] = dy * h;
+          gb[j] = to_bf16(g);
+        }
+        st_row16(sm + FT_G3, r, c + 16 * hh, gb);
+        const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
+        if (lane < 16) {
+          atomicAdd(&acc[256 + c + 16 * hh + lane], sg);
+          atomicAdd(&acc[384 + c + 16 * hh + lane], sw);
+        }
       }
     }
     publish();
@@ -804,22 +865,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-    // ---- G2 = q2 [h2 > 0], written over h2
-#pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16], gv[16];
-      uint16_t hm[16], gb[16];
-      tmem_ld16(trow + TM_Z + c, v);
-      ld_row16(sm + FT_H2, r, c, hm);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        gv[j] = from_bf16(hm[j]) > 0.0f ? v[j] : 0.0f;
-        gb[j] = to_bf16(gv[j]);
-      }
-      st_row16(sm + FT_H2, r, c, gb);
-      const float sg = chunk_colsum(tbuf, gv);
-      if (lane < 16) atomicAdd(&acc[128 + c + lane], sg);
-    }
+    mask_out(sm + FT_H2, sm + FT_H2, acc + 128);  // G2 = q2 [h2 > 0], over h2
     publish();
     // ---- gW2 += G2^T h1; q1 = G2 W2
     if (threadIdx.x == 0) {
@@ -828,22 +874,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
-    // ---- G1 = q1 [h1 > 0], written over G3
-#pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16], gv[16];
-      uint16_t hm[16], gb[16];
-      tmem_ld16(trow + TM_Z + c, v);
-      ld_row16(sm + FT_H1, r, c, hm);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        gv[j] = from_bf16(hm[j]) > 0.0f ? v[j] : 0.0f;
-        gb[j] = to_bf16(gv[j]);
-      }
-      st_row16(sm + FT_G3, r, c, gb);
-      const float sg = chunk_colsum(tbuf, gv);
-      if (lane < 16) atomicAdd(&acc[c + lane], sg);
-    }
+    mask_out(sm + FT_H1, sm + FT_G3, acc);  // G1 = q1 [h1 > 0], over G3
     publish();
     // ---- gW1 += G1^T X (the next tile overwrites X and G1 only after this)
     if (threadIdx.x == 0) {
@@ -864,21 +895,23 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   float *out = A.part + (size_t)blockIdx.x * (N_PARAMS + 1);
   if (ok && tiles_done > 0) {
 #pragma unroll 1
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(trow + TM_GW3 + c, v);
+    for (int c = c0; c < c0 + 64; c += 32) {
+      float v[32];
+      tmem_ld32(trow + TM_GW3 + c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) out[OFF_W3 + r * 128 + c + j] = v[j];
-      tmem_ld16(trow + TM_GW2 + c, v);
+      for (int j = 0; j < 32; ++j) out[OFF_W3 + r * 128 + c + j] = v[j];
+      tmem_ld32(trow + TM_GW2 + c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) out[OFF_W2 + r * 128 + c + j] = v[j];
+      for (int j = 0; j < 32; ++j) out[OFF_W2 + r * 128 + c + j] = v[j];
     }
+    if (half == 0) {
 #pragma unroll 1
-    for (int c = 0; c < 48; c += 16) {
-      float v[16];
-      tmem_ld16(trow + TM_GW1 + c, v);
+      for (int c = 0; c < 48; c += 16) {
+        float v[16];
+        tmem_ld16(trow + TM_GW1 + c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) out[OFF_W1 + r * 48 + c + j] = v[j];
+        for (int j = 0; j < 16; ++j) out[OFF_W1 + r * 48 + c + j] = v[j];
+      }
     }
   } else {
     for (int i = threadIdx.x; i < 128 * 128; i += blockDim.x) {
@@ -888,13 +921,16 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     for (int i = threadIdx.x; i < 128 * 48; i += blockDim.x) out[OFF_W1 + i] = 0.0f;
   }
   __syncthreads();
-  out[OFF_B1 + r] = acc[r];
-  out[OFF_B2 + r] = acc[128 + r];
-  out[OFF_B3 + r] = acc[256 + r];
-  out[OFF_W4 + r] = acc[384 + r];
-  if (r == 0) {
-    out[OFF_B4] = acc[512];
-    out[N_PARAMS] = acc[513];
+  if (threadIdx.x < 128) {
+    const int t = threadIdx.x;
+    out[OFF_B1 + t] = acc[t];
+    out[OFF_B2 + t] = acc[128 + t];
+    out[OFF_B3 + t] = acc[256 + t];
+    out[OFF_W4 + t] = acc[384 + t];
+    if (t == 0) {
+      out[OFF_B4] = acc[512];
+      out[N_PARAMS] = acc[513];
+    }
   }
   tc_fence_before();
   __syncthreads();
