@@ -773,18 +773,22 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   bool ok = true;
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
     const size_t row = (size_t)tile * 128 + r;
-    // ---- X (BF16, zero padded to 64) and the clipped target of this row
+    // ---- X (BF16, zero padded to 64), read as the tile's contiguous 128 x 48
+    // floats (coalesced), and the clipped target of this row
     {
-      const float4 *xr = (const float4 *)(A.X + row * 48);
+      const float4 *xt = (const float4 *)(A.X + (size_t)tile * 128 * 48);
 #pragma unroll
-      for (int c = 32 * half; c < 32 * half + 32; c += 16) {
-        uint16_t h[16];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 v = c + 4 * q < 48 ? xr[(c >> 2) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-          h[4 * q] = to_bf16(v.x); h[4 * q + 1] = to_bf16(v.y); h[4 * q + 2] = to_bf16(v.z); h[4 * q + 3] = to_bf16(v.w);
-        }
-        st_row16(sm + FT_X, r, c, h);
+      for (int q = threadIdx.x; q < 128 * 12; q += FT_THREADS) {
+        const float4 v = __ldg(&xt[q]);
+        const int xrow = q / 12, col = (q - xrow * 12) * 4;
+        const uint32_t lo = (uint32_t)to_bf16(v.x) | ((uint32_t)to_bf16(v.y) << 16),
+                       hi = (uint32_t)to_bf16(v.z) | ((uint32_t)to_bf16(v.w) << 16);
+        *(uint2 *)(sm + FT_X + sw128(xrow, col >> 3) + (col & 7) * 2) = make_uint2(lo, hi);
+      }
+      if (threadIdx.x < 128) {  // columns 48 .. 63: zero
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 6)) = z;
+        *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 7)) = z;
       }
     }
     const float tgt = fminf(fmaxf(A.t[row], -A.clip), A.clip);
@@ -891,18 +895,21 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     }
     __syncthreads();
   }
-  // ---- this CTA's partial gradients and loss
+  // ---- this CTA's partial gradients and loss: the weight gradients through
+  // shared memory (the operand tiles are free now; rows padded to 129 floats,
+  // conflict-free) and out with coalesced stores
   float *out = A.part + (size_t)blockIdx.x * (N_PARAMS + 1);
   if (ok && tiles_done > 0) {
+    float *st3 = (float *)sm, *st2 = st3 + 128 * 129, *st1 = st2 + 128 * 129;
 #pragma unroll 1
     for (int c = c0; c < c0 + 64; c += 32) {
       float v[32];
       tmem_ld32(trow + TM_GW3 + c, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) out[OFF_W3 + r * 128 + c + j] = v[j];
+      for (int j = 0; j < 32; ++j) st3[r * 129 + c + j] = v[j];
       tmem_ld32(trow + TM_GW2 + c, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) out[OFF_W2 + r * 128 + c + j] = v[j];
+      for (int j = 0; j < 32; ++j) st2[r * 129 + c + j] = v[j];
     }
     if (half == 0) {
 #pragma unroll 1
@@ -910,8 +917,18 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
         float v[16];
         tmem_ld16(trow + TM_GW1 + c, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) out[OFF_W1 + r * 48 + c + j] = v[j];
+        for (int j = 0; j < 16; ++j) st1[r * 49 + c + j] = v[j];
       }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 128 * 128; i += FT_THREADS) {
+      const int o = i >> 7, c = i & 127;
+      out[OFF_W3 + i] = st3[o * 129 + c];
+      out[OFF_W2 + i] = st2[o * 129 + c];
+    }
+    for (int i = threadIdx.x; i < 128 * 48; i += FT_THREADS) {
+      const int o = i / 48, c = i - o * 48;
+      out[OFF_W1 + i] = st1[o * 49 + c];
     }
   } else {
     for (int i = threadIdx.x; i < 128 * 128; i += blockDim.x) {
