@@ -960,8 +960,43 @@ __global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > N_PARAMS) return;
   float s = 0.0f;
-  for (int c = 0; c < n_parts; ++c) s += part[(size_t)c * (N_PARAMS + 1) + i];
+  for (int c = 0; c < n_parts; ++c) s += __ldg(&part[(size_t)c * (N_PARAMS + 1) + i]);
   G[i] = s;
+}
+
+// The step's tail in one launch: the CTAs' partials summed in CTA order, then
+// Adam on the masters (the arithmetic of k_adam) and the BF16 copies the
+// products take (those of k_weights_bf16; the zero padding of W1p is written
+// once at creation).
+__global__ void k_sum_adam(const float *__restrict__ part, int n_parts, float *G, float *P, float *Mm, float *Vv,
+                           float lr, float beta1, float beta2, float eps, float c1, float c2, Bf16Copies C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > N_PARAMS) return;
+  float g = 0.0f;
+  for (int c = 0; c < n_parts; ++c) g += __ldg(&part[(size_t)c * (N_PARAMS + 1) + i]);
+  G[i] = g;
+  if (i == N_PARAMS) return;  // the loss
+  const float m = beta1 * Mm[i] + (1.0f - beta1) * g;
+  const float v = beta2 * Vv[i] + (1.0f - beta2) * g * g;
+  Mm[i] = m;
+  Vv[i] = v;
+  const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+  P[i] = p;
+  const uint16_t b = to_bf16(p);
+  if (i < OFF_B1) {
+    const int o = (i - OFF_W1) / MLP_IN, k = (i - OFF_W1) % MLP_IN;
+    C.W1p[o * 64 + k] = b;
+  } else if (i >= OFF_W2 && i < OFF_B2) {
+    const int o = (i - OFF_W2) / MLP_H, k = (i - OFF_W2) % MLP_H;
+    C.W2[i - OFF_W2] = b;
+    C.W2T[k * MLP_H + o] = b;
+  } else if (i >= OFF_W3 && i < OFF_B3) {
+    const int o = (i - OFF_W3) / MLP_H, k = (i - OFF_W3) % MLP_H;
+    C.W3[i - OFF_W3] = b;
+    C.W3T[k * MLP_H + o] = b;
+  } else if (i >= OFF_W4 && i < OFF_B4) {
+    C.w4[i - OFF_W4] = b;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1156,8 +1191,8 @@ extern "C" int cr_train_set_stream(cr_trainer *t, void *stream) {
   return CR_OK;
 }
 
-// the fused step (k_train_fused, then the CTAs' partials summed in order)
-static int train_grads_fused(cr_trainer *t, const float *X, const float *target, int B) {
+// the fused kernel alone (per-CTA partials in t->part_f)
+static int train_fused_kernel(cr_trainer *t, const float *X, const float *target, int B) {
   if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return CR_ERR_INVALID_ARG;
   static bool attr = false;
   if (!attr) {
@@ -1181,8 +1216,16 @@ static int train_grads_fused(cr_trainer *t, const float *X, const float *target,
   A.err = t->err;
   A.spin = 0;
   k_train_fused<<<grid, FT_THREADS, FT_SMEM, t->stream>>>(A);
-  k_sum_parts<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(t->part_f, grid, t->G);
-  t->launches += 2;
+  t->launches++;
+  return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
+}
+
+// the fused step (k_train_fused, then the CTAs' partials summed in order)
+static int train_grads_fused(cr_trainer *t, const float *X, const float *target, int B) {
+  const int rc = train_fused_kernel(t, X, target, B);
+  if (rc != CR_OK) return rc;
+  k_sum_parts<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(t->part_f, std::min(B / 128, t->sms), t->G);
+  t->launches++;
   return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
 
@@ -1306,9 +1349,21 @@ static int adam_update(cr_trainer *t) {
 }
 
 extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target, int32_t batch, float *loss) {
-  int rc = train_grads(t, X, target, batch);
-  if (rc != CR_OK) return rc;
-  if ((rc = adam_update(t)) != CR_OK) return rc;
+  int rc;
+  if (t && !t->unfused) {  // the fused step, then the partials' sum, Adam and the BF16 copies in one launch
+    if (!X || !target || batch <= 0 || batch % 128 || batch > t->max_batch) return CR_ERR_INVALID_ARG;
+    if ((rc = train_fused_kernel(t, X, target, batch)) != CR_OK) return rc;
+    t->step++;
+    const double c1 = 1.0 - std::pow(t->beta1, (double)t->step), c2 = 1.0 - std::pow(t->beta2, (double)t->step);
+    k_sum_adam<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(
+        t->part_f, std::min(batch / 128, t->sms), t->G, t->P, t->Mm, t->Vv, (float)t->lr, (float)t->beta1,
+        (float)t->beta2, (float)t->eps, (float)c1, (float)c2, t->C);
+    t->launches++;
+    if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;
+  } else {
+    if ((rc = train_grads(t, X, target, batch)) != CR_OK) return rc;
+    if ((rc = adam_update(t)) != CR_OK) return rc;
+  }
   if (loss) {
     if (cudaMemcpyAsync(loss, t->loss, sizeof(float), cudaMemcpyDeviceToHost, t->stream) != cudaSuccess)
       return CR_ERR_CUDA;
