@@ -168,9 +168,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
-    def stop(self, gpu_index, t0=None, t1=None):
+    def stop(self, gpu_index, t0=None, t1=None, wait_s=2.0):
         if self.proc is None:
             return None
+        # a timed region shorter than the period may hold no sample: wait (at
+        # most wait_s) for the first one after its start
+        end = time.perf_counter() + wait_s
+        while (t0 is not None and not any(t >= t0 for t, _ in list(self.rows)) and time.perf_counter() < end
+               and self.proc.poll() is None):
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -543,7 +549,7 @@ def run_ours(args):
         batch.cycle(1, dt, gamma, 1 + s, 1000 + s)
     for g in ctxs:
         g.check()
-    clocks = ClockSampler()
+    clocks = ClockSampler(period_ms=20)
     clocks.start()
     if world > 1:
         torch.distributed.barrier()
@@ -553,7 +559,9 @@ def run_ours(args):
         batch.cycle(1, dt, gamma, 100 + s, 5000 + s)
 
     t_region0 = time.perf_counter()
+    torch.cuda.profiler.start()  # (a profiler started with capture off records the timed region only)
     ms = time_steps(step, args.steps, stream, flush)
+    torch.cuda.profiler.stop()
     t_region1 = time.perf_counter()
     if world > 1:
         torch.distributed.barrier()
