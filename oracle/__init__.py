@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "libcrmc_oracle.so")
 # trial-record flags
 F_ACC, F_NOELIG, F_EDGE, F_OVERLAP = 1, 2, 4, 8
 PLANT = {"none": 0, "drop_ion_count": 1, "dE_sign": 2, "drop_self": 3, "drop_pair_cc": 4,
-         "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7}
+         "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7, "species_count": 8}
 N_FEAT, N_HID = 48, 128
 
 
@@ -89,6 +89,8 @@ def _load():
         lib.or_chem.argtypes = [P, P]
         lib.or_set_pH.argtypes = [P, C.c_double]
         lib.or_ungroup.argtypes = [P, P]
+        lib.or_set_invocation.argtypes = [P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32]
+        lib.or_set_invocation.restype = C.c_int32
         lib.or_particles.argtypes = [P, P, P, P, P, P]
         lib.or_site_states.argtypes = [P, P]
         lib.or_energy.restype = C.c_double
@@ -211,6 +213,15 @@ class Oracle:
         """A new reservoir pH from the next trial on (chemistry recomputed)."""
         self._lib.or_set_pH(self._h, float(pH))
 
+    def set_invocation(self, cation, anion, pI_cation, pI_anion, reactions=7):
+        """Reactions of the following sweeps exchange ions of types `cation`
+        (3 X+ or 6 S+) and `anion` (4 X- or 7 S-) at the given pI; reactions:
+        bit mask acid 1, base 2, salt 4."""
+        rc = self._lib.or_set_invocation(self._h, int(cation), int(anion), float(pI_cation), float(pI_anion),
+                                         int(reactions))
+        if rc != 0:
+            raise ValueError(f"or_set_invocation rejected the arguments ({rc})")
+
     def ungroup(self):
         """Subspecies fractions of the grouped ions: p_S+, p_H+ (in X+),
         p_S-, p_OH- (in X-)."""
@@ -267,10 +278,10 @@ class Oracle:
         return out
 
     def counts(self):
-        c = np.zeros(8, dtype=np.int64)
+        c = np.zeros(10, dtype=np.int64)
         self._lib.or_counts(self._h, _ptr(c))
         return dict(n_A=int(c[0]), n_Am=int(c[1]), n_B=int(c[2]), n_Bp=int(c[3]), n_Xp=int(c[4]), n_Xm=int(c[5]),
-                    n=int(c[6]), net_charge=int(c[7]))
+                    n=int(c[6]), net_charge=int(c[7]), n_Sp=int(c[8]), n_Sm=int(c[9]))
 
     def stats(self):
         s = np.zeros(16, dtype=np.int64)

@@ -46,7 +46,16 @@
 #define OR_ERR_BOND (-6)
 #define OR_ERR_NOMEM (-8)
 
-enum { T_BEAD = 0, T_ACID = 1, T_BASE = 2, T_XP = 3, T_XM = 4, T_CORE = 5 };
+/* Particle types.  T_XP / T_XM are the grouped monovalent ions X+ / X- of
+ * Sec. II.B; T_SP / T_SM are salt ions kept apart from them (S+ / S-) when
+ * the scheme is applied separately to dissociated and salt ions, the
+ * grand-reaction ensemble of Sec. II.B and App. B.  All four interact alike
+ * (charge +-1, the ions' short-range class); only the reactions tell them
+ * apart. */
+enum { T_BEAD = 0, T_ACID = 1, T_BASE = 2, T_XP = 3, T_XM = 4, T_CORE = 5, T_SP = 6, T_SM = 7 };
+static int is_ion(int t) { return t == T_XP || t == T_XM || t == T_SP || t == T_SM; }
+/* kinds of particles for the eligibility lists and counts */
+enum { K_A0 = 0, K_A1 = 1, K_B0 = 2, K_B1 = 3, K_XP = 4, K_XM = 5, K_SP = 6, K_SM = 7, K_OTHER = 8, N_KIND = 9 };
 enum { R_ACID = 0, R_BASE = 1, R_SALT = 2 };
 enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 #define CLS_NONE 3
@@ -55,7 +64,7 @@ enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 /* Planted mistakes, used only by the tests that show the pins catch them. */
 enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
        PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5,
-       PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7 };
+       PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7, PLANT_SPECIES_COUNT = 8 };
 
 /* ----------------------------------------------------------------------- */
 /* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
@@ -128,6 +137,9 @@ typedef struct {
   double *pK;  /* per site: pKa or pKb as given */
   int *site_type; /* per site: T_ACID or T_BASE */
   int react[3], n_react;
+  /* the invocation: kinds (and types) of the cation and anion that the acid,
+   * base and salt reactions exchange with the reservoir */
+  int kxp, kxm, txp, txm;
   /* particles */
   int n, cap;
   float *x, *y, *z;
@@ -201,8 +213,8 @@ static double qeff(const Oracle *o, int t, int ionised) {
   switch (t) {
     case T_ACID: return ionised ? -1.0 : 0.0;
     case T_BASE: return ionised ? 1.0 : 0.0;
-    case T_XP: return o->ion_coupling ? 1.0 : 0.0;
-    case T_XM: return o->ion_coupling ? -1.0 : 0.0;
+    case T_XP: case T_SP: return o->ion_coupling ? 1.0 : 0.0;
+    case T_XM: case T_SM: return o->ion_coupling ? -1.0 : 0.0;
     default: return 0.0;
   }
 }
@@ -210,8 +222,8 @@ static int qnom(int t, int ionised) {
   switch (t) {
     case T_ACID: return ionised ? -1 : 0;
     case T_BASE: return ionised ? 1 : 0;
-    case T_XP: return 1;
-    case T_XM: return -1;
+    case T_XP: case T_SP: return 1;
+    case T_XM: case T_SM: return -1;
     default: return 0;
   }
 }
@@ -331,10 +343,10 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   for (int i = 0; i < p->n; ++i) {
     float X = xyz[3 * i], Y = xyz[3 * i + 1], Z = xyz[3 * i + 2];
     if (!(X >= 0.0f && X < o->Lf && Y >= 0.0f && Y < o->Lf && Z >= 0.0f && Z < o->Lf)) { or_destroy(o); return NULL; }
-    if (type[i] < 0 || type[i] > T_CORE || cls[i] < 0 || cls[i] > 3) { or_destroy(o); return NULL; }
+    if (type[i] < 0 || type[i] > T_SM || cls[i] < 0 || cls[i] > 3) { or_destroy(o); return NULL; }
     o->x[i] = X; o->y[i] = Y; o->z[i] = Z;
     o->type[i] = type[i];
-    o->cls[i] = (type[i] == T_XP || type[i] == T_XM) ? (o->ion_coupling ? o->ion_cls : CLS_NONE) : cls[i];
+    o->cls[i] = is_ion(type[i]) ? (o->ion_coupling ? o->ion_cls : CLS_NONE) : cls[i];
     o->id[i] = (uint64_t)i;
     o->site[i] = -1;
     o->st[i] = 0;
@@ -356,14 +368,14 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   if (nA > 0) o->react[o->n_react++] = R_ACID;
   if (nB > 0) o->react[o->n_react++] = R_BASE;
   o->react[o->n_react++] = R_SALT;
+  o->kxp = K_XP; o->kxm = K_XM; o->txp = T_XP; o->txm = T_XM;
   /* bonds */
   o->nb = p->n_bonds; o->K = p->fene_K; o->R0 = p->fene_R0;
   o->bi = malloc((size_t)(o->nb > 0 ? o->nb : 1) * sizeof(int));
   o->bj = malloc((size_t)(o->nb > 0 ? o->nb : 1) * sizeof(int));
   for (int b = 0; b < o->nb; ++b) {
     int i = bonds[2 * b], j = bonds[2 * b + 1];
-    if (i < 0 || j < 0 || i >= p->n || j >= p->n || type[i] == T_XP || type[i] == T_XM ||
-        type[j] == T_XP || type[j] == T_XM) { or_destroy(o); return NULL; }
+    if (i < 0 || j < 0 || i >= p->n || j >= p->n || is_ion(type[i]) || is_ion(type[j])) { or_destroy(o); return NULL; }
     o->bi[b] = i; o->bj[b] = j;
   }
   o->plant = g_plant;
@@ -470,13 +482,14 @@ static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, 
 }
 
 /* kind of a particle for the eligibility lists */
-enum { K_A0 = 0, K_A1 = 1, K_B0 = 2, K_B1 = 3, K_XP = 4, K_XM = 5, K_OTHER = 6 };
 static int kind_of(const Oracle *o, int j) {
   switch (o->type[j]) {
     case T_ACID: return o->st[j] ? K_A1 : K_A0;
     case T_BASE: return o->st[j] ? K_B1 : K_B0;
     case T_XP: return K_XP;
     case T_XM: return K_XM;
+    case T_SP: return K_SP;
+    case T_SM: return K_SM;
     default: return K_OTHER;
   }
 }
@@ -505,8 +518,8 @@ static int kth_eligible(const Oracle *o, const int off[3], int d, int kind, int6
   return buf[kth].idx;
 }
 
-static void domain_counts(const Oracle *o, const int off[3], int d, int64_t cnt[7]) {
-  for (int i = 0; i < 7; ++i) cnt[i] = 0;
+static void domain_counts(const Oracle *o, const int off[3], int d, int64_t cnt[N_KIND]) {
+  for (int i = 0; i < N_KIND; ++i) cnt[i] = 0;
   for (int j = 0; j < o->n; ++j) {
     int dom, rank;
     domain_of(o, off, o->x[j], o->y[j], o->z[j], &dom, &rank);
@@ -712,7 +725,7 @@ static void da_features(const Oracle *o, const change_t *ch, float *F) {
       if (sh < 0) continue;
       const int t = o->type[j];
       const int q = iround(qeff(o, t, o->st[j]));
-      if (t == T_XP || t == T_XM) acc[24 * s + sh] += dq * q;
+      if (is_ion(t)) acc[24 * s + sh] += dq * q;
       else if (t == T_ACID || t == T_BASE) acc[24 * s + 8 + sh] += dq * q;
       acc[24 * s + 16 + sh] += eta;
     }
@@ -761,8 +774,14 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
   t.lnu = log(unif53(P2[2], P2[3]));
   o->stats[t.move]++;
 
-  int64_t cnt[7];
+  int64_t cnt[N_KIND];
   domain_counts(o, off, d, cnt);
+  int64_t cnt_acc[N_KIND]; /* the counts the acceptance rules use */
+  memcpy(cnt_acc, cnt, sizeof cnt);
+  if (g_plant == PLANT_SPECIES_COUNT) {
+    cnt_acc[o->kxp] = cnt[K_XP] + cnt[K_SP];
+    cnt_acc[o->kxm] = cnt[K_XM] + cnt[K_SM];
+  }
   /* origin cell of the domain and the two candidate insertion points */
   int dd[3] = {d % o->nd, (d / o->nd) % o->nd, d / (o->nd * o->nd)};
   int org[3];
@@ -782,7 +801,7 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
   if (g_plant == PLANT_WRONG_VOLUME) lnz += 1.0;
   if (r == R_ACID || r == R_BASE) {
     int k0 = r == R_ACID ? K_A0 : K_B0, k1 = r == R_ACID ? K_A1 : K_B1;
-    int kx = r == R_ACID ? K_XP : K_XM;
+    int kx = r == R_ACID ? o->kxp : o->kxm;
     double qs = r == R_ACID ? -1.0 : 1.0;
     if (fwd) {
       if (cnt[k0] == 0) noelig = 1;
@@ -797,7 +816,7 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
                            o->ion_coupling ? -qs : 0.0, 0, 1};
         nch = 2;
         ln_ratio = log((double)cnt[k0]) + lnz - log((double)(cnt[k1] + 1));
-        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt[kx] + 1));
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt_acc[kx] + 1));
         ln_ratio += o->lnK[o->site[site]];
       }
     } else {
@@ -811,7 +830,7 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
                            qeff(o, o->type[ionA], 0), 0.0, 1, 0};
         nch = 2;
         ln_ratio = log((double)cnt[k1]) - log((double)(cnt[k0] + 1)) - lnz;
-        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt[kx]);
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt_acc[kx]);
         ln_ratio -= o->lnK[o->site[site]];
       }
     }
@@ -828,18 +847,18 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
       ch[1] = (change_t){-1, pb[0], pb[1], pb[2], icls, 0.0, o->ion_coupling ? -1.0 : 0.0, 0, 1};
       nch = 2;
       ln_ratio = 2.0 * lnz + o->ln_salt;
-      if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt[K_XP] + 1)) + log((double)(cnt[K_XM] + 1));
+      if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio -= log((double)(cnt_acc[o->kxp] + 1)) + log((double)(cnt_acc[o->kxm] + 1));
     } else {
-      if (cnt[K_XP] == 0 || cnt[K_XM] == 0) noelig = 1;
+      if (cnt[o->kxp] == 0 || cnt[o->kxm] == 0) noelig = 1;
       else {
-        ionA = kth_eligible(o, off, d, K_XP, pick(P0[2], cnt[K_XP]), buf);
-        ionB = kth_eligible(o, off, d, K_XM, pick(P0[3], cnt[K_XM]), buf);
+        ionA = kth_eligible(o, off, d, o->kxp, pick(P0[2], cnt[o->kxp]), buf);
+        ionB = kth_eligible(o, off, d, o->kxm, pick(P0[3], cnt[o->kxm]), buf);
         t.id_a = o->id[ionA]; t.id_b = o->id[ionB];
-        ch[0] = (change_t){ionA, o->x[ionA], o->y[ionA], o->z[ionA], o->cls[ionA], qeff(o, T_XP, 0), 0.0, 1, 0};
-        ch[1] = (change_t){ionB, o->x[ionB], o->y[ionB], o->z[ionB], o->cls[ionB], qeff(o, T_XM, 0), 0.0, 1, 0};
+        ch[0] = (change_t){ionA, o->x[ionA], o->y[ionA], o->z[ionA], o->cls[ionA], qeff(o, o->txp, 0), 0.0, 1, 0};
+        ch[1] = (change_t){ionB, o->x[ionB], o->y[ionB], o->z[ionB], o->cls[ionB], qeff(o, o->txm, 0), 0.0, 1, 0};
         nch = 2;
         ln_ratio = -2.0 * lnz - o->ln_salt;
-        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt[K_XP]) + log((double)cnt[K_XM]);
+        if (g_plant != PLANT_DROP_ION_COUNT) ln_ratio += log((double)cnt_acc[o->kxp]) + log((double)cnt_acc[o->kxm]);
       }
     }
   }
@@ -910,15 +929,15 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
     if (r == R_ACID || r == R_BASE) {
       if (fwd) {
         o->st[site] = 1;
-        if (add_ion(o, r == R_ACID ? T_XP : T_XM, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
+        if (add_ion(o, r == R_ACID ? o->txp : o->txm, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
       } else {
         o->st[site] = 0;
         remove_particle(o, ionA);
       }
     } else {
       if (fwd) {
-        if (add_ion(o, T_XP, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
-        if (add_ion(o, T_XM, pb[0], pb[1], pb[2], idB, vb)) return OR_ERR_CAPACITY;
+        if (add_ion(o, o->txp, pa[0], pa[1], pa[2], idA, va)) return OR_ERR_CAPACITY;
+        if (add_ion(o, o->txm, pb[0], pb[1], pb[2], idB, vb)) return OR_ERR_CAPACITY;
       } else {
         int hi = ionA > ionB ? ionA : ionB, lo = ionA > ionB ? ionB : ionA;
         remove_particle(o, hi);
@@ -992,15 +1011,17 @@ int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, cons
   return rc;
 }
 
-/* counts: [n_A, n_A-, n_B, n_B+, n_X+, n_X-, n, net charge] */
+/* counts: [n_A, n_A-, n_B, n_B+, n_X+, n_X-, n, net charge, n_S+, n_S-] */
 void or_counts(const Oracle *o, int64_t *out) {
-  int64_t c[8] = {0};
+  int64_t c[10] = {0};
   for (int j = 0; j < o->n; ++j) {
     switch (o->type[j]) {
       case T_ACID: c[0]++; if (o->st[j]) c[1]++; break;
       case T_BASE: c[2]++; if (o->st[j]) c[3]++; break;
       case T_XP: c[4]++; break;
       case T_XM: c[5]++; break;
+      case T_SP: c[8]++; break;
+      case T_SM: c[9]++; break;
       default: break;
     }
   }
@@ -1032,6 +1053,42 @@ void or_set_pH(Oracle *o, double pH) {
   for (int s = 0; s < o->n_sites; ++s)
     o->lnK[s] = o->site_type[s] == T_ACID ? LN10 * ((o->pH - o->pK[s]) - o->pIXp)
                                           : LN10 * ((o->pOH - o->pK[s]) - o->pIXm);
+}
+
+/* One invocation of the scheme (App. B: the method can be invoked repeatedly
+ * with different types of ions, which realises the grand-reaction ensemble;
+ * Sec. II.B: applied separately to dissociated and salt ions).  The acid,
+ * base and salt reactions of Eqs. (acid_new)-(salt_new) of the following
+ * sweeps exchange a cation of type `cation` (T_XP or T_SP) and an anion of
+ * type `anion` (T_XM or T_SM) with the reservoir, at chemical potentials
+ * pI_cation and pI_anion in place of pI_X+ and pI_X-:
+ *   K_A = 10^(pH - pKa - pI_cation), K_B = 10^(pOH - pKb - pI_anion),
+ *   K_ion = 10^(-pI_cation - pI_anion);
+ * the count n_X+- in the acceptance rules is the count of the invocation's
+ * own type (each species has its own ideal term in Eq. (QQ)).  `reactions`
+ * selects acid (1), base (2) and salt (4) moves, kept only where the system
+ * has such sites.  The pI values stay fixed through a later pH change. */
+int32_t or_set_invocation(Oracle *o, int32_t cation, int32_t anion, double pI_cation, double pI_anion,
+                          int32_t reactions) {
+  if ((cation != T_XP && cation != T_SP) || (anion != T_XM && anion != T_SM)) return OR_ERR_ARG;
+  if (!isfinite(pI_cation) || !isfinite(pI_anion) || reactions <= 0 || reactions > 7) return OR_ERR_ARG;
+  int nA = 0, nB = 0;
+  for (int s = 0; s < o->n_sites; ++s) { if (o->site_type[s] == T_ACID) nA++; else nB++; }
+  int react[3], nr = 0;
+  if ((reactions & 1) && nA > 0) react[nr++] = R_ACID;
+  if ((reactions & 2) && nB > 0) react[nr++] = R_BASE;
+  if (reactions & 4) react[nr++] = R_SALT;
+  if (nr == 0) return OR_ERR_ARG;
+  memcpy(o->react, react, sizeof react);
+  o->n_react = nr;
+  o->txp = cation; o->txm = anion;
+  o->kxp = cation == T_XP ? K_XP : K_SP;
+  o->kxm = anion == T_XM ? K_XM : K_SM;
+  o->pIX_explicit = 1;
+  o->pIXp = pI_cation;
+  o->pIXm = pI_anion;
+  or_set_pH(o, o->pH);
+  return OR_OK;
 }
 
 /* Ungrouping of the combined ions (Sec. II.D, last paragraph): a grouped

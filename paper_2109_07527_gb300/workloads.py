@@ -16,7 +16,8 @@ r_ij > 2^(1/6) sigma and no salt overlap):
 * ``config4``    -- 64 replicas, chain lengths log-uniform in [50, 1000]
 * ``config5``    -- 100 chains x 200 beads, L = 250, ~25 000 ion pairs
 
-Particle type codes (input encoding): 0 bead, 1 acid, 2 base, 3 X+, 4 X-, 5 core.
+Particle type codes (input encoding): 0 bead, 1 acid, 2 base, 3 X+, 4 X-, 5 core,
+6 S+, 7 S- (salt ions kept apart from X+- by grand-reaction invocations).
 Short-range classes: 0..2 use the WCA table; 3 has no short-range interaction.
 """
 from __future__ import annotations
@@ -25,7 +26,7 @@ import dataclasses
 import math
 import numpy as np
 
-BEAD, ACID, BASE, XP, XM, CORE = 0, 1, 2, 3, 4, 5
+BEAD, ACID, BASE, XP, XM, CORE, SP, SM = 0, 1, 2, 3, 4, 5, 6, 7
 CLS_NONE = 3
 WCA_CUT = 2.0 ** (1.0 / 6.0)
 
@@ -203,6 +204,25 @@ def ideal(n_sites=50, L=40.0, pH=5.0, pKa=5.0, pIS=2.0, n_pairs=20, seed=1, rc=1
                             pIS_minus=pIS, schedule=schedule, trials_per_domain=trials_per_domain,
                             sigma_nm=sigma_nm)
     return _assemble("ideal", [sites, ions], params, 4 * n_sites + 4096, rng, with_vel=False)
+
+
+def weak_acid_electrolyte(n_acid=500, L=100.0, pH=7.0, pKa=6.5, pIS=2.0, rc=20.0, seed=1, trials_per_domain=500,
+                          sigma_nm=0.355, alpha=0.15):
+    """The weak-acid electrolyte of the method comparison (Sec. III.A, Fig. 2):
+    n_acid individual acid groups (pKa 6.5) placed at random with every pair
+    farther apart than 2^(1/6) sigma, no free ions at the start, in a cubic
+    box of L = 50 l_B (l_B = 2 sigma = 0.71 nm), pH 7 and pI_S+- = 2 (about
+    0.01 M salt); electrostatics by DSF with r_c = 10 l_B (the paper's real-
+    space cutoff; its PPPM long-range part is replaced by the damped shifted
+    force), one domain (the global schedule: every trial sees the whole box)."""
+    rng = np.random.default_rng(seed)
+    grid = _Grid(L, 1.2)
+    sx = np.array([_place(rng, grid, L, WCA_CUT, i) for i in range(n_acid)], np.float32).reshape(-1, 3)
+    sites = (sx, np.full(n_acid, ACID, np.int32), np.zeros(n_acid, np.int32), np.zeros(n_acid, np.int8),
+             np.full(n_acid, pKa))
+    params = default_params(box_L=L, rc=rc, lB=2.0, alpha=alpha, ion_coupling=1, pH=pH, pIS_plus=pIS,
+                            pIS_minus=pIS, schedule=1, trials_per_domain=trials_per_domain, sigma_nm=sigma_nm)
+    return _assemble("weak_acid_electrolyte", [sites], params, 4096, rng, with_vel=False)
 
 
 def enum_sites(n_sites=8, L=24.0, rc=8.0, lB=2.0, pH=5.0, pKa=5.0, pIS=2.0, n_pairs=4, seed=3, n_base=0,

@@ -538,3 +538,100 @@ def test_planted_mistake_fails_energy_pin(kind):
         if rec["flags"] & oracle.F_ACC and abs((e1 - e0) - rec["dE"]) > 1e-6:
             bad += 1
     assert bad > 0
+
+
+# ---------------------------------------------------------------- grand-reaction invocations
+# Types of the four monovalent species when they are kept apart (App. B: the
+# scheme invoked repeatedly with different types of ions; Sec. II.B: applied
+# separately to dissociated and salt ions = the grand-reaction ensemble).
+H_, OH_, SP_, SM_ = W.XP, W.XM, W.SP, W.SM
+
+
+def grand_reaction_cycle(o, pH, pOH, pIS_p, pIS_m, T, seed):
+    """One cycle of the grand-reaction ensemble as four invocations: the acid
+    and salt reactions with (H+, OH-) and with (S+, S-), the mixed salt
+    reactions (H+, S-) and (S+, OH-); every reaction attempted T/2 times."""
+    tps = o.trials_per_sweep
+    for k, (c, a, pc, pa, r, n) in enumerate(((H_, OH_, pH, pOH, 5, T), (SP_, SM_, pIS_p, pIS_m, 5, T),
+                                              (H_, SM_, pH, pIS_m, 4, T // 2), (SP_, OH_, pIS_p, pOH, 4, T // 2))):
+        o.set_invocation(c, a, pc, pa, r)
+        o.sweep(max(tps, (n // tps) * tps), seed * 8 + k)
+
+
+def _grand_reaction_run(w, pH, pIS, n_sites, cycles, per_batch, seed):
+    o = oracle.Oracle(w)
+    pOH = 14.0 - pH
+    for c in range(20):
+        grand_reaction_cycle(o, pH, pOH, pIS, pIS, 256, seed + c)
+    al, fH, fOH = [], [], []
+    for b in range(cycles):
+        a = h = np_ = oh = nm = 0.0
+        for r in range(per_batch):
+            grand_reaction_cycle(o, pH, pOH, pIS, pIS, 256, seed + 1000 + b * per_batch + r)
+            k = o.counts()
+            assert k["net_charge"] == 0
+            a += k["n_Am"] / n_sites
+            h += k["n_Xp"]
+            np_ += k["n_Xp"] + k["n_Sp"]
+            oh += k["n_Xm"]
+            nm += k["n_Xm"] + k["n_Sm"]
+        al.append(a / per_batch)
+        fH.append(h / max(np_, 1.0))
+        fOH.append(oh / max(nm, 1.0))
+    return [(float(np.mean(v)), float(np.std(v, ddof=1) / math.sqrt(len(v)))) for v in (al, fH, fOH)]
+
+
+def test_grand_reaction_samples_the_grouped_distribution():
+    """Ideal acids under the four grand-reaction invocations: the degree of
+    dissociation is the grouped closed form (the H+/S+ ideal terms summed,
+    Eqs. (mux1)-(mux2)), and the fraction of H+ among the cations is
+    10^-pH / (10^-pH + 10^-pI_S+) (the ungrouping probability of Sec. III.A;
+    multinomial at fixed totals in the ideal limit)."""
+    n, L, pH, pIS, pKa, sig = 50, 40.0, 2.3, 2.0, 2.5, 0.355
+    w = W.ideal(n_sites=n, L=L, pH=pH, pKa=pKa, pIS=pIS, n_pairs=20, seed=11, schedule=1, trials_per_domain=256)
+    ln10 = math.log(10.0)
+    lnV = math.log(0.602214076 * (L * sig) ** 3)
+    pOH = 14.0 - pH
+    pIXp = -math.log10(10 ** -pH + 10 ** -pIS)
+    pIXm = -math.log10(10 ** -pOH + 10 ** -pIS)
+    a_ex = exact_alpha(n, ln10 * (pH - pKa), lnV - ln10 * pIXp, lnV - ln10 * pIXm)
+    pH_frac = 10 ** -pH / (10 ** -pH + 10 ** -pIS)
+    (a, sa), (fh, sh), (foh, soh) = _grand_reaction_run(w, pH, pIS, n, 30, 8, seed=3)
+    assert abs(a - a_ex) <= max(4.0 * sa, 0.004), (a, sa, a_ex)
+    assert abs(fh - pH_frac) <= max(4.0 * sh, 0.01), (fh, sh, pH_frac)
+    assert foh < 1e-3  # OH- at pOH 11.7 is absent from the box
+
+
+def test_rxmc_invocation_matches_its_closed_form():
+    """The RxMC special case (pI_X+ = pH, pI_X- = pOH; App. B) samples Eq.
+    (QQ) with the dissociated ions alone: the closed form with z+ = V 10^-pH
+    and z- = V 10^-pOH."""
+    n, L, pH, pKa, sig = 50, 40.0, 3.5, 3.0, 0.355
+    w = W.ideal(n_sites=n, L=L, pH=pH, pKa=pKa, pIS=2.0, n_pairs=20, seed=12, schedule=1, trials_per_domain=256)
+    o = oracle.Oracle(w)
+    o.set_invocation(H_, OH_, pH, 14.0 - pH, 7)
+    ln10 = math.log(10.0)
+    lnV = math.log(0.602214076 * (L * sig) ** 3)
+    a_ex = exact_alpha(n, ln10 * (pH - pKa), lnV - ln10 * pH, lnV - ln10 * (14.0 - pH))
+    mean, se = run_alpha(o, n, 40, 4096, seed=21, burn=40000)
+    assert abs(mean - a_ex) <= max(4.0 * se, 0.003), (mean, se, a_ex)
+
+
+def test_invocation_arguments_are_checked():
+    w = W.ideal(n_sites=5, seed=2, schedule=1, trials_per_domain=16)
+    o = oracle.Oracle(w)
+    for args in ((W.ACID, OH_, 2.0, 2.0, 7), (H_, SP_, 2.0, 2.0, 7), (H_, OH_, float("nan"), 2.0, 7),
+                 (H_, OH_, 2.0, 2.0, 0), (H_, OH_, 2.0, 2.0, 2)):  # 2: bases only, and there are none
+        with pytest.raises(ValueError):
+            o.set_invocation(*args)
+
+
+def test_planted_species_count_fails_the_grand_reaction_pin():
+    """Counting every like-charged ion (instead of the invocation's species)
+    in the acceptance rules shifts the H+ fraction off its closed form."""
+    oracle.plant("species_count")
+    n, L, pH, pIS, pKa = 50, 40.0, 2.3, 2.0, 2.5
+    w = W.ideal(n_sites=n, L=L, pH=pH, pKa=pKa, pIS=pIS, n_pairs=20, seed=11, schedule=1, trials_per_domain=256)
+    (a, sa), (fh, sh), _ = _grand_reaction_run(w, pH, pIS, n, 10, 8, seed=5)
+    pH_frac = 10 ** -pH / (10 ** -pH + 10 ** -pIS)
+    assert abs(fh - pH_frac) > 0.05, (fh, pH_frac)
