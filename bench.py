@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-da", action="store_true")
     ap.add_argument("--no-config4", action="store_true")
+    ap.add_argument("--no-fig2", action="store_true")
+    ap.add_argument("--train-only", action="store_true",
+                    help="time only the surrogate's training step (batch 32,768, synthetic features) and exit")
     return ap.parse_args()
 
 
@@ -477,6 +480,68 @@ def run_config5(crmc, torch, stream, flush, mlp, steps):
             "da_over_plain": v_da / v_plain}
 
 
+def run_method_comparison(crmc, n_rep=128, blocks=40, m=250):
+    """Sec. III.A / Fig. 2: alpha(trials) of the weak-acid electrolyte under
+    CR-MC, the grand-reaction ensemble and RxMC (the same random starts), and
+    the trials each needs to come within 5 % of CR-MC's plateau."""
+    import time
+    from paper_2109_07527_gb300 import methods
+    t0 = time.perf_counter()
+    r = methods.compare_convergence(crmc, n_rep=n_rep, blocks=blocks, m=m, seed=1)
+    plateau = float(np.mean(r["crmc"][blocks // 2:]))
+    t95 = {}
+    for k in ("crmc", "grxmc", "rxmc"):
+        a = np.asarray(r[k])
+        hit = np.flatnonzero(np.abs(a - plateau) <= 0.05 * plateau)
+        t95[k] = int(r["trials"][hit[0]]) if len(hit) else None
+    return {"workload": "500 acid groups (pKa 6.5), L = 50 l_B, pH 7, pI_S = 2, DSF r_c = 10 l_B, "
+                        "global schedule, no ions at the start",
+            "replicas_per_method": n_rep, "trials": r["trials"],
+            "alpha": {k: [round(x, 4) for x in r[k]] for k in ("crmc", "grxmc", "rxmc")},
+            "alpha_plateau_crmc": plateau,
+            "alpha_plateau_grxmc": float(np.mean(r["grxmc"][blocks // 2:])),
+            "alpha_plateau_rxmc": float(np.mean(r["rxmc"][blocks // 2:])),
+            "trials_to_within_5pct": t95, "wall_s": time.perf_counter() - t0}
+
+
+def run_train_only(args):
+    """The surrogate's training step alone, at the DA leg's batch (32,768 rows
+    of 48 integer features; the targets a fixed linear map of them), timed
+    with CUDA events after warm-up: a short program for profiling the fused
+    training kernel."""
+    import torch
+    from paper_2109_07527_gb300 import crmc, workloads as W
+    B = 32768
+    rng = np.random.default_rng(0)
+    X = rng.integers(-6, 7, (4 * B, 48)).astype(np.float32)
+    y = (0.1 * X[:, 0] - 0.05 * X[:, 8]).astype(np.float32)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    tr = crmc.Trainer(W.random_mlp(seed=6, gain=0.5), max_batch=B, lr=1e-3, target_clip=20.0)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        b = k % 4
+        tr.step(Xd.data_ptr() + b * B * 48 * 4, yd.data_ptr() + b * B * 4, B)
+
+    for k in range(max(3, args.warmup)):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tpeak, tkind = measured_tensor_peak()
+    tflops = B * TRAIN_FLOPS_PER_ROW / (ms / 1e3) / 1e12
+    print(json.dumps({"metric": "surrogate training rows/s (fused tcgen05 step, batch 32768)",
+                      "value": B / (ms / 1e3), "unit": "rows/s", "steps": args.steps, "ms_per_step": ms,
+                      "roofline": {"bound": "tensor", "achieved": tflops, "peak": tpeak, "unit": "TFLOP/s",
+                                   "frac": tflops / tpeak, "peak_source": tkind}}), flush=True)
+    tr.close()
+
+
 def run_config4(crmc, torch, stream, flush, steps):
     """The batched titration: 64 replicas, chain lengths log-uniform in
     [50, 1000], pH uniform in [2, 10], boxes at 10^-3 monomers per sigma^3
@@ -629,6 +694,9 @@ def run_ours(args):
     cfg4 = None
     if rank == 0 and not args.no_config4:
         cfg4 = run_config4(crmc, torch, stream, flush, max(10, min(args.steps, 50)))
+    fig2 = None
+    if rank == 0 and not args.no_fig2:
+        fig2 = run_method_comparison(crmc)
 
     # ---- end to end through the public API with host buffers: each step
     # uploads every replica's configuration from pinned host memory, runs the
@@ -688,7 +756,7 @@ def run_ours(args):
            "roofline": roofline, "gpu_launches": tm["launches"],
            "graph_launches_per_step": 1, "kernels_per_step": tm["launches"] / args.steps,
            "clocks": cl, "e2e": e2e, "plain": plain,
-           "surrogate_da": da, "batched_titration": cfg4,
+           "surrogate_da": da, "batched_titration": cfg4, "method_comparison": fig2,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"], alpha_o = cpu_baseline(ph_sweep_workloads(0))
@@ -702,5 +770,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.train_only:
+        run_train_only(a)
     else:
         run_ours(a)

@@ -66,6 +66,13 @@ extern "C" {
 #define CR_XP 3   /* grouped monovalent cation X+ */
 #define CR_XM 4   /* grouped monovalent anion X- */
 #define CR_CORE 5 /* neutral nanoparticle core (expanded WCA) */
+/* Salt ions kept apart from X+- (Sec. II.B: the scheme applied separately to
+ * dissociated and salt ions, the grand-reaction ensemble; App. B: the method
+ * invoked repeatedly with different types of ions).  They interact exactly as
+ * X+- (charge +-1, the ions' class); only cr_set_invocation tells them apart.
+ * Without invocations, X+ and X- play the roles of H+ and OH-. */
+#define CR_SP 6   /* salt cation S+ */
+#define CR_SM 7   /* salt anion S- */
 
 /* short-range class 3 never interacts by WCA */
 #define CR_CLS_NONE 3
@@ -186,6 +193,7 @@ typedef struct {
 typedef struct {
   int64_t n, n_A, n_Am, n_B, n_Bp, n_Xp, n_Xm, net_charge;
   double alpha;          /* n_A- / n_A (0 when there are no acids) */
+  int64_t n_Sp, n_Sm;    /* salt ions kept apart (CR_SP, CR_SM; 0 without invocations) */
   float *xyz;            /* [3n] */
   float *vel;            /* [3n] */
   float *force;          /* [3n] forces of the last cr_md_forces (zero once a sweep or step ran) */
@@ -377,6 +385,30 @@ int cr_get_timing(cr_ctx *ctx, double *ms, int64_t *launches, int64_t *launches_
  * order (trials queued before the call keep the old pH).  Batches holding the
  * context pick the change up at their next sweep.  Synchronises. */
 int cr_set_pH(cr_ctx *ctx, double pH);
+
+/* One invocation of the scheme for the following sweeps (App. B: the method
+ * can be invoked repeatedly to perform reactions with different types of
+ * ions, which realises the grand-reaction ensemble; Sec. II.B).  The acid,
+ * base and salt reactions of Eqs. (acid_new)-(salt_new) then exchange a
+ * cation of type `cation` (CR_XP or CR_SP) and an anion of type `anion`
+ * (CR_XM or CR_SM) with the reservoir at chemical potentials pI_cation and
+ * pI_anion in place of pI_X+ and pI_X-:
+ *   K_A = 10^(pH - pKa - pI_cation), K_B = 10^(pOH - pKb - pI_anion),
+ *   K_ion = 10^(-pI_cation - pI_anion);
+ * the ion counts in the acceptance rules (Eqs. (MCmetro)-(MCmetro2)) are the
+ * counts of those two types (each species has its own ideal term in Eq.
+ * (QQ)); ions of the other two types are bystanders that only interact.
+ * `reactions` is a bit mask: 1 acid, 2 base, 4 salt moves, kept where the
+ * system has such sites (the move is drawn uniformly among those kept).
+ * Examples: RxMC is (CR_XP, CR_XM, pH, pOH, 7); the grand-reaction ensemble
+ * alternates (CR_XP, CR_XM, pH, pOH, 5), (CR_SP, CR_SM, pI_S+, pI_S-, 5),
+ * (CR_XP, CR_SM, pH, pI_S-, 4), (CR_SP, CR_XM, pI_S+, pOH, 4).  The pI values
+ * stay as given through a later cr_set_pH (which recomputes K_A and K_B from
+ * them).  In stream order, like cr_set_pH; batches holding the context pick
+ * it up at their next sweep.  INVALID_ARG for other types, a non-finite pI or
+ * no reaction left.  Synchronises. */
+int cr_set_invocation(cr_ctx *ctx, int32_t cation, int32_t anion, double pI_cation, double pI_anion,
+                      uint32_t reactions);
 
 /* Ungrouping of the combined ions (Sec. II.D, last paragraph): a grouped ion
  * belongs to subspecies i with probability p_i = 10^(-pI_i + pI_X), exact in

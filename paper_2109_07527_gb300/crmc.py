@@ -55,9 +55,9 @@ class cr_sweep_stats(C.Structure):
 class cr_state_view(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_A", C.c_int64), ("n_Am", C.c_int64), ("n_B", C.c_int64),
                 ("n_Bp", C.c_int64), ("n_Xp", C.c_int64), ("n_Xm", C.c_int64), ("net_charge", C.c_int64),
-                ("alpha", C.c_double), ("xyz", C.c_void_p), ("vel", C.c_void_p), ("force", C.c_void_p),
-                ("id", C.c_void_p), ("type", C.c_void_p), ("state", C.c_void_p), ("site_state", C.c_void_p),
-                ("cls", C.c_void_p)]
+                ("alpha", C.c_double), ("n_Sp", C.c_int64), ("n_Sm", C.c_int64), ("xyz", C.c_void_p),
+                ("vel", C.c_void_p), ("force", C.c_void_p), ("id", C.c_void_p), ("type", C.c_void_p),
+                ("state", C.c_void_p), ("site_state", C.c_void_p), ("cls", C.c_void_p)]
 
 
 class cr_load_args(C.Structure):
@@ -98,7 +98,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
            "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
            "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup",
-           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle")
+           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle", "cr_set_invocation")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -191,6 +191,8 @@ def _lib():
         lib.cr_strerror.argtypes = [C.c_int]
         lib.cr_set_pH.restype = C.c_int
         lib.cr_set_pH.argtypes = [P, C.c_double]
+        lib.cr_set_invocation.restype = C.c_int
+        lib.cr_set_invocation.argtypes = [P, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint32]
         lib.cr_ungroup.restype = C.c_int
         lib.cr_ungroup.argtypes = [P, C.POINTER(cr_ungrouped)]
         lib.cr_checkpoint.restype = C.c_int
@@ -257,7 +259,7 @@ def _view(**arrays):
 
 def _view_counts(v):
     return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
-                net_charge=v.net_charge, alpha=v.alpha)
+                net_charge=v.net_charge, alpha=v.alpha, n_Sp=v.n_Sp, n_Sm=v.n_Sm)
 
 
 def _torch_stream():
@@ -432,8 +434,7 @@ class Context:
     def counts(self):
         v = cr_state_view()
         _chk(self._lib.cr_state(self._h, C.byref(v)), "cr_state")
-        return dict(n=v.n, n_A=v.n_A, n_Am=v.n_Am, n_B=v.n_B, n_Bp=v.n_Bp, n_Xp=v.n_Xp, n_Xm=v.n_Xm,
-                    net_charge=v.net_charge, alpha=v.alpha)
+        return _view_counts(v)
 
     def state_into(self, xyz=None, vel=None, id=None, type=None, state=None, site_state=None, force=None, cls=None):
         """cr_state into caller-owned host arrays (numpy arrays or raw pointers,
@@ -464,6 +465,13 @@ class Context:
     def set_pH(self, pH):
         """cr_set_pH: a new reservoir pH from the next trial on."""
         _chk(self._lib.cr_set_pH(self._h, float(pH)), "cr_set_pH")
+
+    def set_invocation(self, cation, anion, pI_cation, pI_anion, reactions=7):
+        """cr_set_invocation: the following sweeps' reactions exchange ions of
+        types `cation` (CR_XP 3 / CR_SP 6) and `anion` (CR_XM 4 / CR_SM 7) at the
+        given pI; reactions: bit mask acid 1, base 2, salt 4."""
+        _chk(self._lib.cr_set_invocation(self._h, int(cation), int(anion), float(pI_cation), float(pI_anion),
+                                         int(reactions)), "cr_set_invocation")
 
     def ungroup(self):
         """cr_ungroup: subspecies fractions of X+ / X- and their expected numbers."""

@@ -40,7 +40,7 @@ struct cr_ctx {
   SysParams *d_reps = nullptr;  // device copy of P (the phase kernel reads it)
   int64_t per_sweep = 0;
   // sizes
-  int n_input = 0, n_sites = 0, n_other = 0;
+  int n_input = 0, n_sites = 0, n_other = 0, n_acid = 0, n_base = 0;
   int64_t capacity = 0;
   // device buffers
   int *d_cnt = nullptr, *d_cnt2 = nullptr, *d_info = nullptr, *d_info2 = nullptr;
@@ -50,8 +50,8 @@ struct cr_ctx {
   long long *d_lnK = nullptr, *d_lntab = nullptr;
   long long *d_counts = nullptr;
   int *d_perm = nullptr, *d_bond_off = nullptr, *d_bond_nbr = nullptr;
-  // d_counts holds 8 words: [0..5] kind counts, [6] ions found by cr_state
-  // (an int), [7] the error word (an int), read back with one copy
+  // d_counts holds N_KIND + 2 words: [0, N_KIND) kind counts, [N_KIND] ions found by cr_state
+  // (an int), [N_KIND + 1] the error word (an int), read back with one copy
   int *d_err = nullptr, *d_counter = nullptr;
   cr_trial *d_log = nullptr;
   size_t log_cap = 0;
@@ -91,10 +91,11 @@ struct cr_ctx {
   unsigned long long *d_out_id = nullptr;
   int *d_out_type = nullptr, *d_out_cls = nullptr;
   int8_t *d_out_state = nullptr, *d_out_site = nullptr;
-  long long *h_small = nullptr;           // pinned: kind counts [6], ions found, error word
+  long long *h_small = nullptr;           // pinned: kind counts [N_KIND], ions found, error word
   // chemistry kept for cr_set_pH: reservoir, per-site pK and kind, the
   // current pH and pI_X, and a version that batches compare against
   double pH = 7.0, pIXp = 0.0, pIXm = 0.0;
+  bool inv_explicit = false;  // pI values set by cr_set_invocation (kept through pH changes)
   cr_mu_ions mu{};
   std::vector<double> site_pK;
   std::vector<char> site_is_acid;
@@ -253,7 +254,7 @@ struct Layout {
   std::vector<float4> pos, vel;
   std::vector<unsigned long long> pid;
   std::vector<int> info;
-  long long kinds[7] = {0, 0, 0, 0, 0, 0, 0};
+  long long kinds[K_OTHER + 1] = {};
   int max_occ = 0;
 };
 
@@ -288,8 +289,7 @@ static int layout_particles(const SysParams &P, int n, const float *xyz, const f
     int cl = cls[i];
     if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
     else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
-    else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
-    else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+    else if (is_ion_type(t)) { q = (float)ion_sign(t) * P.ion_q; cl = P.ion_cls; }
     Lo.pos[g] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], q);
     if (vel) Lo.vel[g] = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0f);
     Lo.pid[g] = (unsigned long long)i;
@@ -301,6 +301,8 @@ static int layout_particles(const SysParams &P, int n, const float *xyz, const f
     else if (t == CR_BASE) kd = ion ? K_B1 : K_B0;
     else if (t == CR_XP) kd = K_XP;
     else if (t == CR_XM) kd = K_XM;
+    else if (t == CR_SP) kd = K_SP;
+    else if (t == CR_SM) kd = K_SM;
     Lo.kinds[kd]++;
   }
   return CR_OK;
@@ -413,7 +415,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     const float X = sys->xyz[3 * i], Y = sys->xyz[3 * i + 1], Z = sys->xyz[3 * i + 2];
     if (!(X >= 0.0f && X < Lf && Y >= 0.0f && Y < Lf && Z >= 0.0f && Z < Lf)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
     const int t = sys->type[i];
-    if (t < CR_BEAD || t > CR_CORE || sys->cls[i] < 0 || sys->cls[i] > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    if (t < CR_BEAD || t > CR_SM || sys->cls[i] < 0 || sys->cls[i] > 3) { free_ctx(c); return CR_ERR_INVALID_ARG; }
     if (t == CR_ACID || t == CR_BASE) {
       site_of[i] = (int)lnK.size();
       c->site_pK.push_back(pK[i]);
@@ -422,8 +424,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
       else { lnK.push_back(LN10 * ((pOH - pK[i]) - pIXm)); nB++; }
       const int ion = sys->state[i] ? 1 : 0;
       qsum += ion ? (t == CR_ACID ? -1 : 1) : 0;
-    } else if (t == CR_XP) qsum += 1;
-    else if (t == CR_XM) qsum -= 1;
+    } else if (is_ion_type(t)) qsum += ion_sign(t);
   }
   if ((int)lnK.size() >= MAX_SITES) { free_ctx(c); return CR_ERR_INVALID_ARG; }
   if (qsum != 0) { free_ctx(c); return CR_ERR_NOT_NEUTRAL; }
@@ -431,6 +432,12 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   if (nA > 0) P.react[P.n_react++] = R_ACID;
   if (nB > 0) P.react[P.n_react++] = R_BASE;
   P.react[P.n_react++] = R_SALT;
+  P.kxp = K_XP;
+  P.kxm = K_XM;
+  P.txp = CR_XP;
+  P.txm = CR_XM;
+  c->n_acid = nA;
+  c->n_base = nB;
   c->n_input = n;
   c->n_sites = (int)lnK.size();
   c->capacity = sys->capacity;
@@ -451,7 +458,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   c->init_type.assign(sys->type, sys->type + n);
   c->init_site = site_of;
   for (int i = 0; i < n; ++i)
-    if (sys->type[i] != CR_XP && sys->type[i] != CR_XM) c->n_fixed_end = i + 1;
+    if (!is_ion_type(sys->type[i])) c->n_fixed_end = i + 1;
   c->n_other = (int)kinds[K_OTHER];
 
   // ---- bonds (CSR by permanent particle)
@@ -462,7 +469,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
     const int i = sys->bonds[2 * b], j = sys->bonds[2 * b + 1];
     if (i < 0 || j < 0 || i >= n || j >= n || i == j) { free_ctx(c); return CR_ERR_INVALID_ARG; }
     const int ti = sys->type[i], tj = sys->type[j];
-    if (ti == CR_XP || ti == CR_XM || tj == CR_XP || tj == CR_XM) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    if (is_ion_type(ti) || is_ion_type(tj)) { free_ctx(c); return CR_ERR_INVALID_ARG; }
     deg[i + 1]++;
     deg[j + 1]++;
   }
@@ -586,7 +593,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_stats, 16);
   ALLOC(c->d_lnK, std::max<size_t>(lnK.size(), 1));
   ALLOC(c->d_lntab, P.lnmax);
-  ALLOC(c->d_counts, 8);
+  ALLOC(c->d_counts, N_KIND + 2);
   ALLOC(c->d_perm, std::max(n, 1));
   ALLOC(c->d_bond_off, n + 1);
   ALLOC(c->d_bond_nbr, std::max(2 * nb, 1));
@@ -664,11 +671,11 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_perm, h_perm.data(), (size_t)std::max(n, 1));
   COPY(c->d_bond_off, deg.data(), (size_t)n + 1);
   COPY(c->d_bond_nbr, nbr.data(), nbr.size());
-  c->d_counter = (int *)(c->d_counts + 6);
-  c->d_err = (int *)(c->d_counts + 7);
-  cudaMemset(c->d_counts, 0, sizeof(long long) * 8);
+  c->d_counter = (int *)(c->d_counts + N_KIND);
+  c->d_err = (int *)(c->d_counts + N_KIND + 1);
+  cudaMemset(c->d_counts, 0, sizeof(long long) * (N_KIND + 2));
   cudaMemset(c->d_present, 0, sizeof(int) * (size_t)std::max(n, 1));
-  COPY(c->d_counts, kinds, (size_t)6);
+  COPY(c->d_counts, kinds, (size_t)N_KIND);
   if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
   if (n > 0) COPY(c->d_init_type, sys->type, (size_t)n);
 #undef COPY
@@ -716,13 +723,10 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   return CR_OK;
 }
 
-extern "C" int cr_set_pH(cr_ctx *ctx, double pH) {
-  if (!ctx || !std::isfinite(pH)) return CR_ERR_INVALID_ARG;
-  const cr_mu_ions &mu = ctx->mu;
-  const double pOH = mu.pKw - pH;
-  double pIXp, pIXm;
-  if (mu.pIX_explicit) { pIXp = mu.pIX_plus; pIXm = mu.pIX_minus; }
-  else { pIXp = pIX_of(mu.pI_S_plus, pH, pOH); pIXm = pIX_of(mu.pI_S_minus, pH, pOH); }
+// the chemistry of the following trials: K_A, K_B per site and K_ion from
+// pH and the pI of the exchanged cation and anion, in stream order
+static int apply_chem(cr_ctx *ctx, double pH, double pIXp, double pIXm) {
+  const double pOH = ctx->mu.pKw - pH;
   const size_t ns = ctx->site_pK.size();
   ctx->h_lnK_fx.resize(ns);
   for (size_t i = 0; i < ns; ++i)
@@ -739,6 +743,38 @@ extern "C" int cr_set_pH(cr_ctx *ctx, double pH) {
   ctx->pIXm = pIXm;
   ctx->chem_version++;
   return CR_OK;
+}
+
+extern "C" int cr_set_pH(cr_ctx *ctx, double pH) {
+  if (!ctx || !std::isfinite(pH)) return CR_ERR_INVALID_ARG;
+  const cr_mu_ions &mu = ctx->mu;
+  const double pOH = mu.pKw - pH;
+  double pIXp, pIXm;
+  if (ctx->inv_explicit) { pIXp = ctx->pIXp; pIXm = ctx->pIXm; }
+  else if (mu.pIX_explicit) { pIXp = mu.pIX_plus; pIXm = mu.pIX_minus; }
+  else { pIXp = pIX_of(mu.pI_S_plus, pH, pOH); pIXm = pIX_of(mu.pI_S_minus, pH, pOH); }
+  return apply_chem(ctx, pH, pIXp, pIXm);
+}
+
+extern "C" int cr_set_invocation(cr_ctx *ctx, int32_t cation, int32_t anion, double pI_cation, double pI_anion,
+                                 uint32_t reactions) {
+  if (!ctx || (cation != CR_XP && cation != CR_SP) || (anion != CR_XM && anion != CR_SM)) return CR_ERR_INVALID_ARG;
+  if (!std::isfinite(pI_cation) || !std::isfinite(pI_anion) || reactions == 0 || reactions > 7)
+    return CR_ERR_INVALID_ARG;
+  SysParams &P = ctx->P;
+  int react[3], nr = 0;
+  if ((reactions & 1u) && ctx->n_acid > 0) react[nr++] = R_ACID;
+  if ((reactions & 2u) && ctx->n_base > 0) react[nr++] = R_BASE;
+  if (reactions & 4u) react[nr++] = R_SALT;
+  if (nr == 0) return CR_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i) P.react[i] = i < nr ? react[i] : 0;
+  P.n_react = nr;
+  P.txp = cation;
+  P.txm = anion;
+  P.kxp = cation == CR_XP ? K_XP : K_SP;
+  P.kxm = anion == CR_XM ? K_XM : K_SM;
+  ctx->inv_explicit = true;
+  return apply_chem(ctx, ctx->pH, pI_cation, pI_anion);
 }
 
 extern "C" int cr_ungroup(cr_ctx *ctx, cr_ungrouped *out) {
@@ -785,7 +821,7 @@ extern "C" int cr_get_info(const cr_ctx *ctx, cr_info *out) {
 
 extern "C" int cr_check(cr_ctx *ctx) {
   if (!ctx) return CR_ERR_INVALID_ARG;
-  int *bits = (int *)(ctx->h_small + 7);  // pinned
+  int *bits = (int *)(ctx->h_small + N_KIND + 1);  // pinned
   CR_CUDA(cudaMemcpyAsync(bits, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CR_CUDA(cudaStreamSynchronize(ctx->stream));
   return err_bits_to_code(*bits);
@@ -1128,7 +1164,7 @@ static int ion_end_bit(const cr_ctx *ctx) {
 // the counts of the view and queues the ordering and one copy per array.
 static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, StateBufs &B, bool &want,
                        bool integrator_forces = false) {
-  long long *hs = ctx->h_small;  // pinned: [0..5] kind counts, [6] ions found, [7] error word
+  long long *hs = ctx->h_small;  // pinned: [0, N_KIND) kind counts, [N_KIND] ions found, [N_KIND + 1] error word
   want = out->xyz || out->vel || out->force || out->id || out->type || out->state || out->site_state || out->cls;
   B = StateBufs{};
   B.n_input = ctx->n_input;
@@ -1159,21 +1195,23 @@ static int state_begin(cr_ctx *ctx, const cr_state_view *out, cudaStream_t s, St
     ctx->launches_total++;
   }
   // kind counts, ions found and the error word: adjacent, one copy
-  CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, 8 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  CR_CUDA(cudaMemcpyAsync(hs, ctx->d_counts, (N_KIND + 2) * sizeof(long long), cudaMemcpyDeviceToHost, s));
   return CR_OK;
 }
 
 static int state_arrays(cr_ctx *ctx, cr_state_view *out, cudaStream_t s, const StateBufs &B, bool want) {
   const long long *hs = ctx->h_small;
-  const int n_ions = *(const int *)(hs + 6), bits = *(const int *)(hs + 7);
+  const int n_ions = *(const int *)(hs + N_KIND), bits = *(const int *)(hs + N_KIND + 1);
   out->n_A = hs[K_A0] + hs[K_A1];
   out->n_Am = hs[K_A1];
   out->n_B = hs[K_B0] + hs[K_B1];
   out->n_Bp = hs[K_B1];
   out->n_Xp = hs[K_XP];
   out->n_Xm = hs[K_XM];
-  out->n = out->n_A + out->n_B + out->n_Xp + out->n_Xm + ctx->n_other;
-  out->net_charge = out->n_Xp - out->n_Xm - out->n_Am + out->n_Bp;
+  out->n_Sp = hs[K_SP];
+  out->n_Sm = hs[K_SM];
+  out->n = out->n_A + out->n_B + out->n_Xp + out->n_Xm + out->n_Sp + out->n_Sm + ctx->n_other;
+  out->net_charge = out->n_Xp + out->n_Sp - out->n_Xm - out->n_Sm - out->n_Am + out->n_Bp;
   out->alpha = out->n_A > 0 ? (double)out->n_Am / (double)out->n_A : 0.0;
   const int err0 = err_bits_to_code(bits);
   if (!want) return err0;
@@ -1264,7 +1302,7 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
   }
-  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * 6, s));
+  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * N_KIND, s));
   LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
              ctx->d_in_state, n, ctx->n_input, ctx->d_init_type};
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1299,7 +1337,7 @@ extern "C" int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float 
       }
     }
     for (int i = 0; i < ctx->n_input; ++i)
-      if (!seen[i] && ctx->init_type[i] != CR_XP && ctx->init_type[i] != CR_XM) return CR_ERR_INVALID_ARG;
+      if (!seen[i] && !is_ion_type(ctx->init_type[i])) return CR_ERR_INVALID_ARG;
     std::sort(ions.begin(), ions.end());
     if (std::adjacent_find(ions.begin(), ions.end()) != ions.end()) return CR_ERR_INVALID_ARG;
   }
@@ -1317,7 +1355,7 @@ extern "C" int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float 
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_cls, cls, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     CR_CUDA(cudaMemcpyAsync(ctx->d_in_state, state, sizeof(int8_t) * n, cudaMemcpyHostToDevice, s));
   }
-  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * 6, s));
+  CR_CUDA(cudaMemsetAsync(ctx->d_counts, 0, sizeof(long long) * N_KIND, s));
   LoadBufs I{ctx->d_in_xyz, vel ? ctx->d_in_vel : nullptr, ctx->d_in_type, ctx->d_in_cls, ctx->d_site_map,
              ctx->d_in_state, n, ctx->n_input, ctx->d_init_type, ctx->d_in_id, with_f ? ctx->d_in_frc : nullptr};
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1631,6 +1669,8 @@ extern "C" void cr_batch_destroy(cr_batch *b) {
   delete b;
 }
 
+static int batch_refresh_chem(cr_batch *b);
+
 // one persistent sweep launch of every replica (words zeroed first)
 static int batch_launch_persistent(cr_batch *b, const PhaseShape &SS, int T, int R, bool da, uint32_t swc,
                                    uint32_t sweep0, uint32_t k0, uint32_t k1, int withhold = -1,
@@ -1679,16 +1719,9 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
     if (changed)
       CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice, s));
   }
-  {  // a context's pH changed (cr_set_pH): its copy in the batch follows
-    bool changed = false;
-    for (int r = 0; r < n; ++r)
-      if (b->chem_seen[r] != b->ctx[r]->chem_version) {
-        b->reps[r].lnsalt_fx = b->ctx[r]->P.lnsalt_fx;
-        b->chem_seen[r] = b->ctx[r]->chem_version;
-        changed = true;
-      }
-    if (changed)
-      CR_CUDA(cudaMemcpyAsync(b->d_reps, b->reps.data(), sizeof(SysParams) * n, cudaMemcpyHostToDevice, s));
+  {  // a context's chemistry changed: its copy in the batch follows
+    const int rc = batch_refresh_chem(b);
+    if (rc != CR_OK) return rc;
   }
   const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const uint32_t sweep0 = (uint32_t)c0->sweep;
@@ -1834,13 +1867,22 @@ extern "C" int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t se
   return batch_md(b, [&](cr_ctx *c, uint64_t r) { return cr_md_end(c, dt, gamma, seed ^ (r << 32)); });
 }
 
-// a context's pH changed (cr_set_pH): its copy in the batch follows
+// a context's chemistry changed (cr_set_pH, cr_set_invocation): its copy in
+// the batch follows (the per-site constants are the context's own array)
 static int batch_refresh_chem(cr_batch *b) {
   bool changed = false;
   const int n = (int)b->ctx.size();
   for (int r = 0; r < n; ++r)
     if (b->chem_seen[r] != b->ctx[r]->chem_version) {
-      b->reps[r].lnsalt_fx = b->ctx[r]->P.lnsalt_fx;
+      const SysParams &Pc = b->ctx[r]->P;
+      SysParams &Pb = b->reps[r];
+      Pb.lnsalt_fx = Pc.lnsalt_fx;
+      Pb.n_react = Pc.n_react;
+      for (int i = 0; i < 3; ++i) Pb.react[i] = Pc.react[i];
+      Pb.kxp = Pc.kxp;
+      Pb.kxm = Pc.kxm;
+      Pb.txp = Pc.txp;
+      Pb.txm = Pc.txm;
       b->chem_seen[r] = b->ctx[r]->chem_version;
       changed = true;
     }

@@ -15,8 +15,17 @@
 
 namespace crmc {
 
-enum Kind { K_A0 = 0, K_A1 = 1, K_B0 = 2, K_B1 = 3, K_XP = 4, K_XM = 5, K_OTHER = 6 };
+// kinds of slots: site states, the grouped ions X+- and the salt ions S+-
+// kept apart from them (grand-reaction invocations); K_OTHER is never counted
+enum Kind { K_A0 = 0, K_A1 = 1, K_B0 = 2, K_B1 = 3, K_XP = 4, K_XM = 5, K_SP = 6, K_SM = 7, K_OTHER = 8 };
+constexpr int N_KIND = 8;  // counted kinds
+// per-CTA counters of a phase: [0] list size, [1 + kind] kind counts (kinds
+// 0..K_OTHER), [MISC_INIT + kind] the counted kinds' values at the start
+constexpr int MISC_INIT = 10, MISC_N = 20;
 enum Reaction { R_ACID = 0, R_BASE = 1, R_SALT = 2 };
+// free monovalent ions: the grouped X+- and the salt ions S+- (same interactions)
+__host__ __device__ inline bool is_ion_type(int t) { return t == CR_XP || t == CR_XM || t == CR_SP || t == CR_SM; }
+__host__ __device__ inline int ion_sign(int t) { return (t == CR_XP || t == CR_SP) ? 1 : -1; }
 
 constexpr int INFO_TYPE_MASK = 15;
 constexpr int INFO_CLS_SHIFT = 4;
@@ -64,6 +73,10 @@ struct SysParams {
   long long lnz1_fx, lnsalt_fx, lBself_fx;
   int n_react;
   int react[3];
+  // the invocation: kinds and types of the cation and anion that the
+  // reactions exchange with the reservoir (K_XP / CR_XP or K_SP / CR_SP, and
+  // K_XM / CR_XM or K_SM / CR_SM)
+  int kxp, kxm, txp, txm;
   const long long *lnK_fx;    // per site
   const long long *lntab_fx;  // ln(i) for 0 < i < lnmax
   int lnmax;
@@ -83,7 +96,7 @@ struct SysParams {
   int dcap_glob;        // entries per CTA region (k^3 * cap + 2 m)
   // bookkeeping
   unsigned long long *stats;  // [16]: attempts[6], accepts[6], no-elig, edge, overlap, trials
-  long long *counts;          // [6] global counts per kind K_A0..K_XM
+  long long *counts;          // [N_KIND] global counts per kind K_A0..K_SM
   int *err;                   // error bits
   cr_trial *log;              // trial records (device) or null
   long long per_sweep;        // trials per sweep (log indexing)

@@ -87,10 +87,11 @@ __device__ __forceinline__ long long fix24(float v) {
 __device__ __forceinline__ int kind_of(int info) {
   const int t = info & INFO_TYPE_MASK;
   const int ion = (info >> 6) & 1;
-  // (type, ionised) -> kind; table nibbles for index 2*type + ionised
-  const unsigned long long tab = 0x665544321066ull;
+  // (type, ionised) -> kind; table nibbles for index 2*type + ionised, types
+  // bead, acid, base, X+, X-, core, S+, S-
+  const unsigned long long tab = 0x7766885544321088ull;
   const int idx = 2 * t + ion;
-  return idx < 12 ? (int)((tab >> (4 * idx)) & 15ull) : K_OTHER;
+  return idx < 16 ? (int)((tab >> (4 * idx)) & 15ull) : K_OTHER;
 }
 
 

@@ -387,7 +387,7 @@ __global__ void k_rebuild_sort(SysParams P, RebuildBufs B, int *perm_slot, int n
 // the loaded configuration must be neutral (kind counts of the load)
 __global__ void k_load_neutral(SysParams P) {
   if (threadIdx.x != 0) return;
-  const long long q = P.counts[K_XP] - P.counts[K_XM] - P.counts[K_A1] + P.counts[K_B1];
+  const long long q = P.counts[K_XP] + P.counts[K_SP] - P.counts[K_XM] - P.counts[K_SM] - P.counts[K_A1] + P.counts[K_B1];
   if (q != 0) atomicOr(P.err, ERRB_NOT_NEUTRAL);
 }
 
@@ -401,9 +401,9 @@ __device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs
   const unsigned long long pid = I.id ? I.id[i] : (unsigned long long)i;
   {  // the particle must be valid and a bonded / site particle of cr_init must keep its id and type
     const int ti = pid < (unsigned long long)I.n_site_map ? I.init_type[pid] : CR_XP;
-    const bool fixed = ti != CR_XP && ti != CR_XM;
-    const bool ok = t >= CR_BEAD && t <= CR_CORE && I.cls[i] >= 0 && I.cls[i] <= 3 && x >= 0.0f && x < P.Lf &&
-                    y >= 0.0f && y < P.Lf && z >= 0.0f && z < P.Lf && (fixed ? t == ti : (t == CR_XP || t == CR_XM));
+    const bool fixed = !is_ion_type(ti);
+    const bool ok = t >= CR_BEAD && t <= CR_SM && I.cls[i] >= 0 && I.cls[i] <= 3 && x >= 0.0f && x < P.Lf &&
+                    y >= 0.0f && y < P.Lf && z >= 0.0f && z < P.Lf && (fixed ? t == ti : is_ion_type(t));
     if (!ok) {
       atomicOr(P.err, ERRB_ARG);
       return;
@@ -414,12 +414,11 @@ __device__ __forceinline__ void load_particle(const SysParams &P, const LoadBufs
   int cl = I.cls[i];
   if (t == CR_ACID) q = ion ? -1.0f : 0.0f;
   else if (t == CR_BASE) q = ion ? 1.0f : 0.0f;
-  else if (t == CR_XP) { q = P.ion_q; cl = P.ion_cls; }
-  else if (t == CR_XM) { q = -P.ion_q; cl = P.ion_cls; }
+  else if (is_ion_type(t)) { q = (float)ion_sign(t) * P.ion_q; cl = P.ion_cls; }
   {  // global kind counts (zeroed by the host before the launch)
     const int kd = t == CR_ACID ? (ion ? K_A1 : K_A0)
                    : t == CR_BASE ? (ion ? K_B1 : K_B0)
-                   : t == CR_XP ? K_XP : (t == CR_XM ? K_XM : K_OTHER);
+                   : t == CR_XP ? K_XP : t == CR_XM ? K_XM : t == CR_SP ? K_SP : t == CR_SM ? K_SM : K_OTHER;
     if (kd < K_OTHER) atomicAdd((unsigned long long *)&P.counts[kd], 1ull);
   }
   const int site = (pid < (unsigned long long)I.n_site_map && I.site[pid] >= 0) ? I.site[pid] : 0;
@@ -445,7 +444,7 @@ __global__ void k_load_scatter(SysParams P, LoadBufs I, RebuildBufs B) {
 // Loads of every replica of a batch (blockIdx.y = replica): counts zeroed,
 // particles placed, cells sorted, neutrality checked, one launch per step.
 __global__ void k_load_zero_batch(const SysParams *__restrict__ reps) {
-  if (threadIdx.x < 6) reps[blockIdx.x].counts[threadIdx.x] = 0;
+  if (threadIdx.x < N_KIND) reps[blockIdx.x].counts[threadIdx.x] = 0;
 }
 __global__ void k_load_scatter_batch(const SysParams *__restrict__ reps, const LoadJob *__restrict__ jobs) {
   const LoadJob &J = jobs[blockIdx.y];
@@ -458,7 +457,7 @@ __global__ void k_rebuild_sort_batch(const SysParams *__restrict__ reps, const L
 __global__ void k_load_neutral_batch(const SysParams *__restrict__ reps) {
   if (threadIdx.x != 0) return;
   const SysParams &P = reps[blockIdx.x];
-  const long long q = P.counts[K_XP] - P.counts[K_XM] - P.counts[K_A1] + P.counts[K_B1];
+  const long long q = P.counts[K_XP] + P.counts[K_SP] - P.counts[K_XM] - P.counts[K_SM] - P.counts[K_A1] + P.counts[K_B1];
   if (q != 0) atomicOr(P.err, ERRB_NOT_NEUTRAL);
 }
 

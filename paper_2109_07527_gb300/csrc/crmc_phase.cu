@@ -648,7 +648,7 @@ __device__ __forceinline__ void select_trial(const SysParams &P, const DomList &
   int pa_o = 0, pa_n = 0, pb_o = 0, pb_n = 0;
   if (r == R_ACID || r == R_BASE) {
     const int kn = r == R_ACID ? K_A0 : K_B0, ki = r == R_ACID ? K_A1 : K_B1;
-    const int kx = r == R_ACID ? K_XP : K_XM;
+    const int kx = r == R_ACID ? P.kxp : P.kxm;
     const float qs = r == R_ACID ? -1.0f : 1.0f;
     const int n0 = misc[1 + kn], n1 = misc[1 + ki], nx = misc[1 + kx];
     if (fwd) {
@@ -691,7 +691,7 @@ __device__ __forceinline__ void select_trial(const SysParams &P, const DomList &
       }
     }
   } else {
-    const int nxp = misc[1 + K_XP], nxm = misc[1 + K_XM];
+    const int nxp = misc[1 + P.kxp], nxm = misc[1 + P.kxm];
     if (fwd) {
       if (q.rankA < 0 || q.rankB < 0) flags |= CR_TRIAL_EDGE;
       id_a = newid;
@@ -706,8 +706,8 @@ __device__ __forceinline__ void select_trial(const SysParams &P, const DomList &
     } else {
       if (nxp == 0 || nxm == 0) flags |= CR_TRIAL_NO_ELIGIBLE;
       else {
-        ionA = warp_kth(L.info, n, K_XP, pick32(q.w2, nxp));
-        ionB = warp_kth(L.info, n, K_XM, pick32(q.w3, nxm));
+        ionA = warp_kth(L.info, n, P.kxp, pick32(q.w2, nxp));
+        ionB = warp_kth(L.info, n, P.kxm, pick32(q.w3, nxm));
         if (ionA < 0 || ionB < 0) { ionA = max(ionA, 0); ionB = max(ionB, 0); bad = true; }
         id_a = L.id[ionA];
         id_b = L.id[ionB];
@@ -962,7 +962,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
         L.vel[p] = vel[0];
         L.id[p] = C.newid;
         L.lnk[p] = 0;
-        L.info[p] = (r == R_ACID ? CR_XP : CR_XM) | (P.ion_cls << INFO_CLS_SHIFT);
+        L.info[p] = (r == R_ACID ? P.txp : P.txm) | (P.ion_cls << INFO_CLS_SHIFT);
         L.rank[p] = q.rankA;
       }
       n += 1;
@@ -971,7 +971,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
       n -= 1;
     }
     if (lane == 0) {
-      const int kn = r == R_ACID ? K_A0 : K_B0, ki = kn + 1, kx = r == R_ACID ? K_XP : K_XM;
+      const int kn = r == R_ACID ? K_A0 : K_B0, ki = kn + 1, kx = r == R_ACID ? P.kxp : P.kxm;
       const int dlt = fwd ? 1 : -1;
       misc[1 + kn] -= dlt;
       misc[1 + ki] += dlt;
@@ -986,7 +986,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
         L.vel[p] = vel[0];
         L.id[p] = C.newid;
         L.lnk[p] = 0;
-        L.info[p] = CR_XP | (P.ion_cls << INFO_CLS_SHIFT);
+        L.info[p] = P.txp | (P.ion_cls << INFO_CLS_SHIFT);
         L.rank[p] = q.rankA;
       }
       __syncwarp();
@@ -1000,7 +1000,7 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
         L.vel[p] = vel[1];
         L.id[p] = C.newid + 1u;
         L.lnk[p] = 0;
-        L.info[p] = CR_XM | (P.ion_cls << INFO_CLS_SHIFT);
+        L.info[p] = P.txm | (P.ion_cls << INFO_CLS_SHIFT);
         L.rank[p] = q.rankB;
       }
       n += 1;
@@ -1013,8 +1013,8 @@ __device__ __forceinline__ int commit_trial(const SysParams &P, const DomList &L
     }
     if (lane == 0) {
       const int dlt = fwd ? 1 : -1;
-      misc[1 + K_XP] += dlt;
-      misc[1 + K_XM] += dlt;
+      misc[1 + P.kxp] += dlt;
+      misc[1 + P.kxm] += dlt;
     }
   }
   __syncwarp();
@@ -1076,7 +1076,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
   float *qbuf = (float *)take(sizeof(float) * 2 * QCAP * NW);
   int *redov = (int *)take(sizeof(int) * MAX_WARPS);
   int *scan_tmp = (int *)take(sizeof(int) * 32);
-  int *misc = (int *)take(sizeof(int) * 16);  // [0] list size, [1..7] kind counts, [9..15] at start
+  int *misc = (int *)take(sizeof(int) * MISC_N);  // [0] list size, [1 + kind] counts, [MISC_INIT + kind] at start
   int *hcnt = (int *)take(sizeof(int) * (S.nr3 + 1));
   int *hcell = (int *)take(sizeof(int) * (S.nr3 + 1));
   int *hpre = (int *)take(sizeof(int) * (S.nr3 + 1));
@@ -1153,10 +1153,8 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
     hcnt[i] = c;
     hcell[i] = cell;
   }
-  if (tid < 16) {
-    misc[tid] = 0;
-    st[tid] = 0ull;
-  }
+  if (tid < MISC_N) misc[tid] = 0;
+  if (tid < 16) st[tid] = 0ull;
   __syncthreads();
   block_scan(dcnt, KC, dpre, scan_tmp);
   block_scan(hcnt, NR, hpre, scan_tmp);
@@ -1191,7 +1189,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
     L.lnk[j] = (t == CR_ACID || t == CR_BASE) ? P.lnK_fx[info >> INFO_SITE_SHIFT] : 0ll;
     L.info[j] = info;
     L.rank[j] = r;
-    atomicAdd(&misc[1 + min(kind_of(info), 6)], 1);
+    atomicAdd(&misc[1 + min(kind_of(info), (int)K_OTHER)], 1);
   }
   // flat frame (frame_x): a region spanning less than half the box along
   // every axis is compared without minimum-image tests; strad marks the
@@ -1241,7 +1239,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
         const int g = cell * P.cap + sl;
         const int t = P.info[g] & INFO_TYPE_MASK;
         const int q = __float2int_rn(P.pos[g].w);
-        if (t == CR_XP || t == CR_XM) qi += q;
+        if (is_ion_type(t)) qi += q;
         else if (t == CR_ACID || t == CR_BASE) qs += q;
       }
       aQi[i] = qi;
@@ -1251,7 +1249,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
   }
   if (tid == 0) misc[0] = ND;
   __syncthreads();
-  if (tid < 7) misc[9 + tid] = misc[1 + tid];
+  if (tid < N_KIND) misc[MISC_INIT + tid] = misc[1 + tid];
   const int cc_thread = NW > 1 ? 32 : 0;  // the thread that adds the changed-pair term
   const long long log_dom = (long long)(sweep - sweep0) * P.per_sweep + (long long)colour * P.nact * m +
                             (long long)bdom * m;
@@ -1506,8 +1504,9 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
     if (id < (unsigned long long)P.n_perm) P.perm_slot[id] = g;
   }
   if (tid < 16 && st[tid]) atomicAdd(&P.stats[tid], st[tid]);
-  if (tid < 6 && misc[1 + tid] != misc[9 + tid])
-    atomicAdd((unsigned long long *)&P.counts[tid], (unsigned long long)(long long)(misc[1 + tid] - misc[9 + tid]));
+  if (tid < N_KIND && misc[1 + tid] != misc[MISC_INIT + tid])
+    atomicAdd((unsigned long long *)&P.counts[tid],
+              (unsigned long long)(long long)(misc[1 + tid] - misc[MISC_INIT + tid]));
 }
 
 // ---------------------------------------------------------------------------
@@ -1795,7 +1794,7 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
                           sizeof(float) * 2 * QCAP * (threads / 32),
                           sizeof(int) * MAX_WARPS,
                           sizeof(int) * 32,
-                          sizeof(int) * 16,
+                          sizeof(int) * MISC_N,
                           sizeof(int) * (S.nr3 + 1),
                           sizeof(int) * (S.nr3 + 1),
                           sizeof(int) * (S.nr3 + 1),

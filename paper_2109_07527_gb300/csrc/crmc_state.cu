@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(ORDER_THREADS) k_state_order_batch(const SysPa
   const SysParams &P = reps[r];
   const StateBufs &B = bufs[r];
   const long long *cn = B.counts;
-  const long long n = cn[K_A0] + cn[K_A1] + cn[K_B0] + cn[K_B1] + cn[K_XP] + cn[K_XM] + B.n_other;
+  const long long n = cn[K_A0] + cn[K_A1] + cn[K_B0] + cn[K_B1] + cn[K_XP] + cn[K_XM] + cn[K_SP] + cn[K_SM] + B.n_other;
   const int n_ions = *B.n_ions;
   const long long n_present = n - n_ions;
   const bool ok = n_ions >= 0 && n_ions <= STATE_BLOCK_SORT_MAX && n <= B.cap && n_present >= 0 &&

@@ -86,7 +86,7 @@ def compare_states(g, o, n_sites):
     assert np.array_equal(sg["state"], so["state"])
     assert np.array_equal(sg["site_state"], o.site_states(n_sites))
     co = o.counts()
-    for k in ("n", "n_Am", "n_Bp", "n_Xp", "n_Xm"):
+    for k in ("n", "n_Am", "n_Bp", "n_Xp", "n_Xm", "n_Sp", "n_Sm"):
         assert sg[k] == co[k], (k, sg[k], co[k])
     assert sg["net_charge"] == 0
     return sg, so
