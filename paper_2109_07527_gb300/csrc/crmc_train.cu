@@ -581,9 +581,13 @@ constexpr uint32_t FT_ACC = FT_MISC + 8 * 32 * 17 * 4;     // [4][128] gb1, gb2,
 constexpr uint32_t FT_BIAS = FT_ACC + (4 * 128 + 4) * 4;  // [4][128] b1, b2, b3 and w4 (FP32), staged once
 constexpr uint32_t FT_YP = FT_BIAS + 4 * 128 * 4;          // [2][128] the output layer's two half sums
 constexpr uint32_t FT_BAR = FT_YP + 2 * 128 * 4;
-constexpr size_t FT_SMEM = 1024 + FT_BAR + 64;
-// tensor-memory columns: the products' accumulator, then the weight gradients
-constexpr uint32_t TM_Z = 0, TM_GW3 = 128, TM_GW2 = 256, TM_GW1 = 384;
+constexpr uint32_t FT_ONES = (FT_BAR + 64 + 1023) / 1024 * 1024;  // [16 x 64] BF16 ones (a K-major B operand)
+constexpr size_t FT_SMEM = 1024 + FT_ONES + 2048;
+// tensor-memory columns: the products' accumulator, the weight gradients and
+// the bias gradients (G^T 1: 16 equal columns each)
+constexpr uint32_t TM_Z = 0, TM_GW3 = 128, TM_GW2 = 256, TM_GW1 = 384, TM_GB3 = 432, TM_GB2 = 448, TM_GB1 = 464;
+// per-CTA partials: the parameters' gradients and the loss, padded to 16 bytes
+constexpr int PART_STRIDE = (N_PARAMS + 1 + 3) / 4 * 4;
 
 // byte offset of 16-byte chunk j (of 8) of row r in a K-major 128-byte-swizzled slice
 __device__ __forceinline__ uint32_t sw128(int r, int j) {
@@ -624,46 +628,59 @@ __device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr) {
 }
 constexpr uint32_t IDESC_TA = 1u << 15, IDESC_TB = 1u << 16;  // A / B MN-major
 
-// D = A B^T with both K-major (K = 64 * kslices), by thread 0
-__device__ __forceinline__ void ft_mma_kk(uint32_t d, uint32_t a, uint32_t b, int kslices, uint32_t idesc) {
-  for (int kk = 0; kk < 4 * kslices; ++kk)
-    umma_bf16(d, sdesc_sw128(a + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32),
-              sdesc_sw128(b + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32), idesc, kk ? 1u : 0u);
+// A descriptor moved on by a byte offset (the start-address field holds
+// address >> 4 and stays below its 14-bit limit inside shared memory), so
+// that the unrolled issue loops below add constants to two base descriptors
+// instead of building each descriptor anew.
+__device__ __forceinline__ uint64_t dmove(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+// byte offset of K step kk (16 elements) in a K-major tile of 64-column slices
+__host__ __device__ constexpr uint32_t kstep(int kk) { return (uint32_t)(kk >> 2) * FT_TILE + (uint32_t)(kk & 3) * 32; }
+
+// D = A B^T with both K-major (K = 64 * KS), by thread 0
+template <int KS>
+__device__ __forceinline__ void ft_mma_kk(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc) {
+  const uint64_t da = sdesc_sw128(a), db = sdesc_sw128(b);
+#pragma unroll
+  for (int kk = 0; kk < 4 * KS; ++kk) umma_bf16(d, dmove(da, kstep(kk)), dmove(db, kstep(kk)), idesc, kk ? 1u : 0u);
 }
 // D (+)= A^T B over the tile's 128 rows (K = stored rows; A and B MN-major views)
 __device__ __forceinline__ void ft_mma_mn(uint32_t d, uint32_t a, uint32_t b, uint32_t idesc, bool acc) {
-  for (int kk = 0; kk < 8; ++kk)
-    umma_bf16(d, sdesc_mn128(a + kk * 2048), sdesc_mn128(b + kk * 2048), idesc, (acc || kk) ? 1u : 0u);
+  const uint64_t da = sdesc_mn128(a), db = sdesc_mn128(b);
+  const uint32_t acc0 = acc ? 1u : 0u;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) umma_bf16(d, dmove(da, kk * 2048), dmove(db, kk * 2048), idesc, kk ? 1u : acc0);
 }
 // D = A W with A K-major (K = W's stored rows) and W read as an MN-major operand
 __device__ __forceinline__ void ft_mma_kmn(uint32_t d, uint32_t a, uint32_t w, uint32_t idesc) {
-  for (int kk = 0; kk < 8; ++kk)
-    umma_bf16(d, sdesc_sw128(a + (uint32_t)(kk >> 2) * FT_TILE + (kk & 3) * 32), sdesc_mn128(w + kk * 2048), idesc,
-              kk ? 1u : 0u);
+  const uint64_t da = sdesc_sw128(a), dw = sdesc_mn128(w);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) umma_bf16(d, dmove(da, kstep(kk)), dmove(dw, kk * 2048), idesc, kk ? 1u : 0u);
+}
+
+// D (+)= G^T 1 over the tile's 128 rows: the column sums of G (MN-major view)
+// into 16 equal accumulator columns; the ones operand is uniform, so every
+// K step reads the same 64-element block
+__device__ __forceinline__ void ft_mma_colsum(uint32_t d, uint32_t g, uint32_t ones, uint32_t idesc, bool acc) {
+  const uint64_t dg = sdesc_mn128(g), d1 = sdesc_sw128(ones);
+  const uint32_t acc0 = acc ? 1u : 0u;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) umma_bf16(d, dmove(dg, kk * 2048), dmove(d1, (kk & 3) * 32), idesc, kk ? 1u : acc0);
 }
 
 struct FusedArgs {
   const float *X, *t;  // [B][48] features, [B] targets
   int B;
   float clip, inv_batch;
-  const uint16_t *W1p, *W2, *W3, *w4;  // BF16 copies of the masters
+  const uint16_t *w4;                  // BF16 copy of the output weights (the others come by TMA)
   const float *P;                      // FP32 masters (biases)
-  float *part;                         // [gridDim.x][N_PARAMS + 1] partial gradients and loss
+  float *part;                         // [gridDim.x][PART_STRIDE] partial gradients and loss
   int *err;
   uint32_t spin;
 };
 
-// rows of a [rows x cols] BF16 matrix in global memory into a swizzled tile
-__device__ __forceinline__ void ft_stage_weights(uint8_t *tile, const uint16_t *W, int rows, int cols) {
-  const int chunks = cols / 8;  // 16-byte chunks per row
-  for (int i = threadIdx.x; i < rows * chunks; i += blockDim.x) {
-    const int r = i / chunks, c = i % chunks;
-    const uint4 v = *(const uint4 *)(W + (size_t)r * cols + c * 8);
-    *(uint4 *)(tile + (uint32_t)(c >> 3) * FT_TILE + sw128(r, c & 7)) = v;
-  }
-}
-
-__global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
+__global__ void __launch_bounds__(FT_THREADS, 1)
+    k_train_fused(const __grid_constant__ CUtensorMap mW1, const __grid_constant__ CUtensorMap mW2,
+                  const __grid_constant__ CUtensorMap mW3, FusedArgs A) {
   extern __shared__ uint8_t smem_raw[];
   // aligned by an offset from the shared array itself, so that the compiler
   // keeps shared-memory (not generic) accesses
@@ -671,8 +688,11 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   float *tbuf_all = (float *)(sm + FT_MISC);
   float *acc = (float *)(sm + FT_ACC);  // [0..127] gb1, [128..] gb2, [256..] gb3, [384..] gw4, [512] gb4, [513] loss
   float *yp = (float *)(sm + FT_YP);
-  uint64_t *bar = (uint64_t *)(sm + FT_BAR);
+  uint64_t *bar = (uint64_t *)(sm + FT_BAR);        // the products' commits
+  uint64_t *wbar = (uint64_t *)(sm + FT_BAR + 8);   // the weights' copies
   uint32_t *tmem_slot = (uint32_t *)(sm + FT_BAR + 16);
+  uint64_t *bar2 = (uint64_t *)(sm + FT_BAR + 24);  // the weight-gradient products of a backward stage
+  uint64_t *dbar = (uint64_t *)(sm + FT_BAR + 32);  // the drain after an expired wait
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;
   const int r = quarter * 32 + lane;  // this thread's row of the tile (its tensor-memory lane)
@@ -681,12 +701,24 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   const uint32_t lim = A.spin ? A.spin : SPIN_LIMIT;
   const uint32_t sbase = smem_u32(sm);
   constexpr uint32_t ID_KK = idesc_bf16(128, 128), ID_MN = idesc_bf16(128, 128) | IDESC_TA | IDESC_TB,
-                     ID_MN48 = idesc_bf16(128, 48) | IDESC_TA | IDESC_TB, ID_KMN = idesc_bf16(128, 128) | IDESC_TB;
+                     ID_MN48 = idesc_bf16(128, 48) | IDESC_TA | IDESC_TB, ID_KMN = idesc_bf16(128, 128) | IDESC_TB,
+                     ID_ONES = idesc_bf16(128, 16) | IDESC_TA;
 
   for (int i = threadIdx.x; i < 4 * 128 + 4; i += blockDim.x) acc[i] = 0.0f;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
+    mbar_init(wbar, 1);
+    mbar_init(bar2, 1);
+    mbar_init(dbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the BF16 weights by TMA, 128-row x 64-column boxes in the 128-byte
+    // swizzle (the K-major operand layout), while the rest is set up
+    mbar_expect_tx(wbar, 5 * FT_TILE);
+    tma_load_2d(&mW1, wbar, sm + FT_W1, 0, 0);
+    tma_load_2d(&mW2, wbar, sm + FT_W2, 0, 0);
+    tma_load_2d(&mW2, wbar, sm + FT_W2 + FT_TILE, 64, 0);
+    tma_load_2d(&mW3, wbar, sm + FT_W3, 0, 0);
+    tma_load_2d(&mW3, wbar, sm + FT_W3 + FT_TILE, 64, 0);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -694,9 +726,8 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  ft_stage_weights(sm + FT_W1, A.W1p, 128, 64);
-  ft_stage_weights(sm + FT_W2, A.W2, 128, 128);
-  ft_stage_weights(sm + FT_W3, A.W3, 128, 128);
+  for (int i = threadIdx.x; i < 2048 / 16; i += blockDim.x)
+    *(uint4 *)(sm + FT_ONES + 16 * i) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
   float *bias = (float *)(sm + FT_BIAS);  // the epilogues read these as broadcasts
   if (threadIdx.x < 128) {
     bias[threadIdx.x] = A.P[OFF_B1 + threadIdx.x];
@@ -714,11 +745,28 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
   const float b4 = A.P[OFF_B4];
   uint32_t phase = 0;
   int tiles_done = 0;
+  // the weights have landed (bounded wait; on expiry a second bounded wait
+  // for the copies still in flight, then no tile is run)
+  bool wok = mbar_wait(wbar, 0, lim);
+  wok = __syncthreads_or(!wok) == 0;
+  if (!wok && threadIdx.x == 0) {
+    mbar_wait(wbar, 0, lim);
+    atomicOr(A.err, ERRB_TIMEOUT);
+  }
 
-  // every thread: wait for the last commit (bounded); false when it ran out
+  // every thread: wait for the last commit on bar (bounded); false when it ran out
   auto wait_mma = [&]() -> bool {
     const bool ok = mbar_wait(bar, phase, lim);
     phase ^= 1u;
+    const int f = __syncthreads_or(!ok);
+    tc_fence_after();
+    return f == 0;
+  };
+  // the same for the commits on bar2
+  uint32_t phase2 = 0;
+  auto wait_mma2 = [&]() -> bool {
+    const bool ok = mbar_wait(bar2, phase2, lim);
+    phase2 ^= 1u;
     const int f = __syncthreads_or(!ok);
     tc_fence_after();
     return f == 0;
@@ -745,57 +793,61 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       }
     }
   };
-  // G = q [h > 0] of this thread's 64 columns into a tile (BF16), the FP32
-  // column sums into the bias gradient
-  auto mask_out = [&](const uint8_t *hmask, uint8_t *tile, float *gbias) {
+  // G = q [h > 0] of this thread's 64 columns into a tile (BF16; its column
+  // sums, the bias gradient, are taken on the tensor cores)
+  auto mask_out = [&](const uint8_t *hmask, uint8_t *tile) {
 #pragma unroll 1
     for (int c = c0; c < c0 + 64; c += 32) {
       float v[32];
       tmem_ld32(trow + TM_Z + c, v);
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        float gv[16];
         uint16_t hm[16], gb[16];
         ld_row16(hmask, r, c + 16 * hh, hm);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          gv[j] = from_bf16(hm[j]) > 0.0f ? v[16 * hh + j] : 0.0f;
-          gb[j] = to_bf16(gv[j]);
-        }
+        for (int j = 0; j < 16; ++j) gb[j] = to_bf16(from_bf16(hm[j]) > 0.0f ? v[16 * hh + j] : 0.0f);
         st_row16(tile, r, c + 16 * hh, gb);
-        const float sg = chunk_colsum(tbuf, gv);
-        if (lane < 16) atomicAdd(&gbias[c + 16 * hh + lane], sg);
       }
     }
   };
 
   const int n_tiles = A.B / 128;
   bool ok = true;
-  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    const size_t row = (size_t)tile * 128 + r;
-    // ---- X (BF16, zero padded to 64), read as the tile's contiguous 128 x 48
-    // floats (coalesced), and the clipped target of this row
-    {
-      const float4 *xt = (const float4 *)(A.X + (size_t)tile * 128 * 48);
+  // X of the next tile (its 128 x 48 floats, contiguous, coalesced) and this
+  // thread's row target, loaded into registers one tile ahead
+  constexpr int XQ = 128 * 12 / FT_THREADS;
+  static_assert(128 * 12 % FT_THREADS == 0, "X tile split");
+  float4 xn[XQ];
+  float tn = 0.0f;
+  auto load_x = [&](int t) {
+    const float4 *xt = (const float4 *)(A.X + (size_t)t * 128 * 48);
 #pragma unroll
-      for (int q = threadIdx.x; q < 128 * 12; q += FT_THREADS) {
-        const float4 v = __ldg(&xt[q]);
-        const int xrow = q / 12, col = (q - xrow * 12) * 4;
-        const uint32_t lo = (uint32_t)to_bf16(v.x) | ((uint32_t)to_bf16(v.y) << 16),
-                       hi = (uint32_t)to_bf16(v.z) | ((uint32_t)to_bf16(v.w) << 16);
-        *(uint2 *)(sm + FT_X + sw128(xrow, col >> 3) + (col & 7) * 2) = make_uint2(lo, hi);
-      }
-      if (threadIdx.x < 128) {  // columns 48 .. 63: zero
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 6)) = z;
-        *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 7)) = z;
-      }
+    for (int k = 0; k < XQ; ++k) xn[k] = __ldg(&xt[threadIdx.x + k * FT_THREADS]);
+    tn = __ldg(&A.t[(size_t)t * 128 + r]);
+  };
+  if (blockIdx.x < n_tiles) load_x(blockIdx.x);
+  for (int tile = blockIdx.x; tile < n_tiles && ok && wok; tile += gridDim.x) {
+    // ---- X (BF16, zero padded to 64) into its tile, and the clipped target
+#pragma unroll
+    for (int k = 0; k < XQ; ++k) {
+      const int q = threadIdx.x + k * FT_THREADS;
+      const float4 v = xn[k];
+      const int xrow = q / 12, col = (q - xrow * 12) * 4;
+      const uint32_t lo = (uint32_t)to_bf16(v.x) | ((uint32_t)to_bf16(v.y) << 16),
+                     hi = (uint32_t)to_bf16(v.z) | ((uint32_t)to_bf16(v.w) << 16);
+      *(uint2 *)(sm + FT_X + sw128(xrow, col >> 3) + (col & 7) * 2) = make_uint2(lo, hi);
     }
-    const float tgt = fminf(fmaxf(A.t[row], -A.clip), A.clip);
+    if (threadIdx.x < 128) {  // columns 48 .. 63: zero
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 6)) = z;
+      *(uint4 *)(sm + FT_X + sw128(threadIdx.x, 7)) = z;
+    }
+    const float tgt = fminf(fmaxf(tn, -A.clip), A.clip);
     publish();
+    if (tile + (int)gridDim.x < n_tiles) load_x(tile + (int)gridDim.x);  // lands while this tile runs
     // ---- z1 = X W1^T; h1 = relu(z1 + b1)
     if (threadIdx.x == 0) {
-      ft_mma_kk(tmem + TM_Z, sbase + FT_X, sbase + FT_W1, 1, ID_KK);
+      ft_mma_kk<1>(tmem + TM_Z, sbase + FT_X, sbase + FT_W1, ID_KK);
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
@@ -803,7 +855,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     publish();
     // ---- z2 = h1 W2^T; h2 = relu(z2 + b2)
     if (threadIdx.x == 0) {
-      ft_mma_kk(tmem + TM_Z, sbase + FT_H1, sbase + FT_W2, 2, ID_KK);
+      ft_mma_kk<2>(tmem + TM_Z, sbase + FT_H1, sbase + FT_W2, ID_KK);
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
@@ -811,7 +863,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     publish();
     // ---- z3 = h2 W3^T; h3 = relu(z3 + b3) (BF16); y = h3 . w4 + b4; loss; G3 = dy w4 [h3 > 0]
     if (threadIdx.x == 0) {
-      ft_mma_kk(tmem + TM_Z, sbase + FT_H2, sbase + FT_W3, 2, ID_KK);
+      ft_mma_kk<2>(tmem + TM_Z, sbase + FT_H2, sbase + FT_W3, ID_KK);
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
@@ -842,74 +894,109 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
       tmem_ld32(trow + TM_Z + c, v);
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        float gv[16], wv[16];
+        float wv[16];
         uint16_t gb[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = c + 16 * hh + j;
           const float h = from_bf16(to_bf16(fmaxf(v[16 * hh + j] + b3[n], 0.0f)));
-          const float g = h > 0.0f ? dy * w4f[n] : 0.0f;
-          gv[j] = g;
           wv[j] = dy * h;
-          gb[j] = to_bf16(g);
+          gb[j] = to_bf16(h > 0.0f ? dy * w4f[n] : 0.0f);
         }
         st_row16(sm + FT_G3, r, c + 16 * hh, gb);
-        const float sg = chunk_colsum(tbuf, gv), sw = chunk_colsum(tbuf, wv);
-        if (lane < 16) {
-          atomicAdd(&acc[256 + c + 16 * hh + lane], sg);
-          atomicAdd(&acc[384 + c + 16 * hh + lane], sw);
-        }
+        const float sw = chunk_colsum(tbuf, wv);
+        if (lane < 16) atomicAdd(&acc[384 + c + 16 * hh + lane], sw);
       }
     }
     publish();
-    // ---- gW3 += G3^T h2; q2 = G3 W3
+    // ---- q2 = G3 W3 (committed first), then gW3 += G3^T h2 and gb3 += G3^T 1,
+    // which run while the threads form G2 = q2 [h2 > 0] in registers; G2
+    // replaces h2 once those products have read it
     if (threadIdx.x == 0) {
-      ft_mma_mn(tmem + TM_GW3, sbase + FT_G3, sbase + FT_H2, ID_MN, tiles_done > 0);
       ft_mma_kmn(tmem + TM_Z, sbase + FT_G3, sbase + FT_W3, ID_KMN);
       umma_commit(bar);
+      ft_mma_mn(tmem + TM_GW3, sbase + FT_G3, sbase + FT_H2, ID_MN, tiles_done > 0);
+      ft_mma_colsum(tmem + TM_GB3, sbase + FT_G3, sbase + FT_ONES, ID_ONES, tiles_done > 0);
+      umma_commit(bar2);
     }
     if (!(ok = wait_mma())) break;
-    mask_out(sm + FT_H2, sm + FT_H2, acc + 128);  // G2 = q2 [h2 > 0], over h2
+    {
+      uint32_t g2[32];  // this thread's 64 columns of G2, BF16 pairs
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc) {
+        float v[32];
+        tmem_ld32(trow + TM_Z + c0 + 32 * cc, v);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint16_t hm[16];
+          ld_row16(sm + FT_H2, r, c0 + 32 * cc + 16 * hh, hm);
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const uint32_t lo = to_bf16(from_bf16(hm[j]) > 0.0f ? v[16 * hh + j] : 0.0f),
+                           hi = to_bf16(from_bf16(hm[j + 1]) > 0.0f ? v[16 * hh + j + 1] : 0.0f);
+            g2[16 * cc + 8 * hh + j / 2] = lo | (hi << 16);
+          }
+        }
+      }
+      if (!(ok = wait_mma2())) break;  // gW3 and gb3 have read h2
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint8_t *sl = sm + FT_H2 + (uint32_t)(c0 >> 6) * FT_TILE;
+        const int j = 2 * q;  // 16-byte chunks j, j + 1 of the row's 64-column slice
+        *(uint4 *)(sl + sw128(r, j)) = make_uint4(g2[8 * q], g2[8 * q + 1], g2[8 * q + 2], g2[8 * q + 3]);
+        *(uint4 *)(sl + sw128(r, j + 1)) = make_uint4(g2[8 * q + 4], g2[8 * q + 5], g2[8 * q + 6], g2[8 * q + 7]);
+      }
+    }
     publish();
-    // ---- gW2 += G2^T h1; q1 = G2 W2
+    // ---- q1 = G2 W2 (committed first), then gW2 += G2^T h1 and gb2 += G2^T 1,
+    // which run while the threads form G1 = q1 [h1 > 0] over G3 (free: the
+    // products that read G3 are done)
     if (threadIdx.x == 0) {
-      ft_mma_mn(tmem + TM_GW2, sbase + FT_H2, sbase + FT_H1, ID_MN, tiles_done > 0);
       ft_mma_kmn(tmem + TM_Z, sbase + FT_H2, sbase + FT_W2, ID_KMN);
       umma_commit(bar);
+      ft_mma_mn(tmem + TM_GW2, sbase + FT_H2, sbase + FT_H1, ID_MN, tiles_done > 0);
+      ft_mma_colsum(tmem + TM_GB2, sbase + FT_H2, sbase + FT_ONES, ID_ONES, tiles_done > 0);
+      umma_commit(bar2);
     }
     if (!(ok = wait_mma())) break;
-    mask_out(sm + FT_H1, sm + FT_G3, acc);  // G1 = q1 [h1 > 0], over G3
+    mask_out(sm + FT_H1, sm + FT_G3);
     publish();
-    // ---- gW1 += G1^T X (the next tile overwrites X and G1 only after this)
+    // ---- gW1 += G1^T X, gb1 += G1^T 1 (the next tile overwrites X, G1, h1 and
+    // G2 only after this; the products complete in issue order)
     if (threadIdx.x == 0) {
       ft_mma_mn(tmem + TM_GW1, sbase + FT_G3, sbase + FT_X, ID_MN48, tiles_done > 0);
+      ft_mma_colsum(tmem + TM_GB1, sbase + FT_G3, sbase + FT_ONES, ID_ONES, tiles_done > 0);
       umma_commit(bar);
     }
     if (!(ok = wait_mma())) break;
+    if (!(ok = wait_mma2())) break;  // gW2's commit (complete by now)
     ++tiles_done;
   }
   if (!ok) {  // a wait ran out: let the products in flight finish (bounded) before the memory goes
     if (threadIdx.x == 0) {
-      mbar_wait(bar, phase ^ 1u, lim);  // the phase the failed wait was waiting for
+      umma_commit(dbar);  // arrives once every product this thread issued is done
+      mbar_wait(dbar, 0, lim);
       atomicOr(A.err, ERRB_TIMEOUT);
     }
     __syncthreads();
   }
   // ---- this CTA's partial gradients and loss: the weight gradients through
-  // shared memory (the operand tiles are free now; rows padded to 129 floats,
-  // conflict-free) and out with coalesced stores
-  float *out = A.part + (size_t)blockIdx.x * (N_PARAMS + 1);
-  if (ok && tiles_done > 0) {
-    float *st3 = (float *)sm, *st2 = st3 + 128 * 129, *st1 = st2 + 128 * 129;
+  // shared memory (the operand tiles are free now; rows padded to 132 floats,
+  // 16-byte stores and loads without bank conflicts) and out with coalesced
+  // 16-byte stores; the bias gradients from their accumulator columns
+  float *out = A.part + (size_t)blockIdx.x * PART_STRIDE;
+  if (ok && wok && tiles_done > 0) {
+    constexpr int LD = 132;
+    float *st3 = (float *)sm, *st2 = st3 + 128 * LD, *st1 = st2 + 128 * LD;
 #pragma unroll 1
     for (int c = c0; c < c0 + 64; c += 32) {
       float v[32];
       tmem_ld32(trow + TM_GW3 + c, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) st3[r * 129 + c + j] = v[j];
+      for (int j = 0; j < 32; j += 4) *(float4 *)&st3[r * LD + c + j] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       tmem_ld32(trow + TM_GW2 + c, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) st2[r * 129 + c + j] = v[j];
+      for (int j = 0; j < 32; j += 4) *(float4 *)&st2[r * LD + c + j] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
     }
     if (half == 0) {
 #pragma unroll 1
@@ -917,18 +1004,26 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
         float v[16];
         tmem_ld16(trow + TM_GW1 + c, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) st1[r * 49 + c + j] = v[j];
+        for (int j = 0; j < 16; j += 4) *(float4 *)&st1[r * LD + c + j] = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
       }
+    } else {  // the bias gradients: column 0 of each accumulator, row r = unit r
+      float v[16];
+      tmem_ld16(trow + TM_GB1, v);
+      acc[r] = v[0];
+      tmem_ld16(trow + TM_GB2, v);
+      acc[128 + r] = v[0];
+      tmem_ld16(trow + TM_GB3, v);
+      acc[256 + r] = v[0];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 128 * 128; i += FT_THREADS) {
-      const int o = i >> 7, c = i & 127;
-      out[OFF_W3 + i] = st3[o * 129 + c];
-      out[OFF_W2 + i] = st2[o * 129 + c];
+    for (int i = threadIdx.x; i < 128 * 128 / 4; i += FT_THREADS) {
+      const int o = i >> 5, c = (i & 31) * 4;
+      *(float4 *)&out[OFF_W3 + 4 * i] = *(const float4 *)&st3[o * LD + c];
+      *(float4 *)&out[OFF_W2 + 4 * i] = *(const float4 *)&st2[o * LD + c];
     }
-    for (int i = threadIdx.x; i < 128 * 48; i += FT_THREADS) {
-      const int o = i / 48, c = i - o * 48;
-      out[OFF_W1 + i] = st1[o * 49 + c];
+    for (int i = threadIdx.x; i < 128 * 48 / 4; i += FT_THREADS) {
+      const int o = i / 12, c = (i - o * 12) * 4;
+      *(float4 *)&out[OFF_W1 + 4 * i] = *(const float4 *)&st1[o * LD + c];
     }
   } else {
     for (int i = threadIdx.x; i < 128 * 128; i += blockDim.x) {
@@ -955,25 +1050,68 @@ __global__ void __launch_bounds__(FT_THREADS, 1) k_train_fused(FusedArgs A) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
 }
 
-// G[i] = sum over the CTAs' partials in CTA order (deterministic)
-__global__ void k_sum_parts(const float *__restrict__ part, int n_parts, float *G) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > N_PARAMS) return;
-  float s = 0.0f;
-  for (int c = 0; c < n_parts; ++c) s += __ldg(&part[(size_t)c * (N_PARAMS + 1) + i]);
-  G[i] = s;
+// Sum of the CTAs' partials in a fixed order (deterministic): a CTA of
+// SUM_THREADS threads takes SUM_PAR consecutive parameters; each thread of
+// slice s (SUM_SLICES slices) loads 4 consecutive parameters (16 bytes) of the
+// partials c = s, s + SUM_SLICES, ... (a few loads per thread), and the slices
+// are added in order through shared memory.  Many threads with wide loads
+// keep enough bytes in flight to stream the partials at L2 bandwidth.  Returns the sum of parameter blockIdx.x *
+// SUM_PAR + threadIdx.x for the first SUM_PAR threads (the partials are padded
+// to PART_STRIDE, so the last group of 4 stays inside them).
+constexpr int SUM_THREADS = 256, SUM_SLICES = 32, SUM_LANES = SUM_THREADS / SUM_SLICES, SUM_PAR = 4 * SUM_LANES,
+              SUM_LOADS = 4;
+__device__ __forceinline__ float sum_partials(const float *__restrict__ part, int n_parts, float *red) {
+  const int pl = threadIdx.x % SUM_LANES, sl = threadIdx.x / SUM_LANES;
+  const int i4 = blockIdx.x * SUM_PAR + 4 * pl;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i4 < PART_STRIDE) {
+    for (int c = sl; c < n_parts; c += SUM_LOADS * SUM_SLICES) {
+      float4 v[SUM_LOADS];
+#pragma unroll
+      for (int j = 0; j < SUM_LOADS; ++j) {  // unconditional loads (clamped index): all issued at once
+        const int cj = min(c + j * SUM_SLICES, n_parts - 1);
+        v[j] = __ldg((const float4 *)&part[(size_t)cj * PART_STRIDE + i4]);
+      }
+#pragma unroll
+      for (int j = 0; j < SUM_LOADS; ++j)
+        if (c + j * SUM_SLICES < n_parts) {
+          s.x += v[j].x;
+          s.y += v[j].y;
+          s.z += v[j].z;
+          s.w += v[j].w;
+        }
+    }
+  }
+  *(float4 *)&red[sl * SUM_PAR + 4 * pl] = s;
+  __syncthreads();
+  float g = 0.0f;
+  if (threadIdx.x < SUM_PAR) {
+    g = red[threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < SUM_SLICES; ++k) g += red[k * SUM_PAR + threadIdx.x];
+  }
+  return g;
 }
 
-// The step's tail in one launch: the CTAs' partials summed in CTA order, then
+// G[i] = sum over the CTAs' partials (fixed order)
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_parts(const float *__restrict__ part, int n_parts, float *G) {
+  __shared__ __align__(16) float red[SUM_SLICES * SUM_PAR];
+  const int i = blockIdx.x * SUM_PAR + threadIdx.x;
+  const float g = sum_partials(part, n_parts, red);
+  if (threadIdx.x < SUM_PAR && i <= N_PARAMS) G[i] = g;
+}
+
+// The step's tail in one launch: the CTAs' partials summed (fixed order), then
 // Adam on the masters (the arithmetic of k_adam) and the BF16 copies the
 // products take (those of k_weights_bf16; the zero padding of W1p is written
 // once at creation).
-__global__ void k_sum_adam(const float *__restrict__ part, int n_parts, float *G, float *P, float *Mm, float *Vv,
-                           float lr, float beta1, float beta2, float eps, float c1, float c2, Bf16Copies C) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > N_PARAMS) return;
-  float g = 0.0f;
-  for (int c = 0; c < n_parts; ++c) g += __ldg(&part[(size_t)c * (N_PARAMS + 1) + i]);
+__global__ void __launch_bounds__(SUM_THREADS) k_sum_adam(const float *__restrict__ part, int n_parts, float *G,
+                                                           float *P, float *Mm, float *Vv, float lr, float beta1,
+                                                           float beta2, float eps, float c1, float c2, Bf16Copies C) {
+  __shared__ __align__(16) float red[SUM_SLICES * SUM_PAR];
+  const int i = blockIdx.x * SUM_PAR + threadIdx.x;
+  const float g = sum_partials(part, n_parts, red);
+  if (threadIdx.x >= SUM_PAR || i > N_PARAMS) return;
   G[i] = g;
   if (i == N_PARAMS) return;  // the loss
   const float m = beta1 * Mm[i] + (1.0f - beta1) * g;
@@ -1075,9 +1213,10 @@ struct cr_trainer {
   float *part = nullptr;   // split-K slices of a weight gradient [max_splits][128][128]
   int max_splits = 0;
   bool unfused = false;     // one product per launch (k_mma) instead of the fused step
-  float *part_f = nullptr;  // fused step: per-CTA partial gradients and loss [sms][N_PARAMS + 1]
+  float *part_f = nullptr;  // fused step: per-CTA partial gradients and loss [sms][PART_STRIDE]
   int sms = 1;
   Bf16Copies C{};
+  CUtensorMap mW1{}, mW2{}, mW3{};  // TMA maps of the BF16 weights (fused step)
   int64_t launches = 0;
 };
 
@@ -1132,7 +1271,7 @@ extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train
     t->max_splits = (cfg->max_batch + ks - 1) / ks;
     al(&t->part, (size_t)t->max_splits * MLP_H * MLP_H);
   }
-  al(&t->part_f, (size_t)std::min(t->sms, cfg->max_batch / 128) * (N_PARAMS + 1));
+  al(&t->part_f, (size_t)std::min(t->sms, cfg->max_batch / 128) * PART_STRIDE);
   if (!ok) {
     free_trainer(t);
     return CR_ERR_NOMEM;
@@ -1144,6 +1283,11 @@ extern "C" int cr_train_create(cr_trainer **out, const cr_mlp *m, const cr_train
   t->C.W3 = t->C.W2T + MLP_H * MLP_H;
   t->C.W3T = t->C.W3 + MLP_H * MLP_H;
   t->C.w4 = t->C.W3T + MLP_H * MLP_H;
+  if (make_map(&t->mW1, t->C.W1p, MLP_H, 64, 128) != CR_OK || make_map(&t->mW2, t->C.W2, MLP_H, MLP_H, 128) != CR_OK ||
+      make_map(&t->mW3, t->C.W3, MLP_H, MLP_H, 128) != CR_OK) {
+    free_trainer(t);
+    return CR_ERR_CUDA;
+  }
   // masters from the BF16 initial weights
   std::vector<float> h(N_PARAMS);
   auto bf = [](uint16_t b) {
@@ -1191,6 +1335,15 @@ extern "C" int cr_train_set_stream(cr_trainer *t, void *stream) {
   return CR_OK;
 }
 
+// CTAs of the fused step: as many as give every CTA the same number of
+// tiles as the busiest one (at most one per SM), so that no CTA writes a
+// partial for less work than the kernel's duration allows
+static int fused_grid(int B, int sms) {
+  const int tiles = B / 128;
+  const int per = (tiles + sms - 1) / std::max(sms, 1);
+  return (tiles + per - 1) / std::max(per, 1);
+}
+
 // the fused kernel alone (per-CTA partials in t->part_f)
 static int train_fused_kernel(cr_trainer *t, const float *X, const float *target, int B) {
   if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return CR_ERR_INVALID_ARG;
@@ -1200,22 +1353,19 @@ static int train_fused_kernel(cr_trainer *t, const float *X, const float *target
       return CR_ERR_CUDA;
     attr = true;
   }
-  const int grid = std::min(B / 128, t->sms);
+  const int grid = fused_grid(B, t->sms);
   FusedArgs A{};
   A.X = X;
   A.t = target;
   A.B = B;
   A.clip = (float)t->clip;
   A.inv_batch = 1.0f / (float)B;
-  A.W1p = t->C.W1p;
-  A.W2 = t->C.W2;
-  A.W3 = t->C.W3;
   A.w4 = t->C.w4;
   A.P = t->P;
   A.part = t->part_f;
   A.err = t->err;
   A.spin = 0;
-  k_train_fused<<<grid, FT_THREADS, FT_SMEM, t->stream>>>(A);
+  k_train_fused<<<grid, FT_THREADS, FT_SMEM, t->stream>>>(t->mW1, t->mW2, t->mW3, A);
   t->launches++;
   return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
@@ -1224,7 +1374,8 @@ static int train_fused_kernel(cr_trainer *t, const float *X, const float *target
 static int train_grads_fused(cr_trainer *t, const float *X, const float *target, int B) {
   const int rc = train_fused_kernel(t, X, target, B);
   if (rc != CR_OK) return rc;
-  k_sum_parts<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(t->part_f, std::min(B / 128, t->sms), t->G);
+  k_sum_parts<<<(N_PARAMS + 1 + SUM_PAR - 1) / SUM_PAR, SUM_THREADS, 0, t->stream>>>(t->part_f,
+                                                                                 fused_grid(B, t->sms), t->G);
   t->launches++;
   return cudaGetLastError() == cudaSuccess ? CR_OK : CR_ERR_CUDA;
 }
@@ -1355,8 +1506,8 @@ extern "C" int cr_train_step(cr_trainer *t, const float *X, const float *target,
     if ((rc = train_fused_kernel(t, X, target, batch)) != CR_OK) return rc;
     t->step++;
     const double c1 = 1.0 - std::pow(t->beta1, (double)t->step), c2 = 1.0 - std::pow(t->beta2, (double)t->step);
-    k_sum_adam<<<(N_PARAMS + 1 + 255) / 256, 256, 0, t->stream>>>(
-        t->part_f, std::min(batch / 128, t->sms), t->G, t->P, t->Mm, t->Vv, (float)t->lr, (float)t->beta1,
+    k_sum_adam<<<(N_PARAMS + 1 + SUM_PAR - 1) / SUM_PAR, SUM_THREADS, 0, t->stream>>>(
+        t->part_f, fused_grid(batch, t->sms), t->G, t->P, t->Mm, t->Vv, (float)t->lr, (float)t->beta1,
         (float)t->beta2, (float)t->eps, (float)c1, (float)c2, t->C);
     t->launches++;
     if (cudaGetLastError() != cudaSuccess) return CR_ERR_CUDA;

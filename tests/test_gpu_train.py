@@ -94,9 +94,11 @@ def _gradient_bounds(p, X, t):
     the kernels compute it: BF16 operands (X and the weights are the same BF16
     values on both sides), FP32 accumulation of every product and sum, h1, h2,
     h3 and the back-propagated errors G3, G2, G1 rounded to BF16 where they are
-    stored between products (the bias gradients sum the FP32 values before
-    that rounding), a ReLU mask that may differ where |z| is within its error
-    bound.  Returns (reference loss, reference gradients, loss bound, bounds)."""
+    stored between products (the bias gradients of the fused step are column
+    sums of those stored BF16 values, taken on the tensor cores; the unfused
+    path sums the FP32 values, which the same bound covers), a ReLU mask that
+    may differ where |z| is within its error bound.  Returns (reference loss,
+    reference gradients, loss bound, bounds)."""
     A = np.abs
     B = X.shape[0]
     y, c = MO.forward(p, X)
@@ -130,7 +132,7 @@ def _gradient_bounds(p, X, t):
         _gamma(B) * (A(dy)[:, None] * A(h3)).sum(0)
     bnd["b4"] = float(e_dy.sum() + _gamma(B) * A(dy).sum())
     bnd["W3"] = e_g3s.T @ A(h2) + A(g3).T @ e_h2 + e_g3s.T @ e_h2 + _gamma(B) * (A(g3).T @ A(h2))
-    bnd["b3"] = e_g3.sum(0) + _gamma(B) * A(g3).sum(0)
+    bnd["b3"] = e_g3s.sum(0) + _gamma(B) * A(g3).sum(0)
     # G2 = (G3 W3) [z2 > 0]
     q2 = g3 @ W3
     e_q2 = e_g3s @ A(W3) + _gamma(128) * (A(g3) @ A(W3))
@@ -138,7 +140,7 @@ def _gradient_bounds(p, X, t):
     g2 = q2 * (z2 > 0)
     e_g2s = e_g2 + U_BF16 * A(g2)
     bnd["W2"] = e_g2s.T @ A(h1) + A(g2).T @ e_h1 + e_g2s.T @ e_h1 + _gamma(B) * (A(g2).T @ A(h1))
-    bnd["b2"] = e_g2.sum(0) + _gamma(B) * A(g2).sum(0)
+    bnd["b2"] = e_g2s.sum(0) + _gamma(B) * A(g2).sum(0)
     # G1 = (G2 W2) [z1 > 0]
     q1 = g2 @ W2
     e_q1 = e_g2s @ A(W2) + _gamma(128) * (A(g2) @ A(W2))
@@ -146,7 +148,7 @@ def _gradient_bounds(p, X, t):
     g1 = q1 * (z1 > 0)
     e_g1s = e_g1 + U_BF16 * A(g1)
     bnd["W1"] = e_g1s.T @ A(X) + _gamma(B) * (A(g1).T @ A(X))
-    bnd["b1"] = e_g1.sum(0) + _gamma(B) * A(g1).sum(0)
+    bnd["b1"] = e_g1s.sum(0) + _gamma(B) * A(g1).sum(0)
     return ref_loss, ref, e_loss, bnd
 
 
