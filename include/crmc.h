@@ -429,6 +429,36 @@ int cr_get_info(const cr_ctx *ctx, cr_info *out);
 /* Use a caller CUDA stream (a cudaStream_t passed as void*; NULL = default). */
 int cr_set_stream(cr_ctx *ctx, void *stream);
 
+/* ---- device memory owned by the caller ----
+ * The paper has no counterpart: this is the boundary's memory rule, under
+ * which the caller's allocator (e.g. PyTorch tensors) may own the device
+ * memory of the configuration and read it in place.  The buffers are the
+ * slot arrays of the cell list in the layout cr_get_info describes: n_cells
+ * = nc^3 cells of cap slots, slot g = cell * cap + i for i < cnt[cell], the
+ * particles of a cell in ascending id:
+ *   cnt  [n_cells]    int32   particles per cell                (4-byte aligned)
+ *   pos  [4 n_slots]  float   x, y, z, effective charge        (16-byte aligned)
+ *   vel  [4 n_slots]  float   vx, vy, vz, 0                     (16-byte aligned)
+ *   id   [n_slots]    uint64  particle id (input index; inserted ions >= 2^32)
+ *   info [n_slots]    int32   type | cls << 4 | ionised << 6 | site index << 8
+ * The context copies its configuration into them, frees its own copies of
+ * these arrays and works in the caller's buffers from then on (sweeps, MD,
+ * cr_state, cr_load, checkpoints); the caller keeps them allocated and does
+ * not write them until cr_destroy, which does not free them.  Contents are
+ * current after any synchronising call (cr_check, cr_state).  One bind per
+ * context, before the context joins a batch.  Errors: INVALID_ARG (NULL or
+ * misaligned pointer, a size below the layout's, memory that is not device
+ * memory of the context's device, a second bind, a context in a batch), CUDA.
+ * Synchronises. */
+typedef struct {
+  int32_t *cnt;
+  float *pos, *vel;
+  uint64_t *id;
+  int32_t *info;
+  int64_t n_cells, n_slots;
+} cr_device_buffers;
+int cr_bind_device_buffers(cr_ctx *ctx, const cr_device_buffers *buf);
+
 /* Check the device error word (synchronises): CR_OK or the first error. */
 int cr_check(cr_ctx *ctx);
 

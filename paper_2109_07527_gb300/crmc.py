@@ -83,6 +83,11 @@ DA_DTYPE = np.dtype([("dE_sur", "<f4"), ("stage", "<i4"), ("lnA2", "<f8"), ("lnu
 N_FEAT = 48
 
 
+class cr_device_buffers(C.Structure):
+    _fields_ = [("cnt", C.c_void_p), ("pos", C.c_void_p), ("vel", C.c_void_p), ("id", C.c_void_p),
+                ("info", C.c_void_p), ("n_cells", C.c_int64), ("n_slots", C.c_int64)]
+
+
 class cr_mlp(C.Structure):
     _fields_ = [("W1", C.c_void_p), ("b1", C.c_void_p), ("W2", C.c_void_p), ("b2", C.c_void_p),
                 ("W3", C.c_void_p), ("b3", C.c_void_p), ("w4", C.c_void_p), ("b4", C.c_float)]
@@ -98,7 +103,8 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_batch_md_end", "cr_batch_set_launch_shape", "cr_batch_state", "cr_batch_load",
            "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
            "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup",
-           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle", "cr_set_invocation")
+           "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle", "cr_set_invocation",
+           "cr_bind_device_buffers")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -169,6 +175,8 @@ def _lib():
         lib.cr_batch_sweep_da.argtypes = [P, C.c_uint64, C.c_uint64]
         lib.cr_md_forces_noalloc.restype = C.c_int
         lib.cr_md_forces_noalloc.argtypes = [P, P, P, C.c_int64]
+        lib.cr_bind_device_buffers.restype = C.c_int
+        lib.cr_bind_device_buffers.argtypes = [P, C.POINTER(cr_device_buffers)]
         lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
         lib.cr_state.restype = C.c_int
         lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
@@ -392,6 +400,14 @@ class Context:
         pointers: force [4 * n_slots] float32, id [n_slots] uint64."""
         _chk(self._lib.cr_md_forces_noalloc(self._h, C.c_void_p(int(force_ptr)), C.c_void_p(int(id_ptr)),
                                             int(n_slots)), "cr_md_forces_noalloc")
+
+    def bind_device_buffers(self, cnt_ptr, pos_ptr, vel_ptr, id_ptr, info_ptr, n_cells, n_slots):
+        """cr_bind_device_buffers: the configuration's slot arrays in caller-owned
+        device memory given as raw pointers (cnt [n_cells] int32, pos and vel
+        [4 n_slots] float32, id [n_slots] uint64, info [n_slots] int32)."""
+        b = cr_device_buffers(C.c_void_p(int(cnt_ptr)), C.c_void_p(int(pos_ptr)), C.c_void_p(int(vel_ptr)),
+                              C.c_void_p(int(id_ptr)), C.c_void_p(int(info_ptr)), int(n_cells), int(n_slots))
+        _chk(self._lib.cr_bind_device_buffers(self._h, C.byref(b)), "cr_bind_device_buffers")
 
     def md_begin(self, dt, gamma, seed):
         _chk(self._lib.cr_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_md_begin")

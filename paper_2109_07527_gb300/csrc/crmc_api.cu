@@ -119,6 +119,9 @@ struct cr_ctx {
   double ms[2] = {0.0, 0.0};
   int64_t launches[2] = {0, 0};
   int64_t launches_total = 0;
+  // caller-owned slot arrays (cr_bind_device_buffers) and batch membership
+  bool bound = false;
+  int batch_refs = 0;
 };
 
 namespace {
@@ -186,6 +189,13 @@ extern "C" const char *cr_strerror(int code) {
 
 static void free_ctx(cr_ctx *c) {
   if (!c) return;
+  if (c->bound) {  // the caller's buffers stay with the caller
+    c->d_cnt = nullptr;
+    c->d_pos = nullptr;
+    c->d_vel = nullptr;
+    c->d_pid = nullptr;
+    c->d_info = nullptr;
+  }
   void *ptrs[] = {c->d_cnt, c->d_cnt2, c->d_info, c->d_info2, c->d_pos, c->d_pos2, c->d_vel, c->d_vel2,
                   c->d_frc, c->d_frc2, c->d_fcons, c->d_pid, c->d_pid2, c->d_stats, c->d_lnK, c->d_lntab,
                   c->d_counts, c->d_perm, c->d_bond_off, c->d_bond_nbr, c->d_log,
@@ -817,6 +827,53 @@ extern "C" int cr_get_info(const cr_ctx *ctx, cr_info *out) {
   out->cell_side = P.a;
   out->domain_side = P.global ? (double)P.Lf : P.k * P.a;
   return CR_OK;
+}
+
+// whether p is device memory of device dev
+static bool device_memory_of(const void *p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
+extern "C" int cr_bind_device_buffers(cr_ctx *ctx, const cr_device_buffers *b) {
+  if (!ctx || !b || !b->cnt || !b->pos || !b->vel || !b->id || !b->info) return CR_ERR_INVALID_ARG;
+  if (ctx->bound || ctx->batch_refs > 0) return CR_ERR_INVALID_ARG;
+  const int64_t ncell = ctx->P.ncell, nslot = (int64_t)ctx->P.ncell * ctx->P.cap;
+  if (b->n_cells < ncell || b->n_slots < nslot) return CR_ERR_INVALID_ARG;
+  const uintptr_t a4 = (uintptr_t)b->cnt | (uintptr_t)b->info, a8 = (uintptr_t)b->id,
+                  a16 = (uintptr_t)b->pos | (uintptr_t)b->vel;
+  if ((a4 & 3u) || (a8 & 7u) || (a16 & 15u)) return CR_ERR_INVALID_ARG;
+  const void *ps[] = {b->cnt, b->pos, b->vel, b->id, b->info};
+  for (const void *p : ps)
+    if (!device_memory_of(p, ctx->device)) return CR_ERR_INVALID_ARG;
+  cudaStream_t s = ctx->stream;
+  CR_CUDA(cudaMemcpyAsync(b->cnt, ctx->d_cnt, sizeof(int) * (size_t)ncell, cudaMemcpyDeviceToDevice, s));
+  CR_CUDA(cudaMemcpyAsync(b->pos, ctx->d_pos, sizeof(float4) * (size_t)nslot, cudaMemcpyDeviceToDevice, s));
+  CR_CUDA(cudaMemcpyAsync(b->vel, ctx->d_vel, sizeof(float4) * (size_t)nslot, cudaMemcpyDeviceToDevice, s));
+  CR_CUDA(cudaMemcpyAsync(b->id, ctx->d_pid, sizeof(unsigned long long) * (size_t)nslot, cudaMemcpyDeviceToDevice, s));
+  CR_CUDA(cudaMemcpyAsync(b->info, ctx->d_info, sizeof(int) * (size_t)nslot, cudaMemcpyDeviceToDevice, s));
+  CR_CUDA(cudaStreamSynchronize(s));
+  void *old[] = {ctx->d_cnt, ctx->d_pos, ctx->d_vel, ctx->d_pid, ctx->d_info};
+  for (void *p : old) cudaFree(p);
+  ctx->d_cnt = b->cnt;
+  ctx->d_pos = reinterpret_cast<float4 *>(b->pos);
+  ctx->d_vel = reinterpret_cast<float4 *>(b->vel);
+  ctx->d_pid = reinterpret_cast<unsigned long long *>(b->id);
+  ctx->d_info = b->info;
+  ctx->bound = true;
+  SysParams &P = ctx->P;
+  P.cnt = ctx->d_cnt;
+  P.pos = ctx->d_pos;
+  P.vel = ctx->d_vel;
+  P.pid = ctx->d_pid;
+  P.info = ctx->d_info;
+  CR_CUDA(cudaMemcpyAsync(ctx->d_reps, &P, sizeof(SysParams), cudaMemcpyHostToDevice, s));
+  CR_CUDA(cudaStreamSynchronize(s));
+  return cr_check(ctx);
 }
 
 extern "C" int cr_check(cr_ctx *ctx) {
@@ -1493,6 +1550,7 @@ struct cr_batch {
   unsigned long long *d_pk_id = nullptr;
   int *d_pk_type = nullptr, *d_pk_cls = nullptr;
   int8_t *d_pk_state = nullptr;
+  bool holds_refs = false;  // the contexts' batch_refs count this batch
 };
 
 // The device address of caller memory the GPU can access directly (device
@@ -1637,6 +1695,8 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
       return CR_ERR_NOMEM;
     }
   }
+  for (cr_ctx *c : b->ctx) c->batch_refs++;  // (contexts in a batch cannot be bound)
+  b->holds_refs = true;
   *out = b;
   return CR_OK;
 }
@@ -1644,6 +1704,9 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
 extern "C" void cr_batch_destroy(cr_batch *b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
+  if (b->holds_refs)
+    for (cr_ctx *c : b->ctx)
+      if (c) c->batch_refs--;
   for (size_t r = 0; r < b->streams.size(); ++r) {
     cudaStreamSynchronize(b->streams[r]);
     cudaStreamDestroy(b->streams[r]);

@@ -56,7 +56,7 @@ def test_struct_layouts_match_header(tmp_path):
                "cr_state_view": crmc.cr_state_view, "cr_info": crmc.cr_info, "cr_mlp": crmc.cr_mlp,
                "cr_load_args": crmc.cr_load_args, "cr_batch_packed": crmc.cr_batch_packed,
                "cr_counters": crmc.cr_counters, "cr_train_cfg": crmc.cr_train_cfg,
-               "cr_ungrouped": crmc.cr_ungrouped}
+               "cr_ungrouped": crmc.cr_ungrouped, "cr_device_buffers": crmc.cr_device_buffers}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crmc.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
