@@ -22,7 +22,8 @@ _LIB = os.path.join(_HERE, "libcrmc_oracle.so")
 # trial-record flags
 F_ACC, F_NOELIG, F_EDGE, F_OVERLAP = 1, 2, 4, 8
 PLANT = {"none": 0, "drop_ion_count": 1, "dE_sign": 2, "drop_self": 3, "drop_pair_cc": 4,
-         "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7, "species_count": 8}
+         "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7, "species_count": 8,
+         "ewald_half_recip": 9}
 N_FEAT, N_HID = 48, 128
 
 
@@ -49,7 +50,7 @@ class _Params(C.Structure):
                 ("wca_eps", C.c_double * 16), ("wca_sig", C.c_double * 16), ("wca_del", C.c_double * 16),
                 ("wca_on", C.c_int32 * 16),
                 ("fene_K", C.c_double), ("fene_R0", C.c_double),
-                ("n_bonds", C.c_int32)]
+                ("n_bonds", C.c_int32), ("ewald_kmax", C.c_int32)]
 
 
 TRIAL_DTYPE = np.dtype([("move", "<i4"), ("flags", "<i4"), ("id_a", "<u8"), ("id_b", "<u8"),
@@ -95,6 +96,9 @@ def _load():
         lib.or_site_states.argtypes = [P, P]
         lib.or_energy.restype = C.c_double
         lib.or_energy.argtypes = [P]
+        lib.or_ewald_parts.argtypes = [P, P]
+        lib.or_ewald_nk.restype = C.c_int32
+        lib.or_ewald_nk.argtypes = [P]
         lib.or_bond_energy.restype = C.c_double
         lib.or_bond_energy.argtypes = [P]
         lib.or_forces.restype = C.c_int32
@@ -177,6 +181,7 @@ class Oracle:
             p.wca_on[i] = int(q["wca_on"][i])
         p.fene_K, p.fene_R0 = q["fene_K"], q["fene_R0"]
         p.n_bonds = int(w.bonds.shape[0])
+        p.ewald_kmax = int(q.get("ewald_kmax", 0))
         self._keep = [np.ascontiguousarray(w.xyz, dtype=np.float32), np.ascontiguousarray(w.type, dtype=np.int32),
                       np.ascontiguousarray(w.cls, dtype=np.int32), np.ascontiguousarray(w.state, dtype=np.int8),
                       np.ascontiguousarray(w.pK, dtype=np.float64), np.ascontiguousarray(w.bonds, dtype=np.int32),
@@ -307,6 +312,16 @@ class Oracle:
 
     def energy(self) -> float:
         return float(self._lib.or_energy(self._h))
+
+    def ewald_parts(self):
+        """Ewald parts of the Coulomb energy: (real space within rc, reciprocal, self)."""
+        out = np.zeros(3)
+        self._lib.or_ewald_parts(self._h, _ptr(out))
+        return tuple(float(v) for v in out)
+
+    @property
+    def ewald_nk(self) -> int:
+        return int(self._lib.or_ewald_nk(self._h))
 
     def bond_energy(self) -> float:
         return float(self._lib.or_bond_energy(self._h))

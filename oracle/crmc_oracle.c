@@ -21,7 +21,10 @@
  *   - Eq. (LJe)/(LJ): WCA with an optional expanded distance Delta.
  * Readings where the paper is silent:
  *   - The energy model is a damped-shifted-force (DSF) Coulomb cutoff sum plus
- *     WCA (the paper uses PPPM), with the DSF self term.
+ *     WCA (the paper uses PPPM), with the DSF self term; or, under the global
+ *     schedule, the Ewald sum that PPPM evaluates on a mesh (real-space erfc
+ *     within rc, reciprocal vectors 0 < |n| <= kmax, self term), S(k)
+ *     recomputed at every sweep and carried by the accepted trials within it.
  *   - Moves are domain-local under an 8-colour checkerboard schedule: the
  *     paired ion is inserted in / deleted from the trial's domain, and the
  *     acceptance uses that domain's volume and counts.  The "global" schedule
@@ -64,7 +67,8 @@ enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 /* Planted mistakes, used only by the tests that show the pins catch them. */
 enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
        PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5,
-       PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7, PLANT_SPECIES_COUNT = 8 };
+       PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7, PLANT_SPECIES_COUNT = 8,
+       PLANT_EWALD_HALF_RECIP = 9 };
 
 /* ----------------------------------------------------------------------- */
 /* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
@@ -110,6 +114,7 @@ typedef struct {
   int32_t wca_on[16];
   double fene_K, fene_R0;
   int32_t n_bonds;
+  int32_t ewald_kmax; /* 0: DSF cutoff energy; > 0: Ewald sum with reciprocal vectors 0 < |n|^2 <= kmax^2 */
 } or_params;
 
 typedef struct {
@@ -159,6 +164,13 @@ typedef struct {
    * floats), on when has_mlp and da are set */
   int has_mlp, da;
   float *W1, *b1, *W2, *b2, *W3, *b3, *w4, b4;
+  /* Ewald electrostatics (ewald_kmax > 0): reciprocal vectors k = 2 pi n / L
+   * (kn: n, 3 ints each), their weights kA = (2 pi lB / V) exp(-k^2/(4 alpha^2)) / k^2,
+   * the structure factor S(k) = sum_j q_j exp(i k.r_j) of the current state and
+   * the change dS of the last evaluated trial */
+  int ewald_kmax, nk;
+  int *kn;
+  double *kA, *Sre, *Sim, *dSre, *dSim;
 } Oracle;
 
 static int g_plant = PLANT_NONE;
@@ -258,10 +270,45 @@ void or_destroy(Oracle *o) {
   free(o->id); free(o->vx); free(o->vy); free(o->vz); free(o->fx); free(o->fy); free(o->fz);
   free(o->lnK); free(o->pK); free(o->site_type); free(o->bi); free(o->bj);
   free(o->W1); free(o->b1); free(o->W2); free(o->b2); free(o->W3); free(o->b3); free(o->w4);
+  free(o->kn); free(o->kA); free(o->Sre); free(o->Sim); free(o->dSre); free(o->dSim);
   free(o);
 }
 
 /* pI of the grouped ion from the salt pI and the reservoir pH, Eq. (pIXgen) */
+/* ---- Ewald sum (standard form; e.g. Frenkel & Smit, Understanding Molecular
+ * Simulation, ch. 12): E = E_real + E_rec + E_self with
+ *   E_real = lB sum_{i<j, r < rc} q_i q_j erfc(alpha r) / r   (minimum image),
+ *   E_rec  = (2 pi lB / V) sum_{k != 0} exp(-k^2 / (4 alpha^2)) / k^2 |S(k)|^2,
+ *   E_self = -lB alpha / sqrt(pi) sum_i q_i^2,
+ * tin-foil boundary (no surface term; every state here is neutral).  The
+ * paper's energy model is PPPM (Sec. III.A), a mesh evaluation of this sum. */
+static double ewald_phase(const Oracle *o, int i, double x, double y, double z) {
+  const double kf = 2.0 * M_PI / o->L;
+  return kf * ((double)o->kn[3 * i] * x + (double)o->kn[3 * i + 1] * y + (double)o->kn[3 * i + 2] * z);
+}
+/* S(k) of the current state, from scratch */
+static void ewald_structure(const Oracle *o, double *re, double *im) {
+  for (int i = 0; i < o->nk; ++i) {
+    re[i] = 0.0;
+    im[i] = 0.0;
+  }
+  for (int j = 0; j < o->n; ++j) {
+    const double q = qeff(o, o->type[j], o->st[j]);
+    if (q == 0.0) continue;
+    for (int i = 0; i < o->nk; ++i) {
+      const double ph = ewald_phase(o, i, o->x[j], o->y[j], o->z[j]);
+      re[i] += q * cos(ph);
+      im[i] += q * sin(ph);
+    }
+  }
+}
+static double ewald_recip_energy(const Oracle *o, const double *re, const double *im) {
+  double E = 0.0;
+  for (int i = 0; i < o->nk; ++i) E += o->kA[i] * (re[i] * re[i] + im[i] * im[i]);
+  if (g_plant == PLANT_EWALD_HALF_RECIP) E *= 0.5;
+  return E;
+}
+
 static double pIX_of(double pIS, double pH, double pOH) {
   double m = pH < pOH ? pH : pOH;
   return -log10(pow(10.0, -pIS) + pow(10.0, -m));
@@ -283,6 +330,45 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   o->phi_c2 = erfc(o->alpha * o->rc) / (o->rc * o->rc) +
               2.0 * o->alpha / sqrt(M_PI) * exp(-o->alpha * o->alpha * o->rc * o->rc) / o->rc;
   o->self_coef = -(erfc(o->alpha * o->rc) / (2.0 * o->rc) + o->alpha / sqrt(M_PI));
+  o->ewald_kmax = p->ewald_kmax;
+  if (o->ewald_kmax < 0 || o->ewald_kmax > 64) { free(o); return NULL; }
+  if (o->ewald_kmax > 0) {
+    /* Ewald: the real-space term lB q_i q_j erfc(alpha r) / r within rc (DSF
+     * without its shift), the self term -lB alpha / sqrt(pi) q^2 and the
+     * reciprocal sum.  Only the global schedule (one trial at a time, the
+     * paper's own rule): trials of different domains would interact through
+     * S(k), so concurrent domain-local trials would not be independent. */
+    if (p->schedule != 1) { free(o); return NULL; }
+    o->phi_c1 = 0.0;
+    o->phi_c2 = 0.0;
+    o->self_coef = -o->alpha / sqrt(M_PI);
+    o->dsf_self = 1;
+    const int km = o->ewald_kmax;
+    const double V = o->L * o->L * o->L, kf = 2.0 * M_PI / o->L;
+    int nk = 0;
+    for (int nz = -km; nz <= km; ++nz)
+      for (int ny = -km; ny <= km; ++ny)
+        for (int nx = -km; nx <= km; ++nx) {
+          const int n2 = nx * nx + ny * ny + nz * nz;
+          if (n2 > 0 && n2 <= km * km) nk++;
+        }
+    o->nk = nk;
+    o->kn = malloc((size_t)3 * nk * sizeof(int));
+    o->kA = malloc((size_t)nk * sizeof(double));
+    o->Sre = calloc((size_t)nk, sizeof(double)); o->Sim = calloc((size_t)nk, sizeof(double));
+    o->dSre = calloc((size_t)nk, sizeof(double)); o->dSim = calloc((size_t)nk, sizeof(double));
+    nk = 0;
+    for (int nz = -km; nz <= km; ++nz)
+      for (int ny = -km; ny <= km; ++ny)
+        for (int nx = -km; nx <= km; ++nx) {
+          const int n2 = nx * nx + ny * ny + nz * nz;
+          if (!(n2 > 0 && n2 <= km * km)) continue;
+          const double k2 = kf * kf * n2;
+          o->kn[3 * nk] = nx; o->kn[3 * nk + 1] = ny; o->kn[3 * nk + 2] = nz;
+          o->kA[nk] = 2.0 * M_PI * o->lB / V * exp(-k2 / (4.0 * o->alpha * o->alpha)) / k2;
+          nk++;
+        }
+  }
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
       o->eps[i][j] = p->wca_eps[4 * i + j];
@@ -364,6 +450,7 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   }
   o->n_sites = ns;
   if (qsum != 0) { or_destroy(o); *err = OR_ERR_NEUTRAL; return NULL; }
+  if (o->ewald_kmax > 0) ewald_structure(o, o->Sre, o->Sim);
   o->n_react = 0;
   if (nA > 0) o->react[o->n_react++] = R_ACID;
   if (nB > 0) o->react[o->n_react++] = R_BASE;
@@ -431,7 +518,7 @@ static double dist(const Oracle *o, float ax, float ay, float az, float bx, floa
  * changed particle, plus the DSF self-energy change.  S = the gross
  * magnitude of the summed terms (gross_coul / gross_wca of the states that
  * differ, plus |self change|), the scale of the FP32 tolerance. */
-static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, double *S_out) {
+static double delta_E(Oracle *o, const change_t *c, int nc, int *overlap, double *S_out) {
   double dE = 0.0, S = 0.0;
   *overlap = 0;
   for (int a = 0; a < nc; ++a) {
@@ -476,6 +563,35 @@ static double delta_E(const Oracle *o, const change_t *c, int nc, int *overlap, 
       dE += ds;
       S += fabs(ds);
     }
+  }
+  if (o->ewald_kmax > 0) {
+    /* reciprocal part: the change of sum_k A_k |S(k)|^2 when the changed
+     * particles' charges dq = q_new - q_old (0 where absent) enter S(k); the
+     * change of S is kept for the commit */
+    double dEr = 0.0, Sr = 0.0;
+    for (int i = 0; i < o->nk; ++i) {
+      double dre = 0.0, dim = 0.0;
+      for (int a = 0; a < nc; ++a) {
+        const double dq = (c[a].pres_new ? c[a].q_new : 0.0) - (c[a].pres_old ? c[a].q_old : 0.0);
+        if (dq == 0.0) continue;
+        const double ph = ewald_phase(o, i, c[a].x, c[a].y, c[a].z);
+        dre += dq * cos(ph);
+        dim += dq * sin(ph);
+      }
+      o->dSre[i] = dre;
+      o->dSim[i] = dim;
+      const double nre = o->Sre[i] + dre, nim = o->Sim[i] + dim;
+      const double term =
+          o->kA[i] * ((nre * nre + nim * nim) - (o->Sre[i] * o->Sre[i] + o->Sim[i] * o->Sim[i]));
+      dEr += term;
+      Sr += fabs(term);
+    }
+    if (g_plant == PLANT_EWALD_HALF_RECIP) {
+      dEr *= 0.5;
+      Sr *= 0.5;
+    }
+    dE += dEr;
+    S += Sr;
   }
   *S_out = S;
   return dE;
@@ -656,6 +772,7 @@ int32_t or_set_surrogate(Oracle *o, const uint16_t *W1, const float *b1, const u
 
 /* delayed acceptance on (1) or off (0); needs a surrogate */
 int32_t or_set_da(Oracle *o, int32_t on) {
+  if (on && o->ewald_kmax > 0) return OR_ERR_ARG;
   if (on && !o->has_mlp) return OR_ERR_ARG;
   o->da = on ? 1 : 0;
   return OR_OK;
@@ -921,6 +1038,11 @@ static int or_trial_one(Oracle *o, const uint32_t key[2], const int off[3], uint
   if (accept) {
     t.flags |= F_ACC;
     o->stats[6 + t.move]++;
+    if (o->ewald_kmax > 0)
+      for (int i = 0; i < o->nk; ++i) {
+        o->Sre[i] += o->dSre[i];
+        o->Sim[i] += o->dSim[i];
+      }
     int s_before = 0;
     if (hist_n > 0) for (int j = 0; j < o->n; ++j) if (o->site[j] >= 0 && o->site[j] < hist_n && o->st[j]) s_before |= 1 << o->site[j];
     double va[3], vb[3];
@@ -985,6 +1107,7 @@ int32_t or_sweep(Oracle *o, int64_t n_trials, uint64_t seed, or_trial *log, cons
   int rc = OR_OK;
   for (int64_t sw = 0; sw < n_trials / per && rc == OR_OK; ++sw) {
     uint64_t s = o->sweep++;
+    if (o->ewald_kmax > 0) ewald_structure(o, o->Sre, o->Sim);  /* from scratch at every sweep */
     int off[3] = {0, 0, 0};
     if (!o->global) {
       uint32_t c[4] = {0u, 0u, (uint32_t)s, 4u}, w[4];
@@ -1134,10 +1257,39 @@ double or_energy(const Oracle *o) {
       double r = dist(o, o->x[i], o->y[i], o->z[i], o->x[j], o->y[j], o->z[j]);
       E += pair_u(o, qi, o->cls[i], qeff(o, o->type[j], o->st[j]), o->cls[j], r, &ov, 0);
     }
-    if (o->dsf_self) E += o->lB * o->self_coef * qi * qi;
+    if (o->dsf_self && !(o->ewald_kmax > 0 && g_plant == PLANT_DROP_SELF)) E += o->lB * o->self_coef * qi * qi;
+  }
+  if (o->ewald_kmax > 0) {
+    double *re = malloc((size_t)o->nk * sizeof(double)), *im = malloc((size_t)o->nk * sizeof(double));
+    ewald_structure(o, re, im);
+    E += ewald_recip_energy(o, re, im);
+    free(re);
+    free(im);
   }
   return E;
 }
+
+/* Ewald parts of the energy: out = {real (pairs within rc, Coulomb only),
+ * reciprocal, self}; zeros without Ewald */
+void or_ewald_parts(const Oracle *o, double *out) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (o->ewald_kmax <= 0) return;
+  for (int i = 0; i < o->n; ++i) {
+    const double qi = qeff(o, o->type[i], o->st[i]);
+    for (int j = i + 1; j < o->n; ++j) {
+      const double qj = qeff(o, o->type[j], o->st[j]);
+      const double r = dist(o, o->x[i], o->y[i], o->z[i], o->x[j], o->y[j], o->z[j]);
+      if (r < o->rc && qi != 0.0 && qj != 0.0) out[0] += o->lB * qi * qj * erfc(o->alpha * r) / r;
+    }
+    out[2] += o->lB * o->self_coef * qi * qi;
+  }
+  double *re = malloc((size_t)o->nk * sizeof(double)), *im = malloc((size_t)o->nk * sizeof(double));
+  ewald_structure(o, re, im);
+  out[1] = ewald_recip_energy(o, re, im);
+  free(re);
+  free(im);
+}
+int32_t or_ewald_nk(const Oracle *o) { return o->nk; }
 
 /* FENE bond energy, U = -K R0^2/2 ln(1 - (r/R0)^2) summed over bonds (the
  * CR-MC moves never change it; the MD tests use it for -grad E). */
@@ -1215,7 +1367,10 @@ static int forces_cons(const Oracle *o, double *F, double *fs) {
   return OR_OK;
 }
 
-int32_t or_forces(const Oracle *o, double *F, double *fs) { return forces_cons(o, F, fs); }
+int32_t or_forces(const Oracle *o, double *F, double *fs) {
+  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
+  return forces_cons(o, F, fs);
+}
 
 /* Langevin part of the force, drawn per particle id and force evaluation:
  * -gamma v + sqrt(2 gamma T / dt) xi, xi ~ N(0,1) from Box-Muller on Philox
@@ -1248,6 +1403,7 @@ static float wrapf(const Oracle *o, double x) {
  * evaluation (unit mass, kT = 1).  Forces are re-evaluated first when the
  * CR-MC stage changed the system since the last evaluation. */
 int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t seed) {
+  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = OR_OK;
   if (!o->f_valid) {
@@ -1284,6 +1440,7 @@ int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t
  * charges after any CR-MC trials run in between) and does the closing half
  * kick.  begin + end with nothing in between is or_md_step with one step. */
 int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
+  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = OR_OK;
   if (!o->f_valid) {
@@ -1304,6 +1461,7 @@ int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
 }
 
 int32_t or_md_end(Oracle *o, double dt, double gamma, uint64_t seed) {
+  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = forces_cons(o, F, NULL);
   if (!rc) {

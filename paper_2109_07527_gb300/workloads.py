@@ -62,7 +62,7 @@ def default_params(**kw) -> dict:
     p = dict(box_L=40.0, sigma_nm=0.355, lB=2.0, rc=10.0, alpha=0.2, dsf_self=1, ion_coupling=1, ion_cls=0,
              pH=5.0, pKw=14.0, pIS_plus=2.0, pIS_minus=2.0, pIX_explicit=0, pIX_plus=0.0, pIX_minus=0.0,
              nc=0, cells_per_rc=2, domain_cells=2, trials_per_domain=10, schedule=0,
-             wca_eps=eps, wca_sig=sig, wca_del=dele, wca_on=on, fene_K=30.0, fene_R0=1.5)
+             wca_eps=eps, wca_sig=sig, wca_del=dele, wca_on=on, fene_K=30.0, fene_R0=1.5, ewald_kmax=0)
     p.update(kw)
     return p
 
