@@ -480,23 +480,29 @@ def run_config5(crmc, torch, stream, flush, mlp, steps):
             "da_over_plain": v_da / v_plain}
 
 
-def run_method_comparison(crmc, n_rep=128, blocks=40, m=250):
+def run_method_comparison(crmc, n_rep=128, blocks=40, m=250, ewald_kmax=0):
     """Sec. III.A / Fig. 2: alpha(trials) of the weak-acid electrolyte under
     CR-MC, the grand-reaction ensemble and RxMC (the same random starts), and
-    the trials each needs to come within 5 % of CR-MC's plateau."""
+    the trials each needs to come within 5 % of CR-MC's plateau; with
+    ewald_kmax > 0 under Ewald electrostatics (the paper's energy model) with
+    the trials/s of each method's batch sweeps."""
     import time
     from paper_2109_07527_gb300 import methods
     t0 = time.perf_counter()
-    r = methods.compare_convergence(crmc, n_rep=n_rep, blocks=blocks, m=m, seed=1)
+    r = methods.compare_convergence(crmc, n_rep=n_rep, blocks=blocks, m=m, seed=1, ewald_kmax=ewald_kmax)
     plateau = float(np.mean(r["crmc"][blocks // 2:]))
     t95 = {}
     for k in ("crmc", "grxmc", "rxmc"):
         a = np.asarray(r[k])
         hit = np.flatnonzero(np.abs(a - plateau) <= 0.05 * plateau)
         t95[k] = int(r["trials"][hit[0]]) if len(hit) else None
-    return {"workload": "500 acid groups (pKa 6.5), L = 50 l_B, pH 7, pI_S = 2, DSF r_c = 10 l_B, "
+    energy = (f"Ewald: real space r_c = 10 l_B, alpha = 0.15/sigma, reciprocal |n| <= {ewald_kmax}" if ewald_kmax
+              else "DSF r_c = 10 l_B")
+    trials = n_rep * (r["trials"][-1] - r["trials"][blocks // 2 - 1])  # the timed second half of the blocks
+    return {"workload": f"500 acid groups (pKa 6.5), L = 50 l_B, pH 7, pI_S = 2, {energy}, "
                         "global schedule, no ions at the start",
             "replicas_per_method": n_rep, "trials": r["trials"],
+            "trials_per_s": {k: trials / r[k + "_sweep_s"] for k in ("crmc", "grxmc", "rxmc")},
             "alpha": {k: [round(x, 4) for x in r[k]] for k in ("crmc", "grxmc", "rxmc")},
             "alpha_plateau_crmc": plateau,
             "alpha_plateau_grxmc": float(np.mean(r["grxmc"][blocks // 2:])),
@@ -694,9 +700,10 @@ def run_ours(args):
     cfg4 = None
     if rank == 0 and not args.no_config4:
         cfg4 = run_config4(crmc, torch, stream, flush, max(10, min(args.steps, 50)))
-    fig2 = None
+    fig2 = fig2_ewald = None
     if rank == 0 and not args.no_fig2:
         fig2 = run_method_comparison(crmc)
+        fig2_ewald = run_method_comparison(crmc, n_rep=64, blocks=20, ewald_kmax=16)
 
     # ---- end to end through the public API with host buffers: each step
     # uploads every replica's configuration from pinned host memory, runs the
@@ -757,6 +764,7 @@ def run_ours(args):
            "graph_launches_per_step": 1, "kernels_per_step": tm["launches"] / args.steps,
            "clocks": cl, "e2e": e2e, "plain": plain,
            "surrogate_da": da, "batched_titration": cfg4, "method_comparison": fig2,
+           "method_comparison_ewald": fig2_ewald,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"], alpha_o = cpu_baseline(ph_sweep_workloads(0))

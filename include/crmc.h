@@ -116,7 +116,23 @@ typedef struct {
   int32_t cell_capacity;   /* slots per cell; 0 = automatic */
   int32_t list_capacity;   /* domain particles held in shared memory per CTA; 0 = automatic */
   int32_t halo_capacity;   /* halo particles held on chip per CTA; 0 = automatic */
+  int32_t ewald_kmax;      /* 0: DSF energy; > 0: Ewald electrostatics (global schedule only), below */
 } cr_system;
+
+/* Ewald electrostatics (ewald_kmax > 0).  The paper's energy model is PPPM
+ * (Sec. III.A), a mesh evaluation of the Ewald sum; here the sum is taken
+ * directly: E = E_real + E_rec + E_self with E_real = lB sum_{i<j, r < rc}
+ * q_i q_j erfc(alpha r) / r (alpha = dsf_alpha), E_rec = (2 pi lB / V) sum_k
+ * exp(-k^2 / (4 alpha^2)) / k^2 |S(k)|^2 over k = 2 pi n / L with
+ * 0 < |n|^2 <= ewald_kmax^2, S(k) = sum_j q_j exp(i k.r_j), and E_self = -lB
+ * alpha / sqrt(pi) sum_j q_j^2 (tin-foil boundary; every state is neutral).
+ * A trial's Delta E is the real-space pair sum of its changed particles, the
+ * self change and the change of E_rec, with S(k) recomputed at every sweep and
+ * carried by the accepted trials within it.  Only with CR_SCHED_GLOBAL, the
+ * paper's one-trial-at-a-time rule: trials of different domains would
+ * interact through S(k), so concurrent domain-local trials would not be
+ * independent.  MD (forces are DSF) and delayed acceptance are not available
+ * with Ewald (INVALID_ARG).  ewald_kmax <= 32. */
 
 /* Reservoir ions: pI_S of the symmetric salt per sign and pKw; with
  * pIX_explicit = 1 the grouped pI_X+- are taken as given (e.g. pIX+ = pH,

@@ -39,7 +39,8 @@ class cr_system(C.Structure):
                 ("dsf_alpha", C.c_double), ("dsf_self", C.c_int32), ("ion_coupling", C.c_int32),
                 ("ion_cls", C.c_int32), ("cells_per_rc", C.c_int32), ("domain_cells", C.c_int32),
                 ("trials_per_domain", C.c_int32), ("schedule", C.c_int32), ("nc", C.c_int32),
-                ("cell_capacity", C.c_int32), ("list_capacity", C.c_int32), ("halo_capacity", C.c_int32)]
+                ("cell_capacity", C.c_int32), ("list_capacity", C.c_int32), ("halo_capacity", C.c_int32),
+                ("ewald_kmax", C.c_int32)]
 
 
 class cr_mu_ions(C.Structure):
@@ -311,6 +312,7 @@ class Context:
         s.cell_capacity = int(cell_capacity)
         s.list_capacity = int(list_capacity)
         s.halo_capacity = int(halo_capacity)
+        s.ewald_kmax = int(q.get("ewald_kmax", 0))
         mu = cr_mu_ions(q["pIS_plus"], q["pIS_minus"], q["pKw"], int(q.get("pIX_explicit", 0)),
                         q.get("pIX_plus", 0.0), q.get("pIX_minus", 0.0))
         h = C.c_void_p()

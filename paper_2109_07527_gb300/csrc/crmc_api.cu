@@ -119,6 +119,11 @@ struct cr_ctx {
   double ms[2] = {0.0, 0.0};
   int64_t launches[2] = {0, 0};
   int64_t launches_total = 0;
+  // Ewald electrostatics: reciprocal vectors, weights, structure factor
+  int *d_ek_n = nullptr;
+  float *d_ek_A = nullptr;
+  double *d_ek_S = nullptr;
+  int *d_ek_list = nullptr, *d_ek_np = nullptr;
   // caller-owned slot arrays (cr_bind_device_buffers) and batch membership
   bool bound = false;
   int batch_refs = 0;
@@ -204,7 +209,8 @@ static void free_ctx(cr_ctx *c) {
                   c->d_out_xyz, c->d_out_vel, c->d_out_frc, c->d_out_id, c->d_out_type, c->d_out_cls,
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
-                  c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order};
+                  c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order,
+                  c->d_ek_n, c->d_ek_A, c->d_ek_S, c->d_ek_list, c->d_ek_np};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_small) cudaFreeHost(c->h_small);
@@ -383,6 +389,31 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.c2 = (float)(erc / (rc * rc) + 2.0 * alpha / std::sqrt(M_PI) * std::exp(-alpha * alpha * rc * rc) / rc);
   P.lBf = (float)lB;
   P.lB_self = sys->dsf_self ? lB * (-(erc / (2.0 * rc) + alpha / std::sqrt(M_PI))) : 0.0;
+  // Ewald electrostatics (global schedule only): the real-space term without
+  // the DSF shift, the Ewald self term, the reciprocal vectors and weights
+  std::vector<int> ek_n;
+  std::vector<float> ek_A;
+  if (sys->ewald_kmax < 0 || sys->ewald_kmax > 32) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+  if (sys->ewald_kmax > 0) {
+    if (!global) { free_ctx(c); return CR_ERR_INVALID_ARG; }
+    P.c1 = 0.0f;
+    P.c2 = 0.0f;
+    P.lB_self = lB * (-alpha / std::sqrt(M_PI));
+    const int km = sys->ewald_kmax;
+    const double V = L * L * L, kf = 2.0 * M_PI / L;
+    for (int nz = -km; nz <= km; ++nz)
+      for (int ny = -km; ny <= km; ++ny)
+        for (int nx = -km; nx <= km; ++nx) {
+          const int n2 = nx * nx + ny * ny + nz * nz;
+          if (!(n2 > 0 && n2 <= km * km)) continue;
+          const double k2 = kf * kf * n2;
+          ek_n.push_back((nx & 255) | ((ny & 255) << 8) | ((nz & 255) << 16));
+          ek_A.push_back((float)(2.0 * M_PI * lB / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2));
+        }
+  }
+  P.ewald_kmax = sys->ewald_kmax;
+  P.ewald_nk = (int)ek_n.size();
+  P.invLd = 1.0 / L;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
       WcaEntry &w = P.wca[4 * i + j];
@@ -544,6 +575,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   S.nr3 = P.nr * P.nr * P.nr;
   S.kc3 = k * k * k;
   S.chunk = std::min(P.m, TRIAL_CHUNK);
+  S.ewk = P.ewald_nk > 0 ? P.ewald_kmax + 1 : 0;
   // Shared-memory list and halo capacities: the densest domain of the
   // starting configuration with room for growth, and its densest halo.  The
   // compact set (Sc) is sized for the 90th percentile instead, so that more
@@ -657,6 +689,13 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_plist, (size_t)std::max(sys->capacity, 1));
   ALLOC(c->d_nparts, 1);
   ALLOC(c->d_fsum, 3 * (size_t)std::max(sys->capacity, 1));
+  if (P.ewald_nk > 0) {
+    ALLOC(c->d_ek_n, (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_A, (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_S, 2 * (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_list, (size_t)std::max(sys->capacity, 1));
+    ALLOC(c->d_ek_np, 1);
+  }
 #undef ALLOC
   {
     if (cudaHostAlloc((void **)&c->h_small, 16 * sizeof(long long), 0) != cudaSuccess) {
@@ -688,6 +727,10 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   COPY(c->d_counts, kinds, (size_t)N_KIND);
   if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
   if (n > 0) COPY(c->d_init_type, sys->type, (size_t)n);
+  if (P.ewald_nk > 0) {
+    COPY(c->d_ek_n, ek_n.data(), ek_n.size());
+    COPY(c->d_ek_A, ek_A.data(), ek_A.size());
+  }
 #undef COPY
   cudaMemset(c->d_cnt2, 0, sizeof(int) * P.ncell);
   cudaMemset(c->d_frc, 0, sizeof(float4) * nslot);
@@ -712,6 +755,12 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.gs_lnk = c->d_gs_lnk;
   P.gs_info = c->d_gs_info;
   P.gs_rank = c->d_gs_rank;
+  P.ek_n = c->d_ek_n;
+  P.ek_A = c->d_ek_A;
+  P.ek_S = c->d_ek_S;
+  P.ek_list = c->d_ek_list;
+  P.ek_np = c->d_ek_np;
+  P.ek_cap = (int)std::max<int64_t>(sys->capacity, 1);
   P.order = nullptr;
   if (!global && P.nact <= ORDER_MAX_NACT) {
     // densest-first launch order, recomputed every sweep; starts as the identity
@@ -985,6 +1034,10 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
       CR_CUDA(launch_domain_order(ctx->d_reps, 1, P.ncol, P.nact, s, swc, k0, k1));
       ctx->launches_total++;
     }
+    if (P.ewald_nk > 0) {  // S(k) from scratch at every sweep
+      CR_CUDA(launch_ewald_sk(ctx->d_reps, 1, P.ewald_nk, s));
+      ctx->launches_total += 2;
+    }
     for (int col = 0; col < P.ncol; ++col) {
       int ti;
       tbegin(ctx, 0, &ti);
@@ -1060,6 +1113,7 @@ extern "C" int cr_sweep_da_log(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr
 
 extern "C" int cr_set_surrogate(cr_ctx *ctx, const cr_mlp *m) {
   if (!ctx || !m || !m->W1 || !m->b1 || !m->W2 || !m->b2 || !m->W3 || !m->b3 || !m->w4) return CR_ERR_INVALID_ARG;
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // the surrogate's features are local
   const SysParams &P0 = ctx->P;
   // the features use the 5^3 stencil of half-cutoff cells inside the phase's region
   if (P0.global || P0.h != 2 || P0.nc < P0.k + 4 || !std::isfinite(m->b4)) return CR_ERR_INVALID_ARG;
@@ -1139,7 +1193,7 @@ static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
 }
 
 extern "C" int cr_md_forces(cr_ctx *ctx) {
-  if (!ctx) return CR_ERR_INVALID_ARG;
+  if (!ctx || ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
   int rc = md_force_eval(ctx, md_params(ctx, 0, 0.0, 0.0, 0));
   if (rc != CR_OK) return rc;
   ctx->fcons_valid = true;
@@ -1148,6 +1202,7 @@ extern "C" int cr_md_forces(cr_ctx *ctx) {
 
 extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed) {
   if (!ctx || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1170,6 +1225,7 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
 
 extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1197,6 +1253,7 @@ static int md_end_impl(cr_ctx *ctx, double dt, double gamma, uint64_t seed, cons
 
 extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   int rc;
   if ((rc = md_end_impl(ctx, dt, gamma, seed, nullptr, 0)) != CR_OK) return rc;
   ctx->md_eval++;
@@ -1551,6 +1608,7 @@ struct cr_batch {
   int *d_pk_type = nullptr, *d_pk_cls = nullptr;
   int8_t *d_pk_state = nullptr;
   bool holds_refs = false;  // the contexts' batch_refs count this batch
+  int ewald_nk_max = 0;     // largest number of Ewald reciprocal vectors over the replicas
 };
 
 // The device address of caller memory the GPU can access directly (device
@@ -1635,12 +1693,15 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
     b->S.nr3 = std::max(b->S.nr3, c->S.nr3);
     b->S.kc3 = std::max(b->S.kc3, c->S.kc3);
     b->S.chunk = std::max(b->S.chunk, c->S.chunk);
+    b->S.ewk = std::max(b->S.ewk, c->S.ewk);
+    b->ewald_nk_max = std::max(b->ewald_nk_max, c->P.ewald_nk);
     b->Sc.dcs = std::max(b->Sc.dcs, c->Sc.dcs);
     b->Sc.hcs = std::max(b->Sc.hcs, c->Sc.hcs);
     b->Sc.lns = std::max(b->Sc.lns, c->Sc.lns);
     b->Sc.nr3 = std::max(b->Sc.nr3, c->Sc.nr3);
     b->Sc.kc3 = std::max(b->Sc.kc3, c->Sc.kc3);
     b->Sc.chunk = std::max(b->Sc.chunk, c->Sc.chunk);
+    b->Sc.ewk = std::max(b->Sc.ewk, c->Sc.ewk);
     b->grid_x = std::max(b->grid_x, c->P.nact);
     maxR = std::max(maxR, c->R);
   }
@@ -1818,6 +1879,10 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
     if (b->order_nc > 0) {
       CR_CUDA(launch_domain_order(b->d_reps, n, b->ncol, b->order_nact, s, swc, k0, k1));
       c0->launches_total++;
+    }
+    if (b->ewald_nk_max > 0) {  // S(k) of every replica from scratch at every sweep
+      CR_CUDA(launch_ewald_sk(b->d_reps, n, b->ewald_nk_max, s));
+      c0->launches_total += 2;
     }
     if (persistent) {
       const int rc = batch_launch_persistent(b, SS, T, R, da, swc, sweep0, k0, k1);
@@ -2064,6 +2129,8 @@ static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
 extern "C" int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t sweep_seed0,
                               uint64_t md_seed0, int32_t da) {
   if (!b || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
+  for (cr_ctx *c : b->ctx)
+    if (c->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
   cr_ctx *c0 = b->ctx[0];
   cudaStream_t s = c0->stream;
   if (da)
@@ -2344,6 +2411,7 @@ extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, in
 namespace crmc {
 
 int ctx_md_forces_into(cr_ctx *ctx, float4 *fout, int *plist, int *n_particles, int max_particles) {
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
   MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
   M.fout = fout;
   CR_CUDA(launch_md_forces(ctx->P, M, plist, n_particles, max_particles, ctx->stream));

@@ -109,6 +109,16 @@ struct SysParams {
   // launch order of each colour's domains, largest region first (ncol x nact),
   // or null for the natural order
   int *order;
+  // Ewald electrostatics (ewald_nk > 0, global schedule): the reciprocal
+  // vectors n (three signed bytes each), their weights A_k = (2 pi lB / V)
+  // exp(-k^2 / (4 alpha^2)) / k^2 (FP32) and S(k) of the state (FP64 re, im)
+  int ewald_nk, ewald_kmax;
+  const int *ek_n;
+  const float *ek_A;
+  double *ek_S;
+  double invLd;  // 1 / L in FP64
+  int *ek_list, *ek_np;  // occupied slots (the structure-factor kernel's particle list) and their number
+  int ek_cap;            // entries of ek_list (the capacity in particles)
 };
 
 // domains are launched densest first for colours of at most this many domains
@@ -133,6 +143,7 @@ struct PhaseShape {
   int nr3;     // region cells
   int kc3;     // domain cells
   int chunk;   // trials whose random numbers are drawn at once (min(m, TRIAL_CHUNK))
+  int ewk;     // Ewald: kmax + 1 phase factors per axis and changed particle (0 without Ewald)
 };
 
 // error bits in *err

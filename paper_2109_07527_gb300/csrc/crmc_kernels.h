@@ -147,6 +147,10 @@ size_t state_sort_temp_bytes(int cap);
 // per-context path; err_out[r] its error word
 cudaError_t launch_state_batch(const SysParams *d_reps, const StateBufs *d_bufs, int n_rep, int max_slots,
                                int max_cap, long long *d_n_out, int *d_err_out, cudaStream_t s);
+// Ewald: S(k) of every replica of a batch from scratch (the occupied slots
+// listed, then one thread per reciprocal vector); max_nk: the largest
+// number of reciprocal vectors over the replicas
+cudaError_t launch_ewald_sk(const SysParams *d_reps, int n_rep, int max_nk, cudaStream_t s);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                           uint4 *out, cudaStream_t s);
 

@@ -68,6 +68,7 @@ struct TrialCtl {
   // delayed acceptance: in-domain cell ranks of a and b, charge and presence
   // changes, feature group of a (0 ion, 8 site), stage-1 outcome
   int rka, rkb, dqa, dqb, eta_a, eta_b, cat_a, go;
+  int ewacc;             // Ewald: the trial was accepted (S(k) follows)
   float sur;             // surrogate dE~ (DA)
   long long sur_fx;      // dE~ clamped, 2^-48 fixed point (DA)
 };
@@ -923,6 +924,89 @@ __device__ __forceinline__ void sweep_pairs(const PairK &K, const WcaEntry *wca,
   }
 }
 
+// ---- Ewald reciprocal part (global schedule): the change of
+// sum_k A_k |S(k)|^2 when the changed particles' charges dq enter S(k).  The
+// phase exp(i 2 pi n u), u = x / L, is reduced exactly in integers: U = u in
+// 0.32 fixed point (FP64), n U mod 2^32 is the fraction of n u; FP32 sincospi
+// of that fraction gives the factor.  A reciprocal vector's factor is the
+// product of its three axes' factors (the conjugate for negative n).
+__device__ __forceinline__ uint32_t ew_frac32(float x, double invL) {
+  return (uint32_t)(unsigned long long)llrint((double)x * invL * 4294967296.0);
+}
+__device__ __forceinline__ float2 ew_factor(uint32_t U, int n) {
+  const uint32_t t = (uint32_t)n * U;
+  float sn, cs;
+  sincospif((float)t * (2.0f / 4294967296.0f), &sn, &cs);
+  return make_float2(cs, sn);
+}
+__device__ __forceinline__ float2 ew_cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 ew_axis(const float2 *f, int n) {
+  const float2 v = f[n < 0 ? -n : n];
+  return make_float2(v.x, n < 0 ? -v.y : v.y);
+}
+__device__ __forceinline__ void ew_decode(int code, int &nx, int &ny, int &nz) {
+  nx = (int)(signed char)(code & 255);
+  ny = (int)(signed char)((code >> 8) & 255);
+  nz = (int)(signed char)((code >> 16) & 255);
+}
+
+// the axis factors of the trial's two changed particles (f[c][axis][n], n <=
+// kmax) and their charge changes dq[c] (0 where absent); threads tid of T
+__device__ __noinline__ void ewald_factors(const SysParams &P, const TrialCtl &C, float2 *f, float *dq, int ewk, int tid,
+                                           int T) {
+  for (int i = tid; i < 6 * ewk; i += T) {
+    const int c = i / (3 * ewk), ax = (i / ewk) % 3, n = i % ewk;
+    const Desc &D = C.c[c];
+    const float x = ax == 0 ? D.x : (ax == 1 ? D.y : D.z);
+    f[i] = ew_factor(ew_frac32(x, P.invLd), n);
+  }
+  if (tid == 0) {
+    dq[0] = (C.pa_n ? C.qa_n : 0.0f) - (C.pa_o ? C.qa_o : 0.0f);
+    dq[1] = (C.pb_n ? C.qb_n : 0.0f) - (C.pb_o ? C.qb_o : 0.0f);
+  }
+}
+
+// dS(k) of the trial for reciprocal vector i
+__device__ __forceinline__ float2 ewald_dS(const SysParams &P, const float2 *f, const float *dq, int ewk, int i) {
+  int nx, ny, nz;
+  ew_decode(P.ek_n[i], nx, ny, nz);
+  const float2 ea = ew_cmul(ew_cmul(ew_axis(f, nx), ew_axis(f + ewk, ny)), ew_axis(f + 2 * ewk, nz));
+  const float2 eb = ew_cmul(ew_cmul(ew_axis(f + 3 * ewk, nx), ew_axis(f + 4 * ewk, ny)), ew_axis(f + 5 * ewk, nz));
+  return make_float2(dq[0] * ea.x + dq[1] * eb.x, dq[0] * ea.y + dq[1] * eb.y);
+}
+
+// this thread's share of the reciprocal energy change, into 2^-32 fixed point
+template <bool WITH_S>
+__device__ __noinline__ PairSum ewald_dE(const SysParams &P, const float2 *f, const float *dq, int ewk, int tid,
+                                         int T) {
+  PairSum out{0, 0ull, 0};
+  for (int i = tid; i < P.ewald_nk; i += T) {
+    const float2 d = ewald_dS(P, f, dq, ewk, i);
+    const float sr = (float)P.ek_S[2 * i], si = (float)P.ek_S[2 * i + 1];
+    const float term = P.ek_A[i] * (2.0f * (sr * d.x + si * d.y) + (d.x * d.x + d.y * d.y));
+    if (!(fabsf(term) < BIG_TERM)) {
+      out.ov = 1;
+    } else {
+      out.acc += fix32(term);
+      if (WITH_S) out.sacc += (unsigned long long)fix32(fabsf(term));
+    }
+  }
+  return out;
+}
+
+// an accepted trial: S(k) += dS(k) for this thread's reciprocal vectors (the
+// same vectors ewald_dE gave it)
+__device__ __noinline__ void ewald_update(const SysParams &P, const float2 *f, const float *dq, int ewk, int tid,
+                                          int T) {
+  for (int i = tid; i < P.ewald_nk; i += T) {
+    const float2 d = ewald_dS(P, f, dq, ewk, i);
+    P.ek_S[2 * i] += (double)d.x;
+    P.ek_S[2 * i + 1] += (double)d.y;
+  }
+}
+
 // room for the ions an accepted insertion adds: their cells below the cell
 // capacity and the list below its capacity (belowA / sameA: entries of the
 // list before and in the first ion's cell, where it goes)
@@ -1083,6 +1167,9 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
   int *dcnt = (int *)take(sizeof(int) * (S.kc3 + 1));
   int *dpre = (int *)take(sizeof(int) * (S.kc3 + 1));
   float *qr2 = qbuf + warp * 2 * QCAP, *qqp = qr2 + QCAP;
+  // Ewald: the changed particles' axis factors and charge changes
+  float2 *ewf = (float2 *)take(sizeof(float2) * 6 * S.ewk);
+  float *ewq = (float *)take(sizeof(float) * 4);
   // delayed acceptance: region cell aggregates (ion charge, site charge,
   // particles), feature bins, the two surrogate inputs and hidden layers
   int *aQi = nullptr, *aQs = nullptr, *aN = nullptr, *dfeat = nullptr;
@@ -1267,6 +1354,12 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
       // shared memory (*ctl) across the sweep
       if (warp == 0) select_trial<DA>(P, L, misc, lnt, tp[t], d, m, kk, phi, *ctl);
       cta_sync<T>();
+      // Ewald (global schedule): the changed particles' phase factors
+      const bool ew = !DA && P.ewald_nk > 0 && ctl->nch;
+      if (ew) {
+        ewald_factors(P, *ctl, ewf, ewq, S.ewk, tid, T);
+        cta_sync<T>();
+      }
       // ---- delayed acceptance, stage 1: surrogate features and MLP (all
       // threads), decision in warp 0; a rejection skips the pair sweep
       if (DA && ctl->nch) {
@@ -1362,6 +1455,12 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
           sacc += cc.sacc;
           ov |= cc.ov;
         }
+        if (ew) {
+          const PairSum e = ewald_dE<LOG>(P, ewf, ewq, S.ewk, tid, T);
+          acc += e.acc;
+          sacc += e.sacc;
+          ov |= e.ov;
+        }
         acc = warp_allsum(acc);
         if (LOG) sacc = (unsigned long long)warp_allsum((long long)sacc);
         ov = __any_sync(FULL, ov) ? 1 : 0;
@@ -1427,6 +1526,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
         }
         (void)r;
         (void)fwd;
+        if (lane == 0) ctl->ewacc = accept ? 1 : 0;
         if (accept) {
           flags |= CR_TRIAL_ACCEPTED;
           if (DA && lane == 0) {  // region aggregates follow the committed change
@@ -1476,6 +1576,7 @@ __device__ __forceinline__ void phase_task(unsigned char *smem, const SysParams 
         }
       }
       cta_sync<T>();
+      if (ew && ctl->ewacc) ewald_update(P, ewf, ewq, S.ewk, tid, T);
     }
   }
   // ---- write the domain back (id-sorted cells) and publish counts
@@ -1773,6 +1874,98 @@ cudaError_t launch_domain_order(const SysParams *d_reps, int n_rep, int ncol, in
 }
 
 // ---------------------------------------------------------------------------
+// Ewald structure factor S(k) = sum_j q_j exp(i k.r_j) of every replica from
+// scratch (at every sweep): k_ewald_list lists each replica's occupied slots
+// (one CTA per replica, cells in order), k_ewald_sk gives each reciprocal
+// vector a thread, the particles in tiles of 32 whose axis factors the CTA
+// computes together in shared memory (FP32 products summed per tile, tiles
+// summed in FP64).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ewald_list(const SysParams *__restrict__ reps) {
+  const SysParams &P = reps[blockIdx.x];
+  if (P.ewald_nk <= 0) return;
+  __shared__ int warp_tot[8];
+  __shared__ int base_s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < P.ncell; c0 += 256) {
+    const int c = c0 + (int)threadIdx.x;
+    const int n = c < P.ncell ? P.cnt[c] : 0;
+    int x = n;  // inclusive scan over the CTA
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    int before = base_s;
+    for (int i = 0; i < w; ++i) before += warp_tot[i];
+    const int start = before + x - n;
+    for (int sl = 0; sl < n; ++sl) {
+      if (start + sl < P.ek_cap) P.ek_list[start + sl] = c * P.cap + sl;
+      else atomicOr(P.err, ERRB_CAPACITY);  // more particles than the context's capacity
+    }
+    __syncthreads();
+    if (threadIdx.x == 255) base_s = start + n;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *P.ek_np = min(base_s, P.ek_cap);
+}
+
+constexpr int EW_TILE = 32;
+constexpr int EW_KMAX = 32;
+
+__global__ void __launch_bounds__(256) k_ewald_sk(const SysParams *__restrict__ reps) {
+  const SysParams &P = reps[blockIdx.y];
+  const int nk = P.ewald_nk;
+  if (nk <= 0 || (int)blockIdx.x * 256 >= nk) return;  // uniform over the CTA
+  __shared__ float2 fac[EW_TILE][3][EW_KMAX + 1];
+  __shared__ float qt[EW_TILE];
+  const int ewk = P.ewald_kmax + 1, np = *P.ek_np;
+  const int i = (int)blockIdx.x * 256 + (int)threadIdx.x;
+  int nx = 0, ny = 0, nz = 0;
+  if (i < nk) ew_decode(P.ek_n[i], nx, ny, nz);
+  double re = 0.0, im = 0.0;
+  for (int t0 = 0; t0 < np; t0 += EW_TILE) {
+    const int nt = min(EW_TILE, np - t0);
+    for (int v = threadIdx.x; v < nt * 3 * ewk; v += 256) {
+      const int p = v / (3 * ewk), ax = (v / ewk) % 3, n = v % ewk;
+      const float4 r = P.pos[P.ek_list[t0 + p]];
+      const float x = ax == 0 ? r.x : (ax == 1 ? r.y : r.z);
+      fac[p][ax][n] = ew_factor(ew_frac32(x, P.invLd), n);
+    }
+    if (threadIdx.x < nt) qt[threadIdx.x] = P.pos[P.ek_list[t0 + threadIdx.x]].w;
+    __syncthreads();
+    if (i < nk) {
+      float tr = 0.0f, ti = 0.0f;
+      for (int p = 0; p < nt; ++p) {
+        const float q = qt[p];
+        if (q == 0.0f) continue;
+        const float2 e = ew_cmul(ew_cmul(ew_axis(fac[p][0], nx), ew_axis(fac[p][1], ny)), ew_axis(fac[p][2], nz));
+        tr += q * e.x;
+        ti += q * e.y;
+      }
+      re += (double)tr;
+      im += (double)ti;
+    }
+    __syncthreads();
+  }
+  if (i < nk) {
+    P.ek_S[2 * i] = re;
+    P.ek_S[2 * i + 1] = im;
+  }
+}
+
+cudaError_t launch_ewald_sk(const SysParams *d_reps, int n_rep, int max_nk, cudaStream_t s) {
+  if (n_rep <= 0 || max_nk <= 0) return cudaSuccess;
+  k_ewald_list<<<n_rep, 256, 0, s>>>(d_reps);
+  k_ewald_sk<<<dim3((unsigned)((max_nk + 255) / 256), (unsigned)n_rep), 256, 0, s>>>(d_reps);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
@@ -1799,7 +1992,9 @@ size_t phase_smem_bytes(const PhaseShape &S, int threads, bool da) {
                           sizeof(int) * (S.nr3 + 1),
                           sizeof(int) * (S.nr3 + 1),
                           sizeof(int) * (S.kc3 + 1),
-                          sizeof(int) * (S.kc3 + 1)};
+                          sizeof(int) * (S.kc3 + 1),
+                          sizeof(float2) * 6 * S.ewk,
+                          sizeof(float) * 4};
   size_t b = 0;
   for (size_t x : sizes) b += (x + 15) / 16 * 16;
   if (da) {

@@ -40,15 +40,23 @@ def grand_reaction_invocations(pH: float, pIS_plus: float, pIS_minus: float, pKw
             ((XP, SM, pH, pIS_minus, 4), 1), ((SP, XM, pIS_plus, pOH, 4), 1)]
 
 
-def compare_convergence(crmc, n_rep=64, blocks=40, m=250, n_acid=500, seed=1, methods=("crmc", "grxmc", "rxmc")):
+def compare_convergence(crmc, n_rep=64, blocks=40, m=250, n_acid=500, seed=1, methods=("crmc", "grxmc", "rxmc"),
+                        ewald_kmax=0):
     """alpha(trials) of the weak-acid electrolyte (Sec. III.A) under each
     method.  A block is 6 x m trials per replica (6 batch sweeps of m trials:
     all moves of CR-MC and RxMC; the grand-reaction invocations in the shares
-    2:2:1:1).  Returns {"trials": [...], method: mean alpha per block, method +
-    "_se": its standard error over the replicas}."""
+    2:2:1:1).  ewald_kmax > 0: Ewald electrostatics (the paper's PPPM energy,
+    as a direct Ewald sum with reciprocal vectors |n| <= ewald_kmax) instead of
+    DSF.  Returns {"trials": [...], method: mean alpha per block, method +
+    "_se": its standard error over the replicas, method + "_sweep_s": the
+    wall time of its batch sweeps in the second half of the blocks, after the
+    launch-shape tuner's sweeps}."""
+    import time
     out = {"trials": [6 * m * (b + 1) for b in range(blocks)]}
     for method in methods:
         ws = [W.weak_acid_electrolyte(n_acid=n_acid, seed=seed + r, trials_per_domain=m) for r in range(n_rep)]
+        for w in ws:
+            w.params["ewald_kmax"] = int(ewald_kmax)
         ctxs = [crmc.Context(w) for w in ws]
         b = crmc.Batch(ctxs)
         pH = float(ws[0].params["pH"])
@@ -59,7 +67,9 @@ def compare_convergence(crmc, n_rep=64, blocks=40, m=250, n_acid=500, seed=1, me
         inv = grand_reaction_invocations(pH, *pS, reactions=1)
         alpha = np.zeros((blocks, n_rep))
         k = 0
+        t_sweep = 0.0
         for blk in range(blocks):
+            t0 = time.perf_counter()
             if method == "grxmc":
                 for args, share in inv:
                     for c in ctxs:
@@ -69,6 +79,9 @@ def compare_convergence(crmc, n_rep=64, blocks=40, m=250, n_acid=500, seed=1, me
             else:
                 b.sweep(6, 7919 * seed + k)
                 k += 1
+            ctxs[0].check()  # the batch's stream is synchronised: the sweeps are done
+            if blk >= blocks // 2:
+                t_sweep += time.perf_counter() - t0
             for r, c in enumerate(ctxs):
                 alpha[blk, r] = c.counts()["alpha"]
         for c in ctxs:
@@ -77,5 +90,6 @@ def compare_convergence(crmc, n_rep=64, blocks=40, m=250, n_acid=500, seed=1, me
         for c in ctxs:
             c.close()
         out[method] = alpha.mean(axis=1).tolist()
+        out[method + "_sweep_s"] = t_sweep
         out[method + "_se"] = (alpha.std(axis=1, ddof=1) / np.sqrt(n_rep)).tolist()
     return out

@@ -1,0 +1,84 @@
+"""Ewald electrostatics on the GPU (the paper's PPPM energy model, Sec. III.A,
+evaluated as a direct Ewald sum) under the global schedule, trial by trial
+against the oracle: moves, chosen ids and decisions identical, Delta E within
+1e-6 of the gross term sum (the reciprocal part's FP32 terms and structure-
+factor updates included), final states identical; batches of replicas equal
+the per-replica oracle runs; MD, delayed acceptance and the coloured schedule
+are refused with Ewald."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_07527_gb300 import workloads as W
+from parity_util import compare_logs, compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def crmc():
+    from paper_2109_07527_gb300 import crmc as m
+    m._lib()
+    return m
+
+
+def _replica_seed(seed, r):
+    return seed ^ (r << 32)
+
+
+def _electrolyte(n_acid=30, L=20.0, rc=8.0, alpha=0.4, kmax=6, m=50, seed=3, pH=7.0):
+    w = W.weak_acid_electrolyte(n_acid=n_acid, L=L, pH=pH, pKa=6.5, pIS=2.0, rc=rc, seed=seed,
+                                trials_per_domain=m, alpha=alpha)
+    w.params["ewald_kmax"] = kmax
+    return w
+
+
+@pytest.mark.parametrize("kmax,threads", [(6, 128), (6, 512), (12, 256)])
+def test_ewald_trials_match_the_oracle(crmc, kmax, threads):
+    w = _electrolyte(kmax=kmax)
+    g = crmc.Context(w)
+    g.set_launch_shape(threads, 0)
+    n = g.trials_per_sweep * 8
+    lg = g.sweep(n, 41, log=True)["log"]
+    o, lo, ties = compare_logs(w, lg, n, 41)
+    compare_states(g, o, w.n_sites)
+    acc = (lo["flags"] & oracle.F_ACC) != 0
+    assert acc.sum() > 20 and ties <= 2
+
+
+def test_ewald_paper_electrolyte_box(crmc):
+    """The method comparison's weak-acid electrolyte (500 acids, L = 50 l_B,
+    r_c = 10 l_B) with a reciprocal sum over |n| <= 10."""
+    w = _electrolyte(n_acid=500, L=100.0, rc=20.0, alpha=0.16, kmax=10, m=200, seed=1)
+    g = crmc.Context(w)
+    n = g.trials_per_sweep * 3
+    lg = g.sweep(n, 5, log=True)["log"]
+    o, lo, ties = compare_logs(w, lg, n, 5)
+    compare_states(g, o, w.n_sites)
+
+
+def test_ewald_batch_matches_oracle(crmc):
+    ws = [_electrolyte(seed=s, pH=pH) for s, pH in ((5, 5.0), (6, 7.0), (7, 9.0))]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(5, 88)
+    for r, (w, g) in enumerate(zip(ws, ctxs)):
+        o = oracle.Oracle(w)
+        o.sweep(o.trials_per_sweep * 5, _replica_seed(88, r))
+        compare_states(g, o, w.n_sites)
+    b.close()
+
+
+def test_ewald_refusals(crmc):
+    w = _electrolyte()
+    with pytest.raises(crmc.CrError) as e:
+        crmc.Context(w, schedule=crmc.SCHED_COLOURED)
+    assert e.value.code == -1
+    g = crmc.Context(w)
+    for f in (lambda: g.md_forces(), lambda: g.md_step(1, 0.005, 1.0, 1), lambda: g.md_begin(0.005, 1.0, 1),
+              lambda: g.set_surrogate(W.random_mlp(seed=1))):
+        with pytest.raises(crmc.CrError) as e:
+            f()
+        assert e.value.code == -1
+    g.sweep(g.trials_per_sweep, 3)  # the context still works
+    g.close()
