@@ -120,9 +120,8 @@ struct cr_ctx {
   int64_t launches[2] = {0, 0};
   int64_t launches_total = 0;
   // Ewald electrostatics: reciprocal vectors, weights, structure factor
-  int *d_ek_n = nullptr;
-  float *d_ek_A = nullptr;
-  double *d_ek_S = nullptr;
+  int2 *d_ek_nA = nullptr;
+  float2 *d_ek_Shi = nullptr, *d_ek_Slo = nullptr;
   int *d_ek_list = nullptr, *d_ek_np = nullptr;
   // caller-owned slot arrays (cr_bind_device_buffers) and batch membership
   bool bound = false;
@@ -210,7 +209,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
                   c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order,
-                  c->d_ek_n, c->d_ek_A, c->d_ek_S, c->d_ek_list, c->d_ek_np};
+                  c->d_ek_nA, c->d_ek_Shi, c->d_ek_Slo, c->d_ek_list, c->d_ek_np};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_small) cudaFreeHost(c->h_small);
@@ -391,8 +390,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.lB_self = sys->dsf_self ? lB * (-(erc / (2.0 * rc) + alpha / std::sqrt(M_PI))) : 0.0;
   // Ewald electrostatics (global schedule only): the real-space term without
   // the DSF shift, the Ewald self term, the reciprocal vectors and weights
-  std::vector<int> ek_n;
-  std::vector<float> ek_A;
+  std::vector<int2> ek_nA;
   if (sys->ewald_kmax < 0 || sys->ewald_kmax > 32) { free_ctx(c); return CR_ERR_INVALID_ARG; }
   if (sys->ewald_kmax > 0) {
     if (!global) { free_ctx(c); return CR_ERR_INVALID_ARG; }
@@ -406,13 +404,17 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
         for (int nx = -km; nx <= km; ++nx) {
           const int n2 = nx * nx + ny * ny + nz * nz;
           if (!(n2 > 0 && n2 <= km * km)) continue;
+          // one half space: -k contributes the same term (S(-k) = conj S(k))
+          if (!(nx > 0 || (nx == 0 && (ny > 0 || (ny == 0 && nz > 0))))) continue;
           const double k2 = kf * kf * n2;
-          ek_n.push_back((nx & 255) | ((ny & 255) << 8) | ((nz & 255) << 16));
-          ek_A.push_back((float)(2.0 * M_PI * lB / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2));
+          const float A = (float)(2.0 * 2.0 * M_PI * lB / V * std::exp(-k2 / (4.0 * alpha * alpha)) / k2);
+          int Ab;
+          std::memcpy(&Ab, &A, sizeof Ab);
+          ek_nA.push_back(make_int2((nx & 255) | ((ny & 255) << 8) | ((nz & 255) << 16), Ab));
         }
   }
   P.ewald_kmax = sys->ewald_kmax;
-  P.ewald_nk = (int)ek_n.size();
+  P.ewald_nk = (int)ek_nA.size();
   P.invLd = 1.0 / L;
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
@@ -690,9 +692,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_nparts, 1);
   ALLOC(c->d_fsum, 3 * (size_t)std::max(sys->capacity, 1));
   if (P.ewald_nk > 0) {
-    ALLOC(c->d_ek_n, (size_t)P.ewald_nk);
-    ALLOC(c->d_ek_A, (size_t)P.ewald_nk);
-    ALLOC(c->d_ek_S, 2 * (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_nA, (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_Shi, (size_t)P.ewald_nk);
+    ALLOC(c->d_ek_Slo, (size_t)P.ewald_nk);
     ALLOC(c->d_ek_list, (size_t)std::max(sys->capacity, 1));
     ALLOC(c->d_ek_np, 1);
   }
@@ -728,8 +730,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   if (n > 0) COPY(c->d_site_map, site_of.data(), (size_t)n);
   if (n > 0) COPY(c->d_init_type, sys->type, (size_t)n);
   if (P.ewald_nk > 0) {
-    COPY(c->d_ek_n, ek_n.data(), ek_n.size());
-    COPY(c->d_ek_A, ek_A.data(), ek_A.size());
+    COPY(c->d_ek_nA, ek_nA.data(), ek_nA.size());
   }
 #undef COPY
   cudaMemset(c->d_cnt2, 0, sizeof(int) * P.ncell);
@@ -755,9 +756,9 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.gs_lnk = c->d_gs_lnk;
   P.gs_info = c->d_gs_info;
   P.gs_rank = c->d_gs_rank;
-  P.ek_n = c->d_ek_n;
-  P.ek_A = c->d_ek_A;
-  P.ek_S = c->d_ek_S;
+  P.ek_nA = c->d_ek_nA;
+  P.ek_Shi = c->d_ek_Shi;
+  P.ek_Slo = c->d_ek_Slo;
   P.ek_list = c->d_ek_list;
   P.ek_np = c->d_ek_np;
   P.ek_cap = (int)std::max<int64_t>(sys->capacity, 1);

@@ -110,12 +110,14 @@ struct SysParams {
   // or null for the natural order
   int *order;
   // Ewald electrostatics (ewald_nk > 0, global schedule): the reciprocal
-  // vectors n (three signed bytes each), their weights A_k = (2 pi lB / V)
-  // exp(-k^2 / (4 alpha^2)) / k^2 (FP32) and S(k) of the state (FP64 re, im)
+  // vectors n of one half space (three signed bytes each; S(-k) is the
+  // conjugate of S(k), so -k adds the same term) with their weights
+  // 2 A_k = 2 (2 pi lB / V) exp(-k^2 / (4 alpha^2)) / k^2 (FP32), and S(k) of
+  // the state as an unevaluated sum hi + lo of two FP32 complex numbers
+  // (about 48 bits; the trials read hi)
   int ewald_nk, ewald_kmax;
-  const int *ek_n;
-  const float *ek_A;
-  double *ek_S;
+  const int2 *ek_nA;  // (n code, weight bits) of each reciprocal vector
+  float2 *ek_Shi, *ek_Slo;
   double invLd;  // 1 / L in FP64
   int *ek_list, *ek_np;  // occupied slots (the structure-factor kernel's particle list) and their number
   int ek_cap;            // entries of ek_list (the capacity in particles)

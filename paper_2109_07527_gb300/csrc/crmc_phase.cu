@@ -968,32 +968,59 @@ __device__ __noinline__ void ewald_factors(const SysParams &P, const TrialCtl &C
   }
 }
 
-// dS(k) of the trial for reciprocal vector i
-__device__ __forceinline__ float2 ewald_dS(const SysParams &P, const float2 *f, const float *dq, int ewk, int i) {
+// dS(k) of the trial for the reciprocal vector of code `code`
+__device__ __forceinline__ float2 ewald_dS(const float2 *f, const float *dq, int ewk, int code) {
   int nx, ny, nz;
-  ew_decode(P.ek_n[i], nx, ny, nz);
+  ew_decode(code, nx, ny, nz);
   const float2 ea = ew_cmul(ew_cmul(ew_axis(f, nx), ew_axis(f + ewk, ny)), ew_axis(f + 2 * ewk, nz));
   const float2 eb = ew_cmul(ew_cmul(ew_axis(f + 3 * ewk, nx), ew_axis(f + 4 * ewk, ny)), ew_axis(f + 5 * ewk, nz));
   return make_float2(dq[0] * ea.x + dq[1] * eb.x, dq[0] * ea.y + dq[1] * eb.y);
 }
 
 // this thread's share of the reciprocal energy change, into 2^-32 fixed point
+// (vectors tid, tid + T, ...; four loaded ahead at a time)
 template <bool WITH_S>
 __device__ __noinline__ PairSum ewald_dE(const SysParams &P, const float2 *f, const float *dq, int ewk, int tid,
                                          int T) {
   PairSum out{0, 0ull, 0};
-  for (int i = tid; i < P.ewald_nk; i += T) {
-    const float2 d = ewald_dS(P, f, dq, ewk, i);
-    const float sr = (float)P.ek_S[2 * i], si = (float)P.ek_S[2 * i + 1];
-    const float term = P.ek_A[i] * (2.0f * (sr * d.x + si * d.y) + (d.x * d.x + d.y * d.y));
-    if (!(fabsf(term) < BIG_TERM)) {
-      out.ov = 1;
-    } else {
-      out.acc += fix32(term);
-      if (WITH_S) out.sacc += (unsigned long long)fix32(fabsf(term));
+  const int nk = P.ewald_nk;
+  const int2 *nA = P.ek_nA;
+  const float2 *S32 = P.ek_Shi;
+  for (int i0 = tid; i0 < nk; i0 += 4 * T) {
+    int2 v[4];
+    float2 sv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * T;
+      v[u] = i < nk ? nA[i] : make_int2(0, 0);
+      sv[u] = i < nk ? S32[i] : make_float2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (i0 + u * T >= nk) continue;
+      const float2 d = ewald_dS(f, dq, ewk, v[u].x);
+      const float term = __int_as_float(v[u].y) * (2.0f * (sv[u].x * d.x + sv[u].y * d.y) + (d.x * d.x + d.y * d.y));
+      if (!(fabsf(term) < BIG_TERM)) {
+        out.ov = 1;
+      } else {
+        out.acc += fix32(term);
+        if (WITH_S) out.sacc += (unsigned long long)fix32(fabsf(term));
+      }
     }
   }
   return out;
+}
+
+// hi + lo += d in FP32 with the rounding error kept (Knuth's two-sum, then
+// Dekker's fast two-sum to renormalise: hi stays the FP32 value of the sum)
+__device__ __forceinline__ void ew_add2(float &hi, float &lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+  const float l = __fadd_rn(lo, err);
+  const float h = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(h, s));
+  hi = h;
 }
 
 // an accepted trial: S(k) += dS(k) for this thread's reciprocal vectors (the
@@ -1001,9 +1028,12 @@ __device__ __noinline__ PairSum ewald_dE(const SysParams &P, const float2 *f, co
 __device__ __noinline__ void ewald_update(const SysParams &P, const float2 *f, const float *dq, int ewk, int tid,
                                           int T) {
   for (int i = tid; i < P.ewald_nk; i += T) {
-    const float2 d = ewald_dS(P, f, dq, ewk, i);
-    P.ek_S[2 * i] += (double)d.x;
-    P.ek_S[2 * i + 1] += (double)d.y;
+    const float2 d = ewald_dS(f, dq, ewk, P.ek_nA[i].x);
+    float2 hi = P.ek_Shi[i], lo = P.ek_Slo[i];
+    ew_add2(hi.x, lo.x, d.x);
+    ew_add2(hi.y, lo.y, d.y);
+    P.ek_Shi[i] = hi;
+    P.ek_Slo[i] = lo;
   }
 }
 
@@ -1923,20 +1953,25 @@ __global__ void __launch_bounds__(256) k_ewald_sk(const SysParams *__restrict__ 
   if (nk <= 0 || (int)blockIdx.x * 256 >= nk) return;  // uniform over the CTA
   __shared__ float2 fac[EW_TILE][3][EW_KMAX + 1];
   __shared__ float qt[EW_TILE];
+  __shared__ uint32_t ut[EW_TILE][3];
   const int ewk = P.ewald_kmax + 1, np = *P.ek_np;
   const int i = (int)blockIdx.x * 256 + (int)threadIdx.x;
   int nx = 0, ny = 0, nz = 0;
-  if (i < nk) ew_decode(P.ek_n[i], nx, ny, nz);
+  if (i < nk) ew_decode(P.ek_nA[i].x, nx, ny, nz);
   double re = 0.0, im = 0.0;
   for (int t0 = 0; t0 < np; t0 += EW_TILE) {
     const int nt = min(EW_TILE, np - t0);
+    if (threadIdx.x < 3 * nt) {  // the tile's coordinates as 0.32 fixed-point fractions of L
+      const int p = threadIdx.x / 3, ax = threadIdx.x % 3;
+      const float4 r = P.pos[P.ek_list[t0 + p]];
+      ut[p][ax] = ew_frac32(ax == 0 ? r.x : (ax == 1 ? r.y : r.z), P.invLd);
+      if (ax == 0) qt[p] = r.w;
+    }
+    __syncthreads();
     for (int v = threadIdx.x; v < nt * 3 * ewk; v += 256) {
       const int p = v / (3 * ewk), ax = (v / ewk) % 3, n = v % ewk;
-      const float4 r = P.pos[P.ek_list[t0 + p]];
-      const float x = ax == 0 ? r.x : (ax == 1 ? r.y : r.z);
-      fac[p][ax][n] = ew_factor(ew_frac32(x, P.invLd), n);
+      fac[p][ax][n] = ew_factor(ut[p][ax], n);
     }
-    if (threadIdx.x < nt) qt[threadIdx.x] = P.pos[P.ek_list[t0 + threadIdx.x]].w;
     __syncthreads();
     if (i < nk) {
       float tr = 0.0f, ti = 0.0f;
@@ -1953,8 +1988,9 @@ __global__ void __launch_bounds__(256) k_ewald_sk(const SysParams *__restrict__ 
     __syncthreads();
   }
   if (i < nk) {
-    P.ek_S[2 * i] = re;
-    P.ek_S[2 * i + 1] = im;
+    const float hr = (float)re, hm = (float)im;
+    P.ek_Shi[i] = make_float2(hr, hm);
+    P.ek_Slo[i] = make_float2((float)(re - (double)hr), (float)(im - (double)hm));
   }
 }
 
