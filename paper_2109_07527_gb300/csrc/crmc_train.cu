@@ -2,8 +2,13 @@
 // 48 -> 128 -> 128 -> 128 -> 1, ReLU) by mean squared error with Adam, on the
 // fifth-generation tensor cores of sm_103a.
 //
-// Every matrix product of the forward and backward passes is one launch of
-// k_mma: D[M x N] = A[M x K] B[N x K]^T with BF16 operands that TMA stages
+// The training step runs as one kernel, k_train_fused (below): each SM's CTA
+// takes its share of the batch's 128-row tiles through every product of the
+// step on the tensor cores with the weights resident in shared memory, and
+// k_sum_adam sums the CTAs' partial gradients in order and applies Adam.
+// The unfused form (cr_train_cfg.unfused) and the exposed product
+// cr_mma_bf16 use k_mma, one launch per product:
+// D[M x N] = A[M x K] B[N x K]^T with BF16 operands that TMA stages
 // into 128-byte-swizzled shared memory (a 4-deep ring of 64-wide K slices),
 // tcgen05.mma (cta_group::1, M = 128) accumulating FP32 in tensor memory,
 // and an epilogue that reads the accumulator with tcgen05.ld and applies
