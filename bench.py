@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-fig2", action="store_true")
     ap.add_argument("--train-only", action="store_true",
                     help="time only the surrogate's training step (batch 32,768, synthetic features) and exit")
+    ap.add_argument("--ewald-only", action="store_true",
+                    help="time only CR-MC sweeps with Ewald electrostatics (the 500-acid box of the method "
+                         "comparison, 64 replicas, |n| <= 16, global schedule) and exit")
     return ap.parse_args()
 
 
@@ -548,6 +551,42 @@ def run_train_only(args):
     tr.close()
 
 
+def run_ewald_only(args):
+    """CR-MC sweeps of the method comparison's weak-acid electrolyte under
+    Ewald electrostatics (|n| <= 16, alpha = 0.15/sigma, r_c = 10 l_B; global
+    schedule): 64 replicas in one batch, the launch shape tuned first, then
+    `steps` sweeps of 250 trials per replica timed with CUDA events between
+    profiler start / stop (a short program for profiling the Ewald trials)."""
+    import torch
+    from paper_2109_07527_gb300 import crmc, workloads as W
+    n_rep, m = 64, 250
+    ws = [W.weak_acid_electrolyte(n_acid=500, seed=1 + r, trials_per_domain=m) for r in range(n_rep)]
+    for w in ws:
+        w.params["ewald_kmax"] = 16
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(BATCH_TUNE_SWEEPS + max(3, args.warmup), 11)  # the tuner's sweeps and the warm-up
+    ctxs[0].check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record(stream)
+    b.sweep(args.steps, 12)
+    e1.record(stream)
+    torch.cuda.profiler.stop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ctxs[0].check()
+    print(json.dumps({"metric": "CR-MC trials/s with Ewald electrostatics (global schedule)",
+                      "value": n_rep * m / (ms / 1e3), "unit": "trials/s", "steps": args.steps,
+                      "ms_per_sweep": ms, "replicas": n_rep, "trials_per_sweep": m,
+                      "launch_shape": list(b.launch_shape()),
+                      "alpha_end": float(np.mean([c.counts()["alpha"] for c in ctxs]))}), flush=True)
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
 def run_config4(crmc, torch, stream, flush, steps):
     """The batched titration: 64 replicas, chain lengths log-uniform in
     [50, 1000], pH uniform in [2, 10], boxes at 10^-3 monomers per sigma^3
@@ -780,5 +819,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.train_only:
         run_train_only(a)
+    elif a.ewald_only:
+        run_ewald_only(a)
     else:
         run_ours(a)
