@@ -2247,31 +2247,28 @@ extern "C" int cr_batch_state_packed(cr_batch *b, cr_batch_packed *p) {
   }
   if (p->stride < capmax) return CR_ERR_INVALID_ARG;
   const int64_t S = p->stride;
-  if (capmax > STATE_BLOCK_SORT_MAX) {  // ion lists beyond the tile ranking: per-context reads
-    std::vector<cr_state_view> v(R);
-    for (size_t r = 0; r < R; ++r) {
-      v[r] = cr_state_view{};
-      v[r].xyz = p->xyz ? p->xyz + 3 * r * S : nullptr;
-      v[r].vel = p->vel ? p->vel + 3 * r * S : nullptr;
-      v[r].id = p->id ? p->id + r * S : nullptr;
-      v[r].type = p->type ? p->type + r * S : nullptr;
-      v[r].state = p->state ? p->state + r * S : nullptr;
-      v[r].cls = p->cls ? p->cls + r * S : nullptr;
-    }
-    const int rc = cr_batch_state(b, v.data());
-    for (size_t r = 0; r < R; ++r) p->n[r] = v[r].n;
-    return rc;
-  }
+  // the view of replica r in the packed arrays (the per-context read of a
+  // replica whose ion list is beyond the batched ranking)
+  auto view_of = [&](size_t r) {
+    cr_state_view v{};
+    v.xyz = p->xyz ? p->xyz + 3 * r * S : nullptr;
+    v.vel = p->vel ? p->vel + 3 * r * S : nullptr;
+    v.id = p->id ? p->id + r * S : nullptr;
+    v.type = p->type ? p->type + r * S : nullptr;
+    v.state = p->state ? p->state + r * S : nullptr;
+    v.cls = p->cls ? p->cls + r * S : nullptr;
+    return v;
+  };
   int rc = ensure_packed(b, S);
   if (rc != CR_OK) return rc;
   cudaStream_t s = b->ctx[0]->stream;
-  // outputs go through the device staging and one bulk copy per array (the
-  // kernels' scattered small records written straight into pinned host
-  // memory measured slower than the staging and the copy)
-  float *zx = nullptr, *zv = nullptr;
-  uint64_t *zi = nullptr;
-  int32_t *zt = nullptr, *zc = nullptr;
-  int8_t *zs = nullptr;
+  // host arrays the GPU can address (pinned memory) are written in place by
+  // the ordering kernel, whose threads write consecutive entries; the others
+  // go through the device staging and one bulk copy per array
+  float *zx = device_view(p->xyz), *zv = device_view(p->vel);
+  uint64_t *zi = device_view(p->id);
+  int32_t *zt = device_view(p->type), *zc = device_view(p->cls);
+  int8_t *zs = device_view(p->state);
   for (size_t r = 0; r < R; ++r) {
     cr_ctx *c = b->ctx[r];
     StateBufs &B = b->h_sbufs[r];
@@ -2314,7 +2311,11 @@ extern "C" int cr_batch_state_packed(cr_batch *b, cr_batch_packed *p) {
     p->n[r] = b->h_nout[r];
     const int e = err_bits_to_code(herr[r]);
     if (rc == CR_OK && e != CR_OK) rc = e;
-    if (rc == CR_OK && b->h_nout[r] < 0) rc = CR_ERR_CUDA;
+    if (rc == CR_OK && b->h_nout[r] < 0) {  // more ions than the batched ranking takes: read it by itself
+      cr_state_view v = view_of(r);
+      rc = cr_state(b->ctx[r], &v);
+      p->n[r] = v.n;
+    }
   }
   return rc;
 }

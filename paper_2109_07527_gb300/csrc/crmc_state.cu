@@ -96,50 +96,56 @@ __device__ __forceinline__ void emit(const SysParams &P, const StateBufs &B, int
   if (B.site && (t == CR_ACID || t == CR_BASE)) B.site[info >> INFO_SITE_SHIFT] = (int8_t)ionised;
 }
 
-// The input ids present, by an exclusive prefix count (each thread a
-// contiguous range), written and unmarked (one CTA).
+// The input ids present, in id order, written and unmarked (one CTA): the
+// ids are taken 1024 at a time, each thread one id, and a present id's place
+// is the number of present ids before it (ballots and a scan of the warps'
+// counts), so that consecutive threads write consecutive entries.
 __device__ __forceinline__ void order_inputs(const SysParams &P, const StateBufs &B, int *part) {
+  __shared__ int base_s;
   const int t = threadIdx.x;
   const int lane = t & 31, w = t >> 5;
   const int n = B.n_input;
-  const int per = (n + ORDER_THREADS - 1) / ORDER_THREADS;
-  const int lo = min(n, t * per), hi = min(n, lo + per);
-  int s = 0;
-  for (int i = lo; i < hi; ++i) s += B.present[i] != 0;
-  int x = s;
+  if (t == 0) base_s = 0;
+  for (int c0 = 0; c0 < n; c0 += ORDER_THREADS) {
+    const int i = c0 + t;
+    const int g = i < n ? B.present[i] - 1 : -1;
+    const unsigned bal = __ballot_sync(0xffffffffu, g >= 0);
+    if (lane == 0) part[w] = __popc(bal);
+    __syncthreads();
+    if (w == 0) {  // inclusive scan of the warps' counts
+      int v = part[lane];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) part[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int v = part[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      part[lane] = v;
     }
-    part[lane] = v;
-  }
-  __syncthreads();
-  int run = x - s + (w > 0 ? part[w - 1] : 0);
-  for (int i = lo; i < hi; ++i) {
-    const int g = B.present[i] - 1;
+    __syncthreads();
     if (g >= 0) {
-      emit(P, B, g, run++);
+      emit(P, B, g, base_s + (w > 0 ? part[w - 1] : 0) + __popc(bal & ((1u << lane) - 1u)));
       B.present[i] = 0;
     }
+    __syncthreads();
+    if (t == 0) base_s += part[ORDER_THREADS / 32 - 1];
   }
 }
 
-// The ions after the input ids, in id order: at their ranks, or in the
-// order of the device-wide sort (sorted_slot).
+// The ions after the input ids, in id order: in the order of the device-wide
+// sort (sorted_slot), or by their ranks, which are first turned into the slot
+// of each rank (the ranked keys' array takes it) so that the entries are
+// written in order.
 __device__ __forceinline__ void order_ions(const SysParams &P, const StateBufs &B, int n_present, int n_ions,
                                            const int *sorted_slot) {
-  for (int r = threadIdx.x; r < n_ions; r += ORDER_THREADS)
-    emit(P, B, sorted_slot ? sorted_slot[r] : B.ion_val[r], n_present + (sorted_slot ? r : B.ion_rank[r]));
+  if (sorted_slot) {
+    for (int r = threadIdx.x; r < n_ions; r += ORDER_THREADS) emit(P, B, sorted_slot[r], n_present + r);
+    return;
+  }
+  unsigned long long *slot_of_rank = B.ion_key;  // the keys were consumed by the ranking
+  for (int i = threadIdx.x; i < n_ions; i += ORDER_THREADS)
+    slot_of_rank[B.ion_rank[i]] = (unsigned long long)B.ion_val[i];
+  __syncthreads();
+  for (int r = threadIdx.x; r < n_ions; r += ORDER_THREADS) emit(P, B, (int)slot_of_rank[r], n_present + r);
 }
 
 // CTA 0 the input ids, CTA 1 the ions (counts from the host)

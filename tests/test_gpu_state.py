@@ -228,6 +228,34 @@ def test_packed_batch_state_and_load(crmc):
     assert np.all(n2 > 0)
 
 
+def test_packed_batch_state_with_a_replica_beyond_the_batched_ranking(crmc):
+    """In a packed batch read a replica with more than 16,384 inserted ions
+    (past the batched ranking) is read by itself, the others by the batched
+    kernels; every block equals the context's own read."""
+    import dataclasses
+    ws = [dataclasses.replace(W.ideal(n_sites=10, L=120.0, pIS=pis, n_pairs=20, seed=3 + i), capacity=48000)
+          for i, pis in enumerate((2.0, 0.5, 1.5))]
+    ctxs = [crmc.Context(w) for w in ws]
+    b = crmc.Batch(ctxs)
+    b.sweep(3, 31)
+    refs = [g.state() for g in ctxs]
+    assert int(np.sum(refs[1]["id"] >= np.uint64(1 << 32))) > 16384
+    assert int(np.sum(refs[0]["id"] >= np.uint64(1 << 32))) < 16384
+    R, S = len(ws), 48000
+    arr = dict(xyz=np.zeros((R * S, 3), np.float32), vel=np.zeros((R * S, 3), np.float32),
+               id=np.zeros(R * S, np.uint64), type=np.zeros(R * S, np.int32), cls=np.zeros(R * S, np.int32),
+               state=np.zeros(R * S, np.int8))
+    n = np.zeros(R, np.int64)
+    for _ in range(2):  # twice: the marks of the first read are cleared
+        b.state_packed(S, arr, n)
+        for r, ref in enumerate(refs):
+            k = int(n[r])
+            assert k == int(ref["n"])
+            for key in ("xyz", "vel", "id", "type", "cls", "state"):
+                assert np.array_equal(arr[key][r * S:r * S + k], ref[key]), (r, key)
+    b.close()
+
+
 def test_packed_batch_io_on_pinned_memory(crmc):
     """Pinned host arrays (read in place by the load kernels) give the same
     results as pageable arrays, both ways."""
