@@ -137,9 +137,38 @@ __device__ __forceinline__ int upper_idx(const int *pre, int n, int j) {
   return lo;
 }
 
-// warp: index of the kth (0-based) list entry of a kind, -1 if none
+// warp: index of the kth (0-based) list entry of a kind in a long list (four
+// 32-entry chunks per round, their loads in flight together; out of line)
+__device__ __noinline__ int warp_kth_long(const int *info, int n, int kind, int kth) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int base = 0; base < n; base += 128) {
+    bool m[4];
+    unsigned b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = base + 32 * u + lane;
+      m[u] = j < n && kind_of(info[j]) == kind;
+      b[u] = __ballot_sync(0xffffffffu, m[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = __popc(b[u]);
+      if (kth < c) {
+        const unsigned hit = __ballot_sync(0xffffffffu, m[u] && __popc(b[u] & lt) == kth);
+        return base + 32 * u + __ffs(hit) - 1;
+      }
+      kth -= c;
+    }
+  }
+  return -1;
+}
+
+// warp: index of the kth (0-based) list entry of a kind, -1 if none (lists
+// longer than four chunks: warp_kth_long)
 __device__ __forceinline__ int warp_kth(const int *info, int n, int kind, int kth) {
   const int lane = threadIdx.x & 31;
+  if (n > 128) return warp_kth_long(info, n, kind, kth);
   for (int base = 0; base < n; base += 32) {
     const int j = base + lane;
     const bool m = j < n && kind_of(info[j]) == kind;
@@ -155,50 +184,71 @@ __device__ __forceinline__ int warp_kth(const int *info, int n, int kind, int kt
   return -1;
 }
 
-// warp: number of entries with rank < r and rank == r
+// warp: number of entries with rank < r and rank == r (four chunks per round)
 __device__ __forceinline__ void warp_rank_count(const int *rank, int n, int r, int &below, int &same) {
   const int lane = threadIdx.x & 31;
   below = 0;
   same = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int j = base + lane;
-    const int rk = j < n ? rank[j] : INT_MAX;
-    below += __popc(__ballot_sync(0xffffffffu, rk < r));
-    same += __popc(__ballot_sync(0xffffffffu, rk == r));
+  for (int base = 0; base < n; base += 128) {
+    int rk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = base + 32 * u + lane;
+      rk[u] = j < n ? rank[j] : INT_MAX;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      below += __popc(__ballot_sync(0xffffffffu, rk[u] < r));
+      same += __popc(__ballot_sync(0xffffffffu, rk[u] == r));
+    }
   }
 }
 
-// warp: open a hole at p (entries [p, n) move up by one)
+// one list entry held in registers while the list shifts
+struct EntryRegs {
+  float4 a, v;
+  unsigned long long b;
+  long long e;
+  int c, d;
+};
+__device__ __forceinline__ EntryRegs entry_load(const DomList &L, int j) {
+  return EntryRegs{L.pos[j], L.vel[j], L.id[j], L.lnk[j], L.info[j], L.rank[j]};
+}
+__device__ __forceinline__ void entry_store(const DomList &L, int j, const EntryRegs &x) {
+  L.pos[j] = x.a; L.vel[j] = x.v; L.id[j] = x.b; L.lnk[j] = x.e; L.info[j] = x.c; L.rank[j] = x.d;
+}
+
+// warp: open a hole at p (entries [p, n) move up by one), 64 entries per
+// round from the top down: every load of a round before its stores
 __device__ void warp_insert_gap(DomList L, int n, int p) {
   const int lane = threadIdx.x & 31;
-  for (int hi = n; hi > p; hi -= 32) {
-    const int lo = max(p, hi - 32);
-    const int j = lo + lane;
-    const bool act = j < hi;
-    float4 a, v;
-    unsigned long long b = 0;
-    long long e = 0;
-    int c = 0, d = 0;
-    if (act) { a = L.pos[j]; v = L.vel[j]; b = L.id[j]; e = L.lnk[j]; c = L.info[j]; d = L.rank[j]; }
+  for (int hi = n; hi > p; hi -= 64) {
+    const int lo = max(p, hi - 64);
+    const int j0 = lo + lane, j1 = lo + 32 + lane;
+    const bool a0 = j0 < hi, a1 = j1 < hi;
+    EntryRegs x0{}, x1{};
+    if (a0) x0 = entry_load(L, j0);
+    if (a1) x1 = entry_load(L, j1);
     __syncwarp();
-    if (act) { L.pos[j + 1] = a; L.vel[j + 1] = v; L.id[j + 1] = b; L.lnk[j + 1] = e; L.info[j + 1] = c; L.rank[j + 1] = d; }
+    if (a0) entry_store(L, j0 + 1, x0);
+    if (a1) entry_store(L, j1 + 1, x1);
     __syncwarp();
   }
 }
 
-// warp: remove entry p (entries (p, n) move down by one)
+// warp: remove entry p (entries (p, n) move down by one), 64 entries per
+// round from the bottom up
 __device__ void warp_remove(DomList L, int n, int p) {
   const int lane = threadIdx.x & 31;
-  for (int lo = p + 1; lo < n; lo += 32) {
-    const int j = lo + lane;
-    const bool act = j < n;
-    float4 a, v;
-    unsigned long long b = 0;
-    long long e = 0;
-    int c = 0, d = 0;
-    if (act) { a = L.pos[j]; v = L.vel[j]; b = L.id[j]; e = L.lnk[j]; c = L.info[j]; d = L.rank[j]; }
+  for (int lo = p + 1; lo < n; lo += 64) {
+    const int j0 = lo + lane, j1 = lo + 32 + lane;
+    const bool a0 = j0 < n, a1 = j1 < n;
+    EntryRegs x0{}, x1{};
+    if (a0) x0 = entry_load(L, j0);
+    if (a1) x1 = entry_load(L, j1);
     __syncwarp();
-    if (act) { L.pos[j - 1] = a; L.vel[j - 1] = v; L.id[j - 1] = b; L.lnk[j - 1] = e; L.info[j - 1] = c; L.rank[j - 1] = d; }
+    if (a0) entry_store(L, j0 - 1, x0);
+    if (a1) entry_store(L, j1 - 1, x1);
     __syncwarp();
   }
 }
