@@ -82,3 +82,65 @@ def test_ewald_refusals(crmc):
         assert e.value.code == -1
     g.sweep(g.trials_per_sweep, 3)  # the context still works
     g.close()
+
+
+def test_ewald_with_invocations_and_a_pH_change(crmc):
+    """Grand-reaction invocations (salt ions as their own types) and a new
+    reservoir pH between sweeps, under Ewald: trial by trial vs the oracle."""
+    from paper_2109_07527_gb300 import methods
+    w = _electrolyte(m=100)
+    g = crmc.Context(w)
+    n = g.trials_per_sweep * 2
+    inv = methods.grand_reaction_invocations(7.0, 2.0, 2.0, reactions=1)
+    steps = [(inv[0][0], 7.0), (inv[1][0], 7.0), (inv[2][0], 5.5), (inv[3][0], 5.5)]
+    done = []
+    for k, (args, pH) in enumerate(steps):
+        seed = 70 + k
+        g.set_pH(pH)
+        g.set_invocation(*args)
+        lg = g.sweep(n, seed, log=True)["log"]
+
+        def prep(o, done=tuple(done), args=args, pH=pH):
+            for (a, p), sd in done:
+                o.set_pH(p)
+                o.set_invocation(*a)
+                o.sweep(n, sd)
+            o.set_pH(pH)
+            o.set_invocation(*args)
+        o, lo, ties = compare_logs(w, lg, n, seed, prep=prep)
+        compare_states(g, o, w.n_sites)
+        done.append(((args, pH), seed))
+    g.close()
+
+
+def test_ewald_checkpoint_and_bound_buffers_continue_the_chain(crmc):
+    """A checkpoint restored into a fresh context, and a context whose
+    configuration lives in caller-owned device memory, both continue the
+    unsplit Ewald chain bit for bit (S(k) is rebuilt from the state at every
+    sweep)."""
+    import torch
+    w = _electrolyte(m=100)
+    a, b = crmc.Context(w), crmc.Context(w)
+    for s in range(3):
+        a.sweep(a.trials_per_sweep, 10 + s)
+        b.sweep(b.trials_per_sweep, 10 + s)
+    ck = b.checkpoint()
+    c = crmc.Context(w)
+    c.restore(ck)
+    i = c.info
+    ncell, nslot = i["nc"] ** 3, i["nc"] ** 3 * i["cap"]
+    t = dict(cnt=torch.zeros(ncell, dtype=torch.int32, device="cuda"),
+             pos=torch.zeros(4 * nslot, dtype=torch.float32, device="cuda"),
+             vel=torch.zeros(4 * nslot, dtype=torch.float32, device="cuda"),
+             id=torch.zeros(nslot, dtype=torch.int64, device="cuda"),
+             info=torch.zeros(nslot, dtype=torch.int32, device="cuda"))
+    c.bind_device_buffers(t["cnt"].data_ptr(), t["pos"].data_ptr(), t["vel"].data_ptr(), t["id"].data_ptr(),
+                          t["info"].data_ptr(), ncell, nslot)
+    for s in range(3, 6):
+        a.sweep(a.trials_per_sweep, 10 + s)
+        c.sweep(c.trials_per_sweep, 10 + s)
+    sa, sc = a.state(), c.state()
+    for k in ("id", "xyz", "type", "state", "site_state"):
+        assert np.array_equal(sa[k], sc[k]), k
+    for g in (a, b, c):
+        g.close()
