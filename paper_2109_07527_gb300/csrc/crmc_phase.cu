@@ -137,38 +137,9 @@ __device__ __forceinline__ int upper_idx(const int *pre, int n, int j) {
   return lo;
 }
 
-// warp: index of the kth (0-based) list entry of a kind in a long list (four
-// 32-entry chunks per round, their loads in flight together; out of line)
-__device__ __noinline__ int warp_kth_long(const int *info, int n, int kind, int kth) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int base = 0; base < n; base += 128) {
-    bool m[4];
-    unsigned b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = base + 32 * u + lane;
-      m[u] = j < n && kind_of(info[j]) == kind;
-      b[u] = __ballot_sync(0xffffffffu, m[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = __popc(b[u]);
-      if (kth < c) {
-        const unsigned hit = __ballot_sync(0xffffffffu, m[u] && __popc(b[u] & lt) == kth);
-        return base + 32 * u + __ffs(hit) - 1;
-      }
-      kth -= c;
-    }
-  }
-  return -1;
-}
-
-// warp: index of the kth (0-based) list entry of a kind, -1 if none (lists
-// longer than four chunks: warp_kth_long)
+// warp: index of the kth (0-based) list entry of a kind, -1 if none
 __device__ __forceinline__ int warp_kth(const int *info, int n, int kind, int kth) {
   const int lane = threadIdx.x & 31;
-  if (n > 128) return warp_kth_long(info, n, kind, kth);
   for (int base = 0; base < n; base += 32) {
     const int j = base + lane;
     const bool m = j < n && kind_of(info[j]) == kind;
