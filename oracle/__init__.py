@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "libcrmc_oracle.so")
 F_ACC, F_NOELIG, F_EDGE, F_OVERLAP = 1, 2, 4, 8
 PLANT = {"none": 0, "drop_ion_count": 1, "dE_sign": 2, "drop_self": 3, "drop_pair_cc": 4,
          "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7, "species_count": 8,
-         "ewald_half_recip": 9}
+         "ewald_half_recip": 9, "rigid_torque_sign": 10, "rigid_no_rot_noise": 11}
 N_FEAT, N_HID = 48, 128
 
 
@@ -110,6 +110,12 @@ def _load():
             getattr(lib, f).argtypes = [P, C.c_double, C.c_double, C.c_uint64]
         lib.or_set_positions.restype = C.c_int32
         lib.or_set_positions.argtypes = [P, P, P, P, C.c_int32]
+        lib.or_set_bodies.restype = C.c_int32
+        lib.or_set_bodies.argtypes = [P, C.c_int32, P, P]
+        lib.or_body_state.restype = C.c_int32
+        lib.or_body_state.argtypes = [P, P]
+        lib.or_set_body_state.restype = C.c_int32
+        lib.or_set_body_state.argtypes = [P, P, C.c_int32]
         lib.or_philox.argtypes = [P, P, P]
         lib.or_plant.argtypes = [C.c_int]
         for f in ("or_dsf_phi", "or_dsf_force"):
@@ -355,6 +361,29 @@ class Oracle:
         rc = self._lib.or_md_end(self._h, float(dt), float(gamma), C.c_uint64(seed))
         if rc != 0:
             raise RuntimeError(f"or_md_end failed with code {rc}")
+
+    def set_bodies(self, first, count):
+        """Declare rigid bodies: body b is the permanent ids [first[b], first[b] + count[b])."""
+        f = np.ascontiguousarray(first, dtype=np.int32)
+        c = np.ascontiguousarray(count, dtype=np.int32)
+        if f.shape != c.shape:
+            raise ValueError("first and count differ in length")
+        rc = self._lib.or_set_bodies(self._h, len(f), _ptr(f), _ptr(c))
+        if rc != 0:
+            raise ValueError(f"or_set_bodies refused the bodies (code {rc})")
+        self._n_bodies = len(f)
+        self.bodies = (f.copy(), c.copy())
+
+    def body_state(self):
+        """Per body: X[3], V[3], R[9] (row-major, lab = R body), pi[3] (body frame), I[3], M."""
+        out = np.zeros((getattr(self, "_n_bodies", 0), 22))
+        self._lib.or_body_state(self._h, _ptr(out))
+        return out
+
+    def set_body_state(self, rec):
+        rec = np.ascontiguousarray(rec, dtype=np.float64)
+        if self._lib.or_set_body_state(self._h, _ptr(rec), len(rec)) != 0:
+            raise ValueError("body count mismatch")
 
     def set_positions(self, ids, xyz, vel=None):
         ids = np.ascontiguousarray(ids, dtype=np.uint64)

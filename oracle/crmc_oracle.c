@@ -68,7 +68,7 @@ enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
        PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5,
        PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7, PLANT_SPECIES_COUNT = 8,
-       PLANT_EWALD_HALF_RECIP = 9 };
+       PLANT_EWALD_HALF_RECIP = 9, PLANT_RIGID_TORQUE_SIGN = 10, PLANT_RIGID_NO_ROT_NOISE = 11 };
 
 /* ----------------------------------------------------------------------- */
 /* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
@@ -123,6 +123,22 @@ typedef struct {
   double dE, S, lnA, lnu;
 } or_trial;
 
+/* A rigid body (Sec. IV.B: the nanoparticles' sites are rigidly attached to
+ * the shell; the body's mass is the sum of its members', one unit each): the
+ * permanent particles with ids [first, first + count).  State: centre of mass
+ * X (not wrapped) and its velocity V, orientation R (row-major; lab = R body,
+ * the body axes the principal axes, in ascending order of the moments I),
+ * angular momentum pi in the body frame; F and T are the force and the torque
+ * (lab frame, Langevin terms included) of the last force evaluation; d the
+ * members' offsets from X in the body frame. */
+typedef struct {
+  int first, count;
+  double M, I[3];
+  double X[3], V[3], R[9], pi[3];
+  double F[3], T[3];
+  double *d;
+} or_body;
+
 typedef struct {
   /* box, cells and schedule */
   double L, a;
@@ -171,6 +187,10 @@ typedef struct {
   int ewald_kmax, nk;
   int *kn;
   double *kA, *Sre, *Sim, *dSre, *dSim;
+  /* rigid bodies (or_set_bodies); body_of: body of each permanent id, -1 none */
+  int n_input, nbody;
+  or_body *body;
+  int *body_of;
 } Oracle;
 
 static int g_plant = PLANT_NONE;
@@ -271,6 +291,8 @@ void or_destroy(Oracle *o) {
   free(o->lnK); free(o->pK); free(o->site_type); free(o->bi); free(o->bj);
   free(o->W1); free(o->b1); free(o->W2); free(o->b2); free(o->W3); free(o->b3); free(o->w4);
   free(o->kn); free(o->kA); free(o->Sre); free(o->Sim); free(o->dSre); free(o->dSim);
+  for (int b = 0; b < o->nbody; ++b) free(o->body[b].d);
+  free(o->body); free(o->body_of);
   free(o);
 }
 
@@ -412,7 +434,7 @@ Oracle *or_create(const or_params *p, const float *xyz, const int32_t *type, con
   o->ln_z1 = log(RHO0_NA * v_nm3);
   o->ln_salt = -LN10 * (o->pIXp + o->pIXm);
   /* particles */
-  o->n = p->n; o->cap = p->capacity;
+  o->n = p->n; o->cap = p->capacity; o->n_input = p->n;
   size_t C = (size_t)(o->cap > 0 ? o->cap : 1);
   o->x = malloc(C * sizeof(float)); o->y = malloc(C * sizeof(float)); o->z = malloc(C * sizeof(float));
   o->type = malloc(C * sizeof(int)); o->cls = malloc(C * sizeof(int)); o->site = malloc(C * sizeof(int));
@@ -1375,10 +1397,12 @@ int32_t or_forces(const Oracle *o, double *F, double *fs) {
 /* Langevin part of the force, drawn per particle id and force evaluation:
  * -gamma v + sqrt(2 gamma T / dt) xi, xi ~ N(0,1) from Box-Muller on Philox
  * (key = seed, counter = (id_lo, id_hi, eval, 5)), uniforms ((w >> 8) + 0.5) 2^-24. */
+static int is_member(const Oracle *o, int j);
 static void langevin(const Oracle *o, double *F, double gamma, double T, double dt, uint64_t seed, uint64_t ev) {
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   double amp = sqrt(2.0 * gamma * T / dt);
   for (int j = 0; j < o->n; ++j) {
+    if (is_member(o, j)) continue; /* a rigid body's thermostat acts on the body */
     uint32_t c[4] = {(uint32_t)o->id[j], (uint32_t)(o->id[j] >> 32), (uint32_t)ev, 5u}, w[4];
     philox(c, key, w);
     double u[4];
@@ -1399,6 +1423,327 @@ static float wrapf(const Oracle *o, double x) {
   return f;
 }
 
+/* ----------------------------------------------------------------------- */
+/* Rigid bodies.  Newton-Euler equations for each body, with the Langevin
+ * thermostat acting on the body as a whole (the reading of Sec. IV.B's
+ * Langevin-thermostatted nanoparticles): the force on the centre of mass gets
+ * -gamma M V + sqrt(2 gamma M / dt) xi, the torque (lab frame)
+ * -gamma L + sqrt(2 gamma / dt) I_lab^(1/2) xi' with L = R pi the angular
+ * momentum and I_lab^(1/2) = R diag(sqrt(I)) R^T, so that every translational
+ * and rotational degree of freedom relaxes at the rate gamma towards kT = 1.
+ * xi, xi': Box-Muller normals of the Philox blocks (body, 0, eval, 8) and
+ * (body, 0, eval, 9) under the MD key.  Members get no thermostat of their
+ * own; their pair forces act on the body.
+ * Velocity Verlet: half kicks V += dt/2 F/M, pi += dt/2 R^T T; the drift
+ * X += dt V and the free rotation by the symmetric splitting of Dullweber,
+ * Leimkuhler and McLachlan (J. Chem. Phys. 107, 5840 (1997)): exact rotations
+ * about the body axes 1, 2, 3, 2, 1 for dt/2, dt/2, dt, dt/2, dt/2.  A member
+ * then sits at wrap(X + R d) with the velocity V + omega x (R d),
+ * omega = R (pi / I). */
+
+static int is_member(const Oracle *o, int j) {
+  return o->nbody > 0 && o->id[j] < (uint64_t)o->n_input && o->body_of[o->id[j]] >= 0;
+}
+
+/* index of every permanent id (-1 absent) */
+static int *permanent_index(const Oracle *o) {
+  int *where = malloc((size_t)(o->n_input > 0 ? o->n_input : 1) * sizeof(int));
+  for (int j = 0; j < o->n_input; ++j) where[j] = -1;
+  for (int j = 0; j < o->n; ++j) if (o->id[j] < (uint64_t)o->n_input) where[o->id[j]] = j;
+  return where;
+}
+
+static void rb_mul(const double R[9], const double v[3], double out[3]) {
+  for (int a = 0; a < 3; ++a) out[a] = R[3 * a] * v[0] + R[3 * a + 1] * v[1] + R[3 * a + 2] * v[2];
+}
+static void rb_tmul(const double R[9], const double v[3], double out[3]) {
+  for (int a = 0; a < 3; ++a) out[a] = R[a] * v[0] + R[3 + a] * v[1] + R[6 + a] * v[2];
+}
+static void rb_cross(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Eigenvalues w and eigenvectors (the columns of V) of a symmetric 3x3 matrix
+ * by cyclic Jacobi rotations (Golub & Van Loan, Matrix Computations, Sec. 8.5). */
+static void jacobi3(const double A_in[9], double w[3], double V[9]) {
+  double A[9];
+  memcpy(A, A_in, sizeof(A));
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    double diag = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int r = 0; r < 3; ++r) {
+      int p = PQ[r][0], q = PQ[r][1];
+      double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      double tau = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+      double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+      for (int k = 0; k < 3; ++k) { /* A <- A J, V <- V J */
+        double akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - s * akq;
+        A[3 * k + q] = s * akp + c * akq;
+        double vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - s * vkq;
+        V[3 * k + q] = s * vkp + c * vkq;
+      }
+      for (int k = 0; k < 3; ++k) { /* A <- J^T A */
+        double apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - s * aqk;
+        A[3 * q + k] = s * apk + c * aqk;
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) w[k] = A[4 * k];
+}
+
+/* exact free rotation about body axis k for a time t: R <- R Rot_k(theta),
+ * pi <- Rot_k(theta)^T pi, theta = t pi_k / I_k */
+static void rb_rotate(or_body *b, int k, double t) {
+  double th = t * b->pi[k] / b->I[k], c = cos(th), s = sin(th);
+  int i = (k + 1) % 3, j = (k + 2) % 3;
+  for (int a = 0; a < 3; ++a) {
+    double ri = b->R[3 * a + i], rj = b->R[3 * a + j];
+    b->R[3 * a + i] = c * ri + s * rj;
+    b->R[3 * a + j] = -s * ri + c * rj;
+  }
+  double pi_i = b->pi[i], pi_j = b->pi[j];
+  b->pi[i] = c * pi_i + s * pi_j;
+  b->pi[j] = -s * pi_i + c * pi_j;
+}
+
+/* members' velocities (and, with pos, positions) from the body's state */
+static void rb_place(Oracle *o, const or_body *b, const int *where, int pos) {
+  double om[3], w[3];
+  for (int k = 0; k < 3; ++k) w[k] = b->pi[k] / b->I[k];
+  rb_mul(b->R, w, om);
+  for (int m = 0; m < b->count; ++m) {
+    int j = where[b->first + m];
+    double a[3], u[3];
+    rb_mul(b->R, b->d + 3 * m, a);
+    rb_cross(om, a, u);
+    o->vx[j] = b->V[0] + u[0]; o->vy[j] = b->V[1] + u[1]; o->vz[j] = b->V[2] + u[2];
+    if (pos) {
+      o->x[j] = wrapf(o, b->X[0] + a[0]);
+      o->y[j] = wrapf(o, b->X[1] + a[1]);
+      o->z[j] = wrapf(o, b->X[2] + a[2]);
+    }
+  }
+}
+
+/* three normal deviates from the Philox block (c0, 0, eval, purpose), the
+ * Box-Muller form of the particles' Langevin noise */
+static void rb_normals(const uint32_t key[2], uint32_t c0, uint32_t ev, uint32_t purpose, double g[3]) {
+  uint32_t c[4] = {c0, 0u, ev, purpose}, w[4];
+  philox(c, key, w);
+  double u[4];
+  for (int i = 0; i < 4; ++i) u[i] = (double)(((float)(w[i] >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  double r1 = sqrt(-2.0 * log(u[0])), r2 = sqrt(-2.0 * log(u[2]));
+  g[0] = r1 * cos(2.0 * M_PI * u[1]);
+  g[1] = r1 * sin(2.0 * M_PI * u[1]);
+  g[2] = r2 * cos(2.0 * M_PI * u[3]);
+}
+
+/* force and torque of every body from its members' forces F, plus the
+ * Langevin terms; kick: the half kick that closes a step */
+static void rb_forces(Oracle *o, const double *F, double gamma, double dt, uint64_t seed, uint64_t ev, int kick) {
+  if (o->nbody == 0) return;
+  int *where = permanent_index(o);
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int bi = 0; bi < o->nbody; ++bi) {
+    or_body *b = &o->body[bi];
+    double Fb[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    for (int m = 0; m < b->count; ++m) {
+      int j = where[b->first + m];
+      double a[3], t[3];
+      rb_mul(b->R, b->d + 3 * m, a);
+      if (g_plant == PLANT_RIGID_TORQUE_SIGN) rb_cross(F + 3 * j, a, t);
+      else rb_cross(a, F + 3 * j, t);
+      for (int k = 0; k < 3; ++k) { Fb[k] += F[3 * j + k]; T[k] += t[k]; }
+    }
+    double gt[3], gr[3], L[3], sg[3], S[3];
+    rb_normals(key, (uint32_t)bi, (uint32_t)ev, 8u, gt);
+    rb_normals(key, (uint32_t)bi, (uint32_t)ev, 9u, gr);
+    double at = sqrt(2.0 * gamma * b->M / dt), ar = sqrt(2.0 * gamma / dt);
+    rb_mul(b->R, b->pi, L);
+    rb_tmul(b->R, gr, sg); /* I_lab^(1/2) xi' = R diag(sqrt I) R^T xi' */
+    for (int k = 0; k < 3; ++k) sg[k] *= sqrt(b->I[k]);
+    rb_mul(b->R, sg, S);
+    for (int k = 0; k < 3; ++k) {
+      Fb[k] += -gamma * b->M * b->V[k] + at * gt[k];
+      T[k] += -gamma * L[k] + (g_plant == PLANT_RIGID_NO_ROT_NOISE ? 0.0 : ar * S[k]);
+      b->F[k] = Fb[k];
+      b->T[k] = T[k];
+    }
+    if (kick) {
+      double tb[3];
+      rb_tmul(b->R, b->T, tb);
+      for (int k = 0; k < 3; ++k) { b->V[k] += 0.5 * dt * b->F[k] / b->M; b->pi[k] += 0.5 * dt * tb[k]; }
+      rb_place(o, b, where, 0);
+    }
+  }
+  free(where);
+}
+
+/* the opening half kick and the drift of every body; members follow */
+static void rb_kick_drift(Oracle *o, double dt) {
+  if (o->nbody == 0) return;
+  int *where = permanent_index(o);
+  for (int bi = 0; bi < o->nbody; ++bi) {
+    or_body *b = &o->body[bi];
+    double tb[3];
+    rb_tmul(b->R, b->T, tb);
+    for (int k = 0; k < 3; ++k) { b->V[k] += 0.5 * dt * b->F[k] / b->M; b->pi[k] += 0.5 * dt * tb[k]; }
+    for (int k = 0; k < 3; ++k) b->X[k] += dt * b->V[k];
+    rb_rotate(b, 0, 0.5 * dt);
+    rb_rotate(b, 1, 0.5 * dt);
+    rb_rotate(b, 2, dt);
+    rb_rotate(b, 1, 0.5 * dt);
+    rb_rotate(b, 0, 0.5 * dt);
+    rb_place(o, b, where, 1);
+  }
+  free(where);
+}
+
+/* Declare rigid bodies: body b is the permanent particles with ids
+ * [first[b], first[b] + count[b]) (at least two, none of them an ion, no id
+ * in two bodies).  The centre of mass and the inertia tensor come from the
+ * current positions (minimum-image offsets from the first member), V from
+ * the members' total momentum, the angular momentum from their velocities
+ * about the centre; the body axes are the principal axes, in ascending order
+ * of the moments, each of the first two with its largest component positive,
+ * the third their cross product.  A body whose smallest moment is below
+ * 1e-9 of the trace (collinear members) is refused.  The members' velocities
+ * become the rigid ones.  n = 0 removes every body. */
+int32_t or_set_bodies(Oracle *o, int32_t nb, const int32_t *first, const int32_t *count) {
+  if (nb < 0 || (nb > 0 && (!first || !count))) return OR_ERR_ARG;
+  int *mark = calloc((size_t)(o->n_input > 0 ? o->n_input : 1), sizeof(int));
+  int *where = permanent_index(o);
+  int rc = OR_OK;
+  for (int b = 0; b < nb && rc == OR_OK; ++b) {
+    if (count[b] < 2 || first[b] < 0 || (int64_t)first[b] + count[b] > o->n_input) { rc = OR_ERR_ARG; break; }
+    for (int m = 0; m < count[b]; ++m) {
+      int id = first[b] + m;
+      if (mark[id] || where[id] < 0 || is_ion(o->type[where[id]])) { rc = OR_ERR_ARG; break; }
+      mark[id] = 1;
+    }
+  }
+  free(mark);
+  or_body *nbody = NULL;
+  if (rc == OR_OK && nb > 0) {
+    nbody = calloc((size_t)nb, sizeof(or_body));
+    for (int bi = 0; bi < nb && rc == OR_OK; ++bi) {
+      or_body *b = &nbody[bi];
+      b->first = first[bi];
+      b->count = count[bi];
+      b->M = (double)b->count;
+      b->d = malloc((size_t)b->count * 3 * sizeof(double));
+      int j0 = where[b->first];
+      double r0[3] = {o->x[j0], o->y[j0], o->z[j0]}, s[3] = {0, 0, 0}, P[3] = {0, 0, 0};
+      for (int m = 0; m < b->count; ++m) {
+        int j = where[b->first + m];
+        double r[3] = {o->x[j], o->y[j], o->z[j]}, v[3] = {o->vx[j], o->vy[j], o->vz[j]};
+        for (int k = 0; k < 3; ++k) {
+          b->d[3 * m + k] = min_image(r[k] - r0[k], o->L);
+          s[k] += b->d[3 * m + k];
+          P[k] += v[k];
+        }
+      }
+      double I[9] = {0}, L[3] = {0, 0, 0};
+      for (int k = 0; k < 3; ++k) { b->X[k] = r0[k] + s[k] / b->M; b->V[k] = P[k] / b->M; }
+      for (int m = 0; m < b->count; ++m) {
+        int j = where[b->first + m];
+        double *d = b->d + 3 * m, v[3] = {o->vx[j], o->vy[j], o->vz[j]}, l[3];
+        for (int k = 0; k < 3; ++k) d[k] -= s[k] / b->M;
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        for (int a = 0; a < 3; ++a)
+          for (int c = 0; c < 3; ++c) I[3 * a + c] += (a == c ? d2 : 0.0) - d[a] * d[c];
+        rb_cross(d, v, l);
+        for (int k = 0; k < 3; ++k) L[k] += l[k];
+      }
+      double w[3], V[9];
+      jacobi3(I, w, V);
+      int ord[3] = {0, 1, 2}; /* ascending moments */
+      for (int a = 0; a < 3; ++a)
+        for (int c = a + 1; c < 3; ++c)
+          if (w[ord[c]] < w[ord[a]]) { int t = ord[a]; ord[a] = ord[c]; ord[c] = t; }
+      double e[3][3];
+      for (int k = 0; k < 2; ++k) {
+        int big = 0;
+        for (int a = 0; a < 3; ++a) {
+          e[k][a] = V[3 * a + ord[k]];
+          if (fabs(e[k][a]) > fabs(e[k][big])) big = a;
+        }
+        if (e[k][big] < 0.0) for (int a = 0; a < 3; ++a) e[k][a] = -e[k][a];
+      }
+      rb_cross(e[0], e[1], e[2]);
+      for (int k = 0; k < 3; ++k) {
+        b->I[k] = w[ord[k]];
+        for (int a = 0; a < 3; ++a) b->R[3 * a + k] = e[k][a];
+      }
+      if (!(b->I[0] > 1e-9 * (b->I[0] + b->I[1] + b->I[2]))) { rc = OR_ERR_ARG; break; }
+      rb_tmul(b->R, L, b->pi);
+      for (int m = 0; m < b->count; ++m) {
+        double dl[3] = {b->d[3 * m], b->d[3 * m + 1], b->d[3 * m + 2]};
+        rb_tmul(b->R, dl, b->d + 3 * m);
+      }
+    }
+  }
+  if (rc != OR_OK) {
+    if (nbody) for (int b = 0; b < nb; ++b) free(nbody[b].d);
+    free(nbody);
+    free(where);
+    return rc;
+  }
+  for (int b = 0; b < o->nbody; ++b) free(o->body[b].d);
+  free(o->body);
+  free(o->body_of);
+  o->body = nbody;
+  o->nbody = nb;
+  o->body_of = malloc((size_t)(o->n_input > 0 ? o->n_input : 1) * sizeof(int));
+  for (int j = 0; j < o->n_input; ++j) o->body_of[j] = -1;
+  for (int b = 0; b < nb; ++b)
+    for (int m = 0; m < o->body[b].count; ++m) o->body_of[o->body[b].first + m] = b;
+  for (int b = 0; b < nb; ++b) rb_place(o, &o->body[b], where, 0);
+  free(where);
+  o->f_valid = 0;
+  return OR_OK;
+}
+
+/* per body 22 values: X[3], V[3], R[9] (row-major), pi[3], I[3], M */
+int32_t or_body_state(const Oracle *o, double *out) {
+  for (int b = 0; b < o->nbody; ++b) {
+    const or_body *B = &o->body[b];
+    double *r = out + 22 * b;
+    memcpy(r, B->X, 3 * sizeof(double));
+    memcpy(r + 3, B->V, 3 * sizeof(double));
+    memcpy(r + 6, B->R, 9 * sizeof(double));
+    memcpy(r + 15, B->pi, 3 * sizeof(double));
+    memcpy(r + 18, B->I, 3 * sizeof(double));
+    r[21] = B->M;
+  }
+  return o->nbody;
+}
+
+/* overwrite X, V, R and pi of every body (records as or_body_state writes
+ * them; I and M are kept) to re-synchronise with another run */
+int32_t or_set_body_state(Oracle *o, const double *in, int32_t nb) {
+  if (nb != o->nbody) return OR_ERR_ARG;
+  for (int b = 0; b < nb; ++b) {
+    or_body *B = &o->body[b];
+    const double *r = in + 22 * b;
+    memcpy(B->X, r, 3 * sizeof(double));
+    memcpy(B->V, r + 3, 3 * sizeof(double));
+    memcpy(B->R, r + 6, 9 * sizeof(double));
+    memcpy(B->pi, r + 15, 3 * sizeof(double));
+  }
+  return OR_OK;
+}
+
 /* Velocity Verlet with Langevin friction/noise added at each force
  * evaluation (unit mass, kT = 1).  Forces are re-evaluated first when the
  * CR-MC stage changed the system since the last evaluation. */
@@ -1409,22 +1754,27 @@ int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t
   if (!o->f_valid) {
     rc = forces_cons(o, F, NULL);
     if (rc) { free(F); return rc; }
+    rb_forces(o, F, gamma, dt, seed, o->md_evals, 0);
     langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
     for (int j = 0; j < o->n; ++j) { o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2]; }
     o->f_valid = 1;
   }
   for (int s = 0; s < n_steps; ++s) {
     for (int j = 0; j < o->n; ++j) {
+      if (is_member(o, j)) continue;
       o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
       o->x[j] = wrapf(o, (double)o->x[j] + dt * o->vx[j]);
       o->y[j] = wrapf(o, (double)o->y[j] + dt * o->vy[j]);
       o->z[j] = wrapf(o, (double)o->z[j] + dt * o->vz[j]);
     }
+    rb_kick_drift(o, dt);
     rc = forces_cons(o, F, NULL);
     if (rc) break;
+    rb_forces(o, F, gamma, dt, seed, o->md_evals, 1);
     langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
     for (int j = 0; j < o->n; ++j) {
       o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2];
+      if (is_member(o, j)) continue;
       o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
     }
   }
@@ -1446,15 +1796,18 @@ int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
   if (!o->f_valid) {
     rc = forces_cons(o, F, NULL);
     if (rc) { free(F); return rc; }
+    rb_forces(o, F, gamma, dt, seed, o->md_evals, 0);
     langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
     for (int j = 0; j < o->n; ++j) { o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2]; }
   }
   for (int j = 0; j < o->n; ++j) {
+    if (is_member(o, j)) continue;
     o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
     o->x[j] = wrapf(o, (double)o->x[j] + dt * o->vx[j]);
     o->y[j] = wrapf(o, (double)o->y[j] + dt * o->vy[j]);
     o->z[j] = wrapf(o, (double)o->z[j] + dt * o->vz[j]);
   }
+  rb_kick_drift(o, dt);
   o->f_valid = 0;
   free(F);
   return rc;
@@ -1465,9 +1818,11 @@ int32_t or_md_end(Oracle *o, double dt, double gamma, uint64_t seed) {
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = forces_cons(o, F, NULL);
   if (!rc) {
+    rb_forces(o, F, gamma, dt, seed, o->md_evals, 1);
     langevin(o, F, gamma, 1.0, dt, seed, o->md_evals++);
     for (int j = 0; j < o->n; ++j) {
       o->fx[j] = F[3 * j]; o->fy[j] = F[3 * j + 1]; o->fz[j] = F[3 * j + 2];
+      if (is_member(o, j)) continue;
       o->vx[j] += 0.5 * dt * o->fx[j]; o->vy[j] += 0.5 * dt * o->fy[j]; o->vz[j] += 0.5 * dt * o->fz[j];
     }
     o->f_valid = 1;

@@ -305,10 +305,12 @@ def fibonacci_sphere(n, radius):
 
 
 def config3(separation=12.0, seed=1, L=100.0, n_sites=1000, R=5.0, pIS=None):
-    """Two fixed nanoparticles of radius 5 sigma, each with 1000 surface sites
-    on a Fibonacci lattice at radius R - 0.5 sigma (NP1 acids pKa 4, NP2 bases
+    """Two nanoparticles of radius 5 sigma, each with 1000 surface sites on a
+    Fibonacci lattice at radius R - 0.5 sigma (NP1 acids pKa 4, NP2 bases
     pKb 4), pH 7, 20 mM salt, l_B = 0.7 sigma, r_c = 12 sigma.  Cores interact
-    with ions by expanded WCA with Delta = R - r (Eq. LJe, Table II)."""
+    with ions by expanded WCA with Delta = R - r (Eq. LJe, Table II).  Fixed
+    unless declared rigid bodies: ``meta["bodies"]`` gives each
+    nanoparticle's first id and member count (core and sites)."""
     rng = np.random.default_rng(seed)
     grid = _Grid(L, 1.2)
     c1 = np.array([L / 2 - separation / 2, L / 2, L / 2])
@@ -351,8 +353,11 @@ def config3(separation=12.0, seed=1, L=100.0, n_sites=1000, R=5.0, pIS=None):
     dele[0 * 4 + 1] = dele[1 * 4 + 0] = R - r_ion
     dele[1 * 4 + 1] = 2 * R - 2 * r_ion
     params = default_params(box_L=L, rc=12.0, lB=0.7, pH=7.0, pIS_plus=pIS, pIS_minus=pIS, wca_del=dele)
+    # each nanoparticle (its core and its sites, ids in that order) as one
+    # rigid body: first ids and member counts
+    bodies = ([0, 1 + n_sites], [1 + n_sites, 1 + n_sites])
     return _assemble("config3", parts, params, 2 * n_sites * 2 + 8192, rng,
-                     meta=dict(separation=separation), with_vel=False)
+                     meta=dict(separation=separation, bodies=bodies), with_vel=False)
 
 
 def config4(seed=1, n_rep=64, density=1e-3, lo=50, hi=1000):
