@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-da", action="store_true")
     ap.add_argument("--no-config4", action="store_true")
     ap.add_argument("--no-fig2", action="store_true")
+    ap.add_argument("--no-config3", action="store_true")
     ap.add_argument("--train-only", action="store_true",
                     help="time only the surrogate's training step (batch 32,768, synthetic features) and exit")
     ap.add_argument("--ewald-only", action="store_true",
@@ -618,6 +619,41 @@ def run_config4(crmc, torch, stream, flush, steps):
     return out
 
 
+def run_config3_mobile(crmc, torch, stream, flush, steps):
+    """The two-nanoparticle system as a full MD run with mobile rigid
+    nanoparticles: 2 x 1000 sites (acids pKa 4 on one, bases pKb 4 on the
+    other) on spheres of radius 5 at 12 sigma, L = 100, 20 mM salt, pH 7; each
+    nanoparticle (core and sites) one rigid body; each step one MD step
+    (dt 0.005, Langevin damping time 20) around one CR-MC sweep."""
+    from paper_2109_07527_gb300 import workloads as W
+    w = W.config3(separation=12.0, seed=1)
+    g = crmc.Context(w)
+    g.set_rigid_bodies(*w.meta["bodies"])
+    dt, gamma = 0.005, 0.05
+    n = g.trials_per_sweep
+
+    def step(s):
+        g.md_begin(dt, gamma, 7000 + s)
+        g.sweep(n, 9000 + s)
+        g.md_end(dt, gamma, 7000 + s)
+
+    for s in range(5):
+        step(s)
+    b0 = g.rigid_body_state()
+    ms = time_steps(lambda s: step(100 + s), steps, stream, flush)
+    b1 = g.rigid_body_state()
+    g.check()
+    st = g.state()
+    out = {"workload": "two nanoparticles (R 5, 1000 sites each) as rigid bodies at 12 sigma, L=100, "
+                       "20 mM, pH 7, l_B 0.7, r_c 12", "particles": int(st["n"]), "trials_per_step": n,
+           "md_cr_cycles_per_s": steps / (ms / 1e3), "trials_per_s": n * steps / (ms / 1e3),
+           "ms_per_step": ms / steps, "steps": steps,
+           "body_displacement": float(np.abs(b1[:, 0:3] - b0[:, 0:3]).max()),
+           "alpha_end": float(st["alpha"])}
+    g.close()
+    return out
+
+
 def time_steps(step_fn, steps, stream, flush):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -739,6 +775,9 @@ def run_ours(args):
     cfg4 = None
     if rank == 0 and not args.no_config4:
         cfg4 = run_config4(crmc, torch, stream, flush, max(10, min(args.steps, 50)))
+    cfg3 = None
+    if rank == 0 and not args.no_config3:
+        cfg3 = run_config3_mobile(crmc, torch, stream, flush, max(10, min(args.steps, 50)))
     fig2 = fig2_ewald = None
     if rank == 0 and not args.no_fig2:
         fig2 = run_method_comparison(crmc)
@@ -803,7 +842,7 @@ def run_ours(args):
            "graph_launches_per_step": 1, "kernels_per_step": tm["launches"] / args.steps,
            "clocks": cl, "e2e": e2e, "plain": plain,
            "surrogate_da": da, "batched_titration": cfg4, "method_comparison": fig2,
-           "method_comparison_ewald": fig2_ewald,
+           "method_comparison_ewald": fig2_ewald, "mobile_nanoparticles": cfg3,
            "md_cr_cycles_per_s": job_rate(args.steps, world, ms / 1e3)}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"], alpha_o = cpu_baseline(ph_sweep_workloads(0))

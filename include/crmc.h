@@ -291,6 +291,42 @@ int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t s
 int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
 int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
 
+/* ---- rigid bodies (mobile nanoparticles) ----
+ * Sec. IV.B's nanoparticles carry their acid / base groups rigidly attached
+ * to the shell, the body's mass the sum of its members' (257 m for a core and
+ * 256 groups), under a Langevin thermostat.  cr_set_rigid_bodies declares
+ * n_bodies bodies: body b is the permanent particles with ids
+ * [first[b], first[b] + count[b]) (input indices of cr_init; at least two
+ * members, none of them an ion, no id in two bodies; n_bodies <=
+ * CR_MAX_BODIES).  From the current configuration (on the device): the
+ * centre of mass X (minimum-image offsets from the first member, unit mass
+ * per member), V from the members' momentum, the principal axes of the
+ * inertia tensor in ascending order of the moments I (the first two with
+ * their largest component positive, the third their cross product) as the
+ * body frame R (lab = R body), the angular momentum from the members'
+ * velocities about X; the members' velocities become the rigid ones.  From
+ * then on cr_md_step / cr_md_begin / cr_md_end move each body as a whole:
+ * the members' pair forces give the body's force and torque, the thermostat
+ * acts on the body (centre of mass: -gamma M V + sqrt(2 gamma M / dt) xi;
+ * rotation, lab frame: -gamma L + sqrt(2 gamma / dt) R diag(sqrt I) R^T xi',
+ * Box-Muller normals of the Philox blocks (b, 0, evaluation, 8) and
+ * (b, 0, evaluation, 9) under the MD seed), velocity Verlet kicks V and the
+ * body-frame angular momentum pi, the drift moves X and rotates the body by
+ * the symmetric splitting of Dullweber, Leimkuhler and McLachlan (J. Chem.
+ * Phys. 107, 5840 (1997): exact rotations about the body axes 1, 2, 3, 2, 1
+ * for dt/2, dt/2, dt, dt/2, dt/2); members sit at X + R d, wrapped, with the
+ * velocity V + omega x (R d).  Body arithmetic in FP64.  CR-MC trials change
+ * the members' charge states as before.  n_bodies = 0 removes the bodies.
+ * Errors: INVALID_ARG (a range or member as above, collinear members, Ewald
+ * electrostatics, a context in a batch); nothing changes then.  While bodies
+ * are declared, cr_load and cr_restore are refused (declare them again after
+ * a load into a fresh context) and the context cannot join a batch.
+ * cr_rigid_body_state writes 22 doubles per body: X[3], V[3], R[9]
+ * (row-major), pi[3], I[3], M; n_bodies must be the number declared. */
+#define CR_MAX_BODIES (1 << 20)
+int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t *first, const int32_t *count);
+int cr_rigid_body_state(cr_ctx *ctx, int32_t n_bodies, double *out);
+
 /* The force evaluation of cr_md_forces, allocating nothing, with the results
  * written to caller-owned device memory.  The paper has no counterpart: this
  * entry point exists for callers that cannot let a library allocate device

@@ -105,7 +105,7 @@ EXPORTS = ("cr_init", "cr_sweep", "cr_sweep_log", "cr_md_forces", "cr_md_step", 
            "cr_batch_state_packed", "cr_batch_load_packed", "cr_train_apply", "cr_train_moments",
            "cr_checkpoint", "cr_restore", "cr_selftest_mma_timeout", "cr_set_pH", "cr_ungroup",
            "cr_batch_set_persistent", "cr_batch_selftest_wait_timeout", "cr_batch_cycle", "cr_set_invocation",
-           "cr_bind_device_buffers")
+           "cr_bind_device_buffers", "cr_set_rigid_bodies", "cr_rigid_body_state")
 N_PARAMS = 39425  # CR_TRAIN_N_PARAMS
 
 
@@ -178,6 +178,10 @@ def _lib():
         lib.cr_md_forces_noalloc.argtypes = [P, P, P, C.c_int64]
         lib.cr_bind_device_buffers.restype = C.c_int
         lib.cr_bind_device_buffers.argtypes = [P, C.POINTER(cr_device_buffers)]
+        lib.cr_set_rigid_bodies.restype = C.c_int
+        lib.cr_set_rigid_bodies.argtypes = [P, C.c_int32, P, P]
+        lib.cr_rigid_body_state.restype = C.c_int
+        lib.cr_rigid_body_state.argtypes = [P, C.c_int32, P]
         lib.cr_md_step.argtypes = [P, C.c_int32, C.c_double, C.c_double, C.c_uint64]
         lib.cr_state.restype = C.c_int
         lib.cr_state.argtypes = [P, C.POINTER(cr_state_view)]
@@ -410,6 +414,23 @@ class Context:
         b = cr_device_buffers(C.c_void_p(int(cnt_ptr)), C.c_void_p(int(pos_ptr)), C.c_void_p(int(vel_ptr)),
                               C.c_void_p(int(id_ptr)), C.c_void_p(int(info_ptr)), int(n_cells), int(n_slots))
         _chk(self._lib.cr_bind_device_buffers(self._h, C.byref(b)), "cr_bind_device_buffers")
+
+    def set_rigid_bodies(self, first, count):
+        """cr_set_rigid_bodies: body b is the permanent ids [first[b], first[b] + count[b])."""
+        f = np.ascontiguousarray(first, dtype=np.int32)
+        c = np.ascontiguousarray(count, dtype=np.int32)
+        if f.shape != c.shape or f.ndim != 1:
+            raise ValueError("first and count must be 1-d arrays of one length")
+        _chk(self._lib.cr_set_rigid_bodies(self._h, len(f), f.ctypes.data_as(C.c_void_p),
+                                           c.ctypes.data_as(C.c_void_p)), "cr_set_rigid_bodies")
+        self.n_bodies = len(f)
+
+    def rigid_body_state(self):
+        """cr_rigid_body_state: per body X[3], V[3], R[9] (row-major), pi[3], I[3], M."""
+        n = getattr(self, "n_bodies", 0)
+        out = np.zeros((n, 22))
+        _chk(self._lib.cr_rigid_body_state(self._h, n, out.ctypes.data_as(C.c_void_p)), "cr_rigid_body_state")
+        return out
 
     def md_begin(self, dt, gamma, seed):
         _chk(self._lib.cr_md_begin(self._h, float(dt), float(gamma), int(seed)), "cr_md_begin")

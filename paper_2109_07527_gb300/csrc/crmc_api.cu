@@ -126,6 +126,12 @@ struct cr_ctx {
   // caller-owned slot arrays (cr_bind_device_buffers) and batch membership
   bool bound = false;
   int batch_refs = 0;
+  // rigid bodies (cr_set_rigid_bodies)
+  int n_bodies = 0, n_members = 0;
+  RigidBody *d_bodies = nullptr;
+  int *d_body_member = nullptr;
+  double *d_body_d = nullptr;
+  float4 *d_body_newpos = nullptr;
 };
 
 namespace {
@@ -209,7 +215,8 @@ static void free_ctx(cr_ctx *c) {
                   c->d_out_state, c->d_out_site,
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
                   c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order,
-                  c->d_ek_nA, c->d_ek_Shi, c->d_ek_Slo, c->d_ek_list, c->d_ek_np};
+                  c->d_ek_nA, c->d_ek_Shi, c->d_ek_Slo, c->d_ek_list, c->d_ek_np,
+                  c->d_bodies, c->d_body_member, c->d_body_d, c->d_body_newpos};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_small) cudaFreeHost(c->h_small);
@@ -1178,7 +1185,117 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
     if (ctx->P.wca[i].on) reach2 = std::max(reach2, (double)ctx->P.wca[i].wcut2);
   const double reach = std::sqrt(reach2) * 1.001 + 1e-3;
   M.reach2 = (float)(reach * reach);
+  M.n_bodies = ctx->n_bodies;
+  M.bodies = ctx->d_bodies;
+  M.body_member = ctx->d_body_member;
+  M.body_d = ctx->d_body_d;
+  M.body_newpos = ctx->d_body_newpos;
+  M.body_dt = dt;
+  M.body_gamma = gamma;
   return M;
+}
+
+static void free_bodies(cr_ctx *ctx) {
+  void *ptrs[] = {ctx->d_bodies, ctx->d_body_member, ctx->d_body_d, ctx->d_body_newpos};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  ctx->d_bodies = nullptr;
+  ctx->d_body_member = nullptr;
+  ctx->d_body_d = nullptr;
+  ctx->d_body_newpos = nullptr;
+  ctx->n_bodies = ctx->n_members = 0;
+}
+
+extern "C" int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t *first, const int32_t *count) {
+  if (!ctx || n_bodies < 0 || n_bodies > CR_MAX_BODIES || (n_bodies > 0 && (!first || !count)))
+    return CR_ERR_INVALID_ARG;
+  if (ctx->P.ewald_nk > 0 || ctx->batch_refs > 0) return CR_ERR_INVALID_ARG;
+  std::vector<int> member((size_t)std::max(ctx->n_input, 1), -1);
+  std::vector<RigidBody> hb((size_t)n_bodies);
+  int64_t nm = 0;
+  for (int b = 0; b < n_bodies; ++b) {
+    if (count[b] < 2 || first[b] < 0 || (int64_t)first[b] + count[b] > ctx->n_input) return CR_ERR_INVALID_ARG;
+    for (int m = 0; m < count[b]; ++m) {
+      if (member[first[b] + m] >= 0) return CR_ERR_INVALID_ARG;  // in two bodies
+      member[first[b] + m] = (int)(nm + m);
+    }
+    hb[b] = RigidBody{};
+    hb[b].first = first[b];
+    hb[b].count = count[b];
+    hb[b].mfirst = (int)nm;
+    nm += count[b];
+  }
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (n_bodies == 0) {
+    free_bodies(ctx);
+    ctx->f_valid = false;
+    return CR_OK;
+  }
+  // the new arrays, adopted once every body is valid
+  RigidBody *d_b = nullptr;
+  int *d_m = nullptr;
+  double *d_d = nullptr;
+  float4 *d_n = nullptr;
+  auto release = [&]() {
+    void *ptrs[] = {d_b, d_m, d_d, d_n};
+    for (void *p : ptrs)
+      if (p) cudaFree(p);
+  };
+  cudaError_t e = cudaMalloc(&d_b, hb.size() * sizeof(RigidBody));
+  if (e == cudaSuccess) e = cudaMalloc(&d_m, member.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_d, (size_t)nm * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_n, (size_t)nm * sizeof(float4));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_b, hb.data(), hb.size() * sizeof(RigidBody), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_m, member.data(), member.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+  MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
+  M.n_bodies = n_bodies;
+  M.bodies = d_b;
+  M.body_member = d_m;
+  M.body_d = d_d;
+  M.body_newpos = d_n;
+  if (e == cudaSuccess) e = launch_body_setup(ctx->P, M, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hb.data(), d_b, hb.size() * sizeof(RigidBody), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  bool bad = false;
+  for (const RigidBody &b : hb) bad = bad || b.bad != 0;
+  if (e == cudaSuccess && !bad) e = launch_body_member_velocities(ctx->P, M, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess || bad) {
+    release();
+    return e != cudaSuccess ? CR_ERR_CUDA : CR_ERR_INVALID_ARG;
+  }
+  free_bodies(ctx);
+  ctx->n_bodies = n_bodies;
+  ctx->n_members = (int)nm;
+  ctx->d_bodies = d_b;
+  ctx->d_body_member = d_m;
+  ctx->d_body_d = d_d;
+  ctx->d_body_newpos = d_n;
+  ctx->f_valid = false;  // the next step evaluates the bodies' forces and torques
+  ctx->launches_total += 2;
+  return CR_OK;
+}
+
+extern "C" int cr_rigid_body_state(cr_ctx *ctx, int32_t n_bodies, double *out) {
+  if (!ctx || n_bodies != ctx->n_bodies || (n_bodies > 0 && !out)) return CR_ERR_INVALID_ARG;
+  if (n_bodies == 0) return CR_OK;
+  std::vector<RigidBody> hb((size_t)n_bodies);
+  CR_CUDA(cudaMemcpyAsync(hb.data(), ctx->d_bodies, hb.size() * sizeof(RigidBody), cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  CR_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int b = 0; b < n_bodies; ++b) {
+    double *r = out + 22 * (size_t)b;
+    std::memcpy(r, hb[b].X, 3 * sizeof(double));
+    std::memcpy(r + 3, hb[b].V, 3 * sizeof(double));
+    std::memcpy(r + 6, hb[b].R, 9 * sizeof(double));
+    std::memcpy(r + 15, hb[b].pi, 3 * sizeof(double));
+    std::memcpy(r + 18, hb[b].I, 3 * sizeof(double));
+    r[21] = hb[b].M;
+  }
+  return CR_OK;
 }
 
 // one force evaluation
@@ -1403,7 +1520,7 @@ extern "C" int cr_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uin
 
 extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const int32_t *type,
                        const int32_t *cls, const int8_t *state) {
-  if (!ctx || n < 0 || n > ctx->capacity) return CR_ERR_INVALID_ARG;
+  if (!ctx || n < 0 || n > ctx->capacity || ctx->n_bodies > 0) return CR_ERR_INVALID_ARG;
   if (n > 0 && (!xyz || !type || !cls || !state)) return CR_ERR_INVALID_ARG;
   // every bonded / site particle of cr_init must be there (at its index; the
   // load kernels check each particle and the neutrality on the device)
@@ -1431,7 +1548,7 @@ extern "C" int cr_load(cr_ctx *ctx, int32_t n, const float *xyz, const float *ve
 extern "C" int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const float *force,
                           const uint64_t *id, const int32_t *type, const int32_t *cls, const int8_t *state,
                           const cr_counters *counters) {
-  if (!ctx || !counters || n < 0 || n > ctx->capacity) return CR_ERR_INVALID_ARG;
+  if (!ctx || !counters || n < 0 || n > ctx->capacity || ctx->n_bodies > 0) return CR_ERR_INVALID_ARG;
   if (n > 0 && (!xyz || !type || !cls || !state || !id)) return CR_ERR_INVALID_ARG;
   if (counters->forces_valid && n > 0 && !force) return CR_ERR_INVALID_ARG;
   if (counters->sweep > (uint64_t)UINT32_MAX / (uint64_t)std::max(ctx->P.ncol, 1)) return CR_ERR_INVALID_ARG;
@@ -1681,7 +1798,8 @@ extern "C" int cr_batch_create(cr_batch **out, cr_ctx *const *ctxs, int32_t n) {
   int maxR = 1;
   for (int r = 0; r < n; ++r) {
     cr_ctx *c = ctxs[r];
-    if (!c || c->P.ncol != ctxs[0]->P.ncol || c->sweep != ctxs[0]->sweep || c->stream != ctxs[0]->stream) {
+    if (!c || c->P.ncol != ctxs[0]->P.ncol || c->sweep != ctxs[0]->sweep || c->stream != ctxs[0]->stream ||
+        c->n_bodies > 0) {
       delete b;
       return CR_ERR_INVALID_ARG;
     }

@@ -17,6 +17,20 @@ struct StepDyn {
   unsigned int sweep0, eval0;
 };
 
+// A rigid body (a nanoparticle and its sites): the permanent particles with
+// ids [first, first + count), members mfirst .. mfirst + count - 1 of the
+// body arrays.  X (not wrapped) and V: centre of mass and its velocity; R
+// (row-major, lab = R body): orientation, the body axes the principal axes in
+// ascending order of the moments I; pi: angular momentum in the body frame;
+// M: mass (one unit per member); F, T: force and torque (lab frame, Langevin
+// terms included) of the last force evaluation.  bad: set by the setup when
+// a member is missing or an ion, or the moments are degenerate.
+struct RigidBody {
+  double X[3], V[3], R[9], pi[3], I[3], M;
+  double F[3], T[3];
+  int first, count, mfirst, bad;
+};
+
 struct MdParams {
   float dt, gamma, amp;   // time step, friction, sqrt(2 gamma kT / dt)
   uint32_t key0, key1, eval;
@@ -33,6 +47,15 @@ struct MdParams {
                            // per-particle finish kernel; null: the force kernel finishes itself
   const StepDyn *dyn;      // non-null in a captured cycle: key = (md_seed0 + step) ^ (rep << 32), eval = eval0 + step
   unsigned int rep;
+  // rigid bodies (n_bodies > 0): body_member[id] = member index of permanent
+  // id, -1 for a free particle; body_d: [3 members] offsets in the body frame;
+  // body_newpos: [members] member positions after the drift
+  int n_bodies;
+  RigidBody *bodies;
+  const int *body_member;
+  double *body_d;
+  float4 *body_newpos;
+  double body_dt, body_gamma;  // the step and the friction in FP64 for the bodies
 };
 
 struct RebuildBufs {
@@ -151,6 +174,11 @@ cudaError_t launch_state_batch(const SysParams *d_reps, const StateBufs *d_bufs,
 // listed, then one thread per reciprocal vector); max_nk: the largest
 // number of reciprocal vectors over the replicas
 cudaError_t launch_ewald_sk(const SysParams *d_reps, int n_rep, int max_nk, cudaStream_t s);
+// rigid bodies: centre, principal frame, body-frame offsets and momenta from
+// the current configuration (bodies[] carries first, count and mfirst);
+// then, once every body is valid, the members' rigid velocities
+cudaError_t launch_body_setup(const SysParams &P, const MdParams &M, cudaStream_t s);
+cudaError_t launch_body_member_velocities(const SysParams &P, const MdParams &M, cudaStream_t s);
 cudaError_t launch_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, int n,
                           uint4 *out, cudaStream_t s);
 

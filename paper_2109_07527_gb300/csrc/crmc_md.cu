@@ -77,7 +77,8 @@ __device__ __forceinline__ void finish_particle(const SysParams &P, const MdPara
     }
   }
   float4 f = make_float4((float)fx * FFIX_INV, (float)fy * FFIX_INV, (float)fz * FFIX_INV, 0.0f);
-  if (M.mode == 0) {
+  // mode 0, or a rigid body's member (its body takes the thermostat and the kicks)
+  if (M.mode == 0 || (M.n_bodies > 0 && id < (unsigned long long)M.n_perm && M.body_member[id] >= 0)) {
     M.fout[gi] = f;
     return;
   }
@@ -313,15 +314,27 @@ __global__ void k_md_kick_drift_scatter(SysParams P, MdParams M, RebuildBufs B) 
   if (g - c * P.cap >= P.cnt[c]) return;
   float4 v = M.vel[g];
   const float4 f = M.fout[g];
-  v.x += 0.5f * M.dt * f.x;
-  v.y += 0.5f * M.dt * f.y;
-  v.z += 0.5f * M.dt * f.z;
   const float4 p = P.pos[g];
-  float x[3] = {p.x + M.dt * v.x, p.y + M.dt * v.y, p.z + M.dt * v.z};
-  for (int i = 0; i < 3; ++i) {
-    x[i] -= P.Lf * floorf(x[i] * P.invL);
-    if (x[i] >= P.Lf) x[i] -= P.Lf;
-    if (x[i] < 0.0f) x[i] = 0.0f;
+  const unsigned long long id = P.pid[g];
+  const int mb = (M.n_bodies > 0 && id < (unsigned long long)M.n_perm) ? M.body_member[id] : -1;
+  float x[3];
+  if (mb >= 0) {  // a rigid body's member: placed by its body (k_body_drift)
+    const float4 q = M.body_newpos[mb];
+    x[0] = q.x;
+    x[1] = q.y;
+    x[2] = q.z;
+  } else {
+    v.x += 0.5f * M.dt * f.x;
+    v.y += 0.5f * M.dt * f.y;
+    v.z += 0.5f * M.dt * f.z;
+    x[0] = p.x + M.dt * v.x;
+    x[1] = p.y + M.dt * v.y;
+    x[2] = p.z + M.dt * v.z;
+    for (int i = 0; i < 3; ++i) {
+      x[i] -= P.Lf * floorf(x[i] * P.invL);
+      if (x[i] >= P.Lf) x[i] -= P.Lf;
+      if (x[i] < 0.0f) x[i] = 0.0f;
+    }
   }
   const int nc = P.nc;
   const int cell = cell_of(x[0], P.scf, nc) + nc * (cell_of(x[1], P.scf, nc) + nc * cell_of(x[2], P.scf, nc));
@@ -332,7 +345,7 @@ __global__ void k_md_kick_drift_scatter(SysParams P, MdParams M, RebuildBufs B) 
   }
   const int o = cell * P.cap + s;
   B.pos[o] = make_float4(x[0], x[1], x[2], p.w);
-  B.pid[o] = P.pid[g];
+  B.pid[o] = id;
   B.info[o] = P.info[g];
   B.vel[o] = v;
   B.frc[o] = f;
@@ -475,6 +488,354 @@ __global__ void k_step_advance(StepDyn *dyn) {
   if (threadIdx.x == 0) dyn->step += 1;
 }
 
+// ---------------------------------------------------------------------------
+// Rigid bodies (Sec. IV.B: the nanoparticles' sites are rigidly attached to
+// the shell; the thermostat acts on each nanoparticle as a whole).
+// Newton-Euler equations with Langevin friction and noise on the centre of
+// mass (-gamma M V + sqrt(2 gamma M / dt) xi) and on the rotation (lab frame:
+// -gamma L + sqrt(2 gamma / dt) R diag(sqrt I) R^T xi', L = R pi), the normals
+// xi, xi' from the Philox blocks (body, 0, eval, 8) and (body, 0, eval, 9)
+// under the MD key.  Velocity Verlet: half kicks V += dt/2 F/M and
+// pi += dt/2 R^T T; the drift X += dt V and the free rotation as exact
+// rotations about the body axes 1, 2, 3, 2, 1 for dt/2, dt/2, dt, dt/2, dt/2
+// (the symmetric splitting of Dullweber, Leimkuhler and McLachlan, J. Chem.
+// Phys. 107, 5840 (1997)).  Members sit at wrap(X + R d) and move with
+// V + omega x (R d), omega = R (pi / I); they get no thermostat of their own.
+// One CTA per body, FP64 body arithmetic; sums over the members go thread by
+// thread in member order, then through a fixed tree, so the result does not
+// depend on where the members sit in the cell list.
+// ---------------------------------------------------------------------------
+constexpr int RB_THREADS = 256;
+
+__device__ __forceinline__ void rb_mul(const double *R, const double *v, double *o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = R[3 * a] * v[0] + R[3 * a + 1] * v[1] + R[3 * a + 2] * v[2];
+}
+__device__ __forceinline__ void rb_tmul(const double *R, const double *v, double *o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = R[a] * v[0] + R[3 + a] * v[1] + R[6 + a] * v[2];
+}
+__device__ __forceinline__ void rb_cross(const double *a, const double *b, double *o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// the CTA's sums of NV per-thread values (every thread gets them)
+template <int NV>
+__device__ void rb_sum(double (&v)[NV], double *sh) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k * RB_THREADS + t] = v[k];
+  __syncthreads();
+  for (int h = RB_THREADS / 2; h > 0; h >>= 1) {
+    if (t < h) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k * RB_THREADS + t] += sh[k * RB_THREADS + t + h];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = sh[k * RB_THREADS];
+  __syncthreads();
+}
+
+// symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (Golub & Van
+// Loan, Matrix Computations, Sec. 8.5): w the eigenvalues, the columns of V
+// the eigenvectors
+__device__ void rb_eigen(double *A, double *w, double *V) {
+  for (int i = 0; i < 9; ++i) V[i] = (i == 0 || i == 4 || i == 8) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    if (off == 0.0 || off <= 1e-32 * (A[0] * A[0] + A[4] * A[4] + A[8] * A[8])) break;
+    for (int r = 0; r < 3; ++r) {
+      const int p = r == 2 ? 1 : 0, q = r == 0 ? 1 : 2;
+      const double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      const double tau = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+      const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+      for (int k = 0; k < 3; ++k) {  // columns p, q of A and V: times the rotation
+        const double x = A[3 * k + p], y = A[3 * k + q];
+        A[3 * k + p] = c * x - s * y;
+        A[3 * k + q] = s * x + c * y;
+        const double u = V[3 * k + p], z = V[3 * k + q];
+        V[3 * k + p] = c * u - s * z;
+        V[3 * k + q] = s * u + c * z;
+      }
+      for (int k = 0; k < 3; ++k) {  // rows p, q of A: the transposed rotation
+        const double x = A[3 * p + k], y = A[3 * q + k];
+        A[3 * p + k] = c * x - s * y;
+        A[3 * q + k] = s * x + c * y;
+      }
+    }
+  }
+  w[0] = A[0];
+  w[1] = A[4];
+  w[2] = A[8];
+}
+
+// a member's slot, or -1 when the id is not a present non-ion particle
+__device__ __forceinline__ int rb_slot(const SysParams &P, const MdParams &M, int id) {
+  const int s = M.perm_slot[id];
+  if (s < 0 || s >= P.ncell * P.cap) return -1;
+  if (P.pid[s] != (unsigned long long)id || is_ion_type(P.info[s] & 15)) return -1;
+  return s;
+}
+
+__device__ __forceinline__ double rb_min_image(double d, double L) { return d - L * rint(d / L); }
+
+__device__ __forceinline__ float rb_wrap(double x, double L, float Lf) {
+  x -= L * floor(x / L);
+  float f = __double2float_rn(x);
+  if (f >= Lf) f -= Lf;
+  if (f < 0.0f) f = 0.0f;
+  return f;
+}
+
+__global__ void __launch_bounds__(RB_THREADS) k_body_setup(SysParams P, MdParams M) {
+  __shared__ double sh[9 * RB_THREADS];
+  __shared__ double R_s[9], sub_s[3];
+  __shared__ int bad_s;
+  RigidBody *B = M.bodies + blockIdx.x;
+  const int t = threadIdx.x, first = B->first, count = B->count, mf = B->mfirst;
+  const double L = (double)P.Lf;
+  if (t == 0) bad_s = 0;
+  __syncthreads();
+  const int s0 = rb_slot(P, M, first);
+  if (s0 < 0) {
+    if (t == 0) B->bad = 1;
+    return;
+  }
+  const float4 p0 = P.pos[s0];
+  const double r0[3] = {(double)p0.x, (double)p0.y, (double)p0.z};
+  double a[6] = {0, 0, 0, 0, 0, 0};  // offset sums, momentum
+  for (int m = t; m < count; m += RB_THREADS) {
+    const int s = rb_slot(P, M, first + m);
+    if (s < 0) {
+      bad_s = 1;
+      continue;
+    }
+    const float4 p = P.pos[s], v = M.vel[s];
+    a[0] += rb_min_image((double)p.x - r0[0], L);
+    a[1] += rb_min_image((double)p.y - r0[1], L);
+    a[2] += rb_min_image((double)p.z - r0[2], L);
+    a[3] += (double)v.x;
+    a[4] += (double)v.y;
+    a[5] += (double)v.z;
+  }
+  rb_sum<6>(a, sh);
+  if (bad_s) {
+    if (t == 0) B->bad = 1;
+    return;
+  }
+  const double Mb = (double)count, sub[3] = {a[0] / Mb, a[1] / Mb, a[2] / Mb};
+  double b[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // dx dx, dy dy, dz dz, dx dy, dx dz, dy dz; angular momentum
+  for (int m = t; m < count; m += RB_THREADS) {
+    const int s = rb_slot(P, M, first + m);
+    const float4 p = P.pos[s], v = M.vel[s];
+    const double d[3] = {rb_min_image((double)p.x - r0[0], L) - sub[0], rb_min_image((double)p.y - r0[1], L) - sub[1],
+                         rb_min_image((double)p.z - r0[2], L) - sub[2]};
+    const double u[3] = {(double)v.x, (double)v.y, (double)v.z};
+    double l[3];
+    rb_cross(d, u, l);
+    b[0] += d[0] * d[0];
+    b[1] += d[1] * d[1];
+    b[2] += d[2] * d[2];
+    b[3] += d[0] * d[1];
+    b[4] += d[0] * d[2];
+    b[5] += d[1] * d[2];
+    b[6] += l[0];
+    b[7] += l[1];
+    b[8] += l[2];
+  }
+  rb_sum<9>(b, sh);
+  if (t == 0) {
+    double A[9] = {b[1] + b[2], -b[3], -b[4], -b[3], b[0] + b[2], -b[5], -b[4], -b[5], b[0] + b[1]};
+    double w[3], V[9];
+    rb_eigen(A, w, V);
+    int o[3] = {0, 1, 2};  // ascending moments
+    for (int i = 0; i < 3; ++i)
+      for (int j = i + 1; j < 3; ++j)
+        if (w[o[j]] < w[o[i]]) {
+          const int x = o[i];
+          o[i] = o[j];
+          o[j] = x;
+        }
+    double e[3][3];
+    for (int k = 0; k < 2; ++k) {  // the largest component of the first two axes positive
+      int big = 0;
+      for (int i = 0; i < 3; ++i) {
+        e[k][i] = V[3 * i + o[k]];
+        if (fabs(e[k][i]) > fabs(e[k][big])) big = i;
+      }
+      if (e[k][big] < 0.0)
+        for (int i = 0; i < 3; ++i) e[k][i] = -e[k][i];
+    }
+    rb_cross(e[0], e[1], e[2]);
+    for (int k = 0; k < 3; ++k) {
+      B->I[k] = w[o[k]];
+      for (int i = 0; i < 3; ++i) R_s[3 * i + k] = e[k][i];
+    }
+    for (int i = 0; i < 9; ++i) B->R[i] = R_s[i];
+    const double Lm[3] = {b[6], b[7], b[8]};
+    rb_tmul(R_s, Lm, B->pi);
+    for (int k = 0; k < 3; ++k) {
+      B->X[k] = r0[k] + sub[k];
+      B->V[k] = a[3 + k] / Mb;
+      B->F[k] = 0.0;
+      B->T[k] = 0.0;
+      sub_s[k] = sub[k];
+    }
+    B->M = Mb;
+    B->bad = (B->I[0] > 1e-9 * (B->I[0] + B->I[1] + B->I[2])) ? 0 : 1;
+  }
+  __syncthreads();
+  for (int m = t; m < count; m += RB_THREADS) {
+    const int s = rb_slot(P, M, first + m);
+    const float4 p = P.pos[s];
+    const double d[3] = {rb_min_image((double)p.x - r0[0], L) - sub_s[0],
+                         rb_min_image((double)p.y - r0[1], L) - sub_s[1],
+                         rb_min_image((double)p.z - r0[2], L) - sub_s[2]};
+    rb_tmul(R_s, d, M.body_d + 3 * (mf + m));
+  }
+}
+
+// the members' rigid velocities V + omega x (R d) (and, with newpos, the
+// positions X + R d after a drift, wrapped into the box)
+__device__ void rb_members(const SysParams &P, const MdParams &M, const RigidBody &B, bool newpos) {
+  double w[3], om[3];
+  for (int k = 0; k < 3; ++k) w[k] = B.pi[k] / B.I[k];
+  rb_mul(B.R, w, om);
+  const double L = (double)P.Lf;
+  for (int m = threadIdx.x; m < B.count; m += RB_THREADS) {
+    const int s = M.perm_slot[B.first + m];
+    double a[3], u[3];
+    rb_mul(B.R, M.body_d + 3 * (B.mfirst + m), a);
+    rb_cross(om, a, u);
+    float4 v = M.vel[s];
+    v.x = (float)(B.V[0] + u[0]);
+    v.y = (float)(B.V[1] + u[1]);
+    v.z = (float)(B.V[2] + u[2]);
+    M.vel[s] = v;
+    if (newpos)
+      M.body_newpos[B.mfirst + m] = make_float4(rb_wrap(B.X[0] + a[0], L, P.Lf), rb_wrap(B.X[1] + a[1], L, P.Lf),
+                                                rb_wrap(B.X[2] + a[2], L, P.Lf), 0.0f);
+  }
+}
+
+__global__ void __launch_bounds__(RB_THREADS) k_body_member_velocities(SysParams P, MdParams M) {
+  rb_members(P, M, M.bodies[blockIdx.x], false);
+}
+
+// three normals from the Philox block (body, 0, eval, purpose): the Box-Muller
+// form of the particles' Langevin noise, in FP64
+__device__ void rb_normals(uint32_t body, uint32_t eval, uint32_t purpose, uint32_t k0, uint32_t k1, double *g) {
+  const uint4 w = philox10(body, 0u, eval, purpose, k0, k1);
+  const double u0 = (double)(((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  const double u1 = (double)(((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  const double u2 = (double)(((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  const double u3 = (double)(((float)(w.w >> 8) + 0.5f) * (1.0f / 16777216.0f));
+  const double r1 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s3, &c3);
+  g[0] = r1 * c1;
+  g[1] = r1 * s1;
+  g[2] = r2 * c3;
+}
+
+// force and torque of each body from its members' conservative forces, plus
+// the Langevin terms; kick: the closing half kick; then the members' velocities
+__global__ void __launch_bounds__(RB_THREADS) k_body_forces(SysParams P, MdParams M, int kick) {
+  __shared__ double sh[6 * RB_THREADS];
+  __shared__ RigidBody B;
+  const int t = threadIdx.x;
+  if (t == 0) B = M.bodies[blockIdx.x];
+  __syncthreads();
+  double a[6] = {0, 0, 0, 0, 0, 0};
+  for (int m = t; m < B.count; m += RB_THREADS) {
+    const int s = M.perm_slot[B.first + m];
+    const float4 f4 = M.fout[s];
+    const double f[3] = {(double)f4.x, (double)f4.y, (double)f4.z};
+    double r[3], q[3];
+    rb_mul(B.R, M.body_d + 3 * (B.mfirst + m), r);
+    rb_cross(r, f, q);
+    for (int k = 0; k < 3; ++k) {
+      a[k] += f[k];
+      a[3 + k] += q[k];
+    }
+  }
+  rb_sum<6>(a, sh);
+  if (t == 0) {
+    double gt[3], gr[3], Lm[3], y[3], S[3];
+    rb_normals(blockIdx.x, M.eval, 8u, M.key0, M.key1, gt);
+    rb_normals(blockIdx.x, M.eval, 9u, M.key0, M.key1, gr);
+    const double gam = M.body_gamma, dt = M.body_dt;
+    const double at = sqrt(2.0 * gam * B.M / dt), ar = sqrt(2.0 * gam / dt);
+    rb_mul(B.R, B.pi, Lm);
+    rb_tmul(B.R, gr, y);
+    for (int k = 0; k < 3; ++k) y[k] *= sqrt(B.I[k]);
+    rb_mul(B.R, y, S);
+    for (int k = 0; k < 3; ++k) {
+      B.F[k] = a[k] - gam * B.M * B.V[k] + at * gt[k];
+      B.T[k] = a[3 + k] - gam * Lm[k] + ar * S[k];
+    }
+    if (kick) {
+      double tb[3];
+      rb_tmul(B.R, B.T, tb);
+      for (int k = 0; k < 3; ++k) {
+        B.V[k] += 0.5 * dt * B.F[k] / B.M;
+        B.pi[k] += 0.5 * dt * tb[k];
+      }
+    }
+    M.bodies[blockIdx.x] = B;
+  }
+  __syncthreads();
+  if (kick) rb_members(P, M, B, false);
+}
+
+// exact free rotation about body axis k for a time h
+__device__ void rb_rotate(RigidBody &B, int k, double h) {
+  const double th = h * B.pi[k] / B.I[k];
+  double s, c;
+  sincos(th, &s, &c);
+  const int i = (k + 1) % 3, j = (k + 2) % 3;
+  for (int r = 0; r < 3; ++r) {
+    const double x = B.R[3 * r + i], y = B.R[3 * r + j];
+    B.R[3 * r + i] = c * x + s * y;
+    B.R[3 * r + j] = -s * x + c * y;
+  }
+  const double pi_i = B.pi[i], pi_j = B.pi[j];
+  B.pi[i] = c * pi_i + s * pi_j;
+  B.pi[j] = -s * pi_i + c * pi_j;
+}
+
+// the opening half kick and the drift of each body, the members' new
+// positions into body_newpos and their velocities
+__global__ void __launch_bounds__(RB_THREADS) k_body_drift(SysParams P, MdParams M) {
+  __shared__ RigidBody B;
+  if (threadIdx.x == 0) {
+    B = M.bodies[blockIdx.x];
+    const double dt = M.body_dt;
+    double tb[3];
+    rb_tmul(B.R, B.T, tb);
+    for (int k = 0; k < 3; ++k) {
+      B.V[k] += 0.5 * dt * B.F[k] / B.M;
+      B.pi[k] += 0.5 * dt * tb[k];
+      B.X[k] += dt * B.V[k];
+    }
+    rb_rotate(B, 0, 0.5 * dt);
+    rb_rotate(B, 1, 0.5 * dt);
+    rb_rotate(B, 2, dt);
+    rb_rotate(B, 1, 0.5 * dt);
+    rb_rotate(B, 0, 0.5 * dt);
+    M.bodies[blockIdx.x] = B;
+  }
+  __syncthreads();
+  rb_members(P, M, B, true);
+}
+
 cudaError_t launch_step_advance(StepDyn *dyn, cudaStream_t s) {
   k_step_advance<<<1, 32, 0, s>>>(dyn);
   return cudaGetLastError();
@@ -504,12 +865,14 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
     else if (P.h == 1 && P.nc >= 3) k_md_forces<3, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
     else k_md_forces<0, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
   }
+  if (M.n_bodies > 0 && M.mode != 0) k_body_forces<<<M.n_bodies, RB_THREADS, 0, s>>>(P, Q, M.mode == 2 ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_kick_drift_rebuild(const SysParams &P, const MdParams &M, const RebuildBufs &B, int *perm_slot,
                                       int n_perm, cudaStream_t s) {
   const int n = P.ncell * P.cap;
+  if (M.n_bodies > 0) k_body_drift<<<M.n_bodies, RB_THREADS, 0, s>>>(P, M);
   k_md_kick_drift_scatter<<<(n + 255) / 256, 256, 0, s>>>(P, M, B);
   k_rebuild_sort<<<(P.ncell * 32 + 255) / 256, 256, 0, s>>>(P, B, perm_slot, n_perm);
   return cudaGetLastError();
@@ -529,6 +892,16 @@ cudaError_t launch_load_batch(const SysParams *d_reps, const LoadJob *d_jobs, in
   if (max_n > 0) k_load_scatter_batch<<<dim3((max_n + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
   k_rebuild_sort_batch<<<dim3((max_cells * 32 + 255) / 256, n_rep), 256, 0, s>>>(d_reps, d_jobs);
   k_load_neutral_batch<<<n_rep, 32, 0, s>>>(d_reps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_body_setup(const SysParams &P, const MdParams &M, cudaStream_t s) {
+  if (M.n_bodies > 0) k_body_setup<<<M.n_bodies, RB_THREADS, 0, s>>>(P, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_body_member_velocities(const SysParams &P, const MdParams &M, cudaStream_t s) {
+  if (M.n_bodies > 0) k_body_member_velocities<<<M.n_bodies, RB_THREADS, 0, s>>>(P, M);
   return cudaGetLastError();
 }
 
