@@ -131,8 +131,13 @@ typedef struct {
  * carried by the accepted trials within it.  Only with CR_SCHED_GLOBAL, the
  * paper's one-trial-at-a-time rule: trials of different domains would
  * interact through S(k), so concurrent domain-local trials would not be
- * independent.  MD (forces are DSF) and delayed acceptance are not available
- * with Ewald (INVALID_ARG).  ewald_kmax <= 32. */
+ * independent.  MD forces are minus the gradient of the same energy: the
+ * real-space erfc pair forces plus F_j = 2 q_j sum_k A_k k Im(S(k)^*
+ * exp(i k.r_j)) (A_k the weights above), S(k) recomputed from the positions
+ * at every force evaluation (cr_md_forces, cr_md_step, cr_md_begin /
+ * cr_md_end).  Not available with Ewald (INVALID_ARG): delayed acceptance,
+ * the captured batch cycle (cr_batch_cycle), cr_md_forces_noalloc and rigid
+ * bodies.  ewald_kmax <= 32. */
 
 /* Reservoir ions: pI_S of the symmetric salt per sign and pKw; with
  * pIX_explicit = 1 the grouped pI_X+- are taken as given (e.g. pIX+ = pH,

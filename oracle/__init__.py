@@ -23,7 +23,8 @@ _LIB = os.path.join(_HERE, "libcrmc_oracle.so")
 F_ACC, F_NOELIG, F_EDGE, F_OVERLAP = 1, 2, 4, 8
 PLANT = {"none": 0, "drop_ion_count": 1, "dE_sign": 2, "drop_self": 3, "drop_pair_cc": 4,
          "wrong_volume": 5, "da_one_sided": 6, "da_stage2_full": 7, "species_count": 8,
-         "ewald_half_recip": 9, "rigid_torque_sign": 10, "rigid_no_rot_noise": 11}
+         "ewald_half_recip": 9, "rigid_torque_sign": 10, "rigid_no_rot_noise": 11,
+         "ewald_force_sign": 12}
 N_FEAT, N_HID = 48, 128
 
 

@@ -68,7 +68,8 @@ enum { F_ACC = 1, F_NOELIG = 2, F_EDGE = 4, F_OVERLAP = 8 };
 enum { PLANT_NONE = 0, PLANT_DROP_ION_COUNT = 1, PLANT_DE_SIGN = 2,
        PLANT_DROP_SELF = 3, PLANT_DROP_PAIR_CC = 4, PLANT_WRONG_VOLUME = 5,
        PLANT_DA_ONE_SIDED = 6, PLANT_DA_STAGE2_FULL = 7, PLANT_SPECIES_COUNT = 8,
-       PLANT_EWALD_HALF_RECIP = 9, PLANT_RIGID_TORQUE_SIGN = 10, PLANT_RIGID_NO_ROT_NOISE = 11 };
+       PLANT_EWALD_HALF_RECIP = 9, PLANT_RIGID_TORQUE_SIGN = 10, PLANT_RIGID_NO_ROT_NOISE = 11,
+       PLANT_EWALD_FORCE_SIGN = 12 };
 
 /* ----------------------------------------------------------------------- */
 /* Philox4x32-10: 10 rounds of the Philox S-box on a 128-bit counter with a
@@ -1331,9 +1332,38 @@ double or_bond_energy(const Oracle *o) {
 }
 
 /* ----------------------------------------------------------------------- */
+/* Reciprocal-space Ewald forces, minus the gradient of E_rec over r_j:
+ * F_j = 2 q_j sum_k A_k k Im(S(k)^* exp(i k.r_j)), Im(...) = C sin - D cos
+ * with S = C + i D of the current positions (every k of the sphere).  fs
+ * gets the per-component sums of the terms' magnitudes. */
+static void ewald_recip_forces(const Oracle *o, double *F, double *fs) {
+  double *re = malloc((size_t)o->nk * sizeof(double)), *im = malloc((size_t)o->nk * sizeof(double));
+  ewald_structure(o, re, im);
+  const double kf = 2.0 * M_PI / o->L;
+  for (int j = 0; j < o->n; ++j) {
+    const double q = qeff(o, o->type[j], o->st[j]);
+    if (q == 0.0) continue;
+    for (int i = 0; i < o->nk; ++i) {
+      const double ph = ewald_phase(o, i, o->x[j], o->y[j], o->z[j]);
+      double t = 2.0 * q * o->kA[i] * (re[i] * sin(ph) - im[i] * cos(ph));
+      if (g_plant == PLANT_EWALD_FORCE_SIGN) t = -t;
+      for (int c = 0; c < 3; ++c) {
+        const double fc = t * kf * (double)o->kn[3 * i + c];
+        F[3 * j + c] += fc;
+        if (fs) fs[3 * j + c] += fabs(fc);
+      }
+    }
+  }
+  free(re);
+  free(im);
+}
+
+/* ----------------------------------------------------------------------- */
 /* MD: conservative forces (DSF Coulomb + WCA over all pairs within the
  * cutoffs, brute force with the minimum image, plus FENE bonds
- * U = -K R0^2/2 ln(1 - (r/R0)^2)).  fs: per component sum of |pair force|. */
+ * U = -K R0^2/2 ln(1 - (r/R0)^2)); with Ewald electrostatics the real-space
+ * erfc pair forces plus the reciprocal-space forces.  fs: per component sum
+ * of |pair force|. */
 static int forces_cons(const Oracle *o, double *F, double *fs) {
   memset(F, 0, (size_t)o->n * 3 * sizeof(double));
   if (fs) memset(fs, 0, (size_t)o->n * 3 * sizeof(double));
@@ -1365,6 +1395,7 @@ static int forces_cons(const Oracle *o, double *F, double *fs) {
       }
     }
   }
+  if (o->ewald_kmax > 0) ewald_recip_forces(o, F, fs);
   if (o->nb > 0) {
     /* permanent particles keep their input index as id; map id -> index */
     int *where = malloc((size_t)o->cap * sizeof(int));
@@ -1390,7 +1421,6 @@ static int forces_cons(const Oracle *o, double *F, double *fs) {
 }
 
 int32_t or_forces(const Oracle *o, double *F, double *fs) {
-  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   return forces_cons(o, F, fs);
 }
 
@@ -1748,7 +1778,6 @@ int32_t or_set_body_state(Oracle *o, const double *in, int32_t nb) {
  * evaluation (unit mass, kT = 1).  Forces are re-evaluated first when the
  * CR-MC stage changed the system since the last evaluation. */
 int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t seed) {
-  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = OR_OK;
   if (!o->f_valid) {
@@ -1790,7 +1819,6 @@ int32_t or_md_step(Oracle *o, int32_t n_steps, double dt, double gamma, uint64_t
  * charges after any CR-MC trials run in between) and does the closing half
  * kick.  begin + end with nothing in between is or_md_step with one step. */
 int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
-  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = OR_OK;
   if (!o->f_valid) {
@@ -1814,7 +1842,6 @@ int32_t or_md_begin(Oracle *o, double dt, double gamma, uint64_t seed) {
 }
 
 int32_t or_md_end(Oracle *o, double dt, double gamma, uint64_t seed) {
-  if (o->ewald_kmax > 0) return OR_ERR_ARG; /* MD forces are DSF only */
   double *F = malloc((size_t)(o->n > 0 ? o->n : 1) * 3 * sizeof(double));
   int rc = forces_cons(o, F, NULL);
   if (!rc) {

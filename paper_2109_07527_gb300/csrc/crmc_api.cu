@@ -1304,6 +1304,10 @@ static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
   tbegin(ctx, 1, &ti);
   MdParams Q = M;
   Q.fsum = ctx->d_fsum;
+  if (ctx->P.ewald_nk > 0) {  // S(k) of the current positions for the reciprocal forces
+    CR_CUDA(launch_ewald_sk(ctx->d_reps, 1, ctx->P.ewald_nk, ctx->stream));
+    ctx->launches_total += 3;  // occupied slots, S(k), reciprocal forces
+  }
   CR_CUDA(launch_md_forces(ctx->P, Q, ctx->d_plist, ctx->d_nparts, (int)ctx->capacity, ctx->stream));
   tend(ctx, 1, ti);
   ctx->launches_total += 3;  // particle list, pair forces, per-particle finish
@@ -1311,7 +1315,7 @@ static int md_force_eval(cr_ctx *ctx, const MdParams &M) {
 }
 
 extern "C" int cr_md_forces(cr_ctx *ctx) {
-  if (!ctx || ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
+  if (!ctx) return CR_ERR_INVALID_ARG;
   int rc = md_force_eval(ctx, md_params(ctx, 0, 0.0, 0.0, 0));
   if (rc != CR_OK) return rc;
   ctx->fcons_valid = true;
@@ -1320,7 +1324,6 @@ extern "C" int cr_md_forces(cr_ctx *ctx) {
 
 extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma, uint64_t seed) {
   if (!ctx || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
-  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1343,7 +1346,6 @@ extern "C" int cr_md_step(cr_ctx *ctx, int32_t n_steps, double dt, double gamma,
 
 extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
-  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   cudaStream_t s = ctx->stream;
   const SysParams &P = ctx->P;
   RebuildBufs B{ctx->d_cnt2, ctx->d_pos2, ctx->d_pid2, ctx->d_info2, ctx->d_vel2, ctx->d_frc2, ctx->d_vel, ctx->d_frc};
@@ -1371,7 +1373,6 @@ static int md_end_impl(cr_ctx *ctx, double dt, double gamma, uint64_t seed, cons
 
 extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
   if (!ctx || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
-  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;
   int rc;
   if ((rc = md_end_impl(ctx, dt, gamma, seed, nullptr, 0)) != CR_OK) return rc;
   ctx->md_eval++;
@@ -2249,7 +2250,7 @@ extern "C" int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double ga
                               uint64_t md_seed0, int32_t da) {
   if (!b || n_steps < 0 || !(dt > 0.0) || !(gamma >= 0.0)) return CR_ERR_INVALID_ARG;
   for (cr_ctx *c : b->ctx)
-    if (c->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
+    if (c->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // the captured cycle has no S(k) nodes
   cr_ctx *c0 = b->ctx[0];
   cudaStream_t s = c0->stream;
   if (da)
@@ -2531,7 +2532,7 @@ extern "C" int cr_batch_get_launch_shape(const cr_batch *b, int32_t *threads, in
 namespace crmc {
 
 int ctx_md_forces_into(cr_ctx *ctx, float4 *fout, int *plist, int *n_particles, int max_particles) {
-  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // MD forces are DSF only
+  if (ctx->P.ewald_nk > 0) return CR_ERR_INVALID_ARG;  // no S(k) scratch here: DSF forces only
   MdParams M = md_params(ctx, 0, 0.0, 0.0, 0);
   M.fout = fout;
   CR_CUDA(launch_md_forces(ctx->P, M, plist, n_particles, max_particles, ctx->stream));

@@ -3,8 +3,10 @@ evaluated as a direct Ewald sum) under the global schedule, trial by trial
 against the oracle: moves, chosen ids and decisions identical, Delta E within
 1e-6 of the gross term sum (the reciprocal part's FP32 terms and structure-
 factor updates included), final states identical; batches of replicas equal
-the per-replica oracle runs; MD, delayed acceptance and the coloured schedule
-are refused with Ewald."""
+the per-replica oracle runs; the MD forces (real-space erfc plus reciprocal
+part) equal the oracle's and MD/CR-MC cycles follow it; delayed acceptance,
+the coloured schedule, rigid bodies and the captured cycle are refused with
+Ewald."""
 import numpy as np
 import pytest
 
@@ -75,13 +77,76 @@ def test_ewald_refusals(crmc):
         crmc.Context(w, schedule=crmc.SCHED_COLOURED)
     assert e.value.code == -1
     g = crmc.Context(w)
-    for f in (lambda: g.md_forces(), lambda: g.md_step(1, 0.005, 1.0, 1), lambda: g.md_begin(0.005, 1.0, 1),
-              lambda: g.set_surrogate(W.random_mlp(seed=1))):
+    for f in (lambda: g.set_surrogate(W.random_mlp(seed=1)), lambda: g.set_rigid_bodies([0], [2])):
         with pytest.raises(crmc.CrError) as e:
             f()
         assert e.value.code == -1
+    b = crmc.Batch([g])
+    with pytest.raises(crmc.CrError) as e:
+        b.cycle(1, 0.005, 1.0, 1, 2)
+    assert e.value.code == -1
+    b.close()
     g.sweep(g.trials_per_sweep, 3)  # the context still works
     g.close()
+
+
+F_REL = 4e-6  # FP32 force terms against FP64, relative to the gross sum of the terms
+
+
+@pytest.mark.parametrize("box", ["small", "paper"])
+def test_ewald_md_forces_match_oracle(crmc, box):
+    if box == "small":
+        w = _electrolyte()
+    else:  # the method comparison's box, |n| <= 10
+        w = _electrolyte(n_acid=500, L=100.0, rc=20.0, alpha=0.16, kmax=10, m=50, seed=1)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    n = g.trials_per_sweep * 6
+    lg = g.sweep(n, 9, log=True)["log"]
+    lo = o.sweep(n, 9, log=True)["log"]
+    assert np.array_equal(lg["flags"], lo["flags"])
+    g.md_forces()
+    st = g.state()
+    ids, F, S = o.forces()
+    assert np.array_equal(st["id"], ids)
+    err = np.abs(st["force"].astype(np.float64) - F)
+    assert np.all(err <= F_REL * S + 2e-6), (np.argmax(err - F_REL * S), err.max())
+    assert np.abs(F).max() > 0.05  # not vacuous
+
+
+def _wrapdiff(a, b, L):
+    d = a.astype(np.float64) - b.astype(np.float64)
+    return d - L * np.round(d / L)
+
+
+def test_ewald_md_cycles_match_oracle(crmc):
+    """md_begin -> sweep -> md_end under Ewald: positions and velocities within the
+    MD tolerances, the trials decision by decision (the oracle synchronised to the
+    GPU's positions after the drift)."""
+    w = _electrolyte(seed=4)
+    w.vel = np.random.default_rng(4).normal(size=(w.n, 3)).astype(np.float32)
+    g = crmc.Context(w)
+    o = oracle.Oracle(w)
+    L = float(np.float32(w.params["box_L"]))
+    n = g.trials_per_sweep * 2
+    for cyc in range(5):
+        g.md_begin(0.005, 1.0, 31)
+        o.md_begin(0.005, 1.0, 31)
+        sg, so = g.state(), o.particles()
+        assert np.array_equal(sg["id"], so["id"])
+        assert np.abs(_wrapdiff(sg["xyz"], so["xyz"], L)).max() < 2e-5
+        assert np.abs(sg["vel"] - so["vel"]).max() < 2e-4
+        o.set_positions(sg["id"], sg["xyz"], sg["vel"])
+        lg = g.sweep(n, 60 + cyc, log=True)["log"]
+        lo = o.sweep(n, 60 + cyc, log=True)["log"]
+        assert np.array_equal(lg["flags"], lo["flags"]) and np.array_equal(lg["id_a"], lo["id_a"])
+        g.md_end(0.005, 1.0, 31)
+        o.md_end(0.005, 1.0, 31)
+        sg, so = g.state(), o.particles()
+        assert np.array_equal(sg["id"], so["id"])
+        assert np.abs(_wrapdiff(sg["xyz"], so["xyz"], L)).max() < 2e-5
+        assert np.abs(sg["vel"] - so["vel"]).max() < 2e-4
+    g.check()
 
 
 def test_ewald_with_invocations_and_a_pH_change(crmc):

@@ -11,7 +11,11 @@ checked against values that do not come from its own formula:
 * Delta E = E_after - E_before for every accepted trial of a CR-MC run under
   the global schedule (the trials' reciprocal part is an update of S(k), the
   energy a recomputation from scratch);
-* planted mistakes (half the reciprocal part, no self term) fail these pins.
+* planted mistakes (half the reciprocal part, no self term) fail these pins;
+* the MD forces (real-space erfc pair forces plus the reciprocal-space forces)
+  are minus the gradient of the Ewald energy (central finite differences),
+  sum to zero, and keep kinetic plus potential energy in a run without the
+  thermostat; a reciprocal force of the wrong sign fails the gradient pin.
 """
 import math
 
@@ -148,3 +152,64 @@ def test_ewald_needs_the_global_schedule():
     w = _cr_system()
     with pytest.raises(ValueError):
         oracle.Oracle(w, schedule=0)
+
+
+def _ionised(seed=3):
+    w = _cr_system(seed)
+    o = oracle.Oracle(w)
+    o.sweep(o.trials_per_sweep * 30, 11)  # ionise acids, insert ions
+    return o
+
+
+def _fd_errors(o, n_pick=10, h=1e-3):
+    ids, F, S = o.forces()
+    p = o.particles()
+    xyz = p["xyz"].copy()
+    charged = np.flatnonzero(np.isin(p["type"], (W.XP, W.XM)) | (p["state"] == 1))
+    picks = np.random.default_rng(0).choice(charged, size=n_pick, replace=False)
+    worst = 0.0
+    for i in picks:
+        for c in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[i, c] = np.float32(xyz[i, c] + h)
+            xm[i, c] = np.float32(xyz[i, c] - h)
+            hh = float(xp[i, c]) - float(xm[i, c])
+            o.set_positions(p["id"], xp)
+            ep = o.energy()
+            o.set_positions(p["id"], xm)
+            em = o.energy()
+            worst = max(worst, abs(-(ep - em) / hh - F[i, c]) / max(1.0, S[i, c]))
+    o.set_positions(p["id"], xyz)
+    return worst, F, S
+
+
+def test_ewald_forces_are_minus_energy_gradient():
+    o = _ionised()
+    worst, F, S = _fd_errors(o)
+    assert worst < 2e-4, worst
+    assert np.abs(F).max() > 0.1  # not vacuous
+    assert np.all(np.abs(F.sum(0)) < 1e-9 * max(1.0, S.sum()))  # Newton's third law, reciprocal part included
+
+
+def test_planted_reciprocal_force_sign_fails_the_gradient_pin():
+    oracle.plant("ewald_force_sign")
+    try:
+        o = _ionised()
+        worst, _, _ = _fd_errors(o)
+    finally:
+        oracle.plant("none")
+    assert worst > 1e-2, worst
+
+
+def test_ewald_md_conserves_energy():
+    o = _ionised(seed=5)
+    o.md_step(1, 0.002, 0.0, 1)
+
+    def etot():
+        v = o.particles()["vel"]
+        return o.energy() + 0.5 * float((v * v).sum())
+
+    e0 = etot()
+    o.md_step(200, 0.002, 0.0, 1)
+    e1 = etot()
+    assert abs(e1 - e0) < 1e-4, (e0, e1)  # velocity Verlet at dt = 0.002 (1.5e-6 measured)
