@@ -654,6 +654,41 @@ def run_config3_mobile(crmc, torch, stream, flush, steps):
     return out
 
 
+def run_ewald_md(crmc, torch, stream, flush, steps):
+    """MD/CR-MC cycles of the method comparison's weak-acid electrolyte (500
+    acids, L = 100, pH 7) under Ewald electrostatics (alpha 0.15, r_c 20,
+    |n| <= 16, global schedule) against the same box with the DSF energy
+    (r_c 20): each step one MD step (dt 0.005, gamma 1) around one sweep of
+    250 trials; the force evaluations timed by CUDA events."""
+    from paper_2109_07527_gb300 import workloads as W
+    out = {"workload": "weak-acid electrolyte, 500 acids, L=100, pH 7, alpha 0.15, r_c 20, global schedule, "
+                       "one MD step around 250 trials per step"}
+    for name, kmax in (("ewald", 16), ("dsf", 0)):
+        w = W.weak_acid_electrolyte(n_acid=500, L=100.0, pH=7.0, rc=20.0, seed=1, trials_per_domain=250)
+        w.params["ewald_kmax"] = kmax
+        g = crmc.Context(w)
+        n = g.trials_per_sweep
+
+        def step(s):
+            g.md_begin(0.005, 1.0, 300 + s)
+            g.sweep(n, 500 + s)
+            g.md_end(0.005, 1.0, 300 + s)
+
+        for s in range(40):  # ions appear, the launch-shape tuner settles
+            step(s)
+        g.set_timing(True)
+        g.timing(reset=True)
+        ms = time_steps(lambda s: step(1000 + s), steps, stream, flush)
+        tm = g.timing(reset=True)
+        g.check()
+        st = g.state()
+        out[name] = {"md_cr_cycles_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "md_force_ms_per_eval": tm["md_ms"] / max(1, tm["md_launches"]),
+                     "particles": int(st["n"]), "alpha_end": float(st["alpha"])}
+        g.close()
+    return out
+
+
 def time_steps(step_fn, steps, stream, flush):
     import torch
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -782,6 +817,7 @@ def run_ours(args):
     if rank == 0 and not args.no_fig2:
         fig2 = run_method_comparison(crmc)
         fig2_ewald = run_method_comparison(crmc, n_rep=64, blocks=20, ewald_kmax=16)
+        fig2_ewald["md_cycles"] = run_ewald_md(crmc, torch, stream, flush, 20)
 
     # ---- end to end through the public API with host buffers: each step
     # uploads every replica's configuration from pinned host memory, runs the
