@@ -136,8 +136,8 @@ typedef struct {
  * exp(i k.r_j)) (A_k the weights above), S(k) recomputed from the positions
  * at every force evaluation (cr_md_forces, cr_md_step, cr_md_begin /
  * cr_md_end).  Not available with Ewald (INVALID_ARG): delayed acceptance,
- * the captured batch cycle (cr_batch_cycle), cr_md_forces_noalloc and rigid
- * bodies.  ewald_kmax <= 32. */
+ * the captured batch cycle (cr_batch_cycle) and cr_md_forces_noalloc.
+ * ewald_kmax <= 32. */
 
 /* Reservoir ions: pI_S of the symmetric salt per sign and pKw; with
  * pIX_explicit = 1 the grouped pI_X+- are taken as given (e.g. pIX+ = pH,
@@ -322,8 +322,8 @@ int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed);
  * for dt/2, dt/2, dt, dt/2, dt/2); members sit at X + R d, wrapped, with the
  * velocity V + omega x (R d).  Body arithmetic in FP64.  CR-MC trials change
  * the members' charge states as before.  n_bodies = 0 removes the bodies.
- * Errors: INVALID_ARG (a range or member as above, collinear members, Ewald
- * electrostatics, a context in a batch); nothing changes then.  While bodies
+ * Errors: INVALID_ARG (a range or member as above, collinear members, a
+ * context in a batch); nothing changes then.  While bodies
  * are declared, cr_load and cr_restore are refused (declare them again after
  * a load into a fresh context) and the context cannot join a batch.
  * cr_rigid_body_state writes 22 doubles per body: X[3], V[3], R[9]

@@ -1209,7 +1209,7 @@ static void free_bodies(cr_ctx *ctx) {
 extern "C" int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t *first, const int32_t *count) {
   if (!ctx || n_bodies < 0 || n_bodies > CR_MAX_BODIES || (n_bodies > 0 && (!first || !count)))
     return CR_ERR_INVALID_ARG;
-  if (ctx->P.ewald_nk > 0 || ctx->batch_refs > 0) return CR_ERR_INVALID_ARG;
+  if (ctx->batch_refs > 0) return CR_ERR_INVALID_ARG;
   std::vector<int> member((size_t)std::max(ctx->n_input, 1), -1);
   std::vector<RigidBody> hb((size_t)n_bodies);
   int64_t nm = 0;

@@ -5,8 +5,7 @@ against the oracle: moves, chosen ids and decisions identical, Delta E within
 factor updates included), final states identical; batches of replicas equal
 the per-replica oracle runs; the MD forces (real-space erfc plus reciprocal
 part) equal the oracle's and MD/CR-MC cycles follow it; delayed acceptance,
-the coloured schedule, rigid bodies and the captured cycle are refused with
-Ewald."""
+the coloured schedule and the captured cycle are refused with Ewald."""
 import numpy as np
 import pytest
 
@@ -77,7 +76,7 @@ def test_ewald_refusals(crmc):
         crmc.Context(w, schedule=crmc.SCHED_COLOURED)
     assert e.value.code == -1
     g = crmc.Context(w)
-    for f in (lambda: g.set_surrogate(W.random_mlp(seed=1)), lambda: g.set_rigid_bodies([0], [2])):
+    for f in (lambda: g.set_surrogate(W.random_mlp(seed=1)),):
         with pytest.raises(crmc.CrError) as e:
             f()
         assert e.value.code == -1

@@ -124,6 +124,14 @@ def test_cycles_match_oracle_full_size(crmc):
     _cycles(crmc, w, 2, trials_mult=1)
 
 
+def test_cycles_match_oracle_with_ewald(crmc):
+    """The same cycles under Ewald electrostatics (global schedule, |n| <= 6):
+    the bodies feel the reciprocal-space forces too."""
+    w = _pair(seed=6)
+    w.params.update(schedule=1, ewald_kmax=6, trials_per_domain=100)
+    _cycles(crmc, w, 4)
+
+
 def test_md_step_equals_begin_end_and_bodies_stay_rigid(crmc):
     w = _pair(seed=4)
     first, count = w.meta["bodies"]
