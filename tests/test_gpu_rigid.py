@@ -124,6 +124,20 @@ def test_cycles_match_oracle_full_size(crmc):
     _cycles(crmc, w, 2, trials_mult=1)
 
 
+def test_cycles_match_oracle_across_the_periodic_boundary(crmc):
+    """The first nanoparticle centred on the box corner, so that it straddles
+    all three periodic boundaries."""
+    w = _pair(seed=7)
+    L = float(w.params["box_L"])
+    x = np.mod(w.xyz.astype(np.float64) + [L / 2 + 4.5, L / 2, L / 2], L).astype(np.float32)
+    x[x >= np.float32(L)] = 0.0
+    w.xyz = x
+    first, count = w.meta["bodies"]
+    nb = x[first[0]:first[0] + count[0]]
+    assert np.all(nb.min(0) < 2.0) and np.all(nb.max(0) > L - 2.0)  # split by every boundary
+    _cycles(crmc, w, 4)
+
+
 def test_cycles_match_oracle_with_ewald(crmc):
     """The same cycles under Ewald electrostatics (global schedule, |n| <= 6):
     the bodies feel the reciprocal-space forces too."""
