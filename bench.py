@@ -353,8 +353,8 @@ def measured_tensor_peak():
 
 # unlogged sweeps that time every launch shape once: 12 plain shapes for a
 # context; for a batch each of them also as a persistent sweep (24)
-TUNE_SWEEPS = 14
-BATCH_TUNE_SWEEPS = 26
+TUNE_SWEEPS = 26  # the context tuner: 12 shapes, two passes
+BATCH_TUNE_SWEEPS = 50  # the batch tuner: 12 shapes in two launch forms, two passes
 
 # exact (feature, pair energy) pairs recorded for the surrogate's training
 TRAIN_PAIRS = 1_000_000
@@ -423,7 +423,7 @@ def run_da(crmc, torch, stream, flush, ws, dt, gamma, steps):
     for c in ctxs:
         c.set_surrogate(mlp)
     b = crmc.Batch(ctxs)
-    b.sweep_da(12, 0xDA)  # launch-shape tuning of the DA variant (5 shapes, each in both launch forms)
+    b.sweep_da(22, 0xDA)  # launch-shape tuning of the DA variant (5 shapes in both launch forms, two passes)
     for s in range(3):
         b.cycle(1, dt, gamma, 1 + s, 1000 + s, da=True)
 
@@ -467,7 +467,7 @@ def run_config5(crmc, torch, stream, flush, mlp, steps):
     g.close()
     h = crmc.Context(w5)
     h.set_surrogate(mlp)
-    h.sweep_da(tps * 6, 0x55)  # DA shapes
+    h.sweep_da(tps * 11, 0x55)  # DA shapes (5, two passes)
     ms_da = time_steps(lambda s: h.sweep_da(tps, 300 + s), steps, stream, flush)
     a_da = h.counts()["alpha"]
     r = h.sweep_da(tps, 999, log=True, features=False)
@@ -637,7 +637,7 @@ def run_config3_mobile(crmc, torch, stream, flush, steps):
         g.sweep(n, 9000 + s)
         g.md_end(dt, gamma, 7000 + s)
 
-    for s in range(5):
+    for s in range(TUNE_SWEEPS + 4):  # the launch-shape tuner's sweeps and a warm-up
         step(s)
     b0 = g.rigid_body_state()
     ms = time_steps(lambda s: step(100 + s), steps, stream, flush)

@@ -417,8 +417,9 @@ int cr_restore(cr_ctx *ctx, int32_t n, const float *xyz, const float *vel, const
 /* Launch shape of the colour-phase kernel: threads per domain and halo
  * particles held in registers per thread.  Supported pairs: (32|64|128|256|512,
  * 0) halo in shared memory; (128, 4), (256, 2), (512, 1) halo in registers.
- * By default the first unlogged sweeps time every supported shape once (with
- * full and with compact shared-memory capacities) and keep the fastest; the
+ * By default the first unlogged sweeps time every supported shape (with full
+ * and with compact shared-memory capacities) in two passes, one shape per
+ * sweep, and keep the shape with the shortest time; the
  * trial outcomes never depend on the shape (the energy sums are exact fixed
  * point).  cr_set_launch_shape(ctx, 0, 0) restarts the tuning; an unsupported
  * pair gives CR_ERR_INVALID_ARG. */
@@ -603,8 +604,8 @@ int cr_batch_state(cr_batch *b, cr_state_view *views);
  * batch.  Mode 2: a domain waits for its replica's whole previous colour
  * (also what mode 1 does when a replica's halo reaches past its neighbouring
  * domains).  Mode 0: one launch per colour.  Mode -1 (the default): the
- * launch-shape tuner times every shape in both forms (mode 1 and mode 0) and
- * keeps the fastest; fixing a shape with cr_batch_set_launch_shape then
+ * launch-shape tuner times every shape in both forms (mode 1 and mode 0), in
+ * two passes, and keeps the fastest; fixing a shape with cr_batch_set_launch_shape then
  * selects mode 0 unless a mode was set.  ctas_per_sm > 0 caps the
  * resident CTAs per SM of a persistent launch (0: as many as fit).  Every
  * wait is bounded in time; one that runs out sets CR_ERR_TIMEOUT on its

@@ -31,7 +31,7 @@ struct cr_ctx {
   // on it: the energy sums are exact fixed point)
   int T = 128, R = 4;
   int smem_max = 0;
-  int tune_next = 0;     // next candidate to time; >= count when done
+  int tune_next = 0;     // sweeps timed so far (TUNE_ROUNDS passes over the candidates)
   bool tuning = true;
   float tune_ms[16] = {};
   PhaseShape S{};   // shared-memory capacities for the densest domain
@@ -954,11 +954,16 @@ static int grow(TT **p, size_t *cap, size_t n) {
 }
 
 // Online launch-shape tuning (shared by plain and delayed-acceptance sweeps):
-// the first sweeps of unlogged calls time each shape of the set once (shapes
-// whose shared memory does not fit are skipped), then the fastest is kept.
+// the first sweeps of unlogged calls time each shape of the set (shapes whose
+// shared memory does not fit are skipped) in TUNE_ROUNDS round-robin passes,
+// and the shape with the shortest of its times is kept: a single pass was
+// swayed by one slow sweep and by the state's drift while the chain starts.
 // For batches whose persistent mode is left to the tuner (pers != null), the
 // candidates are every shape with one launch per colour, then every shape as
-// a persistent sweep; *pers receives the chosen mode.
+// a persistent sweep; *pers receives the chosen mode.  next counts the timed
+// sweeps; candidate next % tune_count.
+constexpr int TUNE_ROUNDS = 2;
+
 struct TuneRef {
   int &T, &R, &next;
   bool &on;
@@ -968,23 +973,29 @@ struct TuneRef {
 };
 
 static int tune_count(const TuneRef &t, bool da) { return phase_shape_count(da) * (t.pers ? 2 : 1); }
+static int tune_total(const TuneRef &t, bool da) { return tune_count(t, da) * TUNE_ROUNDS; }
+static int tune_cand(const TuneRef &t, bool da) { return t.next % tune_count(t, da); }
 
 static void tune_skip(TuneRef t, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
   const int nshape = phase_shape_count(da);
-  while (t.on && t.next < tune_count(t, da)) {
+  while (t.on && t.next < tune_total(t, da)) {
+    const int c = tune_cand(t, da);
     int t_, r_;
-    phase_shape(t.next % nshape, &t_, &r_, da);
-    const PhaseShape &Q = phase_shape_compact(t.next % nshape, da) ? Sc : S;
+    phase_shape(c % nshape, &t_, &r_, da);
+    const PhaseShape &Q = phase_shape_compact(c % nshape, da) ? Sc : S;
     if (phase_shape_smem(Q, t_, r_, da) <= (size_t)smem_max) break;
-    t.ms[t.next++] = 1e30f;
+    t.ms[c] = 1e30f;
+    t.next++;
   }
 }
 
 static void tune_finish(TuneRef t, float ms, const PhaseShape &S, const PhaseShape &Sc, int smem_max, bool da) {
-  t.ms[t.next++] = ms;
+  const int c = tune_cand(t, da);
+  t.ms[c] = t.next < tune_count(t, da) ? ms : std::min(t.ms[c], ms);
+  t.next++;
   tune_skip(t, S, Sc, smem_max, da);
   const int nshape = phase_shape_count(da);
-  if (t.next == tune_count(t, da)) {
+  if (t.next == tune_total(t, da)) {
     int best = 0;
     for (int i = 1; i < tune_count(t, da); ++i)
       if (t.ms[i] < t.ms[best]) best = i;
@@ -1027,13 +1038,13 @@ static int sweep_impl(cr_ctx *ctx, uint64_t n_trials, uint64_t seed, cr_sweep_st
   for (uint64_t sw = 0; sw < n_sweeps; ++sw) {
     const uint32_t swc = (uint32_t)ctx->sweep++;
     if (!log) tune_skip(tr, ctx->S, ctx->Sc, ctx->smem_max, da);
-    const bool tune = tr.on && !log && tr.next < phase_shape_count(da);
+    const bool tune = tr.on && !log && tr.next < tune_total(tr, da);
     int T = tr.T, R = tr.R;
-    const bool compact = tune ? phase_shape_compact(tr.next, da) : tr.C;
+    const bool compact = tune ? phase_shape_compact(tune_cand(tr, da), da) : tr.C;
     const PhaseShape &SS = compact ? ctx->Sc : ctx->S;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
-      phase_shape(tr.next, &T, &R, da);
+      phase_shape(tune_cand(tr, da), &T, &R, da);
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);
@@ -1983,15 +1994,16 @@ static int batch_sweep_impl(cr_batch *b, uint64_t n_sweeps, uint64_t seed, bool 
       c->fcons_valid = false;
     }
     tune_skip(tr, b->S, b->Sc, b->smem_max, da);
-    const bool tune = tr.on && tr.next < tune_count(tr, da);
+    const bool tune = tr.on && tr.next < tune_total(tr, da);
     int T = tr.T, R = tr.R;
     bool persistent = pers_choice;
-    const bool compact = tune ? phase_shape_compact(tr.next % nshape, da) : tr.C;
+    const int cand = tune ? tune_cand(tr, da) : 0;
+    const bool compact = tune ? phase_shape_compact(cand % nshape, da) : tr.C;
     const PhaseShape &SS = compact ? b->Sc : b->S;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (tune) {
-      phase_shape(tr.next % nshape, &T, &R, da);
-      if (tr.pers) persistent = tr.next >= nshape;
+      phase_shape(cand % nshape, &T, &R, da);
+      if (tr.pers) persistent = cand >= nshape;
       cudaEventCreate(&e0);
       cudaEventCreate(&e1);
       cudaEventRecord(e0, s);

@@ -841,13 +841,16 @@ __global__ void __launch_bounds__(RB_THREADS) k_body_drift(SysParams P, MdParams
 // space of k with the doubled weights A' (the vectors the CR-MC trials use),
 // F_j = 2 q_j sum_k A'_k k Im(S(k)^* exp(i k.r_j)), Im(...) = C sin - D cos,
 // S = C + i D of the current positions (k_ewald_sk runs just before).  One
-// warp per particle of the force kernel's list; the axis factors
+// CTA of 256 threads per particle of the force kernel's list (a particle's
+// sum spans thousands of vectors: eight warps keep the SM busy where one warp
+// per particle left it waiting on latencies); the axis factors
 // exp(i 2 pi n x / L), n <= kmax, from the coordinate's 0.32 fixed-point
-// fraction (an exact phase reduction); each lane sums its vectors in order,
-// the warp by a fixed butterfly; the result joins the particle's 2^-24
-// fixed-point force sums before k_md_finish.
+// fraction (an exact phase reduction); each thread sums every 256th vector in
+// order, the warps by a fixed butterfly, the eight warp sums in warp order;
+// the result joins the particle's 2^-24 fixed-point force sums before
+// k_md_finish.
 // ---------------------------------------------------------------------------
-constexpr int EWF_NW = 8;
+constexpr int EWF_THREADS = 256;
 constexpr int EWF_K1 = 33;  // kmax + 1 for kmax <= 32
 
 __device__ __forceinline__ float2 ewf_factor(float x, double invL, int n) {
@@ -867,27 +870,27 @@ __device__ __forceinline__ float2 ewf_mul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__global__ void __launch_bounds__(EWF_NW * 32) k_ewald_forces(SysParams P, MdParams M) {
-  __shared__ float2 fac[EWF_NW][3 * EWF_K1];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int w = blockIdx.x * EWF_NW + wl;
-  if (w >= *M.n_particles || w >= M.max_particles) return;  // whole warp
+__global__ void __launch_bounds__(EWF_THREADS) k_ewald_forces(SysParams P, MdParams M) {
+  __shared__ float2 f[3 * EWF_K1];
+  __shared__ float part[EWF_THREADS / 32][3];
+  const int w = blockIdx.x, t = threadIdx.x, lane = t & 31, wl = t >> 5;
+  if (w >= *M.n_particles || w >= M.max_particles) return;  // whole CTA
   const int gi = M.plist[w];
   const float4 p = P.pos[gi];
   if (p.w == 0.0f) return;
   const int ewk = P.ewald_kmax + 1;
-  float2 *f = fac[wl];
-  for (int i = lane; i < 3 * ewk; i += 32) {
+  for (int i = t; i < 3 * ewk; i += EWF_THREADS) {
     const int ax = i / ewk, n = i - ax * ewk;
     f[i] = ewf_factor(ax == 0 ? p.x : (ax == 1 ? p.y : p.z), P.invLd, n);
   }
-  __syncwarp();
+  __syncthreads();
   float gx = 0.0f, gy = 0.0f, gz = 0.0f;
-  for (int i = lane; i < P.ewald_nk; i += 32) {
+#pragma unroll 4
+  for (int i = t; i < P.ewald_nk; i += EWF_THREADS) {
     const int2 v = P.ek_nA[i];
+    const float2 hi = P.ek_Shi[i], lo = P.ek_Slo[i];
     const int nx = (int)(signed char)(v.x & 255), ny = (int)(signed char)((v.x >> 8) & 255),
               nz = (int)(signed char)((v.x >> 16) & 255);
-    const float2 hi = P.ek_Shi[i], lo = P.ek_Slo[i];
     const float C = hi.x + lo.x, D = hi.y + lo.y;
     const float2 e = ewf_mul(ewf_mul(ewf_get(f, nx), ewf_get(f + ewk, ny)), ewf_get(f + 2 * ewk, nz));
     const float g = __int_as_float(v.y) * (C * e.y - D * e.x);
@@ -902,10 +905,22 @@ __global__ void __launch_bounds__(EWF_NW * 32) k_ewald_forces(SysParams P, MdPar
     gz += __shfl_xor_sync(0xffffffffu, gz, o);
   }
   if (lane == 0) {
+    part[wl][0] = gx;
+    part[wl][1] = gy;
+    part[wl][2] = gz;
+  }
+  __syncthreads();
+  if (t == 0) {
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int k = 0; k < EWF_THREADS / 32; ++k) {
+      sx += part[k][0];
+      sy += part[k][1];
+      sz += part[k][2];
+    }
     const float s = 2.0f * p.w * (float)(6.283185307179586 * P.invLd);
-    M.fsum[3 * w] += fix24(s * gx);
-    M.fsum[3 * w + 1] += fix24(s * gy);
-    M.fsum[3 * w + 2] += fix24(s * gz);
+    M.fsum[3 * w] += fix24(s * sx);
+    M.fsum[3 * w + 1] += fix24(s * sy);
+    M.fsum[3 * w + 2] += fix24(s * sz);
   }
 }
 
@@ -931,7 +946,7 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
     else if (P.h == 1 && P.nc >= 3) k_md_forces<3, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
     else k_md_forces<0, true><<<grid, MD_THREADS, 0, s>>>(P, Q);
     if (P.ewald_nk > 0)  // S(k) of these positions is current (launch_ewald_sk before this call)
-      k_ewald_forces<<<(unsigned)((max_particles + EWF_NW - 1) / EWF_NW), EWF_NW * 32, 0, s>>>(P, Q);
+      k_ewald_forces<<<(unsigned)max_particles, EWF_THREADS, 0, s>>>(P, Q);
     k_md_finish<<<(unsigned)((max_particles + 255) / 256), 256, 0, s>>>(P, Q);
   } else {
     if (P.h == 2 && P.nc >= 5) k_md_forces<5, false><<<grid, MD_THREADS, 0, s>>>(P, Q);
