@@ -1375,11 +1375,24 @@ extern "C" int cr_md_begin(cr_ctx *ctx, double dt, double gamma, uint64_t seed) 
 
 // cr_md_end's force evaluation; in a captured cycle (dyn) the key and the
 // evaluation counter come from the step parameters in device memory
-static int md_end_impl(cr_ctx *ctx, double dt, double gamma, uint64_t seed, const StepDyn *dyn, unsigned rep) {
+static int md_end_impl(cr_ctx *ctx, double dt, double gamma, uint64_t seed, const StepDyn *dyn, unsigned rep,
+                       int eval_off = 0) {
   MdParams M = md_params(ctx, 2, dt, gamma, seed);
   M.dyn = dyn;
   M.rep = rep;
+  M.eval_off = eval_off;
   return md_force_eval(ctx, M);
+}
+
+// the force evaluation that opens a captured step whose forces are stale (as
+// cr_md_begin does it call by call: Langevin terms, no kick), counters from dyn
+static int md_first_impl(cr_ctx *ctx, double dt, double gamma, const StepDyn *dyn, unsigned rep) {
+  MdParams M = md_params(ctx, 1, dt, gamma, 0);
+  M.dyn = dyn;
+  M.rep = rep;
+  const int rc = md_force_eval(ctx, M);
+  if (rc == CR_OK) ctx->f_valid = true;  // the captured md_begin then only kicks and drifts
+  return rc;
 }
 
 extern "C" int cr_md_end(cr_ctx *ctx, double dt, double gamma, uint64_t seed) {
@@ -1705,6 +1718,7 @@ struct cr_batch {
   double g_dt = 0.0, g_gamma = 0.0;
   int g_T = 0, g_R = 0, g_da = -1;
   bool g_C = false, g_pers = false, g_fine = false, g_timing = false;
+  bool g_ff = false;  // the graph's step evaluates the forces first (a step after a load)
   int64_t g_kernels = 0;                      // kernels per graph launch
   std::vector<std::pair<int, int>> g_pairs;  // phase-kernel event pairs recorded by the graph (timing)
   SysParams *d_reps = nullptr;  // one entry per replica (key_xor = replica index)
@@ -2155,9 +2169,12 @@ static int batch_refresh_chem(cr_batch *b) {
 // Capture one cycle of every replica -- MD begin (kick, drift, cell
 // rebuild), one sweep with the tuned launch form, MD end (forces with the
 // new charges, closing kick), step advance -- as a CUDA graph whose kernels
-// read the step's seeds and counters from b->d_dyn.  The contexts' host-side
-// counters are left as they were (the caller advances them per launch).
-static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
+// read the step's seeds and counters from b->d_dyn.  ff: the step opens with
+// a force evaluation (forces stale, e.g. after a load), as cr_md_begin does
+// call by call; its closing evaluation then counts one further.  The
+// contexts' host-side counters are left as they were (the caller advances
+// them per launch).
+static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da, bool ff) {
   cr_ctx *c0 = b->ctx[0];
   const int n = (int)b->ctx.size();
   // captured on the batch's own stream (the caller's may be the legacy
@@ -2175,10 +2192,12 @@ static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
   std::vector<uint64_t> sweeps(n);
   std::vector<uint32_t> evals(n);
   std::vector<int64_t> launches(n);
+  std::vector<char> fvalid(n);
   for (int r = 0; r < n; ++r) {
     sweeps[r] = b->ctx[r]->sweep;
     evals[r] = b->ctx[r]->md_eval;
     launches[r] = b->ctx[r]->launches_total;
+    fvalid[r] = b->ctx[r]->f_valid ? 1 : 0;
   }
   const int T = da ? b->da_T : b->T, R = da ? b->da_R : b->R;
   const bool C = da ? b->da_C : b->C, pers = da ? b->da_persistent : b->persistent;
@@ -2198,7 +2217,8 @@ static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
     return CR_ERR_CUDA;
   }
   {
-    rc = batch_md(b, [&](cr_ctx *c, uint64_t) { return cr_md_begin(c, dt, gamma, 0); });
+    if (ff) rc = batch_md(b, [&](cr_ctx *c, uint64_t r) { return md_first_impl(c, dt, gamma, dyn, (unsigned)r); });
+    if (rc == CR_OK) rc = batch_md(b, [&](cr_ctx *c, uint64_t) { return cr_md_begin(c, dt, gamma, 0); });
     if (rc == CR_OK && b->order_nc > 0) {
       if (launch_domain_order(b->d_reps, n, b->ncol, b->order_nact, s, 0, 0, 0, dyn) != cudaSuccess) rc = CR_ERR_CUDA;
       c0->launches_total++;
@@ -2218,7 +2238,9 @@ static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
       }
     }
     if (rc == CR_OK)
-      rc = batch_md(b, [&](cr_ctx *c, uint64_t r) { return md_end_impl(c, dt, gamma, 0, dyn, (unsigned)r); });
+      rc = batch_md(b, [&](cr_ctx *c, uint64_t r) {
+        return md_end_impl(c, dt, gamma, 0, dyn, (unsigned)r, ff ? 1 : 0);
+      });
     if (rc == CR_OK && launch_step_advance(b->d_dyn, s) != cudaSuccess) rc = CR_ERR_CUDA;
     c0->launches_total++;
   }
@@ -2241,10 +2263,11 @@ static int batch_capture_cycle(cr_batch *b, double dt, double gamma, bool da) {
     b->ctx[r]->launches_total = launches[r];
     b->ctx[r]->sweep = sweeps[r];
     b->ctx[r]->md_eval = evals[r];
-    b->ctx[r]->f_valid = true;
+    b->ctx[r]->f_valid = fvalid[r] != 0;
     b->ctx[r]->fcons_valid = false;
   }
   for (cr_ctx *c : b->ctx) c->stream = user;
+  b->g_ff = ff;
   b->g_kernels = kernels;
   b->g_dt = dt;
   b->g_gamma = gamma;
@@ -2268,21 +2291,25 @@ extern "C" int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double ga
   if (da)
     for (cr_ctx *c : b->ctx)
       if (!c->has_mlp) return CR_ERR_INVALID_ARG;
-  // a step runs from the graph once the tuner has finished and every replica
-  // holds the forces of a completed step (same counters); earlier steps run
-  // call by call
-  auto graphable = [&]() {
+  // a step runs from the graph once the tuner has finished and the replicas'
+  // counters agree: the step's own graph when every replica holds the forces
+  // of a completed step, the graph that evaluates them first when none does
+  // (a step after a load); otherwise steps run call by call
+  auto graphable = [&](bool forces) {
     if (da ? b->da_tuning : b->tuning) return false;
     for (cr_ctx *c : b->ctx)
-      if (!c->f_valid || c->md_eval != c0->md_eval || c->sweep != c0->sweep || c->stream != s) return false;
+      if (c->f_valid != forces || c->md_eval != c0->md_eval || c->sweep != c0->sweep || c->stream != s) return false;
     return true;
   };
   int step = 0;
   int rc = CR_OK;
-  for (; step < n_steps && !graphable(); ++step) {
-    if ((rc = cr_batch_md_begin(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
-    if ((rc = batch_sweep_impl(b, 1, sweep_seed0 + (uint64_t)step, da != 0)) != CR_OK) return rc;
-    if ((rc = cr_batch_md_end(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
+  const bool ff = graphable(false);
+  if (!ff) {
+    for (; step < n_steps && !graphable(true); ++step) {
+      if ((rc = cr_batch_md_begin(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
+      if ((rc = batch_sweep_impl(b, 1, sweep_seed0 + (uint64_t)step, da != 0)) != CR_OK) return rc;
+      if ((rc = cr_batch_md_end(b, dt, gamma, md_seed0 + (uint64_t)step)) != CR_OK) return rc;
+    }
   }
   if (step == n_steps) return CR_OK;
   if ((rc = batch_refresh_chem(b)) != CR_OK) return rc;
@@ -2300,33 +2327,41 @@ extern "C" int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double ga
   if (!b->d_dyn) CR_CUDA(cudaMalloc((void **)&b->d_dyn, sizeof(StepDyn)));
   const int T = da ? b->da_T : b->T, R = da ? b->da_R : b->R;
   const bool C = da ? b->da_C : b->C, pers = da ? b->da_persistent : b->persistent;
-  if (!b->graph || b->g_dt != dt || b->g_gamma != gamma || b->g_T != T || b->g_R != R || b->g_C != C ||
-      b->g_pers != pers || b->g_fine != b->fine || b->g_da != (da ? 1 : 0) || b->g_timing != c0->timing) {
-    if ((rc = batch_capture_cycle(b, dt, gamma, da != 0)) != CR_OK) return rc;
-  }
-  // this call's seeds and counters (a pageable source: staged before the call returns)
-  StepDyn d{};
-  d.step = 0;
-  d.sweep_seed0 = sweep_seed0 + (uint64_t)step;
-  d.md_seed0 = md_seed0 + (uint64_t)step;
-  d.sweep0 = (uint32_t)c0->sweep;
-  d.eval0 = c0->md_eval;
-  CR_CUDA(cudaMemcpyAsync(b->d_dyn, &d, sizeof(StepDyn), cudaMemcpyHostToDevice, s));
-  for (; step < n_steps; ++step) {
-    CR_CUDA(cudaGraphLaunch(b->graph, s));
-    for (cr_ctx *c : b->ctx) {
-      c->sweep++;
-      c->md_eval++;
-      c->f_valid = true;
-      c->fcons_valid = false;
+  while (step < n_steps) {
+    const bool first = ff && step == 0;  // only a call's first step can have stale forces
+    if (!b->graph || b->g_dt != dt || b->g_gamma != gamma || b->g_T != T || b->g_R != R || b->g_C != C ||
+        b->g_pers != pers || b->g_fine != b->fine || b->g_da != (da ? 1 : 0) || b->g_timing != c0->timing ||
+        b->g_ff != first) {
+      if ((rc = batch_capture_cycle(b, dt, gamma, da != 0, first)) != CR_OK) return rc;
     }
-    c0->launches_total += b->g_kernels;
-    if (c0->timing) {  // the phase kernels' event pairs of this launch
-      CR_CUDA(cudaStreamSynchronize(s));
-      for (auto &pr : b->g_pairs) {
-        float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, c0->ev_pool[pr.first], c0->ev_pool[pr.second]) == cudaSuccess) c0->ms[0] += ms;
-        c0->launches[0]++;
+    // this call's seeds and counters (a pageable source: staged before the call returns)
+    StepDyn d{};
+    d.step = 0;
+    d.sweep_seed0 = sweep_seed0 + (uint64_t)step;
+    d.md_seed0 = md_seed0 + (uint64_t)step;
+    d.sweep0 = (uint32_t)c0->sweep;
+    d.eval0 = c0->md_eval;
+    CR_CUDA(cudaMemcpyAsync(b->d_dyn, &d, sizeof(StepDyn), cudaMemcpyHostToDevice, s));
+    for (; step < n_steps; ++step) {
+      CR_CUDA(cudaGraphLaunch(b->graph, s));
+      for (cr_ctx *c : b->ctx) {
+        c->sweep++;
+        c->md_eval += first ? 2 : 1;
+        c->f_valid = true;
+        c->fcons_valid = false;
+      }
+      c0->launches_total += b->g_kernels;
+      if (c0->timing) {  // the phase kernels' event pairs of this launch
+        CR_CUDA(cudaStreamSynchronize(s));
+        for (auto &pr : b->g_pairs) {
+          float ms = 0.0f;
+          if (cudaEventElapsedTime(&ms, c0->ev_pool[pr.first], c0->ev_pool[pr.second]) == cudaSuccess) c0->ms[0] += ms;
+          c0->launches[0]++;
+        }
+      }
+      if (first) {  // the following steps use the step's own graph
+        ++step;
+        break;
       }
     }
   }

@@ -45,8 +45,10 @@ struct MdParams {
   float reach2;            // squared interaction reach with a margin (cells beyond it are skipped)
   long long *fsum;         // [3 max_particles] pair-force sums (2^-24 fixed point) handed to the
                            // per-particle finish kernel; null: the force kernel finishes itself
-  const StepDyn *dyn;      // non-null in a captured cycle: key = (md_seed0 + step) ^ (rep << 32), eval = eval0 + step
+  const StepDyn *dyn;      // non-null in a captured cycle: key = (md_seed0 + step) ^ (rep << 32),
+                           // eval = eval0 + step + eval_off
   unsigned int rep;
+  int eval_off;            // 1 for the closing evaluation of a captured step that evaluated the forces first
   // rigid bodies (n_bodies > 0): body_member[id] = member index of permanent
   // id, -1 for a free particle; body_d: [3 members] offsets in the body frame;
   // body_newpos: [members] member positions after the drift

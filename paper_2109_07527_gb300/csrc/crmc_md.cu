@@ -90,7 +90,7 @@ __device__ __forceinline__ void finish_particle(const SysParams &P, const MdPara
     const unsigned long long step = M.dyn->step, seed = M.dyn->md_seed0 + step;
     key0 = (uint32_t)seed;
     key1 = (uint32_t)(seed >> 32) ^ M.rep;
-    eval = M.dyn->eval0 + (uint32_t)step;
+    eval = M.dyn->eval0 + (uint32_t)step + (uint32_t)M.eval_off;
   }
   const uint4 w = philox10((uint32_t)id, (uint32_t)(id >> 32), eval, 5u, key0, key1);
   const float u0 = ((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
