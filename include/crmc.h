@@ -551,8 +551,10 @@ int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
  * forces of a completed step, each step is one launch of a CUDA graph
  * captured from those calls (captured again when dt, gamma, the launch form
  * or timing change); its kernels read the step's seeds and counters from
- * device memory.  Earlier steps run call by call.  The chain is the same as
- * the calls made one by one. */
+ * device memory.  When no replica holds valid forces (e.g. every replica was
+ * just loaded), the call's first step is one launch of a graph that opens
+ * with the force evaluation cr_md_begin would make.  Other steps run call by
+ * call.  The chain is the same as the calls made one by one. */
 int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t sweep_seed0, uint64_t md_seed0,
                    int32_t da);
 /* cr_load of every replica of the batch: args[0 .. n-1], one per context in
