@@ -19,12 +19,19 @@
  *     the base pair, (MCsaltf), (MCmetro2), written in log form.
  *   - App. C, Eq. (pIXgen): 10^-pI_X = 10^-pI_S + 10^-min(pH, pOH).
  *   - Eq. (LJe)/(LJ): WCA with an optional expanded distance Delta.
+ *   - Sec. III.A: velocity Verlet with a Langevin thermostat; Sec. IV.B: the
+ *     nanoparticles carry their sites rigidly (rigid bodies, see
+ *     or_set_bodies).
  * Readings where the paper is silent:
  *   - The energy model is a damped-shifted-force (DSF) Coulomb cutoff sum plus
  *     WCA (the paper uses PPPM), with the DSF self term; or, under the global
  *     schedule, the Ewald sum that PPPM evaluates on a mesh (real-space erfc
  *     within rc, reciprocal vectors 0 < |n| <= kmax, self term), S(k)
- *     recomputed at every sweep and carried by the accepted trials within it.
+ *     recomputed at every sweep and carried by the accepted trials within it;
+ *     the MD forces are minus the gradient of the same energy.
+ *   - Rigid bodies: unit mass per member, the principal frame, the symmetric
+ *     rotation splitting of Dullweber, Leimkuhler and McLachlan, and the
+ *     Langevin thermostat acting on each body as a whole.
  *   - Moves are domain-local under an 8-colour checkerboard schedule: the
  *     paired ion is inserted in / deleted from the trial's domain, and the
  *     acceptance uses that domain's volume and counts.  The "global" schedule
