@@ -102,7 +102,7 @@ typedef struct {
   int32_t n_bonds;      /* FENE bonds */
   const int32_t *bonds; /* [2 n_bonds] particle indices; no ions */
   double fene_K, fene_R0;
-  double wca_eps[16], wca_sig[16], wca_del[16]; /* class-pair table [4*ci + cj] */
+  double wca_eps[16], wca_sig[16], wca_del[16]; /* class-pair table [4*ci + cj], symmetric */
   int32_t wca_on[16];
   double dsf_alpha;        /* DSF damping (1/sigma) */
   int32_t dsf_self;        /* 1: include the DSF self energy of each charge */

@@ -61,7 +61,7 @@ struct cr_ctx {
   long long *d_gs_lnk = nullptr;
   int *d_gs_info = nullptr, *d_gs_rank = nullptr;
   int *d_plist = nullptr, *d_nparts = nullptr;  // MD particle list
-  long long *d_fsum = nullptr;                    // MD pair-force sums per listed particle
+  long long *d_fsum = nullptr;                    // MD pair-force sums per slot
   int *d_order = nullptr;                       // launch order of the domains of each colour
   // delayed acceptance: surrogate on the device, records, its own launch-shape tuner
   uint16_t *d_mlp_w = nullptr;
@@ -423,6 +423,13 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   P.ewald_kmax = sys->ewald_kmax;
   P.ewald_nk = (int)ek_nA.size();
   P.invLd = 1.0 / L;
+  for (int i = 0; i < 4; ++i)  // a pair potential: the class-pair table is symmetric
+    for (int j = 0; j < i; ++j)
+      if (sys->wca_eps[4 * i + j] != sys->wca_eps[4 * j + i] || sys->wca_sig[4 * i + j] != sys->wca_sig[4 * j + i] ||
+          sys->wca_del[4 * i + j] != sys->wca_del[4 * j + i] || (sys->wca_on[4 * i + j] != 0) != (sys->wca_on[4 * j + i] != 0)) {
+        free_ctx(c);
+        return CR_ERR_INVALID_ARG;
+      }
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
       WcaEntry &w = P.wca[4 * i + j];
@@ -697,7 +704,7 @@ extern "C" int cr_init(cr_ctx **out, const cr_system *sys, double pH, const doub
   ALLOC(c->d_reps, 1);
   ALLOC(c->d_plist, (size_t)std::max(sys->capacity, 1));
   ALLOC(c->d_nparts, 1);
-  ALLOC(c->d_fsum, 3 * (size_t)std::max(sys->capacity, 1));
+  ALLOC(c->d_fsum, 3 * (size_t)P.ncell * (size_t)P.cap);  // per slot: both ends of each pair add to it
   if (P.ewald_nk > 0) {
     ALLOC(c->d_ek_nA, (size_t)P.ewald_nk);
     ALLOC(c->d_ek_Shi, (size_t)P.ewald_nk);

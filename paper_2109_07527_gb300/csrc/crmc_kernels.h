@@ -43,8 +43,9 @@ struct MdParams {
   const int *n_particles;  // entries of plist
   int max_particles;       // capacity of plist
   float reach2;            // squared interaction reach with a margin (cells beyond it are skipped)
-  long long *fsum;         // [3 max_particles] pair-force sums (2^-24 fixed point) handed to the
-                           // per-particle finish kernel; null: the force kernel finishes itself
+  long long *fsum;         // [3 slots] pair-force sums (2^-24 fixed point) by slot, each pair evaluated once
+                           // and added to both ends, handed to the per-particle finish kernel;
+                           // null: every pair from both ends, the force kernel finishes itself
   const StepDyn *dyn;      // non-null in a captured cycle: key = (md_seed0 + step) ^ (rep << 32),
                            // eval = eval0 + step + eval_off
   unsigned int rep;

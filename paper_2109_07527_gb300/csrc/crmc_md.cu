@@ -20,6 +20,11 @@ constexpr float FFIX_INV = 1.0f / 16777216.0f;
 
 // FLAT: i and j are given in the stencil's flat frame (md_frame), where the
 // plain difference is the minimum-image one bit for bit
+// The pair's force on i in 2^-24 fixed point (zero out of range).  The terms
+// are odd in (i, j): exchanging the particles negates dx, dy, dz exactly and
+// leaves r^2 and g unchanged (charges are 0 or +-1, the WCA table is
+// symmetric), and fix24 rounds symmetrically, so the force on j is exactly
+// the negated value.
 template <bool FLAT = false>
 __device__ __forceinline__ void force_pair(const SysParams &P, float xi, float yi, float zi, float qi, int ci,
                                            float xj, float yj, float zj, float qj, int cj, long long &fx,
@@ -127,7 +132,7 @@ __device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc 
 __device__ __forceinline__ float md_frame(float x, bool s, float halfL, float L) { return s && x >= halfL ? x - L : x; }
 
 // compact list of occupied slots; one atomic per warp of 32 cells
-__global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
+__global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out, long long *fsum) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
   const int n = c < P.ncell ? P.cnt[c] : 0;
   int x = n;
@@ -144,6 +149,12 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
   // entries that fit are written even then, so every entry the force kernel
   // reads (below min(count, max_out)) names a slot of this system
   for (int s = 0; s < n && o + s < max_out; ++s) plist[o + s] = c * P.cap + s;
+  if (fsum)  // the occupied slots' force sums start from zero (k_md_forces adds both ends of each pair)
+    for (int s = 0; s < n; ++s) {
+      fsum[3 * (c * P.cap + s)] = 0;
+      fsum[3 * (c * P.cap + s) + 1] = 0;
+      fsum[3 * (c * P.cap + s) + 2] = 0;
+    }
 }
 
 // MD forces: one warp per particle.  The candidates of the (2h+1)^3 stencil of
@@ -157,6 +168,30 @@ __global__ void k_plist(SysParams P, int *plist, int *n_out, int max_out) {
 // thread per particle) instead of finishing it on lane 0 while 31 lanes idle.
 // FLAT (with NBC > 0): the stencil spans less than 0.4 L, distances are taken
 // in its flat frame (md_frame) without minimum-image tests.
+// One queued pair (i, j = slot g2): the force on i into this lane's sums;
+// SPLIT: each pair is evaluated once, and the force on j (the exact negation)
+// goes into j's fixed-point sums by 64-bit integer atomics (exact and
+// order-free, so the sums equal those of evaluating the pair from both ends).
+template <bool SPLIT, bool FLAT>
+__device__ __forceinline__ void md_pair(const SysParams &P, const MdParams &M, int g2, float xi, float yi, float zi,
+                                        float qi, int clsi, bool sx, bool sy, bool sz, long long &fx, long long &fy,
+                                        long long &fz) {
+  const float4 pj = P.pos[g2];
+  long long vx = 0, vy = 0, vz = 0;
+  force_pair<FLAT>(P, xi, yi, zi, qi, clsi, FLAT ? md_frame(pj.x, sx, P.halfL, P.Lf) : pj.x,
+                   FLAT ? md_frame(pj.y, sy, P.halfL, P.Lf) : pj.y, FLAT ? md_frame(pj.z, sz, P.halfL, P.Lf) : pj.z,
+                   pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, vx, vy, vz);
+  fx += vx;
+  fy += vy;
+  fz += vz;
+  if (SPLIT && (vx | vy | vz) != 0) {
+    unsigned long long *d = reinterpret_cast<unsigned long long *>(M.fsum) + 3 * g2;
+    atomicAdd(d, (unsigned long long)(-vx));
+    atomicAdd(d + 1, (unsigned long long)(-vy));
+    atomicAdd(d + 2, (unsigned long long)(-vz));
+  }
+}
+
 template <int NBC, bool SPLIT, bool FLAT = false>  // NBC: 2h+1 when the box has at least that many cells per dimension, else 0
 __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams M) {
   __shared__ int queue[MD_NW][MD_QCAP];
@@ -248,7 +283,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     int gj = -1;
     if (c < total) {
       gj = cbs[wl][cell_o] + (c - pre[cell_o]);
-      if (gj != gi) {
+      if (SPLIT ? gj > gi : gj != gi) {  // SPLIT: each pair once, from its lower slot
         const float4 pj = P.pos[gj];
         const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
         const float dx = FLAT ? xi - md_frame(pj.x, sx, P.halfL, P.Lf) : wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
@@ -264,11 +299,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     qn += __popc(m);
     if (qn >= 32) {
       __syncwarp();
-      const int g2 = q[lane];
-      const float4 pj = P.pos[g2];
-      force_pair<FLAT>(P, xi, yi, zi, pi.w, clsi, FLAT ? md_frame(pj.x, sx, P.halfL, P.Lf) : pj.x,
-                       FLAT ? md_frame(pj.y, sy, P.halfL, P.Lf) : pj.y, FLAT ? md_frame(pj.z, sz, P.halfL, P.Lf) : pj.z,
-                       pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
+      md_pair<SPLIT, FLAT>(P, M, q[lane], xi, yi, zi, pi.w, clsi, sx, sy, sz, fx, fy, fz);
       const int rest = qn - 32;
       int keep = 0;
       if (lane < rest) keep = q[32 + lane];
@@ -279,18 +310,14 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     }
   }
   __syncwarp();
-  if (lane < qn) {
-    const int g2 = q[lane];
-    const float4 pj = P.pos[g2];
-    force_pair<FLAT>(P, xi, yi, zi, pi.w, clsi, FLAT ? md_frame(pj.x, sx, P.halfL, P.Lf) : pj.x,
-                     FLAT ? md_frame(pj.y, sy, P.halfL, P.Lf) : pj.y, FLAT ? md_frame(pj.z, sz, P.halfL, P.Lf) : pj.z,
-                     pj.w, (P.info[g2] >> INFO_CLS_SHIFT) & 3, fx, fy, fz);
-  }
+  if (lane < qn) md_pair<SPLIT, FLAT>(P, M, q[lane], xi, yi, zi, pi.w, clsi, sx, sy, sz, fx, fy, fz);
   fx = warp_sum_i64(fx);
   fy = warp_sum_i64(fy);
   fz = warp_sum_i64(fz);
-  if (SPLIT) {
-    if (lane < 3) M.fsum[3 * w + lane] = lane == 0 ? fx : (lane == 1 ? fy : fz);
+  if (SPLIT) {  // this particle's own pairs join what its partners added
+    if (lane < 3)
+      atomicAdd(reinterpret_cast<unsigned long long *>(M.fsum) + 3 * gi + lane,
+                (unsigned long long)(lane == 0 ? fx : (lane == 1 ? fy : fz)));
   } else if (lane == 0) {
     finish_particle(P, M, gi, pi, fx, fy, fz);
   }
@@ -302,7 +329,7 @@ __global__ void k_md_finish(SysParams P, MdParams M) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= *M.n_particles || w >= M.max_particles) return;
   const int gi = M.plist[w];
-  finish_particle(P, M, gi, P.pos[gi], M.fsum[3 * w], M.fsum[3 * w + 1], M.fsum[3 * w + 2]);
+  finish_particle(P, M, gi, P.pos[gi], M.fsum[3 * gi], M.fsum[3 * gi + 1], M.fsum[3 * gi + 2]);
 }
 
 // v += dt/2 f; x += dt v; wrap into [0, L); the particle goes straight into
@@ -918,9 +945,9 @@ __global__ void __launch_bounds__(EWF_THREADS) k_ewald_forces(SysParams P, MdPar
       sz += part[k][2];
     }
     const float s = 2.0f * p.w * (float)(6.283185307179586 * P.invLd);
-    M.fsum[3 * w] += fix24(s * sx);
-    M.fsum[3 * w + 1] += fix24(s * sy);
-    M.fsum[3 * w + 2] += fix24(s * sz);
+    M.fsum[3 * gi] += fix24(s * sx);
+    M.fsum[3 * gi + 1] += fix24(s * sy);
+    M.fsum[3 * gi + 2] += fix24(s * sz);
   }
 }
 
@@ -933,7 +960,7 @@ cudaError_t launch_md_forces(const SysParams &P, const MdParams &M, int *plist, 
                              cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(n_particles, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  k_plist<<<(P.ncell + 255) / 256, 256, 0, s>>>(P, plist, n_particles, max_particles);
+  k_plist<<<(P.ncell + 255) / 256, 256, 0, s>>>(P, plist, n_particles, max_particles, M.fsum);
   MdParams Q = M;
   Q.plist = plist;
   Q.n_particles = n_particles;
