@@ -235,7 +235,8 @@ typedef struct {
 /* Create a context: copies the system to the device, precomputes the
  * chemical constants (pH, per-particle pK [n] of sites, reservoir ions,
  * Bjerrum length lB, cutoff rc).  Errors: INVALID_ARG (geometry, ranges,
- * rc > L/2), NOT_NEUTRAL, NO_DEVICE, NOMEM, CUDA. */
+ * rc > L/2, a WCA class-pair table that is not symmetric), NOT_NEUTRAL,
+ * NO_DEVICE, NOMEM, CUDA. */
 int cr_init(cr_ctx **out, const cr_system *sys, double pH, const double *pK, cr_mu_ions mu, double lB,
             double rc);
 
