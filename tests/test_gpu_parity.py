@@ -217,6 +217,17 @@ def test_md_forces_match_oracle(crmc):
     assert np.abs(F).max() > 1.0  # the check is not vacuous
 
 
+def test_asymmetric_wca_table_refused(crmc):
+    """A pair potential's class table is symmetric; the force kernel evaluates
+    each pair once and relies on it, so an asymmetric table is refused."""
+    w = W.config1(seed=5)
+    w.params["wca_del"] = list(w.params["wca_del"])
+    w.params["wca_del"][0 * 4 + 1] = 0.5  # (0, 1) but not (1, 0)
+    with pytest.raises(crmc.CrError) as e:
+        crmc.Context(w)
+    assert e.value.code == -1
+
+
 def test_md_forces_full_size_sampled(crmc):
     """Forces of the full polyelectrolyte box: every particle vs the oracle's brute-force sum."""
     w = W.config2(seed=1)
