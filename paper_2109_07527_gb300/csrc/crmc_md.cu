@@ -122,6 +122,7 @@ constexpr int MD_THREADS = 128;
 constexpr int MD_NW = MD_THREADS / 32;
 constexpr int MD_QCAP = 64;
 constexpr int MD_CPL = 4;  // stencil cells per lane (125 cells of a 5^3 stencil over 32 lanes)
+constexpr int HALF5 = 62;  // the own cell's index in a 5^3 stencil; the higher indices are its upper half
 
 __device__ __forceinline__ int wrap_cell(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
 
@@ -223,7 +224,11 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
   for (int t = 0; t < MD_CPL; ++t) {
     const int o = lane + 32 * t;
     int n = 0, base = 0;
-    if (o < nb3) {
+    // SPLIT over a 5^3 stencil (at least 5 cells per dimension, so no two
+    // offsets name the same cell): only the upper half of the offsets, the
+    // own cell (o = 62) with its higher slots; the partner's warp finds the
+    // pair through the opposite offset otherwise
+    if (o < nb3 && !(SPLIT && NBC == 5 && o < HALF5)) {
       const int ox = o % nb, oy = (o / nb) % nb, oz = o / (nb * nb);
       const int jx = all ? ox : wrap_cell(cx + ox - h, nc);
       const int jy = all ? oy : wrap_cell(cy + oy - h, nc);
@@ -283,7 +288,9 @@ __global__ void __launch_bounds__(MD_THREADS) k_md_forces(SysParams P, MdParams 
     int gj = -1;
     if (c < total) {
       gj = cbs[wl][cell_o] + (c - pre[cell_o]);
-      if (SPLIT ? gj > gi : gj != gi) {  // SPLIT: each pair once, from its lower slot
+      // SPLIT: each pair once (the upper half of a 5^3 stencil and the higher
+      // slots of the own cell; otherwise every pair from its lower slot)
+      if (SPLIT ? ((NBC == 5 && cell_o != HALF5) || gj > gi) : gj != gi) {
         const float4 pj = P.pos[gj];
         const int cj = (P.info[gj] >> INFO_CLS_SHIFT) & 3;
         const float dx = FLAT ? xi - md_frame(pj.x, sx, P.halfL, P.Lf) : wrap_diff(pi.x, pj.x, P.Lf, P.halfL);
