@@ -554,7 +554,8 @@ int cr_batch_md_end(cr_batch *b, double dt, double gamma, uint64_t seed);
  * or timing change); its kernels read the step's seeds and counters from
  * device memory.  When no replica holds valid forces (e.g. every replica was
  * just loaded), the call's first step is one launch of a graph that opens
- * with the force evaluation cr_md_begin would make.  Other steps run call by
+ * with the force evaluation cr_md_begin would make (one graph is kept: a
+ * change between the two forms captures again).  Other steps run call by
  * call.  The chain is the same as the calls made one by one. */
 int cr_batch_cycle(cr_batch *b, int32_t n_steps, double dt, double gamma, uint64_t sweep_seed0, uint64_t md_seed0,
                    int32_t da);
