@@ -48,7 +48,9 @@ def _check(ref, force, ids):
     assert np.array_equal(got_id, ref["id"])
     # the same FP32 pair terms summed in the same exact 2^-24 fixed point:
     # equal to the bit, although this entry runs the lane-0 finishing variant
-    # without the flat frame (the flat-frame differences are exact)
+    # without the flat frame (the flat-frame differences are exact) and
+    # evaluates every pair from both ends, where cr_md_forces evaluates each
+    # pair once over half the stencil and adds the partner's share by atomics
     assert np.array_equal(got_f, ref["force"].astype(np.float64))
     assert np.all(force[full][:, 3] == 0.0)
 
