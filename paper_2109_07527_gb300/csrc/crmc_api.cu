@@ -131,7 +131,7 @@ struct cr_ctx {
   RigidBody *d_bodies = nullptr;
   int *d_body_member = nullptr;
   double *d_body_d = nullptr;
-  float4 *d_body_newpos = nullptr;
+  float4 *d_body_df = nullptr, *d_body_newpos = nullptr;
 };
 
 namespace {
@@ -216,7 +216,7 @@ static void free_ctx(cr_ctx *c) {
                   c->d_reps, c->d_gs_pos, c->d_gs_vel, c->d_gs_id, c->d_gs_lnk, c->d_gs_info, c->d_gs_rank,
                   c->d_plist, c->d_nparts, c->d_fsum, c->d_mlp_w, c->d_mlp_b, c->d_dlog, c->d_feat, c->d_order,
                   c->d_ek_nA, c->d_ek_Shi, c->d_ek_Slo, c->d_ek_list, c->d_ek_np,
-                  c->d_bodies, c->d_body_member, c->d_body_d, c->d_body_newpos};
+                  c->d_bodies, c->d_body_member, c->d_body_d, c->d_body_df, c->d_body_newpos};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_small) cudaFreeHost(c->h_small);
@@ -1207,6 +1207,7 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
   M.bodies = ctx->d_bodies;
   M.body_member = ctx->d_body_member;
   M.body_d = ctx->d_body_d;
+  M.body_df = ctx->d_body_df;
   M.body_newpos = ctx->d_body_newpos;
   M.body_dt = dt;
   M.body_gamma = gamma;
@@ -1214,12 +1215,13 @@ static MdParams md_params(cr_ctx *ctx, int mode, double dt, double gamma, uint64
 }
 
 static void free_bodies(cr_ctx *ctx) {
-  void *ptrs[] = {ctx->d_bodies, ctx->d_body_member, ctx->d_body_d, ctx->d_body_newpos};
+  void *ptrs[] = {ctx->d_bodies, ctx->d_body_member, ctx->d_body_d, ctx->d_body_df, ctx->d_body_newpos};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   ctx->d_bodies = nullptr;
   ctx->d_body_member = nullptr;
   ctx->d_body_d = nullptr;
+  ctx->d_body_df = nullptr;
   ctx->d_body_newpos = nullptr;
   ctx->n_bodies = ctx->n_members = 0;
 }
@@ -1253,15 +1255,16 @@ extern "C" int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t 
   RigidBody *d_b = nullptr;
   int *d_m = nullptr;
   double *d_d = nullptr;
-  float4 *d_n = nullptr;
+  float4 *d_f = nullptr, *d_n = nullptr;
   auto release = [&]() {
-    void *ptrs[] = {d_b, d_m, d_d, d_n};
+    void *ptrs[] = {d_b, d_m, d_d, d_f, d_n};
     for (void *p : ptrs)
       if (p) cudaFree(p);
   };
   cudaError_t e = cudaMalloc(&d_b, hb.size() * sizeof(RigidBody));
   if (e == cudaSuccess) e = cudaMalloc(&d_m, member.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&d_d, (size_t)nm * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_f, (size_t)nm * sizeof(float4));
   if (e == cudaSuccess) e = cudaMalloc(&d_n, (size_t)nm * sizeof(float4));
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_b, hb.data(), hb.size() * sizeof(RigidBody), cudaMemcpyHostToDevice, ctx->stream);
@@ -1272,6 +1275,7 @@ extern "C" int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t 
   M.bodies = d_b;
   M.body_member = d_m;
   M.body_d = d_d;
+  M.body_df = d_f;
   M.body_newpos = d_n;
   if (e == cudaSuccess) e = launch_body_setup(ctx->P, M, ctx->stream);
   if (e == cudaSuccess)
@@ -1291,6 +1295,7 @@ extern "C" int cr_set_rigid_bodies(cr_ctx *ctx, int32_t n_bodies, const int32_t 
   ctx->d_bodies = d_b;
   ctx->d_body_member = d_m;
   ctx->d_body_d = d_d;
+  ctx->d_body_df = d_f;
   ctx->d_body_newpos = d_n;
   ctx->f_valid = false;  // the next step evaluates the bodies' forces and torques
   ctx->launches_total += 2;

@@ -57,6 +57,7 @@ struct MdParams {
   RigidBody *bodies;
   const int *body_member;
   double *body_d;
+  float4 *body_df;     // [members] the same offsets in FP32 (the per-member products)
   float4 *body_newpos;
   double body_dt, body_gamma;  // the step and the friction in FP64 for the bodies
 };

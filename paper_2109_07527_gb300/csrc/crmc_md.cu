@@ -539,7 +539,7 @@ __global__ void k_step_advance(StepDyn *dyn) {
 // thread in member order, then through a fixed tree, so the result does not
 // depend on where the members sit in the cell list.
 // ---------------------------------------------------------------------------
-constexpr int RB_THREADS = 256;
+constexpr int RB_THREADS = 512;
 
 __device__ __forceinline__ void rb_mul(const double *R, const double *v, double *o) {
 #pragma unroll
@@ -619,8 +619,8 @@ __device__ __forceinline__ int rb_slot(const SysParams &P, const MdParams &M, in
 
 __device__ __forceinline__ double rb_min_image(double d, double L) { return d - L * rint(d / L); }
 
-__device__ __forceinline__ float rb_wrap(double x, double L, float Lf) {
-  x -= L * floor(x / L);
+__device__ __forceinline__ float rb_wrap(double x, double L, double invL, float Lf) {
+  x -= L * floor(x * invL);
   float f = __double2float_rn(x);
   if (f >= Lf) f -= Lf;
   if (f < 0.0f) f = 0.0f;
@@ -731,30 +731,61 @@ __global__ void __launch_bounds__(RB_THREADS) k_body_setup(SysParams P, MdParams
     const double d[3] = {rb_min_image((double)p.x - r0[0], L) - sub_s[0],
                          rb_min_image((double)p.y - r0[1], L) - sub_s[1],
                          rb_min_image((double)p.z - r0[2], L) - sub_s[2]};
-    rb_tmul(R_s, d, M.body_d + 3 * (mf + m));
+    double *db = M.body_d + 3 * (mf + m);
+    rb_tmul(R_s, d, db);
+    M.body_df[mf + m] = make_float4((float)db[0], (float)db[1], (float)db[2], 0.0f);
   }
 }
 
 // the members' rigid velocities V + omega x (R d) (and, with newpos, the
 // positions X + R d after a drift, wrapped into the box)
-__device__ void rb_members(const SysParams &P, const MdParams &M, const RigidBody &B, bool newpos) {
+// (the per-member products in FP32: an arm of a few sigma rounds far below the
+// FP32 resolution of the positions; the centre and the sums stay FP64)
+__device__ __forceinline__ void rb_fmul(const float *R, float4 d, float *o) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) o[a] = R[3 * a] * d.x + R[3 * a + 1] * d.y + R[3 * a + 2] * d.z;
+}
+
+// R, omega = R (pi / I) and V of the body in FP32, formed once by thread 0
+// (the FP64 pipe is narrow: every thread forming them cost more than the members)
+struct RbF32 {
+  float R[9], om[3], V[3];
+};
+__device__ __forceinline__ void rb_f32(const RigidBody &B, RbF32 &F) {
   double w[3], om[3];
   for (int k = 0; k < 3; ++k) w[k] = B.pi[k] / B.I[k];
   rb_mul(B.R, w, om);
+  for (int k = 0; k < 9; ++k) F.R[k] = (float)B.R[k];
+  for (int k = 0; k < 3; ++k) {
+    F.om[k] = (float)om[k];
+    F.V[k] = (float)B.V[k];
+  }
+}
+
+__device__ void rb_members(const SysParams &P, const MdParams &M, const RigidBody &B, bool newpos) {
+  __shared__ RbF32 F;
+  if (threadIdx.x == 0) rb_f32(B, F);
+  __syncthreads();
+  float Rf[9], omf[3], Vf[3];
+  for (int k = 0; k < 9; ++k) Rf[k] = F.R[k];
+  for (int k = 0; k < 3; ++k) {
+    omf[k] = F.om[k];
+    Vf[k] = F.V[k];
+  }
   const double L = (double)P.Lf;
   for (int m = threadIdx.x; m < B.count; m += RB_THREADS) {
     const int s = M.perm_slot[B.first + m];
-    double a[3], u[3];
-    rb_mul(B.R, M.body_d + 3 * (B.mfirst + m), a);
-    rb_cross(om, a, u);
+    float a[3];
+    rb_fmul(Rf, M.body_df[B.mfirst + m], a);
     float4 v = M.vel[s];
-    v.x = (float)(B.V[0] + u[0]);
-    v.y = (float)(B.V[1] + u[1]);
-    v.z = (float)(B.V[2] + u[2]);
+    v.x = Vf[0] + (omf[1] * a[2] - omf[2] * a[1]);
+    v.y = Vf[1] + (omf[2] * a[0] - omf[0] * a[2]);
+    v.z = Vf[2] + (omf[0] * a[1] - omf[1] * a[0]);
     M.vel[s] = v;
     if (newpos)
-      M.body_newpos[B.mfirst + m] = make_float4(rb_wrap(B.X[0] + a[0], L, P.Lf), rb_wrap(B.X[1] + a[1], L, P.Lf),
-                                                rb_wrap(B.X[2] + a[2], L, P.Lf), 0.0f);
+      M.body_newpos[B.mfirst + m] =
+          make_float4(rb_wrap(B.X[0] + (double)a[0], L, P.invLd, P.Lf), rb_wrap(B.X[1] + (double)a[1], L, P.invLd, P.Lf),
+                      rb_wrap(B.X[2] + (double)a[2], L, P.invLd, P.Lf), 0.0f);
   }
 }
 
@@ -763,20 +794,20 @@ __global__ void __launch_bounds__(RB_THREADS) k_body_member_velocities(SysParams
 }
 
 // three normals from the Philox block (body, 0, eval, purpose): the Box-Muller
-// form of the particles' Langevin noise, in FP64
+// form of the particles' Langevin noise, in FP32 as theirs
 __device__ void rb_normals(uint32_t body, uint32_t eval, uint32_t purpose, uint32_t k0, uint32_t k1, double *g) {
   const uint4 w = philox10(body, 0u, eval, purpose, k0, k1);
-  const double u0 = (double)(((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f));
-  const double u1 = (double)(((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f));
-  const double u2 = (double)(((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f));
-  const double u3 = (double)(((float)(w.w >> 8) + 0.5f) * (1.0f / 16777216.0f));
-  const double r1 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
-  double s1, c1, s3, c3;
-  sincospi(2.0 * u1, &s1, &c1);
-  sincospi(2.0 * u3, &s3, &c3);
-  g[0] = r1 * c1;
-  g[1] = r1 * s1;
-  g[2] = r2 * c3;
+  const float u0 = ((float)(w.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u1 = ((float)(w.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = ((float)(w.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float u3 = ((float)(w.w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+  const float r1 = sqrtf(-2.0f * logf(u0)), r2 = sqrtf(-2.0f * logf(u2));
+  float s1, c1, s3, c3;
+  sincospif(2.0f * u1, &s1, &c1);
+  sincospif(2.0f * u3, &s3, &c3);
+  g[0] = (double)(r1 * c1);
+  g[1] = (double)(r1 * s1);
+  g[2] = (double)(r2 * c3);
 }
 
 // force and torque of each body from its members' conservative forces, plus
@@ -787,19 +818,23 @@ __global__ void __launch_bounds__(RB_THREADS) k_body_forces(SysParams P, MdParam
   const int t = threadIdx.x;
   if (t == 0) B = M.bodies[blockIdx.x];
   __syncthreads();
-  double a[6] = {0, 0, 0, 0, 0, 0};
+  float Rf[9];
+  for (int k = 0; k < 9; ++k) Rf[k] = (float)B.R[k];
+  float af[6] = {0, 0, 0, 0, 0, 0};  // this thread's few members, FP32
   for (int m = t; m < B.count; m += RB_THREADS) {
     const int s = M.perm_slot[B.first + m];
-    const float4 f4 = M.fout[s];
-    const double f[3] = {(double)f4.x, (double)f4.y, (double)f4.z};
-    double r[3], q[3];
-    rb_mul(B.R, M.body_d + 3 * (B.mfirst + m), r);
-    rb_cross(r, f, q);
-    for (int k = 0; k < 3; ++k) {
-      a[k] += f[k];
-      a[3 + k] += q[k];
-    }
+    const float4 f = M.fout[s];
+    float r[3];
+    rb_fmul(Rf, M.body_df[B.mfirst + m], r);
+    af[0] += f.x;
+    af[1] += f.y;
+    af[2] += f.z;
+    af[3] += r[1] * f.z - r[2] * f.y;
+    af[4] += r[2] * f.x - r[0] * f.z;
+    af[5] += r[0] * f.y - r[1] * f.x;
   }
+  double a[6];
+  for (int k = 0; k < 6; ++k) a[k] = (double)af[k];
   rb_sum<6>(a, sh);
   if (t == 0) {
     double gt[3], gr[3], Lm[3], y[3], S[3];
@@ -833,7 +868,13 @@ __global__ void __launch_bounds__(RB_THREADS) k_body_forces(SysParams P, MdParam
 __device__ void rb_rotate(RigidBody &B, int k, double h) {
   const double th = h * B.pi[k] / B.I[k];
   double s, c;
-  sincos(th, &s, &c);
+  if (fabs(th) < 1e-2) {  // the Taylor series, truncated below FP64 rounding (|th|^7 / 7! < 2e-18)
+    const double t2 = th * th;
+    s = th * (1.0 - t2 * (1.0 / 6.0) * (1.0 - t2 * (1.0 / 20.0) * (1.0 - t2 * (1.0 / 42.0))));
+    c = 1.0 - t2 * 0.5 * (1.0 - t2 * (1.0 / 12.0) * (1.0 - t2 * (1.0 / 30.0) * (1.0 - t2 * (1.0 / 56.0))));
+  } else {
+    sincos(th, &s, &c);
+  }
   const int i = (k + 1) % 3, j = (k + 2) % 3;
   for (int r = 0; r < 3; ++r) {
     const double x = B.R[3 * r + i], y = B.R[3 * r + j];
