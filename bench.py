@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-config3", action="store_true")
     ap.add_argument("--train-only", action="store_true",
                     help="time only the surrogate's training step (batch 32,768, synthetic features) and exit")
+    ap.add_argument("--mobile-only", action="store_true",
+                    help="time only the MD/CR-MC cycles of the two rigid nanoparticles and exit")
     ap.add_argument("--ewald-only", action="store_true",
                     help="time only CR-MC sweeps with Ewald electrostatics (the 500-acid box of the method "
                          "comparison, 64 replicas, |n| <= 16, global schedule) and exit")
@@ -593,6 +595,28 @@ def run_ewald_only(args):
         c.close()
 
 
+def run_mobile_only(args):
+    """The two-nanoparticle system with rigid bodies (the bench leg
+    `mobile_nanoparticles`) alone: the tuner's and warm-up steps, then `steps`
+    MD/CR-MC cycles timed with CUDA events between profiler start / stop (a
+    short program for profiling the rigid-body cycle)."""
+    import torch
+    from paper_2109_07527_gb300 import crmc
+    crmc._lib()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def bracket(fn, steps, stream_, flush_):
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        ms = time_steps(fn, steps, stream_, flush_)
+        torch.cuda.profiler.stop()
+        return ms
+
+    out = run_config3_mobile(crmc, torch, stream, flush, args.steps, timer=bracket)
+    print(json.dumps({"metric": "MD/CR-MC cycles/s, two rigid nanoparticles", **out}), flush=True)
+
+
 def run_config4(crmc, torch, stream, flush, steps):
     """The batched titration: 64 replicas, chain lengths log-uniform in
     [50, 1000], pH uniform in [2, 10], boxes at 10^-3 monomers per sigma^3
@@ -624,7 +648,7 @@ def run_config4(crmc, torch, stream, flush, steps):
     return out
 
 
-def run_config3_mobile(crmc, torch, stream, flush, steps):
+def run_config3_mobile(crmc, torch, stream, flush, steps, timer=None):
     """The two-nanoparticle system as a full MD run with mobile rigid
     nanoparticles: 2 x 1000 sites (acids pKa 4 on one, bases pKb 4 on the
     other) on spheres of radius 5 at 12 sigma, L = 100, 20 mM salt, pH 7; each
@@ -645,7 +669,7 @@ def run_config3_mobile(crmc, torch, stream, flush, steps):
     for s in range(TUNE_SWEEPS + 4):  # the launch-shape tuner's sweeps and a warm-up
         step(s)
     b0 = g.rigid_body_state()
-    ms = time_steps(lambda s: step(100 + s), steps, stream, flush)
+    ms = (timer or time_steps)(lambda s: step(100 + s), steps, stream, flush)
     b1 = g.rigid_body_state()
     g.check()
     st = g.state()
@@ -905,5 +929,7 @@ if __name__ == "__main__":
         run_train_only(a)
     elif a.ewald_only:
         run_ewald_only(a)
+    elif a.mobile_only:
+        run_mobile_only(a)
     else:
         run_ours(a)
