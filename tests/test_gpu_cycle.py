@@ -129,19 +129,23 @@ def test_graph_cycle_equals_calls(crmc, mode):
             assert np.array_equal(a[k], c[k]), k
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_graph_cycle_after_a_load_equals_calls(crmc, mode):
+@pytest.mark.parametrize("mode,da", [(0, False), (1, False), (0, True)])
+def test_graph_cycle_after_a_load_equals_calls(crmc, mode, da):
     """A cycle whose forces are stale (every replica just loaded, as in a
     coupling that uploads the configuration each step) runs its first step
     from the graph that evaluates the forces first, then the step's own graph:
-    bit for bit the calls md_begin (which evaluates them), sweep, md_end."""
+    bit for bit the calls md_begin (which evaluates them), sweep, md_end; also
+    with delayed-acceptance sweeps."""
     ws = [W.config2(seed=15, scale=0.5, pH=p) for p in (3.5, 5.0)]
     runs = []
     for graph in (True, False):
         ctxs = [crmc.Context(w) for w in ws]
+        if da:
+            for g in ctxs:
+                g.set_surrogate(W.random_mlp(seed=16, out_gain=1.5))
         b = crmc.Batch(ctxs)
         b.set_persistent(mode)
-        b.set_launch_shape(64, 0)
+        b.set_launch_shape(128 if da else 64, 0)  # a shape of both sets: no tuning, so the graphs run
         step = 0
         for it in range(3):
             for g in ctxs:  # reload each replica's own state: the forces become stale
@@ -149,12 +153,15 @@ def test_graph_cycle_after_a_load_equals_calls(crmc, mode):
                 g.load(st["n"], *[np.ascontiguousarray(st[k]) for k in ("xyz", "vel", "type", "cls", "state")])
             if graph:
                 ctxs[0].timing(reset=True)
-                b.cycle(2, 0.005, 1.0, 100 + step, 500 + step)
+                b.cycle(2, 0.005, 1.0, 100 + step, 500 + step, da=da)
                 assert ctxs[0].timing(reset=True)["launches"] > 0
             else:
                 for s in range(2):
                     b.md_begin(0.005, 1.0, 500 + step + s)
-                    b.sweep(1, 100 + step + s)
+                    if da:
+                        b.sweep_da(1, 100 + step + s)
+                    else:
+                        b.sweep(1, 100 + step + s)
                     b.md_end(0.005, 1.0, 500 + step + s)
             step += 2
         for g in ctxs:
